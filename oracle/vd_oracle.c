@@ -1,0 +1,972 @@
+/*
+ * FP64 CPU oracle for the VolumeDeform lattice solve (arXiv 1603.08161).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline load this library; the product path never does.  It shares no code, header,
+ * table or helper with the CUDA implementation.
+ *
+ * Everything is computed in double precision, plainly and slowly, in the order the
+ * paper states it:
+ *   - space deformation S(x) = R [sum_i alpha_i(x) t_i] + t, trilinear alpha  (Sec. 4)
+ *   - projective association with Phi_r(x) = 1 - x/eps_r and
+ *     w_c = ((Phi_d + Phi_n + Phi_v)/3)^2, pruned if any Phi < 0          (Sec. 5.1)
+ *   - E_total = w_s E_sparse + w_d E_dense + w_r E_reg                     (Eq. 1)
+ *   - point-to-plane E_dense (Eq. 2), feature E_sparse (Eq. 3), ARAP E_reg (Eq. 4)
+ *   - flip-flop: positions with rotations fixed, then rotations with positions
+ *     fixed (Sec. 7.1); positions by preconditioned CG on the normal equations
+ *     (L + B^T B) t = b, rotations by Procrustes/SVD per grid point (Sec. 7.1)
+ *
+ * The Gauss-Newton system is built from an explicitly assembled sparse Jacobian J
+ * (one row per dense residual, three per sparse pair, three per directed lattice
+ * edge), applied as J^T (J p).  The rotation step uses a one-sided (Hestenes) Jacobi
+ * SVD of the 3x3 cross-covariance (Golub & Van Loan, Matrix Computations, 4th ed.,
+ * Sec. 8.6.3).
+ *
+ * Readings of points the paper leaves open (all documented with the build):
+ *   - unknowns are displacements u_i = t_i - t^_i; node i = x + nx (y + ny z);
+ *     t^_i = origin + h (x, y, z);
+ *   - one-ring N_i = 6-neighbourhood restricted to M; both directions of an edge
+ *     are kept (i->j uses R_i, j->i uses R_j);
+ *   - M = corners of cells holding a sample or a sparse point, dilated by the
+ *     6-neighbourhood (surface mode), or every node (all mode);
+ *   - nearest pixel = floor(x + 0.5); target normal by central differences of the
+ *     back-projected depth, oriented towards the camera; v = unit vector from the
+ *     point to the camera centre; model normal n_c = normalise(R sum_k alpha_k R_k n^_c);
+ *   - PCG: x0 = 0 on the increment, scalar Jacobi preconditioner (1/diag, 0 where the
+ *     diagonal is 0), exactly K iterations unless p.Ap <= 0, rho = 0 or
+ *     rho' <= tol^2 rho0;
+ *   - a rotation is kept unchanged (and counted) when its neighbours span fewer than
+ *     two lattice axes, when sigma_2 <= 1e-12 sigma_1, or when det < 0 and
+ *     sigma_2 - sigma_3 <= 1e-12 sigma_1 (the best rotation is then not unique).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define VDO_ACTIVE_SURFACE 0
+#define VDO_ACTIVE_ALL 1
+
+typedef struct {
+    int nrows, cap_rows;
+    long nnz, cap_nnz;
+    long *row_ptr;       /* nrows + 1 */
+    int *col;
+    double *val;
+    double *res;         /* residual of each row */
+} csr_t;
+
+typedef struct vdo_ctx {
+    /* lattice (Sec. 4) */
+    int nx, ny, nz, nn;
+    double o[3], h;
+    int active_mode;
+    /* frame */
+    int W, H;
+    double fx, fy, cx, cy;
+    double Rg[9], tg[3];
+    double *depth;                       /* H*W */
+    double *V, *Nm;                      /* H*W*3 target vertex / normal maps */
+    unsigned char *nvalid;               /* H*W */
+    int C;
+    double *sp, *sn;                     /* C*3 canonical samples / normals */
+    int *cell_c;                         /* C: lower-corner node of the cell or -1 */
+    double *frac_c;                      /* C*3 */
+    int S;
+    double *fh, *ft;                     /* S*3 canonical / observed feature points */
+    int *cell_s;
+    double *frac_s;
+    /* active set M */
+    unsigned char *inM;                  /* nn */
+    int *slot;                           /* nn: unknown index or -1 */
+    int N;
+    /* state: displacement and rotation of every node */
+    double *u;                           /* nn*3 */
+    double *R;                           /* nn*9, row-major */
+    /* association (Sec. 5.1) */
+    int *pix;                            /* C: py*W+px or -1 */
+    double *wc;                          /* C */
+    double *pa, *na;                     /* C*3 target point and normal */
+    int n_valid;
+    int have_assoc;
+    /* weights and thresholds */
+    double w_s, w_d, w_r, eps_d, eps_n, eps_v;
+    /* Jacobian */
+    csr_t J;
+    int have_J;
+} vdo_ctx;
+
+/* ------------------------------------------------------------------ helpers */
+
+static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
+
+static int node_id(const vdo_ctx *c, int x, int y, int z) { return x + c->nx * (y + c->ny * z); }
+
+static void node_xyz(const vdo_ctx *c, int i, int *x, int *y, int *z)
+{
+    *x = i % c->nx;
+    *y = (i / c->nx) % c->ny;
+    *z = i / (c->nx * c->ny);
+}
+
+static void node_pos(const vdo_ctx *c, int i, double p[3])       /* t^_i */
+{
+    int x, y, z;
+    node_xyz(c, i, &x, &y, &z);
+    p[0] = c->o[0] + c->h * x;
+    p[1] = c->o[1] + c->h * y;
+    p[2] = c->o[2] + c->h * z;
+}
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void matvec3(const double *M, const double *v, double *out)  /* row-major M v */
+{
+    for (int r = 0; r < 3; r++) out[r] = M[3 * r] * v[0] + M[3 * r + 1] * v[1] + M[3 * r + 2] * v[2];
+}
+
+static void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* 6-neighbourhood offsets: -x, +x, -y, +y, -z, +z */
+static const int NB_D[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+
+static int neighbour(const vdo_ctx *c, int i, int k)   /* node index or -1 */
+{
+    int x, y, z;
+    node_xyz(c, i, &x, &y, &z);
+    x += NB_D[k][0];
+    y += NB_D[k][1];
+    z += NB_D[k][2];
+    if (x < 0 || y < 0 || z < 0 || x >= c->nx || y >= c->ny || z >= c->nz) return -1;
+    return node_id(c, x, y, z);
+}
+
+/* Cell of a point and its trilinear fractions (Sec. 4).  The cell is named by its
+ * lower corner node; points whose cell would need a node outside the lattice get -1. */
+static int locate(const vdo_ctx *c, const double p[3], double frac[3])
+{
+    int ci[3];
+    int dims[3] = {c->nx, c->ny, c->nz};
+    for (int a = 0; a < 3; a++) {
+        double q = (p[a] - c->o[a]) / c->h;
+        double fl = floor(q);
+        if (!(fl >= 0.0) || fl > (double)(dims[a] - 2)) return -1;
+        ci[a] = (int)fl;
+        frac[a] = q - fl;
+    }
+    return node_id(c, ci[0], ci[1], ci[2]);
+}
+
+/* the 8 corners k = (dx, dy, dz) of a cell and their weights alpha_k */
+static void corners(const vdo_ctx *c, int cell, const double f[3], int node[8], double alpha[8])
+{
+    for (int k = 0; k < 8; k++) {
+        int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        node[k] = cell + dx + c->nx * (dy + c->ny * dz);
+        alpha[k] = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+    }
+}
+
+/* S(x) = R_g [sum_k alpha_k t_k] + t_g with t_k = t^_k + u_k (Sec. 4) */
+static void deform(const vdo_ctx *c, int cell, const double f[3], double out[3])
+{
+    int nd[8];
+    double al[8], acc[3] = {0, 0, 0}, tk[3];
+    corners(c, cell, f, nd, al);
+    for (int k = 0; k < 8; k++) {
+        node_pos(c, nd[k], tk);
+        for (int a = 0; a < 3; a++) acc[a] += al[k] * (tk[a] + c->u[3 * nd[k] + a]);
+    }
+    matvec3(c->Rg, acc, out);
+    for (int a = 0; a < 3; a++) out[a] += c->tg[a];
+}
+
+/* ------------------------------------------------------------------ lifetime */
+
+vdo_ctx *vdo_create(int nx, int ny, int nz, const float origin[3], float h, int active_mode)
+{
+    if (nx < 2 || ny < 2 || nz < 2 || !(h > 0.0f)) return NULL;
+    vdo_ctx *c = (vdo_ctx *)xcalloc(1, sizeof(vdo_ctx));
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->nn = nx * ny * nz;
+    for (int a = 0; a < 3; a++) c->o[a] = (double)origin[a];
+    c->h = (double)h;
+    c->active_mode = active_mode;
+    c->u = (double *)xcalloc((size_t)c->nn * 3, sizeof(double));
+    c->R = (double *)xcalloc((size_t)c->nn * 9, sizeof(double));
+    for (int i = 0; i < c->nn; i++) c->R[9 * i] = c->R[9 * i + 4] = c->R[9 * i + 8] = 1.0;
+    c->inM = (unsigned char *)xcalloc((size_t)c->nn, 1);
+    c->slot = (int *)xcalloc((size_t)c->nn, sizeof(int));
+    for (int a = 0; a < 9; a++) c->Rg[a] = (a % 4 == 0) ? 1.0 : 0.0;
+    c->w_s = 10.0; c->w_d = 1.0; c->w_r = 1.0;
+    c->eps_d = 0.05; c->eps_n = 0.5; c->eps_v = 0.8;
+    return c;
+}
+
+static void free_frame(vdo_ctx *c)
+{
+    free(c->depth); free(c->V); free(c->Nm); free(c->nvalid);
+    free(c->sp); free(c->sn); free(c->cell_c); free(c->frac_c);
+    free(c->pix); free(c->wc); free(c->pa); free(c->na);
+    c->depth = c->V = c->Nm = c->sp = c->sn = c->frac_c = c->wc = c->pa = c->na = NULL;
+    c->nvalid = NULL; c->cell_c = c->pix = NULL;
+}
+
+static void free_J(csr_t *J)
+{
+    free(J->row_ptr); free(J->col); free(J->val); free(J->res);
+    memset(J, 0, sizeof(*J));
+}
+
+void vdo_destroy(vdo_ctx *c)
+{
+    if (!c) return;
+    free_frame(c);
+    free(c->fh); free(c->ft); free(c->cell_s); free(c->frac_s);
+    free(c->u); free(c->R); free(c->inM); free(c->slot);
+    free_J(&c->J);
+    free(c);
+}
+
+void vdo_set_params(vdo_ctx *c, double w_s, double w_d, double w_r,
+                    double eps_d, double eps_n, double eps_v)
+{
+    c->w_s = w_s; c->w_d = w_d; c->w_r = w_r;
+    c->eps_d = eps_d; c->eps_n = eps_n; c->eps_v = eps_v;
+    c->have_assoc = 0;
+    c->have_J = 0;
+}
+
+/* ------------------------------------------------------------------ active set */
+
+static void build_active(vdo_ctx *c)
+{
+    memset(c->inM, 0, (size_t)c->nn);
+    if (c->active_mode == VDO_ACTIVE_ALL) {
+        memset(c->inM, 1, (size_t)c->nn);
+    } else {
+        /* corners of every cell that holds a sample or a sparse point ... */
+        unsigned char *mark = (unsigned char *)xcalloc((size_t)c->nn, 1);
+        int nd[8];
+        double al[8];
+        for (int s = 0; s < c->C; s++)
+            if (c->cell_c[s] >= 0) {
+                corners(c, c->cell_c[s], c->frac_c + 3 * s, nd, al);
+                for (int k = 0; k < 8; k++) mark[nd[k]] = 1;
+            }
+        for (int s = 0; s < c->S; s++)
+            if (c->cell_s[s] >= 0) {
+                corners(c, c->cell_s[s], c->frac_s + 3 * s, nd, al);
+                for (int k = 0; k < 8; k++) mark[nd[k]] = 1;
+            }
+        /* ... plus their one-ring (Sec. 6: "the isosurface plus its one-ring") */
+        for (int i = 0; i < c->nn; i++) {
+            int on = mark[i];
+            for (int k = 0; k < 6 && !on; k++) {
+                int j = neighbour(c, i, k);
+                if (j >= 0 && mark[j]) on = 1;
+            }
+            c->inM[i] = (unsigned char)on;
+        }
+        free(mark);
+    }
+    c->N = 0;
+    for (int i = 0; i < c->nn; i++) c->slot[i] = c->inM[i] ? c->N++ : -1;
+}
+
+/* ------------------------------------------------------------------ frame input */
+
+int vdo_set_frame(vdo_ctx *c, const float *depth, int W, int H, const float K[4], const float *pose,
+                  const float *src_p, const float *src_n, int C)
+{
+    if (W < 0 || H < 0 || C < 0) return 1;
+    free_frame(c);
+    c->W = W; c->H = H;
+    c->fx = K[0]; c->fy = K[1]; c->cx = K[2]; c->cy = K[3];
+    for (int a = 0; a < 9; a++) c->Rg[a] = pose ? (double)pose[a] : ((a % 4 == 0) ? 1.0 : 0.0);
+    for (int a = 0; a < 3; a++) c->tg[a] = pose ? (double)pose[9 + a] : 0.0;
+    size_t np = (size_t)W * H;
+    c->depth = (double *)xcalloc(np, sizeof(double));
+    for (size_t k = 0; k < np; k++) c->depth[k] = (double)depth[k];
+
+    /* target vertex map V and normal map (central differences, facing the camera) */
+    c->V = (double *)xcalloc(np * 3, sizeof(double));
+    c->Nm = (double *)xcalloc(np * 3, sizeof(double));
+    c->nvalid = (unsigned char *)xcalloc(np, 1);
+    for (int v = 0; v < H; v++)
+        for (int uu = 0; uu < W; uu++) {
+            double d = c->depth[(size_t)v * W + uu];
+            double *P = c->V + 3 * ((size_t)v * W + uu);
+            P[0] = d * ((uu - c->cx) / c->fx);
+            P[1] = d * ((v - c->cy) / c->fy);
+            P[2] = d;
+        }
+    for (int v = 1; v + 1 < H; v++)
+        for (int uu = 1; uu + 1 < W; uu++) {
+            size_t k = (size_t)v * W + uu;
+            if (c->depth[k] <= 0 || c->depth[k - 1] <= 0 || c->depth[k + 1] <= 0 ||
+                c->depth[k - W] <= 0 || c->depth[k + W] <= 0)
+                continue;
+            double dx[3], dy[3], n[3];
+            for (int a = 0; a < 3; a++) {
+                dx[a] = c->V[3 * (k + 1) + a] - c->V[3 * (k - 1) + a];
+                dy[a] = c->V[3 * (k + W) + a] - c->V[3 * (k - W) + a];
+            }
+            cross3(dx, dy, n);
+            double L = sqrt(dot3(n, n));
+            if (!(L > 0)) continue;
+            for (int a = 0; a < 3; a++) n[a] /= L;
+            if (dot3(n, c->V + 3 * k) > 0)
+                for (int a = 0; a < 3; a++) n[a] = -n[a];
+            for (int a = 0; a < 3; a++) c->Nm[3 * k + a] = n[a];
+            c->nvalid[k] = 1;
+        }
+
+    c->C = C;
+    c->sp = (double *)xcalloc((size_t)C * 3, sizeof(double));
+    c->sn = (double *)xcalloc((size_t)C * 3, sizeof(double));
+    c->cell_c = (int *)xcalloc((size_t)C, sizeof(int));
+    c->frac_c = (double *)xcalloc((size_t)C * 3, sizeof(double));
+    c->pix = (int *)xcalloc((size_t)C, sizeof(int));
+    c->wc = (double *)xcalloc((size_t)C, sizeof(double));
+    c->pa = (double *)xcalloc((size_t)C * 3, sizeof(double));
+    c->na = (double *)xcalloc((size_t)C * 3, sizeof(double));
+    for (int s = 0; s < C; s++) {
+        for (int a = 0; a < 3; a++) {
+            c->sp[3 * s + a] = src_p[3 * s + a];
+            c->sn[3 * s + a] = src_n[3 * s + a];
+        }
+        c->cell_c[s] = locate(c, c->sp + 3 * s, c->frac_c + 3 * s);
+    }
+    if (!c->fh) c->S = 0;
+    build_active(c);
+    c->have_assoc = 0;
+    c->have_J = 0;
+    return 0;
+}
+
+int vdo_set_correspondences(vdo_ctx *c, const float *canon, const float *target, int S)
+{
+    if (S < 0) return 1;
+    free(c->fh); free(c->ft); free(c->cell_s); free(c->frac_s);
+    c->S = S;
+    c->fh = (double *)xcalloc((size_t)S * 3, sizeof(double));
+    c->ft = (double *)xcalloc((size_t)S * 3, sizeof(double));
+    c->cell_s = (int *)xcalloc((size_t)S, sizeof(int));
+    c->frac_s = (double *)xcalloc((size_t)S * 3, sizeof(double));
+    for (int s = 0; s < S; s++) {
+        for (int a = 0; a < 3; a++) {
+            c->fh[3 * s + a] = canon[3 * s + a];
+            c->ft[3 * s + a] = target[3 * s + a];
+        }
+        c->cell_s[s] = locate(c, c->fh + 3 * s, c->frac_s + 3 * s);
+    }
+    if (c->cell_c || c->C == 0) build_active(c);
+    c->have_J = 0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ state access */
+
+void vdo_set_warp(vdo_ctx *c, const double *u, const double *R)
+{
+    if (u) memcpy(c->u, u, sizeof(double) * 3 * (size_t)c->nn);
+    else memset(c->u, 0, sizeof(double) * 3 * (size_t)c->nn);
+    if (R) memcpy(c->R, R, sizeof(double) * 9 * (size_t)c->nn);
+    else {
+        memset(c->R, 0, sizeof(double) * 9 * (size_t)c->nn);
+        for (int i = 0; i < c->nn; i++) c->R[9 * i] = c->R[9 * i + 4] = c->R[9 * i + 8] = 1.0;
+    }
+    c->have_J = 0;
+}
+
+void vdo_get_warp(const vdo_ctx *c, double *u, double *R)
+{
+    if (u) memcpy(u, c->u, sizeof(double) * 3 * (size_t)c->nn);
+    if (R) memcpy(R, c->R, sizeof(double) * 9 * (size_t)c->nn);
+}
+
+int vdo_num_active(const vdo_ctx *c) { return c->N; }
+
+void vdo_get_active(const vdo_ctx *c, unsigned char *mask) { memcpy(mask, c->inM, (size_t)c->nn); }
+
+void vdo_target_maps(const vdo_ctx *c, double *V, double *Nm, unsigned char *valid)
+{
+    size_t np = (size_t)c->W * c->H;
+    if (V) memcpy(V, c->V, sizeof(double) * 3 * np);
+    if (Nm) memcpy(Nm, c->Nm, sizeof(double) * 3 * np);
+    if (valid) memcpy(valid, c->nvalid, np);
+}
+
+void vdo_sample_cells(const vdo_ctx *c, int *cell, double *frac)
+{
+    if (cell) memcpy(cell, c->cell_c, sizeof(int) * (size_t)c->C);
+    if (frac) memcpy(frac, c->frac_c, sizeof(double) * 3 * (size_t)c->C);
+}
+
+/* ------------------------------------------------------------------ association */
+
+/* Projective association of every sample at the current warp (Sec. 5.1).  Returns
+ * the number of samples with w_c > 0. */
+int vdo_associate(vdo_ctx *c)
+{
+    int nvalid = 0;
+    for (int s = 0; s < c->C; s++) {
+        c->pix[s] = -1;
+        c->wc[s] = 0.0;
+        for (int a = 0; a < 3; a++) c->pa[3 * s + a] = c->na[3 * s + a] = 0.0;
+        int cell = c->cell_c[s];
+        if (cell < 0) continue;
+        double p[3], n[3], acc[3] = {0, 0, 0}, rn[3];
+        deform(c, cell, c->frac_c + 3 * s, p);
+        /* model normal: R_g sum_k alpha_k R_k n^_c, normalised */
+        int nd[8];
+        double al[8];
+        corners(c, cell, c->frac_c + 3 * s, nd, al);
+        for (int k = 0; k < 8; k++) {
+            matvec3(c->R + 9 * nd[k], c->sn + 3 * s, rn);
+            for (int a = 0; a < 3; a++) acc[a] += al[k] * rn[a];
+        }
+        matvec3(c->Rg, acc, n);
+        double nl = sqrt(dot3(n, n));
+        if (!(nl > 0)) continue;
+        for (int a = 0; a < 3; a++) n[a] /= nl;
+        if (!(p[2] > 0)) continue;
+        double uf = c->fx * p[0] / p[2] + c->cx;
+        double vf = c->fy * p[1] / p[2] + c->cy;
+        double px = floor(uf + 0.5), py = floor(vf + 0.5);
+        if (!(px >= 0 && px < c->W && py >= 0 && py < c->H)) continue;
+        size_t k = (size_t)py * c->W + (size_t)px;
+        if (!(c->depth[k] > 0) || !c->nvalid[k]) continue;
+        const double *pa = c->V + 3 * k, *na = c->Nm + 3 * k;
+        double diff[3] = {p[0] - pa[0], p[1] - pa[1], p[2] - pa[2]};
+        double pl = sqrt(dot3(p, p));
+        double view[3] = {-p[0] / pl, -p[1] / pl, -p[2] / pl};
+        double phi_d = 1.0 - sqrt(dot3(diff, diff)) / c->eps_d;
+        double phi_n = 1.0 - (1.0 - dot3(n, na)) / c->eps_n;
+        double phi_v = 1.0 - (1.0 - dot3(n, view)) / c->eps_v;
+        c->pix[s] = (int)k;
+        for (int a = 0; a < 3; a++) {
+            c->pa[3 * s + a] = pa[a];
+            c->na[3 * s + a] = na[a];
+        }
+        if (phi_d < 0 || phi_n < 0 || phi_v < 0) continue;
+        double m = (phi_d + phi_n + phi_v) / 3.0;
+        c->wc[s] = m * m;
+        nvalid++;
+    }
+    c->n_valid = nvalid;
+    c->have_assoc = 1;
+    c->have_J = 0;
+    return nvalid;
+}
+
+void vdo_get_association(const vdo_ctx *c, int *pix, double *w, double *r)
+{
+    for (int s = 0; s < c->C; s++) {
+        if (pix) pix[s] = c->pix[s];
+        if (w) w[s] = c->wc[s];
+        if (r) {
+            r[s] = 0.0;
+            if (c->wc[s] > 0) {
+                double p[3];
+                deform(c, c->cell_c[s], c->frac_c + 3 * s, p);
+                double d[3] = {p[0] - c->pa[3 * s], p[1] - c->pa[3 * s + 1], p[2] - c->pa[3 * s + 2]};
+                r[s] = sqrt(c->w_d * c->wc[s]) * dot3(d, c->na + 3 * s);
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ energy (Eq. 1-4) */
+
+void vdo_energy(const vdo_ctx *c, double out[4])
+{
+    double ed = 0, es = 0, er = 0;
+    for (int s = 0; s < c->C && c->have_assoc; s++) {
+        if (!(c->wc[s] > 0)) continue;
+        double p[3];
+        deform(c, c->cell_c[s], c->frac_c + 3 * s, p);
+        double d[3] = {p[0] - c->pa[3 * s], p[1] - c->pa[3 * s + 1], p[2] - c->pa[3 * s + 2]};
+        double e = dot3(d, c->na + 3 * s);
+        ed += c->wc[s] * e * e;                                          /* Eq. 2 */
+    }
+    for (int s = 0; s < c->S; s++) {
+        if (c->cell_s[s] < 0) continue;
+        double p[3];
+        deform(c, c->cell_s[s], c->frac_s + 3 * s, p);
+        for (int a = 0; a < 3; a++) es += (p[a] - c->ft[3 * s + a]) * (p[a] - c->ft[3 * s + a]);  /* Eq. 3 */
+    }
+    for (int i = 0; i < c->nn; i++) {                                    /* Eq. 4 */
+        if (!c->inM[i]) continue;
+        double ti[3], hi[3];
+        node_pos(c, i, hi);
+        for (int a = 0; a < 3; a++) ti[a] = hi[a] + c->u[3 * i + a];
+        for (int k = 0; k < 6; k++) {
+            int j = neighbour(c, i, k);
+            if (j < 0 || !c->inM[j]) continue;
+            double tj[3], hj[3], e[3], Re[3];
+            node_pos(c, j, hj);
+            for (int a = 0; a < 3; a++) {
+                tj[a] = hj[a] + c->u[3 * j + a];
+                e[a] = hi[a] - hj[a];
+            }
+            matvec3(c->R + 9 * i, e, Re);
+            for (int a = 0; a < 3; a++) {
+                double q = (ti[a] - tj[a]) - Re[a];
+                er += q * q;
+            }
+        }
+    }
+    out[1] = ed;
+    out[2] = es;
+    out[3] = er;
+    out[0] = c->w_s * es + c->w_d * ed + c->w_r * er;                   /* Eq. 1 */
+}
+
+/* ------------------------------------------------------------------ Jacobian */
+
+static void J_reserve(csr_t *J, int rows, long nnz)
+{
+    if (rows + 1 > J->cap_rows) {
+        J->cap_rows = 2 * (rows + 1) + 16;
+        J->row_ptr = (long *)realloc(J->row_ptr, sizeof(long) * (size_t)J->cap_rows);
+        J->res = (double *)realloc(J->res, sizeof(double) * (size_t)J->cap_rows);
+    }
+    if (nnz > J->cap_nnz) {
+        J->cap_nnz = 2 * nnz + 64;
+        J->col = (int *)realloc(J->col, sizeof(int) * (size_t)J->cap_nnz);
+        J->val = (double *)realloc(J->val, sizeof(double) * (size_t)J->cap_nnz);
+    }
+}
+
+static void J_begin_row(csr_t *J, double res)
+{
+    J_reserve(J, J->nrows + 1, J->nnz);
+    J->row_ptr[J->nrows] = J->nnz;
+    J->res[J->nrows] = res;
+}
+
+static void J_entry(csr_t *J, int col, double v)
+{
+    J_reserve(J, J->nrows + 1, J->nnz + 1);
+    J->col[J->nnz] = col;
+    J->val[J->nnz] = v;
+    J->nnz++;
+}
+
+static void J_end_row(csr_t *J)
+{
+    J->nrows++;
+    J_reserve(J, J->nrows + 1, J->nnz);
+    J->row_ptr[J->nrows] = J->nnz;
+}
+
+/* Residual vector r and Jacobian J of E_total w.r.t. the displacements of M at the
+ * current warp, with association and rotations held fixed (Sec. 7.1, position step). */
+static void build_J(vdo_ctx *c)
+{
+    csr_t *J = &c->J;
+    J->nrows = 0;
+    J->nnz = 0;
+    J_reserve(J, 1, 0);
+    J->row_ptr[0] = 0;
+    int nd[8];
+    double al[8];
+    /* dense point-to-plane rows (Eq. 2): sqrt(w_d w_c) n^a . (S(p^c) - p^a) */
+    for (int s = 0; s < c->C; s++) {
+        if (!(c->wc[s] > 0)) continue;
+        double p[3], g[3], sw = sqrt(c->w_d * c->wc[s]);
+        deform(c, c->cell_c[s], c->frac_c + 3 * s, p);
+        double d[3] = {p[0] - c->pa[3 * s], p[1] - c->pa[3 * s + 1], p[2] - c->pa[3 * s + 2]};
+        const double *na = c->na + 3 * s;
+        for (int a = 0; a < 3; a++)                                  /* R_g^T n^a */
+            g[a] = c->Rg[a] * na[0] + c->Rg[3 + a] * na[1] + c->Rg[6 + a] * na[2];
+        J_begin_row(J, sw * dot3(d, na));
+        corners(c, c->cell_c[s], c->frac_c + 3 * s, nd, al);
+        for (int k = 0; k < 8; k++)
+            for (int a = 0; a < 3; a++) J_entry(J, 3 * c->slot[nd[k]] + a, sw * al[k] * g[a]);
+        J_end_row(J);
+    }
+    /* sparse feature rows (Eq. 3): sqrt(w_s) (S(f^s) - f_s) */
+    double sws = sqrt(c->w_s);
+    for (int s = 0; s < c->S; s++) {
+        if (c->cell_s[s] < 0) continue;
+        double p[3];
+        deform(c, c->cell_s[s], c->frac_s + 3 * s, p);
+        corners(c, c->cell_s[s], c->frac_s + 3 * s, nd, al);
+        for (int e = 0; e < 3; e++) {
+            J_begin_row(J, sws * (p[e] - c->ft[3 * s + e]));
+            for (int k = 0; k < 8; k++)
+                for (int a = 0; a < 3; a++) J_entry(J, 3 * c->slot[nd[k]] + a, sws * al[k] * c->Rg[3 * e + a]);
+            J_end_row(J);
+        }
+    }
+    /* ARAP rows (Eq. 4), one triple per directed edge i -> j inside M */
+    double swr = sqrt(c->w_r);
+    for (int i = 0; i < c->nn; i++) {
+        if (!c->inM[i]) continue;
+        double hi[3];
+        node_pos(c, i, hi);
+        for (int k = 0; k < 6; k++) {
+            int j = neighbour(c, i, k);
+            if (j < 0 || !c->inM[j]) continue;
+            double hj[3], e[3], Re[3];
+            node_pos(c, j, hj);
+            for (int a = 0; a < 3; a++) e[a] = hi[a] - hj[a];
+            matvec3(c->R + 9 * i, e, Re);
+            for (int a = 0; a < 3; a++) {
+                double q = (hi[a] + c->u[3 * i + a]) - (hj[a] + c->u[3 * j + a]) - Re[a];
+                J_begin_row(J, swr * q);
+                J_entry(J, 3 * c->slot[i] + a, swr);
+                J_entry(J, 3 * c->slot[j] + a, -swr);
+                J_end_row(J);
+            }
+        }
+    }
+    c->have_J = 1;
+}
+
+static void ensure_J(vdo_ctx *c)
+{
+    if (!c->have_assoc) vdo_associate(c);
+    if (!c->have_J) build_J(c);
+}
+
+/* y = J^T (J x) on the unknowns (length 3N) */
+static void apply_JtJ(const csr_t *J, const double *x, double *y, int n3, double *tmp)
+{
+    for (int r = 0; r < J->nrows; r++) {
+        double acc = 0;
+        for (long k = J->row_ptr[r]; k < J->row_ptr[r + 1]; k++) acc += J->val[k] * x[J->col[k]];
+        tmp[r] = acc;
+    }
+    memset(y, 0, sizeof(double) * (size_t)n3);
+    for (int r = 0; r < J->nrows; r++)
+        for (long k = J->row_ptr[r]; k < J->row_ptr[r + 1]; k++) y[J->col[k]] += J->val[k] * tmp[r];
+}
+
+static void scatter_nodes(const vdo_ctx *c, const double *xs, double *full)   /* 3N -> 3nn */
+{
+    memset(full, 0, sizeof(double) * 3 * (size_t)c->nn);
+    for (int i = 0; i < c->nn; i++)
+        if (c->slot[i] >= 0)
+            for (int a = 0; a < 3; a++) full[3 * i + a] = xs[3 * c->slot[i] + a];
+}
+
+static void gather_nodes(const vdo_ctx *c, const double *full, double *xs)    /* 3nn -> 3N */
+{
+    for (int i = 0; i < c->nn; i++)
+        if (c->slot[i] >= 0)
+            for (int a = 0; a < 3; a++) xs[3 * c->slot[i] + a] = full[3 * i + a];
+}
+
+/* b = -J^T r and the diagonal of J^T J, as full-lattice arrays (0 outside M) */
+void vdo_rhs(vdo_ctx *c, double *b, double *diag)
+{
+    ensure_J(c);
+    int n3 = 3 * c->N;
+    double *bs = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *ds = (double *)xcalloc((size_t)n3, sizeof(double));
+    const csr_t *J = &c->J;
+    for (int r = 0; r < J->nrows; r++)
+        for (long k = J->row_ptr[r]; k < J->row_ptr[r + 1]; k++) {
+            bs[J->col[k]] -= J->val[k] * J->res[r];
+            ds[J->col[k]] += J->val[k] * J->val[k];
+        }
+    if (b) scatter_nodes(c, bs, b);
+    if (diag) scatter_nodes(c, ds, diag);
+    free(bs);
+    free(ds);
+}
+
+void vdo_apply(vdo_ctx *c, const double *p, double *Ap)
+{
+    ensure_J(c);
+    int n3 = 3 * c->N;
+    double *ps = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *qs = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *tmp = (double *)xcalloc((size_t)c->J.nrows, sizeof(double));
+    gather_nodes(c, p, ps);
+    apply_JtJ(&c->J, ps, qs, n3, tmp);
+    scatter_nodes(c, qs, Ap);
+    free(ps); free(qs); free(tmp);
+}
+
+/* Jacobi-preconditioned CG on J^T J delta = -J^T r, x0 = 0 (Sec. 7.1).  Writes the
+ * increment for every node (0 outside M); returns the number of iterations done.
+ * rho_hist (optional, K+1 entries) receives r.z before each iteration. */
+int vdo_pcg(vdo_ctx *c, int K, double tol, double *delta, double *rho_hist)
+{
+    ensure_J(c);
+    int n3 = 3 * c->N;
+    const csr_t *J = &c->J;
+    double *x = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *r = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *z = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *p = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *q = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *Minv = (double *)xcalloc((size_t)n3, sizeof(double));
+    double *tmp = (double *)xcalloc((size_t)J->nrows, sizeof(double));
+    for (int rr = 0; rr < J->nrows; rr++)
+        for (long k = J->row_ptr[rr]; k < J->row_ptr[rr + 1]; k++) {
+            r[J->col[k]] -= J->val[k] * J->res[rr];         /* b = -J^T r */
+            Minv[J->col[k]] += J->val[k] * J->val[k];       /* diag(J^T J) */
+        }
+    for (int k = 0; k < n3; k++) Minv[k] = Minv[k] > 0 ? 1.0 / Minv[k] : 0.0;
+    double rho = 0;
+    for (int k = 0; k < n3; k++) {
+        z[k] = Minv[k] * r[k];
+        p[k] = z[k];
+        rho += r[k] * z[k];
+    }
+    double rho0 = rho;
+    int it = 0;
+    for (; it < K; it++) {
+        if (rho_hist) rho_hist[it] = rho;
+        if (!(rho > 0)) break;
+        apply_JtJ(J, p, q, n3, tmp);
+        double pq = 0;
+        for (int k = 0; k < n3; k++) pq += p[k] * q[k];
+        if (!(pq > 0)) break;
+        double alpha = rho / pq;
+        double rho1 = 0;
+        for (int k = 0; k < n3; k++) {
+            x[k] += alpha * p[k];
+            r[k] -= alpha * q[k];
+            z[k] = Minv[k] * r[k];
+            rho1 += r[k] * z[k];
+        }
+        if (rho1 <= tol * tol * rho0) {
+            rho = rho1;
+            it++;
+            break;
+        }
+        double beta = rho1 / rho;
+        for (int k = 0; k < n3; k++) p[k] = z[k] + beta * p[k];
+        rho = rho1;
+    }
+    if (rho_hist) rho_hist[it] = rho;
+    scatter_nodes(c, x, delta);
+    free(x); free(r); free(z); free(p); free(q); free(Minv); free(tmp);
+    return it;
+}
+
+/* Exact solution of J^T J delta = -J^T r by dense Cholesky (tiny lattices only).
+ * Returns 0 on success, 1 if the matrix is not positive definite. */
+int vdo_cholesky(vdo_ctx *c, double *delta)
+{
+    ensure_J(c);
+    int n = 3 * c->N;
+    const csr_t *J = &c->J;
+    double *A = (double *)xcalloc((size_t)n * n, sizeof(double));
+    double *b = (double *)xcalloc((size_t)n, sizeof(double));
+    for (int r = 0; r < J->nrows; r++)
+        for (long k = J->row_ptr[r]; k < J->row_ptr[r + 1]; k++) {
+            b[J->col[k]] -= J->val[k] * J->res[r];
+            for (long m = J->row_ptr[r]; m < J->row_ptr[r + 1]; m++)
+                A[(size_t)J->col[k] * n + J->col[m]] += J->val[k] * J->val[m];
+        }
+    int bad = 0;
+    for (int j = 0; j < n && !bad; j++) {                 /* A = L L^T, L in the lower half */
+        double s = A[(size_t)j * n + j];
+        for (int k = 0; k < j; k++) s -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+        if (!(s > 0)) { bad = 1; break; }
+        double Ljj = sqrt(s);
+        A[(size_t)j * n + j] = Ljj;
+        for (int i = j + 1; i < n; i++) {
+            double t = A[(size_t)i * n + j];
+            for (int k = 0; k < j; k++) t -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+            A[(size_t)i * n + j] = t / Ljj;
+        }
+    }
+    if (!bad) {
+        for (int i = 0; i < n; i++) {                      /* L y = b */
+            double t = b[i];
+            for (int k = 0; k < i; k++) t -= A[(size_t)i * n + k] * b[k];
+            b[i] = t / A[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; i--) {                 /* L^T x = y */
+            double t = b[i];
+            for (int k = i + 1; k < n; k++) t -= A[(size_t)k * n + i] * b[k];
+            b[i] = t / A[(size_t)i * n + i];
+        }
+        scatter_nodes(c, b, delta);
+    }
+    free(A);
+    free(b);
+    return bad;
+}
+
+void vdo_add_increment(vdo_ctx *c, const double *delta)
+{
+    for (int i = 0; i < c->nn; i++)
+        if (c->inM[i])
+            for (int a = 0; a < 3; a++) c->u[3 * i + a] += delta[3 * i + a];
+    c->have_J = 0;
+}
+
+/* ------------------------------------------------------------------ rotation step */
+
+/* One-sided Jacobi SVD of a 3x3 matrix A = U diag(s) V^T, s descending. */
+void vdo_svd3(const double *A, double *U, double *s, double *V)
+{
+    double B[9];
+    memcpy(B, A, sizeof(B));
+    for (int k = 0; k < 9; k++) V[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    static const int P[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int sweep = 0; sweep < 64; sweep++) {
+        int rotated = 0;
+        for (int m = 0; m < 3; m++) {
+            int p = P[m][0], q = P[m][1];
+            double al = 0, be = 0, ga = 0;
+            for (int r = 0; r < 3; r++) {
+                al += B[3 * r + p] * B[3 * r + p];
+                be += B[3 * r + q] * B[3 * r + q];
+                ga += B[3 * r + p] * B[3 * r + q];
+            }
+            if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+            rotated = 1;
+            double zeta = (be - al) / (2.0 * ga);
+            double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+            for (int r = 0; r < 3; r++) {
+                double bp = B[3 * r + p], bq = B[3 * r + q];
+                B[3 * r + p] = cs * bp - sn * bq;
+                B[3 * r + q] = sn * bp + cs * bq;
+                double vp = V[3 * r + p], vq = V[3 * r + q];
+                V[3 * r + p] = cs * vp - sn * vq;
+                V[3 * r + q] = sn * vp + cs * vq;
+            }
+        }
+        if (!rotated) break;
+    }
+    double sig[3];
+    for (int k = 0; k < 3; k++)
+        sig[k] = sqrt(B[k] * B[k] + B[3 + k] * B[3 + k] + B[6 + k] * B[6 + k]);
+    int ord[3] = {0, 1, 2};
+    for (int a = 0; a < 3; a++)                 /* sort columns by singular value */
+        for (int b2 = a + 1; b2 < 3; b2++)
+            if (sig[ord[b2]] > sig[ord[a]]) { int t = ord[a]; ord[a] = ord[b2]; ord[b2] = t; }
+    double Vs[9];
+    memcpy(Vs, V, sizeof(Vs));
+    for (int k = 0; k < 3; k++) {
+        int o = ord[k];
+        s[k] = sig[o];
+        for (int r = 0; r < 3; r++) {
+            V[3 * r + k] = Vs[3 * r + o];
+            U[3 * r + k] = sig[o] > 0 ? B[3 * r + o] / sig[o] : 0.0;
+        }
+    }
+    /* complete U where a singular value vanished */
+    if (!(s[1] > 0)) {
+        double e[3] = {1, 0, 0};
+        double u0[3] = {U[0], U[3], U[6]};
+        if (fabs(u0[0]) > 0.9) { e[0] = 0; e[1] = 1; }
+        double w[3];
+        cross3(u0, e, w);
+        double L = sqrt(dot3(w, w));
+        for (int r = 0; r < 3; r++) U[3 * r + 1] = w[r] / L;
+    }
+    if (!(s[2] > 0)) {
+        double u0[3] = {U[0], U[3], U[6]}, u1[3] = {U[1], U[4], U[7]}, w[3];
+        cross3(u0, u1, w);
+        for (int r = 0; r < 3; r++) U[3 * r + 2] = w[r];
+    }
+}
+
+static double det3(const double *M)
+{
+    return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+           M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+
+/* Best rotation argmax_R tr(R^T A) = U diag(1, 1, det(U V^T)) V^T.  Returns 0, or 1
+ * when it is not unique (rank <= 1, or a reflection with sigma_2 = sigma_3). */
+int vdo_procrustes(const double *A, double *R)
+{
+    double U[9], s[3], V[9];
+    vdo_svd3(A, U, s, V);
+    double d = det3(U) * det3(V) < 0 ? -1.0 : 1.0;
+    if (!(s[0] > 0) || s[1] <= 1e-12 * s[0]) return 1;
+    if (d < 0 && s[1] - s[2] <= 1e-12 * s[0]) return 1;
+    for (int r = 0; r < 3; r++)
+        for (int q = 0; q < 3; q++)
+            R[3 * r + q] = U[3 * r] * V[3 * q] + U[3 * r + 1] * V[3 * q + 1] + d * U[3 * r + 2] * V[3 * q + 2];
+    return 0;
+}
+
+/* Rotation step of the flip-flop (Sec. 7.1): per node of M, the cross-covariance
+ * A_i = sum_{j in N_i} (t_i - t_j)(t^_i - t^_j)^T and its Procrustes rotation.
+ * Returns the number of nodes whose rotation was left unchanged. */
+int vdo_fit_rotations(vdo_ctx *c)
+{
+    int degenerate = 0;
+    double *Rn = (double *)xcalloc((size_t)c->nn * 9, sizeof(double));
+    memcpy(Rn, c->R, sizeof(double) * 9 * (size_t)c->nn);
+    for (int i = 0; i < c->nn; i++) {
+        if (!c->inM[i]) continue;
+        double A[9] = {0}, hi[3];
+        int axes[3] = {0, 0, 0};
+        node_pos(c, i, hi);
+        for (int k = 0; k < 6; k++) {
+            int j = neighbour(c, i, k);
+            if (j < 0 || !c->inM[j]) continue;
+            axes[k / 2] = 1;
+            double hj[3], d[3], e[3];
+            node_pos(c, j, hj);
+            for (int a = 0; a < 3; a++) {
+                d[a] = (hi[a] + c->u[3 * i + a]) - (hj[a] + c->u[3 * j + a]);
+                e[a] = hi[a] - hj[a];
+            }
+            for (int r = 0; r < 3; r++)
+                for (int q = 0; q < 3; q++) A[3 * r + q] += d[r] * e[q];
+        }
+        if (axes[0] + axes[1] + axes[2] < 2 || vdo_procrustes(A, Rn + 9 * i)) {
+            degenerate++;
+            memcpy(Rn + 9 * i, c->R + 9 * i, sizeof(double) * 9);
+        }
+    }
+    memcpy(c->R, Rn, sizeof(double) * 9 * (size_t)c->nn);
+    free(Rn);
+    c->have_J = 0;
+    return degenerate;
+}
+
+/* ------------------------------------------------------------------ flip-flop driver */
+
+/* Full per-frame solve: for each Gauss-Newton iteration, associate (unless frozen
+ * after the first), solve the position step by PCG (or Cholesky), add the increment,
+ * fit rotations, and record E (Eq. 1) under that iteration's association.
+ * e_hist receives 4 doubles per iteration (total, dense, sparse, reg); cg_hist the
+ * CG iterations of each; stats[0] = valid correspondences of the last association,
+ * stats[1] = degenerate rotations of the last step.  Returns iterations done. */
+int vdo_solve(vdo_ctx *c, int gn_iters, int cg_iters, double cg_tol, int fixed_assoc,
+              int use_cholesky, double *e_hist, int *cg_hist, int *stats)
+{
+    double *delta = (double *)xcalloc((size_t)c->nn * 3, sizeof(double));
+    int g = 0, deg = 0;
+    for (; g < gn_iters; g++) {
+        if (!(fixed_assoc && g > 0 && c->have_assoc)) vdo_associate(c);
+        int it = 0;
+        if (use_cholesky) {
+            if (vdo_cholesky(c, delta)) break;
+        } else {
+            it = vdo_pcg(c, cg_iters, cg_tol, delta, NULL);
+        }
+        vdo_add_increment(c, delta);
+        deg = vdo_fit_rotations(c);
+        if (e_hist) vdo_energy(c, e_hist + 4 * g);
+        if (cg_hist) cg_hist[g] = it;
+    }
+    if (stats) {
+        stats[0] = c->n_valid;
+        stats[1] = deg;
+    }
+    free(delta);
+    return g;
+}

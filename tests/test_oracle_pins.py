@@ -1,0 +1,551 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks a closed form, an
+invariant, a hand computation, a brute-force search or a library routine, chosen so
+that a dropped term, a wrong sign or index, or a transposed operand fails one of them.
+"""
+import dataclasses
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_08161_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_rot(rng, scale=1.0):
+    """Rotation from an axis-angle vector (Rodrigues), angle ~ scale * |N(0, 1)|."""
+    w = rng.normal(size=3) * scale
+    th = np.linalg.norm(w)
+    if th == 0:
+        return np.eye(3)
+    k = w / th
+    Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(th) * Kx + (1 - math.cos(th)) * Kx @ Kx
+
+
+def _node_pos(fr):
+    nx, ny, nz = fr.dims
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    idx = np.stack([x.ravel(), y.ravel(), z.ravel()], 1).astype(np.float64)
+    return fr.origin.astype(np.float64) + float(np.float32(fr.spacing)) * idx
+
+
+def _with_sparse(fr, canon, target):
+    return dataclasses.replace(fr, sp_canon=np.asarray(canon, np.float32).reshape(-1, 3),
+                               sp_target=np.asarray(target, np.float32).reshape(-1, 3))
+
+
+def _no_dense(fr):
+    return dataclasses.replace(fr, src_pts=np.zeros((0, 3), np.float32),
+                               src_nrm=np.zeros((0, 3), np.float32))
+
+
+def _small_frame(n=4, tilt=20.0, shift=(0.0, 0.0, 0.01), n_sparse=6, seed=0):
+    rng = np.random.default_rng(seed)
+    fr = synth.plane_frame(W=32, H=24, f=30.0, n=n, tilt_deg=tilt, shift=shift)
+    lo = fr.origin.astype(np.float64) + 0.1
+    hi = lo + (np.array(fr.dims) - 1) * fr.spacing - 0.2
+    canon = rng.uniform(lo, hi, size=(n_sparse, 3))
+    target = canon + rng.normal(0, 0.01, size=canon.shape)
+    return _with_sparse(fr, canon, target)
+
+
+# ---------------------------------------------------------------- golden single cell
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, *v = line.split()
+                out[k] = np.array([float(x) for x in v])
+    return out
+
+
+def test_single_cell_golden():
+    g = _golden("single_cell.txt")
+    dims = tuple(int(v) for v in g["dims"])
+    fr = synth.Frame(depth=np.zeros((4, 4), np.float32), K=np.array([4, 4, 1.5, 1.5], np.float32),
+                     pose=np.array([1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0], np.float32),
+                     src_pts=np.zeros((0, 3), np.float32), src_nrm=np.zeros((0, 3), np.float32),
+                     sp_canon=g["f_hat"].reshape(1, 3).astype(np.float32),
+                     sp_target=(g["f_hat"] + g["d"]).reshape(1, 3).astype(np.float32),
+                     dims=dims, origin=g["origin"].astype(np.float32), spacing=float(g["spacing"][0]))
+    w = g["weights"]
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL,
+                                 params=dict(w_sparse=w[0], w_dense=w[1], w_reg=w[2]))
+    o.associate()
+    # float32 inputs: the pair's offset is d only up to float32 rounding of f
+    d32 = (np.float32(g["f_hat"] + g["d"]).astype(np.float64) - np.float32(g["f_hat"]).astype(np.float64))
+    e = o.energy()
+    assert e[2] == pytest.approx(float(d32 @ d32), rel=1e-12)
+    assert e[3] == 0.0 and e[1] == 0.0
+    assert e[0] == pytest.approx(w[0] * float(d32 @ d32), rel=1e-12)
+    assert g["E_total"][0] == pytest.approx(w[0] * float(g["d"] @ g["d"]), rel=1e-12)
+    b, diag = o.rhs()
+    np.testing.assert_allclose(b, np.tile(1.25 * d32, (8, 1)), rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(b, np.tile(g["b"], (8, 1)), rtol=2e-5)
+    np.testing.assert_allclose(diag, np.full((8, 3), g["diag"][0]), rtol=1e-6)
+    p = np.zeros((8, 3))
+    p[0, 0] = 1.0
+    q = o.apply(p)
+    assert q[0, 0] == pytest.approx(g["Ap_node0_x"][0], rel=1e-6)
+    for j in (1, 2, 4):
+        assert q[j, 0] == pytest.approx(g["Ap_nbr_x"][0], rel=1e-6)
+    for j in (3, 5, 6, 7):
+        assert q[j, 0] == pytest.approx(g["Ap_far_x"][0], rel=1e-6)
+    assert np.abs(q[:, 1:]).max() < 1e-12
+    delta = o.cholesky()
+    np.testing.assert_allclose(delta, np.tile(d32, (8, 1)), atol=1e-12)
+    o.add_increment(delta)
+    assert o.fit_rotations() == 0
+    _, R = o.get_warp()
+    np.testing.assert_allclose(R, np.tile(np.eye(3), (8, 1, 1)), atol=1e-12)
+    assert o.energy()[0] < 1e-24
+
+
+# ---------------------------------------------------------------- S(x), Sec. 4
+
+@pytest.mark.parametrize("with_pose", [False, True])
+def test_affine_warp_reproduced_exactly(with_pose):
+    """Trilinear interpolation reproduces affine maps: with u_i = (Q - I) t^_i + c,
+    S(x) = R_g (Q x + c) + t_g for every interior x, so targets placed there give
+    E_sparse = 0, and moving one target by e gives E_sparse = |e|^2."""
+    rng = np.random.default_rng(3)
+    fr = _no_dense(synth.plane_frame(n=5))
+    Q = _rand_rot(rng, 0.3) + 0.05 * rng.normal(size=(3, 3))      # a general affine map
+    c = rng.normal(0, 0.02, 3)
+    Rg, tg = (_rand_rot(rng, 0.2), rng.normal(0, 0.05, 3)) if with_pose else (np.eye(3), np.zeros(3))
+    fr = dataclasses.replace(fr, pose=np.concatenate([Rg.ravel(), tg]).astype(np.float32))
+    Rg = fr.pose[:9].astype(np.float64).reshape(3, 3)
+    tg = fr.pose[9:].astype(np.float64)
+    lo = fr.origin.astype(np.float64)
+    hi = lo + (np.array(fr.dims) - 1) * fr.spacing
+    x = rng.uniform(lo + 1e-3, hi - 1e-3, size=(50, 3)).astype(np.float32).astype(np.float64)
+    tgt = (Rg @ (Q @ x.T + c[:, None])).T + tg
+    e = np.zeros_like(tgt)
+    e[7] = [1e-3, -2e-3, 5e-4]
+    fr = _with_sparse(fr, x, (tgt + e))
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    P = _node_pos(fr)
+    o.set_warp(u=(P @ (Q - np.eye(3)).T) + c)
+    tgt32 = (tgt + e).astype(np.float32).astype(np.float64)
+    expect = np.sum(((Rg @ (Q @ x.T + c[:, None])).T + tg - tgt32) ** 2)
+    assert o.energy()[2] == pytest.approx(expect, rel=1e-9, abs=1e-20)
+    assert expect == pytest.approx(e[7] @ e[7], rel=1e-3)
+
+
+# ---------------------------------------------------------------- E_reg, Eq. 4
+
+def test_arap_zero_under_rigid_motion_and_rotation_step_recovers_it():
+    rng = np.random.default_rng(5)
+    fr = _no_dense(synth.plane_frame(n=5))
+    Q = _rand_rot(rng, 0.7)
+    c = rng.normal(0, 0.05, 3)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    P = _node_pos(fr)
+    u = P @ (Q - np.eye(3)).T + c
+    o.set_warp(u=u, R=np.tile(Q, (o.nn, 1, 1)))
+    e = o.energy()
+    assert e[3] < 1e-26 * o.nn
+    o.set_warp(u=u)                         # R = I: the rotation step must find Q
+    assert o.energy()[3] > 1e-4
+    assert o.fit_rotations() == 0
+    _, R = o.get_warp()
+    assert np.abs(R - Q).max() < 1e-12
+    assert o.energy()[3] < 1e-26 * o.nn
+
+
+def test_arap_single_displaced_node_closed_form():
+    """Moving one interior node by delta (R = I) touches 6 undirected edges, each
+    counted in both directions: E_reg = 12 |delta|^2.  A boundary corner: 6 |delta|^2."""
+    fr = _no_dense(synth.plane_frame(n=5))
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    delta = np.array([0.003, -0.001, 0.002])
+    for node, deg in ((2 + 5 * (2 + 5 * 2), 6), (0, 3), (2, 4)):
+        u = np.zeros((o.nn, 3))
+        u[node] = delta
+        o.set_warp(u=u)
+        assert o.energy()[3] == pytest.approx(2 * deg * delta @ delta, rel=1e-12)
+
+
+# ---------------------------------------------------------------- target maps + association
+
+def test_target_maps_plane_by_hand():
+    fr = synth.plane_frame(W=12, H=9, f=10.0, n=4, tilt_deg=25.0)
+    o = oracle.Oracle.from_frame(fr)
+    V, N, valid = o.target_maps()
+    fx, fy, cx, cy = fr.K.astype(np.float64)
+    vv, uu = np.mgrid[0:9, 0:12]
+    D = fr.depth.astype(np.float64)
+    np.testing.assert_allclose(V[..., 2], D, rtol=0, atol=0)
+    np.testing.assert_allclose(V[..., 0], D * (uu - cx) / fx, rtol=1e-15, atol=1e-15)
+    interior = np.zeros_like(valid)
+    interior[1:-1, 1:-1] = True
+    assert (valid == interior).all()
+    th = math.radians(25.0)
+    nrm = np.array([math.sin(th), 0.0, -math.cos(th)])            # plane normal facing camera
+    np.testing.assert_allclose(N[valid], np.tile(nrm, (valid.sum(), 1)), atol=2e-6)
+    # a hole invalidates the centre and its 4-neighbours
+    d2 = fr.depth.copy()
+    d2[4, 5] = 0
+    o2 = oracle.Oracle.from_frame(dataclasses.replace(fr, depth=d2))
+    _, _, v2 = o2.target_maps()
+    for (r, q) in ((4, 5), (3, 5), (5, 5), (4, 4), (4, 6)):
+        assert not v2[r, q]
+    assert v2[3, 4] and v2[5, 6]
+
+
+@pytest.mark.parametrize("tilt,dz,rot", [(0.0, 0.0, 0.0), (0.0, 0.01, 0.0), (30.0, 0.004, 0.0),
+                                         (0.0, 0.0, 25.0), (30.0, 0.004, -20.0)])
+def test_association_weights_by_hand(tilt, dz, rot):
+    """Plane seen through its own pixels: each sample projects to its own pixel, and
+    w_c = ((Phi_d + Phi_n + Phi_v)/3)^2 with Phi_r(x) = 1 - x/eps_r (Sec. 5.1).  With
+    every R_i = Q (u = 0) the model normal is Q n^_c."""
+    eps_d, eps_n, eps_v = 0.05, 0.5, 0.8
+    fr = synth.plane_frame(W=16, H=12, f=12.0, n=8, tilt_deg=tilt, shift=(0, 0, dz))
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    Q = synth._rotation([0.0, 1.0, 0.0], math.radians(rot))
+    o.set_warp(None, np.tile(Q, (o.nn, 1, 1)))
+    o.associate()
+    pix, w, r = o.association()
+    cell, _ = o.sample_cells()
+    fx, fy, cx, cy = fr.K.astype(np.float64)
+    th = math.radians(tilt)
+    nrm = np.array([math.sin(th), 0.0, -math.cos(th)])
+    checked = 0
+    for s in range(fr.C):
+        v, u = divmod(s, fr.W)
+        if cell[s] < 0 or not (1 <= u < fr.W - 1 and 1 <= v < fr.H - 1):
+            assert w[s] == 0
+            continue
+        assert pix[s] == s
+        p = fr.src_pts[s].astype(np.float64)
+        pa = fr.depth[v, u] * np.array([(u - cx) / fx, (v - cy) / fy, 1.0])
+        nc = Q @ fr.src_nrm[s].astype(np.float64)
+        phi_d = 1 - np.linalg.norm(p - pa) / eps_d
+        phi_n = 1.0 - (1.0 - nc @ nrm) / eps_n
+        phi_v = 1 - (1 - nc @ (-p / np.linalg.norm(p))) / eps_v
+        if min(phi_d, phi_n, phi_v) < 0:
+            assert w[s] == 0
+            continue
+        assert w[s] == pytest.approx(((phi_d + phi_n + phi_v) / 3) ** 2, rel=2e-5)
+        assert r[s] == pytest.approx(math.sqrt(w[s]) * (p - pa) @ nrm, abs=2e-7)
+        checked += 1
+    assert checked > 20
+
+
+def test_association_pruning_thresholds():
+    """A sample farther than eps_d from its target, or whose normal deviates by more
+    than eps_n, or seen at a grazing angle beyond eps_v, gets w_c = 0."""
+    fr = synth.plane_frame(W=16, H=12, f=12.0, n=8, shift=(0, 0, 0.06))       # 6 cm > eps_d
+    o = oracle.Oracle.from_frame(fr)
+    assert o.associate() == 0
+    o.set_params(eps_d=0.07)
+    assert o.associate() > 0
+    fr2 = synth.plane_frame(W=16, H=12, f=12.0, n=8, tilt_deg=78.0)           # grazing view
+    o2 = oracle.Oracle.from_frame(fr2)
+    o2.associate()
+    pix, w, _ = o2.association()
+    th = math.radians(78.0)
+    nrm = np.array([math.sin(th), 0.0, -math.cos(th)])
+    p = fr2.src_pts.astype(np.float64)
+    ndotv = -(p @ nrm) / np.linalg.norm(p, axis=1)
+    ok = pix >= 0
+    graze = ok & (1 - ndotv > 0.8)
+    assert graze.sum() >= 3 and (ok & ~graze).sum() >= 3
+    assert np.all(w[graze] == 0) and np.all(w[ok & ~graze] > 0)
+    bent = dataclasses.replace(fr, src_nrm=np.tile(np.float32([0.8, 0, -0.6]), (fr.C, 1)))
+    o3 = oracle.Oracle.from_frame(dataclasses.replace(bent, depth=synth.plane_frame(
+        W=16, H=12, f=12.0, n=8).depth))                                      # 1 - 0.6 = 0.4 < 0.5
+    assert o3.associate() > 0
+    o3.set_params(eps_n=0.35)
+    assert o3.associate() == 0
+
+
+def test_active_set_one_ring():
+    """One sample in cell (1,1,1) of a 5^3 lattice: M = its 8 corners plus their
+    6-neighbours = 8 + 6 * 4 = 32 nodes (Sec. 6)."""
+    fr = _no_dense(synth.plane_frame(n=5))
+    h = fr.spacing
+    x = fr.origin.astype(np.float64) + 1.5 * h
+    fr = dataclasses.replace(fr, src_pts=np.float32([x]), src_nrm=np.float32([[0, 0, -1]]))
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_SURFACE)
+    m = o.active_mask().reshape(5, 5, 5)                     # [z, y, x]
+    assert m.sum() == 32
+    assert m[1:3, 1:3, 1:3].all()
+    assert not m[0, 0, 0] and m[0, 1, 1] and m[1, 1, 3] and not m[3, 3, 3]
+
+
+# ---------------------------------------------------------------- Jacobian vs E
+
+@pytest.mark.parametrize("mode,posed", [(oracle.ACTIVE_ALL, False), (oracle.ACTIVE_SURFACE, False),
+                                         (oracle.ACTIVE_ALL, True)])
+def test_jacobian_matches_finite_differences(mode, posed):
+    """-2 b = grad E (b = -J^T r) against central differences of E (Eq. 1) with the
+    association held fixed, on a 4^3 lattice with random warp and rotations (and a
+    non-identity global pose R_g, t_g)."""
+    rng = np.random.default_rng(11)
+    fr = _small_frame(n=4)
+    if posed:
+        Rg = _rand_rot(np.random.default_rng(99), 0.05)
+        fr = dataclasses.replace(fr, pose=np.concatenate([Rg.ravel(), [0.004, -0.003, 0.002]]).astype(np.float32))
+    o = oracle.Oracle.from_frame(fr, mode, params=dict(w_sparse=3.0, w_dense=2.0, w_reg=0.7))
+    u0 = rng.normal(0, 0.004, (o.nn, 3))
+    R0 = np.stack([_rand_rot(rng, 0.1) for _ in range(o.nn)])
+    o.set_warp(u0, R0)
+    assert o.associate() > 10
+    b, _ = o.rhs()
+    act = o.active_mask()
+    eps = 1e-6
+    worst = 0.0
+    for i in np.nonzero(act)[0]:
+        for a in range(3):
+            up = u0.copy()
+            up[i, a] += eps
+            o.set_warp(up, R0)
+            ep = o.energy()[0]
+            up[i, a] -= 2 * eps
+            o.set_warp(up, R0)
+            em = o.energy()[0]
+            fd = (ep - em) / (2 * eps)
+            worst = max(worst, abs(fd - (-2 * b[i, a])) / (abs(fd) + 1e-3))
+    assert worst < 1e-6
+    assert np.all(b[~act] == 0)
+
+
+# ---------------------------------------------------------------- position step
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_pcg_reaches_cholesky(n):
+    rng = np.random.default_rng(n)
+    fr = _small_frame(n=n, seed=n)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    o.set_warp(rng.normal(0, 0.003, (o.nn, 3)), np.stack([_rand_rot(rng, 0.05) for _ in range(o.nn)]))
+    o.associate()
+    exact = o.cholesky()
+    x, it, _ = o.pcg(3 * o.num_active() + 50, tol=1e-15)
+    assert np.abs(x - exact).max() < 1e-10
+    # the Cholesky solve itself against numpy on the dense normal matrix built column by column
+    N3 = 3 * o.nn
+    A = np.zeros((N3, N3))
+    for k in range(N3):
+        e = np.zeros(N3)
+        e[k] = 1.0
+        A[:, k] = o.apply(e).ravel()
+    b, _ = o.rhs()
+    np.testing.assert_allclose(A, A.T, atol=1e-12)
+    ref = np.linalg.solve(A, b.ravel())
+    assert np.abs(ref - exact.ravel()).max() < 1e-10
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+def test_pcg_iterates_match_textbook_pcg(k):
+    """The first k iterates of the Jacobi-preconditioned CG equal those of a textbook
+    PCG (scipy.sparse.linalg.cg, x0 = 0, M = diag(J^T J)^-1) on the same system."""
+    from scipy.sparse.linalg import cg
+    rng = np.random.default_rng(21)
+    fr = _small_frame(n=4, seed=3)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL, params=dict(w_sparse=30.0, w_reg=0.3))
+    o.set_warp(rng.normal(0, 0.003, (o.nn, 3)))
+    o.associate()
+    N3 = 3 * o.nn
+    A = np.zeros((N3, N3))
+    for j in range(N3):
+        e = np.zeros(N3)
+        e[j] = 1.0
+        A[:, j] = o.apply(e).ravel()
+    b, _ = o.rhs()
+    b = b.ravel()
+    dg = np.diag(A).copy()
+    assert np.ptp(dg) > 1.0                               # a non-trivial preconditioner
+    x_ref, _ = cg(A, b, x0=np.zeros(N3), M=np.diag(1.0 / dg), maxiter=k, rtol=0.0, atol=0.0)
+    x, it, _ = o.pcg(k)
+    assert it == k
+    assert np.abs(x.ravel() - x_ref).max() <= 1e-10 * np.abs(x_ref).max()
+
+
+def test_translation_closed_form():
+    """Sparse-only data with every target f = f^ + d (w_d = 0): the exact position step
+    gives u_i = d on every node of the connected lattice and E = 0."""
+    rng = np.random.default_rng(2)
+    fr = _small_frame(n=5, n_sparse=9)
+    d = np.array([0.012, -0.007, 0.02])
+    fr = _with_sparse(fr, fr.sp_canon, fr.sp_canon.astype(np.float64) + d)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL, params=dict(w_dense=0.0))
+    o.associate()
+    delta = o.cholesky()
+    d32 = (fr.sp_target.astype(np.float64) - fr.sp_canon.astype(np.float64)).mean(0)
+    assert np.abs(delta - d).max() < 5e-8          # float32 rounding of the targets
+    o.add_increment(delta)
+    o.fit_rotations()
+    assert o.energy()[0] < 1e-13
+    x, it, _ = o.pcg(10)
+    assert np.abs(x).max() < 1e-7
+    del d32, rng
+
+
+def test_arap_only_keeps_zero():
+    fr = _small_frame(n=4)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL, params=dict(w_sparse=0.0, w_dense=0.0))
+    res = o.solve(3, 10)
+    u, R = o.get_warp()
+    assert np.all(u == 0) and list(res["cg_done"]) == [0, 0, 0]
+    assert np.abs(R - np.eye(3)).max() == 0
+
+
+def test_rigid_sparse_targets_converge():
+    """Sparse targets under a rigid motion (Q, c): flip-flop drives E to 0 and every
+    R_i to Q (ARAP is minimised exactly by the rigid warp)."""
+    rng = np.random.default_rng(8)
+    fr = _no_dense(synth.plane_frame(n=4))
+    lo = fr.origin.astype(np.float64)
+    hi = lo + 3 * fr.spacing
+    canon = rng.uniform(lo, hi, (12, 3))
+    Q = _rand_rot(rng, 0.15)
+    c = rng.normal(0, 0.01, 3)
+    fr = _with_sparse(fr, canon, (canon @ Q.T) + c)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    o.associate()
+    e0 = o.energy()[0]
+    res = o.solve(60, 3 * 64 + 20, cg_tol=1e-14)
+    e = res["energy"][:, 0]
+    assert e[-1] < 1e-8 * e0
+    _, R = o.get_warp()
+    assert np.abs(R - Q).max() < 1e-3
+
+
+def test_descent_with_fixed_association():
+    """Block-coordinate descent: with the association frozen, E does not increase
+    after any CG iteration (CG minimises the exactly quadratic position energy over
+    growing Krylov spaces) nor after a rotation step (exact minimiser in R)."""
+    rng = np.random.default_rng(4)
+    fr = _small_frame(n=5)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    o.set_warp(rng.normal(0, 0.003, (o.nn, 3)))
+    o.associate()
+    for g in range(3):
+        u0, R0 = o.get_warp()
+        e_prev = o.energy()[0]
+        for k in range(1, 25):
+            o.set_warp(u0, R0)
+            x, it, _ = o.pcg(k)
+            o.add_increment(x)
+            e = o.energy()[0]
+            assert e <= e_prev * (1 + 1e-12)
+            e_prev = e
+        o.set_warp(u0, R0)
+        x, _, _ = o.pcg(24)
+        o.add_increment(x)
+        e_before = o.energy()[0]
+        o.fit_rotations()
+        assert o.energy()[0] <= e_before * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------- rotation step, Sec. 7.1
+
+def _objective(R, D, E):
+    return np.sum((D - E @ R.T) ** 2)
+
+
+def _rotvec(w):
+    th = np.linalg.norm(w)
+    if th < 1e-300:
+        return np.eye(3)
+    k = w / th
+    Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(th) * Kx + (1 - math.cos(th)) * Kx @ Kx
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_procrustes_matches_brute_force(seed):
+    """Per-node rotation = argmin_R sum_j |(t_i - t_j) - R (t^_i - t^_j)|^2.  Compare
+    with a dense search over SO(3) (random unit quaternions) refined by a local
+    search in axis-angle coordinates, with no SVD involved."""
+    rng = np.random.default_rng(seed)
+    h = 0.1
+    E = np.array([[h, 0, 0], [-h, 0, 0], [0, h, 0], [0, -h, 0], [0, 0, h], [0, 0, -h]])
+    Qt = _rand_rot(rng, 1.5)
+    D = E @ Qt.T + rng.normal(0, 0.03, E.shape)
+    if seed == 3:
+        D = D * np.array([1, 1, -1])                          # det(A) < 0 case
+    A = D.T @ E                                               # sum_j d_j e_j^T
+    R = oracle.procrustes(A)
+    assert R is not None
+    assert abs(np.linalg.det(R) - 1) < 1e-12 and np.abs(R.T @ R - np.eye(3)).max() < 1e-12
+    q = rng.normal(size=(100000, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    a, b, c, d = q.T
+    Rs = np.stack([np.stack([a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)], -1),
+                   np.stack([2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)], -1),
+                   np.stack([2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d], -1)], 1)
+    objs = np.sum((D[None] - np.einsum("jb,nab->nja", E, Rs)) ** 2, axis=(1, 2))
+    best = Rs[np.argmin(objs)]
+    f_R = _objective(R, D, E)
+    assert f_R <= objs.min() + 1e-12
+    # local refinement: coordinate search on a left perturbation exp(w) best
+    step = 0.05
+    cur = best
+    fcur = _objective(cur, D, E)
+    while step > 1e-11:
+        improved = False
+        for k in range(3):
+            for sgn in (1.0, -1.0):
+                w = np.zeros(3)
+                w[k] = sgn * step
+                cand = _rotvec(w) @ cur
+                fc = _objective(cand, D, E)
+                if fc < fcur:
+                    cur, fcur, improved = cand, fc, True
+        if not improved:
+            step *= 0.5
+    # a derivative-free search resolves the minimiser only to ~sqrt(eps) ~ 1e-8
+    assert np.abs(cur - R).max() < 1e-7
+    assert f_R <= fcur + 1e-14
+    # first-order optimality in closed form: R^T A is symmetric at the minimiser
+    M = R.T @ A
+    assert np.abs(M - M.T).max() < 1e-12 * np.abs(A).max()
+
+
+def test_svd3_against_library():
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        A = rng.normal(size=(3, 3))
+        U, s, V = oracle.svd3(A)
+        np.testing.assert_allclose(s, np.linalg.svd(A, compute_uv=False), rtol=1e-12)
+        np.testing.assert_allclose(U @ np.diag(s) @ V.T, A, atol=1e-12)
+        np.testing.assert_allclose(U.T @ U, np.eye(3), atol=1e-12)
+        np.testing.assert_allclose(V.T @ V, np.eye(3), atol=1e-12)
+    A = np.outer([1.0, 2, 3], [0.5, -1, 2])                   # rank 1: not unique
+    assert oracle.procrustes(A) is None
+    A2 = np.array([[1.0, 0, 0], [0, 2, 0], [0, 0, 0]])        # rank 2: unique
+    np.testing.assert_allclose(oracle.procrustes(A2), np.eye(3), atol=1e-15)
+
+
+def test_rotation_degenerate_nodes_keep_previous():
+    """When the deformed one-ring collapses onto a line, the best rotation is not
+    unique (rank A_i <= 1): every node keeps its previous R_i and is counted.  A
+    collapse onto a plane (rank 2) still has a unique best rotation."""
+    fr = _no_dense(synth.plane_frame(n=4))
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    P = _node_pos(fr)
+    rng = np.random.default_rng(1)
+    Rr = np.stack([_rand_rot(rng, 0.2) for _ in range(o.nn)])
+    line = np.zeros_like(P)
+    line[:, 0] = P[:, 0]
+    o.set_warp(line - P, Rr)
+    assert o.fit_rotations() == o.nn
+    _, R = o.get_warp()
+    np.testing.assert_array_equal(R, Rr)
+    plane = P.copy()
+    plane[:, 2] = 1.0
+    o.set_warp(plane - P, Rr)
+    assert o.fit_rotations() == 0
+    _, R = o.get_warp()
+    np.testing.assert_allclose(R, np.tile(np.eye(3), (o.nn, 1, 1)), atol=1e-12)
