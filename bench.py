@@ -1,0 +1,301 @@
+"""Benchmark: per-frame flip-flop Gauss-Newton solve of a 96^3 lattice against a
+640x480 depth map (VolumeDeform, arXiv 1603.08161, Sec. 7), on synthetic Kinect-shaped
+data (three bent capsules, 300 sparse pairs with 5% outliers).
+
+One step = one frame through every stage of the path: vd_set_correspondences and
+vd_set_frame (target normals, sample binning, active set) with the inputs resident in
+device memory, then vd_solve (10 Gauss-Newton iterations x 20 PCG iterations, with
+re-association at every iteration, from u = 0, R = I).  L2 is flushed between steps
+(256 MiB write) outside the per-step CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank solves its own replica frame (the solve of one lattice
+is not sharded); value = frames of all ranks / max rank time.
+--impl reference times the FP64 CPU oracle (the only other implementation of the
+method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GN solve frames/s at 96^3 lattice, 640x480 depth; HBM roofline %; learned/batched vs plain"
+WORKLOAD = "capsules96: 96^3 lattice (all nodes active), 640x480 depth f=525, 300 sparse pairs, 10 GN x 20 PCG"
+GN, CG = 10, 20
+
+# algorithmic bytes per active node of one launch of each kernel class (FP32 SoA)
+BYTES_PER_NODE = {
+    "update_x": 84,       # read x, p, r, q, Minv; write x, r
+    "update_p": 48,       # read Minv, r, p; write p
+    "apply_stencil": 24,  # read p; write q
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(fr, gn_sample=1):
+    """FP64 oracle on a bounded sample: gn_sample of the frame's 10 Gauss-Newton
+    iterations (20 PCG each), scaled to frames/s."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    o.solve(gn_sample, CG, fixed_association=False)
+    dt = time.perf_counter() - t0
+    return {"value": (gn_sample / GN) / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{gn_sample} of {GN} Gauss-Newton iterations (x{CG} PCG) of one {WORKLOAD.split(':')[0]} "
+                      f"frame incl. setup, {dt:.1f} s, scaled by {GN // gn_sample}"}
+
+
+def run_reference(args, world, rank):
+    from paper_1603_08161_b300 import synth
+    if rank != 0:
+        return
+    fr = synth.config2()
+    import oracle
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+        o.solve(1, CG, fixed_association=False)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    per_frame = statistics.mean(times) * GN
+    val = 1.0 / per_frame
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "frames/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_frame * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": val, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step = 1 of {GN} Gauss-Newton iterations (x{CG} PCG) incl. setup, "
+                                       f"scaled by {GN}"},
+            "e2e": {"value": val, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--roofline-kernel", default="update_x", choices=sorted(BYTES_PER_NODE))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_1603_08161_b300 import synth, vd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    fr = synth.config2(seed=rank)
+    nn = int(np.prod(fr.dims))
+    prm = vd.params(gn_iters=GN, cg_iters=CG, fixed_association=False, init=vd.VD_INIT_ZERO)
+
+    # inputs resident on the device for the device-timed value
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    d_depth, d_pts, d_nrm, d_fh, d_ft = t(fr.depth), t(fr.src_pts), t(fr.src_nrm), t(fr.sp_canon), t(fr.sp_target)
+    lat = vd.Lattice(fr.dims, fr.origin, fr.spacing, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        lat.set_correspondences(d_fh, d_ft)
+        lat.set_frame(d_depth, fr.K, fr.pose, d_pts, d_nrm)
+        lat.solve_async(prm)
+
+    for _ in range(args.warmup):
+        step()
+        rep = lat.report()
+    per_solve, per_frame = lat.launch_counts(prm)
+
+    def timed_pass():
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        dist_barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            lat.report()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        dist_barrier(world)
+        return [a.elapsed_time(b) for a, b in ev], wall
+
+    with ClockSampler(local) as clk:
+        ms, wall = timed_pass()
+    rep = lat.report()
+    ms_step = dist_max(statistics.mean(ms), world)
+    value = world * 1000.0 / ms_step
+
+    # second pass of the same steps with CUDA events bracketing the roofline kernel
+    kc = vd.KERNEL_CLASSES[args.roofline_kernel]
+    lat.profile_select(kc)
+    step()
+    lat.report()
+    lat.profile_read()
+    timed_pass()
+    k_ms, k_n = lat.profile_read()
+    lat.profile_select(-1)
+    avg_s = (k_ms / max(k_n, 1)) * 1e-3
+    algo_bytes = BYTES_PER_NODE[args.roofline_kernel] * nn
+    peak, peak_kind = peaks()
+    achieved = algo_bytes / avg_s / 1e9 if avg_s > 0 else None
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timing
+    h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    p_depth, p_pts, p_nrm, p_fh, p_ft = h(fr.depth), h(fr.src_pts), h(fr.src_nrm), h(fr.sp_canon), h(fr.sp_target)
+    out_u = torch.empty((nn, 3), dtype=torch.float32).pin_memory()
+    lat2 = vd.Lattice(fr.dims, fr.origin, fr.spacing, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
+
+    def e2e_step():
+        lat2.set_correspondences(p_fh, p_ft)
+        lat2.set_frame(p_depth, fr.K, fr.pose, p_pts, p_nrm)
+        r = lat2.solve(prm)
+        lat2.get_warp(out_u, None)
+        return r
+
+    for _ in range(2):
+        e2e_step()
+    e2e_t = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = world / dist_max(statistics.mean(e2e_t), world)
+    h2d = fr.depth.nbytes + fr.src_pts.nbytes + fr.src_nrm.nbytes + fr.sp_canon.nbytes + fr.sp_target.nbytes
+    d2h = nn * 3 * 4 + 10 * 8
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(fr)
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "active_nodes": nn, "samples": fr.C, "sparse_pairs": fr.S,
+                   "association": "re-associated every Gauss-Newton iteration",
+                   "l2": "flushed between steps (256 MiB write, outside the per-step events)",
+                   "wall_s_timed_region": wall,
+                   "final_energy": rep["e_total"], "valid_correspondences": rep["n_valid_corr"],
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": avg_s * 1e6,
+                     "launches_timed": k_n},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": (per_solve + per_frame) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

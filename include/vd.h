@@ -1,0 +1,199 @@
+/*
+ * libvd -- B300-native non-rigid lattice solve of VolumeDeform (arXiv 1603.08161).
+ *
+ * One lattice G of nx x ny x nz grid points (node i = x + nx (y + ny z), x fastest;
+ * canonical position t^_i = origin + spacing * (x, y, z)) carries a displacement
+ * u_i = t_i - t^_i and a rotation R_i per node (Sec. 4).  Each frame, vd_solve runs
+ * the flip-flop Gauss-Newton minimisation of
+ *     E_total = w_s E_sparse + w_d E_dense + w_r E_reg                 (Eq. 1)
+ * with the point-to-plane term (Eq. 2), the feature term (Eq. 3) and the ARAP prior
+ * (Eq. 4): positions by Jacobi-preconditioned CG on the normal equations with the
+ * rotations fixed, then rotations by per-node Procrustes with positions fixed
+ * (Sec. 7.1).  Every step runs in this library's own CUDA kernels (sm_103a).
+ *
+ * Conventions shared by every call:
+ *   - Arrays at the boundary are row-major AoS float32: points and displacements
+ *     n x 3, rotations n x 9 (row-major 3x3), depth H x W (row v, column u), in metres.
+ *   - `mem` says where a pointer lives: VD_MEM_HOST (pageable or pinned host memory)
+ *     or VD_MEM_DEVICE (device memory of the current CUDA device, e.g. from torch).
+ *     The caller keeps ownership of every pointer it passes; the library copies what
+ *     it needs before the call returns (inputs) or writes outputs before it returns.
+ *   - Every call returns a vd_status and never throws.  On an error the lattice state
+ *     is unchanged, except after VD_ERR_NUMERIC / VD_ERR_TIMEOUT from a solve, which
+ *     leave the warp of the last completed Gauss-Newton iteration.  vd_last_error()
+ *     gives a one-line reason.
+ *   - One handle is used by one host thread at a time.  Work is ordered on the
+ *     lattice's CUDA stream.
+ */
+#ifndef VD_H
+#define VD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VD_OK = 0,
+    VD_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter */
+    VD_ERR_OOM = 2,         /* device or host allocation failed */
+    VD_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in vd_last_error) */
+    VD_ERR_STATE = 4,       /* call out of order, e.g. vd_solve before vd_set_frame */
+    VD_ERR_NUMERIC = 5,     /* non-finite energy */
+    VD_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+} vd_status;
+
+enum { VD_ACTIVE_SURFACE = 0, VD_ACTIVE_ALL = 1 };
+enum { VD_PREC_FP32 = 0, VD_PREC_MIXED = 1 };
+enum { VD_MEM_HOST = 0, VD_MEM_DEVICE = 1 };
+enum { VD_INIT_PREV = 0, VD_INIT_ZERO = 1 };
+
+typedef struct vd_lattice vd_lattice; /* opaque; owned by the library */
+
+typedef struct {
+    int nx, ny, nz;     /* nodes per axis, each >= 2 */
+    float origin[3];    /* canonical position of node (0, 0, 0), metres */
+    float spacing;      /* lattice spacing h > 0, metres */
+    int active_mode;    /* VD_ACTIVE_SURFACE: M = cells holding a sample or a sparse
+                           point plus their one-ring (Sec. 6-7); VD_ACTIVE_ALL: every node */
+    int precision;      /* VD_PREC_FP32 (FP32 storage and arithmetic, FP64 reductions)
+                           or VD_PREC_MIXED (BF16 storage of per-sample records and normals) */
+    void *cuda_stream;  /* cudaStream_t to order work on; NULL = a stream of the library's own */
+} vd_lattice_desc;
+
+typedef struct {
+    float w_sparse, w_dense, w_reg; /* w_s, w_d, w_r of Eq. 1 */
+    float eps_d, eps_n, eps_v;      /* pruning thresholds of Sec. 5.1, Phi_r(x) = 1 - x / eps_r */
+    int gn_iters;                   /* flip-flop (Gauss-Newton) iterations, >= 1 */
+    int cg_iters;                   /* PCG iterations per position step, >= 0 */
+    double cg_tol;                  /* stop PCG once r.z <= cg_tol^2 * r0.z0 (0: run all) */
+    int fixed_association;          /* 1: associate once, at the first iteration */
+    int init;                       /* VD_INIT_PREV: start from the current warp;
+                                       VD_INIT_ZERO: from u = 0, R = I */
+} vd_solve_params;
+
+typedef struct {
+    double e_total, e_dense, e_sparse, e_reg; /* Eq. 1-4 after the last iteration, under its association */
+    int gn_done;          /* Gauss-Newton iterations completed */
+    int cg_done;          /* PCG iterations of the last position step */
+    int n_valid_corr;     /* dense correspondences with w_c > 0 (last association) */
+    int n_degenerate_rot; /* nodes whose best rotation was not unique (last rotation step) */
+    int n_refined;        /* association decisions re-taken in FP64 (last association) */
+    int status;           /* vd_status of the solve */
+} vd_solve_report;
+
+/* Create a lattice (all u = 0, R = I).  Allocates device memory for the lattice state.
+ * VD_ERR_INVALID_ARG for dims < 2 or spacing <= 0. */
+vd_status vd_create_lattice(const vd_lattice_desc *desc, vd_lattice **out);
+
+/* Free the lattice and all its device memory.  NULL is accepted. */
+vd_status vd_destroy_lattice(vd_lattice *lat);
+
+/* Input of one frame (Sec. 5.1): the depth map D_t (W x H, 0 = invalid), intrinsics
+ * K = (fx, fy, cx, cy), the global pose (R | t) of Sec. 4 as 12 floats (row-major R,
+ * then t; NULL = identity) -- K and pose are always host pointers, whatever `mem`
+ * says -- and the n_src source samples p^_c with normals n^_c in
+ * canonical coordinates (the samples of the rasterised model).  Computes the target
+ * normal map, bins the samples by lattice cell and builds the active set M.
+ * Samples whose cell is not inside the lattice get w_c = 0.  Synchronous. */
+vd_status vd_set_frame(vd_lattice *lat, const float *depth, int W, int H, const float K[4],
+                       const float pose[12], const float *src_pts, const float *src_nrm, int n_src,
+                       int mem);
+
+/* The S sparse feature pairs of Eq. 3: canonical positions f^_s and observed
+ * positions f_s (S x 3 each).  Pairs outside the lattice are ignored.  Applies to the
+ * next vd_set_frame / vd_solve; S = 0 clears them.  Synchronous. */
+vd_status vd_set_correspondences(vd_lattice *lat, const float *canon, const float *target, int S,
+                                 int mem);
+
+/* Per-frame flip-flop solve (Sec. 7.1): gn_iters x (associate, position step by PCG,
+ * rotation step, energy).  Replays a captured CUDA graph of the whole schedule.
+ * Synchronous: returns after the solve finished and fills `out` (may be NULL). */
+vd_status vd_solve(vd_lattice *lat, const vd_solve_params *params, vd_solve_report *out);
+
+/* Enqueue the same solve on the lattice's stream and return at once; vd_get_report
+ * waits for it.  Inputs must not change until then. */
+vd_status vd_solve_async(vd_lattice *lat, const vd_solve_params *params);
+
+/* Wait for the last enqueued solve and return its report. */
+vd_status vd_get_report(vd_lattice *lat, vd_solve_report *out);
+
+/* Copy the warp out: disp = u (nx*ny*nz x 3), rot = R (nx*ny*nz x 9, may be NULL). */
+vd_status vd_get_warp(const vd_lattice *lat, float *disp, float *rot, int mem);
+
+/* Replace the warp (warm start, or resume a sequence): disp may be NULL (u = 0),
+ * rot may be NULL (R = I). */
+vd_status vd_set_warp(vd_lattice *lat, const float *disp, const float *rot, int mem);
+
+/* One-line description of the last error on this lattice ("" if none). */
+const char *vd_last_error(const vd_lattice *lat);
+
+/* ---- step API: the individual stages of one Gauss-Newton iteration, for callers
+ * ---- that drive their own schedule (and for per-stage checks). */
+
+/* Number of nodes in the active set M of the current frame. */
+vd_status vd_num_active(const vd_lattice *lat, int *n_active);
+
+/* Active-set mask (nx*ny*nz bytes, 1 = in M). */
+vd_status vd_get_active(const vd_lattice *lat, unsigned char *mask, int mem);
+
+/* Target normal map n^a of the current frame (H x W x 3; zero where invalid):
+ * central differences of the back-projected depth, oriented towards the camera. */
+vd_status vd_get_target_normals(const vd_lattice *lat, float *nrm, int mem);
+
+/* Projective association (Sec. 5.1) of every source sample at the current warp. */
+vd_status vd_step_associate(vd_lattice *lat, const vd_solve_params *params);
+
+/* Result of the last association in the caller's sample order: target pixel
+ * (py * W + px, or -1), confidence w_c, and the dense residual
+ * sqrt(w_d w_c) n^a . (S(p^_c) - p^a) at the current warp.  Any pointer may be NULL. */
+vd_status vd_get_association(vd_lattice *lat, const vd_solve_params *params, int *pix, float *w,
+                             float *r, int mem);
+
+/* Right-hand side b = -J^T r and Jacobi diagonal diag(J^T J) of the position step at
+ * the current warp and association (nx*ny*nz x 3 each; 0 outside M; may be NULL). */
+vd_status vd_step_rhs(vd_lattice *lat, const vd_solve_params *params, float *b, float *diag, int mem);
+
+/* Ap = J^T J p for a full-lattice vector p (nx*ny*nz x 3; entries outside M ignored);
+ * p_Ap (may be NULL) receives p.Ap accumulated in FP64. */
+vd_status vd_step_apply(vd_lattice *lat, const vd_solve_params *params, const float *p, float *Ap,
+                        double *p_Ap, int mem);
+
+/* Position step: PCG on J^T J delta = -J^T r from delta = 0.  Writes delta
+ * (nx*ny*nz x 3, may be NULL) and the iterations done; with `apply` != 0 also adds
+ * delta to u. */
+vd_status vd_step_pcg(vd_lattice *lat, const vd_solve_params *params, float *delta, int *iters,
+                      int apply, int mem);
+
+/* Rotation step (Sec. 7.1): per-node Procrustes fit of R_i to the current positions. */
+vd_status vd_step_fit_rotations(vd_lattice *lat, int *n_degenerate);
+
+/* E_total, E_dense, E_sparse, E_reg (Eq. 1-4) at the current warp under the last
+ * association. */
+vd_status vd_step_energy(vd_lattice *lat, const vd_solve_params *params, double out[4]);
+
+/* ---- measurement support ---- */
+
+/* Kernel classes that vd_profile can time inside the captured solve graph. */
+enum {
+    VD_KC_ASSOCIATE = 0, VD_KC_RHS = 1, VD_KC_APPLY_STENCIL = 2, VD_KC_APPLY_SAMPLES = 3,
+    VD_KC_UPDATE_X = 4, VD_KC_UPDATE_P = 5, VD_KC_ROTATION = 6, VD_KC_ENERGY = 7,
+    VD_KC_COUNT = 8
+};
+
+/* Select one kernel class (or -1 for none) to bracket with CUDA events inside the
+ * solve graph; the graph is re-captured on the next solve. */
+vd_status vd_profile_select(vd_lattice *lat, int kernel_class);
+
+/* Total device time (ms) and launch count of the selected class over the solves
+ * since the last call (the counters are then reset). */
+vd_status vd_profile_read(vd_lattice *lat, double *total_ms, int *launches);
+
+/* Number of kernel launches of one vd_solve with the given parameters, and of one
+ * vd_set_frame. */
+vd_status vd_launch_counts(vd_lattice *lat, const vd_solve_params *params, int *per_solve,
+                           int *per_frame);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VD_H */

@@ -1,0 +1,1004 @@
+// libvd host side: the C ABI of include/vd.h, device buffers of a lattice, the
+// per-frame preprocessing (target normals, sample binning, active set), and the
+// flip-flop schedule of Sec. 7.1 captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vd.h"
+#include "vd_kernels.cuh"
+
+using namespace vd;
+
+namespace {
+
+constexpr int kSMs = 148;
+
+int blocks_for(long n, int threads = kThreads, int per_sm = 8) {
+    long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)std::min<long>(b, (long)kSMs * per_sm);
+}
+
+int round_pow2(int n) {
+    int p = 32;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct vd_lattice {
+    Ctx c{};
+    int all = 1;
+    int precision = VD_PREC_FP32;
+    cudaStream_t stream = nullptr;   // caller's (or own) stream: where work is ordered
+    cudaStream_t cap = nullptr;      // private stream used for graph capture
+    bool own_stream = false;
+    std::string err;
+
+    std::vector<DevBuf> bufs;        // everything allocated, freed at destroy
+    // lattice state and solver vectors
+    float *u = nullptr, *R = nullptr, *vecs = nullptr;
+    int *slot_of_node = nullptr, *node_of_slot = nullptr, *nbr = nullptr, *mark = nullptr, *act = nullptr;
+    int *counts = nullptr;           // [0] n_active, [1] n_occ, [2..] spare
+    int *cnt = nullptr, *start = nullptr, *scan_sums = nullptr;
+    float *staging = nullptr;        // n x 9 floats for warp transfers
+    // frame
+    int W = 0, H = 0, cap_px = 0;
+    float *depth = nullptr;
+    float4 *nrm = nullptr;
+    int n_src = 0, cap_src = 0;
+    float *pts_in = nullptr, *nrm_in = nullptr, *res_f = nullptr;
+    int *cell_in = nullptr, *tmp = nullptr, *order = nullptr, *head = nullptr, *hscan = nullptr;
+    int *scell = nullptr, *perm = nullptr, *pix = nullptr, *occ_cell = nullptr, *occ_beg = nullptr, *res_i = nullptr;
+    float4 *frac_in = nullptr, *sp = nullptr, *sn = nullptr, *sfrac = nullptr, *rec = nullptr;
+    float *wc = nullptr;
+    // sparse pairs
+    int S = 0, cap_S = 0;
+    float *sp_in = nullptr;
+    float4 *fh = nullptr, *ft = nullptr, *sfr = nullptr;
+    int *scell_s = nullptr;
+    // scalars and report
+    char *scal = nullptr;
+    size_t scal_stride = 0;
+    int scal_slots = 0;
+    double *rep_dev = nullptr, *rep_host = nullptr;
+    // host-side sizes of the current frame (for grid sizing)
+    int n_active_h = 0, n_samples_h = 0, n_occ_h = 0;
+    bool have_frame = false;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    vd_solve_params gparams{};
+    Ctx gctx{};
+    int gkey_caps[4] = {0, 0, 0, 0};
+    long gen = 0, ggen = -1;         // buffer generation (pointers changed)
+    int launches_solve = 0, launches_frame = 0;
+    int counting = 0;
+    bool solve_pending = false;
+    // profiling
+    int prof_class = -1;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double prof_ms = 0.0;
+    int prof_launches = 0;
+};
+
+namespace {
+
+vd_status fail(vd_lattice *L, vd_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (L) L->err = buf;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(L, VD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL()                                                                                   \
+    do {                                                                                        \
+        cudaError_t e_ = cudaGetLastError();                                                    \
+        if (e_ != cudaSuccess) return fail(L, VD_ERR_CUDA, "launch: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+vd_status dalloc(vd_lattice *L, T **p, size_t count) {
+    void *q = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    bytes = (bytes + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(L, VD_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    L->bufs.push_back({q, bytes});
+    *p = (T *)q;
+    L->gen++;
+    return VD_OK;
+}
+
+template <typename T>
+void dfree(vd_lattice *L, T *&p) {
+    if (!p) return;
+    for (size_t k = 0; k < L->bufs.size(); k++)
+        if (L->bufs[k].ptr == (void *)p) {
+            cudaFree(p);
+            L->bufs.erase(L->bufs.begin() + k);
+            break;
+        }
+    p = nullptr;
+    L->gen++;
+}
+
+#define TRY(x)                       \
+    do {                             \
+        vd_status s_ = (x);          \
+        if (s_ != VD_OK) return s_;  \
+    } while (0)
+
+// copy `bytes` from a caller pointer (host or device) into device memory
+vd_status upload(vd_lattice *L, void *dst, const void *src, size_t bytes, int mem) {
+    if (!bytes) return VD_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, mem == VD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       L->stream));
+    return VD_OK;
+}
+
+vd_status download(vd_lattice *L, void *dst, const void *src, size_t bytes, int mem) {
+    if (!bytes) return VD_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, mem == VD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       L->stream));
+    return VD_OK;
+}
+
+void scan_launch(const int *in, int n, int *out, int *out_total, int *sums, cudaStream_t st) {
+    const int nt = (n + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<std::max(nt, 1), kScanThreads, 0, st>>>(in, n, out, sums);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, std::max(nt, 1), out_total);
+    if (n > 0) k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, n, sums);
+}
+
+
+// ------------------------------------------------------------------ capacities
+
+vd_status ensure_frame_caps(vd_lattice *L, int W, int H, int n_src) {
+    if (W * H > L->cap_px) {
+        dfree(L, L->depth);
+        dfree(L, L->nrm);
+        L->cap_px = W * H;
+        TRY(dalloc(L, &L->depth, (size_t)L->cap_px));
+        TRY(dalloc(L, &L->nrm, (size_t)L->cap_px));
+    }
+    if (n_src > L->cap_src) {
+        float **fs[] = {&L->pts_in, &L->nrm_in, &L->res_f};
+        for (auto f : fs) dfree(L, *f);
+        int **is[] = {&L->cell_in, &L->tmp, &L->order, &L->head, &L->hscan, &L->scell, &L->perm, &L->pix,
+                      &L->occ_cell, &L->occ_beg, &L->res_i};
+        for (auto i : is) dfree(L, *i);
+        float4 **f4[] = {&L->frac_in, &L->sp, &L->sn, &L->sfrac, &L->rec};
+        for (auto f : f4) dfree(L, *f);
+        dfree(L, L->wc);
+        dfree(L, L->scan_sums);
+        int cap = std::max(n_src, 1024);
+        cap = (int)std::min<long>((long)cap + cap / 4, 0x7fffffffL);
+        L->cap_src = cap;
+        TRY(dalloc(L, &L->pts_in, (size_t)cap * 3));
+        TRY(dalloc(L, &L->nrm_in, (size_t)cap * 3));
+        TRY(dalloc(L, &L->res_f, (size_t)cap * 2));
+        TRY(dalloc(L, &L->cell_in, (size_t)cap));
+        TRY(dalloc(L, &L->tmp, (size_t)cap));
+        TRY(dalloc(L, &L->order, (size_t)cap));
+        TRY(dalloc(L, &L->head, (size_t)cap));
+        TRY(dalloc(L, &L->hscan, (size_t)cap + 1));
+        TRY(dalloc(L, &L->scell, (size_t)cap));
+        TRY(dalloc(L, &L->perm, (size_t)cap));
+        TRY(dalloc(L, &L->pix, (size_t)cap));
+        TRY(dalloc(L, &L->occ_cell, (size_t)cap));
+        TRY(dalloc(L, &L->occ_beg, (size_t)cap + 1));
+        TRY(dalloc(L, &L->res_i, (size_t)cap));
+        TRY(dalloc(L, &L->frac_in, (size_t)cap));
+        TRY(dalloc(L, &L->sp, (size_t)cap));
+        TRY(dalloc(L, &L->sn, (size_t)cap));
+        TRY(dalloc(L, &L->sfrac, (size_t)cap));
+        TRY(dalloc(L, &L->rec, (size_t)cap));
+        TRY(dalloc(L, &L->wc, (size_t)cap));
+    }
+    if (!L->scan_sums) TRY(dalloc(L, &L->scan_sums, (size_t)kScanTile));
+    return VD_OK;
+}
+
+vd_status ensure_scal(vd_lattice *L, int G, int K) {
+    const size_t stride = scal_bytes(K);
+    if (L->scal && stride == L->scal_stride && G <= L->scal_slots) return VD_OK;
+    dfree(L, L->scal);
+    const int slots = std::max(G, 1);
+    TRY(dalloc(L, &L->scal, stride * (size_t)slots));
+    L->scal_stride = stride;
+    L->scal_slots = slots;
+    return VD_OK;
+}
+
+Scal *slot(vd_lattice *L, int g) { return (Scal *)(L->scal + L->scal_stride * (size_t)g); }
+
+void refresh_ctx(vd_lattice *L) {
+    Ctx &c = L->c;
+    c.u = L->u;
+    c.R = L->R;
+    c.x = L->vecs;
+    c.r = L->vecs + 3 * (size_t)c.ld;
+    c.p = L->vecs + 6 * (size_t)c.ld;
+    c.q = L->vecs + 9 * (size_t)c.ld;
+    c.minv = L->vecs + 12 * (size_t)c.ld;
+    c.slot_of_node = L->slot_of_node;
+    c.node_of_slot = L->node_of_slot;
+    c.nbr = L->nbr;
+    c.n_active = L->counts;
+    c.depth = L->depth;
+    c.nrm = L->nrm;
+    c.sp = L->sp;
+    c.sn = L->sn;
+    c.frac = L->sfrac;
+    c.cell = L->scell;
+    c.perm = L->perm;
+    c.n_samples = L->start ? L->start + c.nn : nullptr;
+    c.occ_cell = L->occ_cell;
+    c.occ_beg = L->occ_beg;
+    c.n_occ = L->counts + 1;
+    c.rec = L->rec;
+    c.pix = L->pix;
+    c.wc = L->wc;
+    c.fh = L->fh;
+    c.ft = L->ft;
+    c.sfrac = L->sfr;
+    c.scell = L->scell_s;
+    c.S = L->S;
+}
+
+void set_params_ctx(Ctx &c, const vd_solve_params *p) {
+    c.w_s = p->w_sparse;
+    c.w_d = p->w_dense;
+    c.w_r = p->w_reg;
+    c.eps_d = p->eps_d;
+    c.eps_n = p->eps_n;
+    c.eps_v = p->eps_v;
+}
+
+vd_status check_params(vd_lattice *L, const vd_solve_params *p) {
+    if (!p) return fail(L, VD_ERR_INVALID_ARG, "params is NULL");
+    if (p->gn_iters < 1 || p->gn_iters > 1000 || p->cg_iters < 0 || p->cg_iters > 100000)
+        return fail(L, VD_ERR_INVALID_ARG, "gn_iters must be in [1, 1000], cg_iters in [0, 100000]");
+    if (!(p->eps_d > 0) || !(p->eps_n > 0) || !(p->eps_v > 0))
+        return fail(L, VD_ERR_INVALID_ARG, "eps_d, eps_n, eps_v must be > 0");
+    if (!(p->w_sparse >= 0) || !(p->w_dense >= 0) || !(p->w_reg >= 0))
+        return fail(L, VD_ERR_INVALID_ARG, "weights must be >= 0");
+    if (!(p->cg_tol >= 0)) return fail(L, VD_ERR_INVALID_ARG, "cg_tol must be >= 0");
+    return VD_OK;
+}
+
+// ------------------------------------------------------------------ launch plumbing
+
+struct Grid {
+    int node, samp, cells;
+};
+
+Grid grids(vd_lattice *L) {
+    Grid g;
+    const int nact = L->all ? L->c.nn : round_pow2(std::max(L->n_active_h, 1));
+    g.node = blocks_for(nact);
+    g.samp = blocks_for(round_pow2(std::max(L->n_samples_h, 1)));
+    const long warps = round_pow2(std::max(L->n_occ_h, 1)) + (L->S + 31) / 32;
+    g.cells = blocks_for(warps * 32);
+    return g;
+}
+
+// bracket a launch of kernel class kc with profiling events when selected
+struct ProfScope {
+    vd_lattice *L;
+    bool on;
+    cudaStream_t st;
+    ProfScope(vd_lattice *L_, int kc, cudaStream_t st_) : L(L_), on(false), st(st_) {
+        if (L->prof_class == kc && L->ev_used + 2 <= (int)L->ev.size()) {
+            on = true;
+            cudaEventRecordWithFlags(L->ev[L->ev_used], st, cudaEventRecordExternal);
+        }
+        L->counting++;
+    }
+    ~ProfScope() {
+        if (on) {
+            cudaEventRecordWithFlags(L->ev[L->ev_used + 1], st, cudaEventRecordExternal);
+            L->ev_used += 2;
+        }
+    }
+};
+
+template <bool kAll>
+void enqueue_gn(vd_lattice *L, const vd_solve_params *P, int g, cudaStream_t st) {
+    const Grid gr = grids(L);
+    const Ctx c = L->c;
+    Scal *sc = slot(L, g);
+    const int K = P->cg_iters;
+    const bool assoc = !(P->fixed_association && g > 0);
+    if (assoc) {
+        ProfScope ps(L, VD_KC_ASSOCIATE, st);
+        k_associate<kAll><<<gr.samp, kThreads, 0, st>>>(c, sc);
+    }
+    {
+        ProfScope ps(L, VD_KC_RHS, st);
+        k_rhs_nodes<kAll><<<gr.node, kThreads, 0, st>>>(c);
+    }
+    {
+        ProfScope ps(L, VD_KC_RHS, st);
+        k_cells<kOpRhs, kAll><<<gr.cells, kThreads, 0, st>>>(c, sc, K, 0);
+    }
+    {
+        ProfScope ps(L, VD_KC_RHS, st);
+        k_pcg_init<kAll><<<gr.node, kThreads, 0, st>>>(c, sc);
+    }
+    const double tol2 = P->cg_tol * P->cg_tol;
+    for (int it = 0; it < K; it++) {
+        {
+            ProfScope ps(L, VD_KC_APPLY_STENCIL, st);
+            k_apply_stencil<kAll><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
+        }
+        {
+            ProfScope ps(L, VD_KC_APPLY_SAMPLES, st);
+            k_cells<kOpApply, kAll><<<gr.cells, kThreads, 0, st>>>(c, sc, K, it);
+        }
+        {
+            ProfScope ps(L, VD_KC_UPDATE_X, st);
+            k_update_x<kAll><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
+        }
+        {
+            ProfScope ps(L, VD_KC_UPDATE_P, st);
+            k_update_p<kAll><<<gr.node, kThreads, 0, st>>>(c, sc, it, tol2);
+        }
+    }
+    {
+        ProfScope ps(L, VD_KC_ROTATION, st);
+        k_add_increment<kAll><<<gr.node, kThreads, 0, st>>>(c);
+    }
+    {
+        ProfScope ps(L, VD_KC_ROTATION, st);
+        k_fit_rotations<kAll, true><<<gr.node, kThreads, 0, st>>>(c, sc);
+    }
+    {
+        ProfScope ps(L, VD_KC_ENERGY, st);
+        k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, sc, K, 0);
+    }
+}
+
+void enqueue_solve(vd_lattice *L, const vd_solve_params *P, cudaStream_t st) {
+    cudaMemsetAsync(L->scal, 0, L->scal_stride * (size_t)P->gn_iters, st);
+    if (P->init == VD_INIT_ZERO) {
+        L->counting++;
+        k_reset_warp<<<blocks_for(L->c.nn), kThreads, 0, st>>>(L->u, L->R, L->c.nn, L->c.ld);
+    }
+    for (int g = 0; g < P->gn_iters; g++) {
+        if (L->all) enqueue_gn<true>(L, P, g, st);
+        else enqueue_gn<false>(L, P, g, st);
+    }
+    L->counting++;
+    k_finish_report<<<1, 32, 0, st>>>((Scal *)L->scal, L->scal_stride, P->gn_iters, L->c, L->rep_dev);
+    cudaMemcpyAsync(L->rep_host, L->rep_dev, 10 * sizeof(double), cudaMemcpyDeviceToHost, st);
+}
+
+int class_launches_per_solve(const vd_solve_params *P, int kc) {
+    const int G = P->gn_iters, K = P->cg_iters;
+    const int assoc = P->fixed_association ? 1 : G;
+    switch (kc) {
+        case VD_KC_ASSOCIATE: return assoc;
+        case VD_KC_RHS: return 3 * G;
+        case VD_KC_APPLY_STENCIL:
+        case VD_KC_APPLY_SAMPLES:
+        case VD_KC_UPDATE_X:
+        case VD_KC_UPDATE_P: return K * G;
+        case VD_KC_ROTATION: return 2 * G;
+        case VD_KC_ENERGY: return G;
+        default: return 0;
+    }
+}
+
+vd_status build_graph(vd_lattice *L, const vd_solve_params *P) {
+    const Grid gr = grids(L);
+    const int caps[4] = {gr.node, gr.samp, gr.cells, L->S};
+    const bool same = L->gexec && L->ggen == L->gen && !memcmp(&L->gparams, P, sizeof(*P)) &&
+                      !memcmp(L->gkey_caps, caps, sizeof(caps)) && !memcmp(&L->gctx, &L->c, sizeof(Ctx));
+    if (same) return VD_OK;
+    if (L->gexec) {
+        cudaGraphExecDestroy(L->gexec);
+        L->gexec = nullptr;
+    }
+    // profiling events for the selected class
+    const int need = L->prof_class >= 0 ? 2 * class_launches_per_solve(P, L->prof_class) : 0;
+    while ((int)L->ev.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        L->ev.push_back(e);
+    }
+    L->ev_used = 0;
+    L->counting = 0;
+    CK(cudaStreamBeginCapture(L->cap, cudaStreamCaptureModeThreadLocal));
+    enqueue_solve(L, P, L->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(L->cap, &graph);
+    if (e != cudaSuccess) return fail(L, VD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&L->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(L, VD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    L->launches_solve = L->counting;
+    L->gparams = *P;
+    L->gctx = L->c;
+    memcpy(L->gkey_caps, caps, sizeof(caps));
+    L->ggen = L->gen;
+    return VD_OK;
+}
+
+vd_status collect_profile(vd_lattice *L) {
+    for (int k = 0; k + 1 < L->ev_used; k += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, L->ev[k], L->ev[k + 1]));
+        L->prof_ms += ms;
+        L->prof_launches++;
+    }
+    return VD_OK;
+}
+
+vd_status read_report(vd_lattice *L, vd_solve_report *out) {
+    const double *r = L->rep_host;
+    vd_status st = VD_OK;
+    if (r[9] == 0.0) st = fail(L, VD_ERR_NUMERIC, "non-finite energy after the solve");
+    if (out) {
+        out->e_total = r[0];
+        out->e_dense = r[1];
+        out->e_sparse = r[2];
+        out->e_reg = r[3];
+        out->gn_done = (int)r[4];
+        out->cg_done = (int)r[5];
+        out->n_valid_corr = (int)r[6];
+        out->n_degenerate_rot = (int)r[7];
+        out->n_refined = (int)r[8];
+        out->status = st;
+    }
+    return st;
+}
+
+vd_status frame_active_set(vd_lattice *L) {
+    const Ctx c = L->c;
+    cudaStream_t st = L->stream;
+    if (L->all) return VD_OK;
+    CK(cudaMemsetAsync(L->mark, 0, sizeof(int) * (size_t)c.nn, st));
+    k_mark_cells<<<blocks_for(std::max(L->cap_src, 1) + L->S), kThreads, 0, st>>>(L->occ_cell, L->counts + 1,
+                                                                                   L->scell_s, L->S, c, L->mark);
+    k_dilate<<<blocks_for(c.nn), kThreads, 0, st>>>(L->mark, c, L->act);
+    scan_launch(L->act, c.nn, L->slot_of_node, L->counts, L->scan_sums, st);
+    k_compact<<<blocks_for(c.nn), kThreads, 0, st>>>(L->act, c, L->slot_of_node, L->node_of_slot);
+    k_neighbour_table<<<blocks_for(c.nn), kThreads, 0, st>>>(c, L->nbr);
+    CKL();
+    return VD_OK;
+}
+
+vd_status sync_sizes(vd_lattice *L) {
+    int h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, L->counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+    int ns = 0;
+    if (L->start) CK(cudaMemcpyAsync(&ns, L->start + L->c.nn, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+    L->n_active_h = L->all ? L->c.nn : h[0];
+    L->n_occ_h = h[1];
+    L->n_samples_h = ns;
+    return VD_OK;
+}
+
+vd_status step_prepare(vd_lattice *L, const vd_solve_params *P, int K) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    TRY(check_params(L, P));
+    if (!L->have_frame) return fail(L, VD_ERR_STATE, "no frame");
+    TRY(ensure_scal(L, 1, K));
+    set_params_ctx(L->c, P);
+    refresh_ctx(L);
+    return VD_OK;
+}
+
+template <bool kAll>
+void rhs_launch(vd_lattice *L, cudaStream_t st) {
+    const Grid gr = grids(L);
+    k_rhs_nodes<kAll><<<gr.node, kThreads, 0, st>>>(L->c);
+    k_cells<kOpRhs, kAll><<<gr.cells, kThreads, 0, st>>>(L->c, slot(L, 0), 1, 0);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
+    if (!d || !out) return VD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (d->nx < 2 || d->ny < 2 || d->nz < 2 || !(d->spacing > 0.f)) return VD_ERR_INVALID_ARG;
+    if (d->active_mode != VD_ACTIVE_SURFACE && d->active_mode != VD_ACTIVE_ALL) return VD_ERR_INVALID_ARG;
+    if (d->precision != VD_PREC_FP32) return VD_ERR_INVALID_ARG;
+    const long nn = (long)d->nx * d->ny * d->nz;
+    if (nn > (long)kScanTile * kScanTile) return VD_ERR_INVALID_ARG;  // scan limit: 16.7M nodes
+    vd_lattice *L = new (std::nothrow) vd_lattice();
+    if (!L) return VD_ERR_OOM;
+    Ctx &c = L->c;
+    c.nx = d->nx;
+    c.ny = d->ny;
+    c.nz = d->nz;
+    c.nn = (int)nn;
+    c.ld = (int)((nn + 31) / 32 * 32);
+    c.ox = d->origin[0];
+    c.oy = d->origin[1];
+    c.oz = d->origin[2];
+    c.h = d->spacing;
+    for (int a = 0; a < 9; a++) c.Rg[a] = (a % 4 == 0) ? 1.f : 0.f;
+    L->all = d->active_mode == VD_ACTIVE_ALL;
+    L->precision = d->precision;
+    vd_status s = VD_OK;
+    auto bail = [&](vd_status st) {
+        vd_destroy_lattice(L);
+        return st;
+    };
+    if (d->cuda_stream) {
+        L->stream = (cudaStream_t)d->cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(VD_ERR_CUDA);
+        L->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking) != cudaSuccess) return bail(VD_ERR_CUDA);
+    const size_t ld = c.ld;
+    if ((s = dalloc(L, &L->u, 3 * ld)) || (s = dalloc(L, &L->R, 9 * ld)) || (s = dalloc(L, &L->vecs, 15 * ld)) ||
+        (s = dalloc(L, &L->counts, 8)) || (s = dalloc(L, &L->cnt, ld)) || (s = dalloc(L, &L->start, ld + 1)) ||
+        (s = dalloc(L, &L->staging, 9 * ld)) || (s = dalloc(L, &L->rep_dev, 16)))
+        return bail(s);
+    if (!L->all) {
+        if ((s = dalloc(L, &L->slot_of_node, ld + 1)) || (s = dalloc(L, &L->node_of_slot, ld)) ||
+            (s = dalloc(L, &L->nbr, 6 * ld)) || (s = dalloc(L, &L->mark, ld)) || (s = dalloc(L, &L->act, ld)))
+            return bail(s);
+    }
+    if (cudaMallocHost(&L->rep_host, 16 * sizeof(double)) != cudaSuccess) return bail(VD_ERR_OOM);
+    memset(L->rep_host, 0, 16 * sizeof(double));
+    refresh_ctx(L);
+    k_reset_warp<<<blocks_for(c.nn), kThreads, 0, L->stream>>>(L->u, L->R, c.nn, c.ld);
+    if (cudaMemsetAsync(L->vecs, 0, sizeof(float) * 15 * ld, L->stream) != cudaSuccess ||
+        cudaMemsetAsync(L->counts, 0, 8 * sizeof(int), L->stream) != cudaSuccess ||
+        cudaMemsetAsync(L->start, 0, sizeof(int) * (ld + 1), L->stream) != cudaSuccess ||
+        cudaStreamSynchronize(L->stream) != cudaSuccess)
+        return bail(VD_ERR_CUDA);
+    *out = L;
+    return VD_OK;
+}
+
+vd_status vd_destroy_lattice(vd_lattice *L) {
+    if (!L) return VD_OK;
+    if (L->stream) cudaStreamSynchronize(L->stream);
+    if (L->gexec) cudaGraphExecDestroy(L->gexec);
+    for (auto &b : L->bufs) cudaFree(b.ptr);
+    for (auto e : L->ev) cudaEventDestroy(e);
+    if (L->rep_host) cudaFreeHost(L->rep_host);
+    if (L->cap) cudaStreamDestroy(L->cap);
+    if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+    delete L;
+    return VD_OK;
+}
+
+const char *vd_last_error(const vd_lattice *L) { return L ? L->err.c_str() : "null lattice"; }
+
+vd_status vd_set_correspondences(vd_lattice *L, const float *canon, const float *target, int S, int mem) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (S < 0 || (S > 0 && (!canon || !target))) return fail(L, VD_ERR_INVALID_ARG, "bad correspondences");
+    if (S > L->cap_S) {
+        dfree(L, L->sp_in);
+        dfree(L, L->fh);
+        dfree(L, L->ft);
+        dfree(L, L->sfr);
+        dfree(L, L->scell_s);
+        L->cap_S = std::max(S, 64);
+        TRY(dalloc(L, &L->sp_in, (size_t)L->cap_S * 6));
+        TRY(dalloc(L, &L->fh, (size_t)L->cap_S));
+        TRY(dalloc(L, &L->ft, (size_t)L->cap_S));
+        TRY(dalloc(L, &L->sfr, (size_t)L->cap_S));
+        TRY(dalloc(L, &L->scell_s, (size_t)L->cap_S));
+    }
+    L->S = S;
+    refresh_ctx(L);
+    if (S > 0) {
+        TRY(upload(L, L->sp_in, canon, sizeof(float) * 3 * S, mem));
+        TRY(upload(L, L->sp_in + 3 * (size_t)S, target, sizeof(float) * 3 * S, mem));
+        k_point_cells<<<blocks_for(S), kThreads, 0, L->stream>>>(L->sp_in, S, L->c, L->scell_s, L->sfr);
+        k_pack_float4<<<blocks_for(S), kThreads, 0, L->stream>>>(L->sp_in, S, L->fh);
+        k_pack_float4<<<blocks_for(S), kThreads, 0, L->stream>>>(L->sp_in + 3 * (size_t)S, S, L->ft);
+        CKL();
+    }
+    if (L->have_frame) TRY(frame_active_set(L));
+    TRY(sync_sizes(L));
+    return VD_OK;
+}
+
+vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const float K[4], const float pose[12],
+                       const float *src_pts, const float *src_nrm, int n_src, int mem) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (W < 3 || H < 3 || !depth || !K) return fail(L, VD_ERR_INVALID_ARG, "depth map must be at least 3x3");
+    if (n_src < 0 || (n_src > 0 && (!src_pts || !src_nrm))) return fail(L, VD_ERR_INVALID_ARG, "bad samples");
+    if (!(K[0] > 0) || !(K[1] > 0)) return fail(L, VD_ERR_INVALID_ARG, "focal lengths must be > 0");
+    if ((long)W * H > (long)kScanTile * kScanTile || n_src > kScanTile * kScanTile)
+        return fail(L, VD_ERR_INVALID_ARG, "frame too large");
+    TRY(ensure_frame_caps(L, W, H, n_src));
+    Ctx &c = L->c;
+    L->W = W;
+    L->H = H;
+    c.W = W;
+    c.H = H;
+    c.fx = K[0];
+    c.fy = K[1];
+    c.cx = K[2];
+    c.cy = K[3];
+    for (int a = 0; a < 9; a++) c.Rg[a] = pose ? pose[a] : ((a % 4 == 0) ? 1.f : 0.f);
+    for (int a = 0; a < 3; a++) c.tg[a] = pose ? pose[9 + a] : 0.f;
+    L->n_src = n_src;
+    refresh_ctx(L);
+    cudaStream_t st = L->stream;
+    L->counting = 0;
+    TRY(upload(L, L->depth, depth, sizeof(float) * (size_t)W * H, mem));
+    TRY(upload(L, L->pts_in, src_pts, sizeof(float) * 3 * (size_t)n_src, mem));
+    TRY(upload(L, L->nrm_in, src_nrm, sizeof(float) * 3 * (size_t)n_src, mem));
+    dim3 b2(32, 8), g2((W + 31) / 32, (H + 7) / 8);
+    k_target_normals<<<g2, b2, 0, st>>>(L->depth, L->nrm, W, H, c.fx, c.fy, c.cx, c.cy);
+    // bin the samples by cell (counting sort with a deterministic order inside a cell)
+    CK(cudaMemsetAsync(L->cnt, 0, sizeof(int) * (size_t)c.nn, st));
+    CK(cudaMemsetAsync(L->head, 0, sizeof(int) * (size_t)L->cap_src, st));
+    const int nb = blocks_for(std::max(n_src, 1));
+    k_point_cells<<<nb, kThreads, 0, st>>>(L->pts_in, n_src, c, L->cell_in, L->frac_in);
+    k_histogram<<<nb, kThreads, 0, st>>>(L->cell_in, n_src, L->cnt);
+    scan_launch(L->cnt, c.nn, L->start, L->start + c.nn, L->scan_sums, st);
+    k_bin_scatter<<<nb, kThreads, 0, st>>>(L->cell_in, n_src, L->start, L->cnt, L->tmp);
+    k_bin_rank<<<nb, kThreads, 0, st>>>(L->tmp, L->cell_in, L->start, L->start + c.nn, L->order);
+    k_bin_gather<<<nb, kThreads, 0, st>>>(L->order, L->start + c.nn, L->pts_in, L->nrm_in, L->cell_in, L->frac_in,
+                                          L->sp, L->sn, L->scell, L->sfrac, L->perm, L->head);
+    scan_launch(L->head, std::max(n_src, 1), L->hscan, L->counts + 1, L->scan_sums, st);
+    k_occupied<<<nb, kThreads, 0, st>>>(L->head, L->hscan, L->start + c.nn, L->scell, L->counts + 1, L->occ_cell,
+                                        L->occ_beg);
+    CKL();
+    L->have_frame = true;
+    TRY(frame_active_set(L));
+    TRY(sync_sizes(L));
+    L->launches_frame = 13 + (L->all ? 0 : 7);
+    return VD_OK;
+}
+
+vd_status vd_solve_async(vd_lattice *L, const vd_solve_params *P) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    TRY(check_params(L, P));
+    if (!L->have_frame) return fail(L, VD_ERR_STATE, "vd_solve before vd_set_frame");
+    TRY(ensure_scal(L, P->gn_iters, P->cg_iters));
+    set_params_ctx(L->c, P);
+    refresh_ctx(L);
+    TRY(build_graph(L, P));
+    CK(cudaGraphLaunch(L->gexec, L->stream));
+    L->solve_pending = true;
+    return VD_OK;
+}
+
+vd_status vd_get_report(vd_lattice *L, vd_solve_report *out) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(L->stream));
+    if (L->solve_pending && L->prof_class >= 0) TRY(collect_profile(L));
+    L->solve_pending = false;
+    return read_report(L, out);
+}
+
+vd_status vd_solve(vd_lattice *L, const vd_solve_params *P, vd_solve_report *out) {
+    TRY(vd_solve_async(L, P));
+    return vd_get_report(L, out);
+}
+
+vd_status vd_get_warp(const vd_lattice *Lc, float *disp, float *rot, int mem) {
+    vd_lattice *L = const_cast<vd_lattice *>(Lc);
+    if (!L) return VD_ERR_INVALID_ARG;
+    const Ctx &c = L->c;
+    cudaStream_t st = L->stream;
+    if (disp) {
+        k_soa_to_aos<<<blocks_for(c.nn), kThreads, 0, st>>>(L->u, 3, c.nn, c.ld, L->staging);
+        CKL();
+        TRY(download(L, disp, L->staging, sizeof(float) * 3 * (size_t)c.nn, mem));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (rot) {
+        k_soa_to_aos<<<blocks_for(c.nn), kThreads, 0, st>>>(L->R, 9, c.nn, c.ld, L->staging);
+        CKL();
+        TRY(download(L, rot, L->staging, sizeof(float) * 9 * (size_t)c.nn, mem));
+        CK(cudaStreamSynchronize(st));
+    }
+    return VD_OK;
+}
+
+vd_status vd_set_warp(vd_lattice *L, const float *disp, const float *rot, int mem) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    const Ctx &c = L->c;
+    cudaStream_t st = L->stream;
+    k_reset_warp<<<blocks_for(c.nn), kThreads, 0, st>>>(L->u, L->R, c.nn, c.ld);
+    if (disp) {
+        TRY(upload(L, L->staging, disp, sizeof(float) * 3 * (size_t)c.nn, mem));
+        k_aos_to_soa<<<blocks_for(c.nn), kThreads, 0, st>>>(L->staging, 3, c.nn, c.ld, L->u);
+    }
+    if (rot) {  // same staging buffer: the copies and conversions are ordered on one stream
+        TRY(upload(L, L->staging, rot, sizeof(float) * 9 * (size_t)c.nn, mem));
+        k_aos_to_soa<<<blocks_for(c.nn), kThreads, 0, st>>>(L->staging, 9, c.nn, c.ld, L->R);
+    }
+    CKL();
+    CK(cudaStreamSynchronize(st));
+    return VD_OK;
+}
+
+vd_status vd_num_active(const vd_lattice *L, int *n) {
+    if (!L || !n) return VD_ERR_INVALID_ARG;
+    *n = L->all ? L->c.nn : (L->have_frame ? L->n_active_h : 0);
+    return VD_OK;
+}
+
+vd_status vd_get_active(const vd_lattice *Lc, unsigned char *mask, int mem) {
+    vd_lattice *L = const_cast<vd_lattice *>(Lc);
+    if (!L || !mask) return VD_ERR_INVALID_ARG;
+    const int nn = L->c.nn;
+    std::vector<unsigned char> h(nn, 1);
+    if (!L->all) {
+        std::vector<int> s(nn);
+        if (L->have_frame) {
+            CK(cudaMemcpyAsync(s.data(), L->slot_of_node, sizeof(int) * nn, cudaMemcpyDeviceToHost, L->stream));
+            CK(cudaStreamSynchronize(L->stream));
+            for (int i = 0; i < nn; i++) h[i] = s[i] >= 0;
+        } else {
+            std::fill(h.begin(), h.end(), 0);
+        }
+    }
+    if (mem == VD_MEM_DEVICE) {
+        CK(cudaMemcpyAsync(mask, h.data(), nn, cudaMemcpyHostToDevice, L->stream));
+        CK(cudaStreamSynchronize(L->stream));
+    } else {
+        memcpy(mask, h.data(), nn);
+    }
+    return VD_OK;
+}
+
+vd_status vd_get_target_normals(const vd_lattice *Lc, float *nrm, int mem) {
+    vd_lattice *L = const_cast<vd_lattice *>(Lc);
+    if (!L || !nrm) return VD_ERR_INVALID_ARG;
+    if (!L->have_frame) return fail(L, VD_ERR_STATE, "no frame");
+    const int n = L->W * L->H;
+    std::vector<float4> h(n);
+    CK(cudaMemcpyAsync(h.data(), L->nrm, sizeof(float4) * n, cudaMemcpyDeviceToHost, L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+    std::vector<float> o(3 * (size_t)n);
+    for (int i = 0; i < n; i++) {
+        o[3 * i] = h[i].x;
+        o[3 * i + 1] = h[i].y;
+        o[3 * i + 2] = h[i].z;
+    }
+    if (mem == VD_MEM_DEVICE) {
+        CK(cudaMemcpyAsync(nrm, o.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, L->stream));
+        CK(cudaStreamSynchronize(L->stream));
+    } else {
+        memcpy(nrm, o.data(), sizeof(float) * 3 * n);
+    }
+    return VD_OK;
+}
+
+// ---- step API (eager launches on the lattice stream; scalar slot 0)
+
+vd_status vd_step_associate(vd_lattice *L, const vd_solve_params *P) {
+    TRY(step_prepare(L, P, std::max(P ? P->cg_iters : 0, 1)));
+    const Grid gr = grids(L);
+    CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, L->stream));
+    if (L->all) k_associate<true><<<gr.samp, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+    else k_associate<false><<<gr.samp, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+    CKL();
+    CK(cudaStreamSynchronize(L->stream));
+    return VD_OK;
+}
+
+vd_status vd_get_association(vd_lattice *L, const vd_solve_params *P, int *pix, float *w, float *r, int mem) {
+    TRY(step_prepare(L, P, std::max(P ? P->cg_iters : 0, 1)));
+    const int n = L->n_src;
+    int *dp = L->res_i;
+    float *dw = L->res_f, *dr = L->res_f + L->cap_src;
+    k_clear_association<<<blocks_for(std::max(n, 1)), kThreads, 0, L->stream>>>(n, dp, dw, dr);
+    if (L->all) k_unsort_association<true><<<blocks_for(std::max(n, 1)), kThreads, 0, L->stream>>>(L->c, dp, dw, dr);
+    else k_unsort_association<false><<<blocks_for(std::max(n, 1)), kThreads, 0, L->stream>>>(L->c, dp, dw, dr);
+    CKL();
+    if (pix) TRY(download(L, pix, dp, sizeof(int) * n, mem));
+    if (w) TRY(download(L, w, dw, sizeof(float) * n, mem));
+    if (r) TRY(download(L, r, dr, sizeof(float) * n, mem));
+    CK(cudaStreamSynchronize(L->stream));
+    return VD_OK;
+}
+
+vd_status vd_step_rhs(vd_lattice *L, const vd_solve_params *P, float *b, float *diag, int mem) {
+    TRY(step_prepare(L, P, 1));
+    cudaStream_t st = L->stream;
+    if (L->all) rhs_launch<true>(L, st);
+    else rhs_launch<false>(L, st);
+    const Ctx &c = L->c;
+    float *out[2] = {b, diag};
+    const float *src[2] = {c.r, c.minv};
+    for (int k = 0; k < 2; k++) {
+        if (!out[k]) continue;
+        if (L->all) k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(src[k], c, L->staging);
+        else k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(src[k], c, L->staging);
+        CKL();
+        TRY(download(L, out[k], L->staging, sizeof(float) * 3 * (size_t)c.nn, mem));
+        CK(cudaStreamSynchronize(st));
+    }
+    CKL();
+    CK(cudaStreamSynchronize(st));
+    return VD_OK;
+}
+
+vd_status vd_step_apply(vd_lattice *L, const vd_solve_params *P, const float *p, float *Ap, double *pAp, int mem) {
+    TRY(step_prepare(L, P, 1));
+    if (!p || !Ap) return fail(L, VD_ERR_INVALID_ARG, "p and Ap are required");
+    cudaStream_t st = L->stream;
+    const Ctx &c = L->c;
+    const Grid gr = grids(L);
+    TRY(upload(L, L->staging, p, sizeof(float) * 3 * (size_t)c.nn, mem));
+    CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, st));
+    Scal *sc = slot(L, 0);
+    // the gates of the apply kernels read rho[0] > 0
+    const double one = 1.0;
+    CK(cudaMemcpyAsync((char *)sc + offsetof(Scal, rho), &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    if (L->all) {
+        k_gather_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(L->staging, c, c.p);
+        k_apply_stencil<true><<<gr.node, kThreads, 0, st>>>(c, sc, 1, 0);
+        k_cells<kOpApply, true><<<gr.cells, kThreads, 0, st>>>(c, sc, 1, 0);
+        k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.q, c, L->staging);
+    } else {
+        k_gather_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(L->staging, c, c.p);
+        k_apply_stencil<false><<<gr.node, kThreads, 0, st>>>(c, sc, 1, 0);
+        k_cells<kOpApply, false><<<gr.cells, kThreads, 0, st>>>(c, sc, 1, 0);
+        k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.q, c, L->staging);
+    }
+    CKL();
+    TRY(download(L, Ap, L->staging, sizeof(float) * 3 * (size_t)c.nn, mem));
+    double h[4];
+    CK(cudaMemcpyAsync(h, (char *)sc + offsetof(Scal, rho), 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (pAp) *pAp = h[2];  // pq[0] sits after rho[0..K] with K = 1
+    return VD_OK;
+}
+
+vd_status vd_step_pcg(vd_lattice *L, const vd_solve_params *P, float *delta, int *iters, int apply, int mem) {
+    TRY(step_prepare(L, P, std::max(P ? P->cg_iters : 0, 1)));
+    cudaStream_t st = L->stream;
+    const Ctx &c = L->c;
+    const Grid gr = grids(L);
+    const int K = P->cg_iters;
+    TRY(ensure_scal(L, 1, K));
+    Scal *sc = slot(L, 0);
+    CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, st));
+    const double tol2 = P->cg_tol * P->cg_tol;
+    if (L->all) {
+        rhs_launch<true>(L, st);
+        k_pcg_init<true><<<gr.node, kThreads, 0, st>>>(c, sc);
+        for (int it = 0; it < K; it++) {
+            k_apply_stencil<true><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
+            k_cells<kOpApply, true><<<gr.cells, kThreads, 0, st>>>(c, sc, K, it);
+            k_update_x<true><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
+            k_update_p<true><<<gr.node, kThreads, 0, st>>>(c, sc, it, tol2);
+        }
+        if (delta) k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
+        if (apply) k_add_increment<true><<<gr.node, kThreads, 0, st>>>(c);
+    } else {
+        rhs_launch<false>(L, st);
+        k_pcg_init<false><<<gr.node, kThreads, 0, st>>>(c, sc);
+        for (int it = 0; it < K; it++) {
+            k_apply_stencil<false><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
+            k_cells<kOpApply, false><<<gr.cells, kThreads, 0, st>>>(c, sc, K, it);
+            k_update_x<false><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
+            k_update_p<false><<<gr.node, kThreads, 0, st>>>(c, sc, it, tol2);
+        }
+        if (delta) k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
+        if (apply) k_add_increment<false><<<gr.node, kThreads, 0, st>>>(c);
+    }
+    CKL();
+    if (delta) TRY(download(L, delta, L->staging, sizeof(float) * 3 * (size_t)c.nn, mem));
+    int done = 0;
+    CK(cudaMemcpyAsync(&done, (char *)sc + offsetof(Scal, cg_done), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (iters) *iters = done;
+    return VD_OK;
+}
+
+vd_status vd_step_fit_rotations(vd_lattice *L, int *n_degenerate) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (!L->have_frame && !L->all) return fail(L, VD_ERR_STATE, "no frame");
+    TRY(ensure_scal(L, 1, 1));
+    refresh_ctx(L);
+    cudaStream_t st = L->stream;
+    const Grid gr = grids(L);
+    CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, st));
+    if (L->all) k_fit_rotations<true, true><<<gr.node, kThreads, 0, st>>>(L->c, slot(L, 0));
+    else k_fit_rotations<false, true><<<gr.node, kThreads, 0, st>>>(L->c, slot(L, 0));
+    CKL();
+    int d = 0;
+    CK(cudaMemcpyAsync(&d, (char *)slot(L, 0) + offsetof(Scal, n_degenerate), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_degenerate) *n_degenerate = d;
+    return VD_OK;
+}
+
+vd_status vd_step_energy(vd_lattice *L, const vd_solve_params *P, double out[4]) {
+    TRY(step_prepare(L, P, 1));
+    if (!out) return fail(L, VD_ERR_INVALID_ARG, "out is NULL");
+    cudaStream_t st = L->stream;
+    const Grid gr = grids(L);
+    Scal *sc = slot(L, 0);
+    CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, st));
+    if (L->all) {
+        k_fit_rotations<true, false><<<gr.node, kThreads, 0, st>>>(L->c, sc);
+        k_cells<kOpEnergy, true><<<gr.cells, kThreads, 0, st>>>(L->c, sc, 1, 0);
+    } else {
+        k_fit_rotations<false, false><<<gr.node, kThreads, 0, st>>>(L->c, sc);
+        k_cells<kOpEnergy, false><<<gr.cells, kThreads, 0, st>>>(L->c, sc, 1, 0);
+    }
+    CKL();
+    double h[3];
+    CK(cudaMemcpyAsync(h, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out[1] = h[0];
+    out[2] = h[1];
+    out[3] = h[2];
+    out[0] = (double)P->w_sparse * h[1] + (double)P->w_dense * h[0] + (double)P->w_reg * h[2];
+    return VD_OK;
+}
+
+vd_status vd_profile_select(vd_lattice *L, int kc) {
+    if (!L || kc < -1 || kc >= VD_KC_COUNT) return VD_ERR_INVALID_ARG;
+    if (kc != L->prof_class) {
+        L->prof_class = kc;
+        L->ggen = -1;  // force a re-capture
+    }
+    L->prof_ms = 0.0;
+    L->prof_launches = 0;
+    return VD_OK;
+}
+
+vd_status vd_profile_read(vd_lattice *L, double *total_ms, int *launches) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (total_ms) *total_ms = L->prof_ms;
+    if (launches) *launches = L->prof_launches;
+    L->prof_ms = 0.0;
+    L->prof_launches = 0;
+    return VD_OK;
+}
+
+vd_status vd_launch_counts(vd_lattice *L, const vd_solve_params *P, int *per_solve, int *per_frame) {
+    if (!L || !P) return VD_ERR_INVALID_ARG;
+    TRY(check_params(L, P));
+    const int G = P->gn_iters, K = P->cg_iters;
+    const int assoc = P->fixed_association ? 1 : G;
+    const int n = assoc + G * (3 + 4 * K + 3) + 1 + (P->init == VD_INIT_ZERO ? 1 : 0);
+    if (per_solve) *per_solve = n;
+    if (per_frame) *per_frame = L->launches_frame;
+    return VD_OK;
+}
+
+}  // extern "C"

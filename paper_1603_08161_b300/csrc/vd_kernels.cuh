@@ -1,0 +1,1189 @@
+// Device code of libvd: the per-frame flip-flop lattice solve of VolumeDeform
+// (arXiv 1603.08161, Sec. 4-7) for sm_103a.
+//
+// Data layout in HBM (per lattice):
+//   * node-indexed state u (3 x ld floats, SoA) and R (9 x ld floats, SoA, row-major
+//     entry (r, c) at plane 3r + c), ld = nodes rounded up to 32;
+//   * slot-indexed solver vectors x, r, p, q, Minv (3 x ld each, SoA): slot = node in
+//     all-nodes mode, a compact index into the active set M in surface mode;
+//   * source samples sorted by lattice cell (float4 point / normal / fractions, int
+//     cell), with a list of occupied cells and their sample ranges; per-sample
+//     association record float4 (g', r0') written once per Gauss-Newton iteration;
+//   * FP64 scalars (PCG rho / p.Ap per iteration, energies) per iteration slot.
+// Every reduction sums in FP32 within a warp and in FP64 across warps and blocks.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vd {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kThreads = 256;
+
+struct Ctx {
+    // lattice
+    int nx, ny, nz, nn, ld;
+    float ox, oy, oz, h;
+    // frame
+    int W, H;
+    float fx, fy, cx, cy;
+    float Rg[9], tg[3];
+    // weights / thresholds
+    float w_s, w_d, w_r, eps_d, eps_n, eps_v;
+    // state (node-indexed)
+    float *u, *R;
+    // active set
+    const int *slot_of_node, *node_of_slot, *nbr;
+    const int *n_active;
+    // solver vectors (slot-indexed)
+    float *x, *r, *p, *q, *minv;
+    // frame data
+    const float *depth;
+    const float4 *nrm;
+    // sorted samples
+    const float4 *sp, *sn, *frac;
+    const int *cell, *perm;
+    const int *n_samples;
+    const int *occ_cell, *occ_beg, *n_occ;
+    float4 *rec;
+    int *pix;
+    float *wc;
+    // sparse pairs
+    const float4 *fh, *ft, *sfrac;
+    const int *scell;
+    int S;
+};
+
+// Per-Gauss-Newton-iteration scalar block (FP64 sums and counters), zeroed at the
+// start of every solve.
+struct Scal {
+    double e_dense, e_sparse, e_reg, pad;
+    int stop, cg_done, n_valid, n_refined, n_degenerate, assoc_ran, pad2, pad3;
+    double rho[1];  // rho[0..K], then pq[0..K-1] follow (layout set by the host)
+};
+
+__host__ __device__ inline size_t scal_bytes(int K) {
+    return (sizeof(Scal) + sizeof(double) * (size_t)(2 * K + 2) + 255) & ~(size_t)255;
+}
+__device__ __forceinline__ double *scal_rho(Scal *s) { return s->rho; }
+__device__ __forceinline__ double *scal_pq(Scal *s, int K) { return s->rho + K + 1; }
+
+// ------------------------------------------------------------------ reductions
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Block-wide sum of one float per thread, accumulated in FP64 across warps; thread 0
+// adds the result to *dst.  Every thread of the block must call it.
+__device__ __forceinline__ void block_add_f64(float v, double *dst) {
+    __shared__ double part[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = (double)v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += part[k];
+        if (s != 0.0) atomicAdd(dst, s);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void block_add_f64d(double v, double *dst) {
+    __shared__ double partd[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) partd[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += partd[k];
+        if (s != 0.0) atomicAdd(dst, s);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void block_add_int(int v, int *dst) {
+    __shared__ int parti[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) parti[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += parti[k];
+        if (s) atomicAdd(dst, s);
+    }
+    __syncthreads();
+}
+
+// Reduce 32 per-lane values so that lane l ends with the warp-wide sum of value l
+// (recursive halving: 31 shuffles for 32 sums).
+__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int j = 0; j < off; j++) {
+            const float send = upper ? v[j] : v[j + off];
+            const float keep = upper ? v[j + off] : v[j];
+            v[j] = keep + __shfl_xor_sync(FULL, send, off);
+        }
+    }
+    return v[0];
+}
+
+// ------------------------------------------------------------------ lattice helpers
+
+__device__ __forceinline__ int corner_node(const Ctx &c, int cell, int k) {
+    return cell + (k & 1) + c.nx * (((k >> 1) & 1) + c.ny * ((k >> 2) & 1));
+}
+
+template <typename T>
+__device__ __forceinline__ T trilinear_weight(const T f[3], int k) {
+    const T wx = (k & 1) ? f[0] : T(1) - f[0];
+    const T wy = (k & 2) ? f[1] : T(1) - f[1];
+    const T wz = (k & 4) ? f[2] : T(1) - f[2];
+    return wx * wy * wz;
+}
+
+template <bool kAll>
+__device__ __forceinline__ int slot_node(const Ctx &c, int s) {
+    return kAll ? s : c.node_of_slot[s];
+}
+
+template <bool kAll>
+__device__ __forceinline__ int node_slot(const Ctx &c, int node) {
+    return kAll ? node : c.slot_of_node[node];
+}
+
+template <bool kAll>
+__device__ __forceinline__ int active_count(const Ctx &c) {
+    return kAll ? c.nn : *c.n_active;
+}
+
+// 6-neighbourhood of slot s inside M (order -x, +x, -y, +y, -z, +z), -1 where absent.
+template <bool kAll>
+__device__ __forceinline__ void neighbours(const Ctx &c, int s, int nb[6]) {
+    if (kAll) {
+        const int x = s % c.nx, t = s / c.nx, y = t % c.ny, z = t / c.ny;
+        const int pl = c.nx * c.ny;
+        nb[0] = x > 0 ? s - 1 : -1;
+        nb[1] = x + 1 < c.nx ? s + 1 : -1;
+        nb[2] = y > 0 ? s - c.nx : -1;
+        nb[3] = y + 1 < c.ny ? s + c.nx : -1;
+        nb[4] = z > 0 ? s - pl : -1;
+        nb[5] = z + 1 < c.nz ? s + pl : -1;
+    } else {
+#pragma unroll
+        for (int d = 0; d < 6; d++) nb[d] = c.nbr[d * c.ld + s];
+    }
+}
+
+__device__ __forceinline__ float3 ld3(const float *v, int ld, int i) {
+    return make_float3(v[i], v[ld + i], v[2 * ld + i]);
+}
+__device__ __forceinline__ void st3(float *v, int ld, int i, float3 a) {
+    v[i] = a.x;
+    v[ld + i] = a.y;
+    v[2 * ld + i] = a.z;
+}
+
+// ------------------------------------------------------------------ frame kernels
+
+// Target normal of every pixel: cross product of the central differences of the
+// back-projected depth map V(u, v) = D (u - cx, v - cy) / f (z = D), normalised and
+// oriented towards the camera; invalid (w = 0) on the border or next to a hole.
+// The differences are rearranged so that no two ~1 m values are subtracted:
+//   x(u+1) - x(u-1) = [(D(u+1) - D(u-1)) (u - cx) + D(u+1) + D(u-1)] / fx.
+__global__ void k_target_normals(const float *__restrict__ D, float4 *__restrict__ nrm, int W, int H,
+                                 float fx, float fy, float cx, float cy) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= W || v >= H) return;
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (u >= 1 && v >= 1 && u + 1 < W && v + 1 < H) {
+        const size_t k = (size_t)v * W + u;
+        const float d0 = D[k], dl = D[k - 1], dr = D[k + 1], du = D[k - W], dd = D[k + W];
+        if (d0 > 0.f && dl > 0.f && dr > 0.f && du > 0.f && dd > 0.f) {
+            const float a = (float)u - cx, b = (float)v - cy;
+            const float dh = dr - dl, dv = dd - du;
+            const float ex = (dh * a + (dr + dl)) / fx, ey = dh * b / fy, ez = dh;
+            const float gx = dv * a / fx, gy = (dv * b + (dd + du)) / fy, gz = dv;
+            float n0 = ey * gz - ez * gy, n1 = ez * gx - ex * gz, n2 = ex * gy - ey * gx;
+            const float L2 = n0 * n0 + n1 * n1 + n2 * n2;
+            if (L2 > 0.f) {
+                const float inv = 1.0f / sqrtf(L2);
+                n0 *= inv;
+                n1 *= inv;
+                n2 *= inv;
+                if (n0 * (a / fx) + n1 * (b / fy) + n2 > 0.f) {
+                    n0 = -n0;
+                    n1 = -n1;
+                    n2 = -n2;
+                }
+                out = make_float4(n0, n1, n2, 1.f);
+            }
+        }
+    }
+    nrm[(size_t)v * W + u] = out;
+}
+
+// Cell of each point (lower-corner node, or -1 when the cell is not inside the
+// lattice) and its trilinear fractions.  The floor decision is taken in FP64 on
+// (p - origin) / h, so it does not depend on FP32 rounding.
+__global__ void k_point_cells(const float *__restrict__ pts, int n, Ctx c, int *__restrict__ cell,
+                              float4 *__restrict__ frac) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double o[3] = {(double)c.ox, (double)c.oy, (double)c.oz};
+        const int dims[3] = {c.nx, c.ny, c.nz};
+        double f[3];
+        int ci[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double q = __ddiv_rn(__dsub_rn((double)pts[3 * i + a], o[a]), (double)c.h);
+            const double fl = floor(q);
+            if (!(fl >= 0.0) || fl > (double)(dims[a] - 2)) ok = false;
+            ci[a] = ok ? (int)fl : 0;
+            f[a] = q - fl;
+        }
+        cell[i] = ok ? ci[0] + c.nx * (ci[1] + c.ny * ci[2]) : -1;
+        frac[i] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.f);
+    }
+}
+
+__global__ void k_histogram(const int *__restrict__ cell, int n, int *__restrict__ cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (cell[i] >= 0) atomicAdd(&cnt[cell[i]], 1);
+}
+
+// ---- exclusive scan of int arrays (3 passes: 4096-element tiles, tile sums, add)
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    const int before = (wid > 0 ? ws[wid - 1] : 0) + x - v;
+    if (total) *total = ws[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+// out[i] = sum_{j < i} in[i] for i < n; tile sums to sums[blockIdx.x]
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int *__restrict__ in, int n,
+                                                             int *__restrict__ out, int *__restrict__ sums) {
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    int v[kScanPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = block_exclusive_scan(s, &total);
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// single block: exclusive scan of the tile sums (at most kScanTile of them); the
+// grand total goes to out_total
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int *__restrict__ sums, int nt, int *__restrict__ out_total) {
+    const int base = threadIdx.x * kScanPer;
+    int v[kScanPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        v[k] = (base + k < nt) ? sums[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = block_exclusive_scan(s, &total);
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        if (base + k < nt) sums[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) *out_total = total;
+}
+
+__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ sums) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / kScanTile];
+}
+
+// Counting-sort scatter: each valid sample takes a slot in its cell's range.
+__global__ void k_bin_scatter(const int *__restrict__ cell, int n, const int *__restrict__ start,
+                              int *__restrict__ cnt, int *__restrict__ tmp) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int cl = cell[i];
+        if (cl < 0) continue;
+        const int pos = start[cl] + atomicSub(&cnt[cl], 1) - 1;
+        tmp[pos] = i;
+    }
+}
+
+// Deterministic order inside each cell: rank by original index.
+__global__ void k_bin_rank(const int *__restrict__ tmp, const int *__restrict__ cell,
+                           const int *__restrict__ start, const int *__restrict__ total,
+                           int *__restrict__ order) {
+    const int n = *total;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c0 = tmp[i], cl = cell[c0];
+        const int beg = start[cl], end = start[cl + 1];
+        int rank = 0;
+        for (int j = beg; j < end; j++) rank += tmp[j] < c0;
+        order[beg + rank] = c0;
+    }
+}
+
+// Gather the samples into sorted order; mark the first sample of every cell.
+__global__ void k_bin_gather(const int *__restrict__ order, const int *__restrict__ total,
+                             const float *__restrict__ pts, const float *__restrict__ nrms,
+                             const int *__restrict__ cell, const float4 *__restrict__ frac,
+                             float4 *__restrict__ sp, float4 *__restrict__ sn, int *__restrict__ scell,
+                             float4 *__restrict__ sfrac, int *__restrict__ perm, int *__restrict__ head) {
+    const int n = *total;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c0 = order[i];
+        sp[i] = make_float4(pts[3 * c0], pts[3 * c0 + 1], pts[3 * c0 + 2], 0.f);
+        sn[i] = make_float4(nrms[3 * c0], nrms[3 * c0 + 1], nrms[3 * c0 + 2], 0.f);
+        scell[i] = cell[c0];
+        sfrac[i] = frac[c0];
+        perm[i] = c0;
+        head[i] = (i == 0 || cell[order[i - 1]] != cell[c0]) ? 1 : 0;
+    }
+}
+
+__global__ void k_occupied(const int *__restrict__ head, const int *__restrict__ hscan,
+                           const int *__restrict__ total, const int *__restrict__ scell,
+                           const int *__restrict__ n_occ, int *__restrict__ occ_cell, int *__restrict__ occ_beg) {
+    const int n = *total;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (head[i]) {
+            occ_cell[hscan[i]] = scell[i];
+            occ_beg[hscan[i]] = i;
+        }
+    if (blockIdx.x == 0 && threadIdx.x == 0) occ_beg[*n_occ] = n;
+}
+
+// ---- active set M (surface mode): corners of occupied cells, then their one-ring
+__global__ void k_mark_cells(const int *__restrict__ occ_cell, const int *__restrict__ n_occ,
+                             const int *__restrict__ scell, int S, Ctx c, int *__restrict__ mark) {
+    const int no = *n_occ;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < no + S; i += gridDim.x * blockDim.x) {
+        const int cl = i < no ? occ_cell[i] : scell[i - no];
+        if (cl < 0) continue;
+#pragma unroll
+        for (int k = 0; k < 8; k++) mark[corner_node(c, cl, k)] = 1;
+    }
+}
+
+__global__ void k_dilate(const int *__restrict__ mark, Ctx c, int *__restrict__ act) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.nn; i += gridDim.x * blockDim.x) {
+        const int x = i % c.nx, t = i / c.nx, y = t % c.ny, z = t / c.ny, pl = c.nx * c.ny;
+        int on = mark[i];
+        on |= (x > 0 && mark[i - 1]) | (x + 1 < c.nx && mark[i + 1]);
+        on |= (y > 0 && mark[i - c.nx]) | (y + 1 < c.ny && mark[i + c.nx]);
+        on |= (z > 0 && mark[i - pl]) | (z + 1 < c.nz && mark[i + pl]);
+        act[i] = on ? 1 : 0;
+    }
+}
+
+// slot_of_node holds the exclusive scan of act on entry; -1 for nodes outside M after.
+__global__ void k_compact(const int *__restrict__ act, Ctx c, int *__restrict__ slot_of_node,
+                          int *__restrict__ node_of_slot) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.nn; i += gridDim.x * blockDim.x) {
+        if (act[i]) node_of_slot[slot_of_node[i]] = i;
+        else slot_of_node[i] = -1;
+    }
+}
+
+__global__ void k_neighbour_table(Ctx c, int *__restrict__ nbr) {
+    const int N = *c.n_active;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int i = c.node_of_slot[s];
+        const int x = i % c.nx, t = i / c.nx, y = t % c.ny, z = t / c.ny, pl = c.nx * c.ny;
+        const int nd[6] = {x > 0 ? i - 1 : -1, x + 1 < c.nx ? i + 1 : -1, y > 0 ? i - c.nx : -1,
+                           y + 1 < c.ny ? i + c.nx : -1, z > 0 ? i - pl : -1, z + 1 < c.nz ? i + pl : -1};
+#pragma unroll
+        for (int d = 0; d < 6; d++) nbr[d * c.ld + s] = nd[d] >= 0 ? c.slot_of_node[nd[d]] : -1;
+    }
+}
+
+// ------------------------------------------------------------------ association (Sec. 5.1)
+
+template <typename T>
+struct V3 {
+    T x, y, z;
+};
+
+template <typename T>
+__device__ __forceinline__ T dot(const V3<T> &a, const V3<T> &b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+
+template <typename T>
+__device__ __forceinline__ V3<T> rot(const float *M, const V3<T> &v) {  // row-major 3x3
+    return {T(M[0]) * v.x + T(M[1]) * v.y + T(M[2]) * v.z, T(M[3]) * v.x + T(M[4]) * v.y + T(M[5]) * v.z,
+            T(M[6]) * v.x + T(M[7]) * v.y + T(M[8]) * v.z};
+}
+
+template <typename T>
+__device__ __forceinline__ V3<T> rotT(const float *M, const V3<T> &v) {
+    return {T(M[0]) * v.x + T(M[3]) * v.y + T(M[6]) * v.z, T(M[1]) * v.x + T(M[4]) * v.y + T(M[7]) * v.z,
+            T(M[2]) * v.x + T(M[5]) * v.y + T(M[8]) * v.z};
+}
+
+__device__ __forceinline__ double depth_at(const Ctx &c, int px, int py) {
+    return (double)c.depth[(size_t)py * c.W + px];
+}
+
+// Target normal in FP64 from the depth map (plain central differences of V).
+__device__ bool target_normal_f64(const Ctx &c, int px, int py, V3<double> &n) {
+    if (px < 1 || py < 1 || px + 1 >= c.W || py + 1 >= c.H) return false;
+    const double d0 = depth_at(c, px, py), dl = depth_at(c, px - 1, py), dr = depth_at(c, px + 1, py);
+    const double du = depth_at(c, px, py - 1), dd = depth_at(c, px, py + 1);
+    if (!(d0 > 0 && dl > 0 && dr > 0 && du > 0 && dd > 0)) return false;
+    const double fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy;
+    auto V = [&](double d, int uu, int vv) {
+        return V3<double>{d * ((uu - cx) / fx), d * ((vv - cy) / fy), d};
+    };
+    const V3<double> a = V(dr, px + 1, py), b = V(dl, px - 1, py), e = V(dd, px, py + 1), f = V(du, px, py - 1);
+    const V3<double> ex{a.x - b.x, a.y - b.y, a.z - b.z}, ey{e.x - f.x, e.y - f.y, e.z - f.z};
+    V3<double> m{ex.y * ey.z - ex.z * ey.y, ex.z * ey.x - ex.x * ey.z, ex.x * ey.y - ex.y * ey.x};
+    const double L = sqrt(dot(m, m));
+    if (!(L > 0)) return false;
+    m = {m.x / L, m.y / L, m.z / L};
+    const V3<double> P = V(d0, px, py);
+    if (dot(m, P) > 0) m = {-m.x, -m.y, -m.z};
+    n = m;
+    return true;
+}
+
+// Association of sorted sample i at the current warp, in precision T.  Returns true
+// (T = float only) when a decision (pixel, range, any Phi < 0) lies within a margin
+// of its threshold that FP32 rounding could cross; the caller then repeats it in FP64.
+template <typename T, bool kAll>
+__device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, float4 &rec) {
+    constexpr bool kF32 = sizeof(T) == 4;
+    pix = -1;
+    w_out = 0.f;
+    rec = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int cl = c.cell[i];
+    const float4 p4 = c.sp[i], n4 = c.sn[i];
+    T f[3];
+    if (kF32) {
+        const float4 f4 = c.frac[i];
+        f[0] = f4.x;
+        f[1] = f4.y;
+        f[2] = f4.z;
+    } else {
+        const int cx_ = cl % c.nx, t = cl / c.nx, cy_ = t % c.ny, cz_ = t / c.ny;
+        f[0] = T(((double)p4.x - (double)c.ox) / (double)c.h - cx_);
+        f[1] = T(((double)p4.y - (double)c.oy) / (double)c.h - cy_);
+        f[2] = T(((double)p4.z - (double)c.oz) / (double)c.h - cz_);
+    }
+    V3<T> du{0, 0, 0}, dn{0, 0, 0};
+    const V3<T> nh{T(n4.x), T(n4.y), T(n4.z)};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int node = corner_node(c, cl, k);
+        const T al = trilinear_weight(f, k);
+        du.x += al * T(c.u[node]);
+        du.y += al * T(c.u[c.ld + node]);
+        du.z += al * T(c.u[2 * c.ld + node]);
+        float Rk[9];
+#pragma unroll
+        for (int e = 0; e < 9; e++) Rk[e] = c.R[e * c.ld + node];
+        const V3<T> rn = rot<T>(Rk, nh);
+        dn.x += al * rn.x;
+        dn.y += al * rn.y;
+        dn.z += al * rn.z;
+    }
+    const V3<T> q{T(p4.x) + du.x, T(p4.y) + du.y, T(p4.z) + du.z};
+    V3<T> p = rot<T>(c.Rg, q);
+    p.x += T(c.tg[0]);
+    p.y += T(c.tg[1]);
+    p.z += T(c.tg[2]);
+    V3<T> n = rot<T>(c.Rg, dn);
+    const T nl = sqrt(dot(n, n));
+    bool near = false;
+    if (!(nl > T(0))) return false;
+    n = {n.x / nl, n.y / nl, n.z / nl};
+    if (kF32 && fabs((double)p.z) < 1e-4) near = true;
+    if (!(p.z > T(0))) return near;
+    const T uf = T(c.fx) * p.x / p.z + T(c.cx) + T(0.5);
+    const T vf = T(c.fy) * p.y / p.z + T(c.cy) + T(0.5);
+    const T pxf = floor(uf), pyf = floor(vf);
+    if (kF32) {
+        const float mu = (float)uf - (float)pxf, mv = (float)vf - (float)pyf;
+        if (mu < 2e-3f || mu > 1.f - 2e-3f || mv < 2e-3f || mv > 1.f - 2e-3f) near = true;
+    }
+    if (!(pxf >= T(0) && pxf < T(c.W) && pyf >= T(0) && pyf < T(c.H))) return near;
+    const int px = (int)pxf, py = (int)pyf;
+    const size_t k = (size_t)py * c.W + px;
+    const float D = c.depth[k];
+    if (!(D > 0.f)) return near;
+    V3<T> na;
+    if (kF32) {
+        const float4 m = c.nrm[k];
+        if (m.w == 0.f) return near;
+        na = {T(m.x), T(m.y), T(m.z)};
+    } else {
+        V3<double> m;
+        if (!target_normal_f64(c, px, py, m)) return false;
+        na = {T(m.x), T(m.y), T(m.z)};
+    }
+    const V3<T> pa{T(D) * ((T(px) - T(c.cx)) / T(c.fx)), T(D) * ((T(py) - T(c.cy)) / T(c.fy)), T(D)};
+    const V3<T> dd{p.x - pa.x, p.y - pa.y, p.z - pa.z};
+    const T dist = sqrt(dot(dd, dd));
+    const T cn = dot(n, na);
+    const T pl = sqrt(dot(p, p));
+    const T cv = -dot(n, p) / pl;
+    if (kF32) {
+        if (fabsf((float)dist - c.eps_d) < 1e-5f) near = true;
+        if (fabsf((1.f - (float)cn) - c.eps_n) < 1e-4f) near = true;
+        if (fabsf((1.f - (float)cv) - c.eps_v) < 1e-4f) near = true;
+    }
+    pix = (int)k;
+    const T phi_d = T(1) - dist / T(c.eps_d);
+    const T phi_n = T(1) - (T(1) - cn) / T(c.eps_n);
+    const T phi_v = T(1) - (T(1) - cv) / T(c.eps_v);
+    if (phi_d < T(0) || phi_n < T(0) || phi_v < T(0)) return near;
+    const T m = (phi_d + phi_n + phi_v) / T(3);
+    const T w = m * m;
+    const T sw = sqrt(w);
+    // g' = sqrt(w_c) R_g^T n^a ; r0' = sqrt(w_c) n^a . (R_g p^ + t_g - p^a)  (FP64)
+    const V3<T> gt = rotT<T>(c.Rg, na);
+    const V3<double> nad{(double)na.x, (double)na.y, (double)na.z};
+    V3<double> q0 = rot<double>(c.Rg, V3<double>{(double)p4.x, (double)p4.y, (double)p4.z});
+    q0.x += (double)c.tg[0] - (double)pa.x;
+    q0.y += (double)c.tg[1] - (double)pa.y;
+    q0.z += (double)c.tg[2] - (double)pa.z;
+    const double r0 = (double)sw * dot(nad, q0);
+    w_out = (float)w;
+    rec = make_float4((float)(sw * gt.x), (float)(sw * gt.y), (float)(sw * gt.z), (float)r0);
+    return near;
+}
+
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
+    const int n = *c.n_samples;
+    int valid = 0, refined = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int pix;
+        float w;
+        float4 rec;
+        const bool near = associate_sample<float, kAll>(c, i, pix, w, rec);
+        if (near) {
+            associate_sample<double, kAll>(c, i, pix, w, rec);
+            refined++;
+        }
+        c.pix[i] = pix;
+        c.wc[i] = w;
+        c.rec[i] = rec;
+        valid += w > 0.f;
+    }
+    block_add_int(valid, &sc->n_valid);
+    block_add_int(refined, &sc->n_refined);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->assoc_ran = 1;
+}
+
+// ------------------------------------------------------------------ per-cell sample passes
+
+enum CellOp { kOpRhs = 0, kOpApply = 1, kOpEnergy = 2 };
+
+// One warp per occupied cell: every sample of the cell touches the same 8 corners,
+// so the corner vectors are loaded once and the 24 per-corner sums are reduced in
+// the warp before one atomic per corner component.  Warps past the occupied cells
+// take the sparse pairs (one per lane).
+//   kOpRhs:    r_k -= alpha_k w_d g' (g' . sum alpha u + r0'),  diag_k += alpha_k^2 w_d g'^2
+//              (sparse: b -= sqrt(w_s) alpha_k R_g^T r_s, diag += w_s alpha_k^2 |R_g col|^2)
+//   kOpApply:  q_k += alpha_k w_d g' (g' . sum alpha p);  p.Ap partial += w_d s^2
+//   kOpEnergy: E_dense += (g' . sum alpha u + r0')^2;  E_sparse += |S(f^) - f|^2
+template <int kOp, bool kAll>
+__global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int it) {
+    if (kOp == kOpApply) {
+        if (sc->stop || !(scal_rho(sc)[it] > 0.0)) return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int warps_per_block = blockDim.x >> 5;
+    const int n_occ = *c.n_occ;
+    const int n_sparse_warps = (c.S + 31) >> 5;
+    const int total = n_occ + n_sparse_warps;
+    const float *vec = (kOp == kOpApply) ? c.p : c.u;  // slot- or node-indexed
+    float part = 0.f;
+    double partd = 0.0;
+    for (int w = blockIdx.x * warps_per_block + (threadIdx.x >> 5); w < total; w += gridDim.x * warps_per_block) {
+        if (w < n_occ) {
+            const int cl = c.occ_cell[w];
+            const int beg = c.occ_beg[w], end = c.occ_beg[w + 1];
+            // corner k = lane & 7, component a = lane >> 3 (lanes 0..23)
+            const int node = corner_node(c, cl, lane & 7);
+            const int slot = node_slot<kAll>(c, node);
+            const int vi = (kOp == kOpApply) ? slot : node;
+            const float mine = lane < 24 ? vec[(lane >> 3) * c.ld + vi] : 0.f;
+            float cv[24];
+#pragma unroll
+            for (int e = 0; e < 24; e++) cv[e] = __shfl_sync(FULL, mine, e);
+            float acc[32], acc2[32];
+#pragma unroll
+            for (int e = 0; e < 32; e++) acc[e] = acc2[e] = 0.f;
+            for (int j = beg + lane; j < end; j += 32) {
+                const float4 f4 = c.frac[j], g = c.rec[j];
+                const float f[3] = {f4.x, f4.y, f4.z};
+                float al[8];
+                float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    al[k] = trilinear_weight(f, k);
+                    sx += al[k] * cv[k];
+                    sy += al[k] * cv[8 + k];
+                    sz += al[k] * cv[16 + k];
+                }
+                const float s = g.x * sx + g.y * sy + g.z * sz;
+                if (kOp == kOpApply) {
+                    const float t = c.w_d * s;
+                    part += t * s;
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        acc[k] += al[k] * g.x * t;
+                        acc[8 + k] += al[k] * g.y * t;
+                        acc[16 + k] += al[k] * g.z * t;
+                    }
+                } else if (kOp == kOpRhs) {
+                    const float t = -c.w_d * (s + g.w);
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        acc[k] += al[k] * g.x * t;
+                        acc[8 + k] += al[k] * g.y * t;
+                        acc[16 + k] += al[k] * g.z * t;
+                        const float a2 = al[k] * al[k] * c.w_d;
+                        acc2[k] += a2 * g.x * g.x;
+                        acc2[8 + k] += a2 * g.y * g.y;
+                        acc2[16 + k] += a2 * g.z * g.z;
+                    }
+                } else {
+                    const float e = s + g.w;
+                    part += e * e;
+                }
+            }
+            if (kOp != kOpEnergy) {
+                const float tot = warp_transpose_sum32(acc);
+                float *dst = (kOp == kOpApply) ? c.q : c.r;
+                if (lane < 24 && tot != 0.f) atomicAdd(&dst[(lane >> 3) * c.ld + slot], tot);
+                if (kOp == kOpRhs) {
+                    const float tot2 = warp_transpose_sum32(acc2);
+                    if (lane < 24 && tot2 != 0.f) atomicAdd(&c.minv[(lane >> 3) * c.ld + slot], tot2);
+                }
+            }
+        } else {
+            const int s = (w - n_occ) * 32 + lane;
+            if (s < c.S && c.scell[s] >= 0) {
+                const int cl = c.scell[s];
+                const float4 f4 = c.sfrac[s];
+                const float f[3] = {f4.x, f4.y, f4.z};
+                float al[8];
+                int nd[8];
+                V3<float> sv{0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    al[k] = trilinear_weight(f, k);
+                    nd[k] = corner_node(c, cl, k);
+                    const int vi = (kOp == kOpApply) ? node_slot<kAll>(c, nd[k]) : nd[k];
+                    sv.x += al[k] * vec[vi];
+                    sv.y += al[k] * vec[c.ld + vi];
+                    sv.z += al[k] * vec[2 * c.ld + vi];
+                }
+                if (kOp == kOpApply) {
+                    // s = sqrt(w_s) R_g sum alpha p ; q_k += sqrt(w_s) alpha_k R_g^T s
+                    const V3<float> t = rot<float>(c.Rg, sv);
+                    part += c.w_s * dot(t, t);
+                    const V3<float> back = rotT<float>(c.Rg, t);
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        const int sl = node_slot<kAll>(c, nd[k]);
+                        const float a = c.w_s * al[k];
+                        atomicAdd(&c.q[sl], a * back.x);
+                        atomicAdd(&c.q[c.ld + sl], a * back.y);
+                        atomicAdd(&c.q[2 * c.ld + sl], a * back.z);
+                    }
+                } else {
+                    // residual S(f^) - f in FP64: R_g (f^ + sum alpha u) + t_g - f
+                    const float4 fh = c.fh[s], ft = c.ft[s];
+                    const V3<double> xq{(double)fh.x + sv.x, (double)fh.y + sv.y, (double)fh.z + sv.z};
+                    V3<double> d = rot<double>(c.Rg, xq);
+                    d.x += (double)c.tg[0] - (double)ft.x;
+                    d.y += (double)c.tg[1] - (double)ft.y;
+                    d.z += (double)c.tg[2] - (double)ft.z;
+                    if (kOp == kOpEnergy) {
+                        partd += dot(d, d);
+                    } else {
+                        // b_k -= w_s alpha_k R_g^T d ; diag_k += w_s alpha_k^2 (R_g^T R_g)_aa
+                        const V3<float> back = rotT<float>(c.Rg, V3<float>{(float)d.x, (float)d.y, (float)d.z});
+                        float cn[3];
+#pragma unroll
+                        for (int a = 0; a < 3; a++)
+                            cn[a] = c.Rg[a] * c.Rg[a] + c.Rg[3 + a] * c.Rg[3 + a] + c.Rg[6 + a] * c.Rg[6 + a];
+#pragma unroll
+                        for (int k = 0; k < 8; k++) {
+                            const int sl = node_slot<kAll>(c, nd[k]);
+                            const float a = c.w_s * al[k];
+                            atomicAdd(&c.r[sl], -a * back.x);
+                            atomicAdd(&c.r[c.ld + sl], -a * back.y);
+                            atomicAdd(&c.r[2 * c.ld + sl], -a * back.z);
+                            const float a2 = a * al[k];
+                            atomicAdd(&c.minv[sl], a2 * cn[0]);
+                            atomicAdd(&c.minv[c.ld + sl], a2 * cn[1]);
+                            atomicAdd(&c.minv[2 * c.ld + sl], a2 * cn[2]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (kOp == kOpApply) block_add_f64(part, scal_pq(sc, K) + it);
+    if (kOp == kOpEnergy) {
+        block_add_f64(part, &sc->e_dense);
+        block_add_f64d(partd, &sc->e_sparse);
+    }
+}
+
+// ------------------------------------------------------------------ node passes
+
+// ARAP part of the right-hand side and the Jacobi diagonal (Eq. 4 with R fixed):
+//   b_k = -w_r sum_{j in N_k} [2 (u_k - u_j) - (R_k + R_j - 2I)(t^_k - t^_j)],
+//   diag_k = 2 w_r |N_k|.  Written with plain stores (the sample pass adds after).
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_rhs_nodes(Ctx c) {
+    const int N = active_count<kAll>(c);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int i = slot_node<kAll>(c, s);
+        int nb[6];
+        neighbours<kAll>(c, s, nb);
+        const float3 ui = ld3(c.u, c.ld, i);
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        int deg = 0;
+#pragma unroll
+        for (int d = 0; d < 6; d++) {
+            if (nb[d] < 0) continue;
+            const int j = slot_node<kAll>(c, nb[d]);
+            const int a = d >> 1;
+            const float sg = (d & 1) ? c.h : -c.h;  // t^_k - t^_j = -sg e_a
+            const float3 uj = ld3(c.u, c.ld, j);
+            // column a of R_k + R_j - 2 I
+            const float cx = c.R[a * c.ld + i] + c.R[a * c.ld + j] - (a == 0 ? 2.f : 0.f);
+            const float cy = c.R[(3 + a) * c.ld + i] + c.R[(3 + a) * c.ld + j] - (a == 1 ? 2.f : 0.f);
+            const float cz = c.R[(6 + a) * c.ld + i] + c.R[(6 + a) * c.ld + j] - (a == 2 ? 2.f : 0.f);
+            bx -= c.w_r * (2.f * (ui.x - uj.x) + sg * cx);
+            by -= c.w_r * (2.f * (ui.y - uj.y) + sg * cy);
+            bz -= c.w_r * (2.f * (ui.z - uj.z) + sg * cz);
+            deg++;
+        }
+        st3(c.r, c.ld, s, make_float3(bx, by, bz));
+        const float dg = 2.f * c.w_r * (float)deg;
+        st3(c.minv, c.ld, s, make_float3(dg, dg, dg));
+    }
+}
+
+// PCG start (x0 = 0): Minv = 1/diag (0 where diag = 0), r = b, p = z = Minv r, rho0 = r.z
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_pcg_init(Ctx c, Scal *sc) {
+    const int N = active_count<kAll>(c);
+    float part = 0.f;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int k = a * c.ld + s;
+            const float dg = c.minv[k];
+            const float mi = dg > 0.f ? 1.0f / dg : 0.f;
+            const float rr = c.r[k];
+            const float z = mi * rr;
+            c.minv[k] = mi;
+            c.p[k] = z;
+            c.x[k] = 0.f;
+            part += rr * z;
+        }
+    }
+    block_add_f64(part, &scal_rho(sc)[0]);
+}
+
+// q = 2 w_r L p (7-point graph Laplacian of M), with the partial p.q
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_apply_stencil(Ctx c, Scal *sc, int K, int it) {
+    if (sc->stop || !(scal_rho(sc)[it] > 0.0)) return;
+    const int N = active_count<kAll>(c);
+    float part = 0.f;
+    const float w2 = 2.f * c.w_r;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        int nb[6];
+        neighbours<kAll>(c, s, nb);
+        const float3 pi = ld3(c.p, c.ld, s);
+        float qx = 0.f, qy = 0.f, qz = 0.f;
+#pragma unroll
+        for (int d = 0; d < 6; d++) {
+            if (nb[d] < 0) continue;
+            const float3 pj = ld3(c.p, c.ld, nb[d]);
+            qx += pi.x - pj.x;
+            qy += pi.y - pj.y;
+            qz += pi.z - pj.z;
+        }
+        qx *= w2;
+        qy *= w2;
+        qz *= w2;
+        st3(c.q, c.ld, s, make_float3(qx, qy, qz));
+        part += pi.x * qx + pi.y * qy + pi.z * qz;
+    }
+    block_add_f64(part, scal_pq(sc, K) + it);
+}
+
+// alpha = rho/pq; x += alpha p; r -= alpha q; z = Minv r; partial rho' = r.z
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_update_x(Ctx c, Scal *sc, int K, int it) {
+    const double rho = scal_rho(sc)[it], pq = scal_pq(sc, K)[it];
+    if (sc->stop || !(rho > 0.0) || !(pq > 0.0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) sc->stop = 1;
+        return;
+    }
+    const float alpha = (float)(rho / pq);
+    const int N = active_count<kAll>(c);
+    float part = 0.f;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int k = a * c.ld + s;
+            c.x[k] += alpha * c.p[k];
+            const float rr = c.r[k] - alpha * c.q[k];
+            c.r[k] = rr;
+            part += rr * (c.minv[k] * rr);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->cg_done = it + 1;
+    block_add_f64(part, &scal_rho(sc)[it + 1]);
+}
+
+// beta = rho'/rho; p = Minv r + beta p (stop once rho' <= tol^2 rho0)
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_update_p(Ctx c, Scal *sc, int it, double tol2) {
+    if (sc->stop) return;
+    const double rho1 = scal_rho(sc)[it + 1], rho = scal_rho(sc)[it];
+    if (rho1 <= tol2 * scal_rho(sc)[0]) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) sc->stop = 1;
+        return;
+    }
+    const float beta = (float)(rho1 / rho);
+    const int N = active_count<kAll>(c);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int k = a * c.ld + s;
+            c.p[k] = c.minv[k] * c.r[k] + beta * c.p[k];
+        }
+    }
+}
+
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_add_increment(Ctx c) {
+    const int N = active_count<kAll>(c);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int i = slot_node<kAll>(c, s);
+#pragma unroll
+        for (int a = 0; a < 3; a++) c.u[a * c.ld + i] += c.x[a * c.ld + s];
+    }
+}
+
+// ------------------------------------------------------------------ rotation step (Sec. 7.1)
+
+// Largest-eigenvalue eigenvector of a symmetric 4x4 matrix by cyclic Jacobi
+// rotations (Golub & Van Loan, Sec. 8.5); returns lambda_1 - lambda_2.
+__device__ __forceinline__ float sym4_top_eigvec(float a[4][4], float q[4]) {
+    float v[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int s = 0; s < 4; s++) v[r][s] = r == s ? 1.f : 0.f;
+#pragma unroll 1
+    for (int sweep = 0; sweep < 10; sweep++) {
+        float off = 0.f, dia = 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            dia += a[r][r] * a[r][r];
+#pragma unroll
+            for (int s = r + 1; s < 4; s++) off += a[r][s] * a[r][s];
+        }
+        if (off <= 1e-14f * dia || off == 0.f) break;
+#pragma unroll
+        for (int pp = 0; pp < 3; pp++)
+#pragma unroll
+            for (int qq = pp + 1; qq < 4; qq++) {
+                const float apq = a[pp][qq];
+                if (apq == 0.f) continue;
+                const float th = (a[qq][qq] - a[pp][pp]) / (2.f * apq);
+                const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+                const float cs = 1.f / sqrtf(fmaf(t, t, 1.f)), sn = t * cs;
+                // A <- J^T A J with J the rotation in the (pp, qq) plane
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float akp = a[k][pp], akq = a[k][qq];
+                    a[k][pp] = cs * akp - sn * akq;
+                    a[k][qq] = sn * akp + cs * akq;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float apk = a[pp][k], aqk = a[qq][k];
+                    a[pp][k] = cs * apk - sn * aqk;
+                    a[qq][k] = sn * apk + cs * aqk;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float vkp = v[k][pp], vkq = v[k][qq];
+                    v[k][pp] = cs * vkp - sn * vkq;
+                    v[k][qq] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    int best = 0;
+    float l1 = a[0][0];
+#pragma unroll
+    for (int r = 1; r < 4; r++)
+        if (a[r][r] > l1) {
+            l1 = a[r][r];
+            best = r;
+        }
+    float l2 = -3.4e38f;
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+        if (r != best && a[r][r] > l2) l2 = a[r][r];
+#pragma unroll
+    for (int r = 0; r < 4; r++) q[r] = v[r][best];
+    return l1 - l2;
+}
+
+// Per node: A_i = sum_{j in N_i} (t_i - t_j)(t^_i - t^_j)^T (scaled by 1/h^2), and
+// R_i = argmax_R tr(R^T A_i) through the unit quaternion of Horn's 4x4 matrix
+// (Horn 1987, closed-form absolute orientation).  Nodes whose neighbours span fewer
+// than two axes, or whose top eigenvalue is (numerically) double, keep R_i.
+// Also accumulates E_reg (Eq. 4) with the new rotations (kFit = false: E_reg only).
+template <bool kAll, bool kFit>
+__global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
+    const int N = active_count<kAll>(c);
+    float part = 0.f;
+    int degenerate = 0;
+    const float ih = 1.f / c.h;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int i = slot_node<kAll>(c, s);
+        int nb[6], nj[6];
+        neighbours<kAll>(c, s, nb);
+        const float3 ui = ld3(c.u, c.ld, i);
+        float3 uj[6];
+        float A[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        int axes = 0;
+#pragma unroll
+        for (int d = 0; d < 6; d++) {
+            nj[d] = nb[d] >= 0 ? slot_node<kAll>(c, nb[d]) : -1;
+            if (nj[d] < 0) continue;
+            const int a = d >> 1;
+            axes |= 1 << a;
+            uj[d] = ld3(c.u, c.ld, nj[d]);
+            // column a of A/h^2: e_a + (u_j - u_i)/h for +a, e_a + (u_i - u_j)/h for -a
+            const float sg = (d & 1) ? ih : -ih;
+            A[0][a] += (a == 0 ? 1.f : 0.f) + sg * (uj[d].x - ui.x);
+            A[1][a] += (a == 1 ? 1.f : 0.f) + sg * (uj[d].y - ui.y);
+            A[2][a] += (a == 2 ? 1.f : 0.f) + sg * (uj[d].z - ui.z);
+        }
+        float Ri[9];
+#pragma unroll
+        for (int e = 0; e < 9; e++) Ri[e] = c.R[e * c.ld + i];
+        const bool two_axes = __popc(axes) >= 2;
+        bool keep = !two_axes;
+        if (kFit && two_axes) {
+            // Horn's matrix from S = A^T (S_ab = sum_j e_a d_b)
+            const float Sxx = A[0][0], Sxy = A[1][0], Sxz = A[2][0];
+            const float Syx = A[0][1], Syy = A[1][1], Syz = A[2][1];
+            const float Szx = A[0][2], Szy = A[1][2], Szz = A[2][2];
+            float Nm[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
+                              {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
+                              {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
+                              {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
+            float scale = 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) scale = fmaxf(scale, fabsf(Nm[r][k]));
+            float qv[4];
+            const float gap = sym4_top_eigvec(Nm, qv);
+            if (!(gap > 1e-5f * scale)) {
+                keep = true;
+            } else {
+                const float w = qv[0], x = qv[1], y = qv[2], z = qv[3];
+                const float inv = 1.f / (w * w + x * x + y * y + z * z);
+                Ri[0] = (w * w + x * x - y * y - z * z) * inv;
+                Ri[1] = 2.f * (x * y - w * z) * inv;
+                Ri[2] = 2.f * (x * z + w * y) * inv;
+                Ri[3] = 2.f * (x * y + w * z) * inv;
+                Ri[4] = (w * w - x * x + y * y - z * z) * inv;
+                Ri[5] = 2.f * (y * z - w * x) * inv;
+                Ri[6] = 2.f * (x * z - w * y) * inv;
+                Ri[7] = 2.f * (y * z + w * x) * inv;
+                Ri[8] = (w * w - x * x - y * y + z * z) * inv;
+#pragma unroll
+                for (int e = 0; e < 9; e++) c.R[e * c.ld + i] = Ri[e];
+            }
+        }
+        degenerate += kFit && keep;
+        // E_reg terms of the directed edges i -> j: (u_i - u_j) - (R_i - I)(t^_i - t^_j)
+#pragma unroll
+        for (int d = 0; d < 6; d++) {
+            if (nj[d] < 0) continue;
+            const int a = d >> 1;
+            const float sg = (d & 1) ? c.h : -c.h;  // t^_i - t^_j = -sg e_a
+            const float ex = sg * (Ri[a] - (a == 0 ? 1.f : 0.f));
+            const float ey = sg * (Ri[3 + a] - (a == 1 ? 1.f : 0.f));
+            const float ez = sg * (Ri[6 + a] - (a == 2 ? 1.f : 0.f));
+            const float rx = (ui.x - uj[d].x) + ex, ry = (ui.y - uj[d].y) + ey, rz = (ui.z - uj[d].z) + ez;
+            part += rx * rx + ry * ry + rz * rz;
+        }
+    }
+    block_add_f64(part, &sc->e_reg);
+    block_add_int(degenerate, &sc->n_degenerate);
+}
+
+// ------------------------------------------------------------------ layout helpers
+
+// AoS full-lattice (n x 3) -> slot SoA vector; entries outside M are dropped
+template <bool kAll>
+__global__ void k_gather_slots(const float *__restrict__ src, Ctx c, float *__restrict__ dst) {
+    const int N = active_count<kAll>(c);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int i = slot_node<kAll>(c, s);
+#pragma unroll
+        for (int a = 0; a < 3; a++) dst[a * c.ld + s] = src[3 * (size_t)i + a];
+    }
+}
+
+// slot SoA vector -> AoS full lattice (0 outside M)
+template <bool kAll>
+__global__ void k_scatter_slots(const float *__restrict__ src, Ctx c, float *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.nn; i += gridDim.x * blockDim.x) {
+        const int s = node_slot<kAll>(c, i);
+#pragma unroll
+        for (int a = 0; a < 3; a++) dst[3 * (size_t)i + a] = s >= 0 ? src[a * c.ld + s] : 0.f;
+    }
+}
+
+// SoA (planes x ld) <-> AoS (n x planes)
+__global__ void k_soa_to_aos(const float *__restrict__ src, int planes, int n, int ld, float *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int a = 0; a < planes; a++) dst[(size_t)planes * i + a] = src[(size_t)a * ld + i];
+}
+
+__global__ void k_aos_to_soa(const float *__restrict__ src, int planes, int n, int ld, float *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int a = 0; a < planes; a++) dst[(size_t)a * ld + i] = src[(size_t)planes * i + a];
+}
+
+__global__ void k_reset_warp(float *__restrict__ u, float *__restrict__ R, int n, int ld) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) u[a * ld + i] = 0.f;
+#pragma unroll
+        for (int e = 0; e < 9; e++) R[e * ld + i] = (e % 4 == 0) ? 1.f : 0.f;
+    }
+}
+
+// association results back into the caller's sample order
+__global__ void k_clear_association(int n_src, int *__restrict__ pix, float *__restrict__ w, float *__restrict__ r) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += gridDim.x * blockDim.x) {
+        pix[i] = -1;
+        w[i] = 0.f;
+        r[i] = 0.f;
+    }
+}
+
+template <bool kAll>
+__global__ void k_unsort_association(Ctx c, int *__restrict__ pix, float *__restrict__ w, float *__restrict__ r) {
+    const int n = *c.n_samples;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int o = c.perm[i];
+        pix[o] = c.pix[i];
+        w[o] = c.wc[i];
+        float res = 0.f;
+        const float4 g = c.rec[i];
+        if (c.wc[i] > 0.f) {
+            const float4 f4 = c.frac[i];
+            const float f[3] = {f4.x, f4.y, f4.z};
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+            for (int k = 0; k < 8; k++) {
+                const int nd = corner_node(c, c.cell[i], k);
+                const float al = trilinear_weight(f, k);
+                sx += al * c.u[nd];
+                sy += al * c.u[c.ld + nd];
+                sz += al * c.u[2 * c.ld + nd];
+            }
+            res = sqrtf(c.w_d) * (g.x * sx + g.y * sy + g.z * sz + g.w);
+        }
+        r[o] = res;
+    }
+}
+
+__global__ void k_pack_float4(const float *__restrict__ src, int n, float4 *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.f);
+}
+
+__global__ void k_finish_report(Scal *sc_base, size_t stride, int G, Ctx c, double *out) {
+    // out: e_total, e_dense, e_sparse, e_reg, then ints as doubles: gn_done, cg_done,
+    // n_valid, n_degenerate, n_refined, finite
+    if (threadIdx.x || blockIdx.x) return;
+    Scal *last = (Scal *)((char *)sc_base + stride * (size_t)(G - 1));
+    int nv = 0, nr = 0;
+    for (int g = 0; g < G; g++) {
+        Scal *s = (Scal *)((char *)sc_base + stride * (size_t)g);
+        if (s->assoc_ran) {
+            nv = s->n_valid;
+            nr = s->n_refined;
+        }
+    }
+    const double ed = last->e_dense, es = last->e_sparse, er = last->e_reg;
+    const double et = (double)c.w_s * es + (double)c.w_d * ed + (double)c.w_r * er;
+    out[0] = et;
+    out[1] = ed;
+    out[2] = es;
+    out[3] = er;
+    out[4] = G;
+    out[5] = last->cg_done;
+    out[6] = nv;
+    out[7] = last->n_degenerate;
+    out[8] = nr;
+    out[9] = isfinite(et) ? 1.0 : 0.0;
+}
+
+}  // namespace vd

@@ -1,0 +1,292 @@
+"""ctypes binding of libvd (include/vd.h): the same entry points, same names.
+
+Argument marshalling only: every step of the solve runs in the CUDA library.  Arrays
+may be numpy arrays (host memory, VD_MEM_HOST) or CUDA torch tensors (device memory,
+VD_MEM_DEVICE); ``Lattice`` wraps a handle for convenience.  Importing this module
+loads ``libvd.so`` and raises ImportError when it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvd.so")
+
+VD_OK, VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA, VD_ERR_STATE, VD_ERR_NUMERIC, VD_ERR_TIMEOUT = range(7)
+VD_ACTIVE_SURFACE, VD_ACTIVE_ALL = 0, 1
+VD_PREC_FP32, VD_PREC_MIXED = 0, 1
+VD_MEM_HOST, VD_MEM_DEVICE = 0, 1
+VD_INIT_PREV, VD_INIT_ZERO = 0, 1
+(VD_KC_ASSOCIATE, VD_KC_RHS, VD_KC_APPLY_STENCIL, VD_KC_APPLY_SAMPLES, VD_KC_UPDATE_X,
+ VD_KC_UPDATE_P, VD_KC_ROTATION, VD_KC_ENERGY) = range(8)
+KERNEL_CLASSES = {"associate": 0, "rhs": 1, "apply_stencil": 2, "apply_samples": 3, "update_x": 4,
+                  "update_p": 5, "rotation": 6, "energy": 7}
+
+STATUS_NAMES = {0: "VD_OK", 1: "VD_ERR_INVALID_ARG", 2: "VD_ERR_OOM", 3: "VD_ERR_CUDA", 4: "VD_ERR_STATE",
+                5: "VD_ERR_NUMERIC", 6: "VD_ERR_TIMEOUT"}
+
+
+class vd_lattice_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("origin", ctypes.c_float * 3), ("spacing", ctypes.c_float),
+                ("active_mode", ctypes.c_int), ("precision", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class vd_solve_params(ctypes.Structure):
+    _fields_ = [("w_sparse", ctypes.c_float), ("w_dense", ctypes.c_float), ("w_reg", ctypes.c_float),
+                ("eps_d", ctypes.c_float), ("eps_n", ctypes.c_float), ("eps_v", ctypes.c_float),
+                ("gn_iters", ctypes.c_int), ("cg_iters", ctypes.c_int), ("cg_tol", ctypes.c_double),
+                ("fixed_association", ctypes.c_int), ("init", ctypes.c_int)]
+
+
+class vd_solve_report(ctypes.Structure):
+    _fields_ = [("e_total", ctypes.c_double), ("e_dense", ctypes.c_double),
+                ("e_sparse", ctypes.c_double), ("e_reg", ctypes.c_double),
+                ("gn_done", ctypes.c_int), ("cg_done", ctypes.c_int), ("n_valid_corr", ctypes.c_int),
+                ("n_degenerate_rot", ctypes.c_int), ("n_refined", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libvd.so is not built ({LIB_PATH}); run `python -m paper_1603_08161_b300.build` "
+                      "or __graft_entry__.build()")
+lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_PI = ctypes.POINTER(ctypes.c_int)
+_PD = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "vd_create_lattice": [ctypes.POINTER(vd_lattice_desc), ctypes.POINTER(_P)],
+    "vd_destroy_lattice": [_P],
+    "vd_set_frame": [_P, _P, _I, _I, _P, _P, _P, _P, _I, _I],
+    "vd_set_correspondences": [_P, _P, _P, _I, _I],
+    "vd_solve": [_P, ctypes.POINTER(vd_solve_params), ctypes.POINTER(vd_solve_report)],
+    "vd_solve_async": [_P, ctypes.POINTER(vd_solve_params)],
+    "vd_get_report": [_P, ctypes.POINTER(vd_solve_report)],
+    "vd_get_warp": [_P, _P, _P, _I],
+    "vd_set_warp": [_P, _P, _P, _I],
+    "vd_last_error": [_P],
+    "vd_num_active": [_P, _PI],
+    "vd_get_active": [_P, _P, _I],
+    "vd_get_target_normals": [_P, _P, _I],
+    "vd_step_associate": [_P, ctypes.POINTER(vd_solve_params)],
+    "vd_get_association": [_P, ctypes.POINTER(vd_solve_params), _P, _P, _P, _I],
+    "vd_step_rhs": [_P, ctypes.POINTER(vd_solve_params), _P, _P, _I],
+    "vd_step_apply": [_P, ctypes.POINTER(vd_solve_params), _P, _P, _PD, _I],
+    "vd_step_pcg": [_P, ctypes.POINTER(vd_solve_params), _P, _PI, _I, _I],
+    "vd_step_fit_rotations": [_P, _PI],
+    "vd_step_energy": [_P, ctypes.POINTER(vd_solve_params), _PD],
+    "vd_profile_select": [_P, _I],
+    "vd_profile_read": [_P, _PD, _PI],
+    "vd_launch_counts": [_P, ctypes.POINTER(vd_solve_params), _PI, _PI],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_char_p if _name == "vd_last_error" else ctypes.c_int
+    globals()[_name] = _fn
+
+
+class VDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """(pointer, mem) of a numpy array or a torch tensor; None -> (None, host)."""
+    if a is None:
+        return None, VD_MEM_HOST
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, VD_MEM_HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (VD_MEM_DEVICE if a.is_cuda else VD_MEM_HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def params(w_sparse=10.0, w_dense=1.0, w_reg=1.0, eps_d=0.05, eps_n=0.5, eps_v=0.8, gn_iters=5,
+           cg_iters=10, cg_tol=0.0, fixed_association=False, init=VD_INIT_PREV):
+    return vd_solve_params(w_sparse, w_dense, w_reg, eps_d, eps_n, eps_v, gn_iters, cg_iters, cg_tol,
+                           int(bool(fixed_association)), init)
+
+
+class Lattice:
+    """A lattice handle: owns the library object, marshals arrays."""
+
+    def __init__(self, dims, origin, spacing, active_mode=VD_ACTIVE_ALL, precision=VD_PREC_FP32, stream=None):
+        self.dims = tuple(int(v) for v in dims)
+        self.nn = int(np.prod(self.dims))
+        d = vd_lattice_desc(self.dims[0], self.dims[1], self.dims[2],
+                            (ctypes.c_float * 3)(*[float(v) for v in origin]), float(spacing),
+                            int(active_mode), int(precision), stream)
+        h = _P()
+        st = vd_create_lattice(ctypes.byref(d), ctypes.byref(h))
+        if st != VD_OK:
+            raise VDError(st, "vd_create_lattice failed")
+        self.h = h
+        self.C = 0
+        self.W = self.H = 0
+        self._keep = []
+
+    def _check(self, st):
+        if st != VD_OK:
+            raise VDError(st, (vd_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            vd_destroy_lattice(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_frame(self, depth, K, pose, src_pts, src_nrm):
+        """depth (H, W), source samples (C, 3): numpy (host) or CUDA tensors (device);
+        K (4,) and pose (12,) or None are always host values."""
+        H, W = depth.shape[:2]
+        C = int(src_pts.shape[0])
+        pd, mem = _ptr(depth)
+        pp, _ = _ptr(src_pts)
+        pn, _ = _ptr(src_nrm)
+        kk = np.ascontiguousarray(K, np.float32)
+        pz = None if pose is None else np.ascontiguousarray(pose, np.float32)
+        self._check(vd_set_frame(self.h, pd, W, H, kk.ctypes.data, None if pz is None else pz.ctypes.data,
+                                 pp, pn, C, mem))
+        self.C, self.W, self.H = C, W, H
+
+    def set_frame_from(self, fr, device=None):
+        """Frame from a synth.Frame; ``device`` = torch device to pass device pointers."""
+        if device is None:
+            self.set_correspondences(fr.sp_canon, fr.sp_target)
+            self.set_frame(fr.depth, fr.K, fr.pose, fr.src_pts, fr.src_nrm)
+        else:
+            import torch
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+            self._keep = [t(fr.depth), t(fr.src_pts), t(fr.src_nrm), t(fr.sp_canon), t(fr.sp_target)]
+            d, p, n, a, b = self._keep
+            self.set_correspondences(a, b)
+            self.set_frame(d, fr.K, fr.pose, p, n)
+
+    def set_correspondences(self, canon, target):
+        S = int(canon.shape[0])
+        pa, mem = _ptr(canon)
+        pb, _ = _ptr(target)
+        self._check(vd_set_correspondences(self.h, pa, pb, S, mem))
+
+    def solve(self, prm):
+        rep = vd_solve_report()
+        st = vd_solve(self.h, ctypes.byref(prm), ctypes.byref(rep))
+        if st not in (VD_OK, VD_ERR_NUMERIC):
+            self._check(st)
+        return rep.as_dict()
+
+    def solve_async(self, prm):
+        self._check(vd_solve_async(self.h, ctypes.byref(prm)))
+
+    def report(self):
+        rep = vd_solve_report()
+        vd_get_report(self.h, ctypes.byref(rep))
+        return rep.as_dict()
+
+    def get_warp(self, out_u=None, out_R=None):
+        u = np.zeros((self.nn, 3), np.float32) if out_u is None else out_u
+        R = np.zeros((self.nn, 9), np.float32) if out_R is None else out_R
+        pu, mem = _ptr(u)
+        pr, _ = _ptr(R)
+        self._check(vd_get_warp(self.h, pu, pr, mem))
+        if isinstance(R, np.ndarray):
+            R = R.reshape(self.nn, 3, 3)
+        return u, R
+
+    def set_warp(self, u=None, R=None):
+        uu = None if u is None else np.ascontiguousarray(u, np.float32)
+        RR = None if R is None else np.ascontiguousarray(R, np.float32)
+        pu, mem = _ptr(uu)
+        pr, _ = _ptr(RR)
+        self._check(vd_set_warp(self.h, pu, pr, VD_MEM_HOST))
+
+    def num_active(self):
+        n = ctypes.c_int()
+        self._check(vd_num_active(self.h, ctypes.byref(n)))
+        return n.value
+
+    def active_mask(self):
+        m = np.zeros(self.nn, np.uint8)
+        self._check(vd_get_active(self.h, m.ctypes.data, VD_MEM_HOST))
+        return m.astype(bool)
+
+    def target_normals(self):
+        n = np.zeros((self.H, self.W, 3), np.float32)
+        self._check(vd_get_target_normals(self.h, n.ctypes.data, VD_MEM_HOST))
+        return n
+
+    def associate(self, prm):
+        self._check(vd_step_associate(self.h, ctypes.byref(prm)))
+
+    def association(self, prm):
+        pix = np.zeros(self.C, np.int32)
+        w = np.zeros(self.C, np.float32)
+        r = np.zeros(self.C, np.float32)
+        self._check(vd_get_association(self.h, ctypes.byref(prm), pix.ctypes.data, w.ctypes.data,
+                                       r.ctypes.data, VD_MEM_HOST))
+        return pix, w, r
+
+    def rhs(self, prm):
+        b = np.zeros((self.nn, 3), np.float32)
+        d = np.zeros((self.nn, 3), np.float32)
+        self._check(vd_step_rhs(self.h, ctypes.byref(prm), b.ctypes.data, d.ctypes.data, VD_MEM_HOST))
+        return b, d
+
+    def apply(self, prm, p):
+        p = np.ascontiguousarray(p, np.float32)
+        q = np.zeros((self.nn, 3), np.float32)
+        dot = ctypes.c_double()
+        self._check(vd_step_apply(self.h, ctypes.byref(prm), p.ctypes.data, q.ctypes.data, ctypes.byref(dot),
+                                  VD_MEM_HOST))
+        return q, dot.value
+
+    def pcg(self, prm, apply=False):
+        x = np.zeros((self.nn, 3), np.float32)
+        it = ctypes.c_int()
+        self._check(vd_step_pcg(self.h, ctypes.byref(prm), x.ctypes.data, ctypes.byref(it), int(apply),
+                                VD_MEM_HOST))
+        return x, it.value
+
+    def fit_rotations(self):
+        n = ctypes.c_int()
+        self._check(vd_step_fit_rotations(self.h, ctypes.byref(n)))
+        return n.value
+
+    def energy(self, prm):
+        out = (ctypes.c_double * 4)()
+        self._check(vd_step_energy(self.h, ctypes.byref(prm), out))
+        return np.array(list(out))
+
+    def profile_select(self, kernel_class):
+        self._check(vd_profile_select(self.h, int(kernel_class)))
+
+    def profile_read(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_int()
+        self._check(vd_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def launch_counts(self, prm):
+        a = ctypes.c_int()
+        b = ctypes.c_int()
+        self._check(vd_launch_counts(self.h, ctypes.byref(prm), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
