@@ -188,7 +188,7 @@ vd_status ensure_frame_caps(vd_lattice *L, int W, int H, int n_src) {
         TRY(dalloc(L, &L->depth, (size_t)L->cap_px));
         TRY(dalloc(L, &L->nrm, (size_t)L->cap_px));
     }
-    if (n_src > L->cap_src) {
+    if (n_src > L->cap_src || L->cap_src == 0) {  // the first frame allocates even for n_src = 0
         float **fs[] = {&L->pts_in, &L->nrm_in, &L->res_f};
         for (auto f : fs) dfree(L, *f);
         int **is[] = {&L->cell_in, &L->tmp, &L->order, &L->head, &L->hscan, &L->scell, &L->perm, &L->pix,
