@@ -193,6 +193,38 @@ vd_status vd_profile_read(vd_lattice *lat, double *total_ms, int *launches);
 vd_status vd_launch_counts(vd_lattice *lat, const vd_solve_params *params, int *per_solve,
                            int *per_frame);
 
+/* ---- allocation-free variant ----
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * let the library allocate device memory: programs that reserve their whole device
+ * memory budget up front (real-time pipelines, embedded deployments) and processes
+ * whose device memory belongs to another allocator (a framework's caching allocator),
+ * where a cudaMalloc from inside the library could fail or fragment the pool.
+ *
+ * vd_fit_rotations_noalloc runs the rotation step of vd_step_fit_rotations on a lattice
+ * in which every node is active, reading and writing only the caller's device arrays:
+ *   disp    u, nx*ny*nz x 3 floats (node i = x + nx (y + ny z)), device memory
+ *   rot_in  R before the step, nx*ny*nz x 9 floats (row-major 3x3), device memory
+ *   rot_out R after the step, same layout, device memory (may equal rot_in)
+ *   e_reg   (may be NULL) device double: E_reg (Eq. 4) with the new rotations
+ *   n_degenerate (may be NULL) device int: nodes whose rotation was kept
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its scratch is one
+ * fixed array in device memory of this library (VD_NOALLOC_MAX_NODES x 12 floats plus
+ * 256 bytes, about 3 MB), which every device that loads the library keeps until the
+ * process exits; lattices of more than VD_NOALLOC_MAX_NODES nodes return
+ * VD_ERR_INVALID_ARG.  All calls share that scratch and each one clears the part that
+ * must start at zero; calls that overlap on the GPU (different streams, or different
+ * host threads) race on it, so serialise them.  The work is enqueued on cuda_stream
+ * (NULL = the legacy default stream) and the function returns without waiting.  The
+ * first call on a device looks up the scratch address on that device (with it
+ * current); make that first call before any stream capture.  Errors: VD_ERR_INVALID_ARG
+ * for bad sizes or NULL arrays, VD_ERR_CUDA if a CUDA call fails (there is no handle,
+ * so no vd_last_error message). */
+#define VD_NOALLOC_MAX_NODES 65536
+vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spacing, const float *disp,
+                                   const float *rot_in, float *rot_out, double *e_reg,
+                                   int *n_degenerate, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

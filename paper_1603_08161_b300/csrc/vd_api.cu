@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1002,3 +1003,86 @@ vd_status vd_launch_counts(vd_lattice *L, const vd_solve_params *P, int *per_sol
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free rotation step
+//
+// vd_fit_rotations_noalloc runs the rotation step on caller-owned device arrays without
+// allocating anything.  Its scratch -- the structure-of-arrays copies of u and R that the
+// kernel reads, and the block of FP64 sums and counters -- is one file-scope device array
+// of fixed size, present on every device that loads this library for the life of the
+// process.  Host code must not use the array's name as an address: the address is
+// obtained once per device with cudaGetSymbolAddress and passed to the kernels.
+
+namespace {
+
+constexpr int kNoAllocLd = VD_NOALLOC_MAX_NODES;                   // plane stride of the SoA copies
+constexpr size_t kNoAllocStateBytes = sizeof(float) * 12 * (size_t)kNoAllocLd;  // u (3) + R (9) planes
+constexpr size_t kNoAllocBytes = kNoAllocStateBytes + 256;          // + one scalar block (K = 1)
+static_assert(kNoAllocLd % 32 == 0, "plane stride must keep 128-byte alignment");
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+void *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array on the current device (looked up once per device).
+cudaError_t noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spacing, const float *disp,
+                                              const float *rot_in, float *rot_out, double *e_reg,
+                                              int *n_degenerate, void *cuda_stream) {
+    if (nx < 2 || ny < 2 || nz < 2 || !(spacing > 0.f) || !disp || !rot_in || !rot_out) return VD_ERR_INVALID_ARG;
+    const long nn = (long)nx * ny * nz;
+    if (nn > VD_NOALLOC_MAX_NODES) return VD_ERR_INVALID_ARG;
+    void *base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) {
+        cudaGetLastError();
+        return VD_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Ctx c{};
+    c.nx = nx;
+    c.ny = ny;
+    c.nz = nz;
+    c.nn = (int)nn;
+    c.ld = kNoAllocLd;
+    c.h = spacing;
+    c.u = (float *)base;
+    c.R = c.u + 3 * (size_t)kNoAllocLd;
+    Scal *sc = (Scal *)((char *)base + kNoAllocStateBytes);
+    // the sums and counters accumulate with atomics: clear what the last call left
+    if (cudaMemsetAsync(sc, 0, scal_bytes(1), st) != cudaSuccess) return VD_ERR_CUDA;
+    const int nb = blocks_for(nn);
+    k_aos_to_soa<<<nb, kThreads, 0, st>>>(disp, 3, c.nn, c.ld, c.u);
+    k_aos_to_soa<<<nb, kThreads, 0, st>>>(rot_in, 9, c.nn, c.ld, c.R);
+    k_fit_rotations<true, true><<<nb, kThreads, 0, st>>>(c, sc);
+    k_soa_to_aos<<<nb, kThreads, 0, st>>>(c.R, 9, c.nn, c.ld, rot_out);
+    if (cudaGetLastError() != cudaSuccess) return VD_ERR_CUDA;
+    if (e_reg && cudaMemcpyAsync(e_reg, &sc->e_reg, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return VD_ERR_CUDA;
+    if (n_degenerate &&
+        cudaMemcpyAsync(n_degenerate, &sc->n_degenerate, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return VD_ERR_CUDA;
+    return VD_OK;
+}

@@ -86,7 +86,9 @@ _SIGS = {
     "vd_profile_select": [_P, _I],
     "vd_profile_read": [_P, _PD, _PI],
     "vd_launch_counts": [_P, ctypes.POINTER(vd_solve_params), _PI, _PI],
+    "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
 }
+VD_NOALLOC_MAX_NODES = 65536
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
