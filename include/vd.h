@@ -177,7 +177,8 @@ vd_status vd_step_energy(vd_lattice *lat, const vd_solve_params *params, double 
 enum {
     VD_KC_ASSOCIATE = 0, VD_KC_RHS = 1, VD_KC_APPLY_STENCIL = 2, VD_KC_APPLY_SAMPLES = 3,
     VD_KC_UPDATE_X = 4, VD_KC_UPDATE_P = 5, VD_KC_ROTATION = 6, VD_KC_ENERGY = 7,
-    VD_KC_COUNT = 8
+    VD_KC_PCG = 8, /* the persistent position step (one cooperative launch per step) */
+    VD_KC_COUNT = 9
 };
 
 /* Select one kernel class (or -1 for none) to bracket with CUDA events inside the

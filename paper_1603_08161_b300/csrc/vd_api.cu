@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -95,6 +96,15 @@ struct vd_lattice {
     int ev_used = 0;
     double prof_ms = 0.0;
     int prof_launches = 0;
+    bool use_pdl = true;             // chain solve kernels with programmatic dependent launch
+    // persistent position step
+    int *surf_flag = nullptr, *surf_pos = nullptr, *surf_list = nullptr;
+    double *pcg_part = nullptr;
+    int pcg_part_rows = 0;
+    unsigned *pcg_bar = nullptr;     // [0] arrivals, [1] generation, [2] error flag
+    int num_sms = 148;
+    bool coop = false;               // device supports cooperative launches
+    bool use_persistent = true;      // may be cleared if the graph cannot hold the launch
 };
 
 namespace {
@@ -228,6 +238,11 @@ vd_status ensure_frame_caps(vd_lattice *L, int W, int H, int n_src) {
 }
 
 vd_status ensure_scal(vd_lattice *L, int G, int K) {
+    if (2 * K + 2 > L->pcg_part_rows) {
+        dfree(L, L->pcg_part);
+        L->pcg_part_rows = 2 * K + 2;
+        TRY(dalloc(L, &L->pcg_part, (size_t)L->pcg_part_rows * L->num_sms));
+    }
     const size_t stride = scal_bytes(K);
     if (L->scal && stride == L->scal_stride && G <= L->scal_slots) return VD_OK;
     dfree(L, L->scal);
@@ -298,129 +313,177 @@ vd_status check_params(vd_lattice *L, const vd_solve_params *p) {
 // ------------------------------------------------------------------ launch plumbing
 
 struct Grid {
-    int node, samp, cells;
+    int node;    // blocks over active slots
+    int node4;   // blocks over float4 groups of slots
+    int samp, cells;
+    bool vec4;   // all-nodes lattice with nx % 4 == 0: float4 stencil
 };
 
 Grid grids(vd_lattice *L) {
     Grid g;
     const int nact = L->all ? L->c.nn : round_pow2(std::max(L->n_active_h, 1));
     g.node = blocks_for(nact);
+    g.node4 = blocks_for((nact + 3) / 4, kThreads, 8);
     g.samp = blocks_for(round_pow2(std::max(L->n_samples_h, 1)));
-    const long warps = round_pow2(std::max(L->n_occ_h, 1)) + (L->S + 31) / 32;
-    g.cells = blocks_for(warps * 32);
+    const long slices = (round_pow2(std::max(L->n_occ_h, 1)) + kCellsPerBlock - 1) / kCellsPerBlock;
+    g.cells = (int)std::min<long>(std::max<long>(slices, (L->S + kThreads - 1) / kThreads), (long)kSMs * 8);
+    g.vec4 = L->all && (L->c.nx % 4 == 0);
     return g;
 }
 
-// bracket a launch of kernel class kc with profiling events when selected
-struct ProfScope {
+// Launches the kernels of a schedule on one stream.  Consecutive kernels are chained
+// with programmatic dependent launch (every solve kernel starts with pdl_wait), and a
+// launch of the kernel class selected for profiling is bracketed by CUDA events (which
+// break the chain around it).
+struct Launcher {
     vd_lattice *L;
-    bool on;
     cudaStream_t st;
-    ProfScope(vd_lattice *L_, int kc, cudaStream_t st_) : L(L_), on(false), st(st_) {
-        if (L->prof_class == kc && L->ev_used + 2 <= (int)L->ev.size()) {
-            on = true;
+    bool chain = false;
+    template <typename... KArgs, typename... Args>
+    void go(int kc, void (*kern)(KArgs...), dim3 grid, dim3 block, Args... args) {
+        const bool prof = L->prof_class == kc && L->ev_used + 2 <= (int)L->ev.size();
+        if (prof) {
             cudaEventRecordWithFlags(L->ev[L->ev_used], st, cudaEventRecordExternal);
+            chain = false;
         }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        if (chain && L->use_pdl) {
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+        }
+        cudaLaunchKernelEx(&cfg, kern, args...);
+        chain = true;
         L->counting++;
-    }
-    ~ProfScope() {
-        if (on) {
+        if (prof) {
             cudaEventRecordWithFlags(L->ev[L->ev_used + 1], st, cudaEventRecordExternal);
             L->ev_used += 2;
+            chain = false;
         }
     }
+    void other() { chain = false; }  // a memset or copy was enqueued
 };
 
 template <bool kAll>
-void enqueue_gn(vd_lattice *L, const vd_solve_params *P, int g, cudaStream_t st) {
+void enqueue_rhs(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K) {
+    Lc.go(VD_KC_RHS, k_rhs_nodes<kAll>, gr.node, kThreads, c);
+    Lc.go(VD_KC_RHS, k_cells<kOpRhs, kAll>, gr.cells, kThreads, c, sc, K, 0);
+}
+
+template <bool kAll>
+void enqueue_apply(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K, int it) {
+    if (gr.vec4) Lc.go(VD_KC_APPLY_STENCIL, k_apply_stencil<kAll, true>, gr.node4, kThreads, c, sc, K, it);
+    else Lc.go(VD_KC_APPLY_STENCIL, k_apply_stencil<kAll, false>, gr.node, kThreads, c, sc, K, it);
+    Lc.go(VD_KC_APPLY_SAMPLES, k_cells<kOpApply, kAll>, gr.cells, kThreads, c, sc, K, it);
+}
+
+// PCG position step: init, then K x (apply, x/r update, p update)
+template <bool kAll>
+void enqueue_pcg(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K, double tol2) {
+    Lc.go(VD_KC_RHS, k_pcg_init<kAll>, dim3(gr.node, 3), kThreads, c, sc);
+    for (int it = 0; it < K; it++) {
+        enqueue_apply<kAll>(Lc, c, sc, gr, K, it);
+        Lc.go(VD_KC_UPDATE_X, k_update_x<kAll>, gr.node4, kThreads, c, sc, K, it);
+        Lc.go(VD_KC_UPDATE_P, k_update_p<kAll>, gr.node4, kThreads, c, sc, it, tol2);
+    }
+}
+
+constexpr int kPcgMaxChunk = 6272;  // 9 floats per slot in shared memory: 225,792 bytes (+ 4 KB static)
+
+// Whether the position step runs as one persistent cooperative kernel, with how many
+// CTAs and how many slots per CTA.
+bool persistent_plan(vd_lattice *L, int *G, int *chunk) {
+    if (!L->use_persistent || !L->coop) return false;
+    const int N = L->all ? L->c.nn : L->n_active_h;
+    const int N4 = 4 * ((std::max(N, 1) + 3) / 4);
+    int ch = (N4 + L->num_sms - 1) / L->num_sms;
+    ch = std::max(4 * ((ch + 3) / 4), 1024);
+    if (ch > kPcgMaxChunk) return false;
+    *chunk = ch;
+    *G = (N4 + ch - 1) / ch;
+    return *G <= L->num_sms;
+}
+
+template <bool kAll>
+void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2, int apply, int G, int chunk) {
+    PcgAux ax{L->pcg_part, L->pcg_bar, (int *)(L->pcg_bar + 2), L->surf_list, L->counts + 2,
+              {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk};
+    const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
+    cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
+    Lc.other();
+    if (prof) cudaEventRecordWithFlags(L->ev[L->ev_used], Lc.st, cudaEventRecordExternal);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kPcgThreads);
+    cfg.dynamicSmemBytes = (size_t)36 * chunk;
+    cfg.stream = Lc.st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const Ctx c = L->c;
+    if (kAll && (c.nx % 4 == 0)) cudaLaunchKernelEx(&cfg, k_pcg_persistent<kAll, true>, c, sc, ax, K, tol2, apply);
+    else cudaLaunchKernelEx(&cfg, k_pcg_persistent<kAll, false>, c, sc, ax, K, tol2, apply);
+    L->counting++;
+    if (prof) {
+        cudaEventRecordWithFlags(L->ev[L->ev_used + 1], Lc.st, cudaEventRecordExternal);
+        L->ev_used += 2;
+    }
+    Lc.other();
+}
+
+template <bool kAll>
+void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
     const Grid gr = grids(L);
     const Ctx c = L->c;
     Scal *sc = slot(L, g);
     const int K = P->cg_iters;
-    const bool assoc = !(P->fixed_association && g > 0);
-    if (assoc) {
-        ProfScope ps(L, VD_KC_ASSOCIATE, st);
-        k_associate<kAll><<<gr.samp, kThreads, 0, st>>>(c, sc);
+    if (!(P->fixed_association && g > 0)) Lc.go(VD_KC_ASSOCIATE, k_associate<kAll>, gr.samp, kThreads, c, sc);
+    enqueue_rhs<kAll>(Lc, c, sc, gr, K);
+    int G = 0, chunk = 0;
+    if (persistent_plan(L, &G, &chunk)) {
+        launch_persistent<kAll>(L, Lc, sc, K, P->cg_tol * P->cg_tol, 1, G, chunk);
+    } else {
+        enqueue_pcg<kAll>(Lc, c, sc, gr, K, P->cg_tol * P->cg_tol);
+        Lc.go(VD_KC_ROTATION, k_add_increment<kAll>, gr.node, kThreads, c);
     }
-    {
-        ProfScope ps(L, VD_KC_RHS, st);
-        k_rhs_nodes<kAll><<<gr.node, kThreads, 0, st>>>(c);
-    }
-    {
-        ProfScope ps(L, VD_KC_RHS, st);
-        k_cells<kOpRhs, kAll><<<gr.cells, kThreads, 0, st>>>(c, sc, K, 0);
-    }
-    {
-        ProfScope ps(L, VD_KC_RHS, st);
-        k_pcg_init<kAll><<<gr.node, kThreads, 0, st>>>(c, sc);
-    }
-    const double tol2 = P->cg_tol * P->cg_tol;
-    for (int it = 0; it < K; it++) {
-        {
-            ProfScope ps(L, VD_KC_APPLY_STENCIL, st);
-            k_apply_stencil<kAll><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
-        }
-        {
-            ProfScope ps(L, VD_KC_APPLY_SAMPLES, st);
-            k_cells<kOpApply, kAll><<<gr.cells, kThreads, 0, st>>>(c, sc, K, it);
-        }
-        {
-            ProfScope ps(L, VD_KC_UPDATE_X, st);
-            k_update_x<kAll><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
-        }
-        {
-            ProfScope ps(L, VD_KC_UPDATE_P, st);
-            k_update_p<kAll><<<gr.node, kThreads, 0, st>>>(c, sc, it, tol2);
-        }
-    }
-    {
-        ProfScope ps(L, VD_KC_ROTATION, st);
-        k_add_increment<kAll><<<gr.node, kThreads, 0, st>>>(c);
-    }
-    {
-        ProfScope ps(L, VD_KC_ROTATION, st);
-        k_fit_rotations<kAll, true><<<gr.node, kThreads, 0, st>>>(c, sc);
-    }
-    {
-        ProfScope ps(L, VD_KC_ENERGY, st);
-        k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, sc, K, 0);
-    }
+    Lc.go(VD_KC_ROTATION, k_fit_rotations<kAll, true>, gr.node, kThreads, c, sc);
+    Lc.go(VD_KC_ENERGY, k_cells<kOpEnergy, kAll>, gr.cells, kThreads, c, sc, K, 0);
 }
 
 void enqueue_solve(vd_lattice *L, const vd_solve_params *P, cudaStream_t st) {
+    Launcher Lc{L, st};
     cudaMemsetAsync(L->scal, 0, L->scal_stride * (size_t)P->gn_iters, st);
-    if (P->init == VD_INIT_ZERO) {
-        L->counting++;
-        k_reset_warp<<<blocks_for(L->c.nn), kThreads, 0, st>>>(L->u, L->R, L->c.nn, L->c.ld);
-    }
+    Lc.other();
+    if (P->init == VD_INIT_ZERO)
+        Lc.go(-1, k_reset_warp, blocks_for(L->c.nn), kThreads, L->u, L->R, L->c.nn, L->c.ld);
     for (int g = 0; g < P->gn_iters; g++) {
-        if (L->all) enqueue_gn<true>(L, P, g, st);
-        else enqueue_gn<false>(L, P, g, st);
+        if (L->all) enqueue_gn<true>(Lc, L, P, g);
+        else enqueue_gn<false>(Lc, L, P, g);
     }
-    L->counting++;
-    k_finish_report<<<1, 32, 0, st>>>((Scal *)L->scal, L->scal_stride, P->gn_iters, L->c, L->rep_dev);
-    cudaMemcpyAsync(L->rep_host, L->rep_dev, 10 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    Lc.go(-1, k_finish_report, 1, 32, (Scal *)L->scal, L->scal_stride, P->gn_iters, L->c, L->rep_dev,
+          (const int *)(L->pcg_bar + 2));
+    cudaMemcpyAsync(L->rep_host, L->rep_dev, 11 * sizeof(double), cudaMemcpyDeviceToHost, st);
 }
 
+// upper bound on the launches of one kernel class in a solve (sizes the event pool)
 int class_launches_per_solve(const vd_solve_params *P, int kc) {
-    const int G = P->gn_iters, K = P->cg_iters;
-    const int assoc = P->fixed_association ? 1 : G;
-    switch (kc) {
-        case VD_KC_ASSOCIATE: return assoc;
-        case VD_KC_RHS: return 3 * G;
-        case VD_KC_APPLY_STENCIL:
-        case VD_KC_APPLY_SAMPLES:
-        case VD_KC_UPDATE_X:
-        case VD_KC_UPDATE_P: return K * G;
-        case VD_KC_ROTATION: return 2 * G;
-        case VD_KC_ENERGY: return G;
-        default: return 0;
-    }
+    if (kc < 0) return 0;
+    return std::max(P->cg_iters, 3) * P->gn_iters + 8;
 }
 
 vd_status build_graph(vd_lattice *L, const vd_solve_params *P) {
     const Grid gr = grids(L);
-    const int caps[4] = {gr.node, gr.samp, gr.cells, L->S};
+    int pG = 0, pch = 0;
+    persistent_plan(L, &pG, &pch);
+    const int caps[4] = {gr.node, gr.samp, gr.cells, L->S * 65536 + pch};
     const bool same = L->gexec && L->ggen == L->gen && !memcmp(&L->gparams, P, sizeof(*P)) &&
                       !memcmp(L->gkey_caps, caps, sizeof(caps)) && !memcmp(&L->gctx, &L->c, sizeof(Ctx));
     if (same) return VD_OK;
@@ -437,14 +500,24 @@ vd_status build_graph(vd_lattice *L, const vd_solve_params *P) {
     }
     L->ev_used = 0;
     L->counting = 0;
-    CK(cudaStreamBeginCapture(L->cap, cudaStreamCaptureModeThreadLocal));
-    enqueue_solve(L, P, L->cap);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(L->cap, &graph);
+    cudaError_t e = cudaSuccess;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        L->ev_used = 0;
+        L->counting = 0;
+        CK(cudaStreamBeginCapture(L->cap, cudaStreamCaptureModeThreadLocal));
+        enqueue_solve(L, P, L->cap);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(L->cap, &graph);
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&L->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+        }
+        if (e == cudaSuccess) break;
+        cudaGetLastError();
+        if (!L->use_persistent) break;
+        L->use_persistent = false;  // the graph could not hold the cooperative launch: stream the PCG
+    }
     if (e != cudaSuccess) return fail(L, VD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&L->gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(L, VD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     L->launches_solve = L->counting;
     L->gparams = *P;
     L->gctx = L->c;
@@ -467,6 +540,7 @@ vd_status read_report(vd_lattice *L, vd_solve_report *out) {
     const double *r = L->rep_host;
     vd_status st = VD_OK;
     if (r[9] == 0.0) st = fail(L, VD_ERR_NUMERIC, "non-finite energy after the solve");
+    if (r[10] != 0.0) st = fail(L, VD_ERR_TIMEOUT, "a grid barrier of the persistent position step timed out");
     if (out) {
         out->e_total = r[0];
         out->e_dense = r[1];
@@ -482,10 +556,24 @@ vd_status read_report(vd_lattice *L, vd_solve_report *out) {
     return st;
 }
 
+vd_status frame_surface_list(vd_lattice *L) {
+    refresh_ctx(L);
+    const Ctx c = L->c;
+    cudaStream_t st = L->stream;
+    CK(cudaMemsetAsync(L->surf_flag, 0, sizeof(int) * (size_t)c.nn, st));
+    const int nb = blocks_for(std::max(L->cap_src, 1) + L->S);
+    if (L->all) k_mark_surface<true><<<nb, kThreads, 0, st>>>(L->occ_cell, L->counts + 1, L->scell_s, L->S, c, L->surf_flag);
+    else k_mark_surface<false><<<nb, kThreads, 0, st>>>(L->occ_cell, L->counts + 1, L->scell_s, L->S, c, L->surf_flag);
+    scan_launch(L->surf_flag, c.nn, L->surf_pos, L->counts + 2, L->scan_sums, st);
+    k_compact_list<<<blocks_for(c.nn), kThreads, 0, st>>>(L->surf_flag, L->surf_pos, c.nn, L->surf_list);
+    CKL();
+    return VD_OK;
+}
+
 vd_status frame_active_set(vd_lattice *L) {
     const Ctx c = L->c;
     cudaStream_t st = L->stream;
-    if (L->all) return VD_OK;
+    if (L->all) return frame_surface_list(L);
     CK(cudaMemsetAsync(L->mark, 0, sizeof(int) * (size_t)c.nn, st));
     k_mark_cells<<<blocks_for(std::max(L->cap_src, 1) + L->S), kThreads, 0, st>>>(L->occ_cell, L->counts + 1,
                                                                                    L->scell_s, L->S, c, L->mark);
@@ -494,7 +582,7 @@ vd_status frame_active_set(vd_lattice *L) {
     k_compact<<<blocks_for(c.nn), kThreads, 0, st>>>(L->act, c, L->slot_of_node, L->node_of_slot);
     k_neighbour_table<<<blocks_for(c.nn), kThreads, 0, st>>>(c, L->nbr);
     CKL();
-    return VD_OK;
+    return frame_surface_list(L);
 }
 
 vd_status sync_sizes(vd_lattice *L) {
@@ -521,9 +609,8 @@ vd_status step_prepare(vd_lattice *L, const vd_solve_params *P, int K) {
 
 template <bool kAll>
 void rhs_launch(vd_lattice *L, cudaStream_t st) {
-    const Grid gr = grids(L);
-    k_rhs_nodes<kAll><<<gr.node, kThreads, 0, st>>>(L->c);
-    k_cells<kOpRhs, kAll><<<gr.cells, kThreads, 0, st>>>(L->c, slot(L, 0), 1, 0);
+    Launcher Lc{L, st};
+    enqueue_rhs<kAll>(Lc, L->c, slot(L, 0), grids(L), 1);
 }
 
 }  // namespace
@@ -555,6 +642,7 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
     for (int a = 0; a < 9; a++) c.Rg[a] = (a % 4 == 0) ? 1.f : 0.f;
     L->all = d->active_mode == VD_ACTIVE_ALL;
     L->precision = d->precision;
+    if (const char *e = getenv("VD_PDL")) L->use_pdl = atoi(e) != 0;
     vd_status s = VD_OK;
     auto bail = [&](vd_status st) {
         vd_destroy_lattice(L);
@@ -568,10 +656,36 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
     }
     if (cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking) != cudaSuccess) return bail(VD_ERR_CUDA);
     const size_t ld = c.ld;
-    if ((s = dalloc(L, &L->u, 3 * ld)) || (s = dalloc(L, &L->R, 9 * ld)) || (s = dalloc(L, &L->vecs, 15 * ld)) ||
+    if ((s = dalloc(L, &L->u, 3 * ld)) || (s = dalloc(L, &L->R, 9 * ld)) || (s = dalloc(L, &L->vecs, 18 * ld)) ||
         (s = dalloc(L, &L->counts, 8)) || (s = dalloc(L, &L->cnt, ld)) || (s = dalloc(L, &L->start, ld + 1)) ||
         (s = dalloc(L, &L->staging, 9 * ld)) || (s = dalloc(L, &L->rep_dev, 16)))
         return bail(s);
+    if ((s = dalloc(L, &L->surf_flag, ld)) || (s = dalloc(L, &L->surf_pos, ld + 1)) ||
+        (s = dalloc(L, &L->surf_list, ld)) || (s = dalloc(L, &L->pcg_bar, 4)))
+        return bail(s);
+    {
+        int dev = 0, coop = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+            L->coop = coop != 0;
+            L->num_sms = sms;
+        }
+        const int bytes = 36 * kPcgMaxChunk;
+        if (cudaFuncSetAttribute(k_pcg_persistent<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
+            cudaFuncSetAttribute(k_pcg_persistent<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
+            cudaFuncSetAttribute(k_pcg_persistent<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) {
+            cudaGetLastError();
+            L->coop = false;
+        }
+        int occ = 0;
+        if (L->coop && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_persistent<true, true>, kPcgThreads,
+                                                                       bytes) != cudaSuccess || occ < 1)) {
+            cudaGetLastError();
+            L->coop = false;
+        }
+        if (const char *e = getenv("VD_PERSISTENT")) L->use_persistent = atoi(e) != 0;
+    }
     if (!L->all) {
         if ((s = dalloc(L, &L->slot_of_node, ld + 1)) || (s = dalloc(L, &L->node_of_slot, ld)) ||
             (s = dalloc(L, &L->nbr, 6 * ld)) || (s = dalloc(L, &L->mark, ld)) || (s = dalloc(L, &L->act, ld)))
@@ -581,8 +695,9 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
     memset(L->rep_host, 0, 16 * sizeof(double));
     refresh_ctx(L);
     k_reset_warp<<<blocks_for(c.nn), kThreads, 0, L->stream>>>(L->u, L->R, c.nn, c.ld);
-    if (cudaMemsetAsync(L->vecs, 0, sizeof(float) * 15 * ld, L->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(L->vecs, 0, sizeof(float) * 18 * ld, L->stream) != cudaSuccess ||
         cudaMemsetAsync(L->counts, 0, 8 * sizeof(int), L->stream) != cudaSuccess ||
+        cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), L->stream) != cudaSuccess ||
         cudaMemsetAsync(L->start, 0, sizeof(int) * (ld + 1), L->stream) != cudaSuccess ||
         cudaStreamSynchronize(L->stream) != cudaSuccess)
         return bail(VD_ERR_CUDA);
@@ -683,7 +798,7 @@ vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const fl
     L->have_frame = true;
     TRY(frame_active_set(L));
     TRY(sync_sizes(L));
-    L->launches_frame = 13 + (L->all ? 0 : 7);
+    L->launches_frame = 13 + 5 + (L->all ? 0 : 7);
     return VD_OK;
 }
 
@@ -866,15 +981,14 @@ vd_status vd_step_apply(vd_lattice *L, const vd_solve_params *P, const float *p,
     // the gates of the apply kernels read rho[0] > 0
     const double one = 1.0;
     CK(cudaMemcpyAsync((char *)sc + offsetof(Scal, rho), &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    Launcher Lc{L, st};
     if (L->all) {
         k_gather_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(L->staging, c, c.p);
-        k_apply_stencil<true><<<gr.node, kThreads, 0, st>>>(c, sc, 1, 0);
-        k_cells<kOpApply, true><<<gr.cells, kThreads, 0, st>>>(c, sc, 1, 0);
+        enqueue_apply<true>(Lc, c, sc, gr, 1, 0);
         k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.q, c, L->staging);
     } else {
         k_gather_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(L->staging, c, c.p);
-        k_apply_stencil<false><<<gr.node, kThreads, 0, st>>>(c, sc, 1, 0);
-        k_cells<kOpApply, false><<<gr.cells, kThreads, 0, st>>>(c, sc, 1, 0);
+        enqueue_apply<false>(Lc, c, sc, gr, 1, 0);
         k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.q, c, L->staging);
     }
     CKL();
@@ -896,26 +1010,27 @@ vd_status vd_step_pcg(vd_lattice *L, const vd_solve_params *P, float *delta, int
     Scal *sc = slot(L, 0);
     CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, st));
     const double tol2 = P->cg_tol * P->cg_tol;
-    if (L->all) {
-        rhs_launch<true>(L, st);
-        k_pcg_init<true><<<gr.node, kThreads, 0, st>>>(c, sc);
-        for (int it = 0; it < K; it++) {
-            k_apply_stencil<true><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
-            k_cells<kOpApply, true><<<gr.cells, kThreads, 0, st>>>(c, sc, K, it);
-            k_update_x<true><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
-            k_update_p<true><<<gr.node, kThreads, 0, st>>>(c, sc, it, tol2);
+    Launcher Lc{L, st};
+    int pG = 0, pch = 0;
+    if (persistent_plan(L, &pG, &pch)) {
+        if (L->all) {
+            enqueue_rhs<true>(Lc, c, sc, gr, K);
+            launch_persistent<true>(L, Lc, sc, K, tol2, apply, pG, pch);
+            if (delta) k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
+        } else {
+            enqueue_rhs<false>(Lc, c, sc, gr, K);
+            launch_persistent<false>(L, Lc, sc, K, tol2, apply, pG, pch);
+            if (delta) k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         }
+    } else if (L->all) {
+        enqueue_rhs<true>(Lc, c, sc, gr, K);
+        enqueue_pcg<true>(Lc, c, sc, gr, K, tol2);
+        Lc.other();
         if (delta) k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         if (apply) k_add_increment<true><<<gr.node, kThreads, 0, st>>>(c);
     } else {
-        rhs_launch<false>(L, st);
-        k_pcg_init<false><<<gr.node, kThreads, 0, st>>>(c, sc);
-        for (int it = 0; it < K; it++) {
-            k_apply_stencil<false><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
-            k_cells<kOpApply, false><<<gr.cells, kThreads, 0, st>>>(c, sc, K, it);
-            k_update_x<false><<<gr.node, kThreads, 0, st>>>(c, sc, K, it);
-            k_update_p<false><<<gr.node, kThreads, 0, st>>>(c, sc, it, tol2);
-        }
+        enqueue_rhs<false>(Lc, c, sc, gr, K);
+        enqueue_pcg<false>(Lc, c, sc, gr, K, tol2);
         if (delta) k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         if (apply) k_add_increment<false><<<gr.node, kThreads, 0, st>>>(c);
     }
@@ -996,7 +1111,9 @@ vd_status vd_launch_counts(vd_lattice *L, const vd_solve_params *P, int *per_sol
     TRY(check_params(L, P));
     const int G = P->gn_iters, K = P->cg_iters;
     const int assoc = P->fixed_association ? 1 : G;
-    const int n = assoc + G * (3 + 4 * K + 3) + 1 + (P->init == VD_INIT_ZERO ? 1 : 0);
+    int pG = 0, pch = 0;
+    const int per_gn = persistent_plan(L, &pG, &pch) ? 2 + 1 + 2 : 3 + 4 * K + 3;
+    const int n = assoc + G * per_gn + 1 + (P->init == VD_INIT_ZERO ? 1 : 0);
     if (per_solve) *per_solve = n;
     if (per_frame) *per_frame = L->launches_frame;
     return VD_OK;

@@ -68,6 +68,15 @@ __host__ __device__ inline size_t scal_bytes(int K) {
 __device__ __forceinline__ double *scal_rho(Scal *s) { return s->rho; }
 __device__ __forceinline__ double *scal_pq(Scal *s, int K) { return s->rho + K + 1; }
 
+// ------------------------------------------------------------------ launch ordering
+
+// Programmatic dependent launch: a kernel of the solve may be scheduled while its
+// predecessor drains; it waits here, before touching any memory, until the predecessor
+// grid has completed and its writes are visible, then lets its own successor be
+// scheduled.  Both are no-ops when the kernel was launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------ reductions
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -78,16 +87,23 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Block-wide sum of one float per thread, accumulated in FP64 across warps; thread 0
 // adds the result to *dst.  Every thread of the block must call it.
+// (FP64 work is kept to a 5-level tree in warp 0: B300's FP64 rate is low.)
+__device__ __forceinline__ double warp0_tree_f64(const double *part, int lane) {
+    double s = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    return s;
+}
+
 __device__ __forceinline__ void block_add_f64(float v, double *dst) {
     __shared__ double part[32];
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) part[wid] = (double)v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += part[k];
-        if (s != 0.0) atomicAdd(dst, s);
+    if (wid == 0) {
+        const double s = warp0_tree_f64(part, lane);
+        if (lane == 0 && s != 0.0) atomicAdd(dst, s);
     }
     __syncthreads();
 }
@@ -99,10 +115,9 @@ __device__ __forceinline__ void block_add_f64d(double v, double *dst) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) partd[wid] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += partd[k];
-        if (s != 0.0) atomicAdd(dst, s);
+    if (wid == 0) {
+        const double s = warp0_tree_f64(partd, lane);
+        if (lane == 0 && s != 0.0) atomicAdd(dst, s);
     }
     __syncthreads();
 }
@@ -438,6 +453,25 @@ __global__ void k_neighbour_table(Ctx c, int *__restrict__ nbr) {
     }
 }
 
+// Slots touched by the samples' or sparse pairs' J^T J contributions (corners of their
+// cells), flagged for the persistent position step, then compacted in ascending order.
+template <bool kAll>
+__global__ void k_mark_surface(const int *__restrict__ occ_cell, const int *__restrict__ n_occ,
+                               const int *__restrict__ scell, int S, Ctx c, int *__restrict__ flag) {
+    const int no = *n_occ;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < no + S; i += gridDim.x * blockDim.x) {
+        const int cl = i < no ? occ_cell[i] : scell[i - no];
+        if (cl < 0) continue;
+#pragma unroll
+        for (int k = 0; k < 8; k++) flag[node_slot<kAll>(c, corner_node(c, cl, k))] = 1;
+    }
+}
+
+__global__ void k_compact_list(const int *__restrict__ flag, const int *__restrict__ pos, int n, int *__restrict__ list) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (flag[i]) list[pos[i]] = i;
+}
+
 // ------------------------------------------------------------------ association (Sec. 5.1)
 
 template <typename T>
@@ -596,6 +630,8 @@ __device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, fl
 
 template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
+    pdl_wait();
+    pdl_trigger();
     const int n = *c.n_samples;
     int valid = 0, refined = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -621,155 +657,205 @@ __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
 
 enum CellOp { kOpRhs = 0, kOpApply = 1, kOpEnergy = 2 };
 
-// One warp per occupied cell: every sample of the cell touches the same 8 corners,
-// so the corner vectors are loaded once and the 24 per-corner sums are reduced in
-// the warp before one atomic per corner component.  Warps past the occupied cells
-// take the sparse pairs (one per lane).
-//   kOpRhs:    r_k -= alpha_k w_d g' (g' . sum alpha u + r0'),  diag_k += alpha_k^2 w_d g'^2
-//              (sparse: b -= sqrt(w_s) alpha_k R_g^T r_s, diag += w_s alpha_k^2 |R_g col|^2)
-//   kOpApply:  q_k += alpha_k w_d g' (g' . sum alpha p);  p.Ap partial += w_d s^2
-//   kOpEnergy: E_dense += (g' . sum alpha u + r0')^2;  E_sparse += |S(f^) - f|^2
-template <int kOp, bool kAll>
-__global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int it) {
-    if (kOp == kOpApply) {
-        if (sc->stop || !(scal_rho(sc)[it] > 0.0)) return;
-    }
-    const int lane = threadIdx.x & 31;
-    const int warps_per_block = blockDim.x >> 5;
-    const int n_occ = *c.n_occ;
-    const int n_sparse_warps = (c.S + 31) >> 5;
-    const int total = n_occ + n_sparse_warps;
-    const float *vec = (kOp == kOpApply) ? c.p : c.u;  // slot- or node-indexed
-    float part = 0.f;
-    double partd = 0.0;
-    for (int w = blockIdx.x * warps_per_block + (threadIdx.x >> 5); w < total; w += gridDim.x * warps_per_block) {
-        if (w < n_occ) {
-            const int cl = c.occ_cell[w];
-            const int beg = c.occ_beg[w], end = c.occ_beg[w + 1];
-            // corner k = lane & 7, component a = lane >> 3 (lanes 0..23)
-            const int node = corner_node(c, cl, lane & 7);
-            const int slot = node_slot<kAll>(c, node);
-            const int vi = (kOp == kOpApply) ? slot : node;
-            const float mine = lane < 24 ? vec[(lane >> 3) * c.ld + vi] : 0.f;
-            float cv[24];
-#pragma unroll
-            for (int e = 0; e < 24; e++) cv[e] = __shfl_sync(FULL, mine, e);
-            float acc[32], acc2[32];
-#pragma unroll
-            for (int e = 0; e < 32; e++) acc[e] = acc2[e] = 0.f;
-            for (int j = beg + lane; j < end; j += 32) {
+// Sample passes over the occupied cells.  A block takes a slice of cells [cb, ce) and
+// their (contiguous, cell-sorted) samples in two phases per chunk of blockDim samples:
+//   1. one thread per sample: s = g' . sum_k alpha_k v_k over the 8 corners, and the
+//      per-sample factor t (kept in shared memory);
+//   2. one thread per (cell, corner): sum_j alpha_k(j) g'_j t_j over the cell's samples,
+//      then one atomic per component.
+// vec is the slot-indexed p (kOpApply) or the node-indexed u (kOpRhs / kOpEnergy).
+//   kOpRhs:    t = -w_d (s + r0'):  r_k += alpha_k g' t,  diag_k += alpha_k^2 w_d g'^2
+//   kOpApply:  t = w_d s:           q_k += alpha_k g' t,  part += t s      (= p.J^T J p)
+//   kOpEnergy: part += (s + r0')^2  (E_dense, phase 1 only)
+// kFresh reads vec through L2 (it was written by other CTAs of the same grid).
+template <bool kFresh>
+__device__ __forceinline__ float ldv(const float *p) {
+    return kFresh ? __ldcg(p) : *p;
+}
+
+// The vector a sample pass reads: vec[i], or (inside the persistent position step, where
+// p is formed on the fly) fma(beta, pold[i], vec[i]) with vec = z.
+struct VecView {
+    const float *vec;
+    const float *pold;  // nullptr: plain vec
+    float beta;
+};
+
+template <bool kFresh>
+__device__ __forceinline__ float ldvv(const VecView &v, size_t i) {
+    const float a = ldv<kFresh>(v.vec + i);
+    return v.pold ? fmaf(v.beta, ldv<kFresh>(v.pold + i), a) : a;
+}
+
+// synchronise the threads running a cells_block: the whole block (bar_id 0) or the
+// nt threads of named barrier bar_id
+__device__ __forceinline__ void sub_sync(int bar_id, int nt) {
+    if (bar_id == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nt) : "memory");
+}
+
+template <int kOp, bool kAll, bool kFresh>
+__device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, float *dst, float *dst2, int cb, int ce,
+                                            float *tsm, float &part, int lt, int nt, int bar_id) {
+    const int sb = c.occ_beg[cb], se = c.occ_beg[ce];
+    const int items = kOp == kOpEnergy ? 1 : (ce - cb) * 8;
+    for (int i0 = 0; i0 < items; i0 += nt) {
+        const int item = i0 + lt;
+        const bool has = kOp != kOpEnergy && item < items;
+        const int ci = cb + (has ? item >> 3 : 0), k = item & 7;
+        const int ibeg = has ? c.occ_beg[ci] : 0, iend = has ? c.occ_beg[ci + 1] : 0;
+        float ax = 0.f, ay = 0.f, az = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
+        for (int j0 = sb; j0 < se; j0 += nt) {
+            const int j = j0 + lt;
+            if (j < se) {
+                const int cl = c.cell[j];
                 const float4 f4 = c.frac[j], g = c.rec[j];
                 const float f[3] = {f4.x, f4.y, f4.z};
-                float al[8];
                 float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    al[k] = trilinear_weight(f, k);
-                    sx += al[k] * cv[k];
-                    sy += al[k] * cv[8 + k];
-                    sz += al[k] * cv[16 + k];
+                for (int kk = 0; kk < 8; kk++) {
+                    const int nd = corner_node(c, cl, kk);
+                    const int vi = (kOp == kOpApply) ? node_slot<kAll>(c, nd) : nd;
+                    const float al = trilinear_weight(f, kk);
+                    sx += al * ldvv<kFresh>(vec, vi);
+                    sy += al * ldvv<kFresh>(vec, c.ld + vi);
+                    sz += al * ldvv<kFresh>(vec, 2 * (size_t)c.ld + vi);
                 }
-                const float s = g.x * sx + g.y * sy + g.z * sz;
+                const float sv = g.x * sx + g.y * sy + g.z * sz;
                 if (kOp == kOpApply) {
-                    const float t = c.w_d * s;
-                    part += t * s;
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        acc[k] += al[k] * g.x * t;
-                        acc[8 + k] += al[k] * g.y * t;
-                        acc[16 + k] += al[k] * g.z * t;
-                    }
+                    const float t = c.w_d * sv;
+                    if (i0 == 0) part += t * sv;
+                    tsm[lt] = t;
                 } else if (kOp == kOpRhs) {
-                    const float t = -c.w_d * (s + g.w);
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        acc[k] += al[k] * g.x * t;
-                        acc[8 + k] += al[k] * g.y * t;
-                        acc[16 + k] += al[k] * g.z * t;
-                        const float a2 = al[k] * al[k] * c.w_d;
-                        acc2[k] += a2 * g.x * g.x;
-                        acc2[8 + k] += a2 * g.y * g.y;
-                        acc2[16 + k] += a2 * g.z * g.z;
-                    }
+                    tsm[lt] = -c.w_d * (sv + g.w);
                 } else {
-                    const float e = s + g.w;
+                    const float e = sv + g.w;
                     part += e * e;
                 }
             }
-            if (kOp != kOpEnergy) {
-                const float tot = warp_transpose_sum32(acc);
-                float *dst = (kOp == kOpApply) ? c.q : c.r;
-                if (lane < 24 && tot != 0.f) atomicAdd(&dst[(lane >> 3) * c.ld + slot], tot);
-                if (kOp == kOpRhs) {
-                    const float tot2 = warp_transpose_sum32(acc2);
-                    if (lane < 24 && tot2 != 0.f) atomicAdd(&c.minv[(lane >> 3) * c.ld + slot], tot2);
+            if (kOp == kOpEnergy) continue;
+            sub_sync(bar_id, nt);
+            if (has) {
+                const int lo = max(ibeg, j0), hi = min(iend, j0 + nt);
+                for (int jj = lo; jj < hi; jj++) {
+                    const float4 f4 = c.frac[jj], g = c.rec[jj];
+                    const float f[3] = {f4.x, f4.y, f4.z};
+                    const float al = trilinear_weight(f, k);
+                    const float t = al * tsm[jj - j0];
+                    ax += g.x * t;
+                    ay += g.y * t;
+                    az += g.z * t;
+                    if (kOp == kOpRhs) {
+                        const float a2 = al * al * c.w_d;
+                        dx += a2 * g.x * g.x;
+                        dy += a2 * g.y * g.y;
+                        dz += a2 * g.z * g.z;
+                    }
                 }
             }
+            sub_sync(bar_id, nt);
+        }
+        if (has) {
+            const int sl = node_slot<kAll>(c, corner_node(c, c.occ_cell[ci], k));
+            if (ax != 0.f) atomicAdd(&dst[sl], ax);
+            if (ay != 0.f) atomicAdd(&dst[c.ld + sl], ay);
+            if (az != 0.f) atomicAdd(&dst[2 * c.ld + sl], az);
+            if (kOp == kOpRhs) {
+                if (dx != 0.f) atomicAdd(&dst2[sl], dx);
+                if (dy != 0.f) atomicAdd(&dst2[c.ld + sl], dy);
+                if (dz != 0.f) atomicAdd(&dst2[2 * c.ld + sl], dz);
+            }
+        }
+    }
+}
+
+// Sparse pairs (Eq. 3), one thread per pair; d = R_g (f^ + sum alpha u) + t_g - f in FP64.
+//   kOpRhs:    r_k -= w_s alpha_k R_g^T d,  diag_k += w_s alpha_k^2 |R_g col|^2
+//   kOpApply:  q_k += w_s alpha_k R_g^T R_g sum alpha p;  part += w_s |R_g sum alpha p|^2
+//   kOpEnergy: partd += |d|^2
+template <int kOp, bool kAll, bool kFresh>
+__device__ __forceinline__ void sparse_pairs(const Ctx &c, const VecView vec, float *dst, float *dst2, int t0,
+                                             int nthreads, float &part, double &partd) {
+    for (int sp = t0; sp < c.S; sp += nthreads) {
+        const int cl = c.scell[sp];
+        if (cl < 0) continue;
+        const float4 f4 = c.sfrac[sp];
+        const float f[3] = {f4.x, f4.y, f4.z};
+        float al[8];
+        int sl[8];
+        V3<float> sv{0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            al[k] = trilinear_weight(f, k);
+            const int nd = corner_node(c, cl, k);
+            sl[k] = node_slot<kAll>(c, nd);
+            const int vi = (kOp == kOpApply) ? sl[k] : nd;
+            sv.x += al[k] * ldvv<kFresh>(vec, vi);
+            sv.y += al[k] * ldvv<kFresh>(vec, c.ld + vi);
+            sv.z += al[k] * ldvv<kFresh>(vec, 2 * (size_t)c.ld + vi);
+        }
+        if (kOp == kOpApply) {
+            const V3<float> t = rot<float>(c.Rg, sv);
+            part += c.w_s * dot(t, t);
+            const V3<float> back = rotT<float>(c.Rg, t);
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const float a = c.w_s * al[k];
+                atomicAdd(&dst[sl[k]], a * back.x);
+                atomicAdd(&dst[c.ld + sl[k]], a * back.y);
+                atomicAdd(&dst[2 * c.ld + sl[k]], a * back.z);
+            }
         } else {
-            const int s = (w - n_occ) * 32 + lane;
-            if (s < c.S && c.scell[s] >= 0) {
-                const int cl = c.scell[s];
-                const float4 f4 = c.sfrac[s];
-                const float f[3] = {f4.x, f4.y, f4.z};
-                float al[8];
-                int nd[8];
-                V3<float> sv{0.f, 0.f, 0.f};
+            const float4 fh = c.fh[sp], ft = c.ft[sp];
+            const V3<double> xq{(double)fh.x + sv.x, (double)fh.y + sv.y, (double)fh.z + sv.z};
+            V3<double> d = rot<double>(c.Rg, xq);
+            d.x += (double)c.tg[0] - (double)ft.x;
+            d.y += (double)c.tg[1] - (double)ft.y;
+            d.z += (double)c.tg[2] - (double)ft.z;
+            if (kOp == kOpEnergy) {
+                partd += dot(d, d);
+            } else {
+                const V3<float> back = rotT<float>(c.Rg, V3<float>{(float)d.x, (float)d.y, (float)d.z});
+                const float cn[3] = {c.Rg[0] * c.Rg[0] + c.Rg[3] * c.Rg[3] + c.Rg[6] * c.Rg[6],
+                                     c.Rg[1] * c.Rg[1] + c.Rg[4] * c.Rg[4] + c.Rg[7] * c.Rg[7],
+                                     c.Rg[2] * c.Rg[2] + c.Rg[5] * c.Rg[5] + c.Rg[8] * c.Rg[8]};
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
-                    al[k] = trilinear_weight(f, k);
-                    nd[k] = corner_node(c, cl, k);
-                    const int vi = (kOp == kOpApply) ? node_slot<kAll>(c, nd[k]) : nd[k];
-                    sv.x += al[k] * vec[vi];
-                    sv.y += al[k] * vec[c.ld + vi];
-                    sv.z += al[k] * vec[2 * c.ld + vi];
-                }
-                if (kOp == kOpApply) {
-                    // s = sqrt(w_s) R_g sum alpha p ; q_k += sqrt(w_s) alpha_k R_g^T s
-                    const V3<float> t = rot<float>(c.Rg, sv);
-                    part += c.w_s * dot(t, t);
-                    const V3<float> back = rotT<float>(c.Rg, t);
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        const int sl = node_slot<kAll>(c, nd[k]);
-                        const float a = c.w_s * al[k];
-                        atomicAdd(&c.q[sl], a * back.x);
-                        atomicAdd(&c.q[c.ld + sl], a * back.y);
-                        atomicAdd(&c.q[2 * c.ld + sl], a * back.z);
-                    }
-                } else {
-                    // residual S(f^) - f in FP64: R_g (f^ + sum alpha u) + t_g - f
-                    const float4 fh = c.fh[s], ft = c.ft[s];
-                    const V3<double> xq{(double)fh.x + sv.x, (double)fh.y + sv.y, (double)fh.z + sv.z};
-                    V3<double> d = rot<double>(c.Rg, xq);
-                    d.x += (double)c.tg[0] - (double)ft.x;
-                    d.y += (double)c.tg[1] - (double)ft.y;
-                    d.z += (double)c.tg[2] - (double)ft.z;
-                    if (kOp == kOpEnergy) {
-                        partd += dot(d, d);
-                    } else {
-                        // b_k -= w_s alpha_k R_g^T d ; diag_k += w_s alpha_k^2 (R_g^T R_g)_aa
-                        const V3<float> back = rotT<float>(c.Rg, V3<float>{(float)d.x, (float)d.y, (float)d.z});
-                        float cn[3];
-#pragma unroll
-                        for (int a = 0; a < 3; a++)
-                            cn[a] = c.Rg[a] * c.Rg[a] + c.Rg[3 + a] * c.Rg[3 + a] + c.Rg[6 + a] * c.Rg[6 + a];
-#pragma unroll
-                        for (int k = 0; k < 8; k++) {
-                            const int sl = node_slot<kAll>(c, nd[k]);
-                            const float a = c.w_s * al[k];
-                            atomicAdd(&c.r[sl], -a * back.x);
-                            atomicAdd(&c.r[c.ld + sl], -a * back.y);
-                            atomicAdd(&c.r[2 * c.ld + sl], -a * back.z);
-                            const float a2 = a * al[k];
-                            atomicAdd(&c.minv[sl], a2 * cn[0]);
-                            atomicAdd(&c.minv[c.ld + sl], a2 * cn[1]);
-                            atomicAdd(&c.minv[2 * c.ld + sl], a2 * cn[2]);
-                        }
-                    }
+                    const float a = c.w_s * al[k];
+                    atomicAdd(&dst[sl[k]], -a * back.x);
+                    atomicAdd(&dst[c.ld + sl[k]], -a * back.y);
+                    atomicAdd(&dst[2 * c.ld + sl[k]], -a * back.z);
+                    const float a2 = a * al[k];
+                    atomicAdd(&dst2[sl[k]], a2 * cn[0]);
+                    atomicAdd(&dst2[c.ld + sl[k]], a2 * cn[1]);
+                    atomicAdd(&dst2[2 * c.ld + sl[k]], a2 * cn[2]);
                 }
             }
         }
     }
+}
+
+constexpr int kCellsPerBlock = 16;
+
+template <int kOp, bool kAll>
+__global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int it) {
+    pdl_wait();
+    pdl_trigger();
+    if (kOp == kOpApply) {
+        if (sc->stop || !(scal_rho(sc)[it] > 0.0)) return;
+    }
+    __shared__ float tsm[kThreads];
+    const VecView vec{(kOp == kOpApply) ? c.p : c.u, nullptr, 0.f};
+    float *dst = (kOp == kOpApply) ? c.q : c.r;
+    float part = 0.f;
+    double partd = 0.0;
+    const int n_occ = *c.n_occ;
+    for (int cb = blockIdx.x * kCellsPerBlock; cb < n_occ; cb += gridDim.x * kCellsPerBlock)
+        cells_block<kOp, kAll, false>(c, vec, dst, c.minv, cb, min(cb + kCellsPerBlock, n_occ), tsm, part,
+                                      threadIdx.x, blockDim.x, 0);
+    // pairs spread one per block first: one SM issuing all their atomics would be the tail
+    sparse_pairs<kOp, kAll, false>(c, vec, dst, c.minv, blockIdx.x + gridDim.x * threadIdx.x,
+                                   gridDim.x * blockDim.x, part, partd);
     if (kOp == kOpApply) block_add_f64(part, scal_pq(sc, K) + it);
     if (kOp == kOpEnergy) {
         block_add_f64(part, &sc->e_dense);
@@ -784,6 +870,8 @@ __global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int 
 //   diag_k = 2 w_r |N_k|.  Written with plain stores (the sample pass adds after).
 template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_rhs_nodes(Ctx c) {
+    pdl_wait();
+    pdl_trigger();
     const int N = active_count<kAll>(c);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
         const int i = slot_node<kAll>(c, s);
@@ -814,109 +902,640 @@ __global__ void __launch_bounds__(kThreads) k_rhs_nodes(Ctx c) {
     }
 }
 
+// PCG vectors are walked as float4 groups of one component plane per blockIdx.y (the
+// planes are 128-byte aligned, ld is a multiple of 32).  The pad slots [N, 4 ceil(N/4))
+// are zeroed by k_pcg_init, so a group straddling N only ever adds zeros.
+__device__ __forceinline__ int groups4(int N) { return (N + 3) >> 2; }
+
 // PCG start (x0 = 0): Minv = 1/diag (0 where diag = 0), r = b, p = z = Minv r, rho0 = r.z
 template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_pcg_init(Ctx c, Scal *sc) {
+    pdl_wait();
+    pdl_trigger();
     const int N = active_count<kAll>(c);
+    const size_t off = (size_t)blockIdx.y * c.ld;
+    float *__restrict__ minv = c.minv + off;
+    float *__restrict__ r = c.r + off;
+    float *__restrict__ p = c.p + off;
+    float *__restrict__ x = c.x + off;
+    float *__restrict__ q = c.q + off;
     float part = 0.f;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const int k = a * c.ld + s;
-            const float dg = c.minv[k];
-            const float mi = dg > 0.f ? 1.0f / dg : 0.f;
-            const float rr = c.r[k];
-            const float z = mi * rr;
-            c.minv[k] = mi;
-            c.p[k] = z;
-            c.x[k] = 0.f;
-            part += rr * z;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < 4 * groups4(N); s += gridDim.x * blockDim.x) {
+        if (s >= N) {  // pad slots of the last group
+            minv[s] = 0.f;
+            r[s] = 0.f;
+            p[s] = 0.f;
+            x[s] = 0.f;
+            q[s] = 0.f;
+            continue;
         }
+        const float dg = minv[s];
+        const float mi = dg > 0.f ? 1.0f / dg : 0.f;
+        const float rr = r[s];
+        const float z = mi * rr;
+        minv[s] = mi;
+        p[s] = z;
+        x[s] = 0.f;
+        part += rr * z;
     }
     block_add_f64(part, &scal_rho(sc)[0]);
 }
 
-// q = 2 w_r L p (7-point graph Laplacian of M), with the partial p.q
-template <bool kAll>
+// all-nodes lattice with nx % 4 == 0: q for the 4 nodes of one row starting at s0
+__device__ __forceinline__ float stencil4(const Ctx &c, int s0, float w2) {
+    const int x0 = s0 % c.nx, t = s0 / c.nx, y = t % c.ny, z = t / c.ny, pl = c.nx * c.ny;
+    float part = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float *__restrict__ P = c.p + (size_t)a * c.ld;
+        const float4 pc = *reinterpret_cast<const float4 *>(P + s0);
+        // a missing neighbour is replaced by the node itself: its difference is 0
+        const float left = x0 > 0 ? P[s0 - 1] : pc.x;
+        const float right = x0 + 4 < c.nx ? P[s0 + 4] : pc.w;
+        float4 d = make_float4((pc.x - left) + (pc.x - pc.y), (pc.y - pc.x) + (pc.y - pc.z),
+                               (pc.z - pc.y) + (pc.z - pc.w), (pc.w - pc.z) + (pc.w - right));
+        const int offs[4] = {-c.nx, c.nx, -pl, pl};
+        const bool has[4] = {y > 0, y + 1 < c.ny, z > 0, z + 1 < c.nz};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (!has[k]) continue;
+            const float4 v = *reinterpret_cast<const float4 *>(P + s0 + offs[k]);
+            d.x += pc.x - v.x;
+            d.y += pc.y - v.y;
+            d.z += pc.z - v.z;
+            d.w += pc.w - v.w;
+        }
+        d.x *= w2;
+        d.y *= w2;
+        d.z *= w2;
+        d.w *= w2;
+        *reinterpret_cast<float4 *>(c.q + (size_t)a * c.ld + s0) = d;
+        part += pc.x * d.x + pc.y * d.y + pc.z * d.z + pc.w * d.w;
+    }
+    return part;
+}
+
+// q = 2 w_r L p (7-point graph Laplacian of M), with the partial p.q.
+// kVec4: all-nodes lattice with nx % 4 == 0, one thread per 4 nodes of a row.
+template <bool kAll, bool kVec4>
 __global__ void __launch_bounds__(kThreads) k_apply_stencil(Ctx c, Scal *sc, int K, int it) {
-    if (sc->stop || !(scal_rho(sc)[it] > 0.0)) return;
+    pdl_wait();
+    pdl_trigger();
+    if (it >= 0 && (sc->stop || !(scal_rho(sc)[it] > 0.0))) return;
     const int N = active_count<kAll>(c);
     float part = 0.f;
     const float w2 = 2.f * c.w_r;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
-        int nb[6];
-        neighbours<kAll>(c, s, nb);
-        const float3 pi = ld3(c.p, c.ld, s);
-        float qx = 0.f, qy = 0.f, qz = 0.f;
+    if (kVec4) {
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < (N >> 2); g += gridDim.x * blockDim.x)
+            part += stencil4(c, 4 * g, w2);
+    } else {
+        for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+            int nb[6];
+            neighbours<kAll>(c, s, nb);
+            const float3 pi = ld3(c.p, c.ld, s);
+            float qx = 0.f, qy = 0.f, qz = 0.f;
 #pragma unroll
-        for (int d = 0; d < 6; d++) {
-            if (nb[d] < 0) continue;
-            const float3 pj = ld3(c.p, c.ld, nb[d]);
-            qx += pi.x - pj.x;
-            qy += pi.y - pj.y;
-            qz += pi.z - pj.z;
+            for (int d = 0; d < 6; d++) {
+                if (nb[d] < 0) continue;
+                const float3 pj = ld3(c.p, c.ld, nb[d]);
+                qx += pi.x - pj.x;
+                qy += pi.y - pj.y;
+                qz += pi.z - pj.z;
+            }
+            qx *= w2;
+            qy *= w2;
+            qz *= w2;
+            st3(c.q, c.ld, s, make_float3(qx, qy, qz));
+            part += pi.x * qx + pi.y * qy + pi.z * qz;
         }
-        qx *= w2;
-        qy *= w2;
-        qz *= w2;
-        st3(c.q, c.ld, s, make_float3(qx, qy, qz));
-        part += pi.x * qx + pi.y * qy + pi.z * qz;
     }
-    block_add_f64(part, scal_pq(sc, K) + it);
+    block_add_f64(part, scal_pq(sc, K) + (it >= 0 ? it : 0));
 }
 
-// alpha = rho/pq; x += alpha p; r -= alpha q; z = Minv r; partial rho' = r.z
+// alpha = rho/pq; x += alpha p; r -= alpha q; z = Minv r; partial rho' = r.z.
+// One wave of fat threads: each thread takes float4 group g of all three component
+// planes, so its 15 vector loads are in flight together.
 template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_update_x(Ctx c, Scal *sc, int K, int it) {
-    const double rho = scal_rho(sc)[it], pq = scal_pq(sc, K)[it];
-    if (sc->stop || !(rho > 0.0) || !(pq > 0.0)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) sc->stop = 1;
-        return;
+    pdl_wait();
+    pdl_trigger();
+    __shared__ float s_alpha;
+    __shared__ int s_go;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    if (threadIdx.x == 0) {  // one FP64 division per block
+        const double rho = scal_rho(sc)[it], pq = scal_pq(sc, K)[it];
+        s_go = !sc->stop && rho > 0.0 && pq > 0.0;
+        s_alpha = s_go ? (float)(rho / pq) : 0.f;
+        if (!s_go && lead) sc->stop = 1;
     }
-    const float alpha = (float)(rho / pq);
-    const int N = active_count<kAll>(c);
+    __syncthreads();
+    if (!s_go) return;
+    const float alpha = s_alpha;
+    const int G4 = groups4(active_count<kAll>(c));
+    const int ld4 = c.ld >> 2;
+    float4 *__restrict__ x = reinterpret_cast<float4 *>(c.x);
+    float4 *__restrict__ r = reinterpret_cast<float4 *>(c.r);
+    const float4 *__restrict__ p = reinterpret_cast<const float4 *>(c.p);
+    const float4 *__restrict__ q = reinterpret_cast<const float4 *>(c.q);
+    const float4 *__restrict__ m = reinterpret_cast<const float4 *>(c.minv);
     float part = 0.f;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G4; g += gridDim.x * blockDim.x) {
+        float4 xv[3], pv[3], rv[3], qv[3], mv[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const int k = a * c.ld + s;
-            c.x[k] += alpha * c.p[k];
-            const float rr = c.r[k] - alpha * c.q[k];
-            c.r[k] = rr;
-            part += rr * (c.minv[k] * rr);
+            const int k = a * ld4 + g;
+            xv[a] = x[k];
+            pv[a] = p[k];
+            rv[a] = r[k];
+            qv[a] = q[k];
+            mv[a] = m[k];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int k = a * ld4 + g;
+            const float4 xn = make_float4(fmaf(alpha, pv[a].x, xv[a].x), fmaf(alpha, pv[a].y, xv[a].y),
+                                          fmaf(alpha, pv[a].z, xv[a].z), fmaf(alpha, pv[a].w, xv[a].w));
+            const float4 rn = make_float4(fmaf(-alpha, qv[a].x, rv[a].x), fmaf(-alpha, qv[a].y, rv[a].y),
+                                          fmaf(-alpha, qv[a].z, rv[a].z), fmaf(-alpha, qv[a].w, rv[a].w));
+            x[k] = xn;
+            r[k] = rn;
+            part += rn.x * (mv[a].x * rn.x) + rn.y * (mv[a].y * rn.y) + rn.z * (mv[a].z * rn.z) +
+                    rn.w * (mv[a].w * rn.w);
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->cg_done = it + 1;
+    if (lead) sc->cg_done = it + 1;
     block_add_f64(part, &scal_rho(sc)[it + 1]);
 }
 
 // beta = rho'/rho; p = Minv r + beta p (stop once rho' <= tol^2 rho0)
 template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_update_p(Ctx c, Scal *sc, int it, double tol2) {
-    if (sc->stop) return;
-    const double rho1 = scal_rho(sc)[it + 1], rho = scal_rho(sc)[it];
-    if (rho1 <= tol2 * scal_rho(sc)[0]) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) sc->stop = 1;
-        return;
+    pdl_wait();
+    pdl_trigger();
+    __shared__ float s_beta;
+    __shared__ int s_go;
+    if (threadIdx.x == 0) {  // one FP64 division per block
+        const double rho1 = scal_rho(sc)[it + 1], rho = scal_rho(sc)[it];
+        s_go = !sc->stop && !(rho1 <= tol2 * scal_rho(sc)[0]);
+        s_beta = s_go ? (float)(rho1 / rho) : 0.f;
+        if (!sc->stop && !s_go && blockIdx.x == 0) sc->stop = 1;
     }
-    const float beta = (float)(rho1 / rho);
-    const int N = active_count<kAll>(c);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+    __syncthreads();
+    if (!s_go) return;
+    const float beta = s_beta;
+    const int G4 = groups4(active_count<kAll>(c));
+    const int ld4 = c.ld >> 2;
+    float4 *__restrict__ p = reinterpret_cast<float4 *>(c.p);
+    const float4 *__restrict__ r = reinterpret_cast<const float4 *>(c.r);
+    const float4 *__restrict__ m = reinterpret_cast<const float4 *>(c.minv);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G4; g += gridDim.x * blockDim.x) {
+        float4 pv[3], rv[3], mv[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const int k = a * c.ld + s;
-            c.p[k] = c.minv[k] * c.r[k] + beta * c.p[k];
+            const int k = a * ld4 + g;
+            pv[a] = p[k];
+            rv[a] = r[k];
+            mv[a] = m[k];
         }
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            p[a * ld4 + g] = make_float4(fmaf(beta, pv[a].x, mv[a].x * rv[a].x), fmaf(beta, pv[a].y, mv[a].y * rv[a].y),
+                                         fmaf(beta, pv[a].z, mv[a].z * rv[a].z), fmaf(beta, pv[a].w, mv[a].w * rv[a].w));
     }
 }
 
 template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_add_increment(Ctx c) {
+    pdl_wait();
+    pdl_trigger();
     const int N = active_count<kAll>(c);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
         const int i = slot_node<kAll>(c, s);
 #pragma unroll
         for (int a = 0; a < 3; a++) c.u[a * c.ld + i] += c.x[a * c.ld + s];
+    }
+}
+
+// ------------------------------------------------------------------ persistent PCG (Sec. 7.1 position step)
+
+// One cooperative launch runs a whole position step.  Each CTA owns a contiguous range
+// of `chunk` slots (a multiple of 4) and keeps p, r and q of its slots in shared memory
+// and x in registers for all K iterations; only p is published to global memory (read
+// through L2 by the CTAs whose stencil or samples need it), and the samples' J^T J p
+// contributions go to a global buffer with atomics that the owners fold in and clear.
+// Three grid barriers per iteration (after p.Ap, after r.z, after publishing p).  The
+// reductions are deterministic: every CTA writes its FP64 partial to a per-iteration row
+// and every CTA sums the row in CTA order.  A barrier that waits longer than about a
+// second sets the error flag and the whole grid returns.
+constexpr int kPcgThreads = 1024;
+constexpr int kPcgMaxGroups = 2;  // float4 groups per thread: chunk <= 4 * 2 * 1024
+constexpr int kPcgHalf = kPcgThreads / 2;
+constexpr long long kBarrierCycles = 2000000000LL;
+
+struct PcgAux {
+    double *part;      // rows 0..K: r.z partials, rows K+1..2K: p.Ap partials, G entries each
+    unsigned *bar;     // [0] arrivals, [1] generation of the grid barrier
+    int *err;          // set when a barrier wait gives up
+    const int *surf;   // ascending slots touched by samples or sparse pairs
+    const int *n_surf;
+    float *pbuf[2];    // p of even / odd iterations, published for the other CTAs
+    int chunk;
+};
+
+// Grid barrier that can also reduce: bar[0] counts arrivals, bar[1] is the generation.
+// Thread 0 of each CTA publishes the CTA's writes (fence), reads the generation and
+// arrives.  The last CTA to arrive sums `row` (one FP64 partial per CTA, written before
+// the call) in CTA order, stores the sum in *total, resets the count and bumps the
+// generation (release); the others poll the generation (acquire) for at most
+// kBarrierCycles.  Every CTA then returns the same total through *out.
+__device__ __forceinline__ bool grid_reduce(unsigned *bar, int *err, unsigned G, const double *row, double *total,
+                                            double *out) {
+    __shared__ int s_last, s_ok;
+    __shared__ unsigned s_gen;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        unsigned g0, a;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g0) : "l"(bar + 1) : "memory");
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(a) : "l"(bar) : "memory");
+        s_last = a == G - 1;
+        s_gen = g0;
+    }
+    __syncthreads();
+    int good = 1;
+    if (s_last) {
+        if (threadIdx.x < 32) {
+            double sum = 0.0;
+            if (row) {
+                double v[5];
+#pragma unroll
+                for (int k = 0; k < 5; k++) {  // all loads in flight before the first add
+                    const unsigned b = threadIdx.x + 32u * k;
+                    v[k] = b < G ? __ldcg(row + b) : 0.0;
+                }
+                sum = (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
+                for (unsigned b = threadIdx.x + 160u; b < G; b += 32) sum += __ldcg(row + b);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+            }
+            if (threadIdx.x == 0) {
+                if (row) *total = sum;
+                __threadfence();
+                asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        while (true) {
+            unsigned g;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+            if (g != s_gen) break;
+            if (*(volatile int *)err) {
+                good = 0;
+                break;
+            }
+            if (clock64() - t0 > kBarrierCycles) {
+                atomicExch(err, 1);
+                good = 0;
+                break;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        s_ok = good && !*(volatile int *)err;
+        if (row) *out = __ldcg(total);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, unsigned G) {
+    return grid_reduce(bar, err, G, nullptr, nullptr, nullptr);
+}
+
+// FP64 block sum of one float per thread; valid in thread 0
+__device__ __forceinline__ double block_total(float v, double *red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) s = warp0_tree_f64(red, lane);
+    return s;
+}
+
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
+template <bool kAll, bool kVec4>
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *sc, PcgAux ax, int K, double tol2,
+                                                                   int apply) {
+    // Two grid barriers per iteration.  Phase A forms p = z + beta p_old itself (own
+    // slots in shared memory; a remote neighbour's from its published z and p_old), so
+    // no barrier is needed after the p update:
+    //   A: p update (own), q = 2 w_r L p (stencil warps) | samples' J^T J p (other warps)
+    //   -- barrier + sum p.Ap --
+    //   B: x += alpha p, r -= alpha q, z = Minv r (published), r.z
+    //   -- barrier + sum r.z --
+    // Global buffers: c.minv (Minv), c.r (z, published; holds b on entry), ax.pbuf
+    // (p of even / odd iterations), c.q (the samples' contributions), c.x (result).
+    extern __shared__ float4 sm4[];
+    __shared__ double red[32];
+    __shared__ double bc;
+    __shared__ int sb_lo, sb_hi;
+    __shared__ float tsm[kPcgHalf];
+    __shared__ float s_ab;
+    float *sm = reinterpret_cast<float *>(sm4);
+    const int chunk = ax.chunk;
+    float *__restrict__ P = sm;               // p of own slots
+    float *__restrict__ Rr = sm + 3 * chunk;  // r of own slots
+    float *__restrict__ Q = sm + 6 * chunk;   // z between phases B and A, q within A..B
+    float *__restrict__ Zg = c.r;
+    const unsigned G = gridDim.x;
+    const int N = active_count<kAll>(c);
+    const int N4 = 4 * groups4(N);
+    const int s_beg = blockIdx.x * chunk;
+    const int s_end = min(s_beg + chunk, N4);
+    const int ng = s_end > s_beg ? (s_end - s_beg) >> 2 : 0;
+    const int tid = threadIdx.x;
+    const float w2 = 2.f * c.w_r;
+    const size_t ld = c.ld;
+    float4 xr[kPcgMaxGroups][3];
+    if (tid == 0) {  // own range of the surface list
+        const int n = *ax.n_surf;
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (ax.surf[m] < s_beg) lo = m + 1;
+            else hi = m;
+        }
+        sb_lo = lo;
+        hi = n;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (ax.surf[m] < s_end) lo = m + 1;
+            else hi = m;
+        }
+        sb_hi = lo;
+    }
+    // ---- init: Minv = 1/diag, r = b, z = Minv r, p_old = 0, x = 0; rho0 = r.z
+    float part = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < kPcgMaxGroups; kk++) {
+        const int gl = tid + kk * kPcgThreads;
+#pragma unroll
+        for (int a = 0; a < 3; a++) xr[kk][a] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gl >= ng) continue;
+        const int l = 4 * gl, s = s_beg + l;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const float4 dg = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
+            const float4 rb = __ldcg(reinterpret_cast<const float4 *>(c.r + a * ld + s));
+            const float dv[4] = {dg.x, dg.y, dg.z, dg.w}, rv[4] = {rb.x, rb.y, rb.z, rb.w};
+            float mi[4], rr[4], z[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const bool in = s + e < N;
+                mi[e] = (in && dv[e] > 0.f) ? 1.0f / dv[e] : 0.f;
+                rr[e] = in ? rv[e] : 0.f;
+                z[e] = mi[e] * rr[e];
+                part += rr[e] * z[e];
+            }
+            const float4 z4 = make_float4(z[0], z[1], z[2], z[3]), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4 *>(c.minv + a * ld + s) = make_float4(mi[0], mi[1], mi[2], mi[3]);
+            *reinterpret_cast<float4 *>(Rr + a * chunk + l) = make_float4(rr[0], rr[1], rr[2], rr[3]);
+            *reinterpret_cast<float4 *>(Q + a * chunk + l) = z4;
+            *reinterpret_cast<float4 *>(P + a * chunk + l) = zero;
+            *reinterpret_cast<float4 *>(Zg + a * ld + s) = z4;
+            *reinterpret_cast<float4 *>(ax.pbuf[1] + a * ld + s) = zero;
+        }
+    }
+    __syncthreads();
+    for (int t = sb_lo + tid; t < sb_hi; t += blockDim.x) {
+        const int sl = ax.surf[t];
+#pragma unroll
+        for (int a = 0; a < 3; a++) c.q[a * ld + sl] = 0.f;
+    }
+    double *tot = ax.part + (size_t)(2 * K + 1) * G;  // two broadcast slots
+    {
+        const double bt = block_total(part, red);
+        if (tid == 0) ax.part[blockIdx.x] = bt;
+    }
+    bool ok = grid_reduce(ax.bar, ax.err, G, ax.part, tot, &bc);
+    const double rho0 = ok ? bc : 0.0;
+    double rho = rho0;
+    float beta = 0.f;
+    if (blockIdx.x == 0 && tid == 0) scal_rho(sc)[0] = rho0;
+    int done = 0;
+    int stop = !ok;
+    for (int it = 0; it < K && !stop; it++) {
+        if (!(rho > 0.0)) {
+            stop = 1;
+            break;
+        }
+        const float *__restrict__ pold = ax.pbuf[(it + 1) & 1];
+        float *__restrict__ pnew = ax.pbuf[it & 1];
+        part = 0.f;
+        if (tid < kPcgHalf) {
+            // ---- A1: p = z + beta p_old for own slots
+#pragma unroll 1
+            for (int gl = tid; gl < ng; gl += kPcgHalf) {
+                const int l = 4 * gl, s = s_beg + l;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
+                    const float4 zv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
+                    const float4 pn = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y),
+                                                  fmaf(beta, pv.z, zv.z), fmaf(beta, pv.w, zv.w));
+                    *reinterpret_cast<float4 *>(P + a * chunk + l) = pn;
+                    *reinterpret_cast<float4 *>(pnew + a * ld + s) = pn;
+                }
+            }
+            sub_sync(2, kPcgHalf);
+            // ---- A2: q = 2 w_r L p into Q
+#pragma unroll 1
+            for (int gl = tid; gl < ng; gl += kPcgHalf) {
+                const int l = 4 * gl, s0 = s_beg + l;
+                if (kVec4) {
+                    const int x0 = s0 % c.nx, t = s0 / c.nx, y = t % c.ny, z = t / c.ny, pl = c.nx * c.ny;
+                    const int offs[4] = {-c.nx, c.nx, -pl, pl};
+                    const bool has[4] = {y > 0, y + 1 < c.ny, z > 0, z + 1 < c.nz};
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        const float *Pa = P + a * chunk;
+                        const float *Za = Zg + a * ld, *Oa = pold + a * ld;
+                        const float4 pc = *reinterpret_cast<const float4 *>(Pa + l);
+                        float left = pc.x, right = pc.w;
+                        if (x0 > 0)
+                            left = (s0 - 1 >= s_beg) ? Pa[l - 1]
+                                                     : fmaf(beta, __ldcg(Oa + s0 - 1), __ldcg(Za + s0 - 1));
+                        if (x0 + 4 < c.nx)
+                            right = (s0 + 4 < s_end) ? Pa[l + 4]
+                                                     : fmaf(beta, __ldcg(Oa + s0 + 4), __ldcg(Za + s0 + 4));
+                        float4 d = make_float4((pc.x - left) + (pc.x - pc.y), (pc.y - pc.x) + (pc.y - pc.z),
+                                               (pc.z - pc.y) + (pc.z - pc.w), (pc.w - pc.z) + (pc.w - right));
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            if (!has[k]) continue;
+                            const int sj = s0 + offs[k];
+                            float4 v;
+                            if (sj >= s_beg && sj < s_end) {
+                                v = *reinterpret_cast<const float4 *>(Pa + (sj - s_beg));
+                            } else {
+                                const float4 zz = __ldcg(reinterpret_cast<const float4 *>(Za + sj));
+                                const float4 oo = __ldcg(reinterpret_cast<const float4 *>(Oa + sj));
+                                v = make_float4(fmaf(beta, oo.x, zz.x), fmaf(beta, oo.y, zz.y), fmaf(beta, oo.z, zz.z),
+                                                fmaf(beta, oo.w, zz.w));
+                            }
+                            d.x += pc.x - v.x;
+                            d.y += pc.y - v.y;
+                            d.z += pc.z - v.z;
+                            d.w += pc.w - v.w;
+                        }
+                        d = make_float4(w2 * d.x, w2 * d.y, w2 * d.z, w2 * d.w);
+                        *reinterpret_cast<float4 *>(Q + a * chunk + l) = d;
+                        part += pc.x * d.x + pc.y * d.y + pc.z * d.z + pc.w * d.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int si = s0 + e;
+                        float q3[3] = {0.f, 0.f, 0.f};
+                        if (si < N) {
+                            int nb[6];
+                            neighbours<kAll>(c, si, nb);
+                            float pi[3];
+#pragma unroll
+                            for (int a = 0; a < 3; a++) pi[a] = P[a * chunk + l + e];
+#pragma unroll
+                            for (int d = 0; d < 6; d++) {
+                                const int sj = nb[d];
+                                if (sj < 0) continue;
+                                const bool own = sj >= s_beg && sj < s_end;
+#pragma unroll
+                                for (int a = 0; a < 3; a++) {
+                                    const float pj = own ? P[a * chunk + (sj - s_beg)]
+                                                         : fmaf(beta, __ldcg(pold + a * ld + sj), __ldcg(Zg + a * ld + sj));
+                                    q3[a] += pi[a] - pj;
+                                }
+                            }
+#pragma unroll
+                            for (int a = 0; a < 3; a++) {
+                                q3[a] *= w2;
+                                part += pi[a] * q3[a];
+                            }
+                        }
+#pragma unroll
+                        for (int a = 0; a < 3; a++) Q[a * chunk + l + e] = q3[a];
+                    }
+                }
+            }
+        } else {
+            // ---- A: the samples' J^T J p into c.q (atomics), p formed from z and p_old
+            const int lt = tid - kPcgHalf;
+            const VecView pv{Zg, pold, beta};
+            const int n_occ = *c.n_occ;
+            const int per = (n_occ + (int)G - 1) / (int)G;
+            const int cb = min((int)blockIdx.x * per, n_occ), ce = min(cb + per, n_occ);
+            if (ce > cb) cells_block<kOpApply, kAll, true>(c, pv, c.q, nullptr, cb, ce, tsm, part, lt, kPcgHalf, 1);
+            double pd = 0.0;
+            sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * lt, G * kPcgHalf, part, pd);
+        }
+        {
+            const double bt = block_total(part, red);
+            if (tid == 0) ax.part[(size_t)(K + 1 + it) * G + blockIdx.x] = bt;
+        }
+        ok = grid_reduce(ax.bar, ax.err, G, ax.part + (size_t)(K + 1 + it) * G, tot, &bc);
+        if (!ok) {
+            stop = 1;
+            break;
+        }
+        const double pq = bc;
+        if (!(pq > 0.0)) {
+            stop = 1;
+            break;
+        }
+        if (tid == 0) {  // one FP64 division per CTA
+            s_ab = (float)(rho / pq);
+            if (blockIdx.x == 0) scal_pq(sc, K)[it] = pq;
+        }
+        // fold in (and clear) the samples' contributions to own slots
+        for (int t = sb_lo + tid; t < sb_hi; t += blockDim.x) {
+            const int sl = ax.surf[t];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                Q[a * chunk + (sl - s_beg)] += __ldcg(c.q + a * ld + sl);
+                c.q[a * ld + sl] = 0.f;
+            }
+        }
+        __syncthreads();
+        const float alpha = s_ab;
+        // ---- B: x += alpha p; r -= alpha q; z = Minv r (Q and published); rho' = r.z
+        part = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < kPcgMaxGroups; kk++) {
+            const int gl = tid + kk * kPcgThreads;
+            if (gl >= ng) continue;
+            const int l = 4 * gl, s = s_beg + l;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
+                const float4 qv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
+                const float4 rv = *reinterpret_cast<const float4 *>(Rr + a * chunk + l);
+                const float4 mv = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
+                xr[kk][a] = make_float4(fmaf(alpha, pv.x, xr[kk][a].x), fmaf(alpha, pv.y, xr[kk][a].y),
+                                        fmaf(alpha, pv.z, xr[kk][a].z), fmaf(alpha, pv.w, xr[kk][a].w));
+                const float4 rn = make_float4(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y),
+                                              fmaf(-alpha, qv.z, rv.z), fmaf(-alpha, qv.w, rv.w));
+                const float4 zn = make_float4(mv.x * rn.x, mv.y * rn.y, mv.z * rn.z, mv.w * rn.w);
+                *reinterpret_cast<float4 *>(Rr + a * chunk + l) = rn;
+                *reinterpret_cast<float4 *>(Q + a * chunk + l) = zn;
+                *reinterpret_cast<float4 *>(Zg + a * ld + s) = zn;
+                part += rn.x * zn.x + rn.y * zn.y + rn.z * zn.z + rn.w * zn.w;
+            }
+        }
+        {
+            const double bt = block_total(part, red);
+            if (tid == 0) ax.part[(size_t)(it + 1) * G + blockIdx.x] = bt;
+        }
+        done = it + 1;
+        ok = grid_reduce(ax.bar, ax.err, G, ax.part + (size_t)(it + 1) * G, tot + 1, &bc);
+        if (!ok) {
+            stop = 1;
+            break;
+        }
+        const double rho1 = bc;
+        if (blockIdx.x == 0 && tid == 0) scal_rho(sc)[it + 1] = rho1;
+        if (rho1 <= tol2 * rho0) {
+            stop = 1;
+            break;
+        }
+        if (tid == 0) s_ab = (float)(rho1 / rho);
+        __syncthreads();
+        beta = s_ab;
+        rho = rho1;
+    }
+    // ---- x out (and u += x when the step is applied)
+#pragma unroll
+    for (int kk = 0; kk < kPcgMaxGroups; kk++) {
+        const int gl = tid + kk * kPcgThreads;
+        if (gl >= ng) continue;
+        const int s = s_beg + 4 * gl;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            *reinterpret_cast<float4 *>(c.x + a * ld + s) = xr[kk][a];
+            if (apply) {
+                const float xv[4] = {xr[kk][a].x, xr[kk][a].y, xr[kk][a].z, xr[kk][a].w};
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    if (s + e < N) c.u[a * ld + slot_node<kAll>(c, s + e)] += xv[e];
+            }
+        }
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        sc->cg_done = done;
+        sc->stop = stop;
     }
 }
 
@@ -994,6 +1613,8 @@ __device__ __forceinline__ float sym4_top_eigvec(float a[4][4], float q[4]) {
 // Also accumulates E_reg (Eq. 4) with the new rotations (kFit = false: E_reg only).
 template <bool kAll, bool kFit>
 __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
+    pdl_wait();
+    pdl_trigger();
     const int N = active_count<kAll>(c);
     float part = 0.f;
     int degenerate = 0;
@@ -1111,6 +1732,8 @@ __global__ void k_aos_to_soa(const float *__restrict__ src, int planes, int n, i
 }
 
 __global__ void k_reset_warp(float *__restrict__ u, float *__restrict__ R, int n, int ld) {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int a = 0; a < 3; a++) u[a * ld + i] = 0.f;
@@ -1159,7 +1782,9 @@ __global__ void k_pack_float4(const float *__restrict__ src, int n, float4 *__re
         dst[i] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.f);
 }
 
-__global__ void k_finish_report(Scal *sc_base, size_t stride, int G, Ctx c, double *out) {
+__global__ void k_finish_report(Scal *sc_base, size_t stride, int G, Ctx c, double *out, const int *err) {
+    pdl_wait();
+    pdl_trigger();
     // out: e_total, e_dense, e_sparse, e_reg, then ints as doubles: gn_done, cg_done,
     // n_valid, n_degenerate, n_refined, finite
     if (threadIdx.x || blockIdx.x) return;
@@ -1184,6 +1809,7 @@ __global__ void k_finish_report(Scal *sc_base, size_t stride, int G, Ctx c, doub
     out[7] = last->n_degenerate;
     out[8] = nr;
     out[9] = isfinite(et) ? 1.0 : 0.0;
+    out[10] = *err ? 1.0 : 0.0;  // a grid barrier of the persistent position step gave up
 }
 
 }  // namespace vd

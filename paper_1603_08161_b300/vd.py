@@ -21,9 +21,9 @@ VD_PREC_FP32, VD_PREC_MIXED = 0, 1
 VD_MEM_HOST, VD_MEM_DEVICE = 0, 1
 VD_INIT_PREV, VD_INIT_ZERO = 0, 1
 (VD_KC_ASSOCIATE, VD_KC_RHS, VD_KC_APPLY_STENCIL, VD_KC_APPLY_SAMPLES, VD_KC_UPDATE_X,
- VD_KC_UPDATE_P, VD_KC_ROTATION, VD_KC_ENERGY) = range(8)
+ VD_KC_UPDATE_P, VD_KC_ROTATION, VD_KC_ENERGY, VD_KC_PCG) = range(9)
 KERNEL_CLASSES = {"associate": 0, "rhs": 1, "apply_stencil": 2, "apply_samples": 3, "update_x": 4,
-                  "update_p": 5, "rotation": 6, "energy": 7}
+                  "update_p": 5, "rotation": 6, "energy": 7, "pcg": 8}
 
 STATUS_NAMES = {0: "VD_OK", 1: "VD_ERR_INVALID_ARG", 2: "VD_ERR_OOM", 3: "VD_ERR_CUDA", 4: "VD_ERR_STATE",
                 5: "VD_ERR_NUMERIC", 6: "VD_ERR_TIMEOUT"}
