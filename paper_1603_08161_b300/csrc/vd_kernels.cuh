@@ -1550,7 +1550,7 @@ __device__ __forceinline__ float sym4_top_eigvec(float a[4][4], float q[4]) {
 #pragma unroll
         for (int s = 0; s < 4; s++) v[r][s] = r == s ? 1.f : 0.f;
 #pragma unroll 1
-    for (int sweep = 0; sweep < 10; sweep++) {
+    for (int sweep = 0; sweep < 8; sweep++) {
         float off = 0.f, dia = 0.f;
 #pragma unroll
         for (int r = 0; r < 4; r++) {
@@ -1558,7 +1558,7 @@ __device__ __forceinline__ float sym4_top_eigvec(float a[4][4], float q[4]) {
 #pragma unroll
             for (int s = r + 1; s < 4; s++) off += a[r][s] * a[r][s];
         }
-        if (off <= 1e-14f * dia || off == 0.f) break;
+        if (off <= 1e-12f * dia) break;  // off-diagonals ~1e-6 relative: FP32 cannot go much lower
 #pragma unroll
         for (int pp = 0; pp < 3; pp++)
 #pragma unroll
@@ -1589,27 +1589,52 @@ __device__ __forceinline__ float sym4_top_eigvec(float a[4][4], float q[4]) {
                 }
             }
     }
-    int best = 0;
-    float l1 = a[0][0];
+    // top eigenpair without dynamic register indexing
+    float l1 = a[0][0], l2 = -3.4e38f;
 #pragma unroll
-    for (int r = 1; r < 4; r++)
-        if (a[r][r] > l1) {
-            l1 = a[r][r];
-            best = r;
+    for (int r = 0; r < 4; r++) q[r] = v[r][0];
+#pragma unroll
+    for (int k = 1; k < 4; k++) {
+        const float lk = a[k][k];
+        if (lk > l1) {
+            l2 = l1;
+            l1 = lk;
+#pragma unroll
+            for (int r = 0; r < 4; r++) q[r] = v[r][k];
+        } else if (lk > l2) {
+            l2 = lk;
         }
-    float l2 = -3.4e38f;
-#pragma unroll
-    for (int r = 0; r < 4; r++)
-        if (r != best && a[r][r] > l2) l2 = a[r][r];
-#pragma unroll
-    for (int r = 0; r < 4; r++) q[r] = v[r][best];
+    }
     return l1 - l2;
+}
+
+// unit quaternion (w, x, y, z) of a rotation matrix (Shepperd 1978: divide by the
+// largest of the four diagonal combinations)
+__device__ __forceinline__ void mat_to_quat(const float R[9], float q[4]) {
+    const float tr = R[0] + R[4] + R[8];
+    if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
+        const float w = 0.5f * sqrtf(fmaxf(1.f + tr, 0.f)), s = 0.25f / w;
+        q[0] = w; q[1] = (R[7] - R[5]) * s; q[2] = (R[2] - R[6]) * s; q[3] = (R[3] - R[1]) * s;
+    } else if (R[0] >= R[4] && R[0] >= R[8]) {
+        const float x = 0.5f * sqrtf(fmaxf(1.f + R[0] - R[4] - R[8], 0.f)), s = 0.25f / x;
+        q[0] = (R[7] - R[5]) * s; q[1] = x; q[2] = (R[1] + R[3]) * s; q[3] = (R[2] + R[6]) * s;
+    } else if (R[4] >= R[8]) {
+        const float y = 0.5f * sqrtf(fmaxf(1.f + R[4] - R[0] - R[8], 0.f)), s = 0.25f / y;
+        q[0] = (R[2] - R[6]) * s; q[1] = (R[1] + R[3]) * s; q[2] = y; q[3] = (R[5] + R[7]) * s;
+    } else {
+        const float z = 0.5f * sqrtf(fmaxf(1.f + R[8] - R[0] - R[4], 0.f)), s = 0.25f / z;
+        q[0] = (R[3] - R[1]) * s; q[1] = (R[2] + R[6]) * s; q[2] = (R[5] + R[7]) * s; q[3] = z;
+    }
 }
 
 // Per node: A_i = sum_{j in N_i} (t_i - t_j)(t^_i - t^_j)^T (scaled by 1/h^2), and
 // R_i = argmax_R tr(R^T A_i) through the unit quaternion of Horn's 4x4 matrix
 // (Horn 1987, closed-form absolute orientation).  Nodes whose neighbours span fewer
 // than two axes, or whose top eigenvalue is (numerically) double, keep R_i.
+// Warm start: with the previous rotation R0 (orthonormal), argmax_R tr(R^T A) =
+// R0 argmax_D tr(D^T R0^T A), and Horn's matrix of R0^T A is nearly diagonal when the
+// rotation changed little, so the Jacobi sweeps converge at once; R = R0 D is formed
+// from the product of unit quaternions, which keeps it orthonormal.
 // Also accumulates E_reg (Eq. 4) with the new rotations (kFit = false: E_reg only).
 template <bool kAll, bool kFit>
 __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
@@ -1646,10 +1671,26 @@ __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
         const bool two_axes = __popc(axes) >= 2;
         bool keep = !two_axes;
         if (kFit && two_axes) {
-            // Horn's matrix from S = A^T (S_ab = sum_j e_a d_b)
-            const float Sxx = A[0][0], Sxy = A[1][0], Sxz = A[2][0];
-            const float Syx = A[0][1], Syy = A[1][1], Syz = A[2][1];
-            const float Szx = A[0][2], Szy = A[1][2], Szz = A[2][2];
+            // previous rotation usable as a warm start if orthonormal
+            float orth = 0.f;
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const float d = Ri[r] * Ri[k] + Ri[3 + r] * Ri[3 + k] + Ri[6 + r] * Ri[6 + k] - (r == k ? 1.f : 0.f);
+                    orth = fmaxf(orth, fabsf(d));
+                }
+            const bool warm = orth < 1e-3f;
+            float B[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    B[r][k] = warm ? Ri[r] * A[0][k] + Ri[3 + r] * A[1][k] + Ri[6 + r] * A[2][k] : A[r][k];
+            // Horn's matrix from S = B^T (S_ab = sum_j e_a d_b)
+            const float Sxx = B[0][0], Sxy = B[1][0], Sxz = B[2][0];
+            const float Syx = B[0][1], Syy = B[1][1], Syz = B[2][1];
+            const float Szx = B[0][2], Szy = B[1][2], Szz = B[2][2];
             float Nm[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
                               {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
                               {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
@@ -1664,7 +1705,19 @@ __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
             if (!(gap > 1e-5f * scale)) {
                 keep = true;
             } else {
-                const float w = qv[0], x = qv[1], y = qv[2], z = qv[3];
+                float w = qv[0], x = qv[1], y = qv[2], z = qv[3];
+                if (warm) {  // q = q(R0) * q(D)
+                    float q0[4];
+                    mat_to_quat(Ri, q0);
+                    const float w2 = q0[0] * w - q0[1] * x - q0[2] * y - q0[3] * z;
+                    const float x2 = q0[0] * x + q0[1] * w + q0[2] * z - q0[3] * y;
+                    const float y2 = q0[0] * y - q0[1] * z + q0[2] * w + q0[3] * x;
+                    const float z2 = q0[0] * z + q0[1] * y - q0[2] * x + q0[3] * w;
+                    w = w2;
+                    x = x2;
+                    y = y2;
+                    z = z2;
+                }
                 const float inv = 1.f / (w * w + x * x + y * y + z * z);
                 Ri[0] = (w * w + x * x - y * y - z * z) * inv;
                 Ri[1] = 2.f * (x * y - w * z) * inv;
