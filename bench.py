@@ -205,6 +205,7 @@ def main():
     ap.add_argument("--roofline-kernel", default="pcg", choices=ROOFLINE_KERNELS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision / surface / batched forms")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -229,17 +230,22 @@ def main():
     lat = vd.Lattice(fr.dims, fr.origin, fr.spacing, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step():
-        lat.set_correspondences(d_fh, d_ft)
-        lat.set_frame(d_depth, fr.K, fr.pose, d_pts, d_nrm)
-        lat.solve_async(prm)
+    def make_step(L):
+        def step_fn():
+            L.set_correspondences(d_fh, d_ft)
+            L.set_frame(d_depth, fr.K, fr.pose, d_pts, d_nrm)
+            L.solve_async(prm)
+        return step_fn
+
+    step = make_step(lat)
 
     for _ in range(args.warmup):
         step()
         rep = lat.report()
     per_solve, per_frame = lat.launch_counts(prm)
 
-    def timed_pass():
+    def timed_pass(step_fn=None, L=None):
+        step_fn, L = step_fn or step, L or lat
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         dist_barrier(world)
         torch.cuda.synchronize()
@@ -247,9 +253,9 @@ def main():
         for k in range(args.steps):
             flush.fill_(k & 0xff)
             ev[k][0].record(stream)
-            step()
+            step_fn()
             ev[k][1].record(stream)
-            lat.report()
+            L.report()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         dist_barrier(world)
@@ -281,6 +287,23 @@ def main():
     algo_bytes = algorithmic_bytes(rk, nn, fr.C, fr.S)
     peak, peak_kind = peaks()
     achieved = algo_bytes / avg_s / 1e9 if avg_s > 0 else None
+
+    # the same frame through the other forms of the solve (same steps, same timing)
+    variants = {}
+    if not args.no_variants:
+        for name, mode, prec in (("mixed_precision", vd.VD_ACTIVE_ALL, vd.VD_PREC_MIXED),
+                                 ("surface_active_set", vd.VD_ACTIVE_SURFACE, vd.VD_PREC_FP32)):
+            Lv = vd.Lattice(fr.dims, fr.origin, fr.spacing, mode, prec, stream=stream.cuda_stream)
+            sv = make_step(Lv)
+            for _ in range(args.warmup):
+                sv()
+                Lv.report()
+            msv, _ = timed_pass(sv, Lv)
+            rv = Lv.report()
+            mv = dist_max(statistics.mean(msv), world)
+            variants[name] = {"value": world * 1000.0 / mv, "unit": "frames/s", "ms_per_step": mv,
+                              "active_nodes": Lv.num_active(), "final_energy": rv["e_total"]}
+            Lv.close()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timing
     h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -333,6 +356,7 @@ def main():
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": (per_solve + per_frame) * args.steps,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
 

@@ -402,8 +402,10 @@ bool persistent_plan(vd_lattice *L, int *G, int *chunk) {
     if (!L->use_persistent || !L->coop) return false;
     const int N = L->all ? L->c.nn : L->n_active_h;
     const int N4 = 4 * ((std::max(N, 1) + 3) / 4);
+    // all SMs take part even for a small active set: the samples' share of each
+    // iteration is spread over the CTAs, and a barrier costs the same for any count
     int ch = (N4 + L->num_sms - 1) / L->num_sms;
-    ch = std::max(4 * ((ch + 3) / 4), 1024);
+    ch = std::max(4 * ((ch + 3) / 4), 4);
     if (ch > kPcgMaxChunk) return false;
     *chunk = ch;
     *G = (N4 + ch - 1) / ch;
@@ -624,7 +626,7 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
     *out = nullptr;
     if (d->nx < 2 || d->ny < 2 || d->nz < 2 || !(d->spacing > 0.f)) return VD_ERR_INVALID_ARG;
     if (d->active_mode != VD_ACTIVE_SURFACE && d->active_mode != VD_ACTIVE_ALL) return VD_ERR_INVALID_ARG;
-    if (d->precision != VD_PREC_FP32) return VD_ERR_INVALID_ARG;
+    if (d->precision != VD_PREC_FP32 && d->precision != VD_PREC_MIXED) return VD_ERR_INVALID_ARG;
     const long nn = (long)d->nx * d->ny * d->nz;
     if (nn > (long)kScanTile * kScanTile) return VD_ERR_INVALID_ARG;  // scan limit: 16.7M nodes
     vd_lattice *L = new (std::nothrow) vd_lattice();
@@ -642,6 +644,7 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
     for (int a = 0; a < 9; a++) c.Rg[a] = (a % 4 == 0) ? 1.f : 0.f;
     L->all = d->active_mode == VD_ACTIVE_ALL;
     L->precision = d->precision;
+    c.mixed = d->precision == VD_PREC_MIXED;
     if (const char *e = getenv("VD_PDL")) L->use_pdl = atoi(e) != 0;
     vd_status s = VD_OK;
     auto bail = [&](vd_status st) {
@@ -779,7 +782,7 @@ vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const fl
     TRY(upload(L, L->pts_in, src_pts, sizeof(float) * 3 * (size_t)n_src, mem));
     TRY(upload(L, L->nrm_in, src_nrm, sizeof(float) * 3 * (size_t)n_src, mem));
     dim3 b2(32, 8), g2((W + 31) / 32, (H + 7) / 8);
-    k_target_normals<<<g2, b2, 0, st>>>(L->depth, L->nrm, W, H, c.fx, c.fy, c.cx, c.cy);
+    k_target_normals<<<g2, b2, 0, st>>>(L->depth, L->nrm, W, H, c.fx, c.fy, c.cx, c.cy, c.mixed);
     // bin the samples by cell (counting sort with a deterministic order inside a cell)
     CK(cudaMemsetAsync(L->cnt, 0, sizeof(int) * (size_t)c.nn, st));
     CK(cudaMemsetAsync(L->head, 0, sizeof(int) * (size_t)L->cap_src, st));

@@ -12,6 +12,7 @@
 //   * FP64 scalars (PCG rho / p.Ap per iteration, energies) per iteration slot.
 // Every reduction sums in FP32 within a warp and in FP64 across warps and blocks.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,6 +48,7 @@ struct Ctx {
     const int *occ_cell, *occ_beg, *n_occ;
     float4 *rec;
     int *pix;
+    int mixed;  // VD_PREC_MIXED: target normals and per-sample records stored as BF16 x 4
     float *wc;
     // sparse pairs
     const float4 *fh, *ft, *sfrac;
@@ -210,6 +212,28 @@ __device__ __forceinline__ void st3(float *v, int ld, int i, float3 a) {
     v[2 * ld + i] = a.z;
 }
 
+// BF16 x 4 storage (8 bytes) of a float4, round to nearest even
+__device__ __forceinline__ uint2 pack_bf16x4(float4 v) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+}
+__device__ __forceinline__ float4 unpack_bf16x4(uint2 u) {
+    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+// per-sample association record (g', r0') and target normal, in the lattice's precision
+__device__ __forceinline__ float4 load_rec(const Ctx &c, int j) {
+    return c.mixed ? unpack_bf16x4(reinterpret_cast<const uint2 *>(c.rec)[j]) : c.rec[j];
+}
+__device__ __forceinline__ void store_rec(const Ctx &c, int j, float4 v) {
+    if (c.mixed) reinterpret_cast<uint2 *>(c.rec)[j] = pack_bf16x4(v);
+    else c.rec[j] = v;
+}
+__device__ __forceinline__ float4 load_nrm(const Ctx &c, size_t k) {
+    return c.mixed ? unpack_bf16x4(reinterpret_cast<const uint2 *>(c.nrm)[k]) : c.nrm[k];
+}
+
 // ------------------------------------------------------------------ frame kernels
 
 // Target normal of every pixel: cross product of the central differences of the
@@ -218,7 +242,7 @@ __device__ __forceinline__ void st3(float *v, int ld, int i, float3 a) {
 // The differences are rearranged so that no two ~1 m values are subtracted:
 //   x(u+1) - x(u-1) = [(D(u+1) - D(u-1)) (u - cx) + D(u+1) + D(u-1)] / fx.
 __global__ void k_target_normals(const float *__restrict__ D, float4 *__restrict__ nrm, int W, int H,
-                                 float fx, float fy, float cx, float cy) {
+                                 float fx, float fy, float cx, float cy, int mixed) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y * blockDim.y + threadIdx.y;
     if (u >= W || v >= H) return;
@@ -247,7 +271,8 @@ __global__ void k_target_normals(const float *__restrict__ D, float4 *__restrict
             }
         }
     }
-    nrm[(size_t)v * W + u] = out;
+    if (mixed) reinterpret_cast<uint2 *>(nrm)[(size_t)v * W + u] = pack_bf16x4(out);
+    else nrm[(size_t)v * W + u] = out;
 }
 
 // Cell of each point (lower-corner node, or -1 when the cell is not inside the
@@ -588,7 +613,7 @@ __device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, fl
     if (!(D > 0.f)) return near;
     V3<T> na;
     if (kF32) {
-        const float4 m = c.nrm[k];
+        const float4 m = load_nrm(c, k);
         if (m.w == 0.f) return near;
         na = {T(m.x), T(m.y), T(m.z)};
     } else {
@@ -604,7 +629,8 @@ __device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, fl
     const T cv = -dot(n, p) / pl;
     if (kF32) {
         if (fabsf((float)dist - c.eps_d) < 1e-5f) near = true;
-        if (fabsf((1.f - (float)cn) - c.eps_n) < 1e-4f) near = true;
+        // BF16 target normals carry up to ~4e-3 of rounding in n_c . n^a
+        if (fabsf((1.f - (float)cn) - c.eps_n) < (c.mixed ? 1e-2f : 1e-4f)) near = true;
         if (fabsf((1.f - (float)cv) - c.eps_v) < 1e-4f) near = true;
     }
     pix = (int)k;
@@ -645,7 +671,7 @@ __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
         }
         c.pix[i] = pix;
         c.wc[i] = w;
-        c.rec[i] = rec;
+        store_rec(c, i, rec);
         valid += w > 0.f;
     }
     block_add_int(valid, &sc->n_valid);
@@ -709,7 +735,7 @@ __device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, flo
             const int j = j0 + lt;
             if (j < se) {
                 const int cl = c.cell[j];
-                const float4 f4 = c.frac[j], g = c.rec[j];
+                const float4 f4 = c.frac[j], g = load_rec(c, j);
                 const float f[3] = {f4.x, f4.y, f4.z};
                 float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
@@ -738,7 +764,7 @@ __device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, flo
             if (has) {
                 const int lo = max(ibeg, j0), hi = min(iend, j0 + nt);
                 for (int jj = lo; jj < hi; jj++) {
-                    const float4 f4 = c.frac[jj], g = c.rec[jj];
+                    const float4 f4 = c.frac[jj], g = load_rec(c, jj);
                     const float f[3] = {f4.x, f4.y, f4.z};
                     const float al = trilinear_weight(f, k);
                     const float t = al * tsm[jj - j0];
@@ -1543,59 +1569,61 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
 
 // Largest-eigenvalue eigenvector of a symmetric 4x4 matrix by cyclic Jacobi
 // rotations (Golub & Van Loan, Sec. 8.5); returns lambda_1 - lambda_2.
-__device__ __forceinline__ float sym4_top_eigvec(float a[4][4], float q[4]) {
-    float v[4][4];
+template <typename T>
+__device__ __forceinline__ T sym4_top_eigvec(T a[4][4], T q[4]) {
+    const T one = T(1), zero = T(0);
+    T v[4][4];
 #pragma unroll
     for (int r = 0; r < 4; r++)
 #pragma unroll
-        for (int s = 0; s < 4; s++) v[r][s] = r == s ? 1.f : 0.f;
+        for (int s = 0; s < 4; s++) v[r][s] = r == s ? one : zero;
 #pragma unroll 1
     for (int sweep = 0; sweep < 8; sweep++) {
-        float off = 0.f, dia = 0.f;
+        T off = zero, dia = zero;
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             dia += a[r][r] * a[r][r];
 #pragma unroll
             for (int s = r + 1; s < 4; s++) off += a[r][s] * a[r][s];
         }
-        if (off <= 1e-12f * dia) break;  // off-diagonals ~1e-6 relative: FP32 cannot go much lower
+        if (off <= (sizeof(T) == 4 ? T(1e-12) : T(1e-28)) * dia) break;  // near the rounding floor
 #pragma unroll
         for (int pp = 0; pp < 3; pp++)
 #pragma unroll
             for (int qq = pp + 1; qq < 4; qq++) {
-                const float apq = a[pp][qq];
-                if (apq == 0.f) continue;
-                const float th = (a[qq][qq] - a[pp][pp]) / (2.f * apq);
-                const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
-                const float cs = 1.f / sqrtf(fmaf(t, t, 1.f)), sn = t * cs;
+                const T apq = a[pp][qq];
+                if (apq == zero) continue;
+                const T th = (a[qq][qq] - a[pp][pp]) / (T(2) * apq);
+                const T t = (th >= zero ? one : -one) / (fabs(th) + sqrt(th * th + one));
+                const T cs = one / sqrt(t * t + one), sn = t * cs;
                 // A <- J^T A J with J the rotation in the (pp, qq) plane
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    const float akp = a[k][pp], akq = a[k][qq];
+                    const T akp = a[k][pp], akq = a[k][qq];
                     a[k][pp] = cs * akp - sn * akq;
                     a[k][qq] = sn * akp + cs * akq;
                 }
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    const float apk = a[pp][k], aqk = a[qq][k];
+                    const T apk = a[pp][k], aqk = a[qq][k];
                     a[pp][k] = cs * apk - sn * aqk;
                     a[qq][k] = sn * apk + cs * aqk;
                 }
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    const float vkp = v[k][pp], vkq = v[k][qq];
+                    const T vkp = v[k][pp], vkq = v[k][qq];
                     v[k][pp] = cs * vkp - sn * vkq;
                     v[k][qq] = sn * vkp + cs * vkq;
                 }
             }
     }
     // top eigenpair without dynamic register indexing
-    float l1 = a[0][0], l2 = -3.4e38f;
+    T l1 = a[0][0], l2 = T(-3.4e38);
 #pragma unroll
     for (int r = 0; r < 4; r++) q[r] = v[r][0];
 #pragma unroll
     for (int k = 1; k < 4; k++) {
-        const float lk = a[k][k];
+        const T lk = a[k][k];
         if (lk > l1) {
             l2 = l1;
             l1 = lk;
@@ -1701,8 +1729,22 @@ __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
 #pragma unroll
                 for (int k = 0; k < 4; k++) scale = fmaxf(scale, fabsf(Nm[r][k]));
             float qv[4];
-            const float gap = sym4_top_eigvec(Nm, qv);
-            if (!(gap > 1e-5f * scale)) {
+            const float gap = sym4_top_eigvec<float>(Nm, qv);
+            bool unique = gap > 1e-5f * scale;
+            if (gap < 1e-4f * scale) {
+                // near-singular block (the rotation's sensitivity exceeds 1e4): polar
+                // decomposition again in FP64
+                double Nd[4][4] = {{(double)Sxx + Syy + Szz, (double)Syz - Szy, (double)Szx - Sxz, (double)Sxy - Syx},
+                                   {(double)Syz - Szy, (double)Sxx - Syy - Szz, (double)Sxy + Syx, (double)Szx + Sxz},
+                                   {(double)Szx - Sxz, (double)Sxy + Syx, -(double)Sxx + Syy - Szz, (double)Syz + Szy},
+                                   {(double)Sxy - Syx, (double)Szx + Sxz, (double)Syz + Szy, -(double)Sxx - Syy + Szz}};
+                double qd[4];
+                const double gd = sym4_top_eigvec<double>(Nd, qd);
+                unique = gd > 1e-12 * (double)scale;
+#pragma unroll
+                for (int r = 0; r < 4; r++) qv[r] = (float)qd[r];
+            }
+            if (!unique) {
                 keep = true;
             } else {
                 float w = qv[0], x = qv[1], y = qv[2], z = qv[3];
@@ -1812,7 +1854,7 @@ __global__ void k_unsort_association(Ctx c, int *__restrict__ pix, float *__rest
         pix[o] = c.pix[i];
         w[o] = c.wc[i];
         float res = 0.f;
-        const float4 g = c.rec[i];
+        const float4 g = load_rec(c, i);
         if (c.wc[i] > 0.f) {
             const float4 f4 = c.frac[i];
             const float f[3] = {f4.x, f4.y, f4.z};

@@ -230,15 +230,78 @@ def test_solve_parity_config2_surface(vd, cfg2):
     assert abs(rep["e_total"] - res["energy"][-1, 0]) / res["energy"][-1, 0] <= 1e-5
 
 
+_CFG2_ORACLE = {}
+
+
+def _cfg2_oracle(cfg2):
+    """The FP64 oracle's fixed-association 10 x 20 solve of the 96^3 frame (cached)."""
+    if "res" not in _CFG2_ORACLE:
+        ref = oracle.Oracle.from_frame(cfg2, oracle.ACTIVE_ALL)
+        res = ref.solve(10, 20, fixed_association=True)
+        u0, R0 = ref.get_warp()
+        _CFG2_ORACLE.update(res=res, u0=u0)
+    return _CFG2_ORACLE["res"], _CFG2_ORACLE["u0"]
+
+
 @pytest.mark.slow
 def test_solve_parity_config2_all(vd, cfg2):
     """96^3 lattice, 640x480 depth, 10 x 20 schedule: the benchmark's workload."""
-    lat, ref, rep, res, u, u0, R, R0 = _solve_pair(vd, cfg2, "all", 10, 20)
+    res, u0 = _cfg2_oracle(cfg2)
+    lat = vd.Lattice(cfg2.dims, cfg2.origin, cfg2.spacing, vd.VD_ACTIVE_ALL)
+    lat.set_frame_from(cfg2)
+    rep = lat.solve(vd.params(gn_iters=10, cg_iters=20, fixed_association=True, init=vd.VD_INIT_ZERO))
+    u, _ = lat.get_warp()
     err = float(np.abs(u - u0).max())
     rel = abs(rep["e_total"] - res["energy"][-1, 0]) / res["energy"][-1, 0]
-    print(f"config 2 all-nodes: |du|max = {err:.3e} m (tol {1e-4 * cfg2.spacing:.3e}), dE/E = {rel:.3e}")
+    print(f"config 2 all-nodes FP32: |du|max = {err:.3e} m (tol {1e-4 * cfg2.spacing:.3e}), dE/E = {rel:.3e}")
     assert err <= 1e-4 * cfg2.spacing
     assert rel <= 1e-5
+
+
+# ------------------------------------------------------------------ precision variant
+
+def _mixed_vs_oracle(vd, fr, mode, gn, cg, res=None, u0=None):
+    lat = vd.Lattice(fr.dims, fr.origin, fr.spacing,
+                     vd.VD_ACTIVE_ALL if mode == "all" else vd.VD_ACTIVE_SURFACE, vd.VD_PREC_MIXED)
+    lat.set_frame_from(fr)
+    prm = vd.params(gn_iters=gn, cg_iters=cg, fixed_association=True, init=vd.VD_INIT_ZERO)
+    if res is None:
+        ref = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL if mode == "all" else oracle.ACTIVE_SURFACE)
+        ref.associate()
+        pix0, _, _ = ref.association()
+        lat.associate(prm)
+        pix, _, _ = lat.association(prm)
+        assert (pix == pix0).all()          # decisions are still taken in FP64 near thresholds
+        res = ref.solve(gn, cg, fixed_association=True)
+        u0, _ = ref.get_warp()
+    rep = lat.solve(prm)
+    u, _ = lat.get_warp()
+    err = float(np.abs(u - u0).max())
+    rel = abs(rep["e_total"] - res["energy"][-1, 0]) / res["energy"][-1, 0]
+    return err, rel, rep, res
+
+
+@pytest.mark.parametrize("mode", ["all", "surface"])
+def test_precision_variant_config1(vd, mode):
+    """BF16 storage of target normals and per-sample records, FP32 stencil and
+    accumulation: the error against the FP64 oracle is stated and bounded."""
+    fr = FRAMES["cfg1"]
+    err, rel, rep, res = _mixed_vs_oracle(vd, fr, mode, 5, 10)
+    print(f"mixed precision, config 1 {mode}: |du|max = {err:.3e} m = {err / fr.spacing:.2e} h, dE/E = {rel:.3e}")
+    assert rep["n_valid_corr"] == res["n_valid"]
+    assert err <= 1e-2 * fr.spacing
+    assert rel <= 1e-2
+    assert err > 0.0                      # the BF16 records are really used
+
+
+@pytest.mark.slow
+def test_precision_variant_config2(vd, cfg2):
+    res, u0 = _cfg2_oracle(cfg2)
+    err, rel, rep, _ = _mixed_vs_oracle(vd, cfg2, "all", 10, 20, res=res, u0=u0)
+    print(f"mixed precision, config 2 all-nodes: |du|max = {err:.3e} m = {err / cfg2.spacing:.2e} h, dE/E = {rel:.3e}")
+    assert rep["n_valid_corr"] == res["n_valid"]
+    assert err <= 1e-2 * cfg2.spacing
+    assert rel <= 1e-2
 
 
 # ------------------------------------------------------------------ edge cases
