@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision / surface / batched forms")
+    ap.add_argument("--batch", type=int, default=32, help="lattices in the batched form (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -304,6 +305,54 @@ def main():
             variants[name] = {"value": world * 1000.0 / mv, "unit": "frames/s", "ms_per_step": mv,
                               "active_nodes": Lv.num_active(), "final_energy": rv["e_total"]}
             Lv.close()
+
+    # batched form (32 independent lattices of uneven size, 16^3..96^3, their own
+    # 160x120..640x480 frames): one tuned graph launch per batch, against the same
+    # lattices solved one after another with vd_solve; frames are set before timing
+    if not args.no_variants and args.batch > 0:
+        bframes = synth.batch_frames(args.batch, workers=8)
+        blats = []
+        for bf in bframes:
+            Lb = vd.Lattice(bf.dims, bf.origin, bf.spacing, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
+            Lb.set_frame_from(bf)
+            blats.append(Lb)
+        B = vd.Batch(blats)
+        B.solve(prm)
+        n_streams, _ = B.tune(prm)
+
+        def batch_step():
+            B.solve_async(prm)
+
+        class _BR:
+            def report(self):
+                B.reports()
+
+        def seq_step():
+            for Lb in blats:
+                Lb.solve_async(prm)
+
+        class _SR:
+            def report(self):
+                for Lb in blats:
+                    Lb.report()
+        for _ in range(args.warmup):
+            batch_step()
+            _BR().report()
+            seq_step()
+            _SR().report()
+        msb, _ = timed_pass(batch_step, _BR())
+        mss, _ = timed_pass(seq_step, _SR())
+        tb = dist_max(statistics.mean(msb), world)
+        ts = dist_max(statistics.mean(mss), world)
+        variants["batched"] = {
+            "value": world * len(blats) * 1000.0 / tb, "unit": "solves/s", "ms_per_batch": tb,
+            "lattices": len(blats), "total_nodes": int(sum(int(np.prod(b.dims)) for b in bframes)),
+            "branches": n_streams, "launches_per_batch": B.launch_count(),
+            "sequential_plain": {"value": world * len(blats) * 1000.0 / ts, "unit": "solves/s", "ms": ts},
+            "speedup_vs_plain": ts / tb}
+        B.close()
+        for Lb in blats:
+            Lb.close()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timing
     h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()

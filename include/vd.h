@@ -194,6 +194,43 @@ vd_status vd_profile_read(vd_lattice *lat, double *total_ms, int *launches);
 vd_status vd_launch_counts(vd_lattice *lat, const vd_solve_params *params, int *per_solve,
                            int *per_frame);
 
+/* ---- batched solve: many independent lattices in one graph launch ---- */
+
+typedef struct vd_batch vd_batch; /* opaque; references the lattices, owns no lattice data */
+
+/* Group `count` lattices (each with its frame and correspondences set, all on the
+ * current device) for batched solves.  The lattices must outlive the batch. */
+vd_status vd_batch_create(vd_lattice *const *lattices, int count, vd_batch **out);
+
+/* Free the batch (not the lattices).  NULL is accepted. */
+vd_status vd_batch_destroy(vd_batch *batch);
+
+/* Solve every lattice of the batch with the same parameters (the flip-flop of Sec. 7.1
+ * per lattice, exactly as vd_solve): one captured CUDA graph in which each lattice's
+ * schedule is a branch on one of several streams, launched on the first lattice's
+ * stream.  `out` (may be NULL) receives `count` reports.  Synchronous. */
+vd_status vd_batch_solve(vd_batch *batch, const vd_solve_params *params, vd_solve_report *out);
+
+/* Enqueue the batched solve and return; vd_batch_get_reports waits for it. */
+vd_status vd_batch_solve_async(vd_batch *batch, const vd_solve_params *params);
+vd_status vd_batch_get_reports(vd_batch *batch, vd_solve_report *out);
+
+/* Autotune the batch for these parameters: time the solve for each candidate number
+ * of concurrent branches (1, 2, 4, ... up to the batch size) and branch order (largest
+ * lattice first, or as given), keep the fastest.  Runs the solve several times (the
+ * lattices' warps change).  Reports the choice and its time per batched solve (ms). */
+vd_status vd_batch_tune(vd_batch *batch, const vd_solve_params *params, int *streams, float *ms);
+
+/* Kernel launches in one batched solve (after the first solve or tune). */
+vd_status vd_batch_launch_count(const vd_batch *batch, int *launches);
+
+/* One-line description of the batch's last error. */
+const char *vd_batch_last_error(const vd_batch *batch);
+
+/* Convenience: create a batch, solve once, destroy it (re-captures every call). */
+vd_status vd_solve_batch(vd_lattice *const *lattices, int count, const vd_solve_params *params,
+                         vd_solve_report *out);
+
 /* ---- allocation-free variant ----
  *
  * The paper has no counterpart to this entry point; it exists for callers that cannot

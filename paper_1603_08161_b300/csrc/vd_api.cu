@@ -105,6 +105,7 @@ struct vd_lattice {
     int num_sms = 148;
     bool coop = false;               // device supports cooperative launches
     bool use_persistent = true;      // may be cleared if the graph cannot hold the launch
+    bool in_batch = false;           // being captured into a batch graph: streamed PCG
 };
 
 namespace {
@@ -399,7 +400,7 @@ constexpr int kPcgMaxChunk = 6272;  // 9 floats per slot in shared memory: 225,7
 // Whether the position step runs as one persistent cooperative kernel, with how many
 // CTAs and how many slots per CTA.
 bool persistent_plan(vd_lattice *L, int *G, int *chunk) {
-    if (!L->use_persistent || !L->coop) return false;
+    if (!L->use_persistent || !L->coop || L->in_batch) return false;
     const int N = L->all ? L->c.nn : L->n_active_h;
     const int N4 = 4 * ((std::max(N, 1) + 3) / 4);
     // all SMs take part even for a small active set: the samples' share of each
@@ -1120,6 +1121,249 @@ vd_status vd_launch_counts(vd_lattice *L, const vd_solve_params *P, int *per_sol
     if (per_solve) *per_solve = n;
     if (per_frame) *per_frame = L->launches_frame;
     return VD_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batched solve
+//
+// A batch captures the solve schedules of many lattices into one CUDA graph: each
+// lattice's schedule is a branch on one of P capture streams, so the small lattices'
+// kernels run concurrently with the large ones'.  The position steps are streamed
+// (several cooperative persistent kernels cannot be co-resident at once).  vd_batch_tune
+// times candidate stream counts and branch orders on the batch itself and keeps the
+// fastest.
+
+struct vd_batch {
+    std::vector<vd_lattice *> L;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<char> key;
+    vd_solve_params gparams{};
+    int streams = 0;           // concurrent branches (0: not tuned, use min(count, 8))
+    bool largest_first = true;
+    bool pending = false;
+    int launches = 0;
+    std::string err;
+};
+
+namespace {
+
+vd_status bfail(vd_batch *B, vd_status s, const char *msg) {
+    B->err = msg;
+    return s;
+}
+
+std::vector<char> batch_key(vd_batch *B, const vd_solve_params *P, int streams, bool largest) {
+    std::vector<char> k;
+    auto put = [&](const void *p, size_t n) { k.insert(k.end(), (const char *)p, (const char *)p + n); };
+    put(P, sizeof(*P));
+    put(&streams, sizeof(streams));
+    put(&largest, sizeof(largest));
+    for (vd_lattice *L : B->L) {
+        put(&L->gen, sizeof(L->gen));
+        put(&L->c, sizeof(Ctx));
+        const Grid g = grids(L);
+        put(&g, sizeof(g));
+    }
+    return k;
+}
+
+std::vector<int> batch_order(vd_batch *B, bool largest) {
+    std::vector<int> o(B->L.size());
+    for (size_t i = 0; i < o.size(); i++) o[i] = (int)i;
+    if (largest) {
+        std::stable_sort(o.begin(), o.end(), [&](int a, int b) {
+            const long na = B->L[a]->all ? B->L[a]->c.nn : B->L[a]->n_active_h;
+            const long nb = B->L[b]->all ? B->L[b]->c.nn : B->L[b]->n_active_h;
+            return na > nb;
+        });
+    }
+    return o;
+}
+
+vd_status batch_build(vd_batch *B, const vd_solve_params *P, int streams, bool largest) {
+    std::vector<char> key = batch_key(B, P, streams, largest);
+    if (B->gexec && key == B->key) return VD_OK;
+    if (B->gexec) {
+        cudaGraphExecDestroy(B->gexec);
+        B->gexec = nullptr;
+    }
+    while ((int)B->side.size() < streams) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "stream");
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "event");
+        B->side.push_back(st);
+        B->join.push_back(ev);
+    }
+    for (vd_lattice *L : B->L) {
+        vd_status s = ensure_scal(L, P->gn_iters, P->cg_iters);
+        if (s != VD_OK) return bfail(B, s, L->err.c_str());
+        set_params_ctx(L->c, P);
+        refresh_ctx(L);
+    }
+    const std::vector<int> order = batch_order(B, largest);
+    if (cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bfail(B, VD_ERR_CUDA, "begin capture");
+    cudaEventRecord(B->fork, B->cap);
+    for (int p = 0; p < streams; p++) cudaStreamWaitEvent(B->side[p], B->fork, 0);
+    int launches = 0;
+    for (size_t k = 0; k < order.size(); k++) {
+        vd_lattice *L = B->L[order[k]];
+        const int saved = L->prof_class;
+        L->prof_class = -1;
+        L->in_batch = true;
+        L->counting = 0;
+        enqueue_solve(L, P, B->side[k % streams]);
+        launches += L->counting;
+        L->in_batch = false;
+        L->prof_class = saved;
+    }
+    for (int p = 0; p < streams; p++) {
+        cudaEventRecord(B->join[p], B->side[p]);
+        cudaStreamWaitEvent(B->cap, B->join[p], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&B->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(B, VD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    B->key = key;
+    B->gparams = *P;
+    B->launches = launches;
+    return VD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vd_status vd_batch_create(vd_lattice *const *ls, int count, vd_batch **out) {
+    if (!ls || !out || count < 1) return VD_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < count; i++)
+        if (!ls[i]) return VD_ERR_INVALID_ARG;
+    vd_batch *B = new (std::nothrow) vd_batch();
+    if (!B) return VD_ERR_OOM;
+    B->L.assign(ls, ls + count);
+    if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&B->t0) != cudaSuccess || cudaEventCreate(&B->t1) != cudaSuccess) {
+        vd_batch_destroy(B);
+        return VD_ERR_CUDA;
+    }
+    *out = B;
+    return VD_OK;
+}
+
+vd_status vd_batch_destroy(vd_batch *B) {
+    if (!B) return VD_OK;
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    for (auto st : B->side) cudaStreamDestroy(st);
+    for (auto ev : B->join) cudaEventDestroy(ev);
+    if (B->fork) cudaEventDestroy(B->fork);
+    if (B->t0) cudaEventDestroy(B->t0);
+    if (B->t1) cudaEventDestroy(B->t1);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    delete B;
+    return VD_OK;
+}
+
+const char *vd_batch_last_error(const vd_batch *B) { return B ? B->err.c_str() : "null batch"; }
+
+vd_status vd_batch_solve_async(vd_batch *B, const vd_solve_params *P) {
+    if (!B) return VD_ERR_INVALID_ARG;
+    for (vd_lattice *L : B->L) {
+        vd_status s = check_params(L, P);
+        if (s != VD_OK) return bfail(B, s, L->err.c_str());
+        if (!L->have_frame) return bfail(B, VD_ERR_STATE, "a lattice of the batch has no frame");
+    }
+    const int streams = B->streams > 0 ? B->streams : std::min<int>((int)B->L.size(), 8);
+    vd_status s = batch_build(B, P, streams, B->largest_first);
+    if (s != VD_OK) return s;
+    cudaStream_t main = B->L[0]->stream;
+    if (cudaGraphLaunch(B->gexec, main) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "graph launch");
+    B->pending = true;
+    return VD_OK;
+}
+
+vd_status vd_batch_get_reports(vd_batch *B, vd_solve_report *out) {
+    if (!B) return VD_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(B->L[0]->stream) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "synchronize");
+    B->pending = false;
+    vd_status worst = VD_OK;
+    for (size_t i = 0; i < B->L.size(); i++) {
+        vd_status s = read_report(B->L[i], out ? out + i : nullptr);
+        if (s != VD_OK && worst == VD_OK) worst = s;
+    }
+    return worst;
+}
+
+vd_status vd_batch_solve(vd_batch *B, const vd_solve_params *P, vd_solve_report *out) {
+    vd_status s = vd_batch_solve_async(B, P);
+    if (s != VD_OK) return s;
+    return vd_batch_get_reports(B, out);
+}
+
+vd_status vd_batch_tune(vd_batch *B, const vd_solve_params *P, int *streams_out, float *ms_out) {
+    if (!B) return VD_ERR_INVALID_ARG;
+    const int n = (int)B->L.size();
+    const int cand[] = {1, 2, 4, 8, 16, 32, 64};
+    float best = 3.4e38f;
+    int best_s = 1;
+    bool best_l = true;
+    cudaStream_t main = B->L[0]->stream;
+    for (int lf = 1; lf >= 0; lf--)
+        for (int ci = 0; ci < 7; ci++) {
+            const int st = cand[ci];
+            if (st > n && st != cand[0]) break;
+            vd_status s = batch_build(B, P, st, lf != 0);
+            if (s != VD_OK) return s;
+            float ms = 0.f;
+            for (int rep = 0; rep < 3; rep++) {  // first replay warms the caches
+                cudaEventRecord(B->t0, main);
+                if (cudaGraphLaunch(B->gexec, main) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "graph launch");
+                cudaEventRecord(B->t1, main);
+                if (cudaEventSynchronize(B->t1) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "synchronize");
+                float m = 0.f;
+                cudaEventElapsedTime(&m, B->t0, B->t1);
+                if (rep > 0) ms += m;
+            }
+            if (ms < best) {
+                best = ms;
+                best_s = st;
+                best_l = lf != 0;
+            }
+        }
+    B->streams = best_s;
+    B->largest_first = best_l;
+    if (streams_out) *streams_out = best_s;
+    if (ms_out) *ms_out = best / 2.f;
+    return VD_OK;
+}
+
+vd_status vd_batch_launch_count(const vd_batch *B, int *launches) {
+    if (!B || !launches) return VD_ERR_INVALID_ARG;
+    *launches = B->launches;
+    return VD_OK;
+}
+
+vd_status vd_solve_batch(vd_lattice *const *ls, int count, const vd_solve_params *P, vd_solve_report *out) {
+    vd_batch *B = nullptr;
+    vd_status s = vd_batch_create(ls, count, &B);
+    if (s != VD_OK) return s;
+    s = vd_batch_solve(B, P, out);
+    vd_batch_destroy(B);
+    return s;
 }
 
 }  // extern "C"

@@ -116,9 +116,10 @@ def _march(phi, dirs, z0, z1, step, iters_bisect=48):
     return z, hit
 
 
-def _sphere_trace(sdf, dirs, z0, z1, iters=160, eps=2e-6, iters_bisect=40):
+def _sphere_trace(sdf, dirs, z0, z1, iters=160, eps=2e-6, iters_bisect=40, step=1.0):
     """First surface hit of a signed distance function along each ray (sphere tracing,
-    then bisection of the last bracket to well below 1e-7 m); 0 where no hit."""
+    then bisection of the last bracket to well below 1e-7 m); 0 where no hit.  ``step``
+    < 1 scales the steps for a function that over-estimates the distance by up to 1/step."""
     n = dirs.shape[0]
     L = np.linalg.norm(dirs, axis=1)
     z = np.full(n, float(z0))
@@ -131,7 +132,7 @@ def _sphere_trace(sdf, dirs, z0, z1, iters=160, eps=2e-6, iters_bisect=40):
         d = sdf(z[idx, None] * dirs[idx])
         done = d < eps
         conv[idx[done]] = True
-        z[idx[~done]] += d[~done] / L[idx[~done]]
+        z[idx[~done]] += step * d[~done] / L[idx[~done]]
         live[idx] = ~done
         live &= z < z1
     idx = np.nonzero(conv)[0]
@@ -183,7 +184,7 @@ def _sine_field(centre, amp, wavelength):
 
 def sphere_frame(W=64, H=48, f=60.0, n=16, radius=0.3, centre=(0.0, 0.0, 1.0),
                  amp=0.02, wavelength=0.5, noise=1e-3, n_sparse=20, sparse_noise=1e-3,
-                 invalid_frac=0.0, seed=0, name="sphere"):
+                 invalid_frac=0.0, seed=0, name="sphere", tracer="march"):
     """A sphere bent by d(x) = A sin(...) and seen by a W x H pinhole camera.
 
     The observed surface is {y : |x(y) - c| = r} with x(y) the preimage of y under
@@ -201,7 +202,11 @@ def sphere_frame(W=64, H=48, f=60.0, n=16, radius=0.3, centre=(0.0, 0.0, 1.0),
             x = y - disp(x)
         return np.linalg.norm(x - c, axis=-1) - radius
 
-    z, hit = _march(phi_deformed, dirs, c[2] - radius - 0.1, c[2] + radius + 0.1, 2.5e-3)
+    if tracer == "march":
+        z, hit = _march(phi_deformed, dirs, c[2] - radius - 0.1, c[2] + radius + 0.1, 2.5e-3)
+    else:  # the warp's gradient is at most 2 pi A / wavelength, so 0.75 steps never overshoot
+        z, hit = _sphere_trace(phi_deformed, dirs, c[2] - radius - 0.1, c[2] + radius + 0.1, iters=400,
+                               step=0.75)
     z = z + rng.normal(0.0, noise, z.shape) * hit
     if invalid_frac > 0:
         z[rng.random(z.shape) < invalid_frac] = 0.0
@@ -368,11 +373,20 @@ def config2(seed=0):
     return capsule_frame(W=640, H=480, f=525.0, n=96, seed=seed, name="capsules96")
 
 
-def batch_frames(count=32, base_seed=4):
+def batch_frames(count=32, base_seed=4, workers=1):
     """Lattices of uneven size: n ~ round(exp(U(ln 16, ln 96))), image 160s x 120s with
-    s ~ logU(1, 4), sphere or capsules with probability 1/2, S ~ U{20..300}."""
+    s ~ logU(1, 4), sphere or capsules with probability 1/2, S ~ U{20..300}.
+    ``workers`` > 1 renders the frames in a spawned process pool (same results)."""
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, count)) as pool:
+            return pool.starmap(_batch_frame, [(k, base_seed) for k in range(count)])
+    return [_batch_frame(k, base_seed) for k in range(count)]
+
+
+def _batch_frame(k, base_seed):
     out = []
-    for k in range(count):
+    for k in [k]:
         rng = np.random.default_rng([base_seed, k])
         n = int(round(math.exp(rng.uniform(math.log(16), math.log(96)))))
         s = math.exp(rng.uniform(0.0, math.log(4.0)))
@@ -382,12 +396,12 @@ def batch_frames(count=32, base_seed=4):
         sub = int(rng.integers(0, 2**31 - 1))
         if rng.random() < 0.5:
             fr = sphere_frame(W=W, H=H, f=f, n=n, seed=sub, n_sparse=S, noise=2e-3,
-                              name=f"batch{k}-sphere{n}")
+                              name=f"batch{k}-sphere{n}", tracer="sphere")
         else:
             fr = capsule_frame(W=W, H=H, f=f, n=n, seed=sub, n_sparse=S,
                                name=f"batch{k}-capsules{n}")
         out.append(fr)
-    return out
+    return out[0]
 
 
 def sequence_frames(seed, frames=64, n=96, W=640, H=480, f=525.0, max_step_deg=5.0):

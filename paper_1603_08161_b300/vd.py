@@ -87,12 +87,21 @@ _SIGS = {
     "vd_profile_read": [_P, _PD, _PI],
     "vd_launch_counts": [_P, ctypes.POINTER(vd_solve_params), _PI, _PI],
     "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
+    "vd_batch_create": [_P, _I, ctypes.POINTER(_P)],
+    "vd_batch_destroy": [_P],
+    "vd_batch_solve": [_P, ctypes.POINTER(vd_solve_params), _P],
+    "vd_batch_solve_async": [_P, ctypes.POINTER(vd_solve_params)],
+    "vd_batch_get_reports": [_P, _P],
+    "vd_batch_tune": [_P, ctypes.POINTER(vd_solve_params), _PI, ctypes.POINTER(ctypes.c_float)],
+    "vd_batch_launch_count": [_P, _PI],
+    "vd_batch_last_error": [_P],
+    "vd_solve_batch": [_P, _I, ctypes.POINTER(vd_solve_params), _P],
 }
 VD_NOALLOC_MAX_NODES = 65536
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
-    _fn.restype = ctypes.c_char_p if _name == "vd_last_error" else ctypes.c_int
+    _fn.restype = ctypes.c_char_p if _name in ("vd_last_error", "vd_batch_last_error") else ctypes.c_int
     globals()[_name] = _fn
 
 
@@ -292,3 +301,57 @@ class Lattice:
         b = ctypes.c_int()
         self._check(vd_launch_counts(self.h, ctypes.byref(prm), ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+
+class Batch:
+    """Several lattices solved by one captured graph (vd_batch_*)."""
+
+    def __init__(self, lattices):
+        self.lattices = list(lattices)
+        arr = (_P * len(self.lattices))(*[lt.h for lt in self.lattices])
+        h = _P()
+        st = vd_batch_create(arr, len(self.lattices), ctypes.byref(h))
+        if st != VD_OK:
+            raise VDError(st, "vd_batch_create failed")
+        self.h = h
+
+    def _check(self, st):
+        if st != VD_OK:
+            raise VDError(st, (vd_batch_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            vd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, prm):
+        reps = (vd_solve_report * len(self.lattices))()
+        st = vd_batch_solve(self.h, ctypes.byref(prm), reps)
+        if st not in (VD_OK, VD_ERR_NUMERIC):
+            self._check(st)
+        return [r.as_dict() for r in reps]
+
+    def solve_async(self, prm):
+        self._check(vd_batch_solve_async(self.h, ctypes.byref(prm)))
+
+    def reports(self):
+        reps = (vd_solve_report * len(self.lattices))()
+        vd_batch_get_reports(self.h, reps)
+        return [r.as_dict() for r in reps]
+
+    def tune(self, prm):
+        n = ctypes.c_int()
+        ms = ctypes.c_float()
+        self._check(vd_batch_tune(self.h, ctypes.byref(prm), ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def launch_count(self):
+        n = ctypes.c_int()
+        self._check(vd_batch_launch_count(self.h, ctypes.byref(n)))
+        return n.value
