@@ -263,6 +263,75 @@ vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spacing, const 
                                    const float *rot_in, float *rot_out, double *e_reg,
                                    int *n_degenerate, void *cuda_stream);
 
+/* ---- Gauss-Newton early stop ----
+ *
+ * With a target set, every later solve of this lattice ends its flip-flop loop after
+ * the first iteration whose E_total (Eq. 1) is <= e_target; the report's gn_done counts
+ * the iterations run.  A negative (or NaN) e_target removes the target.  The value is
+ * stored on the device in stream order, so it may change between queued solves without
+ * a new graph capture (setting or removing the target re-captures once). */
+vd_status vd_set_energy_target(vd_lattice *lat, double e_target);
+
+/* ---- learned warm start (the paper has no counterpart: Sec. 7.1 starts each frame from
+ * the previous frame's warp) ----
+ *
+ * A 3-level 3D U-Net (16 / 32 / 64 channels, 3x3x3 convolutions, 2x2x2 average pooling,
+ * nearest up-sampling, skip concatenations) over the lattice grid, in BF16 with FP32
+ * accumulation on the tensor cores.  Input per node (6 floats, node-major, node i =
+ * x + nx (y + ny z)): u_i / h and the data-term gradient scaled by one Jacobi step,
+ * b_i / (h (diag_i + 2 w_r |N_i|)) with b = -J_data^T r; output per node (3 floats): the
+ * predicted change of u in units of h.  Training minimises the mean squared error to
+ * solver increments (u_f - u_{f-1}) / h with Adam (beta 0.9 / 0.999, eps 1e-8).
+ * Arrays passed to the network calls are device memory; a handle's buffers are shared
+ * by its calls, so calls on one handle must not overlap on the GPU. */
+typedef struct vd_unet vd_unet; /* opaque; owned by the library */
+
+/* Network for an nx x ny x nz grid (each a multiple of 4); parameters drawn from a
+ * seeded He-normal initialisation (the output layer scaled by 0.01), Adam moments 0. */
+vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_unet **out);
+vd_status vd_unet_destroy(vd_unet *net);
+vd_status vd_unet_dims(const vd_unet *net, int *nx, int *ny, int *nz);
+/* Number of FP32 parameters: per layer, weights [27][Cin][Cout] (tap = 9 dz + 3 dy + dx
+ * over offsets -1..1) then bias [Cout], layers in the order a1 b1 a2 b2 a3 b3 c2 d2 c1 d1
+ * head. */
+vd_status vd_unet_num_params(const vd_unet *net, int *n);
+vd_status vd_unet_get_params(vd_unet *net, float *host, int n);
+vd_status vd_unet_set_params(vd_unet *net, const float *host, int n);
+/* Gradients of the loss of the last vd_unet_train_step, same layout (host array). */
+vd_status vd_unet_get_grads(vd_unet *net, float *host, int n);
+/* out3 = net(in6); synchronous / enqueued on cuda_stream (NULL = the handle's stream). */
+vd_status vd_unet_forward(vd_unet *net, const float *in6, float *out3);
+vd_status vd_unet_forward_async(vd_unet *net, const float *in6, float *out3, void *cuda_stream);
+/* One Adam step on mean((net(in6) - target3)^2) with learning rate lr (lr = 0: loss
+ * and gradients only); `loss` (host, may be NULL) gets the loss before the step. */
+vd_status vd_unet_train_step(vd_unet *net, const float *in6, const float *target3, float lr,
+                             double *loss);
+/* Parameters to / from a file: "VDUNET01", int32 layer count, int32 Cin[], int32 Cout[],
+ * int32 parameter count, FP32 parameters, all little-endian.  A file whose shapes do
+ * not match gives VD_ERR_INVALID_ARG. */
+vd_status vd_unet_save(vd_unet *net, const char *path);
+vd_status vd_unet_load(vd_unet *net, const char *path);
+
+typedef struct {
+    double e_start;      /* E_total (Eq. 1) of the warp before the call, under its association */
+    double e_predicted;  /* E_total of the predicted warp (rotations refitted), its association */
+    int used_prediction; /* 1 if the prediction was kept (finite and lower energy) */
+    int status;
+} vd_warm_report;
+
+/* The network input for the current frame at the current warp (nx*ny*nz x 6 floats,
+ * zero at inactive nodes), written to in6 (`mem` as elsewhere).  Synchronous. */
+vd_status vd_warm_features(vd_lattice *lat, const vd_solve_params *params, float *in6, int mem);
+
+/* Learned warm start of the current frame: features, network, candidate warp u + h net
+ * (with the rotations refitted to it), kept only if its energy is below the current
+ * warp's; then call vd_solve with init = VD_INIT_PREV.  The network's grid must equal the
+ * lattice's.  Enqueued on the lattice's stream; with `out` non-NULL it waits and fills
+ * it, else vd_get_warm_report does. */
+vd_status vd_warm_start(vd_lattice *lat, vd_unet *net, const vd_solve_params *params,
+                        vd_warm_report *out);
+vd_status vd_get_warm_report(vd_lattice *lat, vd_warm_report *out);
+
 #ifdef __cplusplus
 }
 #endif

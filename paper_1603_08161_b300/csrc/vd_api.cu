@@ -106,6 +106,10 @@ struct vd_lattice {
     bool coop = false;               // device supports cooperative launches
     bool use_persistent = true;      // may be cleared if the graph cannot hold the launch
     bool in_batch = false;           // being captured into a batch graph: streamed PCG
+    // Gauss-Newton early stop: the energy target lives in rep_dev[15]
+    bool gated = false;
+    // learned warm start: features (6 nn), prediction (3 nn), backup of u and R (12 ld)
+    float *warm = nullptr;
 };
 
 namespace {
@@ -288,6 +292,7 @@ void refresh_ctx(vd_lattice *L) {
     c.sfrac = L->sfr;
     c.scell = L->scell_s;
     c.S = L->S;
+    c.e_target = L->gated ? L->rep_dev + 15 : nullptr;
 }
 
 void set_params_ctx(Ctx &c, const vd_solve_params *p) {
@@ -373,7 +378,7 @@ struct Launcher {
 
 template <bool kAll>
 void enqueue_rhs(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K) {
-    Lc.go(VD_KC_RHS, k_rhs_nodes<kAll>, gr.node, kThreads, c);
+    Lc.go(VD_KC_RHS, k_rhs_nodes<kAll>, gr.node, kThreads, c, (const Scal *)sc);
     Lc.go(VD_KC_RHS, k_cells<kOpRhs, kAll>, gr.cells, kThreads, c, sc, K, 0);
 }
 
@@ -455,10 +460,11 @@ void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
         launch_persistent<kAll>(L, Lc, sc, K, P->cg_tol * P->cg_tol, 1, G, chunk);
     } else {
         enqueue_pcg<kAll>(Lc, c, sc, gr, K, P->cg_tol * P->cg_tol);
-        Lc.go(VD_KC_ROTATION, k_add_increment<kAll>, gr.node, kThreads, c);
+        Lc.go(VD_KC_ROTATION, k_add_increment<kAll>, gr.node, kThreads, c, (const Scal *)sc);
     }
     Lc.go(VD_KC_ROTATION, k_fit_rotations<kAll, true>, gr.node, kThreads, c, sc);
     Lc.go(VD_KC_ENERGY, k_cells<kOpEnergy, kAll>, gr.cells, kThreads, c, sc, K, 0);
+    if (c.e_target && g + 1 < P->gn_iters) Lc.go(-1, k_gn_gate, 1, 32, c, (const Scal *)sc, slot(L, g + 1));
 }
 
 void enqueue_solve(vd_lattice *L, const vd_solve_params *P, cudaStream_t st) {
@@ -1031,12 +1037,12 @@ vd_status vd_step_pcg(vd_lattice *L, const vd_solve_params *P, float *delta, int
         enqueue_pcg<true>(Lc, c, sc, gr, K, tol2);
         Lc.other();
         if (delta) k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
-        if (apply) k_add_increment<true><<<gr.node, kThreads, 0, st>>>(c);
+        if (apply) k_add_increment<true><<<gr.node, kThreads, 0, st>>>(c, sc);
     } else {
         enqueue_rhs<false>(Lc, c, sc, gr, K);
         enqueue_pcg<false>(Lc, c, sc, gr, K, tol2);
         if (delta) k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
-        if (apply) k_add_increment<false><<<gr.node, kThreads, 0, st>>>(c);
+        if (apply) k_add_increment<false><<<gr.node, kThreads, 0, st>>>(c, sc);
     }
     CKL();
     if (delta) TRY(download(L, delta, L->staging, sizeof(float) * 3 * (size_t)c.nn, mem));
@@ -1450,3 +1456,117 @@ extern "C" vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spac
         return VD_ERR_CUDA;
     return VD_OK;
 }
+
+// ------------------------------------------------------------------ early stop and learned warm start
+
+namespace {
+
+vd_status warm_prepare(vd_lattice *L, const vd_solve_params *P) {
+    TRY(check_params(L, P));
+    if (!L->have_frame) return fail(L, VD_ERR_STATE, "no frame");
+    // two scalar slots, keeping the solve's slot layout when it already has them
+    if (!L->scal || L->scal_slots < 2) TRY(ensure_scal(L, std::max(2, P->gn_iters), std::max(1, P->cg_iters)));
+    if (!L->warm) TRY(dalloc(L, &L->warm, 9 * (size_t)L->c.nn + 12 * (size_t)L->c.ld));
+    set_params_ctx(L->c, P);
+    refresh_ctx(L);
+    return VD_OK;
+}
+
+// E_total at the current warp (slot 0), then the data-term right-hand side (w_r = 0)
+// and the features
+template <bool kAll>
+void warm_features_enqueue(vd_lattice *L, float *in6) {
+    cudaStream_t st = L->stream;
+    const Grid gr = grids(L);
+    const Ctx c = L->c;
+    Scal *s0 = slot(L, 0);
+    cudaMemsetAsync(L->scal, 0, 2 * L->scal_stride, st);
+    k_associate<kAll><<<gr.samp, kThreads, 0, st>>>(c, s0);
+    k_fit_rotations<kAll, false><<<gr.node, kThreads, 0, st>>>(c, s0);
+    k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, s0, 1, 0);
+    Ctx cd = c;
+    cd.w_r = 0.f;
+    k_rhs_nodes<kAll><<<gr.node, kThreads, 0, st>>>(cd, s0);
+    k_cells<kOpRhs, kAll><<<gr.cells, kThreads, 0, st>>>(cd, s0, 1, 0);
+    if (!kAll) cudaMemsetAsync(in6, 0, sizeof(float) * 6 * (size_t)c.nn, st);
+    k_warm_features<kAll><<<gr.node, kThreads, 0, st>>>(c, c.w_r, in6);
+}
+
+// candidate u + h pred, rotations refitted (slot 1 gets its E_reg), association and
+// energy at the candidate, then keep or restore
+template <bool kAll>
+void warm_select_enqueue(vd_lattice *L, const float *pred) {
+    cudaStream_t st = L->stream;
+    const Grid gr = grids(L);
+    const Ctx c = L->c;
+    Scal *s0 = slot(L, 0), *s1 = slot(L, 1);
+    float *bak = L->warm + 9 * (size_t)c.nn;
+    k_warm_apply<kAll><<<gr.node, kThreads, 0, st>>>(c, pred, bak);
+    k_fit_rotations<kAll, true><<<gr.node, kThreads, 0, st>>>(c, s1);
+    k_associate<kAll><<<gr.samp, kThreads, 0, st>>>(c, s1);
+    k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, s1, 1, 0);
+    k_warm_select<kAll><<<gr.node, kThreads, 0, st>>>(c, s0, s1, bak, L->rep_dev + 11);
+}
+
+}  // namespace
+
+extern "C" {
+
+vd_status vd_set_energy_target(vd_lattice *L, double e_target) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (!(e_target >= 0.0)) {
+        L->gated = false;
+        return VD_OK;
+    }
+    // by value through a kernel argument: ordered on the stream, no host buffer to keep
+    k_store_f64<<<1, 1, 0, L->stream>>>(L->rep_dev + 15, e_target);
+    CKL();
+    L->gated = true;
+    return VD_OK;
+}
+
+vd_status vd_warm_features(vd_lattice *L, const vd_solve_params *P, float *in6, int mem) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (!in6) return fail(L, VD_ERR_INVALID_ARG, "in6 is NULL");
+    TRY(warm_prepare(L, P));
+    if (L->all) warm_features_enqueue<true>(L, L->warm);
+    else warm_features_enqueue<false>(L, L->warm);
+    CKL();
+    TRY(download(L, in6, L->warm, sizeof(float) * 6 * (size_t)L->c.nn, mem));
+    CK(cudaStreamSynchronize(L->stream));
+    return VD_OK;
+}
+
+vd_status vd_warm_start(vd_lattice *L, vd_unet *net, const vd_solve_params *P, vd_warm_report *out) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (!net) return fail(L, VD_ERR_INVALID_ARG, "net is NULL");
+    int nx = 0, ny = 0, nz = 0;
+    TRY(vd_unet_dims(net, &nx, &ny, &nz));
+    if (nx != L->c.nx || ny != L->c.ny || nz != L->c.nz)
+        return fail(L, VD_ERR_INVALID_ARG, "network grid %dx%dx%d != lattice %dx%dx%d", nx, ny, nz, L->c.nx, L->c.ny,
+                    L->c.nz);
+    TRY(warm_prepare(L, P));
+    float *in6 = L->warm, *pred = L->warm + 6 * (size_t)L->c.nn;
+    if (L->all) warm_features_enqueue<true>(L, in6);
+    else warm_features_enqueue<false>(L, in6);
+    CKL();
+    if (vd_unet_forward_async(net, in6, pred, L->stream) != VD_OK) return fail(L, VD_ERR_CUDA, "network launch failed");
+    if (L->all) warm_select_enqueue<true>(L, pred);
+    else warm_select_enqueue<false>(L, pred);
+    CKL();
+    CK(cudaMemcpyAsync(L->rep_host + 11, L->rep_dev + 11, 3 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    if (out) return vd_get_warm_report(L, out);
+    return VD_OK;
+}
+
+vd_status vd_get_warm_report(vd_lattice *L, vd_warm_report *out) {
+    if (!L || !out) return VD_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(L->stream));
+    out->e_start = L->rep_host[11];
+    out->e_predicted = L->rep_host[12];
+    out->used_prediction = L->rep_host[13] != 0.0;
+    out->status = VD_OK;
+    return VD_OK;
+}
+
+}  // extern "C"

@@ -54,13 +54,18 @@ struct Ctx {
     const float4 *fh, *ft, *sfrac;
     const int *scell;
     int S;
+    // Gauss-Newton early stop: after each iteration a gate compares E_total with
+    // *e_target and marks the remaining iterations skipped (NULL: no gates)
+    const double *e_target;
 };
 
 // Per-Gauss-Newton-iteration scalar block (FP64 sums and counters), zeroed at the
 // start of every solve.
 struct Scal {
     double e_dense, e_sparse, e_reg, pad;
-    int stop, cg_done, n_valid, n_refined, n_degenerate, assoc_ran, pad2, pad3;
+    int stop, cg_done, n_valid, n_refined, n_degenerate, assoc_ran;
+    int skip;  // this Gauss-Newton iteration is skipped (the energy target was met)
+    int pad3;
     double rho[1];  // rho[0..K], then pq[0..K-1] follow (layout set by the host)
 };
 
@@ -658,6 +663,7 @@ template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
     pdl_wait();
     pdl_trigger();
+    if (sc->skip) return;
     const int n = *c.n_samples;
     int valid = 0, refined = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -867,6 +873,7 @@ template <int kOp, bool kAll>
 __global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int it) {
     pdl_wait();
     pdl_trigger();
+    if (sc->skip) return;
     if (kOp == kOpApply) {
         if (sc->stop || !(scal_rho(sc)[it] > 0.0)) return;
     }
@@ -895,9 +902,10 @@ __global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int 
 //   b_k = -w_r sum_{j in N_k} [2 (u_k - u_j) - (R_k + R_j - 2I)(t^_k - t^_j)],
 //   diag_k = 2 w_r |N_k|.  Written with plain stores (the sample pass adds after).
 template <bool kAll>
-__global__ void __launch_bounds__(kThreads) k_rhs_nodes(Ctx c) {
+__global__ void __launch_bounds__(kThreads) k_rhs_nodes(Ctx c, const Scal *sc) {
     pdl_wait();
     pdl_trigger();
+    if (sc->skip) return;
     const int N = active_count<kAll>(c);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
         const int i = slot_node<kAll>(c, s);
@@ -938,6 +946,7 @@ template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_pcg_init(Ctx c, Scal *sc) {
     pdl_wait();
     pdl_trigger();
+    if (sc->skip) return;
     const int N = active_count<kAll>(c);
     const size_t off = (size_t)blockIdx.y * c.ld;
     float *__restrict__ minv = c.minv + off;
@@ -1131,9 +1140,10 @@ __global__ void __launch_bounds__(kThreads) k_update_p(Ctx c, Scal *sc, int it, 
 }
 
 template <bool kAll>
-__global__ void __launch_bounds__(kThreads) k_add_increment(Ctx c) {
+__global__ void __launch_bounds__(kThreads) k_add_increment(Ctx c, const Scal *sc) {
     pdl_wait();
     pdl_trigger();
+    if (sc->skip) return;
     const int N = active_count<kAll>(c);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
         const int i = slot_node<kAll>(c, s);
@@ -1278,6 +1288,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     float *__restrict__ Rr = sm + 3 * chunk;  // r of own slots
     float *__restrict__ Q = sm + 6 * chunk;   // z between phases B and A, q within A..B
     float *__restrict__ Zg = c.r;
+    if (sc->skip) return;  // the same flag for every CTA: none reaches a barrier
     const unsigned G = gridDim.x;
     const int N = active_count<kAll>(c);
     const int N4 = 4 * groups4(N);
@@ -1668,6 +1679,7 @@ template <bool kAll, bool kFit>
 __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
     pdl_wait();
     pdl_trigger();
+    if (sc->skip) return;
     const int N = active_count<kAll>(c);
     float part = 0.f;
     int degenerate = 0;
@@ -1877,16 +1889,34 @@ __global__ void k_pack_float4(const float *__restrict__ src, int n, float4 *__re
         dst[i] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.f);
 }
 
+__global__ void k_store_f64(double *dst, double v) { *dst = v; }
+
+// Gauss-Newton early stop: iteration g+1 (slot `next`) is skipped once iteration g was
+// skipped or ended with E_total <= *c.e_target.  The PCG kernels also honour `stop`.
+__global__ void k_gn_gate(Ctx c, const Scal *prev, Scal *next) {
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x || blockIdx.x) return;
+    const double e = (double)c.w_s * prev->e_sparse + (double)c.w_d * prev->e_dense + (double)c.w_r * prev->e_reg;
+    if (prev->skip || e <= *c.e_target) {
+        next->skip = 1;
+        next->stop = 1;
+    }
+}
+
 __global__ void k_finish_report(Scal *sc_base, size_t stride, int G, Ctx c, double *out, const int *err) {
     pdl_wait();
     pdl_trigger();
     // out: e_total, e_dense, e_sparse, e_reg, then ints as doubles: gn_done, cg_done,
     // n_valid, n_degenerate, n_refined, finite
     if (threadIdx.x || blockIdx.x) return;
-    Scal *last = (Scal *)((char *)sc_base + stride * (size_t)(G - 1));
-    int nv = 0, nr = 0;
+    Scal *last = sc_base;
+    int nv = 0, nr = 0, done = 0;
     for (int g = 0; g < G; g++) {
         Scal *s = (Scal *)((char *)sc_base + stride * (size_t)g);
+        if (s->skip) break;
+        last = s;
+        done++;
         if (s->assoc_ran) {
             nv = s->n_valid;
             nr = s->n_refined;
@@ -1898,13 +1928,87 @@ __global__ void k_finish_report(Scal *sc_base, size_t stride, int G, Ctx c, doub
     out[1] = ed;
     out[2] = es;
     out[3] = er;
-    out[4] = G;
+    out[4] = done;
     out[5] = last->cg_done;
     out[6] = nv;
     out[7] = last->n_degenerate;
     out[8] = nr;
     out[9] = isfinite(et) ? 1.0 : 0.0;
     out[10] = *err ? 1.0 : 0.0;  // a grid barrier of the persistent position step gave up
+}
+
+
+// ------------------------------------------------------------------ learned warm start
+
+// Network input at every active node i (node-major, 6 floats; the caller zeroes the
+// rest): the displacement in lattice units u_i / h, and the data-term gradient of the
+// current frame at the current warp, b_i = -(J_data^T r)_i (Eq. 2-3 with w_r = 0, as
+// left in c.r by the right-hand side pass run with w_r = 0), scaled per component by
+// 1 / (h (diag_i + 2 w_r |N_i|)): one Jacobi step of the full system, in lattice units.
+template <bool kAll>
+__global__ void k_warm_features(Ctx c, float w_reg, float *__restrict__ in6) {
+    const int N = active_count<kAll>(c);
+    const float ih = 1.f / c.h;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int i = slot_node<kAll>(c, s);
+        int nb[6];
+        neighbours<kAll>(c, s, nb);
+        int deg = 0;
+#pragma unroll
+        for (int d = 0; d < 6; d++) deg += nb[d] >= 0;
+        const float reg = 2.f * w_reg * (float)deg;
+        const float3 u = ld3(c.u, c.ld, i);
+        const float3 b = ld3(c.r, c.ld, s), dg = ld3(c.minv, c.ld, s);
+        const float dx = dg.x + reg, dy = dg.y + reg, dz = dg.z + reg;
+        float *o = in6 + 6 * (size_t)i;
+        o[0] = u.x * ih;
+        o[1] = u.y * ih;
+        o[2] = u.z * ih;
+        o[3] = dx > 0.f ? b.x * ih / dx : 0.f;
+        o[4] = dy > 0.f ? b.y * ih / dy : 0.f;
+        o[5] = dz > 0.f ? b.z * ih / dz : 0.f;
+    }
+}
+
+// Candidate start: back up u and R of the active nodes, then u_i += h * pred_i.
+template <bool kAll>
+__global__ void k_warm_apply(Ctx c, const float *__restrict__ pred3, float *__restrict__ bak) {
+    const int N = active_count<kAll>(c);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int i = slot_node<kAll>(c, s);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const float v = c.u[a * (size_t)c.ld + i];
+            bak[a * (size_t)c.ld + i] = v;
+            c.u[a * (size_t)c.ld + i] = v + c.h * pred3[3 * (size_t)i + a];
+        }
+#pragma unroll
+        for (int a = 0; a < 9; a++) bak[(3 + a) * (size_t)c.ld + i] = c.R[a * (size_t)c.ld + i];
+    }
+}
+
+// Keep the candidate only if its energy is finite and below the current warp's; else
+// restore u and R.  out: E of the current warp, E of the candidate, 1 if kept.
+template <bool kAll>
+__global__ void k_warm_select(Ctx c, const Scal *cur, const Scal *cand, const float *__restrict__ bak,
+                              double *__restrict__ out) {
+    const double e0 = (double)c.w_s * cur->e_sparse + (double)c.w_d * cur->e_dense + (double)c.w_r * cur->e_reg;
+    const double e1 = (double)c.w_s * cand->e_sparse + (double)c.w_d * cand->e_dense + (double)c.w_r * cand->e_reg;
+    const bool keep = isfinite(e1) && e1 < e0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[0] = e0;
+        out[1] = e1;
+        out[2] = keep ? 1.0 : 0.0;
+    }
+    if (keep) return;
+    const int N = active_count<kAll>(c);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int i = slot_node<kAll>(c, s);
+#pragma unroll
+        for (int a = 0; a < 3; a++) c.u[a * (size_t)c.ld + i] = bak[a * (size_t)c.ld + i];
+#pragma unroll
+        for (int a = 0; a < 9; a++) c.R[a * (size_t)c.ld + i] = bak[(3 + a) * (size_t)c.ld + i];
+    }
 }
 
 }  // namespace vd

@@ -1,0 +1,661 @@
+// Learned warm start of the lattice solve: a 3-level 3D U-Net (16 / 32 / 64 channels)
+// over the lattice grid, BF16 weights and activations with FP32 accumulation on the
+// tensor cores, with its own forward, backward and Adam kernels.
+//
+// Input (6 channels per node): the previous frame's displacement u / h and the current
+// data-term gradient (scaled).  Output (3 channels): the predicted change of u in
+// lattice units.  Convolutions are 3x3x3, "same", with bias; ReLU after every
+// convolution except the head.  Down-sampling is 2x2x2 average pooling, up-sampling is
+// nearest-neighbour x2; skip connections are channel concatenations:
+//   e1 = b1(a1(x))          96^3, 16      cat1 = [up(d2), e1]   96^3, 48
+//   e2 = b2(a2(pool(e1)))   48^3, 32      cat2 = [up(e3), e2]   48^3, 96
+//   e3 = b3(a3(pool(e2)))   24^3, 64      d2 = d2c(c2(cat2))    48^3, 32
+//   out = head(d1c(c1(cat1)))  96^3, 3
+// Activations are stored channels-last with a one-voxel zero halo and 16 voxels of
+// slack after each row, so a 16-voxel tile at any tap offset stays inside its buffer:
+// every implicit-GEMM tile is a plain strided 16x16 matrix for the WMMA loads.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <mma.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "vd.h"
+
+using namespace nvcuda;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int kLayers = 11;
+// Cin, Cout of the layers in parameter order (ReLU after all but the head)
+constexpr int kCin[kLayers] = {6, 16, 16, 32, 32, 64, 96, 32, 48, 16, 16};
+constexpr int kCout[kLayers] = {16, 16, 32, 32, 64, 64, 32, 32, 16, 16, 3};
+enum { A1, B1, A2, B2, A3, B3, C2, D2, C1, D1, HEAD };
+
+int pad16(int c) { return (c + 15) / 16 * 16; }
+
+// A channels-last view: p points at channel c0 of voxel (-1, -1, -1); C is the buffer's
+// channel stride, nc the view's channel count.
+struct View {
+    bf16 *p;
+    int D, H, W, C, Wp, nc;
+};
+
+__host__ __device__ inline size_t vox(const View &t, int z, int y, int x) {
+    return ((size_t)(z + 1) * (t.H + 2) + (y + 1)) * t.Wp + (x + 1);
+}
+
+// ------------------------------------------------------------------ kernels
+
+// out[..., 0:cout_real) = act(conv3x3x3(in) + bias): one warp per 16-voxel row tile and
+// all NF x 16 output channels.  in.nc and the weights' Cin are multiples of 16.
+template <int NF>
+__global__ void __launch_bounds__(128) k_conv3d(View in, const bf16 *__restrict__ Wt, const float *__restrict__ bias,
+                                                View out, int cout_real, int relu) {
+    __shared__ __align__(32) float tile[4][16 * 16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int xt_n = (out.W + 15) / 16;
+    const long t = (long)blockIdx.x * 4 + warp;
+    if (t >= (long)out.D * out.H * xt_n) return;
+    const int xt = (int)(t % xt_n), y = (int)((t / xt_n) % out.H), z = (int)(t / ((long)xt_n * out.H));
+    const int x0 = xt * 16;
+    const int CoutP = NF * 16;
+    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[NF];
+#pragma unroll
+    for (int j = 0; j < NF; j++) wmma::fill_fragment(acc[j], 0.f);
+    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
+    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> b;
+    for (int tap = 0; tap < 27; tap++) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const bf16 *A = in.p + vox(in, z + dz, y + dy, x0 + dx) * in.C;
+        for (int k0 = 0; k0 < in.nc; k0 += 16) {
+            wmma::load_matrix_sync(a, A + k0, in.C);
+#pragma unroll
+            for (int j = 0; j < NF; j++) {
+                wmma::load_matrix_sync(b, Wt + ((size_t)tap * in.nc + k0) * CoutP + 16 * j, CoutP);
+                wmma::mma_sync(acc[j], a, b, acc[j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NF; j++) {
+        wmma::store_matrix_sync(tile[warp], acc[j], 16, wmma::mem_row_major);
+        __syncwarp();
+        for (int e = lane; e < 256; e += 32) {
+            const int r = e >> 4, co = 16 * j + (e & 15);
+            const int x = x0 + r;
+            if (x < out.W && co < cout_real) {
+                float v = tile[warp][e] + (bias ? bias[co] : 0.f);
+                if (relu) v = fmaxf(v, 0.f);
+                out.p[vox(out, z, y, x) * out.C + co] = __float2bfloat16_rn(v);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// dW[tap][ci][co] += sum_v X[v + off(tap)][ci] dY[v][co] over this block's voxel tiles;
+// block = (tap, 16-channel ci group, 16-channel co group, slice), 4 warps.
+__global__ void __launch_bounds__(128) k_wgrad(View X, View dY, float *__restrict__ dW, int CoutP, int slices) {
+    __shared__ __align__(32) float tile[4][16 * 16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nci = X.nc / 16, nco = dY.nc / 16;
+    int b = blockIdx.x;
+    const int slice = b % slices;
+    b /= slices;
+    const int cof = b % nco;
+    b /= nco;
+    const int cif = b % nci;
+    const int tap = b / nci;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int xt_n = (dY.W + 15) / 16;
+    const long ntiles = (long)dY.D * dY.H * xt_n;
+    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
+    wmma::fill_fragment(acc, 0.f);
+    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> a;
+    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> bm;
+    for (long t = (long)slice * 4 + warp; t < ntiles; t += (long)slices * 4) {
+        const int xt = (int)(t % xt_n), y = (int)((t / xt_n) % dY.H), z = (int)(t / ((long)xt_n * dY.H));
+        const int x0 = xt * 16;
+        wmma::load_matrix_sync(a, X.p + vox(X, z + dz, y + dy, x0 + dx) * X.C + 16 * cif, X.C);
+        wmma::load_matrix_sync(bm, dY.p + vox(dY, z, y, x0) * dY.C + 16 * cof, dY.C);
+        wmma::mma_sync(acc, a, bm, acc);
+    }
+    wmma::store_matrix_sync(tile[warp], acc, 16, wmma::mem_row_major);
+    __syncwarp();
+    for (int e = lane; e < 256; e += 32) {
+        const int ci = 16 * cif + (e >> 4), co = 16 * cof + (e & 15);
+        const float v = tile[warp][e];
+        if (v != 0.f) atomicAdd(&dW[((size_t)tap * X.nc + ci) * CoutP + co], v);
+    }
+}
+
+// db[co] += sum_v dY[v][co]
+__global__ void k_bias_grad(View dY, int cout_real, float *__restrict__ db) {
+    const long n = (long)dY.D * dY.H * dY.W;
+    for (int co = 0; co < cout_real; co++) {
+        float s = 0.f;
+        for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+            const int x = (int)(i % dY.W), y = (int)((i / dY.W) % dY.H), z = (int)(i / ((long)dY.W * dY.H));
+            s += __bfloat162float(dY.p[vox(dY, z, y, x) * dY.C + co]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(&db[co], s);
+    }
+}
+
+// g *= (y > 0) over the view's channels
+__global__ void k_relu_bwd(View g, View y) {
+    const long n = (long)g.D * g.H * g.W * g.nc;
+    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % g.nc);
+        const long v = i / g.nc;
+        const int x = (int)(v % g.W), yy = (int)((v / g.W) % g.H), z = (int)(v / ((long)g.W * g.H));
+        if (!(__bfloat162float(y.p[vox(y, z, yy, x) * y.C + c]) > 0.f)) g.p[vox(g, z, yy, x) * g.C + c] = __float2bfloat16_rn(0.f);
+    }
+}
+
+// out = 2x2x2 average of in (out has half the size); accumulate: out += instead
+__global__ void k_pool(View in, View out) {
+    const long n = (long)out.D * out.H * out.W * out.nc;
+    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % out.nc);
+        const long v = i / out.nc;
+        const int x = (int)(v % out.W), y = (int)((v / out.W) % out.H), z = (int)(v / ((long)out.W * out.H));
+        float s = 0.f;
+        for (int k = 0; k < 8; k++)
+            s += __bfloat162float(in.p[vox(in, 2 * z + (k >> 2), 2 * y + ((k >> 1) & 1), 2 * x + (k & 1)) * in.C + c]);
+        out.p[vox(out, z, y, x) * out.C + c] = __float2bfloat16_rn(0.125f * s);
+    }
+}
+
+// gradient of the pooling: gin[2v + k] (+)= gout[v] / 8
+__global__ void k_pool_bwd(View gout, View gin, int accumulate) {
+    const long n = (long)gin.D * gin.H * gin.W * gin.nc;
+    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % gin.nc);
+        const long v = i / gin.nc;
+        const int x = (int)(v % gin.W), y = (int)((v / gin.W) % gin.H), z = (int)(v / ((long)gin.W * gin.H));
+        const float g = 0.125f * __bfloat162float(gout.p[vox(gout, z >> 1, y >> 1, x >> 1) * gout.C + c]);
+        bf16 *dst = gin.p + vox(gin, z, y, x) * gin.C + c;
+        *dst = __float2bfloat16_rn(accumulate ? __bfloat162float(*dst) + g : g);
+    }
+}
+
+// out (twice the size) = nearest-neighbour copy of in
+__global__ void k_upsample(View in, View out) {
+    const long n = (long)out.D * out.H * out.W * out.nc;
+    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % out.nc);
+        const long v = i / out.nc;
+        const int x = (int)(v % out.W), y = (int)((v / out.W) % out.H), z = (int)(v / ((long)out.W * out.H));
+        out.p[vox(out, z, y, x) * out.C + c] = in.p[vox(in, z >> 1, y >> 1, x >> 1) * in.C + c];
+    }
+}
+
+// gradient of the up-sampling: gin[v] = sum of the 8 gout it was copied to
+__global__ void k_upsample_bwd(View gout, View gin) {
+    const long n = (long)gin.D * gin.H * gin.W * gin.nc;
+    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % gin.nc);
+        const long v = i / gin.nc;
+        const int x = (int)(v % gin.W), y = (int)((v / gin.W) % gin.H), z = (int)(v / ((long)gin.W * gin.H));
+        float s = 0.f;
+        for (int k = 0; k < 8; k++)
+            s += __bfloat162float(gout.p[vox(gout, 2 * z + (k >> 2), 2 * y + ((k >> 1) & 1), 2 * x + (k & 1)) * gout.C + c]);
+        gin.p[vox(gin, z, y, x) * gin.C + c] = __float2bfloat16_rn(s);
+    }
+}
+
+// input buffer (16 channels, 6 used) from node-major float arrays (n x 6)
+__global__ void k_pack_input(const float *__restrict__ in6, View x) {
+    const long n = (long)x.D * x.H * x.W;
+    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int xx = (int)(i % x.W), y = (int)((i / x.W) % x.H), z = (int)(i / ((long)x.W * x.H));
+        bf16 *d = x.p + vox(x, z, y, xx) * x.C;
+        for (int c = 0; c < 6; c++) d[c] = __float2bfloat16_rn(in6[6 * i + c]);
+    }
+}
+
+__global__ void k_unpack_output(View o, float *__restrict__ out3) {
+    const long n = (long)o.D * o.H * o.W;
+    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % o.W), y = (int)((i / o.W) % o.H), z = (int)(i / ((long)o.W * o.H));
+        const bf16 *s = o.p + vox(o, z, y, x) * o.C;
+        for (int c = 0; c < 3; c++) out3[3 * i + c] = __bfloat162float(s[c]);
+    }
+}
+
+// loss = mean |out - target|^2 over nodes and the 3 channels; gout = d loss / d out
+__global__ void k_mse(View o, const float *__restrict__ target, View go, double *loss) {
+    const long n = (long)o.D * o.H * o.W;
+    const float scale = 2.f / (3.f * (float)n);
+    float s = 0.f;
+    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % o.W), y = (int)((i / o.W) % o.H), z = (int)(i / ((long)o.W * o.H));
+        for (int c = 0; c < 3; c++) {
+            const float d = __bfloat162float(o.p[vox(o, z, y, x) * o.C + c]) - target[3 * i + c];
+            s += d * d;
+            go.p[vox(go, z, y, x) * go.C + c] = __float2bfloat16_rn(scale * d);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(loss, (double)s / (3.0 * (double)n));
+}
+
+// Adam on the FP32 master parameters, then the BF16 forward weights (padded [27][CinP]
+// [CoutP]) and the flipped, transposed dgrad weights ([27][CoutP][CinP], tap 26 - t).
+struct LayerDev {
+    float *w, *b, *gw, *gb, *mw, *vw, *mb, *vb;  // master / grads / moments (unpadded)
+    bf16 *wf, *wt;                                // forward and dgrad weights (padded)
+    int cin, cout, cinp, coutp;
+};
+
+__global__ void k_adam(LayerDev L, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int nw = 27 * L.cin * L.cout;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw + L.cout; i += gridDim.x * blockDim.x) {
+        float *p, *m, *v, g;
+        if (i < nw) {
+            const int tap = i / (L.cin * L.cout), ci = (i / L.cout) % L.cin, co = i % L.cout;
+            g = L.gw[((size_t)tap * L.cinp + ci) * L.coutp + co];
+            p = L.w + i;
+            m = L.mw + i;
+            v = L.vw + i;
+        } else {
+            g = L.gb[i - nw];
+            p = L.b + (i - nw);
+            m = L.mb + (i - nw);
+            v = L.vb + (i - nw);
+        }
+        *m = b1 * *m + (1.f - b1) * g;
+        *v = b2 * *v + (1.f - b2) * g * g;
+        *p -= lr * (*m / c1) / (sqrtf(*v / c2) + eps);
+    }
+}
+
+__global__ void k_pack_weights(LayerDev L) {
+    const int n = 27 * L.cinp * L.coutp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int tap = i / (L.cinp * L.coutp), ci = (i / L.coutp) % L.cinp, co = i % L.coutp;
+        const float w = (ci < L.cin && co < L.cout) ? L.w[((size_t)tap * L.cin + ci) * L.cout + co] : 0.f;
+        L.wf[i] = __float2bfloat16_rn(w);
+        L.wt[((size_t)(26 - tap) * L.coutp + co) * L.cinp + ci] = __float2bfloat16_rn(w);
+    }
+}
+
+int blocks(long n, int threads = 256) {
+    long b = (n + threads - 1) / threads;
+    return (int)std::max<long>(1, std::min<long>(b, 148 * 8));
+}
+
+}  // namespace
+
+struct vd_unet {
+    int D, H, W;
+    std::vector<void *> bufs;
+    // activations (with halo) and gradients
+    View x, e1a, cat1, p1, e2a, cat2, p2, e3a, e3, d2a, d2, d1a, d1, out;
+    View gx, ge1a, gcat1, gp1, ge2a, gcat2, gp2, ge3a, ge3, gd2a, gd2, gd1a, gd1, gout;
+    LayerDev L[kLayers];
+    double *loss = nullptr;
+    float *io6 = nullptr, *io3 = nullptr;
+    int step = 0;
+    cudaStream_t st = nullptr;
+};
+
+namespace {
+
+template <typename T>
+bool ualloc(vd_unet *U, T **p, size_t n) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaMemset(q, 0, std::max<size_t>(n, 1) * sizeof(T));
+    U->bufs.push_back(q);
+    *p = (T *)q;
+    return true;
+}
+
+bool make_view(vd_unet *U, View *v, int D, int H, int W, int C) {
+    v->D = D;
+    v->H = H;
+    v->W = W;
+    v->C = C;
+    v->Wp = W + 18;
+    v->nc = C;
+    const size_t n = (size_t)(D + 2) * (H + 2) * v->Wp * C + 16 * (size_t)C;
+    bf16 *p;
+    if (!ualloc(U, &p, n)) return false;
+    v->p = p;
+    return true;
+}
+
+View slice(View v, int c0, int nc) {
+    v.p += c0;
+    v.nc = nc;
+    return v;
+}
+
+void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool dgrad) {
+    // forward: in (cinp) -> out (coutp slice); dgrad: in = grad of out (coutp) -> grad of in (cinp)
+    const bf16 *w = dgrad ? L.wt : L.wf;
+    const int nf = (dgrad ? L.cinp : L.coutp) / 16;
+    const int creal = dgrad ? L.cinp : L.cout;
+    const float *bias = dgrad ? nullptr : L.b;
+    const long tiles = (long)out.D * out.H * ((out.W + 15) / 16);
+    const int nb = (int)((tiles + 3) / 4);
+    switch (nf) {
+        case 1: k_conv3d<1><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
+        case 2: k_conv3d<2><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
+        case 3: k_conv3d<3><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
+        case 4: k_conv3d<4><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
+        case 6: k_conv3d<6><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
+        default: break;
+    }
+}
+
+void wgrad(cudaStream_t st, View X, View dY, const LayerDev &L) {
+    const int nci = X.nc / 16, nco = dY.nc / 16;
+    const long tiles = (long)dY.D * dY.H * ((dY.W + 15) / 16);
+    const int slices = (int)std::max<long>(1, std::min<long>(64, (tiles + 63) / 64));
+    k_wgrad<<<27 * nci * nco * slices, 128, 0, st>>>(X, dY, L.gw, L.coutp, slices);
+    k_bias_grad<<<blocks((long)dY.D * dY.H * dY.W), 256, 0, st>>>(dY, L.cout, L.gb);
+}
+
+long nvox(const View &v) { return (long)v.D * v.H * v.W; }
+
+void forward(vd_unet *U, cudaStream_t st) {
+    View e1 = slice(U->cat1, 32, 16), e2 = slice(U->cat2, 64, 32);
+    conv(st, U->x, U->L[A1], U->e1a, true, false);
+    conv(st, U->e1a, U->L[B1], e1, true, false);
+    k_pool<<<blocks(nvox(U->p1) * 16), 256, 0, st>>>(e1, U->p1);
+    conv(st, U->p1, U->L[A2], U->e2a, true, false);
+    conv(st, U->e2a, U->L[B2], e2, true, false);
+    k_pool<<<blocks(nvox(U->p2) * 32), 256, 0, st>>>(e2, U->p2);
+    conv(st, U->p2, U->L[A3], U->e3a, true, false);
+    conv(st, U->e3a, U->L[B3], U->e3, true, false);
+    k_upsample<<<blocks(nvox(U->cat2) * 64), 256, 0, st>>>(U->e3, slice(U->cat2, 0, 64));
+    conv(st, U->cat2, U->L[C2], U->d2a, true, false);
+    conv(st, U->d2a, U->L[D2], U->d2, true, false);
+    k_upsample<<<blocks(nvox(U->cat1) * 32), 256, 0, st>>>(U->d2, slice(U->cat1, 0, 32));
+    conv(st, U->cat1, U->L[C1], U->d1a, true, false);
+    conv(st, U->d1a, U->L[D1], U->d1, true, false);
+    conv(st, U->d1, U->L[HEAD], U->out, false, false);
+}
+
+void relu_bwd(cudaStream_t st, View g, View y) {
+    k_relu_bwd<<<blocks(nvox(g) * g.nc), 256, 0, st>>>(g, y);
+}
+
+// gout must hold d loss / d out; fills every layer's gw, gb
+void backward(vd_unet *U, cudaStream_t st) {
+    View e1 = slice(U->cat1, 32, 16), e2 = slice(U->cat2, 64, 32);
+    View ge1 = slice(U->gcat1, 32, 16), ge2 = slice(U->gcat2, 64, 32);
+    for (int l = 0; l < kLayers; l++) {
+        cudaMemsetAsync(U->L[l].gw, 0, sizeof(float) * 27 * U->L[l].cinp * U->L[l].coutp, st);
+        cudaMemsetAsync(U->L[l].gb, 0, sizeof(float) * U->L[l].cout, st);
+    }
+    // head (linear) and decoder level 1
+    wgrad(st, U->d1, U->gout, U->L[HEAD]);
+    conv(st, U->gout, U->L[HEAD], U->gd1, false, true);
+    relu_bwd(st, U->gd1, U->d1);
+    wgrad(st, U->d1a, U->gd1, U->L[D1]);
+    conv(st, U->gd1, U->L[D1], U->gd1a, false, true);
+    relu_bwd(st, U->gd1a, U->d1a);
+    wgrad(st, U->cat1, U->gd1a, U->L[C1]);
+    conv(st, U->gd1a, U->L[C1], U->gcat1, false, true);  // [d up(d2), d e1 (skip)]
+    // decoder level 2
+    k_upsample_bwd<<<blocks(nvox(U->gd2) * 32), 256, 0, st>>>(slice(U->gcat1, 0, 32), U->gd2);
+    relu_bwd(st, U->gd2, U->d2);
+    wgrad(st, U->d2a, U->gd2, U->L[D2]);
+    conv(st, U->gd2, U->L[D2], U->gd2a, false, true);
+    relu_bwd(st, U->gd2a, U->d2a);
+    wgrad(st, U->cat2, U->gd2a, U->L[C2]);
+    conv(st, U->gd2a, U->L[C2], U->gcat2, false, true);  // [d up(e3), d e2 (skip)]
+    // bottleneck
+    k_upsample_bwd<<<blocks(nvox(U->ge3) * 64), 256, 0, st>>>(slice(U->gcat2, 0, 64), U->ge3);
+    relu_bwd(st, U->ge3, U->e3);
+    wgrad(st, U->e3a, U->ge3, U->L[B3]);
+    conv(st, U->ge3, U->L[B3], U->ge3a, false, true);
+    relu_bwd(st, U->ge3a, U->e3a);
+    wgrad(st, U->p2, U->ge3a, U->L[A3]);
+    conv(st, U->ge3a, U->L[A3], U->gp2, false, true);
+    // encoder level 2: d e2 = skip part + pooling part
+    k_pool_bwd<<<blocks(nvox(ge2) * 32), 256, 0, st>>>(U->gp2, ge2, 1);
+    relu_bwd(st, ge2, e2);
+    wgrad(st, U->e2a, ge2, U->L[B2]);
+    conv(st, ge2, U->L[B2], U->ge2a, false, true);
+    relu_bwd(st, U->ge2a, U->e2a);
+    wgrad(st, U->p1, U->ge2a, U->L[A2]);
+    conv(st, U->ge2a, U->L[A2], U->gp1, false, true);
+    // encoder level 1
+    k_pool_bwd<<<blocks(nvox(ge1) * 16), 256, 0, st>>>(U->gp1, ge1, 1);
+    relu_bwd(st, ge1, e1);
+    wgrad(st, U->e1a, ge1, U->L[B1]);
+    conv(st, ge1, U->L[B1], U->ge1a, false, true);
+    relu_bwd(st, U->ge1a, U->e1a);
+    wgrad(st, U->x, U->ge1a, U->L[A1]);
+}
+
+int num_params() {
+    int n = 0;
+    for (int l = 0; l < kLayers; l++) n += 27 * kCin[l] * kCout[l] + kCout[l];
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_unet **out) {
+    if (!out || nx < 4 || ny < 4 || nz < 4 || nx % 4 || ny % 4 || nz % 4) return VD_ERR_INVALID_ARG;
+    *out = nullptr;
+    vd_unet *U = new (std::nothrow) vd_unet();
+    if (!U) return VD_ERR_OOM;
+    U->D = nz;
+    U->H = ny;
+    U->W = nx;
+    const int D = nz, H = ny, W = nx;
+    bool ok = true;
+    struct {
+        View *v, *g;
+        int s, c;
+    } spec[] = {{&U->x, &U->gx, 1, 16},     {&U->e1a, &U->ge1a, 1, 16}, {&U->cat1, &U->gcat1, 1, 48},
+                {&U->p1, &U->gp1, 2, 16},   {&U->e2a, &U->ge2a, 2, 32}, {&U->cat2, &U->gcat2, 2, 96},
+                {&U->p2, &U->gp2, 4, 32},   {&U->e3a, &U->ge3a, 4, 64}, {&U->e3, &U->ge3, 4, 64},
+                {&U->d2a, &U->gd2a, 2, 32}, {&U->d2, &U->gd2, 2, 32},   {&U->d1a, &U->gd1a, 1, 16},
+                {&U->d1, &U->gd1, 1, 16},   {&U->out, &U->gout, 1, 16}};
+    for (auto &s : spec) {
+        ok = ok && make_view(U, s.v, D / s.s, H / s.s, W / s.s, s.c);
+        ok = ok && make_view(U, s.g, D / s.s, H / s.s, W / s.s, s.c);
+    }
+    std::mt19937_64 rng(seed);
+    for (int l = 0; l < kLayers && ok; l++) {
+        LayerDev &L = U->L[l];
+        L.cin = kCin[l];
+        L.cout = kCout[l];
+        L.cinp = pad16(kCin[l]);
+        L.coutp = pad16(kCout[l]);
+        const size_t nw = 27 * (size_t)L.cin * L.cout, np = 27 * (size_t)L.cinp * L.coutp;
+        ok = ok && ualloc(U, &L.w, nw) && ualloc(U, &L.b, L.cout) && ualloc(U, &L.gw, np) &&
+             ualloc(U, &L.gb, L.cout) && ualloc(U, &L.mw, nw) && ualloc(U, &L.vw, nw) && ualloc(U, &L.mb, L.cout) &&
+             ualloc(U, &L.vb, L.cout) && ualloc(U, &L.wf, np) && ualloc(U, &L.wt, np);
+        if (!ok) break;
+        // He initialisation (the head starts small: the first prediction is ~0)
+        std::normal_distribution<float> nd(0.f, std::sqrt(2.f / (27.f * L.cin)) * (l == HEAD ? 0.01f : 1.f));
+        std::vector<float> w(nw);
+        for (auto &v : w) v = nd(rng);
+        cudaMemcpy(L.w, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
+        k_pack_weights<<<blocks((long)np), 256>>>(L);
+    }
+    ok = ok && ualloc(U, &U->loss, 1) && ualloc(U, &U->io6, (size_t)6 * D * H * W) &&
+         ualloc(U, &U->io3, (size_t)3 * D * H * W);
+    if (!ok || cudaStreamCreateWithFlags(&U->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        vd_unet_destroy(U);
+        return VD_ERR_OOM;
+    }
+    *out = U;
+    return VD_OK;
+}
+
+vd_status vd_unet_destroy(vd_unet *U) {
+    if (!U) return VD_OK;
+    if (U->st) cudaStreamSynchronize(U->st);
+    for (void *p : U->bufs) cudaFree(p);
+    if (U->st) cudaStreamDestroy(U->st);
+    delete U;
+    return VD_OK;
+}
+
+vd_status vd_unet_num_params(const vd_unet *U, int *n) {
+    if (!U || !n) return VD_ERR_INVALID_ARG;
+    *n = num_params();
+    return VD_OK;
+}
+
+static vd_status unet_io(vd_unet *U, void *dst_or_src, int n, int dir, int which) {
+    // which 0: parameters, 1: gradients; dir 0: device -> host, 1: host -> device
+    if (!U || !dst_or_src || n != num_params()) return VD_ERR_INVALID_ARG;
+    float *h = (float *)dst_or_src;
+    size_t off = 0;
+    for (int l = 0; l < kLayers; l++) {
+        LayerDev &L = U->L[l];
+        const size_t nw = 27 * (size_t)L.cin * L.cout;
+        if (which == 0) {
+            if (dir == 0) {
+                cudaMemcpy(h + off, L.w, nw * sizeof(float), cudaMemcpyDeviceToHost);
+                cudaMemcpy(h + off + nw, L.b, L.cout * sizeof(float), cudaMemcpyDeviceToHost);
+            } else {
+                cudaMemcpy(L.w, h + off, nw * sizeof(float), cudaMemcpyHostToDevice);
+                cudaMemcpy(L.b, h + off + nw, L.cout * sizeof(float), cudaMemcpyHostToDevice);
+                k_pack_weights<<<blocks(27L * L.cinp * L.coutp), 256>>>(L);
+            }
+        } else {
+            std::vector<float> g(27 * (size_t)L.cinp * L.coutp);
+            cudaMemcpy(g.data(), L.gw, g.size() * sizeof(float), cudaMemcpyDeviceToHost);
+            for (int t = 0; t < 27; t++)
+                for (int ci = 0; ci < L.cin; ci++)
+                    for (int co = 0; co < L.cout; co++)
+                        h[off + ((size_t)t * L.cin + ci) * L.cout + co] = g[((size_t)t * L.cinp + ci) * L.coutp + co];
+            cudaMemcpy(h + off + nw, L.gb, L.cout * sizeof(float), cudaMemcpyDeviceToHost);
+        }
+        off += nw + L.cout;
+    }
+    return cudaDeviceSynchronize() == cudaSuccess ? VD_OK : VD_ERR_CUDA;
+}
+
+vd_status vd_unet_get_params(vd_unet *U, float *host, int n) { return unet_io(U, host, n, 0, 0); }
+vd_status vd_unet_set_params(vd_unet *U, const float *host, int n) { return unet_io(U, (void *)host, n, 1, 0); }
+vd_status vd_unet_get_grads(vd_unet *U, float *host, int n) { return unet_io(U, host, n, 0, 1); }
+
+vd_status vd_unet_forward_async(vd_unet *U, const float *in6, float *out3, void *stream) {
+    if (!U || !in6 || !out3) return VD_ERR_INVALID_ARG;
+    cudaStream_t st = stream ? (cudaStream_t)stream : U->st;
+    const long n = (long)U->D * U->H * U->W;
+    k_pack_input<<<blocks(n), 256, 0, st>>>(in6, U->x);
+    forward(U, st);
+    k_unpack_output<<<blocks(n), 256, 0, st>>>(U->out, out3);
+    return cudaGetLastError() == cudaSuccess ? VD_OK : VD_ERR_CUDA;
+}
+
+vd_status vd_unet_forward(vd_unet *U, const float *in6, float *out3) {
+    const vd_status s = vd_unet_forward_async(U, in6, out3, nullptr);
+    if (s != VD_OK) return s;
+    return cudaStreamSynchronize(U->st) == cudaSuccess ? VD_OK : VD_ERR_CUDA;
+}
+
+// One Adam step on the mean squared error between network(in6) and target3 (device
+// arrays); lr = 0 only computes the loss and the gradients.
+vd_status vd_unet_train_step(vd_unet *U, const float *in6, const float *target3, float lr, double *loss) {
+    if (!U || !in6 || !target3) return VD_ERR_INVALID_ARG;
+    cudaStream_t st = U->st;
+    const long n = (long)U->D * U->H * U->W;
+    k_pack_input<<<blocks(n), 256, 0, st>>>(in6, U->x);
+    forward(U, st);
+    cudaMemsetAsync(U->loss, 0, sizeof(double), st);
+    k_mse<<<blocks(n), 256, 0, st>>>(U->out, target3, U->gout, U->loss);
+    backward(U, st);
+    if (lr > 0.f) {
+        U->step++;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, (float)U->step), c2 = 1.f - std::pow(b2, (float)U->step);
+        for (int l = 0; l < kLayers; l++) {
+            k_adam<<<blocks(27L * U->L[l].cin * U->L[l].cout + U->L[l].cout), 256, 0, st>>>(U->L[l], lr, b1, b2, 1e-8f,
+                                                                                              c1, c2);
+            k_pack_weights<<<blocks(27L * U->L[l].cinp * U->L[l].coutp), 256, 0, st>>>(U->L[l]);
+        }
+    }
+    double h = 0.0;
+    cudaMemcpyAsync(&h, U->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return VD_ERR_CUDA;
+    if (loss) *loss = h;
+    return VD_OK;
+}
+
+// Weights file: "VDUNET01", int32 layer count, int32 Cin[], int32 Cout[], int32 parameter
+// count, then the FP32 parameters (per layer: weights [27][Cin][Cout], bias [Cout]); all
+// little-endian.
+static const char kMagic[8] = {'V', 'D', 'U', 'N', 'E', 'T', '0', '1'};
+
+static bool little_endian() {
+    const unsigned one = 1;
+    unsigned char b;
+    memcpy(&b, &one, 1);
+    return b == 1;
+}
+
+vd_status vd_unet_save(vd_unet *U, const char *path) {
+    if (!U || !path || !little_endian()) return VD_ERR_INVALID_ARG;
+    const int n = num_params();
+    std::vector<float> h(n);
+    vd_status s = vd_unet_get_params(U, h.data(), n);
+    if (s != VD_OK) return s;
+    FILE *f = fopen(path, "wb");
+    if (!f) return VD_ERR_INVALID_ARG;
+    const int layers = kLayers;
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(&layers, 4, 1, f) == 1 && fwrite(kCin, 4, kLayers, f) == kLayers &&
+              fwrite(kCout, 4, kLayers, f) == kLayers && fwrite(&n, 4, 1, f) == 1 &&
+              fwrite(h.data(), 4, n, f) == (size_t)n;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? VD_OK : VD_ERR_INVALID_ARG;
+}
+
+vd_status vd_unet_load(vd_unet *U, const char *path) {
+    if (!U || !path || !little_endian()) return VD_ERR_INVALID_ARG;
+    FILE *f = fopen(path, "rb");
+    if (!f) return VD_ERR_INVALID_ARG;
+    char magic[8];
+    int layers = 0, cin[kLayers], cout[kLayers], n = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && !memcmp(magic, kMagic, 8) && fread(&layers, 4, 1, f) == 1 &&
+              layers == kLayers && fread(cin, 4, kLayers, f) == kLayers && fread(cout, 4, kLayers, f) == kLayers &&
+              !memcmp(cin, kCin, sizeof(cin)) && !memcmp(cout, kCout, sizeof(cout)) && fread(&n, 4, 1, f) == 1 &&
+              n == num_params();
+    std::vector<float> h(ok ? n : 0);
+    ok = ok && fread(h.data(), 4, n, f) == (size_t)n;
+    fclose(f);
+    if (!ok) return VD_ERR_INVALID_ARG;
+    return vd_unet_set_params(U, h.data(), n);
+}
+
+vd_status vd_unet_dims(const vd_unet *U, int *nx, int *ny, int *nz) {
+    if (!U) return VD_ERR_INVALID_ARG;
+    if (nx) *nx = U->W;
+    if (ny) *ny = U->H;
+    if (nz) *nz = U->D;
+    return VD_OK;
+}
+
+}  // extern "C"

@@ -53,6 +53,14 @@ class vd_solve_report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class vd_warm_report(ctypes.Structure):
+    _fields_ = [("e_start", ctypes.c_double), ("e_predicted", ctypes.c_double),
+                ("used_prediction", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libvd.so is not built ({LIB_PATH}); run `python -m paper_1603_08161_b300.build` "
                       "or __graft_entry__.build()")
@@ -96,6 +104,22 @@ _SIGS = {
     "vd_batch_launch_count": [_P, _PI],
     "vd_batch_last_error": [_P],
     "vd_solve_batch": [_P, _I, ctypes.POINTER(vd_solve_params), _P],
+    "vd_set_energy_target": [_P, ctypes.c_double],
+    "vd_unet_create": [_I, _I, _I, ctypes.c_ulonglong, ctypes.POINTER(_P)],
+    "vd_unet_destroy": [_P],
+    "vd_unet_dims": [_P, _PI, _PI, _PI],
+    "vd_unet_num_params": [_P, _PI],
+    "vd_unet_get_params": [_P, _P, _I],
+    "vd_unet_set_params": [_P, _P, _I],
+    "vd_unet_get_grads": [_P, _P, _I],
+    "vd_unet_forward": [_P, _P, _P],
+    "vd_unet_forward_async": [_P, _P, _P, _P],
+    "vd_unet_train_step": [_P, _P, _P, ctypes.c_float, _PD],
+    "vd_unet_save": [_P, ctypes.c_char_p],
+    "vd_unet_load": [_P, ctypes.c_char_p],
+    "vd_warm_features": [_P, ctypes.POINTER(vd_solve_params), _P, _I],
+    "vd_warm_start": [_P, _P, ctypes.POINTER(vd_solve_params), ctypes.POINTER(vd_warm_report)],
+    "vd_get_warm_report": [_P, ctypes.POINTER(vd_warm_report)],
 }
 VD_NOALLOC_MAX_NODES = 65536
 for _name, _args in _SIGS.items():
@@ -224,11 +248,36 @@ class Lattice:
         return u, R
 
     def set_warp(self, u=None, R=None):
-        uu = None if u is None else np.ascontiguousarray(u, np.float32)
-        RR = None if R is None else np.ascontiguousarray(R, np.float32)
-        pu, mem = _ptr(uu)
+        """u (nn, 3) and R (nn, 9) or None: numpy (host) or CUDA tensors (device)."""
+        dev = any(a is not None and hasattr(a, "is_cuda") and a.is_cuda for a in (u, R))
+        conv = (lambda a: a.contiguous()) if dev else (lambda a: np.ascontiguousarray(a, np.float32))
+        uu = None if u is None else conv(u)
+        RR = None if R is None else conv(R)
+        pu, _ = _ptr(uu)
         pr, _ = _ptr(RR)
-        self._check(vd_set_warp(self.h, pu, pr, VD_MEM_HOST))
+        self._check(vd_set_warp(self.h, pu, pr, VD_MEM_DEVICE if dev else VD_MEM_HOST))
+
+    def set_energy_target(self, e_target):
+        """Stop later solves after the first iteration with E_total <= e_target (< 0: off)."""
+        self._check(vd_set_energy_target(self.h, float(e_target)))
+
+    def warm_features(self, prm, out=None):
+        """Network input (nn, 6) at the current warp; ``out`` may be a CUDA tensor."""
+        x = np.zeros((self.nn, 6), np.float32) if out is None else out
+        px, mem = _ptr(x)
+        self._check(vd_warm_features(self.h, ctypes.byref(prm), px, mem))
+        return x
+
+    def warm_start(self, net, prm, wait=True):
+        """Learned warm start of the current frame (see vd_warm_start)."""
+        rep = vd_warm_report()
+        self._check(vd_warm_start(self.h, net.h, ctypes.byref(prm), ctypes.byref(rep) if wait else None))
+        return rep.as_dict() if wait else None
+
+    def warm_report(self):
+        rep = vd_warm_report()
+        self._check(vd_get_warm_report(self.h, ctypes.byref(rep)))
+        return rep.as_dict()
 
     def num_active(self):
         n = ctypes.c_int()
@@ -355,3 +404,67 @@ class Batch:
         n = ctypes.c_int()
         self._check(vd_batch_launch_count(self.h, ctypes.byref(n)))
         return n.value
+
+
+class UNet:
+    """The warm-start network (vd_unet_*): device arrays in and out (CUDA tensors)."""
+
+    def __init__(self, dims, seed=0):
+        self.dims = tuple(int(v) for v in dims)
+        h = _P()
+        st = vd_unet_create(self.dims[0], self.dims[1], self.dims[2], int(seed), ctypes.byref(h))
+        if st != VD_OK:
+            raise VDError(st, "vd_unet_create failed")
+        self.h = h
+        n = ctypes.c_int()
+        vd_unet_num_params(self.h, ctypes.byref(n))
+        self.n_params = n.value
+
+    @staticmethod
+    def _check(st, what):
+        if st != VD_OK:
+            raise VDError(st, what)
+
+    def close(self):
+        if getattr(self, "h", None):
+            vd_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        a = np.zeros(self.n_params, np.float32)
+        self._check(vd_unet_get_params(self.h, a.ctypes.data, self.n_params), "vd_unet_get_params")
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, np.float32)
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {a.size}")
+        self._check(vd_unet_set_params(self.h, a.ctypes.data, self.n_params), "vd_unet_set_params")
+
+    def get_grads(self):
+        a = np.zeros(self.n_params, np.float32)
+        self._check(vd_unet_get_grads(self.h, a.ctypes.data, self.n_params), "vd_unet_get_grads")
+        return a
+
+    def forward(self, in6, out3):
+        """out3 (nn, 3) = net(in6 (nn, 6)), both CUDA float32 tensors."""
+        self._check(vd_unet_forward(self.h, _ptr(in6)[0], _ptr(out3)[0]), "vd_unet_forward")
+        return out3
+
+    def train_step(self, in6, target3, lr):
+        loss = ctypes.c_double()
+        self._check(vd_unet_train_step(self.h, _ptr(in6)[0], _ptr(target3)[0], float(lr), ctypes.byref(loss)),
+                    "vd_unet_train_step")
+        return loss.value
+
+    def save(self, path):
+        self._check(vd_unet_save(self.h, os.fsencode(path)), f"vd_unet_save({path})")
+
+    def load(self, path):
+        self._check(vd_unet_load(self.h, os.fsencode(path)), f"vd_unet_load({path})")
