@@ -207,6 +207,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision / surface / batched forms")
     ap.add_argument("--batch", type=int, default=32, help="lattices in the batched form (0: skip)")
+    ap.add_argument("--learned-seqs", type=int, default=2,
+                    help="test sequences (seeds 10001..) for the learned warm-start form (0: skip)")
+    ap.add_argument("--learned-frames", type=int, default=9)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -353,6 +356,29 @@ def main():
         B.close()
         for Lb in blats:
             Lb.close()
+
+    # learned warm start (config-2 surfaces in motion, 96^3): per frame from the plain
+    # trajectory's previous warp, the plain solve and the warm-started solve, each until
+    # E <= E_plain (1 + 1e-5), timed with CUDA events (frames set before timing)
+    if not args.no_variants and args.learned_seqs > 0:
+        from paper_1603_08161_b300 import learned
+        if os.path.exists(learned.WEIGHTS):
+            net = vd.UNet(synth.lattice_for(96)[0])
+            net.load(learned.WEIGHTS)
+            summ, _ = learned.evaluate(net, range(10001, 10001 + args.learned_seqs), args.learned_frames,
+                                       log=lambda m: None, render=str(dev))
+            variants["learned"] = {"value": world * summ["fps_learned"], "unit": "frames/s",
+                                   "plain_same_tolerance": world * summ["fps_plain_same_tolerance"],
+                                   "plain_full_schedule": world * summ["fps_plain"],
+                                   "speedup_vs_plain": summ["fps_learned"] / summ["fps_plain_same_tolerance"],
+                                   **{k: summ[k] for k in ("frames", "gn_mean_learned", "gn_mean_plain_same_tolerance",
+                                                           "prediction_used", "fallbacks")},
+                                   "sequences": f"seeds 10001-{10000 + args.learned_seqs}, "
+                                                f"{args.learned_frames} frames each",
+                                   "tolerance": "E <= E_plain (1 + 1e-5)"}
+            net.close()
+        else:
+            variants["learned"] = {"unavailable": "no trained weights file"}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timing
     h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()

@@ -299,13 +299,16 @@ vd_status vd_unet_get_params(vd_unet *net, float *host, int n);
 vd_status vd_unet_set_params(vd_unet *net, const float *host, int n);
 /* Gradients of the loss of the last vd_unet_train_step, same layout (host array). */
 vd_status vd_unet_get_grads(vd_unet *net, float *host, int n);
-/* out3 = net(in6); synchronous / enqueued on cuda_stream (NULL = the handle's stream). */
+/* out3 = net(in6) (the output layer in FP32); synchronous / enqueued on cuda_stream
+ * (NULL = the handle's stream). */
 vd_status vd_unet_forward(vd_unet *net, const float *in6, float *out3);
 vd_status vd_unet_forward_async(vd_unet *net, const float *in6, float *out3, void *cuda_stream);
-/* One Adam step on mean((net(in6) - target3)^2) with learning rate lr (lr = 0: loss
- * and gradients only); `loss` (host, may be NULL) gets the loss before the step. */
-vd_status vd_unet_train_step(vd_unet *net, const float *in6, const float *target3, float lr,
-                             double *loss);
+/* One Adam step with learning rate lr (lr = 0: loss and gradients only) on
+ *     loss = sum_i w_i |net(in6)_i - target3_i|^2 / (3 n),
+ * w_i = 1 + surface_weight (>= 0) at nodes whose gradient input (channels 3-5) is not
+ * all zero, else 1; `loss` (host, may be NULL) gets the loss before the step. */
+vd_status vd_unet_train_step(vd_unet *net, const float *in6, const float *target3,
+                             float surface_weight, float lr, double *loss);
 /* Parameters to / from a file: "VDUNET01", int32 layer count, int32 Cin[], int32 Cout[],
  * int32 parameter count, FP32 parameters, all little-endian.  A file whose shapes do
  * not match gives VD_ERR_INVALID_ARG. */

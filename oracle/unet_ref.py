@@ -13,7 +13,8 @@ start), written with numpy in double precision, and the hand-derived backward pa
   e2 = relu(b2(relu(a2(pool(e1)))))   cat2 = [up(e3), e2]
   e3 = relu(b3(relu(a3(pool(e2)))))   d2 = relu(d2c(relu(c2(cat2))))
   out = head(relu(d1c(relu(c1(cat1)))))
-  loss = mean over nodes and the 3 channels of (out - target)^2.
+  loss = sum over nodes i of w_i |out_i - target_i|^2 / (3 n), with w_i = 1 + lambda at
+      nodes whose gradient input (channels 3-5) is not all zero, else 1.
 
 Parity status: pinned.  tests/test_unet_ref.py checks the convolution against
 scipy.ndimage.correlate, pooling and up-sampling against closed forms, the parameter
@@ -128,14 +129,20 @@ def forward(p, x):
     return a["out"], a
 
 
-def loss(out, target):
-    return float(np.mean((out - target) ** 2))
+def node_weights(x, surface_weight):
+    """w_i = 1 + surface_weight where the gradient input (channels 3-5) is not all zero."""
+    return 1.0 + surface_weight * np.any(x[..., 3:6] != 0, axis=-1, keepdims=True)
 
 
-def backward(p, a, target):
+def loss(out, target, w=1.0):
+    """sum_i w_i |out_i - target_i|^2 / (3 n)."""
+    return float(np.mean(w * (out - target) ** 2))
+
+
+def backward(p, a, target, w=1.0):
     """Gradients of the loss with respect to every parameter: {name: (gw, gb)}."""
     g = {}
-    gout = 2.0 * (a["out"] - target) / a["out"].size
+    gout = 2.0 * w * (a["out"] - target) / a["out"].size
 
     def layer(name, x_in, gy, y_relu=None):
         if y_relu is not None:

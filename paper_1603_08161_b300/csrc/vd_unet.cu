@@ -56,10 +56,11 @@ __host__ __device__ inline size_t vox(const View &t, int z, int y, int x) {
 // ------------------------------------------------------------------ kernels
 
 // out[..., 0:cout_real) = act(conv3x3x3(in) + bias): one warp per 16-voxel row tile and
-// all NF x 16 output channels.  in.nc and the weights' Cin are multiples of 16.
+// all NF x 16 output channels.  in.nc and the weights' Cin are multiples of 16.  With
+// outf set, the result goes to outf[cout_real * node + co] in FP32 instead (the head).
 template <int NF>
 __global__ void __launch_bounds__(128) k_conv3d(View in, const bf16 *__restrict__ Wt, const float *__restrict__ bias,
-                                                View out, int cout_real, int relu) {
+                                                View out, int cout_real, int relu, float *__restrict__ outf) {
     __shared__ __align__(32) float tile[4][16 * 16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int xt_n = (out.W + 15) / 16;
@@ -95,11 +96,86 @@ __global__ void __launch_bounds__(128) k_conv3d(View in, const bf16 *__restrict_
             if (x < out.W && co < cout_real) {
                 float v = tile[warp][e] + (bias ? bias[co] : 0.f);
                 if (relu) v = fmaxf(v, 0.f);
-                out.p[vox(out, z, y, x) * out.C + co] = __float2bfloat16_rn(v);
+                if (outf) outf[((size_t)(z * out.H + y) * out.W + x) * cout_real + co] = v;
+                else out.p[vox(out, z, y, x) * out.C + co] = __float2bfloat16_rn(v);
             }
         }
         __syncwarp();
     }
+}
+
+// The same convolution with the input staged in shared memory, for rows of at most
+// 16 XT voxels: a CTA of 4 warps owns the output rows (z, y0 .. y0+3), whole in x.  For
+// each 16-channel slab of the input it stages the 3 x 6 input rows around them (x from -1
+// to 16 XT, zero outside the volume); each warp then runs the 27 taps over the XT
+// 16-voxel tiles of its row, loading every weight fragment once per tap for all XT tiles.
+constexpr int kRowsPerCta = 4;
+__host__ __device__ constexpr int rows_smem_bytes(int XT) { return 18 * (16 * XT + 2) * 32; }
+
+template <int NF, int XT>
+__global__ void __launch_bounds__(128) k_conv3d_rows(View in, const bf16 *__restrict__ Wt,
+                                                     const float *__restrict__ bias, View out, int cout_real,
+                                                     int relu, float *__restrict__ outf) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(32) float tile[4][16 * 16];
+    bf16 *slab = reinterpret_cast<bf16 *>(smraw);  // [3 planes][6 rows][RW voxels][16 channels]
+    constexpr int RW = 16 * XT + 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nyb = (out.H + kRowsPerCta - 1) / kRowsPerCta;
+    const int z = blockIdx.x / nyb, y0 = (blockIdx.x - z * nyb) * kRowsPerCta;
+    const int y = y0 + warp;
+    const int CoutP = NF * 16;
+    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[XT][NF];
+#pragma unroll
+    for (int t = 0; t < XT; t++)
+#pragma unroll
+        for (int j = 0; j < NF; j++) wmma::fill_fragment(acc[t][j], 0.f);
+    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
+    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> b[NF];
+    for (int k0 = 0; k0 < in.nc; k0 += 16) {
+        __syncthreads();  // the previous slab is consumed
+        for (int i = threadIdx.x; i < 18 * RW * 2; i += blockDim.x) {
+            const int v = i >> 1, half = i & 1;
+            const int xr = v % RW, rr = v / RW;
+            const int zz = z - 1 + rr / 6, yy = y0 - 1 + rr % 6, xx = xr - 1;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (zz <= in.D && yy <= in.H && xx <= in.W)  // -1 and D / H / W are the zero halo
+                val = *reinterpret_cast<const uint4 *>(in.p + vox(in, zz, yy, xx) * in.C + k0 + 8 * half);
+            *reinterpret_cast<uint4 *>(slab + (size_t)v * 16 + 8 * half) = val;
+        }
+        __syncthreads();
+        for (int tap = 0; tap < 27; tap++) {
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+            for (int j = 0; j < NF; j++)
+                wmma::load_matrix_sync(b[j], Wt + ((size_t)tap * in.nc + k0) * CoutP + 16 * j, CoutP);
+            const bf16 *arow = slab + ((size_t)((dz + 1) * 6 + warp + 1 + dy) * RW + dx + 1) * 16;
+#pragma unroll
+            for (int t = 0; t < XT; t++) {
+                wmma::load_matrix_sync(a, arow + t * 256, 16);
+#pragma unroll
+                for (int j = 0; j < NF; j++) wmma::mma_sync(acc[t][j], a, b[j], acc[t][j]);
+            }
+        }
+    }
+    if (y >= out.H) return;
+#pragma unroll
+    for (int t = 0; t < XT; t++)
+#pragma unroll
+        for (int j = 0; j < NF; j++) {
+            wmma::store_matrix_sync(tile[warp], acc[t][j], 16, wmma::mem_row_major);
+            __syncwarp();
+            for (int e = lane; e < 256; e += 32) {
+                const int x = 16 * t + (e >> 4), co = 16 * j + (e & 15);
+                if (x < out.W && co < cout_real) {
+                    float v = tile[warp][e] + (bias ? bias[co] : 0.f);
+                    if (relu) v = fmaxf(v, 0.f);
+                    if (outf) outf[((size_t)(z * out.H + y) * out.W + x) * cout_real + co] = v;
+                    else out.p[vox(out, z, y, x) * out.C + co] = __float2bfloat16_rn(v);
+                }
+            }
+            __syncwarp();
+        }
 }
 
 // dW[tap][ci][co] += sum_v X[v + off(tap)][ci] dY[v][co] over this block's voxel tiles;
@@ -138,114 +214,175 @@ __global__ void __launch_bounds__(128) k_wgrad(View X, View dY, float *__restric
     }
 }
 
-// db[co] += sum_v dY[v][co]
-__global__ void k_bias_grad(View dY, int cout_real, float *__restrict__ db) {
-    const long n = (long)dY.D * dY.H * dY.W;
-    for (int co = 0; co < cout_real; co++) {
-        float s = 0.f;
-        for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-            const int x = (int)(i % dY.W), y = (int)((i / dY.W) % dY.H), z = (int)(i / ((long)dY.W * dY.H));
-            s += __bfloat162float(dY.p[vox(dY, z, y, x) * dY.C + co]);
-        }
+// Element-wise passes walk (voxel, 8-channel chunk) items with 16-byte loads and
+// stores; views' channel offsets and counts are multiples of 8 (16-byte aligned chunks).
+__device__ __forceinline__ void ld8(const bf16 *p, float f[8]) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(p);
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(&db[co], s);
+    for (int k = 0; k < 4; k++) {
+        const float2 t = __bfloat1622float2(h[k]);
+        f[2 * k] = t.x;
+        f[2 * k + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ void st8(bf16 *p, const float f[8]) {
+    uint4 v;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; k++) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+    *reinterpret_cast<uint4 *>(p) = v;
+}
+
+// item i of a view -> (z, y, x) and the chunk's first channel
+struct Item {
+    int z, y, x, c;
+};
+__device__ __forceinline__ Item item(const View &t, int i) {
+    const int nq = t.nc >> 3;
+    const int v = i / nq;
+    Item r;
+    r.c = (i - v * nq) << 3;
+    r.x = v % t.W;
+    const int r2 = v / t.W;
+    r.y = r2 % t.H;
+    r.z = r2 / t.H;
+    return r;
+}
+__device__ __forceinline__ bf16 *at(const View &t, int z, int y, int x, int c) {
+    return t.p + vox(t, z, y, x) * t.C + c;
+}
+__device__ __forceinline__ int items(const View &t) { return t.D * t.H * t.W * (t.nc >> 3); }
+
+// db[co] += sum_v dY[v][co]: the grid stride is a multiple of the chunks per voxel, so
+// each thread keeps one chunk and sums it in registers
+__global__ void k_bias_grad(View dY, int cout_real, float *__restrict__ db) {
+    const int n = items(dY), nq = dY.nc >> 3;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = i0; i < n; i += gridDim.x * blockDim.x) {
+        const Item it = item(dY, i);
+        float f[8];
+        ld8(at(dY, it.z, it.y, it.x, it.c), f);
+#pragma unroll
+        for (int k = 0; k < 8; k++) s[k] += f[k];
+    }
+    // lanes with the same chunk differ by multiples of nq (a power of two <= 8)
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        for (int o = 16; o >= nq; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if ((threadIdx.x & 31) < nq) {
+        const int c = ((i0 % nq) << 3);
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (c + k < cout_real && s[k] != 0.f) atomicAdd(&db[c + k], s[k]);
     }
 }
 
 // g *= (y > 0) over the view's channels
 __global__ void k_relu_bwd(View g, View y) {
-    const long n = (long)g.D * g.H * g.W * g.nc;
-    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % g.nc);
-        const long v = i / g.nc;
-        const int x = (int)(v % g.W), yy = (int)((v / g.W) % g.H), z = (int)(v / ((long)g.W * g.H));
-        if (!(__bfloat162float(y.p[vox(y, z, yy, x) * y.C + c]) > 0.f)) g.p[vox(g, z, yy, x) * g.C + c] = __float2bfloat16_rn(0.f);
+    const int n = items(g);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Item it = item(g, i);
+        float gv[8], yv[8];
+        ld8(at(g, it.z, it.y, it.x, it.c), gv);
+        ld8(at(y, it.z, it.y, it.x, it.c), yv);
+#pragma unroll
+        for (int k = 0; k < 8; k++) gv[k] = yv[k] > 0.f ? gv[k] : 0.f;
+        st8(at(g, it.z, it.y, it.x, it.c), gv);
     }
 }
 
-// out = 2x2x2 average of in (out has half the size); accumulate: out += instead
+// out = 2x2x2 average of in (out has half the size)
 __global__ void k_pool(View in, View out) {
-    const long n = (long)out.D * out.H * out.W * out.nc;
-    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % out.nc);
-        const long v = i / out.nc;
-        const int x = (int)(v % out.W), y = (int)((v / out.W) % out.H), z = (int)(v / ((long)out.W * out.H));
-        float s = 0.f;
-        for (int k = 0; k < 8; k++)
-            s += __bfloat162float(in.p[vox(in, 2 * z + (k >> 2), 2 * y + ((k >> 1) & 1), 2 * x + (k & 1)) * in.C + c]);
-        out.p[vox(out, z, y, x) * out.C + c] = __float2bfloat16_rn(0.125f * s);
+    const int n = items(out);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Item it = item(out, i);
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            float f[8];
+            ld8(at(in, 2 * it.z + (k >> 2), 2 * it.y + ((k >> 1) & 1), 2 * it.x + (k & 1), it.c), f);
+#pragma unroll
+            for (int e = 0; e < 8; e++) s[e] += f[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 8; e++) s[e] *= 0.125f;
+        st8(at(out, it.z, it.y, it.x, it.c), s);
     }
 }
 
 // gradient of the pooling: gin[2v + k] (+)= gout[v] / 8
 __global__ void k_pool_bwd(View gout, View gin, int accumulate) {
-    const long n = (long)gin.D * gin.H * gin.W * gin.nc;
-    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % gin.nc);
-        const long v = i / gin.nc;
-        const int x = (int)(v % gin.W), y = (int)((v / gin.W) % gin.H), z = (int)(v / ((long)gin.W * gin.H));
-        const float g = 0.125f * __bfloat162float(gout.p[vox(gout, z >> 1, y >> 1, x >> 1) * gout.C + c]);
-        bf16 *dst = gin.p + vox(gin, z, y, x) * gin.C + c;
-        *dst = __float2bfloat16_rn(accumulate ? __bfloat162float(*dst) + g : g);
+    const int n = items(gin);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Item it = item(gin, i);
+        float g[8], d[8];
+        ld8(at(gout, it.z >> 1, it.y >> 1, it.x >> 1, it.c), g);
+        bf16 *dst = at(gin, it.z, it.y, it.x, it.c);
+        if (accumulate) ld8(dst, d);
+#pragma unroll
+        for (int e = 0; e < 8; e++) g[e] = 0.125f * g[e] + (accumulate ? d[e] : 0.f);
+        st8(dst, g);
     }
 }
 
 // out (twice the size) = nearest-neighbour copy of in
 __global__ void k_upsample(View in, View out) {
-    const long n = (long)out.D * out.H * out.W * out.nc;
-    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % out.nc);
-        const long v = i / out.nc;
-        const int x = (int)(v % out.W), y = (int)((v / out.W) % out.H), z = (int)(v / ((long)out.W * out.H));
-        out.p[vox(out, z, y, x) * out.C + c] = in.p[vox(in, z >> 1, y >> 1, x >> 1) * in.C + c];
+    const int n = items(out);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Item it = item(out, i);
+        *reinterpret_cast<uint4 *>(at(out, it.z, it.y, it.x, it.c)) =
+            *reinterpret_cast<const uint4 *>(at(in, it.z >> 1, it.y >> 1, it.x >> 1, it.c));
     }
 }
 
 // gradient of the up-sampling: gin[v] = sum of the 8 gout it was copied to
 __global__ void k_upsample_bwd(View gout, View gin) {
-    const long n = (long)gin.D * gin.H * gin.W * gin.nc;
-    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % gin.nc);
-        const long v = i / gin.nc;
-        const int x = (int)(v % gin.W), y = (int)((v / gin.W) % gin.H), z = (int)(v / ((long)gin.W * gin.H));
-        float s = 0.f;
-        for (int k = 0; k < 8; k++)
-            s += __bfloat162float(gout.p[vox(gout, 2 * z + (k >> 2), 2 * y + ((k >> 1) & 1), 2 * x + (k & 1)) * gout.C + c]);
-        gin.p[vox(gin, z, y, x) * gin.C + c] = __float2bfloat16_rn(s);
+    const int n = items(gin);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Item it = item(gin, i);
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            float f[8];
+            ld8(at(gout, 2 * it.z + (k >> 2), 2 * it.y + ((k >> 1) & 1), 2 * it.x + (k & 1), it.c), f);
+#pragma unroll
+            for (int e = 0; e < 8; e++) s[e] += f[e];
+        }
+        st8(at(gin, it.z, it.y, it.x, it.c), s);
     }
 }
 
-// input buffer (16 channels, 6 used) from node-major float arrays (n x 6)
+// input buffer (16 channels, 6 used, the rest zero) from node-major floats (n x 6)
 __global__ void k_pack_input(const float *__restrict__ in6, View x) {
-    const long n = (long)x.D * x.H * x.W;
-    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int xx = (int)(i % x.W), y = (int)((i / x.W) % x.H), z = (int)(i / ((long)x.W * x.H));
-        bf16 *d = x.p + vox(x, z, y, xx) * x.C;
-        for (int c = 0; c < 6; c++) d[c] = __float2bfloat16_rn(in6[6 * i + c]);
+    const int n = x.D * x.H * x.W;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int xx = i % x.W, r = i / x.W;
+        const float2 a = *reinterpret_cast<const float2 *>(in6 + 6 * (size_t)i);
+        const float2 b = *reinterpret_cast<const float2 *>(in6 + 6 * (size_t)i + 2);
+        const float2 c = *reinterpret_cast<const float2 *>(in6 + 6 * (size_t)i + 4);
+        const float f[8] = {a.x, a.y, b.x, b.y, c.x, c.y, 0.f, 0.f};
+        st8(at(x, r / x.H, r % x.H, xx, 0), f);
     }
 }
 
-__global__ void k_unpack_output(View o, float *__restrict__ out3) {
-    const long n = (long)o.D * o.H * o.W;
-    for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % o.W), y = (int)((i / o.W) % o.H), z = (int)(i / ((long)o.W * o.H));
-        const bf16 *s = o.p + vox(o, z, y, x) * o.C;
-        for (int c = 0; c < 3; c++) out3[3 * i + c] = __bfloat162float(s[c]);
-    }
-}
-
-// loss = mean |out - target|^2 over nodes and the 3 channels; gout = d loss / d out
-__global__ void k_mse(View o, const float *__restrict__ target, View go, double *loss) {
-    const long n = (long)o.D * o.H * o.W;
+// loss = sum_i w_i |out_i - target_i|^2 / (3 n) with w_i = 1 + surface_weight at nodes
+// whose data-gradient input (channels 3-5) is non-zero, else 1; gout = d loss / d out
+__global__ void k_mse(const float *__restrict__ outf, const float *__restrict__ target, const float *__restrict__ in6,
+                      float surface_weight, View go, double *loss) {
+    const long n = (long)go.D * go.H * go.W;
     const float scale = 2.f / (3.f * (float)n);
     float s = 0.f;
     for (long i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % o.W), y = (int)((i / o.W) % o.H), z = (int)(i / ((long)o.W * o.H));
+        const int x = (int)(i % go.W), y = (int)((i / go.W) % go.H), z = (int)(i / ((long)go.W * go.H));
+        const bool surf = in6[6 * i + 3] != 0.f || in6[6 * i + 4] != 0.f || in6[6 * i + 5] != 0.f;
+        const float w = surf ? 1.f + surface_weight : 1.f;
         for (int c = 0; c < 3; c++) {
-            const float d = __bfloat162float(o.p[vox(o, z, y, x) * o.C + c]) - target[3 * i + c];
-            s += d * d;
-            go.p[vox(go, z, y, x) * go.C + c] = __float2bfloat16_rn(scale * d);
+            const float d = outf[3 * i + c] - target[3 * i + c];
+            s += w * d * d;
+            go.p[vox(go, z, y, x) * go.C + c] = __float2bfloat16_rn(scale * w * d);
         }
     }
 #pragma unroll
@@ -293,6 +430,8 @@ __global__ void k_pack_weights(LayerDev L) {
     }
 }
 
+long nvox(const View &v) { return (long)v.D * v.H * v.W; }
+
 int blocks(long n, int threads = 256) {
     long b = (n + threads - 1) / threads;
     return (int)std::max<long>(1, std::min<long>(b, 148 * 8));
@@ -308,7 +447,7 @@ struct vd_unet {
     View gx, ge1a, gcat1, gp1, ge2a, gcat2, gp2, ge3a, ge3, gd2a, gd2, gd1a, gd1, gout;
     LayerDev L[kLayers];
     double *loss = nullptr;
-    float *io6 = nullptr, *io3 = nullptr;
+    float *io3 = nullptr;  // FP32 output of the training forward pass
     int step = 0;
     cudaStream_t st = nullptr;
 };
@@ -348,20 +487,34 @@ View slice(View v, int c0, int nc) {
     return v;
 }
 
-void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool dgrad) {
+void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool dgrad, float *outf = nullptr) {
     // forward: in (cinp) -> out (coutp slice); dgrad: in = grad of out (coutp) -> grad of in (cinp)
     const bf16 *w = dgrad ? L.wt : L.wf;
     const int nf = (dgrad ? L.cinp : L.coutp) / 16;
     const int creal = dgrad ? L.cinp : L.cout;
     const float *bias = dgrad ? nullptr : L.b;
-    const long tiles = (long)out.D * out.H * ((out.W + 15) / 16);
+    const int xt = (out.W + 15) / 16;
+    const int XT = xt <= 1 ? 1 : xt <= 2 ? 2 : xt <= 3 ? 3 : xt <= 6 ? 6 : 0;
+    if (XT && XT * nf <= 18) {
+        const int nb = out.D * ((out.H + kRowsPerCta - 1) / kRowsPerCta);
+        const int sm = rows_smem_bytes(XT);
+#define VD_ROWS(N, X) \
+    if (nf == N && XT == X) return k_conv3d_rows<N, X><<<nb, 128, sm, st>>>(in, w, bias, out, creal, relu, outf);
+        VD_ROWS(1, 1) VD_ROWS(1, 2) VD_ROWS(1, 3) VD_ROWS(1, 6)
+        VD_ROWS(2, 1) VD_ROWS(2, 2) VD_ROWS(2, 3) VD_ROWS(2, 6)
+        VD_ROWS(3, 1) VD_ROWS(3, 2) VD_ROWS(3, 3) VD_ROWS(3, 6)
+        VD_ROWS(4, 1) VD_ROWS(4, 2) VD_ROWS(4, 3)
+        VD_ROWS(6, 1) VD_ROWS(6, 2) VD_ROWS(6, 3)
+#undef VD_ROWS
+    }
+    const long tiles = (long)out.D * out.H * xt;
     const int nb = (int)((tiles + 3) / 4);
     switch (nf) {
-        case 1: k_conv3d<1><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
-        case 2: k_conv3d<2><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
-        case 3: k_conv3d<3><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
-        case 4: k_conv3d<4><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
-        case 6: k_conv3d<6><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu); break;
+        case 1: k_conv3d<1><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu, outf); break;
+        case 2: k_conv3d<2><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu, outf); break;
+        case 3: k_conv3d<3><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu, outf); break;
+        case 4: k_conv3d<4><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu, outf); break;
+        case 6: k_conv3d<6><<<nb, 128, 0, st>>>(in, w, bias, out, creal, relu, outf); break;
         default: break;
     }
 }
@@ -371,32 +524,31 @@ void wgrad(cudaStream_t st, View X, View dY, const LayerDev &L) {
     const long tiles = (long)dY.D * dY.H * ((dY.W + 15) / 16);
     const int slices = (int)std::max<long>(1, std::min<long>(64, (tiles + 63) / 64));
     k_wgrad<<<27 * nci * nco * slices, 128, 0, st>>>(X, dY, L.gw, L.coutp, slices);
-    k_bias_grad<<<blocks((long)dY.D * dY.H * dY.W), 256, 0, st>>>(dY, L.cout, L.gb);
+    k_bias_grad<<<blocks(nvox(dY) * dY.nc / 8), 256, 0, st>>>(dY, L.cout, L.gb);
 }
 
-long nvox(const View &v) { return (long)v.D * v.H * v.W; }
-
-void forward(vd_unet *U, cudaStream_t st) {
+// the head writes FP32 to outf (node-major, 3 per node)
+void forward(vd_unet *U, cudaStream_t st, float *outf) {
     View e1 = slice(U->cat1, 32, 16), e2 = slice(U->cat2, 64, 32);
     conv(st, U->x, U->L[A1], U->e1a, true, false);
     conv(st, U->e1a, U->L[B1], e1, true, false);
-    k_pool<<<blocks(nvox(U->p1) * 16), 256, 0, st>>>(e1, U->p1);
+    k_pool<<<blocks(nvox(U->p1) * 2), 256, 0, st>>>(e1, U->p1);
     conv(st, U->p1, U->L[A2], U->e2a, true, false);
     conv(st, U->e2a, U->L[B2], e2, true, false);
-    k_pool<<<blocks(nvox(U->p2) * 32), 256, 0, st>>>(e2, U->p2);
+    k_pool<<<blocks(nvox(U->p2) * 4), 256, 0, st>>>(e2, U->p2);
     conv(st, U->p2, U->L[A3], U->e3a, true, false);
     conv(st, U->e3a, U->L[B3], U->e3, true, false);
-    k_upsample<<<blocks(nvox(U->cat2) * 64), 256, 0, st>>>(U->e3, slice(U->cat2, 0, 64));
+    k_upsample<<<blocks(nvox(U->cat2) * 8), 256, 0, st>>>(U->e3, slice(U->cat2, 0, 64));
     conv(st, U->cat2, U->L[C2], U->d2a, true, false);
     conv(st, U->d2a, U->L[D2], U->d2, true, false);
-    k_upsample<<<blocks(nvox(U->cat1) * 32), 256, 0, st>>>(U->d2, slice(U->cat1, 0, 32));
+    k_upsample<<<blocks(nvox(U->cat1) * 4), 256, 0, st>>>(U->d2, slice(U->cat1, 0, 32));
     conv(st, U->cat1, U->L[C1], U->d1a, true, false);
     conv(st, U->d1a, U->L[D1], U->d1, true, false);
-    conv(st, U->d1, U->L[HEAD], U->out, false, false);
+    conv(st, U->d1, U->L[HEAD], U->out, false, false, outf);
 }
 
 void relu_bwd(cudaStream_t st, View g, View y) {
-    k_relu_bwd<<<blocks(nvox(g) * g.nc), 256, 0, st>>>(g, y);
+    k_relu_bwd<<<blocks(nvox(g) * g.nc / 8), 256, 0, st>>>(g, y);
 }
 
 // gout must hold d loss / d out; fills every layer's gw, gb
@@ -417,7 +569,7 @@ void backward(vd_unet *U, cudaStream_t st) {
     wgrad(st, U->cat1, U->gd1a, U->L[C1]);
     conv(st, U->gd1a, U->L[C1], U->gcat1, false, true);  // [d up(d2), d e1 (skip)]
     // decoder level 2
-    k_upsample_bwd<<<blocks(nvox(U->gd2) * 32), 256, 0, st>>>(slice(U->gcat1, 0, 32), U->gd2);
+    k_upsample_bwd<<<blocks(nvox(U->gd2) * 4), 256, 0, st>>>(slice(U->gcat1, 0, 32), U->gd2);
     relu_bwd(st, U->gd2, U->d2);
     wgrad(st, U->d2a, U->gd2, U->L[D2]);
     conv(st, U->gd2, U->L[D2], U->gd2a, false, true);
@@ -425,7 +577,7 @@ void backward(vd_unet *U, cudaStream_t st) {
     wgrad(st, U->cat2, U->gd2a, U->L[C2]);
     conv(st, U->gd2a, U->L[C2], U->gcat2, false, true);  // [d up(e3), d e2 (skip)]
     // bottleneck
-    k_upsample_bwd<<<blocks(nvox(U->ge3) * 64), 256, 0, st>>>(slice(U->gcat2, 0, 64), U->ge3);
+    k_upsample_bwd<<<blocks(nvox(U->ge3) * 8), 256, 0, st>>>(slice(U->gcat2, 0, 64), U->ge3);
     relu_bwd(st, U->ge3, U->e3);
     wgrad(st, U->e3a, U->ge3, U->L[B3]);
     conv(st, U->ge3, U->L[B3], U->ge3a, false, true);
@@ -433,7 +585,7 @@ void backward(vd_unet *U, cudaStream_t st) {
     wgrad(st, U->p2, U->ge3a, U->L[A3]);
     conv(st, U->ge3a, U->L[A3], U->gp2, false, true);
     // encoder level 2: d e2 = skip part + pooling part
-    k_pool_bwd<<<blocks(nvox(ge2) * 32), 256, 0, st>>>(U->gp2, ge2, 1);
+    k_pool_bwd<<<blocks(nvox(ge2) * 4), 256, 0, st>>>(U->gp2, ge2, 1);
     relu_bwd(st, ge2, e2);
     wgrad(st, U->e2a, ge2, U->L[B2]);
     conv(st, ge2, U->L[B2], U->ge2a, false, true);
@@ -441,7 +593,7 @@ void backward(vd_unet *U, cudaStream_t st) {
     wgrad(st, U->p1, U->ge2a, U->L[A2]);
     conv(st, U->ge2a, U->L[A2], U->gp1, false, true);
     // encoder level 1
-    k_pool_bwd<<<blocks(nvox(ge1) * 16), 256, 0, st>>>(U->gp1, ge1, 1);
+    k_pool_bwd<<<blocks(nvox(ge1) * 2), 256, 0, st>>>(U->gp1, ge1, 1);
     relu_bwd(st, ge1, e1);
     wgrad(st, U->e1a, ge1, U->L[B1]);
     conv(st, ge1, U->L[B1], U->ge1a, false, true);
@@ -500,8 +652,14 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
         cudaMemcpy(L.w, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
         k_pack_weights<<<blocks((long)np), 256>>>(L);
     }
-    ok = ok && ualloc(U, &U->loss, 1) && ualloc(U, &U->io6, (size_t)6 * D * H * W) &&
-         ualloc(U, &U->io3, (size_t)3 * D * H * W);
+    ok = ok && ualloc(U, &U->loss, 1) && ualloc(U, &U->io3, (size_t)3 * D * H * W);
+    // the staged convolutions of 96-voxel rows take more than the default 48 KB
+    ok = ok && cudaFuncSetAttribute(k_conv3d_rows<1, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    rows_smem_bytes(6)) == cudaSuccess &&
+         cudaFuncSetAttribute(k_conv3d_rows<2, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              rows_smem_bytes(6)) == cudaSuccess &&
+         cudaFuncSetAttribute(k_conv3d_rows<3, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              rows_smem_bytes(6)) == cudaSuccess;
     if (!ok || cudaStreamCreateWithFlags(&U->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         vd_unet_destroy(U);
@@ -566,8 +724,7 @@ vd_status vd_unet_forward_async(vd_unet *U, const float *in6, float *out3, void 
     cudaStream_t st = stream ? (cudaStream_t)stream : U->st;
     const long n = (long)U->D * U->H * U->W;
     k_pack_input<<<blocks(n), 256, 0, st>>>(in6, U->x);
-    forward(U, st);
-    k_unpack_output<<<blocks(n), 256, 0, st>>>(U->out, out3);
+    forward(U, st, out3);
     return cudaGetLastError() == cudaSuccess ? VD_OK : VD_ERR_CUDA;
 }
 
@@ -579,14 +736,15 @@ vd_status vd_unet_forward(vd_unet *U, const float *in6, float *out3) {
 
 // One Adam step on the mean squared error between network(in6) and target3 (device
 // arrays); lr = 0 only computes the loss and the gradients.
-vd_status vd_unet_train_step(vd_unet *U, const float *in6, const float *target3, float lr, double *loss) {
-    if (!U || !in6 || !target3) return VD_ERR_INVALID_ARG;
+vd_status vd_unet_train_step(vd_unet *U, const float *in6, const float *target3, float surface_weight, float lr,
+                             double *loss) {
+    if (!U || !in6 || !target3 || !(surface_weight >= 0.f)) return VD_ERR_INVALID_ARG;
     cudaStream_t st = U->st;
     const long n = (long)U->D * U->H * U->W;
     k_pack_input<<<blocks(n), 256, 0, st>>>(in6, U->x);
-    forward(U, st);
+    forward(U, st, U->io3);
     cudaMemsetAsync(U->loss, 0, sizeof(double), st);
-    k_mse<<<blocks(n), 256, 0, st>>>(U->out, target3, U->gout, U->loss);
+    k_mse<<<blocks(n), 256, 0, st>>>(U->io3, target3, in6, surface_weight, U->gout, U->loss);
     backward(U, st);
     if (lr > 0.f) {
         U->step++;

@@ -26,7 +26,7 @@ import math
 import numpy as np
 
 __all__ = ["Frame", "sphere_frame", "capsule_frame", "config1", "config2",
-           "batch_frames", "sequence_frames", "lattice_for", "plane_frame"]
+           "batch_frames", "sequence_frames", "sequences", "lattice_for", "plane_frame"]
 
 
 @dataclasses.dataclass
@@ -292,13 +292,79 @@ class _Capsules:
         return y
 
 
+def _capsules_torch(caps, which, dirs, device):
+    """The same sphere tracing as _sphere_trace, of the posed or canonical capsules, in
+    float64 torch on ``device`` (every ray takes every step; a ray that has converged or
+    left the range keeps its z, which is what the numpy version's compaction does)."""
+    import torch
+    T = lambda a: torch.as_tensor(np.asarray(a, np.float64), device=device)
+    d = T(dirs)
+    parts = []
+    for k in range(3):
+        Q = caps.Q[k] if which == "posed" else np.eye(3)
+        parts.append((T(caps.piv[k]), T(Q), T(caps.a[k]), T(caps.b[k]), float(caps.r[k])))
+
+    def sdf(y):
+        out = None
+        for piv, Q, a, b, r in parts:
+            x = piv + (y - piv) @ Q
+            ab = b - a
+            t = (((x - a) @ ab) / (ab @ ab)).clamp(0.0, 1.0)
+            dist = torch.linalg.norm(x - (a + t[:, None] * ab), dim=1) - r
+            out = dist if out is None else torch.minimum(out, dist)
+        return out
+
+    z0, z1, eps = 0.3, 1.6, 2e-6
+    L = torch.linalg.norm(d, dim=1)
+    z = torch.full((d.shape[0],), z0, dtype=torch.float64, device=device)
+    live = torch.ones(d.shape[0], dtype=torch.bool, device=device)
+    conv = torch.zeros_like(live)
+    for _ in range(160):
+        dist = sdf(z[:, None] * d)
+        done = live & (dist < eps)
+        conv |= done
+        step = live & ~done
+        z = torch.where(step, z + dist / L, z)
+        live = step & (z < z1)
+    lo = z
+    hi = lo + 4 * eps / L + 1e-6
+    for _ in range(8):
+        out = conv & (sdf(hi[:, None] * d) > 0)
+        hi = torch.where(out, hi + 1e-5, hi)
+    conv &= sdf(hi[:, None] * d) <= 0
+    for _ in range(40):
+        m = 0.5 * (lo + hi)
+        pos = sdf(m[:, None] * d) > 0
+        lo = torch.where(pos, m, lo)
+        hi = torch.where(pos, hi, m)
+    zz = torch.where(conv, 0.5 * (lo + hi), torch.zeros_like(lo))
+    return zz.cpu().numpy(), conv.cpu().numpy()
+
+
+def _trace_capsules(caps, which, dirs, device):
+    if device is None:
+        return _sphere_trace(caps.posed_sdf if which == "posed" else caps.canon_sdf, dirs, 0.3, 1.6)
+    return _capsules_torch(caps, which, dirs, device)
+
+
+def _canonical_capsules(caps, dirs, device=None):
+    """Canonical (unbent) surface samples seen by the camera: points, normals, segment."""
+    zc, hitc = _trace_capsules(caps, "canon", dirs, device)
+    src = zc[hitc, None] * dirs[hitc]
+    nrm, seg = caps.canon_normal_and_segment(src)
+    return src, nrm, seg
+
+
 def capsule_frame(W=640, H=480, f=525.0, n=96, seed=0, angles=None, axes=None, radii=None,
                   rel_noise=0.005, invalid_frac=0.05, n_sparse=300, outlier_frac=0.05,
-                  outlier_max=0.10, sparse_noise=1e-3, name="capsules"):
+                  outlier_max=0.10, sparse_noise=1e-3, name="capsules", canon=None, device=None):
     """Three chained capsules (radii U(5, 15) cm) bent at two joints by U(10, 30) degrees.
 
     Depth noise N(0, (rel_noise * z)^2), ``invalid_frac`` of pixels dropped, sparse pairs
     with ``outlier_frac`` outliers displaced by a uniform length in [0, outlier_max] m.
+    ``canon`` = the canonical samples of the same capsules (reused along a sequence; the
+    result is the same as without it).  ``device`` = a torch CUDA device: trace the rays
+    there (same algorithm in float64; depths agree with the numpy trace to rounding).
     """
     rng = np.random.default_rng(seed)
     if radii is None:
@@ -312,14 +378,12 @@ def capsule_frame(W=640, H=480, f=525.0, n=96, seed=0, angles=None, axes=None, r
     K = _intrinsics(W, H, f)
     dirs = _rays(W, H, K)
 
-    z, hit = _sphere_trace(caps.posed_sdf, dirs, 0.3, 1.6)
+    z, hit = _trace_capsules(caps, "posed", dirs, device)
     z = z + rng.normal(0.0, 1.0, z.shape) * rel_noise * z
     z[rng.random(z.shape) < invalid_frac] = 0.0
     depth = np.where(hit, z, 0.0).reshape(H, W)
 
-    zc, hitc = _sphere_trace(caps.canon_sdf, dirs, 0.3, 1.6)
-    src = zc[hitc, None] * dirs[hitc]
-    nrm, seg = caps.canon_normal_and_segment(src)
+    src, nrm, seg = canon if canon is not None else _canonical_capsules(caps, dirs, device)
 
     m = min(n_sparse, src.shape[0])
     pick = rng.choice(src.shape[0], size=m, replace=False) if m > 0 else np.zeros(0, int)
@@ -404,14 +468,16 @@ def _batch_frame(k, base_seed):
     return out[0]
 
 
-def sequence_frames(seed, frames=64, n=96, W=640, H=480, f=525.0, max_step_deg=5.0):
+def sequence_frames(seed, frames=64, n=96, W=640, H=480, f=525.0, max_step_deg=5.0, device=None):
     """Config-2 surfaces whose two bend angles random-walk by U(-5, 5) degrees per frame
-    (reflected into [0, 30]); frame t's source samples are the canonical surface."""
+    (reflected into [0, 30]); frame t's source samples are the canonical surface.
+    ``device``: trace on that torch CUDA device (see capsule_frame)."""
     rng = np.random.default_rng(seed)
     radii = rng.uniform(0.05, 0.15, 3)
     phis = rng.uniform(0.0, 2 * math.pi, 2)
     axes = [np.array([0.0, math.cos(p), math.sin(p)]) for p in phis]
     ang = rng.uniform(10.0, 30.0, 2)
+    canon = _canonical_capsules(_Capsules(radii, np.deg2rad(ang), axes), _rays(W, H, _intrinsics(W, H, f)), device)
     out = []
     for t in range(frames):
         if t > 0:
@@ -420,5 +486,26 @@ def sequence_frames(seed, frames=64, n=96, W=640, H=480, f=525.0, max_step_deg=5
             ang = np.where(ang > 30.0, 60.0 - ang, ang)
         out.append(capsule_frame(W=W, H=H, f=f, n=n, seed=int(rng.integers(0, 2**31 - 1)),
                                  angles=np.deg2rad(ang), axes=axes, radii=radii,
-                                 name=f"seq{seed}-{t}"))
+                                 name=f"seq{seed}-{t}", canon=canon, device=device))
     return out
+
+
+def sequences(seeds, frames=64, workers=1, device=None, **kw):
+    """sequence_frames for several seeds, in a spawned process pool when workers > 1
+    (or traced on a torch CUDA ``device`` in this process); yields (seed, frames) in the
+    order of ``seeds``."""
+    seeds = list(seeds)
+    if device is not None:
+        for s in seeds:
+            yield s, sequence_frames(s, frames, device=device, **kw)
+        return
+    if workers <= 1:
+        for s in seeds:
+            yield s, sequence_frames(s, frames, **kw)
+        return
+    import functools
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(workers, len(seeds))) as pool:
+        fn = functools.partial(sequence_frames, frames=frames, **kw)
+        for s, fr in zip(seeds, pool.imap(fn, seeds)):
+            yield s, fr

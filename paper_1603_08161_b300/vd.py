@@ -114,7 +114,7 @@ _SIGS = {
     "vd_unet_get_grads": [_P, _P, _I],
     "vd_unet_forward": [_P, _P, _P],
     "vd_unet_forward_async": [_P, _P, _P, _P],
-    "vd_unet_train_step": [_P, _P, _P, ctypes.c_float, _PD],
+    "vd_unet_train_step": [_P, _P, _P, ctypes.c_float, ctypes.c_float, _PD],
     "vd_unet_save": [_P, ctypes.c_char_p],
     "vd_unet_load": [_P, ctypes.c_char_p],
     "vd_warm_features": [_P, ctypes.POINTER(vd_solve_params), _P, _I],
@@ -238,10 +238,17 @@ class Lattice:
         return rep.as_dict()
 
     def get_warp(self, out_u=None, out_R=None):
+        """(u, R): numpy arrays, or the given CUDA tensors (out_R None with a CUDA out_u:
+        u only)."""
         u = np.zeros((self.nn, 3), np.float32) if out_u is None else out_u
-        R = np.zeros((self.nn, 9), np.float32) if out_R is None else out_R
         pu, mem = _ptr(u)
-        pr, _ = _ptr(R)
+        if out_R is None and mem == VD_MEM_DEVICE:
+            R = None
+        else:
+            R = np.zeros((self.nn, 9), np.float32) if out_R is None else out_R
+        pr, mr = _ptr(R)
+        if R is not None and mr != mem:
+            raise ValueError("u and R must both be host arrays or both CUDA tensors")
         self._check(vd_get_warp(self.h, pu, pr, mem))
         if isinstance(R, np.ndarray):
             R = R.reshape(self.nn, 3, 3)
@@ -250,6 +257,8 @@ class Lattice:
     def set_warp(self, u=None, R=None):
         """u (nn, 3) and R (nn, 9) or None: numpy (host) or CUDA tensors (device)."""
         dev = any(a is not None and hasattr(a, "is_cuda") and a.is_cuda for a in (u, R))
+        if dev and not all(a is None or (hasattr(a, "is_cuda") and a.is_cuda) for a in (u, R)):
+            raise ValueError("u and R must both be host arrays or both CUDA tensors")
         conv = (lambda a: a.contiguous()) if dev else (lambda a: np.ascontiguousarray(a, np.float32))
         uu = None if u is None else conv(u)
         RR = None if R is None else conv(R)
@@ -457,10 +466,10 @@ class UNet:
         self._check(vd_unet_forward(self.h, _ptr(in6)[0], _ptr(out3)[0]), "vd_unet_forward")
         return out3
 
-    def train_step(self, in6, target3, lr):
+    def train_step(self, in6, target3, lr, surface_weight=0.0):
         loss = ctypes.c_double()
-        self._check(vd_unet_train_step(self.h, _ptr(in6)[0], _ptr(target3)[0], float(lr), ctypes.byref(loss)),
-                    "vd_unet_train_step")
+        self._check(vd_unet_train_step(self.h, _ptr(in6)[0], _ptr(target3)[0], float(surface_weight), float(lr),
+                                       ctypes.byref(loss)), "vd_unet_train_step")
         return loss.value
 
     def save(self, path):

@@ -1,7 +1,8 @@
 """The warm-start U-Net's CUDA kernels (through the C ABI) against the FP64 reference.
 
 The library computes in BF16 (weights, activations and stored gradients rounded to
-8 significant bits, relative step 2^-8) with FP32 accumulation; the reference computes
+8 significant bits, relative step 2^-8) with FP32 accumulation and an FP32 output
+layer; the reference computes
 the same network in FP64 from the same BF16-rounded weights and input.  Eleven
 layers of rounding give relative errors near 1e-2 in the output and a few 1e-2 in the
 gradients; the checks allow 3e-2 (output, loss) and 6e-2 (each layer's gradient), far
@@ -47,7 +48,9 @@ def _case(dims, seed):
     return flat, x, t
 
 
-DIMS = [(16, 16, 16), (12, 8, 20)]  # the second has ragged 16-voxel row tiles
+# (12, 8, 20) has ragged 16-voxel row tiles; (96, 8, 8) has 96-, 48- and 24-voxel rows
+# (the shared-memory staged convolution with 6, 3 and 2 tiles per row)
+DIMS = [(16, 16, 16), (12, 8, 20), (96, 8, 8)]
 
 
 @pytest.mark.parametrize("dims", DIMS)
@@ -67,19 +70,23 @@ def test_forward_matches_reference(env, dims):
 
 
 @pytest.mark.parametrize("dims", DIMS)
-def test_gradients_match_reference(env, dims):
+@pytest.mark.parametrize("lam", [0.0, 4.0])
+def test_gradients_match_reference(env, dims, lam):
     vd, torch = env
     nx, ny, nz = dims
     flat, x, t = _case(dims, 2)
+    x[np.random.default_rng(8).random(x.shape[0]) < 0.6, 3:] = 0.0  # nodes without data gradient
     net = vd.UNet(dims, seed=0)
     net.set_params(flat)
-    loss = net.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), 0.0)
+    loss = net.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), 0.0, surface_weight=lam)
     g = net.get_grads()
     p = U.unpack(bf16(flat))
-    out, acts = U.forward(p, bf16(x).reshape(nz, ny, nx, 6))
+    xv = bf16(x).reshape(nz, ny, nx, 6)
+    w = U.node_weights(xv, lam)
+    out, acts = U.forward(p, xv)
     tt = t.reshape(nz, ny, nx, 3).astype(np.float64)
-    assert abs(loss - U.loss(out, tt)) / U.loss(out, tt) < 3e-2
-    gref = U.backward(p, acts, tt)
+    assert abs(loss - U.loss(out, tt, w)) / U.loss(out, tt, w) < 3e-2
+    gref = U.backward(p, acts, tt, w)
     gg = U.unpack(g)
     for name, _, _ in U.LAYERS:
         assert _rel(gg[name][0], gref[name][0]) < 6e-2, name

@@ -48,20 +48,30 @@ def tiny():
     rng = np.random.default_rng(3)
     flat = U.he_params(5)
     x = rng.normal(size=(4, 4, 4, 6))
+    x[rng.random((4, 4, 4)) < 0.5, 3:] = 0.0  # nodes without data gradient
     t = rng.normal(size=(4, 4, 4, 3)) * 0.3
     return flat, x, t
 
 
-def _loss(flat, x, t):
+def test_node_weights():
+    x = np.zeros((1, 1, 3, 6))
+    x[0, 0, 1, 4] = 2.0
+    x[0, 0, 2, :3] = 1.0
+    np.testing.assert_array_equal(U.node_weights(x, 4.0)[0, 0, :, 0], [1.0, 5.0, 1.0])
+
+
+def _loss(flat, x, t, w=1.0):
     out, _ = U.forward(U.unpack(flat), x)
-    return U.loss(out, t)
+    return U.loss(out, t, w)
 
 
-def test_gradients_match_finite_differences(tiny):
+@pytest.mark.parametrize("lam", [0.0, 4.0])
+def test_gradients_match_finite_differences(tiny, lam):
     flat, x, t = tiny
+    w = U.node_weights(x, lam)
     p = U.unpack(flat)
     out, acts = U.forward(p, x)
-    g = U.pack(U.backward(p, acts, t))
+    g = U.pack(U.backward(p, acts, t, w))
     rng = np.random.default_rng(4)
     # a few entries of every layer's weights and biases
     idx, k = [], 0
@@ -75,7 +85,7 @@ def test_gradients_match_finite_differences(tiny):
         fp[i] += eps
         fm = flat.copy()
         fm[i] -= eps
-        fd = (_loss(fp, x, t) - _loss(fm, x, t)) / (2 * eps)
+        fd = (_loss(fp, x, t, w) - _loss(fm, x, t, w)) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])
 
 
