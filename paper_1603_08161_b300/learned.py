@@ -220,7 +220,8 @@ def summarize(rec):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("cmd", choices=["train", "eval"])
+    ap.add_argument("cmd", choices=["train", "eval", "time"])
+    ap.add_argument("--iters", type=int, default=10, help="time: forward passes and training steps timed")
     ap.add_argument("--seeds", default=None)
     ap.add_argument("--frames", type=int, default=17)
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
@@ -241,7 +242,27 @@ def main(argv=None):
             logf.write(msg + "\n")
             logf.flush()
 
-    if a.cmd == "train":
+    if a.cmd == "time":  # the network alone at 96^3 (random input), CUDA-event timed
+        import torch
+        from . import vd
+        dims = synth.lattice_for(96)[0]
+        net = vd.UNet(dims, seed=1)
+        n = int(np.prod(dims))
+        x = torch.randn((n, 6), device="cuda")
+        t = 0.1 * torch.randn((n, 3), device="cuda")
+        o = torch.empty((n, 3), device="cuda")
+        out = {}
+        for name, fn in (("forward_ms", lambda: net.forward(x, o)), ("train_step_ms", lambda: net.train_step(x, t, 1e-4))):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(a.iters):
+                fn()
+            torch.cuda.synchronize()
+            out[name] = (time.perf_counter() - t0) * 1e3 / a.iters
+        log(json.dumps(out))
+    elif a.cmd == "train":
         seeds = _seeds(a.seeds or "1-96")
         X, T, dims = collect(seeds, a.frames, a.workers, a.max_samples, log, None if a.cpu_render else "cuda")
         log(json.dumps({"samples": len(X)}))
