@@ -256,8 +256,10 @@ __device__ __forceinline__ bf16 *at(const View &t, int z, int y, int x, int c) {
 __device__ __forceinline__ int items(const View &t) { return t.D * t.H * t.W * (t.nc >> 3); }
 
 // db[co] += sum_v dY[v][co]: the grid stride is a multiple of the chunks per voxel, so
-// each thread keeps one chunk and sums it in registers
-__global__ void k_bias_grad(View dY, int cout_real, float *__restrict__ db) {
+// each thread keeps one chunk and sums it in registers; warps fold lanes of the same
+// chunk, the block folds its warps in shared memory, one atomic per channel per block
+__global__ void __launch_bounds__(256) k_bias_grad(View dY, int cout_real, float *__restrict__ db) {
+    __shared__ float red[8][64];
     const int n = items(dY), nq = dY.nc >> 3;
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -272,11 +274,17 @@ __global__ void k_bias_grad(View dY, int cout_real, float *__restrict__ db) {
 #pragma unroll
     for (int k = 0; k < 8; k++)
         for (int o = 16; o >= nq; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
-    if ((threadIdx.x & 31) < nq) {
-        const int c = ((i0 % nq) << 3);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < nq) {
 #pragma unroll
-        for (int k = 0; k < 8; k++)
-            if (c + k < cout_real && s[k] != 0.f) atomicAdd(&db[c + k], s[k]);
+        for (int k = 0; k < 8; k++) red[warp][8 * lane + k] = s[k];  // lane = chunk (i0 % nq)
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c < dY.nc && c < cout_real) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w][c];
+        if (t != 0.f) atomicAdd(&db[c], t);
     }
 }
 
@@ -524,7 +532,7 @@ void wgrad(cudaStream_t st, View X, View dY, const LayerDev &L) {
     const long tiles = (long)dY.D * dY.H * ((dY.W + 15) / 16);
     const int slices = (int)std::max<long>(1, std::min<long>(64, (tiles + 63) / 64));
     k_wgrad<<<27 * nci * nco * slices, 128, 0, st>>>(X, dY, L.gw, L.coutp, slices);
-    k_bias_grad<<<blocks(nvox(dY) * dY.nc / 8), 256, 0, st>>>(dY, L.cout, L.gb);
+    k_bias_grad<<<(int)std::min<long>(2 * 148, (nvox(dY) * dY.nc / 8 + 255) / 256), 256, 0, st>>>(dY, L.cout, L.gb);
 }
 
 // the head writes FP32 to outf (node-major, 3 per node)

@@ -15,7 +15,7 @@ Everything here is plumbing around the C ABI: the features, the network's forwar
 backward passes, Adam and the solves run in the library's CUDA kernels; torch only holds
 device buffers and events.
 
-  python -m paper_1603_08161_b300.learned train --seeds 1-96 --frames 17 --out w.bin
+  python -m paper_1603_08161_b300.learned train --seeds 1-192 --frames 17 --epochs 16 --out w.bin
   python -m paper_1603_08161_b300.learned eval --weights w.bin --seeds 10001-10004
 """
 from __future__ import annotations
@@ -225,7 +225,7 @@ def main(argv=None):
     ap.add_argument("--seeds", default=None)
     ap.add_argument("--frames", type=int, default=17)
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=16)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--surface-weight", type=float, default=9.0)
     ap.add_argument("--max-samples", type=int, default=None)
@@ -263,7 +263,7 @@ def main(argv=None):
             out[name] = (time.perf_counter() - t0) * 1e3 / a.iters
         log(json.dumps(out))
     elif a.cmd == "train":
-        seeds = _seeds(a.seeds or "1-96")
+        seeds = _seeds(a.seeds or "1-192")
         X, T, dims = collect(seeds, a.frames, a.workers, a.max_samples, log, None if a.cpu_render else "cuda")
         log(json.dumps({"samples": len(X)}))
         net, _ = train(X, T, dims, a.epochs, a.lr, a.surface_weight, log=log)

@@ -319,7 +319,9 @@ def _capsules_torch(caps, which, dirs, device):
     z = torch.full((d.shape[0],), z0, dtype=torch.float64, device=device)
     live = torch.ones(d.shape[0], dtype=torch.bool, device=device)
     conv = torch.zeros_like(live)
-    for _ in range(160):
+    for it in range(160):
+        if it % 8 == 0 and not bool(live.any()):
+            break  # no ray left to step (further steps would change nothing)
         dist = sdf(z[:, None] * d)
         done = live & (dist < eps)
         conv |= done

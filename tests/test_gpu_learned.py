@@ -1,5 +1,5 @@
 """What the trained warm-start network gains over the plain solve (test sequences, seeds
-from 10001, which the training seeds 1-128 do not include).
+from 10001, which the training seeds 1-192 do not include).
 
 Per frame, from the plain trajectory's previous warp, the plain solve sets E_plain with
 its full schedule (10 x 20); the plain solve and the learned start are then each run
