@@ -85,7 +85,7 @@ struct vd_lattice {
     cudaGraphExec_t gexec = nullptr;
     vd_solve_params gparams{};
     Ctx gctx{};
-    int gkey_caps[4] = {0, 0, 0, 0};
+    int gkey_caps[5] = {0, 0, 0, 0, 0};
     long gen = 0, ggen = -1;         // buffer generation (pointers changed)
     int launches_solve = 0, launches_frame = 0;
     int counting = 0;
@@ -106,6 +106,7 @@ struct vd_lattice {
     bool coop = false;               // device supports cooperative launches
     bool use_persistent = true;      // may be cleared if the graph cannot hold the launch
     bool in_batch = false;           // being captured into a batch graph: streamed PCG
+    bool use_brick = true;           // persistent step: brick partition where one fits
     // Gauss-Newton early stop: the energy target lives in rep_dev[15]
     bool gated = false;
     // learned warm start: features (6 nn), prediction (3 nn), backup of u and R (12 ld)
@@ -402,10 +403,49 @@ void enqueue_pcg(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K, do
 
 constexpr int kPcgMaxChunk = 6272;  // 9 floats per slot in shared memory: 225,792 bytes (+ 4 KB static)
 
+// Bricks of by x bz full x-rows for the persistent position step of an all-nodes
+// lattice (nx % 4 == 0): the fewest slots per CTA within the SM count, and among those
+// the fewest x-rows with a neighbour in another CTA.  by = bz = 0 when none fits or
+// the bricks would hold more than 1.25x the slots of an even split.
+void brick_plan(const vd_lattice *L, int *by, int *bz) {
+    *by = *bz = 0;
+    const Ctx &c = L->c;
+    if (!L->all || c.nx % 4 || !L->use_brick) return;
+    const long even = ((long)c.nn + L->num_sms - 1) / L->num_sms;
+    long best_chunk = 0, best_faces = 0;
+    for (int y = 1; y <= c.ny; y++) {
+        if (c.ny % y) continue;
+        for (int z = 1; z <= c.nz; z++) {
+            if (c.nz % z || y * z > kPcgMaxRows) continue;
+            const long G = (long)(c.ny / y) * (c.nz / z), chunk = (long)y * z * c.nx;
+            if (G > L->num_sms || chunk > kPcgMaxChunk || 4 * chunk > 5 * even) continue;
+            const long faces = (y < c.ny ? 2L * z : 0) + (z < c.nz ? 2L * y : 0);
+            if (!best_chunk || chunk < best_chunk || (chunk == best_chunk && faces < best_faces)) {
+                best_chunk = chunk;
+                best_faces = faces;
+                *by = y;
+                *bz = z;
+            }
+        }
+    }
+}
+
 // Whether the position step runs as one persistent cooperative kernel, with how many
-// CTAs and how many slots per CTA.
-bool persistent_plan(vd_lattice *L, int *G, int *chunk) {
+// CTAs and how many slots per CTA (and the brick shape, 0 x 0 for a contiguous split).
+bool persistent_plan(vd_lattice *L, int *G, int *chunk, int *by = nullptr, int *bz = nullptr) {
+    if (by) *by = *bz = 0;
     if (!L->use_persistent || !L->coop || L->in_batch) return false;
+    int y = 0, z = 0;
+    brick_plan(L, &y, &z);
+    if (y) {
+        *chunk = y * z * L->c.nx;
+        *G = (L->c.ny / y) * (L->c.nz / z);
+        if (by) {
+            *by = y;
+            *bz = z;
+        }
+        return true;
+    }
     const int N = L->all ? L->c.nn : L->n_active_h;
     const int N4 = 4 * ((std::max(N, 1) + 3) / 4);
     // all SMs take part even for a small active set: the samples' share of each
@@ -420,8 +460,11 @@ bool persistent_plan(vd_lattice *L, int *G, int *chunk) {
 
 template <bool kAll>
 void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2, int apply, int G, int chunk) {
+    int by = 0, bz = 0;
+    brick_plan(L, &by, &bz);
+    if (by && by * bz * L->c.nx != chunk) by = bz = 0;  // the plan the caller sized G for
     PcgAux ax{L->pcg_part, L->pcg_bar, (int *)(L->pcg_bar + 2), L->surf_list, L->counts + 2,
-              {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk};
+              {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk, by, bz};
     const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
     cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
     Lc.other();
@@ -490,9 +533,9 @@ int class_launches_per_solve(const vd_solve_params *P, int kc) {
 
 vd_status build_graph(vd_lattice *L, const vd_solve_params *P) {
     const Grid gr = grids(L);
-    int pG = 0, pch = 0;
-    persistent_plan(L, &pG, &pch);
-    const int caps[4] = {gr.node, gr.samp, gr.cells, L->S * 65536 + pch};
+    int pG = 0, pch = 0, pby = 0, pbz = 0;
+    persistent_plan(L, &pG, &pch, &pby, &pbz);
+    const int caps[5] = {gr.node, gr.samp, gr.cells, L->S * 65536 + pch, pby * 65536 + pbz};
     const bool same = L->gexec && L->ggen == L->gen && !memcmp(&L->gparams, P, sizeof(*P)) &&
                       !memcmp(L->gkey_caps, caps, sizeof(caps)) && !memcmp(&L->gctx, &L->c, sizeof(Ctx));
     if (same) return VD_OK;
@@ -695,6 +738,7 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
             L->coop = false;
         }
         if (const char *e = getenv("VD_PERSISTENT")) L->use_persistent = atoi(e) != 0;
+        if (const char *e = getenv("VD_BRICK")) L->use_brick = atoi(e) != 0;
     }
     if (!L->all) {
         if ((s = dalloc(L, &L->slot_of_node, ld + 1)) || (s = dalloc(L, &L->node_of_slot, ld)) ||

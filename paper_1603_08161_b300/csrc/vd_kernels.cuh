@@ -728,14 +728,17 @@ __device__ __forceinline__ void sub_sync(int bar_id, int nt) {
 
 template <int kOp, bool kAll, bool kFresh>
 __device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, float *dst, float *dst2, int cb, int ce,
-                                            float *tsm, float &part, int lt, int nt, int bar_id) {
-    const int sb = c.occ_beg[cb], se = c.occ_beg[ce];
+                                            float *tsm, float &part, int lt, int nt, int bar_id, int js = 0,
+                                            int je = 0x7fffffff) {
+    // the samples of cells [cb, ce), clipped to [js, je) (a cell may be shared with the
+    // neighbouring range: each range adds its own samples' contributions)
+    const int sb = max(c.occ_beg[cb], js), se = min(c.occ_beg[ce], je);
     const int items = kOp == kOpEnergy ? 1 : (ce - cb) * 8;
     for (int i0 = 0; i0 < items; i0 += nt) {
         const int item = i0 + lt;
         const bool has = kOp != kOpEnergy && item < items;
         const int ci = cb + (has ? item >> 3 : 0), k = item & 7;
-        const int ibeg = has ? c.occ_beg[ci] : 0, iend = has ? c.occ_beg[ci + 1] : 0;
+        const int ibeg = has ? max(c.occ_beg[ci], js) : 0, iend = has ? min(c.occ_beg[ci + 1], je) : 0;
         float ax = 0.f, ay = 0.f, az = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
         for (int j0 = sb; j0 < se; j0 += nt) {
             const int j = j0 + lt;
@@ -1165,7 +1168,8 @@ __global__ void __launch_bounds__(kThreads) k_add_increment(Ctx c, const Scal *s
 // second sets the error flag and the whole grid returns.
 constexpr int kPcgThreads = 1024;
 constexpr int kPcgMaxGroups = 2;  // float4 groups per thread: chunk <= 4 * 2 * 1024
-constexpr int kPcgHalf = kPcgThreads / 2;
+constexpr int kPcgStencil = kPcgThreads / 2;              // threads on the stencil in phase A
+constexpr int kPcgSample = kPcgThreads - kPcgStencil;      // threads on the samples in phase A
 constexpr long long kBarrierCycles = 2000000000LL;
 
 struct PcgAux {
@@ -1175,8 +1179,12 @@ struct PcgAux {
     const int *surf;   // ascending slots touched by samples or sparse pairs
     const int *n_surf;
     float *pbuf[2];    // p of even / odd iterations, published for the other CTAs
-    int chunk;
+    int chunk;         // slots per CTA
+    int by, bz;        // > 0: each CTA owns a brick of by x bz full x-rows (all-nodes
+                       // lattice, ny % by == nz % bz == 0); 0: a contiguous slot range
 };
+
+constexpr int kPcgMaxRows = 128;  // x-rows of one brick
 
 // Grid barrier that can also reduce: bar[0] counts arrivals, bar[1] is the generation.
 // Thread 0 of each CTA publishes the CTA's writes (fence), reads the generation and
@@ -1279,8 +1287,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
     __shared__ double bc;
-    __shared__ int sb_lo, sb_hi;
-    __shared__ float tsm[kPcgHalf];
+    __shared__ int sb_lo, sb_hi, s_cb, s_ce, s_js, s_je;
+    __shared__ int s_rlo[kPcgMaxRows], s_rhi[kPcgMaxRows];
+    __shared__ float tsm[kPcgSample];
     __shared__ float s_ab;
     float *sm = reinterpret_cast<float *>(sm4);
     const int chunk = ax.chunk;
@@ -1292,15 +1301,45 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     const unsigned G = gridDim.x;
     const int N = active_count<kAll>(c);
     const int N4 = 4 * groups4(N);
-    const int s_beg = blockIdx.x * chunk;
-    const int s_end = min(s_beg + chunk, N4);
-    const int ng = s_end > s_beg ? (s_end - s_beg) >> 2 : 0;
+    // own slots: a brick of full x-rows (local index l = x + nx (row), row = yl + by zl)
+    // or the contiguous range [s_beg, s_end) (local index l = slot - s_beg)
+    const bool brick = kVec4 && ax.by > 0;
+    const int nx = c.nx, plane = c.nx * c.ny;
+    const int nby = brick ? c.ny / ax.by : 1;
+    const int y0 = brick ? (int)(blockIdx.x % nby) * ax.by : 0, z0 = brick ? (int)(blockIdx.x / nby) * ax.bz : 0;
+    const int rows = brick ? ax.by * ax.bz : 0;
+    const int s_beg = brick ? 0 : blockIdx.x * chunk;
+    const int s_end = brick ? 0 : min(s_beg + chunk, N4);
+    const int ng = brick ? chunk >> 2 : (s_end > s_beg ? (s_end - s_beg) >> 2 : 0);
+    auto gslot = [&](int l) -> int {
+        if (!brick) return s_beg + l;
+        const int r = l / nx;
+        return (l - r * nx) + nx * (y0 + r % ax.by) + plane * (z0 + r / ax.by);
+    };
     const int tid = threadIdx.x;
     const float w2 = 2.f * c.w_r;
     const size_t ld = c.ld;
     float4 xr[kPcgMaxGroups][3];
-    if (tid == 0) {  // own range of the surface list
+    if (brick && tid < rows) {  // each own row's range of the surface list
+        const int base = nx * (y0 + tid % ax.by) + plane * (z0 + tid / ax.by);
         const int n = *ax.n_surf;
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (ax.surf[m] < base) lo = m + 1;
+            else hi = m;
+        }
+        s_rlo[tid] = lo;
+        hi = n;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (ax.surf[m] < base + nx) lo = m + 1;
+            else hi = m;
+        }
+        s_rhi[tid] = lo;
+    }
+    if (tid == 0) {  // own range of the surface list
+        const int n = brick ? 0 : *ax.n_surf;
         int lo = 0, hi = n;
         while (lo < hi) {
             const int m = (lo + hi) >> 1;
@@ -1315,6 +1354,26 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             else hi = m;
         }
         sb_hi = lo;
+        // an equal share of the sorted samples, and the occupied cells that hold them
+        const int n_occ = *c.n_occ, ns = n_occ > 0 ? c.occ_beg[n_occ] : 0;
+        const int js = (int)(((long long)ns * blockIdx.x) / G), je = (int)(((long long)ns * (blockIdx.x + 1)) / G);
+        lo = 0;
+        hi = n_occ;  // first cell whose end is past js
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (c.occ_beg[m + 1] <= js) lo = m + 1;
+            else hi = m;
+        }
+        s_cb = lo;
+        hi = n_occ;  // first cell that starts at or after je
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (c.occ_beg[m] < je) lo = m + 1;
+            else hi = m;
+        }
+        s_ce = je > js ? lo : s_cb;
+        s_js = js;
+        s_je = je;
     }
     // ---- init: Minv = 1/diag, r = b, z = Minv r, p_old = 0, x = 0; rho0 = r.z
     float part = 0.f;
@@ -1324,7 +1383,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
 #pragma unroll
         for (int a = 0; a < 3; a++) xr[kk][a] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (gl >= ng) continue;
-        const int l = 4 * gl, s = s_beg + l;
+        const int l = 4 * gl, s = gslot(l);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const float4 dg = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
@@ -1349,10 +1408,19 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         }
     }
     __syncthreads();
-    for (int t = sb_lo + tid; t < sb_hi; t += blockDim.x) {
-        const int sl = ax.surf[t];
+    if (brick) {
+        for (int r = tid >> 5; r < rows; r += kPcgThreads >> 5)
+            for (int t = s_rlo[r] + (tid & 31); t < s_rhi[r]; t += 32) {
+                const int sl = ax.surf[t];
 #pragma unroll
-        for (int a = 0; a < 3; a++) c.q[a * ld + sl] = 0.f;
+                for (int a = 0; a < 3; a++) c.q[a * ld + sl] = 0.f;
+            }
+    } else {
+        for (int t = sb_lo + tid; t < sb_hi; t += blockDim.x) {
+            const int sl = ax.surf[t];
+#pragma unroll
+            for (int a = 0; a < 3; a++) c.q[a * ld + sl] = 0.f;
+        }
     }
     double *tot = ax.part + (size_t)(2 * K + 1) * G;  // two broadcast slots
     {
@@ -1374,11 +1442,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         const float *__restrict__ pold = ax.pbuf[(it + 1) & 1];
         float *__restrict__ pnew = ax.pbuf[it & 1];
         part = 0.f;
-        if (tid < kPcgHalf) {
+        if (tid < kPcgStencil) {
             // ---- A1: p = z + beta p_old for own slots
 #pragma unroll 1
-            for (int gl = tid; gl < ng; gl += kPcgHalf) {
-                const int l = 4 * gl, s = s_beg + l;
+            for (int gl = tid; gl < ng; gl += kPcgStencil) {
+                const int l = 4 * gl, s = gslot(l);
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
                     const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
@@ -1389,14 +1457,42 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                     *reinterpret_cast<float4 *>(pnew + a * ld + s) = pn;
                 }
             }
-            sub_sync(2, kPcgHalf);
+            sub_sync(2, kPcgStencil);
             // ---- A2: q = 2 w_r L p into Q
 #pragma unroll 1
-            for (int gl = tid; gl < ng; gl += kPcgHalf) {
-                const int l = 4 * gl, s0 = s_beg + l;
+            for (int gl = tid; gl < ng; gl += kPcgStencil) {
+                const int l = 4 * gl;
                 if (kVec4) {
-                    const int x0 = s0 % c.nx, t = s0 / c.nx, y = t % c.ny, z = t / c.ny, pl = c.nx * c.ny;
-                    const int offs[4] = {-c.nx, c.nx, -pl, pl};
+                    int x0, y, z, s0;
+                    bool own[4];
+                    int loff[4];
+                    const int offs[4] = {-nx, nx, -plane, plane};
+                    if (brick) {
+                        const int r = l / nx, yl = r % ax.by, zl = r / ax.by;
+                        x0 = l - r * nx;
+                        y = y0 + yl;
+                        z = z0 + zl;
+                        s0 = x0 + nx * y + plane * z;
+                        own[0] = yl > 0;
+                        own[1] = yl + 1 < ax.by;
+                        own[2] = zl > 0;
+                        own[3] = zl + 1 < ax.bz;
+                        loff[0] = -nx;
+                        loff[1] = nx;
+                        loff[2] = -ax.by * nx;
+                        loff[3] = ax.by * nx;
+                    } else {
+                        s0 = s_beg + l;
+                        x0 = s0 % nx;
+                        const int t = s0 / nx;
+                        y = t % c.ny;
+                        z = t / c.ny;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            own[k] = s0 + offs[k] >= s_beg && s0 + offs[k] < s_end;
+                            loff[k] = offs[k];
+                        }
+                    }
                     const bool has[4] = {y > 0, y + 1 < c.ny, z > 0, z + 1 < c.nz};
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
@@ -1405,11 +1501,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                         const float4 pc = *reinterpret_cast<const float4 *>(Pa + l);
                         float left = pc.x, right = pc.w;
                         if (x0 > 0)
-                            left = (s0 - 1 >= s_beg) ? Pa[l - 1]
-                                                     : fmaf(beta, __ldcg(Oa + s0 - 1), __ldcg(Za + s0 - 1));
-                        if (x0 + 4 < c.nx)
-                            right = (s0 + 4 < s_end) ? Pa[l + 4]
-                                                     : fmaf(beta, __ldcg(Oa + s0 + 4), __ldcg(Za + s0 + 4));
+                            left = (brick || s0 - 1 >= s_beg)
+                                       ? Pa[l - 1]
+                                       : fmaf(beta, __ldcg(Oa + s0 - 1), __ldcg(Za + s0 - 1));
+                        if (x0 + 4 < nx)
+                            right = (brick || s0 + 4 < s_end)
+                                        ? Pa[l + 4]
+                                        : fmaf(beta, __ldcg(Oa + s0 + 4), __ldcg(Za + s0 + 4));
                         float4 d = make_float4((pc.x - left) + (pc.x - pc.y), (pc.y - pc.x) + (pc.y - pc.z),
                                                (pc.z - pc.y) + (pc.z - pc.w), (pc.w - pc.z) + (pc.w - right));
 #pragma unroll
@@ -1417,8 +1515,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                             if (!has[k]) continue;
                             const int sj = s0 + offs[k];
                             float4 v;
-                            if (sj >= s_beg && sj < s_end) {
-                                v = *reinterpret_cast<const float4 *>(Pa + (sj - s_beg));
+                            if (own[k]) {
+                                v = *reinterpret_cast<const float4 *>(Pa + l + loff[k]);
                             } else {
                                 const float4 zz = __ldcg(reinterpret_cast<const float4 *>(Za + sj));
                                 const float4 oo = __ldcg(reinterpret_cast<const float4 *>(Oa + sj));
@@ -1437,7 +1535,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
-                        const int si = s0 + e;
+                        const int si = s_beg + l + e;  // never a brick here
                         float q3[3] = {0.f, 0.f, 0.f};
                         if (si < N) {
                             int nb[6];
@@ -1470,14 +1568,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             }
         } else {
             // ---- A: the samples' J^T J p into c.q (atomics), p formed from z and p_old
-            const int lt = tid - kPcgHalf;
+            const int lt = tid - kPcgStencil;
             const VecView pv{Zg, pold, beta};
-            const int n_occ = *c.n_occ;
-            const int per = (n_occ + (int)G - 1) / (int)G;
-            const int cb = min((int)blockIdx.x * per, n_occ), ce = min(cb + per, n_occ);
-            if (ce > cb) cells_block<kOpApply, kAll, true>(c, pv, c.q, nullptr, cb, ce, tsm, part, lt, kPcgHalf, 1);
+            if (s_ce > s_cb)
+                cells_block<kOpApply, kAll, true>(c, pv, c.q, nullptr, s_cb, s_ce, tsm, part, lt, kPcgSample, 1, s_js,
+                                                  s_je);
             double pd = 0.0;
-            sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * lt, G * kPcgHalf, part, pd);
+            sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * lt, G * kPcgSample, part, pd);
         }
         {
             const double bt = block_total(part, red);
@@ -1498,12 +1595,26 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             if (blockIdx.x == 0) scal_pq(sc, K)[it] = pq;
         }
         // fold in (and clear) the samples' contributions to own slots
-        for (int t = sb_lo + tid; t < sb_hi; t += blockDim.x) {
-            const int sl = ax.surf[t];
+        if (brick) {
+            for (int r = tid >> 5; r < rows; r += kPcgThreads >> 5) {
+                const int base = nx * (y0 + r % ax.by) + plane * (z0 + r / ax.by);
+                for (int t = s_rlo[r] + (tid & 31); t < s_rhi[r]; t += 32) {
+                    const int sl = ax.surf[t], l = r * nx + (sl - base);
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                Q[a * chunk + (sl - s_beg)] += __ldcg(c.q + a * ld + sl);
-                c.q[a * ld + sl] = 0.f;
+                    for (int a = 0; a < 3; a++) {
+                        Q[a * chunk + l] += __ldcg(c.q + a * ld + sl);
+                        c.q[a * ld + sl] = 0.f;
+                    }
+                }
+            }
+        } else {
+            for (int t = sb_lo + tid; t < sb_hi; t += blockDim.x) {
+                const int sl = ax.surf[t];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    Q[a * chunk + (sl - s_beg)] += __ldcg(c.q + a * ld + sl);
+                    c.q[a * ld + sl] = 0.f;
+                }
             }
         }
         __syncthreads();
@@ -1514,7 +1625,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         for (int kk = 0; kk < kPcgMaxGroups; kk++) {
             const int gl = tid + kk * kPcgThreads;
             if (gl >= ng) continue;
-            const int l = 4 * gl, s = s_beg + l;
+            const int l = 4 * gl, s = gslot(l);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
@@ -1558,7 +1669,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     for (int kk = 0; kk < kPcgMaxGroups; kk++) {
         const int gl = tid + kk * kPcgThreads;
         if (gl >= ng) continue;
-        const int s = s_beg + 4 * gl;
+        const int s = gslot(4 * gl);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             *reinterpret_cast<float4 *>(c.x + a * ld + s) = xr[kk][a];
