@@ -101,7 +101,7 @@ struct vd_lattice {
     int *surf_flag = nullptr, *surf_pos = nullptr, *surf_list = nullptr;
     double *pcg_part = nullptr;
     int pcg_part_rows = 0;
-    unsigned *pcg_bar = nullptr;     // [0] arrivals, [1] generation, [2] error flag
+    unsigned *pcg_bar = nullptr;     // [0] barrier arrival word, [2] error flag
     int num_sms = 148;
     bool coop = false;               // device supports cooperative launches
     bool use_persistent = true;      // may be cleared if the graph cannot hold the launch

@@ -1174,7 +1174,7 @@ constexpr long long kBarrierCycles = 2000000000LL;
 
 struct PcgAux {
     double *part;      // rows 0..K: r.z partials, rows K+1..2K: p.Ap partials, G entries each
-    unsigned *bar;     // [0] arrivals, [1] generation of the grid barrier
+    unsigned *bar;     // [0] the grid barrier's arrival word (top bit flips per barrier)
     int *err;          // set when a barrier wait gives up
     const int *surf;   // ascending slots touched by samples or sparse pairs
     const int *n_surf;
@@ -1186,55 +1186,28 @@ struct PcgAux {
 
 constexpr int kPcgMaxRows = 128;  // x-rows of one brick
 
-// Grid barrier that can also reduce: bar[0] counts arrivals, bar[1] is the generation.
-// Thread 0 of each CTA publishes the CTA's writes (fence), reads the generation and
-// arrives.  The last CTA to arrive sums `row` (one FP64 partial per CTA, written before
-// the call) in CTA order, stores the sum in *total, resets the count and bumps the
-// generation (release); the others poll the generation (acquire) for at most
-// kBarrierCycles.  Every CTA then returns the same total through *out.
-__device__ __forceinline__ bool grid_reduce(unsigned *bar, int *err, unsigned G, const double *row, double *total,
-                                            double *out) {
-    __shared__ int s_last, s_ok;
-    __shared__ unsigned s_gen;
+// Grid barrier that also reduces.  bar[0] is one arrival word: thread 0 of each CTA
+// publishes the CTA's writes (fence) and adds 1 to it (CTA 0 adds 2^31 - (G - 1)), so
+// the G additions of one barrier flip its top bit exactly once, with the last arrival;
+// each CTA polls the word (acquire) until the top bit differs from the value it saw on
+// arriving, for at most kBarrierCycles.  Then every CTA sums `row` (one FP64 partial per
+// CTA, written before the call) itself, in CTA order: all CTAs get the same `sum`, and it
+// does not depend on the order of arrival.
+__device__ __forceinline__ bool grid_reduce(unsigned *bar, int *err, unsigned G, const double *row, double &sum) {
+    __shared__ int s_ok;
+    __shared__ double s_sum;
     __syncthreads();
     if (threadIdx.x == 0) {
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        unsigned g0, a;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g0) : "l"(bar + 1) : "memory");
-        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(a) : "l"(bar) : "memory");
-        s_last = a == G - 1;
-        s_gen = g0;
-    }
-    __syncthreads();
-    int good = 1;
-    if (s_last) {
-        if (threadIdx.x < 32) {
-            double sum = 0.0;
-            if (row) {
-                double v[5];
-#pragma unroll
-                for (int k = 0; k < 5; k++) {  // all loads in flight before the first add
-                    const unsigned b = threadIdx.x + 32u * k;
-                    v[k] = b < G ? __ldcg(row + b) : 0.0;
-                }
-                sum = (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
-                for (unsigned b = threadIdx.x + 160u; b < G; b += 32) sum += __ldcg(row + b);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-            }
-            if (threadIdx.x == 0) {
-                if (row) *total = sum;
-                __threadfence();
-                asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
-                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
-            }
-        }
-    } else if (threadIdx.x == 0) {
+        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (G - 1u) : 1u;
+        unsigned old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(inc) : "memory");
+        int good = 1;
         const long long t0 = clock64();
         while (true) {
-            unsigned g;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
-            if (g != s_gen) break;
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if ((v ^ old) & 0x80000000u) break;
             if (*(volatile int *)err) {
                 good = 0;
                 break;
@@ -1245,17 +1218,25 @@ __device__ __forceinline__ bool grid_reduce(unsigned *bar, int *err, unsigned G,
                 break;
             }
         }
-    }
-    if (threadIdx.x == 0) {
         s_ok = good && !*(volatile int *)err;
-        if (row) *out = __ldcg(total);
     }
     __syncthreads();
+    if (row && threadIdx.x < 32) {
+        double v[5];
+#pragma unroll
+        for (int k = 0; k < 5; k++) {  // all loads in flight before the first add
+            const unsigned b = threadIdx.x + 32u * k;
+            v[k] = b < G ? __ldcg(row + b) : 0.0;
+        }
+        double t = (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
+        for (unsigned b = threadIdx.x + 160u; b < G; b += 32) t += __ldcg(row + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+        if (threadIdx.x == 0) s_sum = t;
+    }
+    __syncthreads();
+    if (row) sum = s_sum;
     return s_ok != 0;
-}
-
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, unsigned G) {
-    return grid_reduce(bar, err, G, nullptr, nullptr, nullptr);
 }
 
 // FP64 block sum of one float per thread; valid in thread 0
@@ -1286,7 +1267,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     // (p of even / odd iterations), c.q (the samples' contributions), c.x (result).
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
-    __shared__ double bc;
     __shared__ int sb_lo, sb_hi, s_cb, s_ce, s_js, s_je;
     __shared__ int s_rlo[kPcgMaxRows], s_rhi[kPcgMaxRows];
     __shared__ float tsm[kPcgSample];
@@ -1422,13 +1402,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             for (int a = 0; a < 3; a++) c.q[a * ld + sl] = 0.f;
         }
     }
-    double *tot = ax.part + (size_t)(2 * K + 1) * G;  // two broadcast slots
     {
         const double bt = block_total(part, red);
         if (tid == 0) ax.part[blockIdx.x] = bt;
     }
-    bool ok = grid_reduce(ax.bar, ax.err, G, ax.part, tot, &bc);
-    const double rho0 = ok ? bc : 0.0;
+    double sum = 0.0;
+    bool ok = grid_reduce(ax.bar, ax.err, G, ax.part, sum);
+    const double rho0 = ok ? sum : 0.0;
     double rho = rho0;
     float beta = 0.f;
     if (blockIdx.x == 0 && tid == 0) scal_rho(sc)[0] = rho0;
@@ -1580,12 +1560,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             const double bt = block_total(part, red);
             if (tid == 0) ax.part[(size_t)(K + 1 + it) * G + blockIdx.x] = bt;
         }
-        ok = grid_reduce(ax.bar, ax.err, G, ax.part + (size_t)(K + 1 + it) * G, tot, &bc);
+        ok = grid_reduce(ax.bar, ax.err, G, ax.part + (size_t)(K + 1 + it) * G, sum);
         if (!ok) {
             stop = 1;
             break;
         }
-        const double pq = bc;
+        const double pq = sum;
         if (!(pq > 0.0)) {
             stop = 1;
             break;
@@ -1648,12 +1628,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             if (tid == 0) ax.part[(size_t)(it + 1) * G + blockIdx.x] = bt;
         }
         done = it + 1;
-        ok = grid_reduce(ax.bar, ax.err, G, ax.part + (size_t)(it + 1) * G, tot + 1, &bc);
+        ok = grid_reduce(ax.bar, ax.err, G, ax.part + (size_t)(it + 1) * G, sum);
         if (!ok) {
             stop = 1;
             break;
         }
-        const double rho1 = bc;
+        const double rho1 = sum;
         if (blockIdx.x == 0 && tid == 0) scal_rho(sc)[it + 1] = rho1;
         if (rho1 <= tol2 * rho0) {
             stop = 1;
