@@ -98,7 +98,7 @@ struct vd_lattice {
     int prof_launches = 0;
     bool use_pdl = true;             // chain solve kernels with programmatic dependent launch
     // persistent position step
-    int *surf_flag = nullptr, *surf_pos = nullptr, *surf_list = nullptr;
+    int *surf_flag = nullptr;        // per slot: touched by a sample or a sparse pair
     double *pcg_part = nullptr;
     int pcg_part_rows = 0;
     unsigned *pcg_bar = nullptr;     // [0] barrier arrival word, [2] error flag
@@ -463,7 +463,7 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     int by = 0, bz = 0;
     brick_plan(L, &by, &bz);
     if (by && by * bz * L->c.nx != chunk) by = bz = 0;  // the plan the caller sized G for
-    PcgAux ax{L->pcg_part, L->pcg_bar, (int *)(L->pcg_bar + 2), L->surf_list, L->counts + 2,
+    PcgAux ax{L->pcg_part, L->pcg_bar, (int *)(L->pcg_bar + 2), L->surf_flag,
               {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk, by, bz};
     const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
     cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
@@ -608,16 +608,14 @@ vd_status read_report(vd_lattice *L, vd_solve_report *out) {
     return st;
 }
 
-vd_status frame_surface_list(vd_lattice *L) {
+vd_status frame_surface_flags(vd_lattice *L) {
     refresh_ctx(L);
     const Ctx c = L->c;
     cudaStream_t st = L->stream;
-    CK(cudaMemsetAsync(L->surf_flag, 0, sizeof(int) * (size_t)c.nn, st));
+    CK(cudaMemsetAsync(L->surf_flag, 0, sizeof(int) * (size_t)c.ld, st));
     const int nb = blocks_for(std::max(L->cap_src, 1) + L->S);
     if (L->all) k_mark_surface<true><<<nb, kThreads, 0, st>>>(L->occ_cell, L->counts + 1, L->scell_s, L->S, c, L->surf_flag);
     else k_mark_surface<false><<<nb, kThreads, 0, st>>>(L->occ_cell, L->counts + 1, L->scell_s, L->S, c, L->surf_flag);
-    scan_launch(L->surf_flag, c.nn, L->surf_pos, L->counts + 2, L->scan_sums, st);
-    k_compact_list<<<blocks_for(c.nn), kThreads, 0, st>>>(L->surf_flag, L->surf_pos, c.nn, L->surf_list);
     CKL();
     return VD_OK;
 }
@@ -625,7 +623,7 @@ vd_status frame_surface_list(vd_lattice *L) {
 vd_status frame_active_set(vd_lattice *L) {
     const Ctx c = L->c;
     cudaStream_t st = L->stream;
-    if (L->all) return frame_surface_list(L);
+    if (L->all) return frame_surface_flags(L);
     CK(cudaMemsetAsync(L->mark, 0, sizeof(int) * (size_t)c.nn, st));
     k_mark_cells<<<blocks_for(std::max(L->cap_src, 1) + L->S), kThreads, 0, st>>>(L->occ_cell, L->counts + 1,
                                                                                    L->scell_s, L->S, c, L->mark);
@@ -634,7 +632,7 @@ vd_status frame_active_set(vd_lattice *L) {
     k_compact<<<blocks_for(c.nn), kThreads, 0, st>>>(L->act, c, L->slot_of_node, L->node_of_slot);
     k_neighbour_table<<<blocks_for(c.nn), kThreads, 0, st>>>(c, L->nbr);
     CKL();
-    return frame_surface_list(L);
+    return frame_surface_flags(L);
 }
 
 vd_status sync_sizes(vd_lattice *L) {
@@ -713,8 +711,7 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
         (s = dalloc(L, &L->counts, 8)) || (s = dalloc(L, &L->cnt, ld)) || (s = dalloc(L, &L->start, ld + 1)) ||
         (s = dalloc(L, &L->staging, 9 * ld)) || (s = dalloc(L, &L->rep_dev, 16)))
         return bail(s);
-    if ((s = dalloc(L, &L->surf_flag, ld)) || (s = dalloc(L, &L->surf_pos, ld + 1)) ||
-        (s = dalloc(L, &L->surf_list, ld)) || (s = dalloc(L, &L->pcg_bar, 4)))
+    if ((s = dalloc(L, &L->surf_flag, ld)) || (s = dalloc(L, &L->pcg_bar, 4)))
         return bail(s);
     {
         int dev = 0, coop = 0, sms = 0;
@@ -852,7 +849,7 @@ vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const fl
     L->have_frame = true;
     TRY(frame_active_set(L));
     TRY(sync_sizes(L));
-    L->launches_frame = 13 + 5 + (L->all ? 0 : 7);
+    L->launches_frame = 13 + 1 + (L->all ? 0 : 7);
     return VD_OK;
 }
 

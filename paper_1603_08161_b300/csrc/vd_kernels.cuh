@@ -484,7 +484,7 @@ __global__ void k_neighbour_table(Ctx c, int *__restrict__ nbr) {
 }
 
 // Slots touched by the samples' or sparse pairs' J^T J contributions (corners of their
-// cells), flagged for the persistent position step, then compacted in ascending order.
+// cells), flagged for the persistent position step (which folds their q per flag).
 template <bool kAll>
 __global__ void k_mark_surface(const int *__restrict__ occ_cell, const int *__restrict__ n_occ,
                                const int *__restrict__ scell, int S, Ctx c, int *__restrict__ flag) {
@@ -497,10 +497,6 @@ __global__ void k_mark_surface(const int *__restrict__ occ_cell, const int *__re
     }
 }
 
-__global__ void k_compact_list(const int *__restrict__ flag, const int *__restrict__ pos, int n, int *__restrict__ list) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        if (flag[i]) list[pos[i]] = i;
-}
 
 // ------------------------------------------------------------------ association (Sec. 5.1)
 
@@ -1176,15 +1172,14 @@ struct PcgAux {
     double *part;      // rows 0..K: r.z partials, rows K+1..2K: p.Ap partials, G entries each
     unsigned *bar;     // [0] the grid barrier's arrival word (top bit flips per barrier)
     int *err;          // set when a barrier wait gives up
-    const int *surf;   // ascending slots touched by samples or sparse pairs
-    const int *n_surf;
+    const int *flag;   // per slot: 1 if a sample or a sparse pair touches it (0 past N)
     float *pbuf[2];    // p of even / odd iterations, published for the other CTAs
     int chunk;         // slots per CTA
     int by, bz;        // > 0: each CTA owns a brick of by x bz full x-rows (all-nodes
                        // lattice, ny % by == nz % bz == 0); 0: a contiguous slot range
 };
 
-constexpr int kPcgMaxRows = 128;  // x-rows of one brick
+constexpr int kPcgMaxRows = 128;  // x-rows of one brick (bounds the plan's search)
 
 // Grid barrier that also reduces.  bar[0] is one arrival word: thread 0 of each CTA
 // publishes the CTA's writes (fence) and adds 1 to it (CTA 0 adds 2^31 - (G - 1)), so
@@ -1267,8 +1262,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     // (p of even / odd iterations), c.q (the samples' contributions), c.x (result).
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
-    __shared__ int sb_lo, sb_hi, s_cb, s_ce, s_js, s_je;
-    __shared__ int s_rlo[kPcgMaxRows], s_rhi[kPcgMaxRows];
+    __shared__ int s_cb, s_ce, s_js, s_je;
     __shared__ float tsm[kPcgSample];
     __shared__ float s_ab;
     float *sm = reinterpret_cast<float *>(sm4);
@@ -1287,7 +1281,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     const int nx = c.nx, plane = c.nx * c.ny;
     const int nby = brick ? c.ny / ax.by : 1;
     const int y0 = brick ? (int)(blockIdx.x % nby) * ax.by : 0, z0 = brick ? (int)(blockIdx.x / nby) * ax.bz : 0;
-    const int rows = brick ? ax.by * ax.bz : 0;
     const int s_beg = brick ? 0 : blockIdx.x * chunk;
     const int s_end = brick ? 0 : min(s_beg + chunk, N4);
     const int ng = brick ? chunk >> 2 : (s_end > s_beg ? (s_end - s_beg) >> 2 : 0);
@@ -1300,45 +1293,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     const float w2 = 2.f * c.w_r;
     const size_t ld = c.ld;
     float4 xr[kPcgMaxGroups][3];
-    if (brick && tid < rows) {  // each own row's range of the surface list
-        const int base = nx * (y0 + tid % ax.by) + plane * (z0 + tid / ax.by);
-        const int n = *ax.n_surf;
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            const int m = (lo + hi) >> 1;
-            if (ax.surf[m] < base) lo = m + 1;
-            else hi = m;
-        }
-        s_rlo[tid] = lo;
-        hi = n;
-        while (lo < hi) {
-            const int m = (lo + hi) >> 1;
-            if (ax.surf[m] < base + nx) lo = m + 1;
-            else hi = m;
-        }
-        s_rhi[tid] = lo;
-    }
-    if (tid == 0) {  // own range of the surface list
-        const int n = brick ? 0 : *ax.n_surf;
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            const int m = (lo + hi) >> 1;
-            if (ax.surf[m] < s_beg) lo = m + 1;
-            else hi = m;
-        }
-        sb_lo = lo;
-        hi = n;
-        while (lo < hi) {
-            const int m = (lo + hi) >> 1;
-            if (ax.surf[m] < s_end) lo = m + 1;
-            else hi = m;
-        }
-        sb_hi = lo;
+    if (tid == 0) {
         // an equal share of the sorted samples, and the occupied cells that hold them
         const int n_occ = *c.n_occ, ns = n_occ > 0 ? c.occ_beg[n_occ] : 0;
         const int js = (int)(((long long)ns * blockIdx.x) / G), je = (int)(((long long)ns * (blockIdx.x + 1)) / G);
-        lo = 0;
-        hi = n_occ;  // first cell whose end is past js
+        int lo = 0, hi = n_occ;  // first cell whose end is past js
         while (lo < hi) {
             const int m = (lo + hi) >> 1;
             if (c.occ_beg[m + 1] <= js) lo = m + 1;
@@ -1386,22 +1345,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             *reinterpret_cast<float4 *>(Zg + a * ld + s) = z4;
             *reinterpret_cast<float4 *>(ax.pbuf[1] + a * ld + s) = zero;
         }
-    }
-    __syncthreads();
-    if (brick) {
-        for (int r = tid >> 5; r < rows; r += kPcgThreads >> 5)
-            for (int t = s_rlo[r] + (tid & 31); t < s_rhi[r]; t += 32) {
-                const int sl = ax.surf[t];
+        const int4 fl = __ldcg(reinterpret_cast<const int4 *>(ax.flag + s));
+        if (fl.x | fl.y | fl.z | fl.w) {  // the samples' contributions arrive here by atomics
 #pragma unroll
-                for (int a = 0; a < 3; a++) c.q[a * ld + sl] = 0.f;
-            }
-    } else {
-        for (int t = sb_lo + tid; t < sb_hi; t += blockDim.x) {
-            const int sl = ax.surf[t];
-#pragma unroll
-            for (int a = 0; a < 3; a++) c.q[a * ld + sl] = 0.f;
+            for (int a = 0; a < 3; a++) *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
+    __syncthreads();
     {
         const double bt = block_total(part, red);
         if (tid == 0) ax.part[blockIdx.x] = bt;
@@ -1574,29 +1524,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             s_ab = (float)(rho / pq);
             if (blockIdx.x == 0) scal_pq(sc, K)[it] = pq;
         }
-        // fold in (and clear) the samples' contributions to own slots
-        if (brick) {
-            for (int r = tid >> 5; r < rows; r += kPcgThreads >> 5) {
-                const int base = nx * (y0 + r % ax.by) + plane * (z0 + r / ax.by);
-                for (int t = s_rlo[r] + (tid & 31); t < s_rhi[r]; t += 32) {
-                    const int sl = ax.surf[t], l = r * nx + (sl - base);
-#pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        Q[a * chunk + l] += __ldcg(c.q + a * ld + sl);
-                        c.q[a * ld + sl] = 0.f;
-                    }
-                }
-            }
-        } else {
-            for (int t = sb_lo + tid; t < sb_hi; t += blockDim.x) {
-                const int sl = ax.surf[t];
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    Q[a * chunk + (sl - s_beg)] += __ldcg(c.q + a * ld + sl);
-                    c.q[a * ld + sl] = 0.f;
-                }
-            }
-        }
         __syncthreads();
         const float alpha = s_ab;
         // ---- B: x += alpha p; r -= alpha q; z = Minv r (Q and published); rho' = r.z
@@ -1606,10 +1533,17 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             const int gl = tid + kk * kPcgThreads;
             if (gl >= ng) continue;
             const int l = 4 * gl, s = gslot(l);
+            const int4 fl = __ldcg(reinterpret_cast<const int4 *>(ax.flag + s));
+            const bool touched = fl.x | fl.y | fl.z | fl.w;
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
-                const float4 qv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
+                float4 qv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
+                if (touched) {  // fold in (and clear) the samples' contributions
+                    float4 *qg = reinterpret_cast<float4 *>(c.q + a * ld + s);
+                    qv = f4add(qv, __ldcg(qg));
+                    *qg = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 const float4 rv = *reinterpret_cast<const float4 *>(Rr + a * chunk + l);
                 const float4 mv = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
                 xr[kk][a] = make_float4(fmaf(alpha, pv.x, xr[kk][a].x), fmaf(alpha, pv.y, xr[kk][a].y),
