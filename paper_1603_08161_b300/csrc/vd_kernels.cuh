@@ -1153,15 +1153,16 @@ __global__ void __launch_bounds__(kThreads) k_add_increment(Ctx c, const Scal *s
 
 // ------------------------------------------------------------------ persistent PCG (Sec. 7.1 position step)
 
-// One cooperative launch runs a whole position step.  Each CTA owns a contiguous range
-// of `chunk` slots (a multiple of 4) and keeps p, r and q of its slots in shared memory
-// and x in registers for all K iterations; only p is published to global memory (read
-// through L2 by the CTAs whose stencil or samples need it), and the samples' J^T J p
+// One cooperative launch runs a whole position step.  Each CTA owns `chunk` slots (a
+// brick of full x-rows of an all-nodes lattice, else a contiguous range, a multiple of 4)
+// and keeps p, r and q of its slots in shared memory for all K iterations (x accumulates
+// in global memory, L2-resident); z and p are published to global memory (read through
+// L2 by the CTAs whose stencil or samples need them), and the samples' J^T J p
 // contributions go to a global buffer with atomics that the owners fold in and clear.
-// Three grid barriers per iteration (after p.Ap, after r.z, after publishing p).  The
-// reductions are deterministic: every CTA writes its FP64 partial to a per-iteration row
-// and every CTA sums the row in CTA order.  A barrier that waits longer than about a
-// second sets the error flag and the whole grid returns.
+// Two grid barriers per iteration (after p.Ap, after r.z).  The reductions are
+// deterministic: every CTA writes its FP64 partial to a per-iteration row and every CTA
+// sums the row in CTA order.  A barrier that waits longer than about a second sets the
+// error flag and the whole grid returns.
 constexpr int kPcgThreads = 1024;
 constexpr int kPcgMaxGroups = 2;  // float4 groups per thread: chunk <= 4 * 2 * 1024
 constexpr int kPcgStencil = kPcgThreads / 2;              // threads on the stencil in phase A
@@ -1180,6 +1181,7 @@ struct PcgAux {
 };
 
 constexpr int kPcgMaxRows = 128;  // x-rows of one brick (bounds the plan's search)
+
 
 // Grid barrier that also reduces.  bar[0] is one arrival word: thread 0 of each CTA
 // publishes the CTA's writes (fence) and adds 1 to it (CTA 0 adds 2^31 - (G - 1)), so
@@ -1292,7 +1294,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     const int tid = threadIdx.x;
     const float w2 = 2.f * c.w_r;
     const size_t ld = c.ld;
-    float4 xr[kPcgMaxGroups][3];
     if (tid == 0) {
         // an equal share of the sorted samples, and the occupied cells that hold them
         const int n_occ = *c.n_occ, ns = n_occ > 0 ? c.occ_beg[n_occ] : 0;
@@ -1319,12 +1320,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
 #pragma unroll
     for (int kk = 0; kk < kPcgMaxGroups; kk++) {
         const int gl = tid + kk * kPcgThreads;
-#pragma unroll
-        for (int a = 0; a < 3; a++) xr[kk][a] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (gl >= ng) continue;
         const int l = 4 * gl, s = gslot(l);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
+            *reinterpret_cast<float4 *>(c.x + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 dg = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
             const float4 rb = __ldcg(reinterpret_cast<const float4 *>(c.r + a * ld + s));
             const float dv[4] = {dg.x, dg.y, dg.z, dg.w}, rv[4] = {rb.x, rb.y, rb.z, rb.w};
@@ -1546,8 +1546,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                 }
                 const float4 rv = *reinterpret_cast<const float4 *>(Rr + a * chunk + l);
                 const float4 mv = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
-                xr[kk][a] = make_float4(fmaf(alpha, pv.x, xr[kk][a].x), fmaf(alpha, pv.y, xr[kk][a].y),
-                                        fmaf(alpha, pv.z, xr[kk][a].z), fmaf(alpha, pv.w, xr[kk][a].w));
+                // x lives in global memory (L2-resident): the 64 registers of a thread of
+                // a 1024-thread CTA cannot hold it as well without spilling
+                float4 *xg = reinterpret_cast<float4 *>(c.x + a * ld + s);
+                const float4 xo = __ldcg(xg);
+                *xg = make_float4(fmaf(alpha, pv.x, xo.x), fmaf(alpha, pv.y, xo.y), fmaf(alpha, pv.z, xo.z),
+                                  fmaf(alpha, pv.w, xo.w));
                 const float4 rn = make_float4(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y),
                                               fmaf(-alpha, qv.z, rv.z), fmaf(-alpha, qv.w, rv.w));
                 const float4 zn = make_float4(mv.x * rn.x, mv.y * rn.y, mv.z * rn.z, mv.w * rn.w);
@@ -1578,7 +1582,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         beta = s_ab;
         rho = rho1;
     }
-    // ---- x out (and u += x when the step is applied)
+    // ---- u += x when the step is applied
 #pragma unroll
     for (int kk = 0; kk < kPcgMaxGroups; kk++) {
         const int gl = tid + kk * kPcgThreads;
@@ -1586,9 +1590,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         const int s = gslot(4 * gl);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            *reinterpret_cast<float4 *>(c.x + a * ld + s) = xr[kk][a];
+            const float4 x4 = __ldcg(reinterpret_cast<const float4 *>(c.x + a * ld + s));
             if (apply) {
-                const float xv[4] = {xr[kk][a].x, xr[kk][a].y, xr[kk][a].z, xr[kk][a].w};
+                const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
                 for (int e = 0; e < 4; e++)
                     if (s + e < N) c.u[a * ld + slot_node<kAll>(c, s + e)] += xv[e];
