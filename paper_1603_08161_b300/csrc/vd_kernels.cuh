@@ -1704,8 +1704,23 @@ __device__ __forceinline__ void mat_to_quat(const float R[9], float q[4]) {
 // rotation changed little, so the Jacobi sweeps converge at once; R = R0 D is formed
 // from the product of unit quaternions, which keeps it orthonormal.
 // Also accumulates E_reg (Eq. 4) with the new rotations (kFit = false: E_reg only).
+// The near-tie redo of the rotation step in FP64 (rare), kept out of line so that its
+// registers do not count against the FP32 path's occupancy.
+__device__ __noinline__ double horn_top_eigvec_f64(float Sxx, float Sxy, float Sxz, float Syx, float Syy, float Syz,
+                                                   float Szx, float Szy, float Szz, float qv[4]) {
+    double Nd[4][4] = {{(double)Sxx + Syy + Szz, (double)Syz - Szy, (double)Szx - Sxz, (double)Sxy - Syx},
+                       {(double)Syz - Szy, (double)Sxx - Syy - Szz, (double)Sxy + Syx, (double)Szx + Sxz},
+                       {(double)Szx - Sxz, (double)Sxy + Syx, -(double)Sxx + Syy - Szz, (double)Syz + Szy},
+                       {(double)Sxy - Syx, (double)Szx + Sxz, (double)Syz + Szy, -(double)Sxx - Syy + Szz}};
+    double qd[4];
+    const double gd = sym4_top_eigvec<double>(Nd, qd);
+#pragma unroll
+    for (int r = 0; r < 4; r++) qv[r] = (float)qd[r];
+    return gd;
+}
+
 template <bool kAll, bool kFit>
-__global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
+__global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) {
     pdl_wait();
     pdl_trigger();
     if (sc->skip) return;
@@ -1718,7 +1733,6 @@ __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
         int nb[6], nj[6];
         neighbours<kAll>(c, s, nb);
         const float3 ui = ld3(c.u, c.ld, i);
-        float3 uj[6];
         float A[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         int axes = 0;
 #pragma unroll
@@ -1727,12 +1741,12 @@ __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
             if (nj[d] < 0) continue;
             const int a = d >> 1;
             axes |= 1 << a;
-            uj[d] = ld3(c.u, c.ld, nj[d]);
+            const float3 uj = ld3(c.u, c.ld, nj[d]);
             // column a of A/h^2: e_a + (u_j - u_i)/h for +a, e_a + (u_i - u_j)/h for -a
             const float sg = (d & 1) ? ih : -ih;
-            A[0][a] += (a == 0 ? 1.f : 0.f) + sg * (uj[d].x - ui.x);
-            A[1][a] += (a == 1 ? 1.f : 0.f) + sg * (uj[d].y - ui.y);
-            A[2][a] += (a == 2 ? 1.f : 0.f) + sg * (uj[d].z - ui.z);
+            A[0][a] += (a == 0 ? 1.f : 0.f) + sg * (uj.x - ui.x);
+            A[1][a] += (a == 1 ? 1.f : 0.f) + sg * (uj.y - ui.y);
+            A[2][a] += (a == 2 ? 1.f : 0.f) + sg * (uj.z - ui.z);
         }
         float Ri[9];
 #pragma unroll
@@ -1775,15 +1789,8 @@ __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
             if (gap < 1e-4f * scale) {
                 // near-singular block (the rotation's sensitivity exceeds 1e4): polar
                 // decomposition again in FP64
-                double Nd[4][4] = {{(double)Sxx + Syy + Szz, (double)Syz - Szy, (double)Szx - Sxz, (double)Sxy - Syx},
-                                   {(double)Syz - Szy, (double)Sxx - Syy - Szz, (double)Sxy + Syx, (double)Szx + Sxz},
-                                   {(double)Szx - Sxz, (double)Sxy + Syx, -(double)Sxx + Syy - Szz, (double)Syz + Szy},
-                                   {(double)Sxy - Syx, (double)Szx + Sxz, (double)Syz + Szy, -(double)Sxx - Syy + Szz}};
-                double qd[4];
-                const double gd = sym4_top_eigvec<double>(Nd, qd);
+                const double gd = horn_top_eigvec_f64(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz, qv);
                 unique = gd > 1e-12 * (double)scale;
-#pragma unroll
-                for (int r = 0; r < 4; r++) qv[r] = (float)qd[r];
             }
             if (!unique) {
                 keep = true;
@@ -1825,7 +1832,8 @@ __global__ void __launch_bounds__(kThreads) k_fit_rotations(Ctx c, Scal *sc) {
             const float ex = sg * (Ri[a] - (a == 0 ? 1.f : 0.f));
             const float ey = sg * (Ri[3 + a] - (a == 1 ? 1.f : 0.f));
             const float ez = sg * (Ri[6 + a] - (a == 2 ? 1.f : 0.f));
-            const float rx = (ui.x - uj[d].x) + ex, ry = (ui.y - uj[d].y) + ey, rz = (ui.z - uj[d].z) + ez;
+            const float3 uj = ld3(c.u, c.ld, nj[d]);  // reloaded (L1): not kept live through the fit
+            const float rx = (ui.x - uj.x) + ex, ry = (ui.y - uj.y) + ey, rz = (ui.z - uj.z) + ez;
             part += rx * rx + ry * ry + rz * rz;
         }
     }
