@@ -57,7 +57,7 @@ def algorithmic_bytes(kernel, nn, C, S):
 # (sha256 prefix of csrc/vd_kernels.cuh); see profiles/.
 NCU_TRAFFIC = {
     "update_x": (53094912 + 29696, "4ab0a9f574523246"),
-    "pcg": (41852160 + 75720960, "93825a7918a3b75b"),   # profiles/k_pcg_persistent_capsules96.md
+    "pcg": (49205248 + 75759360, "e8666cd69984c736"),   # profiles/k_pcg_persistent_capsules96.md
 }
 
 

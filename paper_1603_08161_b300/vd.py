@@ -238,11 +238,11 @@ class Lattice:
         return rep.as_dict()
 
     def get_warp(self, out_u=None, out_R=None):
-        """(u, R): numpy arrays, or the given CUDA tensors (out_R None with a CUDA out_u:
-        u only)."""
+        """(u, R) as new numpy arrays when neither output is given; else into the given
+        arrays (numpy or CUDA tensors), and with out_u alone u only (R is None)."""
         u = np.zeros((self.nn, 3), np.float32) if out_u is None else out_u
         pu, mem = _ptr(u)
-        if out_R is None and mem == VD_MEM_DEVICE:
+        if out_R is None and out_u is not None:
             R = None
         else:
             R = np.zeros((self.nn, 9), np.float32) if out_R is None else out_R
