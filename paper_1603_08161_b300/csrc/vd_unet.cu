@@ -106,11 +106,22 @@ __global__ void __launch_bounds__(128) k_conv3d(View in, const bf16 *__restrict_
 
 // The same convolution with the input staged in shared memory, for rows of at most
 // 16 XT voxels: a CTA of 4 warps owns the output rows (z, y0 .. y0+3), whole in x.  For
-// each 16-channel slab of the input it stages the 3 x 6 input rows around them (x from -1
-// to 16 XT, zero outside the volume); each warp then runs the 27 taps over the XT
-// 16-voxel tiles of its row, loading every weight fragment once per tap for all XT tiles.
+// each 16-channel slab of the input it stages (cp.async, zero-filled outside the volume)
+// the 3 x 6 input rows around them (x from -1 to 16 XT) and the slab's 27 x 16 x 16 NF
+// weights; each warp then runs the 27 taps over the XT 16-voxel tiles of its row,
+// loading every weight fragment once per tap for all XT tiles.
 constexpr int kRowsPerCta = 4;
-__host__ __device__ constexpr int rows_smem_bytes(int XT) { return 18 * (16 * XT + 2) * 32; }
+__host__ __device__ constexpr int rows_slab_bytes(int XT) { return 18 * (16 * XT + 2) * 32; }
+__host__ __device__ constexpr int rows_smem_bytes(int XT, int NF) { return rows_slab_bytes(XT) + 27 * 16 * NF * 32; }
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
 
 template <int NF, int XT>
 __global__ void __launch_bounds__(128) k_conv3d_rows(View in, const bf16 *__restrict__ Wt,
@@ -119,6 +130,7 @@ __global__ void __launch_bounds__(128) k_conv3d_rows(View in, const bf16 *__rest
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(32) float tile[4][16 * 16];
     bf16 *slab = reinterpret_cast<bf16 *>(smraw);  // [3 planes][6 rows][RW voxels][16 channels]
+    bf16 *wsl = reinterpret_cast<bf16 *>(smraw + rows_slab_bytes(XT));  // [27 taps][16][16 NF]
     constexpr int RW = 16 * XT + 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nyb = (out.H + kRowsPerCta - 1) / kRowsPerCta;
@@ -138,17 +150,22 @@ __global__ void __launch_bounds__(128) k_conv3d_rows(View in, const bf16 *__rest
             const int v = i >> 1, half = i & 1;
             const int xr = v % RW, rr = v / RW;
             const int zz = z - 1 + rr / 6, yy = y0 - 1 + rr % 6, xx = xr - 1;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (zz <= in.D && yy <= in.H && xx <= in.W)  // -1 and D / H / W are the zero halo
-                val = *reinterpret_cast<const uint4 *>(in.p + vox(in, zz, yy, xx) * in.C + k0 + 8 * half);
-            *reinterpret_cast<uint4 *>(slab + (size_t)v * 16 + 8 * half) = val;
+            const bool ok = zz <= in.D && yy <= in.H && xx <= in.W;  // -1 and D / H / W are the zero halo
+            cp_async16(slab + (size_t)v * 16 + 8 * half,
+                       ok ? (const void *)(in.p + vox(in, zz, yy, xx) * in.C + k0 + 8 * half) : (const void *)in.p, ok);
         }
+        // the slab's weights: rows tap * in.nc + k0 .. + 15 of Wt, CoutP wide
+        for (int i = threadIdx.x; i < 27 * 16 * 2 * NF; i += blockDim.x) {
+            const int row = i / (2 * NF), col8 = i - row * 2 * NF;  // 8-element pieces
+            const int tap = row >> 4, r = row & 15;
+            cp_async16(wsl + (size_t)row * CoutP + 8 * col8, Wt + ((size_t)tap * in.nc + k0 + r) * CoutP + 8 * col8, true);
+        }
+        cp_async_wait_all();
         __syncthreads();
         for (int tap = 0; tap < 27; tap++) {
             const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
 #pragma unroll
-            for (int j = 0; j < NF; j++)
-                wmma::load_matrix_sync(b[j], Wt + ((size_t)tap * in.nc + k0) * CoutP + 16 * j, CoutP);
+            for (int j = 0; j < NF; j++) wmma::load_matrix_sync(b[j], wsl + (size_t)tap * 16 * CoutP + 16 * j, CoutP);
             const bf16 *arow = slab + ((size_t)((dz + 1) * 6 + warp + 1 + dy) * RW + dx + 1) * 16;
 #pragma unroll
             for (int t = 0; t < XT; t++) {
@@ -505,7 +522,7 @@ void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool
     const int XT = xt <= 1 ? 1 : xt <= 2 ? 2 : xt <= 3 ? 3 : xt <= 6 ? 6 : 0;
     if (XT && XT * nf <= 18) {
         const int nb = out.D * ((out.H + kRowsPerCta - 1) / kRowsPerCta);
-        const int sm = rows_smem_bytes(XT);
+        const int sm = rows_smem_bytes(XT, nf);
 #define VD_ROWS(N, X) \
     if (nf == N && XT == X) return k_conv3d_rows<N, X><<<nb, 128, sm, st>>>(in, w, bias, out, creal, relu, outf);
         VD_ROWS(1, 1) VD_ROWS(1, 2) VD_ROWS(1, 3) VD_ROWS(1, 6)
@@ -661,13 +678,16 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
         k_pack_weights<<<blocks((long)np), 256>>>(L);
     }
     ok = ok && ualloc(U, &U->loss, 1) && ualloc(U, &U->io3, (size_t)3 * D * H * W);
-    // the staged convolutions of 96-voxel rows take more than the default 48 KB
-    ok = ok && cudaFuncSetAttribute(k_conv3d_rows<1, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    rows_smem_bytes(6)) == cudaSuccess &&
-         cudaFuncSetAttribute(k_conv3d_rows<2, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              rows_smem_bytes(6)) == cudaSuccess &&
-         cudaFuncSetAttribute(k_conv3d_rows<3, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              rows_smem_bytes(6)) == cudaSuccess;
+    // the staged convolutions may take more than the default 48 KB of shared memory
+#define VD_ROWS_SMEM(N, X) \
+    ok = ok && cudaFuncSetAttribute(k_conv3d_rows<N, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    rows_smem_bytes(X, N)) == cudaSuccess;
+    VD_ROWS_SMEM(1, 1) VD_ROWS_SMEM(1, 2) VD_ROWS_SMEM(1, 3) VD_ROWS_SMEM(1, 6)
+    VD_ROWS_SMEM(2, 1) VD_ROWS_SMEM(2, 2) VD_ROWS_SMEM(2, 3) VD_ROWS_SMEM(2, 6)
+    VD_ROWS_SMEM(3, 1) VD_ROWS_SMEM(3, 2) VD_ROWS_SMEM(3, 3) VD_ROWS_SMEM(3, 6)
+    VD_ROWS_SMEM(4, 1) VD_ROWS_SMEM(4, 2) VD_ROWS_SMEM(4, 3)
+    VD_ROWS_SMEM(6, 1) VD_ROWS_SMEM(6, 2) VD_ROWS_SMEM(6, 3)
+#undef VD_ROWS_SMEM
     if (!ok || cudaStreamCreateWithFlags(&U->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         vd_unet_destroy(U);
