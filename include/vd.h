@@ -206,9 +206,12 @@ vd_status vd_batch_create(vd_lattice *const *lattices, int count, vd_batch **out
 vd_status vd_batch_destroy(vd_batch *batch);
 
 /* Solve every lattice of the batch with the same parameters (the flip-flop of Sec. 7.1
- * per lattice, exactly as vd_solve): one captured CUDA graph in which each lattice's
- * schedule is a branch on one of several streams, launched on the first lattice's
- * stream.  `out` (may be NULL) receives `count` reports.  Synchronous. */
+ * per lattice, exactly as vd_solve): one captured CUDA graph, launched on the first
+ * lattice's stream, in which the lattices at or above a size threshold (chosen by
+ * vd_batch_tune; none by default) run first, one after another, each with its
+ * persistent position step, and every other lattice's schedule is a branch on one of
+ * several concurrent streams.  `out` (may be NULL) receives `count` reports.
+ * Synchronous. */
 vd_status vd_batch_solve(vd_batch *batch, const vd_solve_params *params, vd_solve_report *out);
 
 /* Enqueue the batched solve and return; vd_batch_get_reports waits for it. */
@@ -217,8 +220,11 @@ vd_status vd_batch_get_reports(vd_batch *batch, vd_solve_report *out);
 
 /* Autotune the batch for these parameters: time the solve for each candidate number
  * of concurrent branches (1, 2, 4, ... up to the batch size) and branch order (largest
- * lattice first, or as given), keep the fastest.  Runs the solve several times (the
- * lattices' warps change).  Reports the choice and its time per batched solve (ms). */
+ * lattice first, or as given), then for the fastest of those each size threshold
+ * (2^19, 2^17, 2^15, 2^13 active nodes) above which lattices run ahead with their
+ * persistent position step; keep the fastest.  Runs the solve several times (the
+ * lattices' warps change).  Reports the number of branches and the time per batched
+ * solve (ms). */
 vd_status vd_batch_tune(vd_batch *batch, const vd_solve_params *params, int *streams, float *ms);
 
 /* Kernel launches in one batched solve (after the first solve or tune). */

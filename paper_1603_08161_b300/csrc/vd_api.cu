@@ -1192,6 +1192,9 @@ struct vd_batch {
     vd_solve_params gparams{};
     int streams = 0;           // concurrent branches (0: not tuned, use min(count, 8))
     bool largest_first = true;
+    long coop_min = 0x7fffffffL;  // lattices of at least this many active nodes run their
+                                  // persistent position step, one after another, before
+                                  // the concurrent branches of the others
     bool pending = false;
     int launches = 0;
     std::string err;
@@ -1204,12 +1207,15 @@ vd_status bfail(vd_batch *B, vd_status s, const char *msg) {
     return s;
 }
 
-std::vector<char> batch_key(vd_batch *B, const vd_solve_params *P, int streams, bool largest) {
+long active_nodes(const vd_lattice *L) { return L->all ? L->c.nn : L->n_active_h; }
+
+std::vector<char> batch_key(vd_batch *B, const vd_solve_params *P, int streams, bool largest, long coop_min) {
     std::vector<char> k;
     auto put = [&](const void *p, size_t n) { k.insert(k.end(), (const char *)p, (const char *)p + n); };
     put(P, sizeof(*P));
     put(&streams, sizeof(streams));
     put(&largest, sizeof(largest));
+    put(&coop_min, sizeof(coop_min));
     for (vd_lattice *L : B->L) {
         put(&L->gen, sizeof(L->gen));
         put(&L->c, sizeof(Ctx));
@@ -1223,17 +1229,14 @@ std::vector<int> batch_order(vd_batch *B, bool largest) {
     std::vector<int> o(B->L.size());
     for (size_t i = 0; i < o.size(); i++) o[i] = (int)i;
     if (largest) {
-        std::stable_sort(o.begin(), o.end(), [&](int a, int b) {
-            const long na = B->L[a]->all ? B->L[a]->c.nn : B->L[a]->n_active_h;
-            const long nb = B->L[b]->all ? B->L[b]->c.nn : B->L[b]->n_active_h;
-            return na > nb;
-        });
+        std::stable_sort(o.begin(), o.end(),
+                         [&](int a, int b) { return active_nodes(B->L[a]) > active_nodes(B->L[b]); });
     }
     return o;
 }
 
-vd_status batch_build(vd_batch *B, const vd_solve_params *P, int streams, bool largest) {
-    std::vector<char> key = batch_key(B, P, streams, largest);
+vd_status batch_build(vd_batch *B, const vd_solve_params *P, int streams, bool largest, long coop_min) {
+    std::vector<char> key = batch_key(B, P, streams, largest, coop_min);
     if (B->gexec && key == B->key) return VD_OK;
     if (B->gexec) {
         cudaGraphExecDestroy(B->gexec);
@@ -1256,16 +1259,30 @@ vd_status batch_build(vd_batch *B, const vd_solve_params *P, int streams, bool l
     const std::vector<int> order = batch_order(B, largest);
     if (cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return bfail(B, VD_ERR_CUDA, "begin capture");
+    int launches = 0;
+    // the large lattices first, one after another on the capture stream: each one's
+    // persistent position step has the whole GPU (its CTAs must all be resident)
+    for (int idx : order) {
+        vd_lattice *L = B->L[idx];
+        if (active_nodes(L) < coop_min) continue;
+        const int saved = L->prof_class;
+        L->prof_class = -1;
+        L->counting = 0;
+        enqueue_solve(L, P, B->cap);
+        launches += L->counting;
+        L->prof_class = saved;
+    }
     cudaEventRecord(B->fork, B->cap);
     for (int p = 0; p < streams; p++) cudaStreamWaitEvent(B->side[p], B->fork, 0);
-    int launches = 0;
-    for (size_t k = 0; k < order.size(); k++) {
-        vd_lattice *L = B->L[order[k]];
+    int k = 0;
+    for (int idx : order) {
+        vd_lattice *L = B->L[idx];
+        if (active_nodes(L) >= coop_min) continue;
         const int saved = L->prof_class;
         L->prof_class = -1;
         L->in_batch = true;
         L->counting = 0;
-        enqueue_solve(L, P, B->side[k % streams]);
+        enqueue_solve(L, P, B->side[k++ % streams]);
         launches += L->counting;
         L->in_batch = false;
         L->prof_class = saved;
@@ -1335,7 +1352,7 @@ vd_status vd_batch_solve_async(vd_batch *B, const vd_solve_params *P) {
         if (!L->have_frame) return bfail(B, VD_ERR_STATE, "a lattice of the batch has no frame");
     }
     const int streams = B->streams > 0 ? B->streams : std::min<int>((int)B->L.size(), 8);
-    vd_status s = batch_build(B, P, streams, B->largest_first);
+    vd_status s = batch_build(B, P, streams, B->largest_first, B->coop_min);
     if (s != VD_OK) return s;
     cudaStream_t main = B->L[0]->stream;
     if (cudaGraphLaunch(B->gexec, main) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "graph launch");
@@ -1369,30 +1386,53 @@ vd_status vd_batch_tune(vd_batch *B, const vd_solve_params *P, int *streams_out,
     int best_s = 1;
     bool best_l = true;
     cudaStream_t main = B->L[0]->stream;
+    // build one candidate and time two replays (after one that warms the caches)
+    auto time_build = [&](int st, bool lf, long cm, float *out) -> vd_status {
+        vd_status s = batch_build(B, P, st, lf, cm);
+        if (s != VD_OK) return s;
+        float ms = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(B->t0, main);
+            if (cudaGraphLaunch(B->gexec, main) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "graph launch");
+            cudaEventRecord(B->t1, main);
+            if (cudaEventSynchronize(B->t1) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "synchronize");
+            float m = 0.f;
+            cudaEventElapsedTime(&m, B->t0, B->t1);
+            if (rep > 0) ms += m;
+        }
+        *out = ms;
+        return VD_OK;
+    };
     for (int lf = 1; lf >= 0; lf--)
         for (int ci = 0; ci < 7; ci++) {
             const int st = cand[ci];
             if (st > n && st != cand[0]) break;
-            vd_status s = batch_build(B, P, st, lf != 0);
-            if (s != VD_OK) return s;
             float ms = 0.f;
-            for (int rep = 0; rep < 3; rep++) {  // first replay warms the caches
-                cudaEventRecord(B->t0, main);
-                if (cudaGraphLaunch(B->gexec, main) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "graph launch");
-                cudaEventRecord(B->t1, main);
-                if (cudaEventSynchronize(B->t1) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "synchronize");
-                float m = 0.f;
-                cudaEventElapsedTime(&m, B->t0, B->t1);
-                if (rep > 0) ms += m;
-            }
+            vd_status s = time_build(st, lf != 0, 0x7fffffffL, &ms);
+            if (s != VD_OK) return s;
             if (ms < best) {
                 best = ms;
                 best_s = st;
                 best_l = lf != 0;
             }
         }
+    // then which lattices run their persistent position step ahead of the branches
+    long best_c = 0x7fffffffL;
+    for (long cm : {1L << 19, 1L << 17, 1L << 15, 1L << 13}) {
+        bool any = false;
+        for (vd_lattice *L : B->L) any = any || active_nodes(L) >= cm;
+        if (!any) continue;
+        float ms = 0.f;
+        vd_status s = time_build(best_s, best_l, cm, &ms);
+        if (s != VD_OK) return s;
+        if (ms < best) {
+            best = ms;
+            best_c = cm;
+        }
+    }
     B->streams = best_s;
     B->largest_first = best_l;
+    B->coop_min = best_c;
     if (streams_out) *streams_out = best_s;
     if (ms_out) *ms_out = best / 2.f;
     return VD_OK;
