@@ -1704,6 +1704,100 @@ __device__ __forceinline__ void mat_to_quat(const float R[9], float q[4]) {
 // rotation changed little, so the Jacobi sweeps converge at once; R = R0 D is formed
 // from the product of unit quaternions, which keeps it orthonormal.
 // Also accumulates E_reg (Eq. 4) with the new rotations (kFit = false: E_reg only).
+// Top eigenvector of a symmetric 4x4 matrix by Rayleigh-quotient iteration from q
+// (cubic convergence near an eigenvector), with a certificate: true only if
+// M = (mu - delta) I - N + 2 delta q q^T is positive definite (Cholesky), which holds
+// exactly when mu = q^T N q is the largest eigenvalue and every other one lies below
+// mu - delta.  On false the caller falls back to the Jacobi solve.
+__device__ __forceinline__ bool sym4_top_rqi(const float N[4][4], float q[4], float delta) {
+#pragma unroll 1
+    for (int it = 0; it < 3; it++) {
+        float Nq[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) Nq[r] = N[r][0] * q[0] + N[r][1] * q[1] + N[r][2] * q[2] + N[r][3] * q[3];
+        const float mu = q[0] * Nq[0] + q[1] * Nq[1] + q[2] * Nq[2] + q[3] * Nq[3];
+        // solve (N - mu I) y = q by Gaussian elimination with partial pivoting
+        float a[4][5];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) a[r][k] = N[r][k] - (r == k ? mu : 0.f);
+            a[r][4] = q[r];
+        }
+        bool ok = true;
+#pragma unroll
+        for (int col = 0; col < 4; col++) {
+            int piv = col;
+            float best = fabsf(a[col][col]);
+#pragma unroll
+            for (int r = col + 1; r < 4; r++)
+                if (fabsf(a[r][col]) > best) {
+                    best = fabsf(a[r][col]);
+                    piv = r;
+                }
+            if (piv != col) {
+#pragma unroll
+                for (int k = 0; k < 5; k++) {
+                    // swap rows col and piv without dynamic indexing of the registers
+#pragma unroll
+                    for (int r = col + 1; r < 4; r++)
+                        if (r == piv) {
+                            const float t = a[col][k];
+                            a[col][k] = a[r][k];
+                            a[r][k] = t;
+                        }
+                }
+            }
+            if (!(best > 1e-30f)) {
+                ok = false;  // exactly singular: q is already an eigenvector
+                break;
+            }
+            const float inv = 1.f / a[col][col];
+#pragma unroll
+            for (int r = col + 1; r < 4; r++) {
+                const float f = a[r][col] * inv;
+#pragma unroll
+                for (int k = col; k < 5; k++) a[r][k] -= f * a[col][k];
+            }
+        }
+        if (!ok) break;
+        float y[4];
+#pragma unroll
+        for (int r = 3; r >= 0; r--) {
+            float t = a[r][4];
+#pragma unroll
+            for (int k = r + 1; k < 4; k++) t -= a[r][k] * y[k];
+            y[r] = t / a[r][r];
+        }
+        const float n2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3];
+        if (!(n2 > 0.f) || !isfinite(n2)) break;
+        const float s = rsqrtf(n2);
+#pragma unroll
+        for (int r = 0; r < 4; r++) q[r] = y[r] * s;
+    }
+    float Nq[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) Nq[r] = N[r][0] * q[0] + N[r][1] * q[1] + N[r][2] * q[2] + N[r][3] * q[3];
+    const float mu = q[0] * Nq[0] + q[1] * Nq[1] + q[2] * Nq[2] + q[3] * Nq[3];
+    // certificate: Cholesky of M (all pivots > 0)
+    float L[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int k = 0; k <= r; k++) {
+            float m = 2.f * delta * q[r] * q[k] - N[r][k] + (r == k ? mu - delta : 0.f);
+#pragma unroll
+            for (int j = 0; j < k; j++) m -= L[r][j] * L[k][j];
+            if (r == k) {
+                if (!(m > 0.f)) return false;
+                L[r][r] = sqrtf(m);
+            } else {
+                L[r][k] = m / L[k][k];
+            }
+        }
+    return true;
+}
+
 // The near-tie redo of the rotation step in FP64 (rare), kept out of line so that its
 // registers do not count against the FP32 path's occupancy.
 __device__ __noinline__ double horn_top_eigvec_f64(float Sxx, float Sxy, float Sxz, float Syx, float Syy, float Syz,
@@ -1783,14 +1877,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) 
             for (int r = 0; r < 4; r++)
 #pragma unroll
                 for (int k = 0; k < 4; k++) scale = fmaxf(scale, fabsf(Nm[r][k]));
-            float qv[4];
-            const float gap = sym4_top_eigvec<float>(Nm, qv);
-            bool unique = gap > 1e-5f * scale;
-            if (gap < 1e-4f * scale) {
-                // near-singular block (the rotation's sensitivity exceeds 1e4): polar
-                // decomposition again in FP64
-                const double gd = horn_top_eigvec_f64(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz, qv);
-                unique = gd > 1e-12 * (double)scale;
+            // fast path: Rayleigh-quotient iteration from the identity (the previous
+            // rotation when warm), certified unique with a gap above 1e-4 of the scale;
+            // otherwise cyclic Jacobi, and FP64 for a near-singular block
+            float qv[4] = {1.f, 0.f, 0.f, 0.f};
+            bool unique = sym4_top_rqi(Nm, qv, 1e-4f * scale);
+            if (!unique) {
+                const float gap = sym4_top_eigvec<float>(Nm, qv);
+                unique = gap > 1e-5f * scale;
+                if (gap < 1e-4f * scale) {
+                    // near-singular block (the rotation's sensitivity exceeds 1e4): polar
+                    // decomposition again in FP64
+                    const double gd = horn_top_eigvec_f64(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz, qv);
+                    unique = gd > 1e-12 * (double)scale;
+                }
             }
             if (!unique) {
                 keep = true;

@@ -224,6 +224,19 @@ def test_solve_free_association(vd, mode):
         assert abs(rep["e_total"] - res["energy"][-1, 0]) / res["energy"][-1, 0] <= 1e-5
 
 
+@pytest.mark.parametrize("n,bricks", [(32, "2x4 rows of 32"), (48, "4x4 rows of 48")])
+def test_solve_parity_brick_partition(vd, n, bricks):
+    """All-nodes lattices whose persistent position step splits the slots into bricks
+    of full x-rows with neighbours in other CTAs along y and z (the host's plan for
+    these sizes on 148 SMs is noted); same tolerance as the other solves."""
+    fr = synth.sphere_frame(W=96, H=72, f=90.0, n=n, seed=6, n_sparse=40, name=f"sphere{n}")
+    lat, ref, rep, res, u, u0, R, R0 = _solve_pair(vd, fr, "all", 3, 10)
+    assert rep["gn_done"] == 3 and rep["cg_done"] == int(res["cg_done"][-1])
+    assert np.abs(u - u0).max() <= 1e-4 * fr.spacing
+    e0 = res["energy"][-1]
+    assert abs(rep["e_total"] - e0[0]) / e0[0] <= 1e-5
+
+
 def test_solve_parity_config2_surface(vd, cfg2):
     lat, ref, rep, res, u, u0, R, R0 = _solve_pair(vd, cfg2, "surface", 10, 20)
     assert np.abs(u - u0).max() <= 1e-4 * cfg2.spacing
