@@ -68,6 +68,7 @@ struct vd_lattice {
     int *scell = nullptr, *perm = nullptr, *pix = nullptr, *occ_cell = nullptr, *occ_beg = nullptr, *res_i = nullptr;
     float4 *frac_in = nullptr, *sp = nullptr, *sn = nullptr, *sfrac = nullptr, *rec = nullptr;
     float *wc = nullptr;
+    int4 *cell_part = nullptr;       // per block of the sample passes (kSMs x 8 entries)
     // sparse pairs
     int S = 0, cap_S = 0;
     float *sp_in = nullptr;
@@ -294,6 +295,7 @@ void refresh_ctx(vd_lattice *L) {
     c.scell = L->scell_s;
     c.S = L->S;
     c.e_target = L->gated ? L->rep_dev + 15 : nullptr;
+    c.cell_part = L->cell_part;
 }
 
 void set_params_ctx(Ctx &c, const vd_solve_params *p) {
@@ -332,8 +334,9 @@ Grid grids(vd_lattice *L) {
     g.node = blocks_for(nact);
     g.node4 = blocks_for((nact + 3) / 4, kThreads, 8);
     g.samp = blocks_for(round_pow2(std::max(L->n_samples_h, 1)));
-    const long slices = (round_pow2(std::max(L->n_occ_h, 1)) + kCellsPerBlock - 1) / kCellsPerBlock;
-    g.cells = (int)std::min<long>(std::max<long>(slices, (L->S + kThreads - 1) / kThreads), (long)kSMs * 8);
+    // about 128 samples per block (a power of two of them, so the grid, and the
+    // captured graph, stay the same for frames of similar size)
+    g.cells = (int)std::min<long>(std::max<long>(round_pow2(std::max(L->n_samples_h, 1)) / 128, 1), (long)kSMs * 8);
     g.vec4 = L->all && (L->c.nx % 4 == 0);
     return g;
 }
@@ -711,7 +714,8 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
         (s = dalloc(L, &L->counts, 8)) || (s = dalloc(L, &L->cnt, ld)) || (s = dalloc(L, &L->start, ld + 1)) ||
         (s = dalloc(L, &L->staging, 9 * ld)) || (s = dalloc(L, &L->rep_dev, 16)))
         return bail(s);
-    if ((s = dalloc(L, &L->surf_flag, ld)) || (s = dalloc(L, &L->pcg_bar, 4)))
+    if ((s = dalloc(L, &L->surf_flag, ld)) || (s = dalloc(L, &L->pcg_bar, 4)) ||
+        (s = dalloc(L, &L->cell_part, (size_t)kSMs * 8)))
         return bail(s);
     {
         int dev = 0, coop = 0, sms = 0;
@@ -849,7 +853,11 @@ vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const fl
     L->have_frame = true;
     TRY(frame_active_set(L));
     TRY(sync_sizes(L));
-    L->launches_frame = 13 + 1 + (L->all ? 0 : 7);
+    const int nbc = grids(L).cells;
+    k_cell_partition<<<(nbc + kThreads - 1) / kThreads, kThreads, 0, st>>>(L->occ_beg, L->counts + 1, nbc,
+                                                                          L->cell_part);
+    CKL();
+    L->launches_frame = 13 + 2 + (L->all ? 0 : 7);
     return VD_OK;
 }
 

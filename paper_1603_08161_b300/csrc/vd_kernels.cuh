@@ -57,6 +57,8 @@ struct Ctx {
     // Gauss-Newton early stop: after each iteration a gate compares E_total with
     // *e_target and marks the remaining iterations skipped (NULL: no gates)
     const double *e_target;
+    // per block of the sample passes: first and end occupied cell, first and end sample
+    const int4 *cell_part;
 };
 
 // Per-Gauss-Newton-iteration scalar block (FP64 sums and counters), zeroed at the
@@ -866,7 +868,29 @@ __device__ __forceinline__ void sparse_pairs(const Ctx &c, const VecView vec, fl
     }
 }
 
-constexpr int kCellsPerBlock = 16;
+// Partition of the sorted samples among the nb blocks of the sample passes: block b
+// takes samples [b n / nb, (b + 1) n / nb) and the occupied cells that hold them.
+__global__ void k_cell_partition(const int *__restrict__ occ_beg, const int *__restrict__ n_occ_p, int nb,
+                                 int4 *__restrict__ part) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int n_occ = *n_occ_p, ns = n_occ > 0 ? occ_beg[n_occ] : 0;
+    const int js = (int)(((long long)ns * b) / nb), je = (int)(((long long)ns * (b + 1)) / nb);
+    int lo = 0, hi = n_occ;  // first cell whose end is past js
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (occ_beg[m + 1] <= js) lo = m + 1;
+        else hi = m;
+    }
+    const int cb = lo;
+    hi = n_occ;  // first cell that starts at or after je
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (occ_beg[m] < je) lo = m + 1;
+        else hi = m;
+    }
+    part[b] = make_int4(cb, je > js ? lo : cb, js, je);
+}
 
 template <int kOp, bool kAll>
 __global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int it) {
@@ -881,10 +905,11 @@ __global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int 
     float *dst = (kOp == kOpApply) ? c.q : c.r;
     float part = 0.f;
     double partd = 0.0;
-    const int n_occ = *c.n_occ;
-    for (int cb = blockIdx.x * kCellsPerBlock; cb < n_occ; cb += gridDim.x * kCellsPerBlock)
-        cells_block<kOp, kAll, false>(c, vec, dst, c.minv, cb, min(cb + kCellsPerBlock, n_occ), tsm, part,
-                                      threadIdx.x, blockDim.x, 0);
+    // an equal share of the sorted samples per block (set up with the frame)
+    const int4 cp = c.cell_part[blockIdx.x];
+    if (cp.y > cp.x)
+        cells_block<kOp, kAll, false>(c, vec, dst, c.minv, cp.x, cp.y, tsm, part, threadIdx.x, blockDim.x, 0, cp.z,
+                                      cp.w);
     // pairs spread one per block first: one SM issuing all their atomics would be the tail
     sparse_pairs<kOp, kAll, false>(c, vec, dst, c.minv, blockIdx.x + gridDim.x * threadIdx.x,
                                    gridDim.x * blockDim.x, part, partd);
