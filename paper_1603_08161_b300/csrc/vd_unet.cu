@@ -104,16 +104,6 @@ __global__ void __launch_bounds__(128) k_conv3d(View in, const bf16 *__restrict_
     }
 }
 
-// The same convolution with the input staged in shared memory, for rows of at most
-// 16 XT voxels: a CTA of 4 warps owns the output rows (z, y0 .. y0+3), whole in x.  For
-// each 16-channel slab of the input it stages (cp.async, zero-filled outside the volume)
-// the 3 x 6 input rows around them (x from -1 to 16 XT) and the slab's 27 x 16 x 16 NF
-// weights; each warp then runs the 27 taps over the XT 16-voxel tiles of its row,
-// loading every weight fragment once per tap for all XT tiles.
-constexpr int kRowsPerCta = 4;
-__host__ __device__ constexpr int rows_slab_bytes(int XT) { return 18 * (16 * XT + 2) * 32; }
-__host__ __device__ constexpr int rows_smem_bytes(int XT, int NF) { return rows_slab_bytes(XT) + 27 * 16 * NF * 32; }
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
@@ -123,76 +113,175 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <int NF, int XT>
-__global__ void __launch_bounds__(128) k_conv3d_rows(View in, const bf16 *__restrict__ Wt,
-                                                     const float *__restrict__ bias, View out, int cout_real,
-                                                     int relu, float *__restrict__ outf) {
-    extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ __align__(32) float tile[4][16 * 16];
-    bf16 *slab = reinterpret_cast<bf16 *>(smraw);  // [3 planes][6 rows][RW voxels][16 channels]
-    bf16 *wsl = reinterpret_cast<bf16 *>(smraw + rows_slab_bytes(XT));  // [27 taps][16][16 NF]
-    constexpr int RW = 16 * XT + 2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nyb = (out.H + kRowsPerCta - 1) / kRowsPerCta;
-    const int z = blockIdx.x / nyb, y0 = (blockIdx.x - z * nyb) * kRowsPerCta;
-    const int y = y0 + warp;
-    const int CoutP = NF * 16;
-    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[XT][NF];
-#pragma unroll
-    for (int t = 0; t < XT; t++)
-#pragma unroll
-        for (int j = 0; j < NF; j++) wmma::fill_fragment(acc[t][j], 0.f);
-    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
-    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> b[NF];
-    for (int k0 = 0; k0 < in.nc; k0 += 16) {
-        __syncthreads();  // the previous slab is consumed
-        for (int i = threadIdx.x; i < 18 * RW * 2; i += blockDim.x) {
-            const int v = i >> 1, half = i & 1;
-            const int xr = v % RW, rr = v / RW;
-            const int zz = z - 1 + rr / 6, yy = y0 - 1 + rr % 6, xx = xr - 1;
-            const bool ok = zz <= in.D && yy <= in.H && xx <= in.W;  // -1 and D / H / W are the zero halo
-            cp_async16(slab + (size_t)v * 16 + 8 * half,
-                       ok ? (const void *)(in.p + vox(in, zz, yy, xx) * in.C + k0 + 8 * half) : (const void *)in.p, ok);
+// ------------------------------------------------------------------ tcgen05 convolution
+//
+// The convolution as an implicit GEMM on the 5th-generation tensor cores: a CTA of 4
+// warps owns the output rows (z, y0 .. y0+3), whole in x.  Output position m = r RW + j
+// (row r, column j < RW = W + 2; columns j >= W are computed and dropped) needs, for tap
+// (dz, dy, dx), the staged input voxel m + off(tap), off = ((dz+1)(R+2) + 1 + dy) RW + 1 + dx,
+// so every tap's A operand (128 positions x 16 channels, K-major) is the staged slab
+// read from a shifted start address.  The slab holds the 3 x 6 input rows (x from -1 to
+// W, zero outside the volume) of one 16-channel slice as two channel-half planes of 16 B
+// per voxel: core matrices of 8 voxels x 8 channels are 128 contiguous bytes (SBO = 128,
+// LBO = the plane stride).  B (N output channels x 16 input channels of one tap, K-major)
+// comes pre-packed in the same core layout.  One thread issues 27 taps x nblk MMAs
+// (M = 128, N = 16 NF, K = 16, BF16 in, FP32 accumulators in TMEM, nblk x N columns) per
+// input slice and commits them to an mbarrier; the warps then read their 32 TMEM lanes
+// (tcgen05.ld) for the epilogue.
+constexpr int kTcRows = 4;
+constexpr int kTcMaxW = 128;  // wider rows take the generic WMMA kernel
+__device__ __forceinline__ void st8(bf16 *p, const float f[8]);
+
+__host__ __device__ inline int tc_rw(int W) { return W + 2; }
+__host__ __device__ inline int tc_nblk(int W) { return (kTcRows * tc_rw(W) + 127) / 128; }
+// staged voxels per plane (the shifted A windows of the last block stay inside)
+__host__ __device__ inline int tc_nvp(int W) {
+    return (tc_nblk(W) * 128 + (2 * (kTcRows + 2) + 2) * tc_rw(W) + 2 + 7) / 8 * 8;
+}
+__host__ __device__ inline int tc_smem_bytes(int W, int NF) { return 2 * tc_nvp(W) * 16 + 27 * 16 * NF * 32 + 64; }
+__host__ inline int tc_tmem_cols(int W, int NF) {
+    int c = 32;
+    while (c < tc_nblk(W) * 16 * NF) c <<= 1;
+    return c;
+}
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    // shared-memory matrix descriptor, no swizzle: start >> 4, LBO >> 4, SBO >> 4, 0b001
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(mb), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+}
+
+template <int NF>
+__global__ void __launch_bounds__(128) k_conv3d_tc(View in, const bf16 *__restrict__ Wtc, const float *__restrict__ bias,
+                                                   View out, int cout_real, int relu, float *__restrict__ outf,
+                                                   int tmem_cols, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    constexpr int N = 16 * NF;
+    const int W = out.W, RW = tc_rw(W), nblk = tc_nblk(W), NVP = tc_nvp(W);
+    bf16 *planes = reinterpret_cast<bf16 *>(smraw);                     // [2][NVP][8]
+    bf16 *wsl = reinterpret_cast<bf16 *>(smraw + 2 * NVP * 16);         // [27][N/8][2][8][8]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nyb = (out.H + kTcRows - 1) / kTcRows;
+    const int z = blockIdx.x / nyb, y0 = (blockIdx.x - z * nyb) * kTcRows;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&tmem_base)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const int nz = 3 * (kTcRows + 2) * RW;  // staged voxels holding real rows
+    const int kchunks = in.nc / 16;
+    bool ok = true;
+    for (int kc = 0; kc < kchunks && ok; kc++) {
+        const int k0 = 16 * kc;
+        // stage the slice: 2 planes x NVP voxels of 16 B, then the slice's weights
+        for (int i = tid; i < 2 * NVP; i += 128) {
+            const int h = i / NVP, v = i - h * NVP;
+            bool valid = false;
+            const bf16 *src = in.p;
+            if (v < nz) {
+                const int xr = v % RW, t = v / RW;
+                const int yy = y0 - 1 + t % (kTcRows + 2), zz = z - 1 + t / (kTcRows + 2), xx = xr - 1;
+                valid = zz <= in.D && yy <= in.H && xx <= in.W;  // -1 and D / H / W are the zero halo
+                if (valid) src = in.p + vox(in, zz, yy, xx) * in.C + k0 + 8 * h;
+            }
+            cp_async16(planes + (size_t)i * 8, src, valid);
         }
-        // the slab's weights: rows tap * in.nc + k0 .. + 15 of Wt, CoutP wide
-        for (int i = threadIdx.x; i < 27 * 16 * 2 * NF; i += blockDim.x) {
-            const int row = i / (2 * NF), col8 = i - row * 2 * NF;  // 8-element pieces
-            const int tap = row >> 4, r = row & 15;
-            cp_async16(wsl + (size_t)row * CoutP + 8 * col8, Wt + ((size_t)tap * in.nc + k0 + r) * CoutP + 8 * col8, true);
-        }
+        const bf16 *wg = Wtc + (size_t)kc * 27 * N * 16;
+        for (int i = tid; i < 27 * N * 2; i += 128) cp_async16(wsl + (size_t)i * 8, wg + (size_t)i * 8, true);
         cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
         __syncthreads();
-        for (int tap = 0; tap < 27; tap++) {
-            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        if (tid == 0) {
+            const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(planes), b0 = (uint32_t)__cvta_generic_to_shared(wsl);
+            // D F32, A and B BF16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+            for (int tap = 0; tap < 27; tap++) {
+                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                const int off = ((dz + 1) * (kTcRows + 2) + 1 + dy) * RW + 1 + dx;
+                const uint64_t db = tc_desc(b0 + (uint32_t)tap * N * 32u, 128, 256);
+                for (int blk = 0; blk < nblk; blk++) {
+                    const uint64_t da = tc_desc(a0 + (uint32_t)(blk * 128 + off) * 16u, (uint32_t)NVP * 16u, 128);
+                    const uint32_t acc = (kc > 0 || tap > 0) ? 1u : 0u;
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                     tmem + (uint32_t)(blk * N)),
+                                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                         : "memory");
+        }
+        // the MMAs have read the slice (and written TMEM) before it is staged again; the
+        // verdict is the same for every thread (a barrier-wide and)
+        ok = __syncthreads_and(mbar_wait(mb, (uint32_t)(kc & 1)));
+        if (!ok && tid == 0) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        for (int blk = 0; blk < nblk; blk++) {
+            const int m = blk * 128 + warp * 32 + lane;
+            const int r = m / RW, j = m - r * RW, y = y0 + r;
+            const bool live = r < kTcRows && y < out.H && j < W;
 #pragma unroll
-            for (int j = 0; j < NF; j++) wmma::load_matrix_sync(b[j], wsl + (size_t)tap * 16 * CoutP + 16 * j, CoutP);
-            const bf16 *arow = slab + ((size_t)((dz + 1) * 6 + warp + 1 + dy) * RW + dx + 1) * 16;
+            for (int h = 0; h < NF; h++) {
+                uint32_t v[16];
+                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(blk * N + 16 * h);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (!live) continue;
+                float f[16];
 #pragma unroll
-            for (int t = 0; t < XT; t++) {
-                wmma::load_matrix_sync(a, arow + t * 256, 16);
+                for (int e = 0; e < 16; e++) {
+                    const int co = 16 * h + e;
+                    float a = __uint_as_float(v[e]) + ((bias && co < cout_real) ? bias[co] : 0.f);
+                    f[e] = relu ? fmaxf(a, 0.f) : a;
+                }
+                if (outf) {
 #pragma unroll
-                for (int j = 0; j < NF; j++) wmma::mma_sync(acc[t][j], a, b[j], acc[t][j]);
+                    for (int e = 0; e < 16; e++)
+                        if (16 * h + e < cout_real) outf[((size_t)(z * out.H + y) * W + j) * cout_real + 16 * h + e] = f[e];
+                } else if (16 * h + 16 <= cout_real) {
+                    bf16 *dst = out.p + vox(out, z, y, j) * out.C + 16 * h;
+                    st8(dst, f);
+                    st8(dst + 8, f + 8);
+                } else {
+                    for (int e = 0; e < 16 && 16 * h + e < cout_real; e++)
+                        out.p[vox(out, z, y, j) * out.C + 16 * h + e] = __float2bfloat16_rn(f[e]);
+                }
             }
         }
     }
-    if (y >= out.H) return;
-#pragma unroll
-    for (int t = 0; t < XT; t++)
-#pragma unroll
-        for (int j = 0; j < NF; j++) {
-            wmma::store_matrix_sync(tile[warp], acc[t][j], 16, wmma::mem_row_major);
-            __syncwarp();
-            for (int e = lane; e < 256; e += 32) {
-                const int x = 16 * t + (e >> 4), co = 16 * j + (e & 15);
-                if (x < out.W && co < cout_real) {
-                    float v = tile[warp][e] + (bias ? bias[co] : 0.f);
-                    if (relu) v = fmaxf(v, 0.f);
-                    if (outf) outf[((size_t)(z * out.H + y) * out.W + x) * cout_real + co] = v;
-                    else out.p[vox(out, z, y, x) * out.C + co] = __float2bfloat16_rn(v);
-                }
-            }
-            __syncwarp();
-        }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
 // dW[tap][ci][co] += sum_v X[v + off(tap)][ci] dY[v][co] over this block's voxel tiles;
@@ -420,6 +509,7 @@ __global__ void k_mse(const float *__restrict__ outf, const float *__restrict__ 
 struct LayerDev {
     float *w, *b, *gw, *gb, *mw, *vw, *mb, *vb;  // master / grads / moments (unpadded)
     bf16 *wf, *wt;                                // forward and dgrad weights (padded)
+    bf16 *wfc, *wtc;                              // the same in the tcgen05 operand layout
     int cin, cout, cinp, coutp;
 };
 
@@ -450,8 +540,16 @@ __global__ void k_pack_weights(LayerDev L) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int tap = i / (L.cinp * L.coutp), ci = (i / L.coutp) % L.cinp, co = i % L.coutp;
         const float w = (ci < L.cin && co < L.cout) ? L.w[((size_t)tap * L.cin + ci) * L.cout + co] : 0.f;
-        L.wf[i] = __float2bfloat16_rn(w);
-        L.wt[((size_t)(26 - tap) * L.coutp + co) * L.cinp + ci] = __float2bfloat16_rn(w);
+        const bf16 wb = __float2bfloat16_rn(w);
+        L.wf[i] = wb;
+        L.wt[((size_t)(26 - tap) * L.coutp + co) * L.cinp + ci] = wb;
+        // tcgen05 B operands, per 16-channel input slice kc and tap: N x 16, K-major core
+        // matrices [N/8][2][8][8]; forward N = Cout (K = Cin), dgrad N = Cin (K = Cout)
+        auto tc = [](int kc, int t, int n, int kl, int N) {
+            return ((((size_t)kc * 27 + t) * (N / 8) + n / 8) * 2 + kl / 8) * 64 + (n % 8) * 8 + (kl % 8);
+        };
+        L.wfc[tc(ci / 16, tap, co, ci % 16, L.coutp)] = wb;
+        L.wtc[tc(co / 16, 26 - tap, ci, co % 16, L.cinp)] = wb;
     }
 }
 
@@ -473,6 +571,7 @@ struct vd_unet {
     LayerDev L[kLayers];
     double *loss = nullptr;
     float *io3 = nullptr;  // FP32 output of the training forward pass
+    int *tc_err = nullptr; // set by a tensor-core convolution whose bounded wait gave up
     int step = 0;
     cudaStream_t st = nullptr;
 };
@@ -512,25 +611,26 @@ View slice(View v, int c0, int nc) {
     return v;
 }
 
-void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool dgrad, float *outf = nullptr) {
+void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool dgrad, int *err,
+          float *outf = nullptr) {
     // forward: in (cinp) -> out (coutp slice); dgrad: in = grad of out (coutp) -> grad of in (cinp)
     const bf16 *w = dgrad ? L.wt : L.wf;
     const int nf = (dgrad ? L.cinp : L.coutp) / 16;
     const int creal = dgrad ? L.cinp : L.cout;
     const float *bias = dgrad ? nullptr : L.b;
     const int xt = (out.W + 15) / 16;
-    const int XT = xt <= 1 ? 1 : xt <= 2 ? 2 : xt <= 3 ? 3 : xt <= 6 ? 6 : 0;
-    if (XT && XT * nf <= 18) {
-        const int nb = out.D * ((out.H + kRowsPerCta - 1) / kRowsPerCta);
-        const int sm = rows_smem_bytes(XT, nf);
-#define VD_ROWS(N, X) \
-    if (nf == N && XT == X) return k_conv3d_rows<N, X><<<nb, 128, sm, st>>>(in, w, bias, out, creal, relu, outf);
-        VD_ROWS(1, 1) VD_ROWS(1, 2) VD_ROWS(1, 3) VD_ROWS(1, 6)
-        VD_ROWS(2, 1) VD_ROWS(2, 2) VD_ROWS(2, 3) VD_ROWS(2, 6)
-        VD_ROWS(3, 1) VD_ROWS(3, 2) VD_ROWS(3, 3) VD_ROWS(3, 6)
-        VD_ROWS(4, 1) VD_ROWS(4, 2) VD_ROWS(4, 3)
-        VD_ROWS(6, 1) VD_ROWS(6, 2) VD_ROWS(6, 3)
-#undef VD_ROWS
+    if (out.W <= kTcMaxW && (nf == 1 || nf == 2 || nf == 3 || nf == 4 || nf == 6)) {
+        const int nb = out.D * ((out.H + kTcRows - 1) / kTcRows);
+        const int sm = tc_smem_bytes(out.W, nf), cols = tc_tmem_cols(out.W, nf);
+        const bf16 *wtc = dgrad ? L.wtc : L.wfc;
+        switch (nf) {
+            case 1: k_conv3d_tc<1><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            case 2: k_conv3d_tc<2><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            case 3: k_conv3d_tc<3><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            case 4: k_conv3d_tc<4><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            default: k_conv3d_tc<6><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
+        }
+        return;
     }
     const long tiles = (long)out.D * out.H * xt;
     const int nb = (int)((tiles + 3) / 4);
@@ -555,21 +655,21 @@ void wgrad(cudaStream_t st, View X, View dY, const LayerDev &L) {
 // the head writes FP32 to outf (node-major, 3 per node)
 void forward(vd_unet *U, cudaStream_t st, float *outf) {
     View e1 = slice(U->cat1, 32, 16), e2 = slice(U->cat2, 64, 32);
-    conv(st, U->x, U->L[A1], U->e1a, true, false);
-    conv(st, U->e1a, U->L[B1], e1, true, false);
+    conv(st, U->x, U->L[A1], U->e1a, true, false, U->tc_err);
+    conv(st, U->e1a, U->L[B1], e1, true, false, U->tc_err);
     k_pool<<<blocks(nvox(U->p1) * 2), 256, 0, st>>>(e1, U->p1);
-    conv(st, U->p1, U->L[A2], U->e2a, true, false);
-    conv(st, U->e2a, U->L[B2], e2, true, false);
+    conv(st, U->p1, U->L[A2], U->e2a, true, false, U->tc_err);
+    conv(st, U->e2a, U->L[B2], e2, true, false, U->tc_err);
     k_pool<<<blocks(nvox(U->p2) * 4), 256, 0, st>>>(e2, U->p2);
-    conv(st, U->p2, U->L[A3], U->e3a, true, false);
-    conv(st, U->e3a, U->L[B3], U->e3, true, false);
+    conv(st, U->p2, U->L[A3], U->e3a, true, false, U->tc_err);
+    conv(st, U->e3a, U->L[B3], U->e3, true, false, U->tc_err);
     k_upsample<<<blocks(nvox(U->cat2) * 8), 256, 0, st>>>(U->e3, slice(U->cat2, 0, 64));
-    conv(st, U->cat2, U->L[C2], U->d2a, true, false);
-    conv(st, U->d2a, U->L[D2], U->d2, true, false);
+    conv(st, U->cat2, U->L[C2], U->d2a, true, false, U->tc_err);
+    conv(st, U->d2a, U->L[D2], U->d2, true, false, U->tc_err);
     k_upsample<<<blocks(nvox(U->cat1) * 4), 256, 0, st>>>(U->d2, slice(U->cat1, 0, 32));
-    conv(st, U->cat1, U->L[C1], U->d1a, true, false);
-    conv(st, U->d1a, U->L[D1], U->d1, true, false);
-    conv(st, U->d1, U->L[HEAD], U->out, false, false, outf);
+    conv(st, U->cat1, U->L[C1], U->d1a, true, false, U->tc_err);
+    conv(st, U->d1a, U->L[D1], U->d1, true, false, U->tc_err);
+    conv(st, U->d1, U->L[HEAD], U->out, false, false, U->tc_err, outf);
 }
 
 void relu_bwd(cudaStream_t st, View g, View y) {
@@ -586,42 +686,42 @@ void backward(vd_unet *U, cudaStream_t st) {
     }
     // head (linear) and decoder level 1
     wgrad(st, U->d1, U->gout, U->L[HEAD]);
-    conv(st, U->gout, U->L[HEAD], U->gd1, false, true);
+    conv(st, U->gout, U->L[HEAD], U->gd1, false, true, U->tc_err);
     relu_bwd(st, U->gd1, U->d1);
     wgrad(st, U->d1a, U->gd1, U->L[D1]);
-    conv(st, U->gd1, U->L[D1], U->gd1a, false, true);
+    conv(st, U->gd1, U->L[D1], U->gd1a, false, true, U->tc_err);
     relu_bwd(st, U->gd1a, U->d1a);
     wgrad(st, U->cat1, U->gd1a, U->L[C1]);
-    conv(st, U->gd1a, U->L[C1], U->gcat1, false, true);  // [d up(d2), d e1 (skip)]
+    conv(st, U->gd1a, U->L[C1], U->gcat1, false, true, U->tc_err);  // [d up(d2), d e1 (skip)]
     // decoder level 2
     k_upsample_bwd<<<blocks(nvox(U->gd2) * 4), 256, 0, st>>>(slice(U->gcat1, 0, 32), U->gd2);
     relu_bwd(st, U->gd2, U->d2);
     wgrad(st, U->d2a, U->gd2, U->L[D2]);
-    conv(st, U->gd2, U->L[D2], U->gd2a, false, true);
+    conv(st, U->gd2, U->L[D2], U->gd2a, false, true, U->tc_err);
     relu_bwd(st, U->gd2a, U->d2a);
     wgrad(st, U->cat2, U->gd2a, U->L[C2]);
-    conv(st, U->gd2a, U->L[C2], U->gcat2, false, true);  // [d up(e3), d e2 (skip)]
+    conv(st, U->gd2a, U->L[C2], U->gcat2, false, true, U->tc_err);  // [d up(e3), d e2 (skip)]
     // bottleneck
     k_upsample_bwd<<<blocks(nvox(U->ge3) * 8), 256, 0, st>>>(slice(U->gcat2, 0, 64), U->ge3);
     relu_bwd(st, U->ge3, U->e3);
     wgrad(st, U->e3a, U->ge3, U->L[B3]);
-    conv(st, U->ge3, U->L[B3], U->ge3a, false, true);
+    conv(st, U->ge3, U->L[B3], U->ge3a, false, true, U->tc_err);
     relu_bwd(st, U->ge3a, U->e3a);
     wgrad(st, U->p2, U->ge3a, U->L[A3]);
-    conv(st, U->ge3a, U->L[A3], U->gp2, false, true);
+    conv(st, U->ge3a, U->L[A3], U->gp2, false, true, U->tc_err);
     // encoder level 2: d e2 = skip part + pooling part
     k_pool_bwd<<<blocks(nvox(ge2) * 4), 256, 0, st>>>(U->gp2, ge2, 1);
     relu_bwd(st, ge2, e2);
     wgrad(st, U->e2a, ge2, U->L[B2]);
-    conv(st, ge2, U->L[B2], U->ge2a, false, true);
+    conv(st, ge2, U->L[B2], U->ge2a, false, true, U->tc_err);
     relu_bwd(st, U->ge2a, U->e2a);
     wgrad(st, U->p1, U->ge2a, U->L[A2]);
-    conv(st, U->ge2a, U->L[A2], U->gp1, false, true);
+    conv(st, U->ge2a, U->L[A2], U->gp1, false, true, U->tc_err);
     // encoder level 1
     k_pool_bwd<<<blocks(nvox(ge1) * 2), 256, 0, st>>>(U->gp1, ge1, 1);
     relu_bwd(st, ge1, e1);
     wgrad(st, U->e1a, ge1, U->L[B1]);
-    conv(st, ge1, U->L[B1], U->ge1a, false, true);
+    conv(st, ge1, U->L[B1], U->ge1a, false, true, U->tc_err);
     relu_bwd(st, U->ge1a, U->e1a);
     wgrad(st, U->x, U->ge1a, U->L[A1]);
 }
@@ -668,7 +768,8 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
         const size_t nw = 27 * (size_t)L.cin * L.cout, np = 27 * (size_t)L.cinp * L.coutp;
         ok = ok && ualloc(U, &L.w, nw) && ualloc(U, &L.b, L.cout) && ualloc(U, &L.gw, np) &&
              ualloc(U, &L.gb, L.cout) && ualloc(U, &L.mw, nw) && ualloc(U, &L.vw, nw) && ualloc(U, &L.mb, L.cout) &&
-             ualloc(U, &L.vb, L.cout) && ualloc(U, &L.wf, np) && ualloc(U, &L.wt, np);
+             ualloc(U, &L.vb, L.cout) && ualloc(U, &L.wf, np) && ualloc(U, &L.wt, np) && ualloc(U, &L.wfc, np) &&
+             ualloc(U, &L.wtc, np);
         if (!ok) break;
         // He initialisation (the head starts small: the first prediction is ~0)
         std::normal_distribution<float> nd(0.f, std::sqrt(2.f / (27.f * L.cin)) * (l == HEAD ? 0.01f : 1.f));
@@ -677,17 +778,13 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
         cudaMemcpy(L.w, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
         k_pack_weights<<<blocks((long)np), 256>>>(L);
     }
-    ok = ok && ualloc(U, &U->loss, 1) && ualloc(U, &U->io3, (size_t)3 * D * H * W);
+    ok = ok && ualloc(U, &U->loss, 1) && ualloc(U, &U->io3, (size_t)3 * D * H * W) && ualloc(U, &U->tc_err, 1);
     // the staged convolutions may take more than the default 48 KB of shared memory
-#define VD_ROWS_SMEM(N, X) \
-    ok = ok && cudaFuncSetAttribute(k_conv3d_rows<N, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    rows_smem_bytes(X, N)) == cudaSuccess;
-    VD_ROWS_SMEM(1, 1) VD_ROWS_SMEM(1, 2) VD_ROWS_SMEM(1, 3) VD_ROWS_SMEM(1, 6)
-    VD_ROWS_SMEM(2, 1) VD_ROWS_SMEM(2, 2) VD_ROWS_SMEM(2, 3) VD_ROWS_SMEM(2, 6)
-    VD_ROWS_SMEM(3, 1) VD_ROWS_SMEM(3, 2) VD_ROWS_SMEM(3, 3) VD_ROWS_SMEM(3, 6)
-    VD_ROWS_SMEM(4, 1) VD_ROWS_SMEM(4, 2) VD_ROWS_SMEM(4, 3)
-    VD_ROWS_SMEM(6, 1) VD_ROWS_SMEM(6, 2) VD_ROWS_SMEM(6, 3)
-#undef VD_ROWS_SMEM
+#define VD_TC_SMEM(N) \
+    ok = ok && cudaFuncSetAttribute(k_conv3d_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    tc_smem_bytes(kTcMaxW, N)) == cudaSuccess;
+    VD_TC_SMEM(1) VD_TC_SMEM(2) VD_TC_SMEM(3) VD_TC_SMEM(4) VD_TC_SMEM(6)
+#undef VD_TC_SMEM
     if (!ok || cudaStreamCreateWithFlags(&U->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         vd_unet_destroy(U);
@@ -756,10 +853,20 @@ vd_status vd_unet_forward_async(vd_unet *U, const float *in6, float *out3, void 
     return cudaGetLastError() == cudaSuccess ? VD_OK : VD_ERR_CUDA;
 }
 
+// after a synchronisation: a tensor-core convolution whose bounded wait gave up
+static vd_status unet_wait_status(vd_unet *U) {
+    int e = 0;
+    if (cudaMemcpy(&e, U->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return VD_ERR_CUDA;
+    if (!e) return VD_OK;
+    cudaMemset(U->tc_err, 0, sizeof(int));
+    return VD_ERR_TIMEOUT;
+}
+
 vd_status vd_unet_forward(vd_unet *U, const float *in6, float *out3) {
     const vd_status s = vd_unet_forward_async(U, in6, out3, nullptr);
     if (s != VD_OK) return s;
-    return cudaStreamSynchronize(U->st) == cudaSuccess ? VD_OK : VD_ERR_CUDA;
+    if (cudaStreamSynchronize(U->st) != cudaSuccess) return VD_ERR_CUDA;
+    return unet_wait_status(U);
 }
 
 // One Adam step on the mean squared error between network(in6) and target3 (device
@@ -788,7 +895,7 @@ vd_status vd_unet_train_step(vd_unet *U, const float *in6, const float *target3,
     cudaMemcpyAsync(&h, U->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return VD_ERR_CUDA;
     if (loss) *loss = h;
-    return VD_OK;
+    return unet_wait_status(U);
 }
 
 // Weights file: "VDUNET01", int32 layer count, int32 Cin[], int32 Cout[], int32 parameter
