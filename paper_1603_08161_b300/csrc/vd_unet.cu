@@ -192,21 +192,26 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(View in, const bf16 *__restri
     const uint32_t tmem = tmem_base;
     const int nz = 3 * (kTcRows + 2) * RW;  // staged voxels holding real rows
     const int kchunks = in.nc / 16;
+    // the tail past the real rows is only ever read by dropped positions: zero it once
+    for (int i = tid; i < 2 * (NVP - nz); i += 128) {
+        const int h = i / (NVP - nz), v = nz + i - h * (NVP - nz);
+        *reinterpret_cast<uint4 *>(planes + ((size_t)h * NVP + v) * 8) = make_uint4(0u, 0u, 0u, 0u);
+    }
     bool ok = true;
     for (int kc = 0; kc < kchunks && ok; kc++) {
         const int k0 = 16 * kc;
-        // stage the slice: 2 planes x NVP voxels of 16 B, then the slice's weights
-        for (int i = tid; i < 2 * NVP; i += 128) {
-            const int h = i / NVP, v = i - h * NVP;
-            bool valid = false;
-            const bf16 *src = in.p;
-            if (v < nz) {
-                const int xr = v % RW, t = v / RW;
-                const int yy = y0 - 1 + t % (kTcRows + 2), zz = z - 1 + t / (kTcRows + 2), xx = xr - 1;
-                valid = zz <= in.D && yy <= in.H && xx <= in.W;  // -1 and D / H / W are the zero halo
-                if (valid) src = in.p + vox(in, zz, yy, xx) * in.C + k0 + 8 * h;
+        // stage the slice, row by row (x from -1 to W): 2 planes of 16 B per voxel, then
+        // the slice's weights
+        for (int t = 0; t < 3 * (kTcRows + 2); t++) {
+            const int yy = y0 - 1 + t % (kTcRows + 2), zz = z - 1 + t / (kTcRows + 2);
+            const bool row_ok = zz <= in.D && yy <= in.H;  // -1 and D / H are the zero halo
+            for (int i = tid; i < 2 * RW; i += 128) {
+                const int h = i >= RW, xr = i - h * RW, xx = xr - 1;
+                const bool valid = row_ok && xx <= in.W;
+                cp_async16(planes + ((size_t)h * NVP + t * RW + xr) * 8,
+                           valid ? (const void *)(in.p + vox(in, zz, yy, xx) * in.C + k0 + 8 * h) : (const void *)in.p,
+                           valid);
             }
-            cp_async16(planes + (size_t)i * 8, src, valid);
         }
         const bf16 *wg = Wtc + (size_t)kc * 27 * N * 16;
         for (int i = tid; i < 27 * N * 2; i += 128) cp_async16(wsl + (size_t)i * 8, wg + (size_t)i * 8, true);
