@@ -116,11 +116,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // ------------------------------------------------------------------ tcgen05 convolution
 //
 // The convolution as an implicit GEMM on the 5th-generation tensor cores: a CTA of 4
-// warps owns the output rows (z, y0 .. y0+3), whole in x.  Output position m = r RW + j
+// warps owns kTcRows output rows (z, y0 ..), whole in x.  Output position m = r RW + j
 // (row r, column j < RW = W + 2; columns j >= W are computed and dropped) needs, for tap
 // (dz, dy, dx), the staged input voxel m + off(tap), off = ((dz+1)(R+2) + 1 + dy) RW + 1 + dx,
 // so every tap's A operand (128 positions x 16 channels, K-major) is the staged slab
-// read from a shifted start address.  The slab holds the 3 x 6 input rows (x from -1 to
+// read from a shifted start address.  The slab holds the 3 x (kTcRows + 2) input rows (x from -1 to
 // W, zero outside the volume) of one 16-channel slice as two channel-half planes of 16 B
 // per voxel: core matrices of 8 voxels x 8 channels are 128 contiguous bytes (SBO = 128,
 // LBO = the plane stride).  B (N output channels x 16 input channels of one tap, K-major)
@@ -128,7 +128,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // (M = 128, N = 16 NF, K = 16, BF16 in, FP32 accumulators in TMEM, nblk x N columns) per
 // input slice and commits them to an mbarrier; the warps then read their 32 TMEM lanes
 // (tcgen05.ld) for the epilogue.
-constexpr int kTcRows = 4;
+constexpr int kTcRows = 2;
 constexpr int kTcMaxW = 128;  // wider rows take the generic WMMA kernel
 __device__ __forceinline__ void st8(bf16 *p, const float f[8]);
 
