@@ -14,12 +14,15 @@
 // Activations are stored channels-last with a one-voxel zero halo and 16 voxels of
 // slack after each row, so a 16-voxel tile at any tap offset stays inside its buffer:
 // every implicit-GEMM tile is a plain strided 16x16 matrix for the WMMA loads.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <mma.h>
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -47,6 +50,7 @@ int pad16(int c) { return (c + 15) / 16 * 16; }
 struct View {
     bf16 *p;
     int D, H, W, C, Wp, nc;
+    int c0;  // channel offset of the view in its buffer (p = buffer + c0)
 };
 
 __host__ __device__ inline size_t vox(const View &t, int z, int y, int x) {
@@ -165,11 +169,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
 }
 
 template <int NF>
-__global__ void __launch_bounds__(128) k_conv3d_tc(View in, const bf16 *__restrict__ Wtc, const float *__restrict__ bias,
+__global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUtensorMap tmap, View in,
+                                                   const bf16 *__restrict__ Wtc, const float *__restrict__ bias,
                                                    View out, int cout_real, int relu, float *__restrict__ outf,
                                                    int tmem_cols, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar, mbar_ld;
     __shared__ uint32_t tmem_base;
     constexpr int N = 16 * NF;
     const int W = out.W, RW = tc_rw(W), nblk = tc_nblk(W), NVP = tc_nvp(W);
@@ -178,8 +183,12 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(View in, const bf16 *__restri
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nyb = (out.H + kTcRows - 1) / kTcRows;
     const int z = blockIdx.x / nyb, y0 = (blockIdx.x - z * nyb) * kTcRows;
-    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar), mbl = (uint32_t)__cvta_generic_to_shared(&mbar_ld);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbl));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(&tmem_base)),
@@ -197,27 +206,36 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(View in, const bf16 *__restri
         const int h = i / (NVP - nz), v = nz + i - h * (NVP - nz);
         *reinterpret_cast<uint4 *>(planes + ((size_t)h * NVP + v) * 8) = make_uint4(0u, 0u, 0u, 0u);
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tail, for the tensor core
     bool ok = true;
     for (int kc = 0; kc < kchunks && ok; kc++) {
         const int k0 = 16 * kc;
-        // stage the slice, row by row (x from -1 to W): 2 planes of 16 B per voxel, then
-        // the slice's weights
-        for (int t = 0; t < 3 * (kTcRows + 2); t++) {
-            const int yy = y0 - 1 + t % (kTcRows + 2), zz = z - 1 + t / (kTcRows + 2);
-            const bool row_ok = zz <= in.D && yy <= in.H;  // -1 and D / H are the zero halo
-            for (int i = tid; i < 2 * RW; i += 128) {
-                const int h = i >= RW, xr = i - h * RW, xx = xr - 1;
-                const bool valid = row_ok && xx <= in.W;
-                cp_async16(planes + ((size_t)h * NVP + t * RW + xr) * 8,
-                           valid ? (const void *)(in.p + vox(in, zz, yy, xx) * in.C + k0 + 8 * h) : (const void *)in.p,
-                           valid);
-            }
+        // stage the slice with the tensor memory accelerator: per channel half one box of
+        // 8 channels x RW voxels x (kTcRows + 2) rows x 3 planes (buffer coordinates: x
+        // from the halo column, rows from y0 - 1, planes from z - 1; rows and planes past
+        // the buffer read as zero), plus the slice's weights by one bulk copy
+        if (tid == 0) {
+            const uint32_t wbytes = 27u * N * 32u;
+            const uint32_t bytes = 2u * (uint32_t)nz * 16u + wbytes;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbl), "r"(bytes) : "memory");
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+                asm volatile(
+                    "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                    "%4, %5}], [%6];" ::"r"((uint32_t)__cvta_generic_to_shared(planes + (size_t)h * NVP * 8)),
+                    "l"(&tmap), "r"(in.c0 + k0 + 8 * h), "r"(0), "r"(y0), "r"(z), "r"(mbl)
+                    : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(wsl)),
+                         "l"(Wtc + (size_t)kc * 27 * N * 16), "r"(wbytes), "r"(mbl)
+                         : "memory");
         }
-        const bf16 *wg = Wtc + (size_t)kc * 27 * N * 16;
-        for (int i = tid; i < 27 * N * 2; i += 128) cp_async16(wsl + (size_t)i * 8, wg + (size_t)i * 8, true);
-        cp_async_wait_all();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
-        __syncthreads();
+        const bool staged = __syncthreads_and(mbar_wait(mbl, (uint32_t)(kc & 1)));
+        if (!staged) {
+            if (tid == 0) atomicExch(err, 1);
+            ok = false;
+            break;
+        }
         if (tid == 0) {
             const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(planes), b0 = (uint32_t)__cvta_generic_to_shared(wsl);
             // D F32, A and B BF16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
@@ -577,6 +595,7 @@ struct vd_unet {
     double *loss = nullptr;
     float *io3 = nullptr;  // FP32 output of the training forward pass
     int *tc_err = nullptr; // set by a tensor-core convolution whose bounded wait gave up
+    std::map<const void *, CUtensorMap> tmaps;  // per activation / gradient buffer (TMA)
     int step = 0;
     cudaStream_t st = nullptr;
 };
@@ -603,6 +622,7 @@ bool make_view(vd_unet *U, View *v, int D, int H, int W, int C) {
     v->C = C;
     v->Wp = W + 18;
     v->nc = C;
+    v->c0 = 0;
     const size_t n = (size_t)(D + 2) * (H + 2) * v->Wp * C + 16 * (size_t)C;
     bf16 *p;
     if (!ualloc(U, &p, n)) return false;
@@ -612,12 +632,14 @@ bool make_view(vd_unet *U, View *v, int D, int H, int W, int C) {
 
 View slice(View v, int c0, int nc) {
     v.p += c0;
+    v.c0 += c0;
     v.nc = nc;
     return v;
 }
 
-void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool dgrad, int *err,
+void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool dgrad, vd_unet *U,
           float *outf = nullptr) {
+    int *err = U->tc_err;
     // forward: in (cinp) -> out (coutp slice); dgrad: in = grad of out (coutp) -> grad of in (cinp)
     const bf16 *w = dgrad ? L.wt : L.wf;
     const int nf = (dgrad ? L.cinp : L.coutp) / 16;
@@ -628,12 +650,13 @@ void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool
         const int nb = out.D * ((out.H + kTcRows - 1) / kTcRows);
         const int sm = tc_smem_bytes(out.W, nf), cols = tc_tmem_cols(out.W, nf);
         const bf16 *wtc = dgrad ? L.wtc : L.wfc;
+        const CUtensorMap &tm = U->tmaps.at(in.p - in.c0);
         switch (nf) {
-            case 1: k_conv3d_tc<1><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
-            case 2: k_conv3d_tc<2><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
-            case 3: k_conv3d_tc<3><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
-            case 4: k_conv3d_tc<4><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
-            default: k_conv3d_tc<6><<<nb, 128, sm, st>>>(in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            case 1: k_conv3d_tc<1><<<nb, 128, sm, st>>>(tm, in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            case 2: k_conv3d_tc<2><<<nb, 128, sm, st>>>(tm, in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            case 3: k_conv3d_tc<3><<<nb, 128, sm, st>>>(tm, in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            case 4: k_conv3d_tc<4><<<nb, 128, sm, st>>>(tm, in, wtc, bias, out, creal, relu, outf, cols, err); break;
+            default: k_conv3d_tc<6><<<nb, 128, sm, st>>>(tm, in, wtc, bias, out, creal, relu, outf, cols, err); break;
         }
         return;
     }
@@ -660,21 +683,21 @@ void wgrad(cudaStream_t st, View X, View dY, const LayerDev &L) {
 // the head writes FP32 to outf (node-major, 3 per node)
 void forward(vd_unet *U, cudaStream_t st, float *outf) {
     View e1 = slice(U->cat1, 32, 16), e2 = slice(U->cat2, 64, 32);
-    conv(st, U->x, U->L[A1], U->e1a, true, false, U->tc_err);
-    conv(st, U->e1a, U->L[B1], e1, true, false, U->tc_err);
+    conv(st, U->x, U->L[A1], U->e1a, true, false, U);
+    conv(st, U->e1a, U->L[B1], e1, true, false, U);
     k_pool<<<blocks(nvox(U->p1) * 2), 256, 0, st>>>(e1, U->p1);
-    conv(st, U->p1, U->L[A2], U->e2a, true, false, U->tc_err);
-    conv(st, U->e2a, U->L[B2], e2, true, false, U->tc_err);
+    conv(st, U->p1, U->L[A2], U->e2a, true, false, U);
+    conv(st, U->e2a, U->L[B2], e2, true, false, U);
     k_pool<<<blocks(nvox(U->p2) * 4), 256, 0, st>>>(e2, U->p2);
-    conv(st, U->p2, U->L[A3], U->e3a, true, false, U->tc_err);
-    conv(st, U->e3a, U->L[B3], U->e3, true, false, U->tc_err);
+    conv(st, U->p2, U->L[A3], U->e3a, true, false, U);
+    conv(st, U->e3a, U->L[B3], U->e3, true, false, U);
     k_upsample<<<blocks(nvox(U->cat2) * 8), 256, 0, st>>>(U->e3, slice(U->cat2, 0, 64));
-    conv(st, U->cat2, U->L[C2], U->d2a, true, false, U->tc_err);
-    conv(st, U->d2a, U->L[D2], U->d2, true, false, U->tc_err);
+    conv(st, U->cat2, U->L[C2], U->d2a, true, false, U);
+    conv(st, U->d2a, U->L[D2], U->d2, true, false, U);
     k_upsample<<<blocks(nvox(U->cat1) * 4), 256, 0, st>>>(U->d2, slice(U->cat1, 0, 32));
-    conv(st, U->cat1, U->L[C1], U->d1a, true, false, U->tc_err);
-    conv(st, U->d1a, U->L[D1], U->d1, true, false, U->tc_err);
-    conv(st, U->d1, U->L[HEAD], U->out, false, false, U->tc_err, outf);
+    conv(st, U->cat1, U->L[C1], U->d1a, true, false, U);
+    conv(st, U->d1a, U->L[D1], U->d1, true, false, U);
+    conv(st, U->d1, U->L[HEAD], U->out, false, false, U, outf);
 }
 
 void relu_bwd(cudaStream_t st, View g, View y) {
@@ -691,42 +714,42 @@ void backward(vd_unet *U, cudaStream_t st) {
     }
     // head (linear) and decoder level 1
     wgrad(st, U->d1, U->gout, U->L[HEAD]);
-    conv(st, U->gout, U->L[HEAD], U->gd1, false, true, U->tc_err);
+    conv(st, U->gout, U->L[HEAD], U->gd1, false, true, U);
     relu_bwd(st, U->gd1, U->d1);
     wgrad(st, U->d1a, U->gd1, U->L[D1]);
-    conv(st, U->gd1, U->L[D1], U->gd1a, false, true, U->tc_err);
+    conv(st, U->gd1, U->L[D1], U->gd1a, false, true, U);
     relu_bwd(st, U->gd1a, U->d1a);
     wgrad(st, U->cat1, U->gd1a, U->L[C1]);
-    conv(st, U->gd1a, U->L[C1], U->gcat1, false, true, U->tc_err);  // [d up(d2), d e1 (skip)]
+    conv(st, U->gd1a, U->L[C1], U->gcat1, false, true, U);  // [d up(d2), d e1 (skip)]
     // decoder level 2
     k_upsample_bwd<<<blocks(nvox(U->gd2) * 4), 256, 0, st>>>(slice(U->gcat1, 0, 32), U->gd2);
     relu_bwd(st, U->gd2, U->d2);
     wgrad(st, U->d2a, U->gd2, U->L[D2]);
-    conv(st, U->gd2, U->L[D2], U->gd2a, false, true, U->tc_err);
+    conv(st, U->gd2, U->L[D2], U->gd2a, false, true, U);
     relu_bwd(st, U->gd2a, U->d2a);
     wgrad(st, U->cat2, U->gd2a, U->L[C2]);
-    conv(st, U->gd2a, U->L[C2], U->gcat2, false, true, U->tc_err);  // [d up(e3), d e2 (skip)]
+    conv(st, U->gd2a, U->L[C2], U->gcat2, false, true, U);  // [d up(e3), d e2 (skip)]
     // bottleneck
     k_upsample_bwd<<<blocks(nvox(U->ge3) * 8), 256, 0, st>>>(slice(U->gcat2, 0, 64), U->ge3);
     relu_bwd(st, U->ge3, U->e3);
     wgrad(st, U->e3a, U->ge3, U->L[B3]);
-    conv(st, U->ge3, U->L[B3], U->ge3a, false, true, U->tc_err);
+    conv(st, U->ge3, U->L[B3], U->ge3a, false, true, U);
     relu_bwd(st, U->ge3a, U->e3a);
     wgrad(st, U->p2, U->ge3a, U->L[A3]);
-    conv(st, U->ge3a, U->L[A3], U->gp2, false, true, U->tc_err);
+    conv(st, U->ge3a, U->L[A3], U->gp2, false, true, U);
     // encoder level 2: d e2 = skip part + pooling part
     k_pool_bwd<<<blocks(nvox(ge2) * 4), 256, 0, st>>>(U->gp2, ge2, 1);
     relu_bwd(st, ge2, e2);
     wgrad(st, U->e2a, ge2, U->L[B2]);
-    conv(st, ge2, U->L[B2], U->ge2a, false, true, U->tc_err);
+    conv(st, ge2, U->L[B2], U->ge2a, false, true, U);
     relu_bwd(st, U->ge2a, U->e2a);
     wgrad(st, U->p1, U->ge2a, U->L[A2]);
-    conv(st, U->ge2a, U->L[A2], U->gp1, false, true, U->tc_err);
+    conv(st, U->ge2a, U->L[A2], U->gp1, false, true, U);
     // encoder level 1
     k_pool_bwd<<<blocks(nvox(ge1) * 2), 256, 0, st>>>(U->gp1, ge1, 1);
     relu_bwd(st, ge1, e1);
     wgrad(st, U->e1a, ge1, U->L[B1]);
-    conv(st, ge1, U->L[B1], U->ge1a, false, true, U->tc_err);
+    conv(st, ge1, U->L[B1], U->ge1a, false, true, U);
     relu_bwd(st, U->ge1a, U->e1a);
     wgrad(st, U->x, U->ge1a, U->L[A1]);
 }
@@ -762,6 +785,39 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
     for (auto &s : spec) {
         ok = ok && make_view(U, s.v, D / s.s, H / s.s, W / s.s, s.c);
         ok = ok && make_view(U, s.g, D / s.s, H / s.s, W / s.s, s.c);
+    }
+    // one TMA tensor map per buffer: dims (C, Wp, H + 2, D + 2), box (8 channels, W + 2
+    // voxels, kTcRows + 2 rows, 3 planes), zero fill past the buffer
+    if (ok) {
+        static void *encode = nullptr;
+        static std::once_flag once;
+        std::call_once(once, [] {
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &encode, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess ||
+                q != cudaDriverEntryPointSuccess)
+                encode = nullptr;
+        });
+        typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                     const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+        ok = encode != nullptr;
+        for (auto &sp : spec) {
+            for (View *v : {sp.v, sp.g}) {
+                if (!ok) break;
+                CUtensorMap tm;
+                const cuuint64_t dims[4] = {(cuuint64_t)v->C, (cuuint64_t)v->Wp, (cuuint64_t)v->H + 2, (cuuint64_t)v->D + 2};
+                const cuuint64_t strides[3] = {(cuuint64_t)v->C * 2, (cuuint64_t)v->C * 2 * v->Wp,
+                                               (cuuint64_t)v->C * 2 * v->Wp * (v->H + 2)};
+                const cuuint32_t box[4] = {8, (cuuint32_t)tc_rw(v->W), kTcRows + 2, 3};
+                const cuuint32_t es[4] = {1, 1, 1, 1};
+                ok = v->W > kTcMaxW ||
+                     ((EncodeFn)encode)(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, v->p, dims, strides, box, es,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                if (ok && v->W <= kTcMaxW) U->tmaps[v->p] = tm;
+            }
+        }
     }
     std::mt19937_64 rng(seed);
     for (int l = 0; l < kLayers && ok; l++) {
