@@ -12,8 +12,9 @@
 //   e3 = b3(a3(pool(e2)))   24^3, 64      d2 = d2c(c2(cat2))    48^3, 32
 //   out = head(d1c(c1(cat1)))  96^3, 3
 // Activations are stored channels-last with a one-voxel zero halo and 16 voxels of
-// slack after each row, so a 16-voxel tile at any tap offset stays inside its buffer:
-// every implicit-GEMM tile is a plain strided 16x16 matrix for the WMMA loads.
+// slack after each row, so a 16-voxel tile at any tap offset stays inside its buffer
+// (a plain strided 16x16 matrix for the WMMA kernels: wgrad and rows wider than 128).
+// The convolutions run on tcgen05 (k_conv3d_tc).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -124,14 +125,15 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // (row r, column j < RW = W + 2; columns j >= W are computed and dropped) needs, for tap
 // (dz, dy, dx), the staged input voxel m + off(tap), off = ((dz+1)(R+2) + 1 + dy) RW + 1 + dx,
 // so every tap's A operand (128 positions x 16 channels, K-major) is the staged slab
-// read from a shifted start address.  The slab holds the 3 x (kTcRows + 2) input rows (x from -1 to
-// W, zero outside the volume) of one 16-channel slice as two channel-half planes of 16 B
-// per voxel: core matrices of 8 voxels x 8 channels are 128 contiguous bytes (SBO = 128,
-// LBO = the plane stride).  B (N output channels x 16 input channels of one tap, K-major)
-// comes pre-packed in the same core layout.  One thread issues 27 taps x nblk MMAs
-// (M = 128, N = 16 NF, K = 16, BF16 in, FP32 accumulators in TMEM, nblk x N columns) per
-// input slice and commits them to an mbarrier; the warps then read their 32 TMEM lanes
-// (tcgen05.ld) for the epilogue.
+// read from a shifted start address.  The slab holds the 3 x (kTcRows + 2) input rows
+// (x from -1 to W, zero outside the volume) of one 16-channel slice as two channel-half
+// planes of 16 B per voxel, staged by two TMA box loads: core matrices of 8 voxels x 8
+// channels are 128 contiguous bytes (SBO = 128, LBO = the plane stride).  B (N output
+// channels x 16 input channels of one tap, K-major) comes pre-packed in the same core
+// layout (one bulk copy).  One thread issues 27 taps x nblk MMAs (M = 128, N = 16 NF,
+// K = 16, BF16 in, FP32 accumulators in TMEM, nblk x N columns) per input slice and
+// commits them to an mbarrier; the warps then read their 32 TMEM lanes (tcgen05.ld) for
+// the epilogue.
 constexpr int kTcRows = 2;
 constexpr int kTcMaxW = 128;  // wider rows take the generic WMMA kernel
 __device__ __forceinline__ void st8(bf16 *p, const float f[8]);
