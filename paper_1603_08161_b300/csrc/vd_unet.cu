@@ -109,15 +109,6 @@ __global__ void __launch_bounds__(128) k_conv3d(View in, const bf16 *__restrict_
     }
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
 // ------------------------------------------------------------------ tcgen05 convolution
 //
 // The convolution as an implicit GEMM on the 5th-generation tensor cores: a CTA of 4
