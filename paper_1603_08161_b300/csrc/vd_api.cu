@@ -65,7 +65,7 @@ struct vd_lattice {
     int n_src = 0, cap_src = 0;
     float *pts_in = nullptr, *nrm_in = nullptr, *res_f = nullptr;
     int *cell_in = nullptr, *tmp = nullptr, *order = nullptr, *head = nullptr, *hscan = nullptr;
-    int *scell = nullptr, *perm = nullptr, *pix = nullptr, *occ_cell = nullptr, *occ_beg = nullptr, *res_i = nullptr;
+    int *scell = nullptr, *perm = nullptr, *pix = nullptr, *refine = nullptr, *occ_cell = nullptr, *occ_beg = nullptr, *res_i = nullptr;
     float4 *frac_in = nullptr, *sp = nullptr, *sn = nullptr, *sfrac = nullptr, *rec = nullptr;
     float *wc = nullptr;
     int4 *cell_part = nullptr;       // per block of the sample passes (kSMs x 8 entries)
@@ -209,7 +209,7 @@ vd_status ensure_frame_caps(vd_lattice *L, int W, int H, int n_src) {
     if (n_src > L->cap_src || L->cap_src == 0) {  // the first frame allocates even for n_src = 0
         float **fs[] = {&L->pts_in, &L->nrm_in, &L->res_f};
         for (auto f : fs) dfree(L, *f);
-        int **is[] = {&L->cell_in, &L->tmp, &L->order, &L->head, &L->hscan, &L->scell, &L->perm, &L->pix,
+        int **is[] = {&L->cell_in, &L->tmp, &L->order, &L->head, &L->hscan, &L->scell, &L->perm, &L->pix, &L->refine,
                       &L->occ_cell, &L->occ_beg, &L->res_i};
         for (auto i : is) dfree(L, *i);
         float4 **f4[] = {&L->frac_in, &L->sp, &L->sn, &L->sfrac, &L->rec};
@@ -230,6 +230,7 @@ vd_status ensure_frame_caps(vd_lattice *L, int W, int H, int n_src) {
         TRY(dalloc(L, &L->scell, (size_t)cap));
         TRY(dalloc(L, &L->perm, (size_t)cap));
         TRY(dalloc(L, &L->pix, (size_t)cap));
+        TRY(dalloc(L, &L->refine, (size_t)cap));
         TRY(dalloc(L, &L->occ_cell, (size_t)cap));
         TRY(dalloc(L, &L->occ_beg, (size_t)cap + 1));
         TRY(dalloc(L, &L->res_i, (size_t)cap));
@@ -288,6 +289,7 @@ void refresh_ctx(vd_lattice *L) {
     c.n_occ = L->counts + 1;
     c.rec = L->rec;
     c.pix = L->pix;
+    c.refine = L->refine;
     c.wc = L->wc;
     c.fh = L->fh;
     c.ft = L->ft;
@@ -325,6 +327,7 @@ struct Grid {
     int node;    // blocks over active slots
     int node4;   // blocks over float4 groups of slots
     int samp, cells;
+    int refine;  // blocks of the FP64 re-association (a grid-stride loop over the list)
     bool vec4;   // all-nodes lattice with nx % 4 == 0: float4 stencil
 };
 
@@ -337,6 +340,7 @@ Grid grids(vd_lattice *L) {
     // about 128 samples per block (a power of two of them, so the grid, and the
     // captured graph, stay the same for frames of similar size)
     g.cells = (int)std::min<long>(std::max<long>(round_pow2(std::max(L->n_samples_h, 1)) / 128, 1), (long)kSMs * 8);
+    g.refine = std::min(g.samp, kSMs);
     g.vec4 = L->all && (L->c.nx % 4 == 0);
     return g;
 }
@@ -499,7 +503,10 @@ void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
     const Ctx c = L->c;
     Scal *sc = slot(L, g);
     const int K = P->cg_iters;
-    if (!(P->fixed_association && g > 0)) Lc.go(VD_KC_ASSOCIATE, k_associate<kAll>, gr.samp, kThreads, c, sc);
+    if (!(P->fixed_association && g > 0)) {
+        Lc.go(VD_KC_ASSOCIATE, k_associate<kAll>, gr.samp, kThreads, c, sc);
+        Lc.go(VD_KC_ASSOCIATE, k_associate_refine<kAll>, gr.refine, kThreads, c, sc);
+    }
     enqueue_rhs<kAll>(Lc, c, sc, gr, K);
     int G = 0, chunk = 0;
     if (persistent_plan(L, &G, &chunk)) {
@@ -984,8 +991,13 @@ vd_status vd_step_associate(vd_lattice *L, const vd_solve_params *P) {
     TRY(step_prepare(L, P, std::max(P ? P->cg_iters : 0, 1)));
     const Grid gr = grids(L);
     CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, L->stream));
-    if (L->all) k_associate<true><<<gr.samp, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
-    else k_associate<false><<<gr.samp, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+    if (L->all) {
+        k_associate<true><<<gr.samp, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+        k_associate_refine<true><<<gr.refine, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+    } else {
+        k_associate<false><<<gr.samp, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+        k_associate_refine<false><<<gr.refine, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+    }
     CKL();
     CK(cudaStreamSynchronize(L->stream));
     return VD_OK;
@@ -1571,6 +1583,7 @@ void warm_features_enqueue(vd_lattice *L, float *in6) {
     Scal *s0 = slot(L, 0);
     cudaMemsetAsync(L->scal, 0, 2 * L->scal_stride, st);
     k_associate<kAll><<<gr.samp, kThreads, 0, st>>>(c, s0);
+    k_associate_refine<kAll><<<gr.refine, kThreads, 0, st>>>(c, s0);
     k_fit_rotations<kAll, false><<<gr.node, kThreads, 0, st>>>(c, s0);
     k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, s0, 1, 0);
     Ctx cd = c;
@@ -1593,6 +1606,7 @@ void warm_select_enqueue(vd_lattice *L, const float *pred) {
     k_warm_apply<kAll><<<gr.node, kThreads, 0, st>>>(c, pred, bak);
     k_fit_rotations<kAll, true><<<gr.node, kThreads, 0, st>>>(c, s1);
     k_associate<kAll><<<gr.samp, kThreads, 0, st>>>(c, s1);
+    k_associate_refine<kAll><<<gr.refine, kThreads, 0, st>>>(c, s1);
     k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, s1, 1, 0);
     k_warm_select<kAll><<<gr.node, kThreads, 0, st>>>(c, s0, s1, bak, L->rep_dev + 11);
 }

@@ -59,6 +59,8 @@ struct Ctx {
     const double *e_target;
     // per block of the sample passes: first and end occupied cell, first and end sample
     const int4 *cell_part;
+    // samples whose FP32 association lies near a threshold, re-taken in FP64
+    int *refine;
 };
 
 // Per-Gauss-Newton-iteration scalar block (FP64 sums and counters), zeroed at the
@@ -67,7 +69,7 @@ struct Scal {
     double e_dense, e_sparse, e_reg, pad;
     int stop, cg_done, n_valid, n_refined, n_degenerate, assoc_ran;
     int skip;  // this Gauss-Newton iteration is skipped (the energy target was met)
-    int pad3;
+    int n_refine;  // entries of c.refine written by this iteration's association
     double rho[1];  // rho[0..K], then pq[0..K-1] follow (layout set by the host)
 };
 
@@ -553,16 +555,14 @@ __device__ bool target_normal_f64(const Ctx &c, int px, int py, V3<double> &n) {
 // Association of sorted sample i at the current warp, in precision T.  Returns true
 // (T = float only) when a decision (pixel, range, any Phi < 0) lies within a margin
 // of its threshold that FP32 rounding could cross; the caller then repeats it in FP64.
-template <typename T, bool kAll>
-__device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, float4 &rec) {
-    constexpr bool kF32 = sizeof(T) == 4;
-    pix = -1;
-    w_out = 0.f;
-    rec = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int cl = c.cell[i];
-    const float4 p4 = c.sp[i], n4 = c.sn[i];
-    T f[3];
-    if (kF32) {
+template <typename T>
+__device__ bool associate_finish(const Ctx &c, const float4 p4, V3<T> du, V3<T> dn, int &pix, float &w_out,
+                                 float4 &rec);
+
+// FP32 or FP64 trilinear weights of sample i in its cell
+template <typename T>
+__device__ __forceinline__ void sample_frac(const Ctx &c, int i, int cl, const float4 p4, T f[3]) {
+    if (sizeof(T) == 4) {
         const float4 f4 = c.frac[i];
         f[0] = f4.x;
         f[1] = f4.y;
@@ -573,6 +573,14 @@ __device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, fl
         f[1] = T(((double)p4.y - (double)c.oy) / (double)c.h - cy_);
         f[2] = T(((double)p4.z - (double)c.oz) / (double)c.h - cz_);
     }
+}
+
+template <typename T, bool kAll>
+__device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, float4 &rec) {
+    const int cl = c.cell[i];
+    const float4 p4 = c.sp[i], n4 = c.sn[i];
+    T f[3];
+    sample_frac<T>(c, i, cl, p4, f);
     V3<T> du{0, 0, 0}, dn{0, 0, 0};
     const V3<T> nh{T(n4.x), T(n4.y), T(n4.z)};
 #pragma unroll
@@ -590,6 +598,20 @@ __device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, fl
         dn.y += al * rn.y;
         dn.z += al * rn.z;
     }
+    return associate_finish<T>(c, p4, du, dn, pix, w_out, rec);
+}
+
+// The association of one sample from its corner sums du = sum alpha_k u_k and
+// dn = sum alpha_k R_k n^ (Sec. 5.1): warped point and model normal, nearest pixel,
+// target point and normal, Phi_d, Phi_n, Phi_v, w_c and the record.  FP32 (returns
+// whether a decision lies near a threshold) or FP64.
+template <typename T>
+__device__ bool associate_finish(const Ctx &c, const float4 p4, V3<T> du, V3<T> dn, int &pix, float &w_out,
+                                 float4 &rec) {
+    constexpr bool kF32 = sizeof(T) == 4;
+    pix = -1;
+    w_out = 0.f;
+    rec = make_float4(0.f, 0.f, 0.f, 0.f);
     const V3<T> q{T(p4.x) + du.x, T(p4.y) + du.y, T(p4.z) + du.z};
     V3<T> p = rot<T>(c.Rg, q);
     p.x += T(c.tg[0]);
@@ -669,9 +691,10 @@ __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
         float w;
         float4 rec;
         const bool near = associate_sample<float, kAll>(c, i, pix, w, rec);
-        if (near) {
-            associate_sample<double, kAll>(c, i, pix, w, rec);
+        if (near) {  // re-taken in FP64 by k_associate_refine (and counted there)
+            c.refine[atomicAdd(&sc->n_refine, 1)] = i;
             refined++;
+            continue;
         }
         c.pix[i] = pix;
         c.wc[i] = w;
@@ -681,6 +704,66 @@ __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
     block_add_int(valid, &sc->n_valid);
     block_add_int(refined, &sc->n_refined);
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->assoc_ran = 1;
+}
+
+// The samples k_associate found near a threshold, associated again in FP64: eight lanes
+// per sample gather the corner sums (one corner each, FP64 shuffles), lane 0 finishes.
+// A warp takes four consecutive list entries and the warps go to different blocks
+// first, so that a short list puts one warp on each SM and no two share an FP64 pipe.
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_associate_refine(Ctx c, Scal *sc) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->skip) return;
+    const int n = sc->n_refine;
+    int valid = 0;
+    const int k = threadIdx.x & 7;
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int wg = warp * gridDim.x + blockIdx.x;      // this warp's rank among all warps
+    const int per_round = 4 * nwarp * gridDim.x;
+    for (int g0 = 4 * wg; g0 < n; g0 += per_round) {  // the warp's loop bound is uniform
+        const int g = g0 + ((threadIdx.x & 31) >> 3);
+        V3<double> du{0.0, 0.0, 0.0}, dn{0.0, 0.0, 0.0};
+        int i = -1;
+        float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < n) {
+            i = c.refine[g];
+            const int cl = c.cell[i];
+            const float4 n4 = c.sn[i];
+            p4 = c.sp[i];
+            double f[3];
+            sample_frac<double>(c, i, cl, p4, f);
+            const int node = corner_node(c, cl, k);
+            const double al = trilinear_weight(f, k);
+            du = {al * (double)c.u[node], al * (double)c.u[c.ld + node], al * (double)c.u[2 * c.ld + node]};
+            float Rk[9];
+#pragma unroll
+            for (int e = 0; e < 9; e++) Rk[e] = c.R[e * c.ld + node];
+            const V3<double> rn = rot<double>(Rk, V3<double>{(double)n4.x, (double)n4.y, (double)n4.z});
+            dn = {al * rn.x, al * rn.y, al * rn.z};
+        }
+        // butterfly over the eight corner lanes (FP64: its order moves the sums by rounding only)
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            du.x += __shfl_xor_sync(FULL, du.x, o);
+            du.y += __shfl_xor_sync(FULL, du.y, o);
+            du.z += __shfl_xor_sync(FULL, du.z, o);
+            dn.x += __shfl_xor_sync(FULL, dn.x, o);
+            dn.y += __shfl_xor_sync(FULL, dn.y, o);
+            dn.z += __shfl_xor_sync(FULL, dn.z, o);
+        }
+        if (k == 0 && g < n) {
+            int pix;
+            float w;
+            float4 rec;
+            associate_finish<double>(c, p4, du, dn, pix, w, rec);
+            c.pix[i] = pix;
+            c.wc[i] = w;
+            store_rec(c, i, rec);
+            valid += w > 0.f;
+        }
+    }
+    block_add_int(valid, &sc->n_valid);
 }
 
 // ------------------------------------------------------------------ per-cell sample passes
