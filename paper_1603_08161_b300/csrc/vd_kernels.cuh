@@ -1817,90 +1817,64 @@ __device__ __forceinline__ void mat_to_quat(const float R[9], float q[4]) {
 // M = (mu - delta) I - N + 2 delta q q^T is positive definite (Cholesky), which holds
 // exactly when mu = q^T N q is the largest eigenvalue and every other one lies below
 // mu - delta.  On false the caller falls back to the Jacobi solve.
-__device__ __forceinline__ bool sym4_top_rqi(const float N[4][4], float q[4], float delta) {
+// The iteration stops once |N q - mu q| <= 1e-6 max|N| (FP32 rounding level), after at
+// most three steps.  Each step solves (N - mu I) y = q through the Schur complement of
+// the leading entry: writing N - mu I = [[m, b^T], [b, C]] (C the trailing 3x3 block),
+//   S = m det C - b^T adj(C) b  (= det(N - mu I)),  y0' = q0 det C - b^T adj(C) q_r,
+//   y  ~  (y0' det C,  S adj(C) q_r - y0' adj(C) b)
+// (the solution times det C * S; the sign and the scale drop out in the normalisation).
+// The step needs neither division nor pivoting, only C nonsingular: by interlacing
+// that holds while the top eigenvector keeps a component along the first axis, as it
+// does for the rotation increments of the warm-started fit; otherwise the step yields
+// no usable direction and the certificate fails.
+__device__ __forceinline__ bool sym4_top_rqi(const float N[4][4], float q[4], float delta, float scale) {
+    const float tol2 = 1e-12f * scale * scale;
+    float mu = 0.f;
 #pragma unroll 1
-    for (int it = 0; it < 3; it++) {
+    for (int it = 0;; it++) {
         float Nq[4];
 #pragma unroll
         for (int r = 0; r < 4; r++) Nq[r] = N[r][0] * q[0] + N[r][1] * q[1] + N[r][2] * q[2] + N[r][3] * q[3];
-        const float mu = q[0] * Nq[0] + q[1] * Nq[1] + q[2] * Nq[2] + q[3] * Nq[3];
-        // solve (N - mu I) y = q by Gaussian elimination with partial pivoting
-        float a[4][5];
+        mu = q[0] * Nq[0] + q[1] * Nq[1] + q[2] * Nq[2] + q[3] * Nq[3];
+        float res2 = 0.f;
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) a[r][k] = N[r][k] - (r == k ? mu : 0.f);
-            a[r][4] = q[r];
-        }
-        bool ok = true;
-#pragma unroll
-        for (int col = 0; col < 4; col++) {
-            int piv = col;
-            float best = fabsf(a[col][col]);
-#pragma unroll
-            for (int r = col + 1; r < 4; r++)
-                if (fabsf(a[r][col]) > best) {
-                    best = fabsf(a[r][col]);
-                    piv = r;
-                }
-            if (piv != col) {
-#pragma unroll
-                for (int k = 0; k < 5; k++) {
-                    // swap rows col and piv without dynamic indexing of the registers
-#pragma unroll
-                    for (int r = col + 1; r < 4; r++)
-                        if (r == piv) {
-                            const float t = a[col][k];
-                            a[col][k] = a[r][k];
-                            a[r][k] = t;
-                        }
-                }
-            }
-            if (!(best > 1e-30f)) {
-                ok = false;  // exactly singular: q is already an eigenvector
-                break;
-            }
-            const float inv = 1.f / a[col][col];
-#pragma unroll
-            for (int r = col + 1; r < 4; r++) {
-                const float f = a[r][col] * inv;
-#pragma unroll
-                for (int k = col; k < 5; k++) a[r][k] -= f * a[col][k];
-            }
-        }
-        if (!ok) break;
-        float y[4];
-#pragma unroll
-        for (int r = 3; r >= 0; r--) {
-            float t = a[r][4];
-#pragma unroll
-            for (int k = r + 1; k < 4; k++) t -= a[r][k] * y[k];
-            y[r] = t / a[r][r];
-        }
+        for (int r = 0; r < 4; r++) res2 += (Nq[r] - mu * q[r]) * (Nq[r] - mu * q[r]);
+        if (res2 <= tol2 || it == 3) break;
+        const float m = N[0][0] - mu, b1 = N[1][0], b2 = N[2][0], b3 = N[3][0];
+        const float c11 = N[1][1] - mu, c12 = N[1][2], c13 = N[1][3];
+        const float c22 = N[2][2] - mu, c23 = N[2][3], c33 = N[3][3] - mu;
+        // adj(C) (symmetric) and det C
+        const float a11 = c22 * c33 - c23 * c23, a12 = c13 * c23 - c12 * c33, a13 = c12 * c23 - c13 * c22;
+        const float a22 = c11 * c33 - c13 * c13, a23 = c12 * c13 - c11 * c23, a33 = c11 * c22 - c12 * c12;
+        const float dC = c11 * a11 + c12 * a12 + c13 * a13;
+        const float zb1 = a11 * b1 + a12 * b2 + a13 * b3, zb2 = a12 * b1 + a22 * b2 + a23 * b3,
+                    zb3 = a13 * b1 + a23 * b2 + a33 * b3;
+        const float zq1 = a11 * q[1] + a12 * q[2] + a13 * q[3], zq2 = a12 * q[1] + a22 * q[2] + a23 * q[3],
+                    zq3 = a13 * q[1] + a23 * q[2] + a33 * q[3];
+        const float S = m * dC - (b1 * zb1 + b2 * zb2 + b3 * zb3);
+        const float y0 = q[0] * dC - (b1 * zq1 + b2 * zq2 + b3 * zq3);
+        const float y[4] = {y0 * dC, S * zq1 - y0 * zb1, S * zq2 - y0 * zb2, S * zq3 - y0 * zb3};
         const float n2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3];
-        if (!(n2 > 0.f) || !isfinite(n2)) break;
-        const float s = rsqrtf(n2);
+        if (!(n2 > 1e-30f) || !isfinite(n2)) break;
+        const float sc = rsqrtf(n2);
 #pragma unroll
-        for (int r = 0; r < 4; r++) q[r] = y[r] * s;
+        for (int r = 0; r < 4; r++) q[r] = y[r] * sc;
     }
-    float Nq[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) Nq[r] = N[r][0] * q[0] + N[r][1] * q[1] + N[r][2] * q[2] + N[r][3] * q[3];
-    const float mu = q[0] * Nq[0] + q[1] * Nq[1] + q[2] * Nq[2] + q[3] * Nq[3];
-    // certificate: Cholesky of M (all pivots > 0)
-    float L[4][4];
+    // certificate: Cholesky of M (all pivots > 0), reciprocal square roots of the pivots
+    float L[4][4], rl[4];
 #pragma unroll
     for (int r = 0; r < 4; r++)
 #pragma unroll
         for (int k = 0; k <= r; k++) {
-            float m = 2.f * delta * q[r] * q[k] - N[r][k] + (r == k ? mu - delta : 0.f);
+            float mm = 2.f * delta * q[r] * q[k] - N[r][k] + (r == k ? mu - delta : 0.f);
 #pragma unroll
-            for (int j = 0; j < k; j++) m -= L[r][j] * L[k][j];
+            for (int j = 0; j < k; j++) mm -= L[r][j] * L[k][j];
             if (r == k) {
-                if (!(m > 0.f)) return false;
-                L[r][r] = sqrtf(m);
+                if (!(mm > 0.f)) return false;
+                rl[r] = rsqrtf(mm);
+                L[r][r] = mm * rl[r];
             } else {
-                L[r][k] = m / L[k][k];
+                L[r][k] = mm * rl[k];
             }
         }
     return true;
@@ -1989,7 +1963,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) 
             // rotation when warm), certified unique with a gap above 1e-4 of the scale;
             // otherwise cyclic Jacobi, and FP64 for a near-singular block
             float qv[4] = {1.f, 0.f, 0.f, 0.f};
-            bool unique = sym4_top_rqi(Nm, qv, 1e-4f * scale);
+            bool unique = sym4_top_rqi(Nm, qv, 1e-4f * scale, scale);
             if (!unique) {
                 const float gap = sym4_top_eigvec<float>(Nm, qv);
                 unique = gap > 1e-5f * scale;
