@@ -505,9 +505,12 @@ void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
     const int K = P->cg_iters;
     if (!(P->fixed_association && g > 0)) {
         Lc.go(VD_KC_ASSOCIATE, k_associate<kAll>, gr.samp, kThreads, c, sc);
-        Lc.go(VD_KC_ASSOCIATE, k_associate_refine<kAll>, gr.refine, kThreads, c, sc);
+        // the FP64 re-association runs in the first blocks of the right-hand side's node pass
+        Lc.go(VD_KC_RHS, k_rhs_nodes_refine<kAll>, gr.refine + gr.node, kThreads, c, sc, gr.refine);
+        Lc.go(VD_KC_RHS, k_cells<kOpRhs, kAll>, gr.cells, kThreads, c, sc, K, 0);
+    } else {
+        enqueue_rhs<kAll>(Lc, c, sc, gr, K);
     }
-    enqueue_rhs<kAll>(Lc, c, sc, gr, K);
     int G = 0, chunk = 0;
     if (persistent_plan(L, &G, &chunk)) {
         launch_persistent<kAll>(L, Lc, sc, K, P->cg_tol * P->cg_tol, 1, G, chunk);
@@ -516,7 +519,9 @@ void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
         Lc.go(VD_KC_ROTATION, k_add_increment<kAll>, gr.node, kThreads, c, (const Scal *)sc);
     }
     Lc.go(VD_KC_ROTATION, k_fit_rotations<kAll, true>, gr.node, kThreads, c, sc);
-    Lc.go(VD_KC_ENERGY, k_cells<kOpEnergy, kAll>, gr.cells, kThreads, c, sc, K, 0);
+    // the energies after the update (this iteration's correspondences): for the report
+    // after the last iteration, and after every one when the energy target gates the next
+    if (c.e_target || g + 1 == P->gn_iters) Lc.go(VD_KC_ENERGY, k_cells<kOpEnergy, kAll>, gr.cells, kThreads, c, sc, K, 0);
     if (c.e_target && g + 1 < P->gn_iters) Lc.go(-1, k_gn_gate, 1, 32, c, (const Scal *)sc, slot(L, g + 1));
 }
 

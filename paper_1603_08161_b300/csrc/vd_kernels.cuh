@@ -710,17 +710,15 @@ __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
 // per sample gather the corner sums (one corner each, FP64 shuffles), lane 0 finishes.
 // A warp takes four consecutive list entries and the warps go to different blocks
 // first, so that a short list puts one warp on each SM and no two share an FP64 pipe.
+// Block `bid` of `nb` blocks on the list.
 template <bool kAll>
-__global__ void __launch_bounds__(kThreads) k_associate_refine(Ctx c, Scal *sc) {
-    pdl_wait();
-    pdl_trigger();
-    if (sc->skip) return;
+__device__ __forceinline__ void associate_refine_block(const Ctx &c, Scal *sc, int bid, int nb) {
     const int n = sc->n_refine;
     int valid = 0;
     const int k = threadIdx.x & 7;
     const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int wg = warp * gridDim.x + blockIdx.x;      // this warp's rank among all warps
-    const int per_round = 4 * nwarp * gridDim.x;
+    const int wg = warp * nb + bid;                    // this warp's rank among all warps
+    const int per_round = 4 * nwarp * nb;
     for (int g0 = 4 * wg; g0 < n; g0 += per_round) {  // the warp's loop bound is uniform
         const int g = g0 + ((threadIdx.x & 31) >> 3);
         V3<double> du{0.0, 0.0, 0.0}, dn{0.0, 0.0, 0.0};
@@ -764,6 +762,14 @@ __global__ void __launch_bounds__(kThreads) k_associate_refine(Ctx c, Scal *sc) 
         }
     }
     block_add_int(valid, &sc->n_valid);
+}
+
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_associate_refine(Ctx c, Scal *sc) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->skip) return;
+    associate_refine_block<kAll>(c, sc, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------ per-cell sample passes
@@ -1009,12 +1015,9 @@ __global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int 
 //   b_k = -w_r sum_{j in N_k} [2 (u_k - u_j) - (R_k + R_j - 2I)(t^_k - t^_j)],
 //   diag_k = 2 w_r |N_k|.  Written with plain stores (the sample pass adds after).
 template <bool kAll>
-__global__ void __launch_bounds__(kThreads) k_rhs_nodes(Ctx c, const Scal *sc) {
-    pdl_wait();
-    pdl_trigger();
-    if (sc->skip) return;
+__device__ __forceinline__ void rhs_nodes_block(const Ctx &c, int bid, int nb) {
     const int N = active_count<kAll>(c);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+    for (int s = bid * blockDim.x + threadIdx.x; s < N; s += nb * blockDim.x) {
         const int i = slot_node<kAll>(c, s);
         int nb[6];
         neighbours<kAll>(c, s, nb);
@@ -1041,6 +1044,26 @@ __global__ void __launch_bounds__(kThreads) k_rhs_nodes(Ctx c, const Scal *sc) {
         const float dg = 2.f * c.w_r * (float)deg;
         st3(c.minv, c.ld, s, make_float3(dg, dg, dg));
     }
+}
+
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_rhs_nodes(Ctx c, const Scal *sc) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->skip) return;
+    rhs_nodes_block<kAll>(c, blockIdx.x, gridDim.x);
+}
+
+// k_rhs_nodes with the FP64 re-association of the listed samples in its first `nref`
+// blocks: the re-association is a latency-bound tail of a few warps, which the node
+// pass (independent of the correspondences) runs beside.
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads, 4) k_rhs_nodes_refine(Ctx c, Scal *sc, int nref) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->skip) return;
+    if ((int)blockIdx.x < nref) associate_refine_block<kAll>(c, sc, blockIdx.x, nref);
+    else rhs_nodes_block<kAll>(c, blockIdx.x - nref, gridDim.x - nref);
 }
 
 // PCG vectors are walked as float4 groups of one component plane per blockIdx.y (the
