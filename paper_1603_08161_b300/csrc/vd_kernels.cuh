@@ -530,143 +530,33 @@ __device__ __forceinline__ double depth_at(const Ctx &c, int px, int py) {
     return (double)c.depth[(size_t)py * c.W + px];
 }
 
-// Target normal in FP64 from the depth map (plain central differences of V).
-__device__ bool target_normal_f64(const Ctx &c, int px, int py, V3<double> &n) {
+// Target normal in FP64 from the depth map (plain central differences of V, with
+// V(d, u, v) = d ((u - c_x) / f_x, (v - c_y) / f_y, 1); rfx, rfy = 1 / f_x, 1 / f_y).
+__device__ bool target_normal_f64(const Ctx &c, int px, int py, double rfx, double rfy, V3<double> &n) {
     if (px < 1 || py < 1 || px + 1 >= c.W || py + 1 >= c.H) return false;
     const double d0 = depth_at(c, px, py), dl = depth_at(c, px - 1, py), dr = depth_at(c, px + 1, py);
     const double du = depth_at(c, px, py - 1), dd = depth_at(c, px, py + 1);
     if (!(d0 > 0 && dl > 0 && dr > 0 && du > 0 && dd > 0)) return false;
-    const double fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy;
-    auto V = [&](double d, int uu, int vv) {
-        return V3<double>{d * ((uu - cx) / fx), d * ((vv - cy) / fy), d};
-    };
+    const double cx = c.cx, cy = c.cy;
+    auto V = [&](double d, int uu, int vv) { return V3<double>{d * ((uu - cx) * rfx), d * ((vv - cy) * rfy), d}; };
     const V3<double> a = V(dr, px + 1, py), b = V(dl, px - 1, py), e = V(dd, px, py + 1), f = V(du, px, py - 1);
     const V3<double> ex{a.x - b.x, a.y - b.y, a.z - b.z}, ey{e.x - f.x, e.y - f.y, e.z - f.z};
     V3<double> m{ex.y * ey.z - ex.z * ey.y, ex.z * ey.x - ex.x * ey.z, ex.x * ey.y - ex.y * ey.x};
-    const double L = sqrt(dot(m, m));
-    if (!(L > 0)) return false;
-    m = {m.x / L, m.y / L, m.z / L};
+    const double L2 = dot(m, m);
+    if (!(L2 > 0)) return false;
+    const double iL = 1.0 / sqrt(L2);
+    m = {m.x * iL, m.y * iL, m.z * iL};
     const V3<double> P = V(d0, px, py);
     if (dot(m, P) > 0) m = {-m.x, -m.y, -m.z};
     n = m;
     return true;
 }
 
-// Association of sorted sample i at the current warp, in precision T.  Returns true
-// (T = float only) when a decision (pixel, range, any Phi < 0) lies within a margin
-// of its threshold that FP32 rounding could cross; the caller then repeats it in FP64.
+// The per-sample record from the target point p^a, target normal n^a and weight w_c:
+//   g' = sqrt(w_c) R_g^T n^a,  r0' = sqrt(w_c) n^a . (R_g p^ + t_g - p^a)  (r0' in FP64)
 template <typename T>
-__device__ bool associate_finish(const Ctx &c, const float4 p4, V3<T> du, V3<T> dn, int &pix, float &w_out,
-                                 float4 &rec);
-
-// FP32 or FP64 trilinear weights of sample i in its cell
-template <typename T>
-__device__ __forceinline__ void sample_frac(const Ctx &c, int i, int cl, const float4 p4, T f[3]) {
-    if (sizeof(T) == 4) {
-        const float4 f4 = c.frac[i];
-        f[0] = f4.x;
-        f[1] = f4.y;
-        f[2] = f4.z;
-    } else {
-        const int cx_ = cl % c.nx, t = cl / c.nx, cy_ = t % c.ny, cz_ = t / c.ny;
-        f[0] = T(((double)p4.x - (double)c.ox) / (double)c.h - cx_);
-        f[1] = T(((double)p4.y - (double)c.oy) / (double)c.h - cy_);
-        f[2] = T(((double)p4.z - (double)c.oz) / (double)c.h - cz_);
-    }
-}
-
-template <typename T, bool kAll>
-__device__ bool associate_sample(const Ctx &c, int i, int &pix, float &w_out, float4 &rec) {
-    const int cl = c.cell[i];
-    const float4 p4 = c.sp[i], n4 = c.sn[i];
-    T f[3];
-    sample_frac<T>(c, i, cl, p4, f);
-    V3<T> du{0, 0, 0}, dn{0, 0, 0};
-    const V3<T> nh{T(n4.x), T(n4.y), T(n4.z)};
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-        const int node = corner_node(c, cl, k);
-        const T al = trilinear_weight(f, k);
-        du.x += al * T(c.u[node]);
-        du.y += al * T(c.u[c.ld + node]);
-        du.z += al * T(c.u[2 * c.ld + node]);
-        float Rk[9];
-#pragma unroll
-        for (int e = 0; e < 9; e++) Rk[e] = c.R[e * c.ld + node];
-        const V3<T> rn = rot<T>(Rk, nh);
-        dn.x += al * rn.x;
-        dn.y += al * rn.y;
-        dn.z += al * rn.z;
-    }
-    return associate_finish<T>(c, p4, du, dn, pix, w_out, rec);
-}
-
-// The association of one sample from its corner sums du = sum alpha_k u_k and
-// dn = sum alpha_k R_k n^ (Sec. 5.1): warped point and model normal, nearest pixel,
-// target point and normal, Phi_d, Phi_n, Phi_v, w_c and the record.  FP32 (returns
-// whether a decision lies near a threshold) or FP64.
-template <typename T>
-__device__ bool associate_finish(const Ctx &c, const float4 p4, V3<T> du, V3<T> dn, int &pix, float &w_out,
-                                 float4 &rec) {
-    constexpr bool kF32 = sizeof(T) == 4;
-    pix = -1;
-    w_out = 0.f;
-    rec = make_float4(0.f, 0.f, 0.f, 0.f);
-    const V3<T> q{T(p4.x) + du.x, T(p4.y) + du.y, T(p4.z) + du.z};
-    V3<T> p = rot<T>(c.Rg, q);
-    p.x += T(c.tg[0]);
-    p.y += T(c.tg[1]);
-    p.z += T(c.tg[2]);
-    V3<T> n = rot<T>(c.Rg, dn);
-    const T nl = sqrt(dot(n, n));
-    bool near = false;
-    if (!(nl > T(0))) return false;
-    n = {n.x / nl, n.y / nl, n.z / nl};
-    if (kF32 && fabs((double)p.z) < 1e-4) near = true;
-    if (!(p.z > T(0))) return near;
-    const T uf = T(c.fx) * p.x / p.z + T(c.cx) + T(0.5);
-    const T vf = T(c.fy) * p.y / p.z + T(c.cy) + T(0.5);
-    const T pxf = floor(uf), pyf = floor(vf);
-    if (kF32) {
-        const float mu = (float)uf - (float)pxf, mv = (float)vf - (float)pyf;
-        if (mu < 2e-3f || mu > 1.f - 2e-3f || mv < 2e-3f || mv > 1.f - 2e-3f) near = true;
-    }
-    if (!(pxf >= T(0) && pxf < T(c.W) && pyf >= T(0) && pyf < T(c.H))) return near;
-    const int px = (int)pxf, py = (int)pyf;
-    const size_t k = (size_t)py * c.W + px;
-    const float D = c.depth[k];
-    if (!(D > 0.f)) return near;
-    V3<T> na;
-    if (kF32) {
-        const float4 m = load_nrm(c, k);
-        if (m.w == 0.f) return near;
-        na = {T(m.x), T(m.y), T(m.z)};
-    } else {
-        V3<double> m;
-        if (!target_normal_f64(c, px, py, m)) return false;
-        na = {T(m.x), T(m.y), T(m.z)};
-    }
-    const V3<T> pa{T(D) * ((T(px) - T(c.cx)) / T(c.fx)), T(D) * ((T(py) - T(c.cy)) / T(c.fy)), T(D)};
-    const V3<T> dd{p.x - pa.x, p.y - pa.y, p.z - pa.z};
-    const T dist = sqrt(dot(dd, dd));
-    const T cn = dot(n, na);
-    const T pl = sqrt(dot(p, p));
-    const T cv = -dot(n, p) / pl;
-    if (kF32) {
-        if (fabsf((float)dist - c.eps_d) < 1e-5f) near = true;
-        // BF16 target normals carry up to ~4e-3 of rounding in n_c . n^a
-        if (fabsf((1.f - (float)cn) - c.eps_n) < (c.mixed ? 1e-2f : 1e-4f)) near = true;
-        if (fabsf((1.f - (float)cv) - c.eps_v) < 1e-4f) near = true;
-    }
-    pix = (int)k;
-    const T phi_d = T(1) - dist / T(c.eps_d);
-    const T phi_n = T(1) - (T(1) - cn) / T(c.eps_n);
-    const T phi_v = T(1) - (T(1) - cv) / T(c.eps_v);
-    if (phi_d < T(0) || phi_n < T(0) || phi_v < T(0)) return near;
-    const T m = (phi_d + phi_n + phi_v) / T(3);
-    const T w = m * m;
-    const T sw = sqrt(w);
-    // g' = sqrt(w_c) R_g^T n^a ; r0' = sqrt(w_c) n^a . (R_g p^ + t_g - p^a)  (FP64)
+__device__ __forceinline__ float4 sample_record(const Ctx &c, const float4 p4, const V3<T> &na, const V3<T> &pa,
+                                                T sw) {
     const V3<T> gt = rotT<T>(c.Rg, na);
     const V3<double> nad{(double)na.x, (double)na.y, (double)na.z};
     V3<double> q0 = rot<double>(c.Rg, V3<double>{(double)p4.x, (double)p4.y, (double)p4.z});
@@ -674,9 +564,156 @@ __device__ bool associate_finish(const Ctx &c, const float4 p4, V3<T> du, V3<T> 
     q0.y += (double)c.tg[1] - (double)pa.y;
     q0.z += (double)c.tg[2] - (double)pa.z;
     const double r0 = (double)sw * dot(nad, q0);
-    w_out = (float)w;
-    rec = make_float4((float)(sw * gt.x), (float)(sw * gt.y), (float)(sw * gt.z), (float)r0);
+    return make_float4((float)(sw * gt.x), (float)(sw * gt.y), (float)(sw * gt.z), (float)r0);
+}
+
+// The association of one sample from its corner sums du = sum alpha_k u_k and
+// dn = sum alpha_k R_k n^ (Sec. 5.1): warped point and model normal, nearest pixel,
+// target point and normal, Phi_d, Phi_n, Phi_v, w_c and the record.  In FP32, with
+// the target normal from the precomputed map; returns true when a decision (pixel,
+// range, any Phi < 0) lies within a margin of its threshold that FP32 rounding could
+// cross, and the sample is then associated again by associate_finish_f64.
+__device__ bool associate_finish_f32(const Ctx &c, const float4 p4, V3<float> du, V3<float> dn, int &pix,
+                                     float &w_out, float4 &rec) {
+    pix = -1;
+    w_out = 0.f;
+    rec = make_float4(0.f, 0.f, 0.f, 0.f);
+    const V3<float> q{p4.x + du.x, p4.y + du.y, p4.z + du.z};
+    V3<float> p = rot<float>(c.Rg, q);
+    p.x += c.tg[0];
+    p.y += c.tg[1];
+    p.z += c.tg[2];
+    V3<float> n = rot<float>(c.Rg, dn);
+    const float nl = sqrtf(dot(n, n));
+    bool near = false;
+    if (!(nl > 0.f)) return false;
+    n = {n.x / nl, n.y / nl, n.z / nl};
+    if (fabs((double)p.z) < 1e-4) near = true;
+    if (!(p.z > 0.f)) return near;
+    const float uf = c.fx * p.x / p.z + c.cx + 0.5f;
+    const float vf = c.fy * p.y / p.z + c.cy + 0.5f;
+    const float pxf = floorf(uf), pyf = floorf(vf);
+    const float mu = uf - pxf, mv = vf - pyf;
+    if (mu < 2e-3f || mu > 1.f - 2e-3f || mv < 2e-3f || mv > 1.f - 2e-3f) near = true;
+    if (!(pxf >= 0.f && pxf < (float)c.W && pyf >= 0.f && pyf < (float)c.H)) return near;
+    const int px = (int)pxf, py = (int)pyf;
+    const size_t k = (size_t)py * c.W + px;
+    const float D = c.depth[k];
+    if (!(D > 0.f)) return near;
+    const float4 m4 = load_nrm(c, k);
+    if (m4.w == 0.f) return near;
+    const V3<float> na{m4.x, m4.y, m4.z};
+    const V3<float> pa{D * ((px - c.cx) / c.fx), D * ((py - c.cy) / c.fy), D};
+    const V3<float> dd{p.x - pa.x, p.y - pa.y, p.z - pa.z};
+    const float dist = sqrtf(dot(dd, dd));
+    const float cn = dot(n, na);
+    const float pl = sqrtf(dot(p, p));
+    const float cv = -dot(n, p) / pl;
+    if (fabsf(dist - c.eps_d) < 1e-5f) near = true;
+    // BF16 target normals carry up to ~4e-3 of rounding in n_c . n^a
+    if (fabsf((1.f - cn) - c.eps_n) < (c.mixed ? 1e-2f : 1e-4f)) near = true;
+    if (fabsf((1.f - cv) - c.eps_v) < 1e-4f) near = true;
+    pix = (int)k;
+    const float phi_d = 1.f - dist / c.eps_d;
+    const float phi_n = 1.f - (1.f - cn) / c.eps_n;
+    const float phi_v = 1.f - (1.f - cv) / c.eps_v;
+    if (phi_d < 0.f || phi_n < 0.f || phi_v < 0.f) return near;
+    const float m = (phi_d + phi_n + phi_v) / 3.f;
+    const float w = m * m;
+    w_out = w;
+    rec = sample_record<float>(c, p4, na, pa, sqrtf(w));
     return near;
+}
+
+// The same association in FP64, with the target normal from the depth map in FP64.
+// Quotients with a common divisor share one reciprocal (one rounding more than a
+// division: the decisions move only for values within a few units in the last place
+// of a threshold, where FP64 rounding decides anyway).
+__device__ void associate_finish_f64(const Ctx &c, const float4 p4, V3<double> du, V3<double> dn, int &pix,
+                                     float &w_out, float4 &rec) {
+    pix = -1;
+    w_out = 0.f;
+    rec = make_float4(0.f, 0.f, 0.f, 0.f);
+    const V3<double> q{p4.x + du.x, p4.y + du.y, p4.z + du.z};
+    V3<double> p = rot<double>(c.Rg, q);
+    p.x += (double)c.tg[0];
+    p.y += (double)c.tg[1];
+    p.z += (double)c.tg[2];
+    V3<double> n = rot<double>(c.Rg, dn);
+    const double nl2 = dot(n, n);
+    if (!(nl2 > 0.0)) return;
+    const double inl = 1.0 / sqrt(nl2);
+    n = {n.x * inl, n.y * inl, n.z * inl};
+    if (!(p.z > 0.0)) return;
+    const double iz = 1.0 / p.z;
+    const double uf = (double)c.fx * p.x * iz + (double)c.cx + 0.5;
+    const double vf = (double)c.fy * p.y * iz + (double)c.cy + 0.5;
+    const double pxf = floor(uf), pyf = floor(vf);
+    if (!(pxf >= 0.0 && pxf < (double)c.W && pyf >= 0.0 && pyf < (double)c.H)) return;
+    const int px = (int)pxf, py = (int)pyf;
+    const size_t k = (size_t)py * c.W + px;
+    const float D = c.depth[k];
+    if (!(D > 0.f)) return;
+    const double rfx = 1.0 / (double)c.fx, rfy = 1.0 / (double)c.fy;
+    V3<double> na;
+    if (!target_normal_f64(c, px, py, rfx, rfy, na)) return;
+    const double Dd = D;
+    const V3<double> pa{Dd * ((px - (double)c.cx) * rfx), Dd * ((py - (double)c.cy) * rfy), Dd};
+    const V3<double> dd{p.x - pa.x, p.y - pa.y, p.z - pa.z};
+    const double dist = sqrt(dot(dd, dd));
+    const double cn = dot(n, na);
+    const double cv = -dot(n, p) / sqrt(dot(p, p));
+    pix = (int)k;
+    const double phi_d = 1.0 - dist / (double)c.eps_d;
+    const double phi_n = 1.0 - (1.0 - cn) / (double)c.eps_n;
+    const double phi_v = 1.0 - (1.0 - cv) / (double)c.eps_v;
+    if (phi_d < 0.0 || phi_n < 0.0 || phi_v < 0.0) return;
+    const double m = (phi_d + phi_n + phi_v) / 3.0;
+    const double w = m * m;
+    w_out = (float)w;
+    rec = sample_record<double>(c, p4, na, pa, sqrt(w));
+}
+
+// FP32 trilinear weights of sample i in its cell (precomputed per frame)
+__device__ __forceinline__ void sample_frac_f32(const Ctx &c, int i, float f[3]) {
+    const float4 f4 = c.frac[i];
+    f[0] = f4.x;
+    f[1] = f4.y;
+    f[2] = f4.z;
+}
+
+// FP64 trilinear weights of sample i in its cell cl, from its position
+__device__ __forceinline__ void sample_frac_f64(const Ctx &c, int cl, const float4 p4, double f[3]) {
+    const int cx_ = cl % c.nx, t = cl / c.nx, cy_ = t % c.ny, cz_ = t / c.ny;
+    f[0] = ((double)p4.x - (double)c.ox) / (double)c.h - cx_;
+    f[1] = ((double)p4.y - (double)c.oy) / (double)c.h - cy_;
+    f[2] = ((double)p4.z - (double)c.oz) / (double)c.h - cz_;
+}
+
+// Association of sorted sample i at the current warp in FP32 (see associate_finish_f32)
+__device__ bool associate_sample_f32(const Ctx &c, int i, int &pix, float &w_out, float4 &rec) {
+    const int cl = c.cell[i];
+    const float4 p4 = c.sp[i], n4 = c.sn[i];
+    float f[3];
+    sample_frac_f32(c, i, f);
+    V3<float> du{0.f, 0.f, 0.f}, dn{0.f, 0.f, 0.f};
+    const V3<float> nh{n4.x, n4.y, n4.z};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int node = corner_node(c, cl, k);
+        const float al = trilinear_weight(f, k);
+        du.x += al * c.u[node];
+        du.y += al * c.u[c.ld + node];
+        du.z += al * c.u[2 * c.ld + node];
+        float Rk[9];
+#pragma unroll
+        for (int e = 0; e < 9; e++) Rk[e] = c.R[e * c.ld + node];
+        const V3<float> rn = rot<float>(Rk, nh);
+        dn.x += al * rn.x;
+        dn.y += al * rn.y;
+        dn.z += al * rn.z;
+    }
+    return associate_finish_f32(c, p4, du, dn, pix, w_out, rec);
 }
 
 template <bool kAll>
@@ -690,7 +727,7 @@ __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
         int pix;
         float w;
         float4 rec;
-        const bool near = associate_sample<float, kAll>(c, i, pix, w, rec);
+        const bool near = associate_sample_f32(c, i, pix, w, rec);
         if (near) {  // re-taken in FP64 by k_associate_refine (and counted there)
             c.refine[atomicAdd(&sc->n_refine, 1)] = i;
             refined++;
@@ -730,7 +767,7 @@ __device__ __forceinline__ void associate_refine_block(const Ctx &c, Scal *sc, i
             const float4 n4 = c.sn[i];
             p4 = c.sp[i];
             double f[3];
-            sample_frac<double>(c, i, cl, p4, f);
+            sample_frac_f64(c, cl, p4, f);
             const int node = corner_node(c, cl, k);
             const double al = trilinear_weight(f, k);
             du = {al * (double)c.u[node], al * (double)c.u[c.ld + node], al * (double)c.u[2 * c.ld + node]};
@@ -754,7 +791,7 @@ __device__ __forceinline__ void associate_refine_block(const Ctx &c, Scal *sc, i
             int pix;
             float w;
             float4 rec;
-            associate_finish<double>(c, p4, du, dn, pix, w, rec);
+            associate_finish_f64(c, p4, du, dn, pix, w, rec);
             c.pix[i] = pix;
             c.wc[i] = w;
             store_rec(c, i, rec);
@@ -821,6 +858,66 @@ __device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, flo
     // neighbouring range: each range adds its own samples' contributions)
     const int sb = max(c.occ_beg[cb], js), se = min(c.occ_beg[ce], je);
     const int items = kOp == kOpEnergy ? 1 : (ce - cb) * 8;
+    if (kOp != kOpEnergy && se - sb <= nt) {
+        // all the samples in one chunk: phase 1 once, then every round of (cell, corner)
+        // items reads the same factors
+        const int j = sb + lt;
+        if (j < se) {
+            const int cl = c.cell[j];
+            const float4 f4 = c.frac[j], g = load_rec(c, j);
+            const float f[3] = {f4.x, f4.y, f4.z};
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 8; kk++) {
+                const int nd = corner_node(c, cl, kk);
+                const int vi = (kOp == kOpApply) ? node_slot<kAll>(c, nd) : nd;
+                const float al = trilinear_weight(f, kk);
+                sx += al * ldvv<kFresh>(vec, vi);
+                sy += al * ldvv<kFresh>(vec, c.ld + vi);
+                sz += al * ldvv<kFresh>(vec, 2 * (size_t)c.ld + vi);
+            }
+            const float sv = g.x * sx + g.y * sy + g.z * sz;
+            if (kOp == kOpApply) {
+                const float t = c.w_d * sv;
+                part += t * sv;
+                tsm[lt] = t;
+            } else {
+                tsm[lt] = -c.w_d * (sv + g.w);
+            }
+        }
+        sub_sync(bar_id, nt);
+        for (int item = lt; item < items; item += nt) {
+            const int ci = cb + (item >> 3), k = item & 7;
+            const int ibeg = max(c.occ_beg[ci], js), iend = min(c.occ_beg[ci + 1], je);
+            float ax = 0.f, ay = 0.f, az = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
+            for (int jj = ibeg; jj < iend; jj++) {
+                const float4 f4 = c.frac[jj], g = load_rec(c, jj);
+                const float f[3] = {f4.x, f4.y, f4.z};
+                const float al = trilinear_weight(f, k);
+                const float t = al * tsm[jj - sb];
+                ax += g.x * t;
+                ay += g.y * t;
+                az += g.z * t;
+                if (kOp == kOpRhs) {
+                    const float a2 = al * al * c.w_d;
+                    dx += a2 * g.x * g.x;
+                    dy += a2 * g.y * g.y;
+                    dz += a2 * g.z * g.z;
+                }
+            }
+            const int sl = node_slot<kAll>(c, corner_node(c, c.occ_cell[ci], k));
+            if (ax != 0.f) atomicAdd(&dst[sl], ax);
+            if (ay != 0.f) atomicAdd(&dst[c.ld + sl], ay);
+            if (az != 0.f) atomicAdd(&dst[2 * c.ld + sl], az);
+            if (kOp == kOpRhs) {
+                if (dx != 0.f) atomicAdd(&dst2[sl], dx);
+                if (dy != 0.f) atomicAdd(&dst2[c.ld + sl], dy);
+                if (dz != 0.f) atomicAdd(&dst2[2 * c.ld + sl], dz);
+            }
+        }
+        sub_sync(bar_id, nt);  // tsm is free again
+        return;
+    }
     for (int i0 = 0; i0 < items; i0 += nt) {
         const int item = i0 + lt;
         const bool has = kOp != kOpEnergy && item < items;
