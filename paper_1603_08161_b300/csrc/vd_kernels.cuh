@@ -1478,6 +1478,13 @@ __device__ __forceinline__ double block_total(float v, double *red) {
 
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
+// x += v for four consecutive floats (16-byte aligned) as one vector reduction in L2
+__device__ __forceinline__ void red_add_f4(float *x, float4 v) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(x), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
 template <bool kAll, bool kVec4>
 __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *sc, PcgAux ax, int K, double tol2,
                                                                    int apply) {
@@ -1761,28 +1768,33 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             const int gl = tid + kk * kPcgThreads;
             if (gl >= ng) continue;
             const int l = 4 * gl, s = gslot(l);
+            // every global load of the group first (one round trip): the flags, the
+            // samples' contributions (used only where flagged) and Minv
             const int4 fl = __ldcg(reinterpret_cast<const int4 *>(ax.flag + s));
+            float4 qg[3], mv[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                qg[a] = __ldcg(reinterpret_cast<const float4 *>(c.q + a * ld + s));
+                mv[a] = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
+            }
             const bool touched = fl.x | fl.y | fl.z | fl.w;
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
                 float4 qv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
                 if (touched) {  // fold in (and clear) the samples' contributions
-                    float4 *qg = reinterpret_cast<float4 *>(c.q + a * ld + s);
-                    qv = f4add(qv, __ldcg(qg));
-                    *qg = make_float4(0.f, 0.f, 0.f, 0.f);
+                    qv = f4add(qv, qg[a]);
+                    *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 const float4 rv = *reinterpret_cast<const float4 *>(Rr + a * chunk + l);
-                const float4 mv = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
-                // x lives in global memory (L2-resident): the 64 registers of a thread of
-                // a 1024-thread CTA cannot hold it as well without spilling
-                float4 *xg = reinterpret_cast<float4 *>(c.x + a * ld + s);
-                const float4 xo = __ldcg(xg);
-                *xg = make_float4(fmaf(alpha, pv.x, xo.x), fmaf(alpha, pv.y, xo.y), fmaf(alpha, pv.z, xo.z),
-                                  fmaf(alpha, pv.w, xo.w));
+                // x lives in global memory (L2-resident; the 64 registers of a thread of a
+                // 1024-thread CTA cannot hold it as well without spilling) and is updated
+                // by a reduction, which needs no load; this thread is its only writer
+                red_add_f4(c.x + a * ld + s, make_float4(alpha * pv.x, alpha * pv.y, alpha * pv.z, alpha * pv.w));
+                const float4 &mvv = mv[a];
                 const float4 rn = make_float4(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y),
                                               fmaf(-alpha, qv.z, rv.z), fmaf(-alpha, qv.w, rv.w));
-                const float4 zn = make_float4(mv.x * rn.x, mv.y * rn.y, mv.z * rn.z, mv.w * rn.w);
+                const float4 zn = make_float4(mvv.x * rn.x, mvv.y * rn.y, mvv.z * rn.z, mvv.w * rn.w);
                 *reinterpret_cast<float4 *>(Rr + a * chunk + l) = rn;
                 *reinterpret_cast<float4 *>(Q + a * chunk + l) = zn;
                 *reinterpret_cast<float4 *>(Zg + a * ld + s) = zn;
