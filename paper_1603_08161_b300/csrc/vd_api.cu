@@ -408,7 +408,9 @@ void enqueue_pcg(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K, do
     }
 }
 
-constexpr int kPcgMaxChunk = 6272;  // 9 floats per slot in shared memory: 225,792 bytes (+ 4 KB static)
+// 9 floats per slot in shared memory (at most 225,792 bytes + 4 KB static), and at most
+// kPcgMaxGroups float4 groups per thread
+constexpr int kPcgMaxChunk = std::min(6272, 4 * kPcgMaxGroups * kPcgThreads);
 
 // Bricks of by x bz full x-rows for the persistent position step of an all-nodes
 // lattice (nx % 4 == 0): the fewest slots per CTA within the SM count, and among those

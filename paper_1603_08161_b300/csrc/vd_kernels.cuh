@@ -1391,9 +1391,12 @@ __global__ void __launch_bounds__(kThreads) k_add_increment(Ctx c, const Scal *s
 // deterministic: every CTA writes its FP64 partial to a per-iteration row and every CTA
 // sums the row in CTA order.  A barrier that waits longer than about a second sets the
 // error flag and the whole grid returns.
-constexpr int kPcgThreads = 1024;
-constexpr int kPcgMaxGroups = 2;  // float4 groups per thread: chunk <= 4 * 2 * 1024
-constexpr int kPcgStencil = kPcgThreads / 2;              // threads on the stencil in phase A
+// 768 threads leave 80 registers to a thread (1024 would leave 64, and spill); the
+// stencil gets 512 of them, the samples 256 (a CTA's share of the samples of a 96^3
+// frame, about 250, fits one chunk of the sample pass)
+constexpr int kPcgThreads = 768;
+constexpr int kPcgMaxGroups = 2;  // float4 groups per thread: chunk <= 4 * 2 * 768
+constexpr int kPcgStencil = 512;                          // threads on the stencil in phase A
 constexpr int kPcgSample = kPcgThreads - kPcgStencil;      // threads on the samples in phase A
 constexpr long long kBarrierCycles = 2000000000LL;
 
@@ -1787,8 +1790,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                     *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 const float4 rv = *reinterpret_cast<const float4 *>(Rr + a * chunk + l);
-                // x lives in global memory (L2-resident; the 64 registers of a thread of a
-                // 1024-thread CTA cannot hold it as well without spilling) and is updated
+                // x lives in global memory (L2-resident; the 80 registers of a thread of a
+                // 768-thread CTA cannot hold it as well without spilling) and is updated
                 // by a reduction, which needs no load; this thread is its only writer
                 red_add_f4(c.x + a * ld + s, make_float4(alpha * pv.x, alpha * pv.y, alpha * pv.z, alpha * pv.w));
                 const float4 &mvv = mv[a];
