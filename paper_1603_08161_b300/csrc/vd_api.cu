@@ -472,8 +472,9 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     int by = 0, bz = 0;
     brick_plan(L, &by, &bz);
     if (by && by * bz * L->c.nx != chunk) by = bz = 0;  // the plan the caller sized G for
+    auto magic = [](int d) { return d > 0 ? (unsigned)(((1ull << 31) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u; };
     PcgAux ax{L->pcg_part, L->pcg_bar, (int *)(L->pcg_bar + 2), L->surf_flag,
-              {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk, by, bz};
+              {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk, by, bz, magic(L->c.nx), magic(by)};
     const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
     cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
     Lc.other();

@@ -1409,7 +1409,12 @@ struct PcgAux {
     int chunk;         // slots per CTA
     int by, bz;        // > 0: each CTA owns a brick of by x bz full x-rows (all-nodes
                        // lattice, ny % by == nz % bz == 0); 0: a contiguous slot range
+    // n / nx and n / by as (2n m) >> 32 with m = ceil(2^31 / d), exact for n d < 2^31
+    // (the local slot and row indices of a brick): no integer division in the loops
+    unsigned m_nx, m_by;
 };
+
+__device__ __forceinline__ int fast_div(int n, unsigned m) { return (int)__umulhi(2u * (unsigned)n, m); }
 
 constexpr int kPcgMaxRows = 128;  // x-rows of one brick (bounds the plan's search)
 
@@ -1526,8 +1531,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     const int ng = brick ? chunk >> 2 : (s_end > s_beg ? (s_end - s_beg) >> 2 : 0);
     auto gslot = [&](int l) -> int {
         if (!brick) return s_beg + l;
-        const int r = l / nx;
-        return (l - r * nx) + nx * (y0 + r % ax.by) + plane * (z0 + r / ax.by);
+        const int r = fast_div(l, ax.m_nx), rz = fast_div(r, ax.m_by);
+        return (l - r * nx) + nx * (y0 + (r - rz * ax.by)) + plane * (z0 + rz);
     };
     const int tid = threadIdx.x;
     const float w2 = 2.f * c.w_r;
@@ -1636,7 +1641,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                     int loff[4];
                     const int offs[4] = {-nx, nx, -plane, plane};
                     if (brick) {
-                        const int r = l / nx, yl = r % ax.by, zl = r / ax.by;
+                        const int r = fast_div(l, ax.m_nx), zl = fast_div(r, ax.m_by), yl = r - zl * ax.by;
                         x0 = l - r * nx;
                         y = y0 + yl;
                         z = z0 + zl;
