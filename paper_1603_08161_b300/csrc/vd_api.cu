@@ -102,7 +102,7 @@ struct vd_lattice {
     int *surf_flag = nullptr;        // per slot: touched by a sample or a sparse pair
     double *pcg_part = nullptr;
     int pcg_part_rows = 0;
-    unsigned *pcg_bar = nullptr;     // [0] barrier arrival word, [2] error flag
+    unsigned *pcg_bar = nullptr;     // [2] error flag of the persistent position step
     int num_sms = 148;
     bool coop = false;               // device supports cooperative launches
     bool use_persistent = true;      // may be cleared if the graph cannot hold the launch
@@ -249,7 +249,8 @@ vd_status ensure_scal(vd_lattice *L, int G, int K) {
     if (2 * K + 2 > L->pcg_part_rows) {
         dfree(L, L->pcg_part);
         L->pcg_part_rows = 2 * K + 2;
-        TRY(dalloc(L, &L->pcg_part, (size_t)L->pcg_part_rows * L->num_sms));
+        // the rows of partials, then one barrier word per row
+        TRY(dalloc(L, &L->pcg_part, (size_t)L->pcg_part_rows * (L->num_sms + 1)));
     }
     const size_t stride = scal_bytes(K);
     if (L->scal && stride == L->scal_stride && G <= L->scal_slots) return VD_OK;
@@ -449,6 +450,7 @@ bool persistent_plan(vd_lattice *L, int *G, int *chunk, int *by = nullptr, int *
     if (y) {
         *chunk = y * z * L->c.nx;
         *G = (L->c.ny / y) * (L->c.nz / z);
+        if (*G > kPcgMaxCtas) return false;
         if (by) {
             *by = y;
             *bz = z;
@@ -464,7 +466,7 @@ bool persistent_plan(vd_lattice *L, int *G, int *chunk, int *by = nullptr, int *
     if (ch > kPcgMaxChunk) return false;
     *chunk = ch;
     *G = (N4 + ch - 1) / ch;
-    return *G <= L->num_sms;
+    return *G <= std::min(L->num_sms, kPcgMaxCtas);
 }
 
 template <bool kAll>
@@ -473,10 +475,12 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     brick_plan(L, &by, &bz);
     if (by && by * bz * L->c.nx != chunk) by = bz = 0;  // the plan the caller sized G for
     auto magic = [](int d) { return d > 0 ? (unsigned)(((1ull << 31) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u; };
-    PcgAux ax{L->pcg_part, L->pcg_bar, (int *)(L->pcg_bar + 2), L->surf_flag,
+    unsigned long long *words = reinterpret_cast<unsigned long long *>(L->pcg_part + (size_t)L->pcg_part_rows * L->num_sms);
+    PcgAux ax{L->pcg_part, words, (int *)(L->pcg_bar + 2), L->surf_flag,
               {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk, by, bz, magic(L->c.nx), magic(by)};
     const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
     cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
+    cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(2 * K + 1), Lc.st);
     Lc.other();
     if (prof) cudaEventRecordWithFlags(L->ev[L->ev_used], Lc.st, cudaEventRecordExternal);
     cudaLaunchConfig_t cfg = {};

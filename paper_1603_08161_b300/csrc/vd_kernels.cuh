@@ -1402,7 +1402,7 @@ constexpr long long kBarrierCycles = 2000000000LL;
 
 struct PcgAux {
     double *part;      // rows 0..K: r.z partials, rows K+1..2K: p.Ap partials, G entries each
-    unsigned *bar;     // [0] the grid barrier's arrival word (top bit flips per barrier)
+    unsigned long long *words;  // one word per grid barrier (2K + 1), zeroed before the launch
     int *err;          // set when a barrier wait gives up
     const int *flag;   // per slot: 1 if a sample or a sparse pair touches it (0 past N)
     float *pbuf[2];    // p of even / odd iterations, published for the other CTAs
@@ -1417,30 +1417,47 @@ struct PcgAux {
 __device__ __forceinline__ int fast_div(int n, unsigned m) { return (int)__umulhi(2u * (unsigned)n, m); }
 
 constexpr int kPcgMaxRows = 128;  // x-rows of one brick (bounds the plan's search)
+constexpr int kPcgMaxCtas = 255;  // the arrival count of a barrier word has 8 bits
 
 
-// Grid barrier that also reduces.  bar[0] is one arrival word: thread 0 of each CTA
-// publishes the CTA's writes (fence) and adds 1 to it (CTA 0 adds 2^31 - (G - 1)), so
-// the G additions of one barrier flip its top bit exactly once, with the last arrival;
-// each CTA polls the word (acquire) until the top bit differs from the value it saw on
-// arriving, for at most kBarrierCycles.  Then every CTA sums `row` (one FP64 partial per
-// CTA, written before the call) itself, in CTA order: all CTAs get the same `sum`, and it
-// does not depend on the order of arrival.
-__device__ __forceinline__ bool grid_reduce(unsigned *bar, int *err, unsigned G, const double *row, double &sum) {
-    __shared__ int s_ok;
+// Grid barrier that also reduces.  Each barrier of a launch has its own 64-bit word
+// (zeroed before the launch).  Thread 0 of each CTA writes the CTA's FP64 partial to
+// `row`, fences (publishing the CTA's writes) and adds to the word 1 (bits 0-7 count the
+// arrivals) plus, when a reference magnitude ref > 0 is given (the previous value of the
+// same sum: the same in every CTA), the partial in fixed point, round(part 2^(32 - e))
+// with ref = m 2^e, in bits 16-63 -- or 256 (bits 8-15) if it is not below 2^39.  Then it
+// polls the word (acquire) until the count is G, for at most kBarrierCycles.  Integer
+// addition is associative, so the final word does not depend on the order of arrival.
+// When no partial overflowed and the fixed-point sum is at least 2^28 (ref / 16; the
+// rounding of at most 160 partials, 80 units, is then below 3e-7 of it, the precision of
+// the FP32 partials themselves) that sum is the result, read with the barrier word;
+// otherwise every CTA sums `row` itself in CTA order.  Either way all CTAs get the same
+// `sum`.
+__device__ __forceinline__ bool grid_reduce(int *err, unsigned G, double *row, unsigned long long *word, double part,
+                                            double ref, double &sum) {
+    __shared__ int s_ok, s_fast;
     __shared__ double s_sum;
     __syncthreads();
     if (threadIdx.x == 0) {
+        row[blockIdx.x] = part;
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (G - 1u) : 1u;
-        unsigned old;
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(inc) : "memory");
+        unsigned long long inc = 1;
+        int e = 0;
+        const bool fixed = ref > 0.0 && isfinite(ref);
+        if (fixed) {
+            e = ilogb(ref);
+            const double f = ldexp(part, 32 - e);
+            if (fabs(f) < 0x1p39) inc += (unsigned long long)llrint(f) << 16;
+            else inc += 256ull;
+        }
+        unsigned long long old;
+        asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(word), "l"(inc) : "memory");
         int good = 1;
+        unsigned long long w = old + inc;
         const long long t0 = clock64();
-        while (true) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-            if ((v ^ old) & 0x80000000u) break;
+        while ((w & 0xFFull) != G) {
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(word) : "memory");
+            if ((w & 0xFFull) == G) break;
             if (*(volatile int *)err) {
                 good = 0;
                 break;
@@ -1451,24 +1468,30 @@ __device__ __forceinline__ bool grid_reduce(unsigned *bar, int *err, unsigned G,
                 break;
             }
         }
+        const long long fx = (long long)w >> 16;
+        const int fast = good && fixed && ((w >> 8) & 0xFFull) == 0 && (fx >= (1ll << 28) || fx <= -(1ll << 28));
+        if (fast) s_sum = ldexp((double)fx, e - 32);
+        s_fast = fast;
         s_ok = good && !*(volatile int *)err;
     }
     __syncthreads();
-    if (row && threadIdx.x < 32) {
-        double v[5];
+    if (!s_fast) {  // the same decision in every CTA
+        if (threadIdx.x < 32) {
+            double v[5];
 #pragma unroll
-        for (int k = 0; k < 5; k++) {  // all loads in flight before the first add
-            const unsigned b = threadIdx.x + 32u * k;
-            v[k] = b < G ? __ldcg(row + b) : 0.0;
+            for (int k = 0; k < 5; k++) {  // all loads in flight before the first add
+                const unsigned b = threadIdx.x + 32u * k;
+                v[k] = b < G ? __ldcg(row + b) : 0.0;
+            }
+            double t = (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
+            for (unsigned b = threadIdx.x + 160u; b < G; b += 32) t += __ldcg(row + b);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+            if (threadIdx.x == 0) s_sum = t;
         }
-        double t = (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
-        for (unsigned b = threadIdx.x + 160u; b < G; b += 32) t += __ldcg(row + b);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-        if (threadIdx.x == 0) s_sum = t;
+        __syncthreads();
     }
-    __syncthreads();
-    if (row) sum = s_sum;
+    sum = s_sum;
     return s_ok != 0;
 }
 
@@ -1595,14 +1618,10 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         }
     }
     __syncthreads();
-    {
-        const double bt = block_total(part, red);
-        if (tid == 0) ax.part[blockIdx.x] = bt;
-    }
     double sum = 0.0;
-    bool ok = grid_reduce(ax.bar, ax.err, G, ax.part, sum);
+    bool ok = grid_reduce(ax.err, G, ax.part, ax.words, block_total(part, red), 0.0, sum);
     const double rho0 = ok ? sum : 0.0;
-    double rho = rho0;
+    double rho = rho0, pq_prev = 0.0;
     float beta = 0.f;
     if (blockIdx.x == 0 && tid == 0) scal_rho(sc)[0] = rho0;
     int done = 0;
@@ -1749,16 +1768,14 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             double pd = 0.0;
             sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * lt, G * kPcgSample, part, pd);
         }
-        {
-            const double bt = block_total(part, red);
-            if (tid == 0) ax.part[(size_t)(K + 1 + it) * G + blockIdx.x] = bt;
-        }
-        ok = grid_reduce(ax.bar, ax.err, G, ax.part + (size_t)(K + 1 + it) * G, sum);
+        ok = grid_reduce(ax.err, G, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it, block_total(part, red),
+                         pq_prev, sum);
         if (!ok) {
             stop = 1;
             break;
         }
         const double pq = sum;
+        pq_prev = pq;
         if (!(pq > 0.0)) {
             stop = 1;
             break;
@@ -1809,12 +1826,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                 part += rn.x * zn.x + rn.y * zn.y + rn.z * zn.z + rn.w * zn.w;
             }
         }
-        {
-            const double bt = block_total(part, red);
-            if (tid == 0) ax.part[(size_t)(it + 1) * G + blockIdx.x] = bt;
-        }
         done = it + 1;
-        ok = grid_reduce(ax.bar, ax.err, G, ax.part + (size_t)(it + 1) * G, sum);
+        ok = grid_reduce(ax.err, G, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it, block_total(part, red), rho,
+                         sum);
         if (!ok) {
             stop = 1;
             break;
