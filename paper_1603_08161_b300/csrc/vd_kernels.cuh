@@ -1531,6 +1531,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
     __shared__ int s_cb, s_ce, s_js, s_je;
+    // per own float4 group: 1 if another CTA reads its p and z (a brick-face row, a slot
+    // that a sample or a sparse pair touches, or any slot of a contiguous range)
+    __shared__ unsigned s_pub[kPcgMaxGroups * kPcgThreads / 32];
     __shared__ float tsm[kPcgSample];
     __shared__ float s_ab;
     float *sm = reinterpret_cast<float *>(sm4);
@@ -1583,11 +1586,18 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     }
     // ---- init: Minv = 1/diag, r = b, z = Minv r, p_old = 0, x = 0; rho0 = r.z
     float part = 0.f;
+    bool pub[kPcgMaxGroups];
 #pragma unroll
     for (int kk = 0; kk < kPcgMaxGroups; kk++) {
         const int gl = tid + kk * kPcgThreads;
+        pub[kk] = false;
         if (gl >= ng) continue;
         const int l = 4 * gl, s = gslot(l);
+        pub[kk] = true;
+        if (brick) {
+            const int r = fast_div(l, ax.m_nx), zl = fast_div(r, ax.m_by), yl = r - zl * ax.by;
+            pub[kk] = yl == 0 || yl == ax.by - 1 || zl == 0 || zl == ax.bz - 1;
+        }
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             *reinterpret_cast<float4 *>(c.x + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1615,8 +1625,15 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         if (fl.x | fl.y | fl.z | fl.w) {  // the samples' contributions arrive here by atomics
 #pragma unroll
             for (int a = 0; a < 3; a++) *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
+            pub[kk] = true;
         }
     }
+#pragma unroll
+    for (int kk = 0; kk < kPcgMaxGroups; kk++) {
+        const unsigned m = __ballot_sync(FULL, pub[kk]);
+        if ((tid & 31) == 0) s_pub[(tid + kk * kPcgThreads) >> 5] = m;
+    }
+    auto published = [&](int gl) -> bool { return (s_pub[gl >> 5] >> (gl & 31)) & 1u; };
     __syncthreads();
     double sum = 0.0;
     bool ok = grid_reduce(ax.err, G, ax.part, ax.words, block_total(part, red), 0.0, sum);
@@ -1639,6 +1656,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
 #pragma unroll 1
             for (int gl = tid; gl < ng; gl += kPcgStencil) {
                 const int l = 4 * gl, s = gslot(l);
+                const bool pg = published(gl);
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
                     const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
@@ -1646,7 +1664,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                     const float4 pn = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y),
                                                   fmaf(beta, pv.z, zv.z), fmaf(beta, pv.w, zv.w));
                     *reinterpret_cast<float4 *>(P + a * chunk + l) = pn;
-                    *reinterpret_cast<float4 *>(pnew + a * ld + s) = pn;
+                    if (pg) *reinterpret_cast<float4 *>(pnew + a * ld + s) = pn;
                 }
             }
             sub_sync(2, kPcgStencil);
@@ -1803,6 +1821,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                 mv[a] = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
             }
             const bool touched = fl.x | fl.y | fl.z | fl.w;
+            const bool pg = published(gl);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
@@ -1822,7 +1841,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                 const float4 zn = make_float4(mvv.x * rn.x, mvv.y * rn.y, mvv.z * rn.z, mvv.w * rn.w);
                 *reinterpret_cast<float4 *>(Rr + a * chunk + l) = rn;
                 *reinterpret_cast<float4 *>(Q + a * chunk + l) = zn;
-                *reinterpret_cast<float4 *>(Zg + a * ld + s) = zn;
+                if (pg) *reinterpret_cast<float4 *>(Zg + a * ld + s) = zn;
                 part += rn.x * zn.x + rn.y * zn.y + rn.z * zn.z + rn.w * zn.w;
             }
         }
