@@ -1534,6 +1534,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     // per own float4 group: 1 if another CTA reads its p and z (a brick-face row, a slot
     // that a sample or a sparse pair touches, or any slot of a contiguous range)
     __shared__ unsigned s_pub[kPcgMaxGroups * kPcgThreads / 32];
+    // per own float4 group: 1 if a sample or a sparse pair touches one of its slots (its
+    // J^T J p contributions arrive in c.q)
+    __shared__ unsigned s_touch[kPcgMaxGroups * kPcgThreads / 32];
     __shared__ float tsm[kPcgSample];
     __shared__ float s_ab;
     float *sm = reinterpret_cast<float *>(sm4);
@@ -1586,11 +1589,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     }
     // ---- init: Minv = 1/diag, r = b, z = Minv r, p_old = 0, x = 0; rho0 = r.z
     float part = 0.f;
-    bool pub[kPcgMaxGroups];
+    bool pub[kPcgMaxGroups], touch[kPcgMaxGroups];
 #pragma unroll
     for (int kk = 0; kk < kPcgMaxGroups; kk++) {
         const int gl = tid + kk * kPcgThreads;
-        pub[kk] = false;
+        pub[kk] = touch[kk] = false;
         if (gl >= ng) continue;
         const int l = 4 * gl, s = gslot(l);
         pub[kk] = true;
@@ -1625,15 +1628,19 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         if (fl.x | fl.y | fl.z | fl.w) {  // the samples' contributions arrive here by atomics
 #pragma unroll
             for (int a = 0; a < 3; a++) *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
-            pub[kk] = true;
+            pub[kk] = touch[kk] = true;
         }
     }
 #pragma unroll
     for (int kk = 0; kk < kPcgMaxGroups; kk++) {
-        const unsigned m = __ballot_sync(FULL, pub[kk]);
-        if ((tid & 31) == 0) s_pub[(tid + kk * kPcgThreads) >> 5] = m;
+        const unsigned m = __ballot_sync(FULL, pub[kk]), t = __ballot_sync(FULL, touch[kk]);
+        if ((tid & 31) == 0) {
+            s_pub[(tid + kk * kPcgThreads) >> 5] = m;
+            s_touch[(tid + kk * kPcgThreads) >> 5] = t;
+        }
     }
     auto published = [&](int gl) -> bool { return (s_pub[gl >> 5] >> (gl & 31)) & 1u; };
+    auto touched_group = [&](int gl) -> bool { return (s_touch[gl >> 5] >> (gl & 31)) & 1u; };
     __syncthreads();
     double sum = 0.0;
     bool ok = grid_reduce(ax.err, G, ax.part, ax.words, block_total(part, red), 0.0, sum);
@@ -1811,17 +1818,15 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             const int gl = tid + kk * kPcgThreads;
             if (gl >= ng) continue;
             const int l = 4 * gl, s = gslot(l);
-            // every global load of the group first (one round trip): the flags, the
-            // samples' contributions (used only where flagged) and Minv
-            const int4 fl = __ldcg(reinterpret_cast<const int4 *>(ax.flag + s));
+            // every global load of the group first (one round trip): Minv, and the
+            // samples' contributions where they arrive
+            const bool touched = touched_group(gl), pg = published(gl);
             float4 qg[3], mv[3];
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                qg[a] = __ldcg(reinterpret_cast<const float4 *>(c.q + a * ld + s));
+                qg[a] = touched ? __ldcg(reinterpret_cast<const float4 *>(c.q + a * ld + s)) : make_float4(0.f, 0.f, 0.f, 0.f);
                 mv[a] = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
             }
-            const bool touched = fl.x | fl.y | fl.z | fl.w;
-            const bool pg = published(gl);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
