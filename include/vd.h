@@ -278,6 +278,17 @@ vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spacing, const 
  * a new graph capture (setting or removing the target re-captures once). */
 vd_status vd_set_energy_target(vd_lattice *lat, double e_target);
 
+/* ---- failure injection (tests; the paper has no counterpart) ----
+ *
+ * With on != 0, every later persistent position step of this lattice waits at its first
+ * grid barrier for one more arrival than it has CTAs.  No CTA can supply it, so the
+ * bounded wait runs out (about 2e9 SM cycles, one second at 2 GHz), the kernel sets its
+ * error word and returns, and the solve reports VD_ERR_TIMEOUT with the warp of the
+ * last completed iteration (each Gauss-Newton iteration's step waits once).  The CUDA
+ * context stays usable; on = 0 restores normal solves.  Solves that stream the position
+ * step (no cooperative launch) are unaffected.  Returns VD_ERR_INVALID_ARG for NULL. */
+vd_status vd_test_stall_barrier(vd_lattice *lat, int on);
+
 /* ---- learned warm start (the paper has no counterpart: Sec. 7.1 starts each frame from
  * the previous frame's warp) ----
  *

@@ -88,6 +88,7 @@ struct vd_lattice {
     Ctx gctx{};
     int gkey_caps[5] = {0, 0, 0, 0, 0};
     long gen = 0, ggen = -1;         // buffer generation (pointers changed)
+    int stall_extra = 0;             // vd_test_stall_barrier: arrivals awaited beyond the grid
     int launches_solve = 0, launches_frame = 0;
     int counting = 0;
     bool solve_pending = false;
@@ -476,7 +477,7 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     if (by && by * bz * L->c.nx != chunk) by = bz = 0;  // the plan the caller sized G for
     auto magic = [](int d) { return d > 0 ? (unsigned)(((1ull << 31) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u; };
     unsigned long long *words = reinterpret_cast<unsigned long long *>(L->pcg_part + (size_t)L->pcg_part_rows * L->num_sms);
-    PcgAux ax{L->pcg_part, words, (int *)(L->pcg_bar + 2), L->surf_flag,
+    PcgAux ax{L->pcg_part, words, L->stall_extra, (int *)(L->pcg_bar + 2), L->surf_flag,
               {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk, by, bz, magic(L->c.nx), magic(by)};
     const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
     cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
@@ -1626,6 +1627,13 @@ void warm_select_enqueue(vd_lattice *L, const float *pred) {
 }  // namespace
 
 extern "C" {
+
+vd_status vd_test_stall_barrier(vd_lattice *L, int on) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    L->stall_extra = on ? 1 : 0;
+    L->ggen = -1;  // the flag is a launch argument of the captured graph: re-capture
+    return VD_OK;
+}
 
 vd_status vd_set_energy_target(vd_lattice *L, double e_target) {
     if (!L) return VD_ERR_INVALID_ARG;

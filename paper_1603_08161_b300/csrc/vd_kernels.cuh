@@ -1403,6 +1403,8 @@ constexpr long long kBarrierCycles = 2000000000LL;
 struct PcgAux {
     double *part;      // rows 0..K: r.z partials, rows K+1..2K: p.Ap partials, G entries each
     unsigned long long *words;  // one word per grid barrier (2K + 1), zeroed before the launch
+    int extra;         // arrivals awaited beyond G: 0, or 1 to make the first wait run out
+                       // (failure injection for tests, vd_test_stall_barrier)
     int *err;          // set when a barrier wait gives up
     const int *flag;   // per slot: 1 if a sample or a sparse pair touches it (0 past N)
     float *pbuf[2];    // p of even / odd iterations, published for the other CTAs
@@ -1433,8 +1435,8 @@ constexpr int kPcgMaxCtas = 255;  // the arrival count of a barrier word has 8 b
 // the FP32 partials themselves) that sum is the result, read with the barrier word;
 // otherwise every CTA sums `row` itself in CTA order.  Either way all CTAs get the same
 // `sum`.
-__device__ __forceinline__ bool grid_reduce(int *err, unsigned G, double *row, unsigned long long *word, double part,
-                                            double ref, double &sum) {
+__device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arrivals, double *row, unsigned long long *word,
+                                            double part, double ref, double &sum) {
     __shared__ int s_ok, s_fast;
     __shared__ double s_sum;
     __syncthreads();
@@ -1455,9 +1457,9 @@ __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, double *row, u
         int good = 1;
         unsigned long long w = old + inc;
         const long long t0 = clock64();
-        while ((w & 0xFFull) != G) {
+        while ((w & 0xFFull) != arrivals) {
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(word) : "memory");
-            if ((w & 0xFFull) == G) break;
+            if ((w & 0xFFull) == arrivals) break;
             if (*(volatile int *)err) {
                 good = 0;
                 break;
@@ -1643,7 +1645,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     auto touched_group = [&](int gl) -> bool { return (s_touch[gl >> 5] >> (gl & 31)) & 1u; };
     __syncthreads();
     double sum = 0.0;
-    bool ok = grid_reduce(ax.err, G, ax.part, ax.words, block_total(part, red), 0.0, sum);
+    const unsigned arrivals = G + ax.extra;
+    bool ok = grid_reduce(ax.err, G, arrivals, ax.part, ax.words, block_total(part, red), 0.0, sum);
     const double rho0 = ok ? sum : 0.0;
     double rho = rho0, pq_prev = 0.0;
     float beta = 0.f;
@@ -1793,7 +1796,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             double pd = 0.0;
             sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * lt, G * kPcgSample, part, pd);
         }
-        ok = grid_reduce(ax.err, G, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it, block_total(part, red),
+        ok = grid_reduce(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it, block_total(part, red),
                          pq_prev, sum);
         if (!ok) {
             stop = 1;
@@ -1851,7 +1854,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             }
         }
         done = it + 1;
-        ok = grid_reduce(ax.err, G, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it, block_total(part, red), rho,
+        ok = grid_reduce(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it, block_total(part, red), rho,
                          sum);
         if (!ok) {
             stop = 1;

@@ -105,6 +105,7 @@ _SIGS = {
     "vd_batch_last_error": [_P],
     "vd_solve_batch": [_P, _I, ctypes.POINTER(vd_solve_params), _P],
     "vd_set_energy_target": [_P, ctypes.c_double],
+    "vd_test_stall_barrier": [_P, _I],
     "vd_unet_create": [_I, _I, _I, ctypes.c_ulonglong, ctypes.POINTER(_P)],
     "vd_unet_destroy": [_P],
     "vd_unet_dims": [_P, _PI, _PI, _PI],
@@ -265,6 +266,10 @@ class Lattice:
         pu, _ = _ptr(uu)
         pr, _ = _ptr(RR)
         self._check(vd_set_warp(self.h, pu, pr, VD_MEM_DEVICE if dev else VD_MEM_HOST))
+
+    def test_stall_barrier(self, on):
+        """Failure injection: make the position step's first grid-barrier wait run out."""
+        self._check(vd_test_stall_barrier(self.h, 1 if on else 0))
 
     def set_energy_target(self, e_target):
         """Stop later solves after the first iteration with E_total <= e_target (< 0: off)."""
