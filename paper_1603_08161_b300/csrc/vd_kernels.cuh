@@ -1989,10 +1989,12 @@ __device__ __forceinline__ void mat_to_quat(const float R[9], float q[4]) {
 // (Horn 1987, closed-form absolute orientation).  Nodes whose neighbours span fewer
 // than two axes, or whose top eigenvalue is (numerically) double, keep R_i.
 // Warm start: with the previous rotation R0 (orthonormal), argmax_R tr(R^T A) =
-// R0 argmax_D tr(D^T R0^T A), and Horn's matrix of R0^T A is nearly diagonal when the
-// rotation changed little, so the Jacobi sweeps converge at once; R = R0 D is formed
-// from the product of unit quaternions, which keeps it orthonormal.
-// Also accumulates E_reg (Eq. 4) with the new rotations (kFit = false: E_reg only).
+// R0 argmax_D tr(D^T R0^T A), and the top eigenvector of Horn's matrix of R0^T A is near
+// the identity quaternion when the rotation changed little, so a Rayleigh-quotient
+// iteration from the identity converges in one or two steps (cyclic Jacobi is the
+// fallback); R = R0 D is formed from the product of unit quaternions, which keeps it
+// orthonormal.  k_fit_rotations (below the eigen-solvers) also accumulates E_reg
+// (Eq. 4) with the new rotations (kFit = false: E_reg only).
 // Top eigenvector of a symmetric 4x4 matrix by Rayleigh-quotient iteration from q
 // (cubic convergence near an eigenvector), with a certificate: true only if
 // M = (mu - delta) I - N + 2 delta q q^T is positive definite (Cholesky), which holds
