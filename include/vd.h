@@ -94,13 +94,17 @@ vd_status vd_destroy_lattice(vd_lattice *lat);
  * says -- and the n_src source samples p^_c with normals n^_c in
  * canonical coordinates (the samples of the rasterised model).  Computes the target
  * normal map, bins the samples by lattice cell and builds the active set M.
- * Samples whose cell is not inside the lattice get w_c = 0.  Synchronous. */
+ * Samples whose cell is not inside the lattice, or whose position or normal is not
+ * finite, get w_c = 0; a depth that is not a positive finite number (0, negative, NaN,
+ * infinite) marks an invalid pixel.  Synchronous. */
 vd_status vd_set_frame(vd_lattice *lat, const float *depth, int W, int H, const float K[4],
                        const float pose[12], const float *src_pts, const float *src_nrm, int n_src,
                        int mem);
 
 /* The S sparse feature pairs of Eq. 3: canonical positions f^_s and observed
- * positions f_s (S x 3 each).  Pairs outside the lattice are ignored.  Applies to the
+ * positions f_s (S x 3 each).  Pairs outside the lattice (or with a non-finite
+ * canonical position) are ignored; an observed position that is not finite makes the
+ * energy non-finite, and the next solve returns VD_ERR_NUMERIC.  Applies to the
  * next vd_set_frame / vd_solve; S = 0 clears them.  Synchronous. */
 vd_status vd_set_correspondences(vd_lattice *lat, const float *canon, const float *target, int S,
                                  int mem);
@@ -227,6 +231,14 @@ vd_status vd_batch_get_reports(vd_batch *batch, vd_solve_report *out);
  * solve (ms). */
 vd_status vd_batch_tune(vd_batch *batch, const vd_solve_params *params, int *streams, float *ms);
 
+/* Set the batch's schedule directly instead of by vd_batch_tune: `streams` concurrent
+ * branches (1..64), branch order (largest_first != 0: by active nodes, descending;
+ * else as given), and the size from which lattices run ahead, one after another, with
+ * their persistent position step (active nodes >= run_ahead_nodes; a value above any
+ * lattice's size, e.g. 2^31 - 1, disables it; 0 makes every lattice run ahead).
+ * VD_ERR_INVALID_ARG for NULL or out-of-range values. */
+vd_status vd_batch_set_plan(vd_batch *batch, int streams, int largest_first, long long run_ahead_nodes);
+
 /* Kernel launches in one batched solve (after the first solve or tune). */
 vd_status vd_batch_launch_count(const vd_batch *batch, int *launches);
 
@@ -262,8 +274,11 @@ vd_status vd_solve_batch(vd_lattice *const *lattices, int count, const vd_solve_
  * (NULL = the legacy default stream) and the function returns without waiting.  The
  * first call on a device looks up the scratch address on that device (with it
  * current); make that first call before any stream capture.  Errors: VD_ERR_INVALID_ARG
- * for bad sizes or NULL arrays, VD_ERR_CUDA if a CUDA call fails (there is no handle,
- * so no vd_last_error message). */
+ * for bad sizes (any dimension, or their product, above VD_NOALLOC_MAX_NODES) or NULL
+ * arrays; VD_ERR_CUDA if a CUDA call fails (there is no handle, so no vd_last_error
+ * message), and also, before anything is enqueued, when a CUDA error from earlier work
+ * of the calling thread is still pending: that error is left in place for the caller
+ * to read with cudaGetLastError. */
 #define VD_NOALLOC_MAX_NODES 65536
 vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spacing, const float *disp,
                                    const float *rot_in, float *rot_out, double *e_reg,

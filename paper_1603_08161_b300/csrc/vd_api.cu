@@ -853,13 +853,14 @@ vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const fl
     TRY(upload(L, L->depth, depth, sizeof(float) * (size_t)W * H, mem));
     TRY(upload(L, L->pts_in, src_pts, sizeof(float) * 3 * (size_t)n_src, mem));
     TRY(upload(L, L->nrm_in, src_nrm, sizeof(float) * 3 * (size_t)n_src, mem));
+    k_sanitize_depth<<<blocks_for((long)W * H), kThreads, 0, st>>>(L->depth, W * H);
     dim3 b2(32, 8), g2((W + 31) / 32, (H + 7) / 8);
     k_target_normals<<<g2, b2, 0, st>>>(L->depth, L->nrm, W, H, c.fx, c.fy, c.cx, c.cy, c.mixed);
     // bin the samples by cell (counting sort with a deterministic order inside a cell)
     CK(cudaMemsetAsync(L->cnt, 0, sizeof(int) * (size_t)c.nn, st));
     CK(cudaMemsetAsync(L->head, 0, sizeof(int) * (size_t)L->cap_src, st));
     const int nb = blocks_for(std::max(n_src, 1));
-    k_point_cells<<<nb, kThreads, 0, st>>>(L->pts_in, n_src, c, L->cell_in, L->frac_in);
+    k_point_cells<<<nb, kThreads, 0, st>>>(L->pts_in, n_src, c, L->cell_in, L->frac_in, L->nrm_in);
     k_histogram<<<nb, kThreads, 0, st>>>(L->cell_in, n_src, L->cnt);
     scan_launch(L->cnt, c.nn, L->start, L->start + c.nn, L->scan_sums, st);
     k_bin_scatter<<<nb, kThreads, 0, st>>>(L->cell_in, n_src, L->start, L->cnt, L->tmp);
@@ -877,7 +878,7 @@ vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const fl
     k_cell_partition<<<(nbc + kThreads - 1) / kThreads, kThreads, 0, st>>>(L->occ_beg, L->counts + 1, nbc,
                                                                           L->cell_part);
     CKL();
-    L->launches_frame = 13 + 2 + (L->all ? 0 : 7);
+    L->launches_frame = 14 + 2 + (L->all ? 0 : 7);
     return VD_OK;
 }
 
@@ -1471,6 +1472,14 @@ vd_status vd_batch_tune(vd_batch *B, const vd_solve_params *P, int *streams_out,
     return VD_OK;
 }
 
+vd_status vd_batch_set_plan(vd_batch *B, int streams, int largest_first, long long run_ahead_nodes) {
+    if (!B || streams < 1 || streams > 64 || run_ahead_nodes < 0) return VD_ERR_INVALID_ARG;
+    B->streams = streams;
+    B->largest_first = largest_first != 0;
+    B->coop_min = run_ahead_nodes > 0x7fffffffLL ? 0x7fffffffL : (long)run_ahead_nodes;
+    return VD_OK;
+}
+
 vd_status vd_batch_launch_count(const vd_batch *B, int *launches) {
     if (!B || !launches) return VD_ERR_INVALID_ARG;
     *launches = B->launches;
@@ -1537,8 +1546,13 @@ extern "C" vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spac
                                               const float *rot_in, float *rot_out, double *e_reg,
                                               int *n_degenerate, void *cuda_stream) {
     if (nx < 2 || ny < 2 || nz < 2 || !(spacing > 0.f) || !disp || !rot_in || !rot_out) return VD_ERR_INVALID_ARG;
-    const long nn = (long)nx * ny * nz;
+    // each factor is bounded before the product is formed, so the product cannot overflow
+    if (nx > VD_NOALLOC_MAX_NODES || ny > VD_NOALLOC_MAX_NODES || nz > VD_NOALLOC_MAX_NODES) return VD_ERR_INVALID_ARG;
+    const long long nn = (long long)nx * ny * nz;
     if (nn > VD_NOALLOC_MAX_NODES) return VD_ERR_INVALID_ARG;
+    // an error left pending by the caller's earlier work is not ours to consume: refuse
+    // before enqueueing anything and leave it for the caller to read
+    if (cudaPeekAtLastError() != cudaSuccess) return VD_ERR_CUDA;
     void *base = nullptr;
     if (noalloc_scratch(&base) != cudaSuccess) {
         cudaGetLastError();
@@ -1557,10 +1571,14 @@ extern "C" vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spac
     Scal *sc = (Scal *)((char *)base + kNoAllocStateBytes);
     // the sums and counters accumulate with atomics: clear what the last call left
     if (cudaMemsetAsync(sc, 0, scal_bytes(1), st) != cudaSuccess) return VD_ERR_CUDA;
+    // no error was pending on entry, so each check below sees only this call's launch
     const int nb = blocks_for(nn);
     k_aos_to_soa<<<nb, kThreads, 0, st>>>(disp, 3, c.nn, c.ld, c.u);
+    if (cudaGetLastError() != cudaSuccess) return VD_ERR_CUDA;
     k_aos_to_soa<<<nb, kThreads, 0, st>>>(rot_in, 9, c.nn, c.ld, c.R);
+    if (cudaGetLastError() != cudaSuccess) return VD_ERR_CUDA;
     k_fit_rotations<true, true><<<nb, kThreads, 0, st>>>(c, sc);
+    if (cudaGetLastError() != cudaSuccess) return VD_ERR_CUDA;
     k_soa_to_aos<<<nb, kThreads, 0, st>>>(c.R, 9, c.nn, c.ld, rot_out);
     if (cudaGetLastError() != cudaSuccess) return VD_ERR_CUDA;
     if (e_reg && cudaMemcpyAsync(e_reg, &sc->e_reg, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)

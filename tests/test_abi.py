@@ -77,6 +77,13 @@ def test_invalid_arguments_rejected_on_host(vd):
     assert vd.vd_set_frame(None, None, 0, 0, None, None, None, None, 0, 0) == vd.VD_ERR_INVALID_ARG
     assert vd.vd_get_warp(None, None, None, 0) == vd.VD_ERR_INVALID_ARG
     assert vd.vd_last_error(None) == b"null lattice"
+    # the allocation-free rotation step bounds every dimension before forming the
+    # product: 2^22 nodes per axis wraps a 64-bit product to 4, and must still be refused
+    one = ctypes.c_void_p(16)
+    big = 1 << 22
+    for dims in [(big, big, big), (vd.VD_NOALLOC_MAX_NODES + 1, 2, 2), (41, 40, 40), (1, 4, 4)]:
+        assert vd.vd_fit_rotations_noalloc(*dims, ctypes.c_float(0.01), one, one, one, None, None,
+                                           None) == vd.VD_ERR_INVALID_ARG
 
 
 def test_oracle_builds_and_is_independent():
