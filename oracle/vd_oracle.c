@@ -35,6 +35,8 @@
  *   - PCG: x0 = 0 on the increment, scalar Jacobi preconditioner (1/diag, 0 where the
  *     diagonal is 0), exactly K iterations unless p.Ap <= 0, rho = 0 or
  *     rho' <= tol^2 rho0;
+ *   - a depth that is not a positive finite number marks an invalid pixel; a sample
+ *     with a non-finite position or normal, or outside the lattice, is ignored;
  *   - a rotation is kept unchanged (and counted) when its neighbours span fewer than
  *     two lattice axes, when sigma_2 <= 1e-12 sigma_1, or when det < 0 and
  *     sigma_2 - sigma_3 <= 1e-12 sigma_1 (the best rotation is then not unique).
@@ -291,7 +293,11 @@ int vdo_set_frame(vdo_ctx *c, const float *depth, int W, int H, const float K[4]
     for (int a = 0; a < 3; a++) c->tg[a] = pose ? (double)pose[9 + a] : 0.0;
     size_t np = (size_t)W * H;
     c->depth = (double *)xcalloc(np, sizeof(double));
-    for (size_t k = 0; k < np; k++) c->depth[k] = (double)depth[k];
+    /* a depth that is not a positive finite number marks an invalid pixel, as 0 does */
+    for (size_t k = 0; k < np; k++) {
+        double d = (double)depth[k];
+        c->depth[k] = (isfinite(d) && d > 0.0) ? d : 0.0;
+    }
 
     /* target vertex map V and normal map (central differences, facing the camera) */
     c->V = (double *)xcalloc(np * 3, sizeof(double));
@@ -341,6 +347,10 @@ int vdo_set_frame(vdo_ctx *c, const float *depth, int W, int H, const float K[4]
             c->sn[3 * s + a] = src_n[3 * s + a];
         }
         c->cell_c[s] = locate(c, c->sp + 3 * s, c->frac_c + 3 * s);
+        /* a sample whose normal is not finite is ignored, like one outside the lattice
+           (a non-finite position already fails locate) */
+        if (!isfinite(c->sn[3 * s]) || !isfinite(c->sn[3 * s + 1]) || !isfinite(c->sn[3 * s + 2]))
+            c->cell_c[s] = -1;
     }
     if (!c->fh) c->S = 0;
     build_active(c);

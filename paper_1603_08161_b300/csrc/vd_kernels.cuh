@@ -284,11 +284,21 @@ __global__ void k_target_normals(const float *__restrict__ D, float4 *__restrict
     else nrm[(size_t)v * W + u] = out;
 }
 
+// A depth that is not a positive finite number marks an invalid pixel, as 0 does: such
+// entries are set to 0 before any kernel reads the map.
+__global__ void k_sanitize_depth(float *__restrict__ D, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float d = D[i];
+        if (!(d > 0.f) || !isfinite(d)) D[i] = 0.f;
+    }
+}
+
 // Cell of each point (lower-corner node, or -1 when the cell is not inside the
 // lattice) and its trilinear fractions.  The floor decision is taken in FP64 on
-// (p - origin) / h, so it does not depend on FP32 rounding.
+// (p - origin) / h, so it does not depend on FP32 rounding.  With normals given, a
+// point whose normal is not finite gets -1 too (it is ignored, like one outside).
 __global__ void k_point_cells(const float *__restrict__ pts, int n, Ctx c, int *__restrict__ cell,
-                              float4 *__restrict__ frac) {
+                              float4 *__restrict__ frac, const float *__restrict__ nrm = nullptr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double o[3] = {(double)c.ox, (double)c.oy, (double)c.oz};
         const int dims[3] = {c.nx, c.ny, c.nz};
@@ -303,6 +313,7 @@ __global__ void k_point_cells(const float *__restrict__ pts, int n, Ctx c, int *
             ci[a] = ok ? (int)fl : 0;
             f[a] = q - fl;
         }
+        if (nrm && !(isfinite(nrm[3 * i]) && isfinite(nrm[3 * i + 1]) && isfinite(nrm[3 * i + 2]))) ok = false;
         cell[i] = ok ? ci[0] + c.nx * (ci[1] + c.ny * ci[2]) : -1;
         frac[i] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.f);
     }

@@ -549,3 +549,89 @@ def test_rotation_degenerate_nodes_keep_previous():
     assert o.fit_rotations() == 0
     _, R = o.get_warp()
     np.testing.assert_allclose(R, np.tile(np.eye(3), (o.nn, 1, 1)), atol=1e-12)
+
+
+def test_flip_flop_order_positions_before_rotations():
+    """Sec. 7.1 fixes the order inside an iteration: positions with the rotations fixed,
+    then rotations with the positions fixed.  From u = 0 and every R_i = Q != I, with one
+    sparse pair whose target is its own canonical point f^ (w_d = 0), the exact position
+    step with R = Q minimises w_s |S(f^) - f^|^2 + w_r E_reg(R = Q), which is zero only for
+    the rigid rotation of the lattice about f^: u_i = (Q - I)(t^_i - f^); the rotation step
+    then keeps R_i = Q.  Rotations first would refit R = I at u = 0 and leave u = 0."""
+    rng = np.random.default_rng(11)
+    fr = _no_dense(synth.plane_frame(n=4))
+    f_hat = fr.origin.astype(np.float64) + np.array([1.3, 1.7, 0.6]) * fr.spacing
+    fr = _with_sparse(fr, f_hat, f_hat)
+    f32 = fr.sp_canon.astype(np.float64)[0]
+    Q = _rand_rot(rng, 0.4)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL, params=dict(w_dense=0.0))
+    o.set_warp(None, np.tile(Q, (o.nn, 1, 1)))
+    res = o.solve(1, 0, cholesky=True)
+    u, R = o.get_warp()
+    u_closed = (_node_pos(fr) - f32) @ (Q - np.eye(3)).T
+    assert np.abs(u - u_closed).max() < 1e-12
+    assert np.abs(R - Q).max() < 1e-12
+    assert res["energy"][-1, 0] < 1e-24
+
+
+def test_solve_is_the_stages_in_the_papers_order():
+    """vdo_solve with re-association equals driving the stages one by one in the order
+    of Sec. 7.1 (associate, position step by PCG, add the increment, rotation step),
+    which the per-iteration association checks of the GPU tests rely on."""
+    fr = synth.config1()
+    a = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    res = a.solve(3, 10, fixed_association=False)
+    b = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    for g in range(3):
+        b.associate()
+        x, it, _ = b.pcg(10)
+        b.add_increment(x)
+        b.fit_rotations()
+        assert np.array_equal(b.energy(), res["energy"][g])
+    ua, Ra = a.get_warp()
+    ub, Rb = b.get_warp()
+    assert np.array_equal(ua, ub) and np.array_equal(Ra, Rb)
+
+
+def test_non_finite_inputs_are_invalid():
+    """A depth that is not a positive finite number is an invalid pixel (like 0), and a
+    sample with a non-finite position or normal is ignored (like one outside the
+    lattice): the frame then gives exactly the association and energy of the frame with
+    those pixels set to 0 and those samples removed."""
+    fr = synth.config1()
+    rng = np.random.default_rng(5)
+    on = np.argwhere(fr.depth > 0)
+    pick = on[rng.choice(len(on), 12, replace=False)]
+    depth = fr.depth.copy()
+    depth[pick[:6, 0], pick[:6, 1]] = np.nan
+    depth[pick[6:9, 0], pick[6:9, 1]] = np.inf
+    depth[pick[9:, 0], pick[9:, 1]] = -np.inf
+    bad = [5, 17, 23, 31, 40]
+    pts, nrm = fr.src_pts.copy(), fr.src_nrm.copy()
+    pts[5] = np.nan
+    pts[17, 1] = np.inf
+    nrm[23] = np.nan
+    nrm[31, 2] = -np.inf
+    nrm[40, 0] = np.inf
+    noisy = dataclasses.replace(fr, depth=depth, src_pts=pts, src_nrm=nrm)
+    keep = np.setdiff1d(np.arange(fr.C), bad)
+    clean = dataclasses.replace(fr, depth=np.where(np.isfinite(depth) & (depth > 0), depth, 0).astype(np.float32),
+                                src_pts=fr.src_pts[keep], src_nrm=fr.src_nrm[keep])
+    a = oracle.Oracle.from_frame(noisy, oracle.ACTIVE_SURFACE)
+    b = oracle.Oracle.from_frame(clean, oracle.ACTIVE_SURFACE)
+    assert np.array_equal(a.active_mask(), b.active_mask())
+    _, Na, va = a.target_maps()
+    _, Nb, vb = b.target_maps()
+    assert np.array_equal(va, vb) and np.array_equal(Na, Nb)
+    ra = a.solve(2, 10, fixed_association=False)
+    rb = b.solve(2, 10, fixed_association=False)
+    pa, wa, _ = a.association()
+    pb, wb, _ = b.association()
+    assert (pa[bad] == -1).all() and (wa[bad] == 0).all()
+    assert np.array_equal(pa[keep], pb) and np.array_equal(wa[keep], wb)
+    assert np.array_equal(ra["energy"], rb["energy"]) and np.isfinite(ra["energy"]).all()
+    # an observed feature position that is not finite makes the energy non-finite
+    ft = fr.sp_target.copy()
+    ft[2, 0] = np.nan
+    c = oracle.Oracle.from_frame(dataclasses.replace(fr, sp_target=ft), oracle.ACTIVE_ALL)
+    assert not np.isfinite(c.solve(1, 5)["energy"][-1, 0])
