@@ -95,6 +95,7 @@ _SIGS = {
     "vd_profile_read": [_P, _PD, _PI],
     "vd_launch_counts": [_P, ctypes.POINTER(vd_solve_params), _PI, _PI],
     "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
+    "vd_batch_set_plan": [_P, _I, _I, ctypes.c_longlong],
     "vd_batch_create": [_P, _I, ctypes.POINTER(_P)],
     "vd_batch_destroy": [_P],
     "vd_batch_solve": [_P, ctypes.POINTER(vd_solve_params), _P],
@@ -418,6 +419,9 @@ class Batch:
         n = ctypes.c_int()
         self._check(vd_batch_launch_count(self.h, ctypes.byref(n)))
         return n.value
+
+    def set_plan(self, streams, largest_first=True, run_ahead_nodes=(1 << 31) - 1):
+        self._check(vd_batch_set_plan(self.h, int(streams), int(bool(largest_first)), int(run_ahead_nodes)))
 
 
 class UNet:

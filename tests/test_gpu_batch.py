@@ -83,3 +83,30 @@ def test_batch_needs_frames(vd):
     with pytest.raises(vd.VDError) as e:
         batch.solve(vd.params())
     assert e.value.status == vd.VD_ERR_STATE
+
+
+@pytest.mark.slow
+def test_batch_run_ahead_persistent_branch(vd):
+    """A 64^3 all-nodes lattice in a batch with small ones, under a plan that makes
+    lattices of at least 2^17 active nodes run ahead with their persistent (cooperative)
+    position step while the others' streamed schedules follow as branches; every lattice
+    of the batch matches the oracle within the parity tolerances."""
+    items = [("all", synth.capsule_frame(W=320, H=240, f=262.5, n=64, seed=9, n_sparse=120)),
+             ("all", synth.capsule_frame(W=160, H=120, f=131.25, n=24, seed=5, n_sparse=40)),
+             ("surface", synth.config1())]
+    prm = vd.params(gn_iters=3, cg_iters=10, fixed_association=True, init=vd.VD_INIT_ZERO)
+    lats = [_lattice(vd, m, fr) for m, fr in items]
+    batch = vd.Batch(lats)
+    batch.set_plan(2, True, 1 << 17)
+    reps = batch.solve(prm)
+    assert 64 ** 3 >= (1 << 17) > 24 ** 3
+    for (mode, fr), lat, rep in zip(items, lats, reps):
+        u, _ = lat.get_warp()
+        ref = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL if mode == "all" else oracle.ACTIVE_SURFACE)
+        res = ref.solve(3, 10, fixed_association=True)
+        u0, _ = ref.get_warp()
+        err = float(np.abs(u - u0).max())
+        rel = abs(rep["e_total"] - res["energy"][-1, 0]) / res["energy"][-1, 0]
+        print(f"batch run-ahead {fr.dims}: |du|max = {err / fr.spacing:.2e} h, dE/E = {rel:.2e}")
+        assert err <= 1e-4 * fr.spacing
+        assert rel <= 1e-5

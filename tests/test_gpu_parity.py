@@ -271,6 +271,54 @@ def test_solve_parity_config2_all(vd, cfg2):
     assert rel <= 1e-5
 
 
+_CFG2_FREE = {}
+
+
+def _cfg2_oracle_free(cfg2, gn=10, cg=20):
+    """The oracle's 10 x 20 solve of the 96^3 frame with re-association at every
+    iteration, stage by stage in the order of Sec. 7.1 (the same as vdo_solve, pinned by
+    test_solve_is_the_stages_in_the_papers_order), keeping each iteration's target
+    pixels (cached)."""
+    if not _CFG2_FREE:
+        ref = oracle.Oracle.from_frame(cfg2, oracle.ACTIVE_ALL)
+        pix = []
+        for g in range(gn):
+            ref.associate()
+            pix.append(ref.association()[0])
+            x, _, _ = ref.pcg(cg)
+            ref.add_increment(x)
+            ref.fit_rotations()
+        u0, _ = ref.get_warp()
+        _CFG2_FREE.update(pix=pix, e=ref.energy(), u0=u0)
+    return _CFG2_FREE
+
+
+@pytest.mark.slow
+def test_solve_parity_config2_free_association(vd, cfg2):
+    """The benchmark's own mode: 96^3 lattice, 640x480 depth, 10 x 20, re-associated at
+    every iteration.  For each iteration g the GPU solve of g + 1 iterations is stopped
+    and its association (taken at the start of iteration g) compared pixel by pixel with
+    the oracle's; the count of differing target pixels is printed per iteration and must
+    stay tiny, and the final warp and energy must meet the parity tolerances."""
+    ref = _cfg2_oracle_free(cfg2)
+    lat = vd.Lattice(cfg2.dims, cfg2.origin, cfg2.spacing, vd.VD_ACTIVE_ALL)
+    lat.set_frame_from(cfg2)
+    diffs = []
+    for g in range(10):
+        prm = vd.params(gn_iters=g + 1, cg_iters=20, fixed_association=False, init=vd.VD_INIT_ZERO)
+        rep = lat.solve(prm)
+        pix, _, _ = lat.association(prm)
+        diffs.append(int((pix != ref["pix"][g]).sum()))
+    u, _ = lat.get_warp()
+    err = float(np.abs(u - ref["u0"]).max())
+    rel = abs(rep["e_total"] - ref["e"][0]) / ref["e"][0]
+    print(f"config 2 free association: differing target pixels per iteration {diffs} of {cfg2.C}; "
+          f"|du|max = {err:.3e} m (tol {1e-4 * cfg2.spacing:.3e}), dE/E = {rel:.3e}")
+    assert max(diffs) <= max(2, cfg2.C // 1000)
+    assert err <= 1e-4 * cfg2.spacing
+    assert rel <= 1e-5
+
+
 # ------------------------------------------------------------------ precision variant
 
 def _mixed_vs_oracle(vd, fr, mode, gn, cg, res=None, u0=None):
@@ -355,6 +403,77 @@ def test_samples_outside_lattice(vd):
     pix, w, _ = lat.association(prm)
     pix0, w0, _ = ref.association()
     assert (pix == pix0).all() and (pix[fr.C:] == -1).all() and (w[fr.C:] == 0).all()
+
+
+def _non_finite_frame(fr, seed=7):
+    """fr with NaN / +inf / -inf depth pixels on the surface, samples with a NaN or
+    infinite position or normal, and one sparse pair with a NaN canonical position."""
+    rng = np.random.default_rng(seed)
+    on = np.argwhere(fr.depth > 0)
+    pick = on[rng.choice(len(on), 12, replace=False)]
+    depth = fr.depth.copy()
+    depth[pick[:6, 0], pick[:6, 1]] = np.nan
+    depth[pick[6:9, 0], pick[6:9, 1]] = np.inf
+    depth[pick[9:, 0], pick[9:, 1]] = -np.inf
+    pts, nrm = fr.src_pts.copy(), fr.src_nrm.copy()
+    pts[5] = np.nan
+    pts[17, 1] = np.inf
+    nrm[23] = np.nan
+    nrm[31, 2] = -np.inf
+    nrm[40, 0] = np.inf
+    fh = fr.sp_canon.copy()
+    fh[3, 1] = np.nan
+    return dataclasses.replace(fr, depth=depth, src_pts=pts, src_nrm=nrm, sp_canon=fh), [5, 17, 23, 31, 40]
+
+
+@pytest.mark.parametrize("mode", ["all", "surface"])
+def test_non_finite_inputs_treated_as_invalid(vd, mode):
+    """Non-finite depth pixels are invalid and samples or pairs with a non-finite
+    canonical position or normal are ignored, exactly as the oracle takes them: the
+    validity map, the active set and the target pixels are bit-exact, the solve within
+    the parity tolerances."""
+    fr, bad = _non_finite_frame(FRAMES["cfg1"])
+    lat, ref = _pair(vd, fr, mode)
+    _, N, valid = ref.target_maps()
+    g = lat.target_normals()
+    assert ((np.abs(g).sum(-1) > 0) == valid).all()
+    assert np.abs(g[valid] - N[valid]).max() < 2e-6
+    assert (lat.active_mask() == ref.active_mask()).all()
+    prm = vd.params()
+    lat.associate(prm)
+    ref.associate()
+    pix, w, _ = lat.association(prm)
+    pix0, w0, _ = ref.association()
+    assert (pix == pix0).all() and (pix[bad] == -1).all() and (w[bad] == 0).all()
+    lat, ref, rep, res, u, u0, R, R0 = _solve_pair(vd, fr, mode, 3, 10)
+    assert rep["status"] == vd.VD_OK and np.isfinite(u).all()
+    assert np.abs(u - u0).max() <= 1e-4 * fr.spacing
+    assert abs(rep["e_total"] - res["energy"][-1, 0]) / res["energy"][-1, 0] <= 1e-5
+
+
+def test_non_finite_target_reports_numeric_error(vd):
+    """A sparse pair whose observed position is NaN makes E_sparse non-finite (the
+    oracle's energy is NaN too): the solve returns VD_ERR_NUMERIC, and the lattice,
+    reset by a zero-initialised solve of a clean frame, solves normally again."""
+    fr = FRAMES["cfg1"]
+    ft = fr.sp_target.copy()
+    ft[2, 0] = np.nan
+    bad = dataclasses.replace(fr, sp_target=ft)
+    ref = oracle.Oracle.from_frame(bad, oracle.ACTIVE_ALL)
+    assert not np.isfinite(ref.solve(2, 10)["energy"][-1, 0])
+    lat = vd.Lattice(fr.dims, fr.origin, fr.spacing, vd.VD_ACTIVE_ALL)
+    lat.set_frame_from(bad)
+    prm = vd.params(gn_iters=2, cg_iters=10, fixed_association=True, init=vd.VD_INIT_ZERO)
+    rep = lat.solve(prm)
+    assert rep["status"] == vd.VD_ERR_NUMERIC
+    lat.set_frame_from(fr)
+    rep = lat.solve(prm)
+    assert rep["status"] == vd.VD_OK
+    ref = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    res = ref.solve(2, 10, fixed_association=True)
+    u, _ = lat.get_warp()
+    u0, _ = ref.get_warp()
+    assert np.abs(u - u0).max() <= 1e-4 * fr.spacing
 
 
 def test_smallest_lattice(vd):
