@@ -2012,7 +2012,11 @@ __device__ __forceinline__ void mat_to_quat(const float R[9], float q[4]) {
 // exactly when mu = q^T N q is the largest eigenvalue and every other one lies below
 // mu - delta.  On false the caller falls back to the Jacobi solve.
 // The iteration stops once |N q - mu q| <= 1e-6 max|N| (FP32 rounding level), after at
-// most three steps.  Each step solves (N - mu I) y = q through the Schur complement of
+// most three steps; if it has not got there by then (a warm start far from the answer)
+// the result is not used.  The certificate's gap is raised to 1e5 |N q - mu q| when that
+// exceeds `delta`: the eigenvector's angular error is at most the residual over the gap
+// (Davis-Kahan), so an accepted q is within 1e-5 rad of the top eigenvector.
+// Each step solves (N - mu I) y = q through the Schur complement of
 // the leading entry: writing N - mu I = [[m, b^T], [b, C]] (C the trailing 3x3 block),
 //   S = m det C - b^T adj(C) b  (= det(N - mu I)),  y0' = q0 det C - b^T adj(C) q_r,
 //   y  ~  (y0' det C,  S adj(C) q_r - y0' adj(C) b)
@@ -2023,14 +2027,14 @@ __device__ __forceinline__ void mat_to_quat(const float R[9], float q[4]) {
 // no usable direction and the certificate fails.
 __device__ __forceinline__ bool sym4_top_rqi(const float N[4][4], float q[4], float delta, float scale) {
     const float tol2 = 1e-12f * scale * scale;
-    float mu = 0.f;
+    float mu = 0.f, res2 = 0.f;
 #pragma unroll 1
     for (int it = 0;; it++) {
         float Nq[4];
 #pragma unroll
         for (int r = 0; r < 4; r++) Nq[r] = N[r][0] * q[0] + N[r][1] * q[1] + N[r][2] * q[2] + N[r][3] * q[3];
         mu = q[0] * Nq[0] + q[1] * Nq[1] + q[2] * Nq[2] + q[3] * Nq[3];
-        float res2 = 0.f;
+        res2 = 0.f;
 #pragma unroll
         for (int r = 0; r < 4; r++) res2 += (Nq[r] - mu * q[r]) * (Nq[r] - mu * q[r]);
         if (res2 <= tol2 || it == 3) break;
@@ -2054,6 +2058,8 @@ __device__ __forceinline__ bool sym4_top_rqi(const float N[4][4], float q[4], fl
 #pragma unroll
         for (int r = 0; r < 4; r++) q[r] = y[r] * sc;
     }
+    if (!(res2 <= tol2)) return false;  // not converged in three steps
+    delta = fmaxf(delta, 1e5f * sqrtf(res2));
     // certificate: Cholesky of M (all pivots > 0), reciprocal square roots of the pivots
     float L[4][4], rl[4];
 #pragma unroll
