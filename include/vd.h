@@ -347,6 +347,23 @@ vd_status vd_unet_train_step(vd_unet *net, const float *in6, const float *target
 vd_status vd_unet_save(vd_unet *net, const char *path);
 vd_status vd_unet_load(vd_unet *net, const char *path);
 
+/* Test support: an intermediate tensor of the last vd_unet_forward / vd_unet_train_step
+ * (activations after the forward pass; gradients with respect to them after the
+ * backward pass, in their final state: ReLU masks applied, the skip and pooling
+ * contributions summed) as dense floats converted from the stored BF16, layout
+ * D x H x W x C (channels fastest, x, then y, then z), C the stored channel count
+ * (padded to a multiple of 16; padding channels are zero).  dims (may be NULL) gets
+ * D, H, W, C; host may be NULL to query dims only, else it needs n >= D H W C floats.
+ * Synchronises the handle's stream.  VD_ERR_INVALID_ARG for a bad id or a short n. */
+enum {
+    VD_UNET_T_X = 0, VD_UNET_T_E1A, VD_UNET_T_E1, VD_UNET_T_P1, VD_UNET_T_E2A, VD_UNET_T_E2, VD_UNET_T_P2,
+    VD_UNET_T_E3A, VD_UNET_T_E3, VD_UNET_T_CAT2, VD_UNET_T_D2A, VD_UNET_T_D2, VD_UNET_T_CAT1, VD_UNET_T_D1A,
+    VD_UNET_T_D1, VD_UNET_T_GOUT, VD_UNET_T_GD1, VD_UNET_T_GD1A, VD_UNET_T_GCAT1, VD_UNET_T_GD2,
+    VD_UNET_T_GD2A, VD_UNET_T_GCAT2, VD_UNET_T_GE3, VD_UNET_T_GE3A, VD_UNET_T_GP2, VD_UNET_T_GE2,
+    VD_UNET_T_GE2A, VD_UNET_T_GP1, VD_UNET_T_GE1, VD_UNET_T_GE1A, VD_UNET_T_COUNT
+};
+vd_status vd_unet_get_tensor(vd_unet *net, int id, float *host, long long n, int dims[4]);
+
 typedef struct {
     double e_start;      /* E_total (Eq. 1) of the warp before the call, under its association */
     double e_predicted;  /* E_total of the predicted warp (rotations refitted), its association */

@@ -25,6 +25,7 @@
 #include <map>
 #include <mutex>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <random>
@@ -995,6 +996,49 @@ vd_status vd_unet_load(vd_unet *U, const char *path) {
     fclose(f);
     if (!ok) return VD_ERR_INVALID_ARG;
     return vd_unet_set_params(U, h.data(), n);
+}
+
+// The intermediate tensors in the order of the VD_UNET_T_* ids of include/vd.h.
+static View unet_tensor(vd_unet *U, int id) {
+    const View e1 = slice(U->cat1, 32, 16), e2 = slice(U->cat2, 64, 32);
+    const View ge1 = slice(U->gcat1, 32, 16), ge2 = slice(U->gcat2, 64, 32);
+    const View t[] = {U->x,    U->e1a,  e1,     U->p1,   U->e2a,  e2,      U->p2,    U->e3a,  U->e3,  U->cat2,
+                      U->d2a,  U->d2,   U->cat1, U->d1a, U->d1,   U->gout, U->gd1,   U->gd1a, U->gcat1, U->gd2,
+                      U->gd2a, U->gcat2, U->ge3, U->ge3a, U->gp2, ge2,      U->ge2a, U->gp1,  ge1,     U->ge1a};
+    static_assert(sizeof(t) / sizeof(t[0]) == VD_UNET_T_COUNT, "tensor table");
+    return t[id];
+}
+
+vd_status vd_unet_get_tensor(vd_unet *U, int id, float *host, long long n, int dims[4]) {
+    if (!U || id < 0 || id >= VD_UNET_T_COUNT) return VD_ERR_INVALID_ARG;
+    const View v = unet_tensor(U, id);
+    if (dims) {
+        dims[0] = v.D;
+        dims[1] = v.H;
+        dims[2] = v.W;
+        dims[3] = v.nc;
+    }
+    if (!host) return VD_OK;
+    const long long need = (long long)v.D * v.H * v.W * v.nc;
+    if (n < need) return VD_ERR_INVALID_ARG;
+    // the whole buffer (halo and slack included) once, then the view's voxels on the host
+    const bf16 *base = v.p - v.c0;
+    const size_t elems = (size_t)(v.D + 2) * (v.H + 2) * v.Wp * v.C + 16 * (size_t)v.C;
+    std::vector<uint16_t> raw(elems);
+    if (cudaStreamSynchronize(U->st) != cudaSuccess ||
+        cudaMemcpy(raw.data(), base, elems * sizeof(uint16_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return VD_ERR_CUDA;
+    size_t k = 0;
+    for (int z = 0; z < v.D; z++)
+        for (int y = 0; y < v.H; y++)
+            for (int x = 0; x < v.W; x++) {
+                const size_t o = vox(v, z, y, x) * v.C + v.c0;
+                for (int c = 0; c < v.nc; c++) {
+                    const uint32_t bits = (uint32_t)raw[o + c] << 16;  // BF16 is the top half of an FP32
+                    memcpy(&host[k++], &bits, sizeof(float));
+                }
+            }
+    return VD_OK;
 }
 
 vd_status vd_unet_dims(const vd_unet *U, int *nx, int *ny, int *nz) {

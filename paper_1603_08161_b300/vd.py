@@ -25,6 +25,10 @@ VD_INIT_PREV, VD_INIT_ZERO = 0, 1
 KERNEL_CLASSES = {"associate": 0, "rhs": 1, "apply_stencil": 2, "apply_samples": 3, "update_x": 4,
                   "update_p": 5, "rotation": 6, "energy": 7, "pcg": 8}
 
+UNET_TENSORS = ["x", "e1a", "e1", "p1", "e2a", "e2", "p2", "e3a", "e3", "cat2", "d2a", "d2", "cat1", "d1a", "d1",
+                "gout", "gd1", "gd1a", "gcat1", "gd2", "gd2a", "gcat2", "ge3", "ge3a", "gp2", "ge2", "ge2a", "gp1",
+                "ge1", "ge1a"]  # ids VD_UNET_T_* of include/vd.h, in order
+
 STATUS_NAMES = {0: "VD_OK", 1: "VD_ERR_INVALID_ARG", 2: "VD_ERR_OOM", 3: "VD_ERR_CUDA", 4: "VD_ERR_STATE",
                 5: "VD_ERR_NUMERIC", 6: "VD_ERR_TIMEOUT"}
 
@@ -96,6 +100,7 @@ _SIGS = {
     "vd_launch_counts": [_P, ctypes.POINTER(vd_solve_params), _PI, _PI],
     "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
     "vd_batch_set_plan": [_P, _I, _I, ctypes.c_longlong],
+    "vd_unet_get_tensor": [_P, _I, _P, ctypes.c_longlong, _PI],
     "vd_batch_create": [_P, _I, ctypes.POINTER(_P)],
     "vd_batch_destroy": [_P],
     "vd_batch_solve": [_P, ctypes.POINTER(vd_solve_params), _P],
@@ -480,6 +485,15 @@ class UNet:
         self._check(vd_unet_train_step(self.h, _ptr(in6)[0], _ptr(target3)[0], float(surface_weight), float(lr),
                                        ctypes.byref(loss)), "vd_unet_train_step")
         return loss.value
+
+    def tensor(self, name):
+        """Intermediate tensor of the last forward / training step, (D, H, W, C) float32."""
+        tid = UNET_TENSORS.index(name)
+        dims = (ctypes.c_int * 4)()
+        self._check(vd_unet_get_tensor(self.h, tid, None, 0, dims), "vd_unet_get_tensor")
+        a = np.zeros(tuple(dims), np.float32)
+        self._check(vd_unet_get_tensor(self.h, tid, a.ctypes.data, a.size, dims), "vd_unet_get_tensor")
+        return a
 
     def save(self, path):
         self._check(vd_unet_save(self.h, os.fsencode(path)), f"vd_unet_save({path})")
