@@ -13,6 +13,10 @@ Parity status of each part (what pins it is in tests/test_oracle_pins.py):
   * Jacobian .............................. pinned (central finite differences of E)
   * PCG position step ...................... pinned (dense Cholesky, closed forms)
   * rotation step .......................... pinned (brute-force search over SO(3))
+  * hierarchy (Sec. 7.2): restriction of the constraints, injection of the state and
+    trilinear prolongation ................. pinned (affine fields reproduced exactly;
+                                             data energies of a coarse-trilinear warp equal
+                                             on both levels; rigid targets recovered)
   * end-to-end accuracy against ground truth: parity unpinned (the paper prints no
     numbers); reported only.
 """
@@ -80,6 +84,9 @@ def _load():
         "vdo_procrustes": (i, [D, D]),
         "vdo_fit_rotations": (i, [P]),
         "vdo_solve": (i, [P, i, i, d, i, i, D, I, I]),
+        "vdo_set_domain": (None, [P, i, i, i, ctypes.c_float]),
+        "vdo_restrict_state": (None, [P, P]),
+        "vdo_prolongate": (None, [P, D, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -131,8 +138,13 @@ class Oracle:
         self.W = self.H = self.C = 0
 
     @classmethod
-    def from_frame(cls, fr, active_mode=ACTIVE_ALL, params=None):
-        o = cls(fr.dims, fr.origin, fr.spacing, active_mode)
+    def from_frame(cls, fr, active_mode=ACTIVE_ALL, params=None, dims=None, spacing=None):
+        """Lattice with the frame's input; dims / spacing override the frame's lattice
+        (a coarse level, whose constraints are gathered from the frame's own lattice)."""
+        o = cls(dims or fr.dims, fr.origin, spacing or fr.spacing, active_mode)
+        if dims is not None:
+            _load().vdo_set_domain(o._c, int(fr.dims[0]), int(fr.dims[1]), int(fr.dims[2]),
+                                   ctypes.c_float(fr.spacing))
         if params is not None:
             o.set_params(**params)
         o.set_correspondences(fr.sp_canon, fr.sp_target)
@@ -263,3 +275,58 @@ class Oracle:
                               _ptr(st, ctypes.c_int))
         return {"gn_done": g, "energy": e.reshape(gn_iters, 4)[:g], "cg_done": cg[:g],
                 "n_valid": int(st[0]), "n_degenerate": int(st[1])}
+
+
+def coarse_dims(dims):
+    """Node counts of the next coarser level (Sec. 7.2): every coarse cell is the parent
+    voxel of 2 x 2 x 2 finer cells, so n nodes per axis become n // 2 + 1 (the nodes
+    0, 2, 4, ... of the finer axis; one past its end when n - 1 is odd)."""
+    return tuple(int(n) // 2 + 1 for n in dims)
+
+
+class Hierarchy:
+    """Nested coarse-to-fine solve of one frame (Sec. 7.2): level 0 is the frame's own
+    lattice, level l has spacing 2^l h and the same origin, and gathers every constraint
+    of the finest level into its coarse cells (each expressed trilinearly in the coarse
+    nodes).  A solve restricts the state to every coarse level (injection), then from
+    the coarsest level up: flip-flop solve of the level, prolongation of its
+    displacement increment to the next finer level, one rotation step there (Sec. 7.1,
+    with the prolongated positions); finally the flip-flop solve of level 0."""
+
+    def __init__(self, fr, levels, active_mode=ACTIVE_ALL, params=None):
+        assert levels >= 1
+        self.levels = [Oracle.from_frame(fr, active_mode, params)]
+        dims, h = tuple(fr.dims), float(np.float32(fr.spacing))
+        for _ in range(1, levels):
+            dims = coarse_dims(dims)
+            h = float(np.float32(2.0 * h))
+            self.levels.append(Oracle.from_frame(fr, active_mode, params, dims=dims, spacing=h))
+
+    def restrict(self):
+        """Injection of the state into every coarse level; returns the start displacements."""
+        lib = _load()
+        starts = [None]
+        for l in range(1, len(self.levels)):
+            lib.vdo_restrict_state(self.levels[l - 1]._c, self.levels[l]._c)
+            starts.append(self.levels[l].get_warp()[0].copy())
+        return starts
+
+    def prolongate(self, l, start):
+        """Add level l's increment (u - start) to level l - 1, trilinearly."""
+        s = np.ascontiguousarray(start, np.float64).reshape(-1)
+        _load().vdo_prolongate(self.levels[l]._c, _ptr(s, ctypes.c_double), self.levels[l - 1]._c)
+
+    def solve(self, schedule, fixed_association=False):
+        """schedule: (gn_iters, cg_iters) per level, coarsest first.  Returns the
+        per-level results of Oracle.solve, coarsest first."""
+        assert len(schedule) == len(self.levels)
+        starts = self.restrict()
+        out = []
+        for l in range(len(self.levels) - 1, 0, -1):
+            gn, cg = schedule[len(self.levels) - 1 - l]
+            out.append(self.levels[l].solve(gn, cg, fixed_association=fixed_association))
+            self.prolongate(l, starts[l])
+            self.levels[l - 1].fit_rotations()
+        gn, cg = schedule[-1]
+        out.append(self.levels[0].solve(gn, cg, fixed_association=fixed_association))
+        return out

@@ -62,6 +62,11 @@ typedef struct vdo_ctx {
     int nx, ny, nz, nn;
     double o[3], h;
     int active_mode;
+    /* coarse level of a hierarchy (Sec. 7.2): the finest lattice's node counts and
+       spacing (same origin); a constraint belongs to this level only if its cell exists
+       on the finest lattice.  dom_h = 0: no such restriction. */
+    int dom_n[3];
+    double dom_h;
     /* frame */
     int W, H;
     double fx, fy, cx, cy;
@@ -153,6 +158,11 @@ static int locate(const vdo_ctx *c, const double p[3], double frac[3])
 {
     int ci[3];
     int dims[3] = {c->nx, c->ny, c->nz};
+    if (c->dom_h > 0)   /* gathered from the finest level: its cell must exist there */
+        for (int a = 0; a < 3; a++) {
+            double fl = floor((p[a] - c->o[a]) / c->dom_h);
+            if (!(fl >= 0.0) || fl > (double)(c->dom_n[a] - 2)) return -1;
+        }
     for (int a = 0; a < 3; a++) {
         double q = (p[a] - c->o[a]) / c->h;
         double fl = floor(q);
@@ -979,4 +989,79 @@ int vdo_solve(vdo_ctx *c, int gn_iters, int cg_iters, double cg_tol, int fixed_a
     }
     free(delta);
     return g;
+}
+
+/* ------------------------------------------------------------------ hierarchy (Sec. 7.2) */
+
+/* Mark c as a coarse level of a hierarchy whose finest lattice has n0 nodes per axis and
+ * spacing h0 (same origin): only constraints whose cell exists on the finest lattice are
+ * gathered.  Call before vdo_set_frame / vdo_set_correspondences. */
+void vdo_set_domain(vdo_ctx *c, int nx0, int ny0, int nz0, float h0)
+{
+    c->dom_n[0] = nx0; c->dom_n[1] = ny0; c->dom_n[2] = nz0;
+    c->dom_h = (double)h0;
+}
+
+/* Start state of a coarse level: every coarse node takes the displacement and rotation
+ * of the finer node it coincides with (node 2X of the finer level).  A coarse node one
+ * spacing past the end of the finer lattice along an axis (n - 1 odd) has no such node:
+ * its displacement is extrapolated linearly along that axis from the last two finer
+ * nodes, 2 u(n - 1) - u(n - 2) (per axis, so affine fields are reproduced exactly), and
+ * it takes the rotation of the finer lattice's nearest node. */
+void vdo_restrict_state(const vdo_ctx *fine, vdo_ctx *coarse)
+{
+    int fd[3] = {fine->nx, fine->ny, fine->nz};
+    for (int I = 0; I < coarse->nn; I++) {
+        int XYZ[3], pos[3][2], npt[3];
+        double wt[3][2];
+        node_xyz(coarse, I, &XYZ[0], &XYZ[1], &XYZ[2]);
+        for (int a = 0; a < 3; a++) {
+            if (2 * XYZ[a] < fd[a]) {
+                npt[a] = 1;
+                pos[a][0] = 2 * XYZ[a];
+                wt[a][0] = 1.0;
+            } else {
+                npt[a] = 2;
+                pos[a][0] = fd[a] - 1;
+                wt[a][0] = 2.0;
+                pos[a][1] = fd[a] - 2;
+                wt[a][1] = -1.0;
+            }
+        }
+        double acc[3] = {0, 0, 0};
+        for (int kx = 0; kx < npt[0]; kx++)
+            for (int ky = 0; ky < npt[1]; ky++)
+                for (int kz = 0; kz < npt[2]; kz++) {
+                    int i = node_id(fine, pos[0][kx], pos[1][ky], pos[2][kz]);
+                    double w = wt[0][kx] * wt[1][ky] * wt[2][kz];
+                    for (int a = 0; a < 3; a++) acc[a] += w * fine->u[3 * i + a];
+                }
+        memcpy(coarse->u + 3 * I, acc, 3 * sizeof(double));
+        int i0 = node_id(fine, pos[0][0], pos[1][0], pos[2][0]);
+        memcpy(coarse->R + 9 * I, fine->R + 9 * i0, 9 * sizeof(double));
+    }
+    coarse->have_J = 0;
+}
+
+/* Jump start of the finer level from the coarse solution: every finer node i adds the
+ * coarse level's displacement increment (u - u_start) interpolated trilinearly at its
+ * canonical position, which lies at coarse coordinates (x/2, y/2, z/2). */
+void vdo_prolongate(const vdo_ctx *coarse, const double *u_start, vdo_ctx *fine)
+{
+    int cd[3] = {coarse->nx, coarse->ny, coarse->nz};
+    for (int i = 0; i < fine->nn; i++) {
+        int xyz[3], ci[3];
+        double f[3], al[8], acc[3] = {0, 0, 0};
+        int nd[8];
+        node_xyz(fine, i, &xyz[0], &xyz[1], &xyz[2]);
+        for (int a = 0; a < 3; a++) {
+            ci[a] = xyz[a] / 2 < cd[a] - 2 ? xyz[a] / 2 : cd[a] - 2;
+            f[a] = 0.5 * xyz[a] - ci[a];
+        }
+        corners(coarse, node_id(coarse, ci[0], ci[1], ci[2]), f, nd, al);
+        for (int k = 0; k < 8; k++)
+            for (int a = 0; a < 3; a++) acc[a] += al[k] * (coarse->u[3 * nd[k] + a] - u_start[3 * nd[k] + a]);
+        for (int a = 0; a < 3; a++) fine->u[3 * i + a] += acc[a];
+    }
+    fine->have_J = 0;
 }

@@ -635,3 +635,121 @@ def test_non_finite_inputs_are_invalid():
     ft[2, 0] = np.nan
     c = oracle.Oracle.from_frame(dataclasses.replace(fr, sp_target=ft), oracle.ACTIVE_ALL)
     assert not np.isfinite(c.solve(1, 5)["energy"][-1, 0])
+
+
+# ---------------------------------------------------------------- hierarchy (Sec. 7.2)
+
+def test_coarse_levels_are_nested_parents():
+    """n nodes per axis -> n // 2 + 1: coarse node X sits on finer node 2X, and the
+    coarse lattice covers the finer one (its last cell is the parent of the last one)."""
+    for n in (2, 3, 4, 9, 16, 17, 48, 49, 96):
+        c = oracle.coarse_dims((n, n, n))[0]
+        assert 2 * (c - 2) <= n - 2 <= 2 * (c - 1) - 1 or n == 2
+        assert 2 * (c - 1) >= n - 1 and 2 * (c - 2) < n - 1 or n == 2
+    assert oracle.coarse_dims((96, 96, 96)) == (49, 49, 49)
+    assert oracle.coarse_dims((49, 49, 49)) == (25, 25, 25)
+
+
+def _affine(pos, A, c):
+    return pos @ A.T + c
+
+
+def test_prolongation_and_injection_reproduce_affine_fields():
+    """Trilinear prolongation reproduces an affine displacement field exactly at every
+    finer node, and injection followed by prolongation onto a zero field gives it back."""
+    rng = np.random.default_rng(12)
+    fr = synth.config1()
+    H = oracle.Hierarchy(fr, 3)
+    A = rng.normal(0, 0.05, (3, 3))
+    c = rng.normal(0, 0.01, 3)
+    fine, coarse = H.levels[0], H.levels[1]
+    pos_f = _node_pos(fr)
+    crs = dataclasses.replace(fr, dims=coarse.dims, spacing=float(np.float32(2 * fr.spacing)))
+    pos_c = _node_pos(crs)
+    # prolongation of an affine coarse increment onto a zero fine field
+    coarse.set_warp(_affine(pos_c, A, c))
+    fine.set_warp(None)
+    H.prolongate(1, np.zeros((coarse.nn, 3)))
+    u, _ = fine.get_warp()
+    assert np.abs(u - _affine(pos_f, A, c)).max() < 1e-13
+    # injection of the fine field: coarse node X takes fine node 2X, and a coarse node
+    # past the end of the (even) fine axis the linear extrapolation: the affine field
+    starts = H.restrict()
+    nx, ny, nz = fr.dims
+    X, Y, Z = np.meshgrid(np.arange(coarse.dims[0]), np.arange(coarse.dims[1]), np.arange(coarse.dims[2]),
+                          indexing="ij")
+    inside = (2 * X < nx) & (2 * Y < ny) & (2 * Z < nz)
+    src = (2 * X + nx * (2 * Y + ny * 2 * Z))[inside]
+    dst = (X + coarse.dims[0] * (Y + coarse.dims[1] * Z))
+    assert np.array_equal(starts[1][dst[inside]], u[src])
+    assert (~inside).any()
+    assert np.abs(starts[1] - _affine(pos_c, A, c)).max() < 1e-13
+    # ... and prolongating the injected field onto zero reproduces the affine field
+    fine.set_warp(None)
+    H.prolongate(1, np.zeros((coarse.nn, 3)))
+    u2, _ = fine.get_warp()
+    assert np.abs(u2 - _affine(pos_f, A, c)).max() < 1e-13
+
+
+def test_coarse_level_gathers_the_finest_constraints():
+    """A coarse level holds exactly the constraints of the finest level, each expressed
+    trilinearly in the coarse nodes: under a warp that is trilinear on the coarse grid
+    (a random coarse field prolongated to the fine lattice, R = I) both levels warp every
+    sample to the same point, so the association and the data energies (Eq. 2, 3)
+    agree to rounding.  Samples outside the finest lattice stay out of the coarse one."""
+    rng = np.random.default_rng(13)
+    base = synth.config1()
+    extra = base.src_pts[:40].copy()
+    extra[:, 2] = 1.5                                          # beyond the fine lattice, inside the coarse
+    fr = dataclasses.replace(base, src_pts=np.concatenate([base.src_pts, extra]),
+                             src_nrm=np.concatenate([base.src_nrm, base.src_nrm[:40]]))
+    H = oracle.Hierarchy(fr, 2)
+    fine, coarse = H.levels
+    cf, _ = fine.sample_cells()
+    cc, _ = coarse.sample_cells()
+    assert np.array_equal(cf < 0, cc < 0) and (cf[fr.C - 40:] < 0).any()
+    coarse.set_warp(rng.normal(0, 0.01, (coarse.nn, 3)))
+    fine.set_warp(None)
+    H.prolongate(1, np.zeros((coarse.nn, 3)))
+    fine.associate()
+    coarse.associate()
+    pf, wf, rf = fine.association()
+    pc, wc, rc = coarse.association()
+    assert np.array_equal(pf, pc) and (wf > 0).sum() > 100
+    assert np.abs(wf - wc).max() < 1e-12 and np.abs(rf - rc).max() < 1e-12
+    ef, ec = fine.energy(), coarse.energy()
+    assert abs(ef[1] - ec[1]) <= 1e-10 * ef[1] and abs(ef[2] - ec[2]) <= 1e-10 * ef[2]
+
+
+def test_hierarchy_recovers_rigid_targets():
+    """Sparse targets under a rigid motion (Q, c): the coarse-to-fine flip-flop drives
+    E to 0 and every fine R_i to Q, as the single level does."""
+    rng = np.random.default_rng(14)
+    fr = _no_dense(synth.plane_frame(n=9))
+    lo = fr.origin.astype(np.float64)
+    canon = rng.uniform(lo, lo + 8 * fr.spacing, (20, 3))
+    Q = _rand_rot(rng, 0.15)
+    c = rng.normal(0, 0.01, 3)
+    fr = _with_sparse(fr, canon, canon @ Q.T + c)
+    H = oracle.Hierarchy(fr, 2)
+    res = H.solve([(30, 3 * 125), (30, 3 * 729)], fixed_association=True)
+    assert res[-1]["energy"][-1, 0] < 1e-12
+    _, R = H.levels[0].get_warp()
+    assert np.abs(R - Q).max() < 1e-4
+
+
+def test_coarse_start_resolves_the_low_frequencies():
+    """The motivation of Sec. 7.2: a translation of every sparse target is a pure
+    low-frequency correction that a few fine CG iterations propagate only a few nodes
+    far; with the coarse levels first, the same fine iterations end far closer to the
+    exact solution (u = d everywhere, E = 0)."""
+    rng = np.random.default_rng(15)
+    fr = _no_dense(synth.plane_frame(n=33))
+    lo = fr.origin.astype(np.float64)
+    canon = rng.uniform(lo, lo + 32 * fr.spacing, (30, 3))
+    fr = _with_sparse(fr, canon, canon + np.array([0.02, -0.01, 0.015]))
+    one = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    e1 = one.solve(2, 10)["energy"][-1, 0]
+    H = oracle.Hierarchy(fr, 3)
+    e3 = H.solve([(2, 10), (2, 10), (2, 10)])[-1]["energy"][-1, 0]
+    assert e3 < 0.1 * e1
