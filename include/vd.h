@@ -175,6 +175,35 @@ vd_status vd_step_fit_rotations(vd_lattice *lat, int *n_degenerate);
  * association. */
 vd_status vd_step_energy(vd_lattice *lat, const vd_solve_params *params, double out[4]);
 
+/* ---- cached B^T B (Sec. 7.1) ----
+ *
+ * The paper precomputes and caches B^T B (the data constraints' part of the normal
+ * matrix) before the PCG iterations, because a cell may hold thousands of constraints.
+ * With VD_APPLY_CACHED the dense samples' part of J^T J is built once per association as
+ * one 24 x 24 block per occupied lattice cell (w_d sum_j (alpha_j (x) g_j)(alpha_j (x)
+ * g_j)^T over the cell's samples, 2,304 bytes per cell) and every PCG iteration applies
+ * the blocks; the sparse pairs and the ARAP stencil stay matrix-free.  The result is
+ * the same matrix as the matrix-free apply (VD_APPLY_MATRIX_FREE, the default, which
+ * reads each sample's record every iteration), in a different summation order.
+ * VD_APPLY_AUTO takes the cached blocks when the frame has at least 32 samples per
+ * occupied cell (the coarse levels of a hierarchy start in this mode). */
+enum { VD_APPLY_MATRIX_FREE = 0, VD_APPLY_CACHED = 1, VD_APPLY_AUTO = 2 };
+
+/* Select how the samples' J^T J p is applied (takes effect from the next solve or
+ * step call; may allocate the blocks).  VD_ERR_INVALID_ARG for an unknown mode. */
+vd_status vd_set_apply_mode(vd_lattice *lat, int mode);
+
+/* The selected mode and whether the current frame uses the cached blocks (either may be
+ * NULL). */
+vd_status vd_get_apply_mode(const vd_lattice *lat, int *mode, int *cached_now);
+
+/* Autotune the apply for this frame and these parameters: time two solves with each of
+ * VD_APPLY_MATRIX_FREE and VD_APPLY_CACHED (after one warm-up solve each), keep the
+ * faster.  ms_out (may be NULL) gets the time per solve of each (ms).  Runs the solve
+ * six times, so the warp changes (VD_INIT_PREV) -- save and restore it around the call
+ * if it matters. */
+vd_status vd_tune_apply(vd_lattice *lat, const vd_solve_params *params, int *mode_out, float ms_out[2]);
+
 /* ---- measurement support ---- */
 
 /* Kernel classes that vd_profile can time inside the captured solve graph. */
@@ -283,6 +312,48 @@ vd_status vd_solve_batch(vd_lattice *const *lattices, int count, const vd_solve_
 vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spacing, const float *disp,
                                    const float *rot_in, float *rot_out, double *e_reg,
                                    int *n_degenerate, void *cuda_stream);
+
+/* ---- hierarchical coarse-to-fine solve (Sec. 7.2) ----
+ *
+ * A hierarchy nests levels - 1 coarse lattices on a lattice (level 0): level l has
+ * n_{l-1} / 2 + 1 nodes per axis (integer division; node X of level l sits on node 2X of
+ * level l - 1, one spacing past its end when n_{l-1} - 1 is odd), spacing 2^l h, the
+ * same origin, active-set mode, precision and CUDA stream.  Every coarse cell is the
+ * parent voxel of 2 x 2 x 2 cells of the level below; a coarse level gathers all the
+ * constraints of level 0 (the dense samples and sparse pairs whose cell exists on level
+ * 0) and expresses each trilinearly in its own nodes.  Each level's energy is Eq. 1-4 on
+ * its own lattice with the same weights.  The hierarchy owns the coarse lattices; level
+ * 0 stays the caller's and must outlive it. */
+typedef struct vd_hierarchy vd_hierarchy; /* opaque; owned by the library */
+
+/* levels >= 1 (1: level 0 alone), at most 8.  Allocates the coarse lattices. */
+vd_status vd_hierarchy_create(vd_lattice *fine, int levels, vd_hierarchy **out);
+vd_status vd_hierarchy_destroy(vd_hierarchy *h);
+
+/* The lattice of one level (0 = the caller's), for vd_get_warp, vd_get_association and
+ * the other per-lattice calls; coarse lattices belong to the hierarchy (do not destroy). */
+vd_status vd_hierarchy_level(vd_hierarchy *h, int level, vd_lattice **out);
+
+/* Coarse-to-fine solve of level 0's current frame.  params[k] is the schedule of level
+ * levels - 1 - k (coarsest first, level 0 last); only the last entry's init is used
+ * (VD_INIT_ZERO resets level 0's warp first).  Steps, on level 0's stream: the state of
+ * every coarse level is restricted from the level below (displacement and rotation of
+ * the coinciding node; along an axis past the end of the level below, the displacement
+ * extrapolated linearly from its last two nodes); then from the coarsest level up: its
+ * flip-flop solve (as vd_solve, starting from the restricted state), the trilinear
+ * prolongation of its displacement increment to every node of the level below, and one
+ * rotation step (Sec. 7.1) there; finally level 0's flip-flop solve.  A coarse level's
+ * frame is copied from level 0 on the first solve after vd_set_frame or
+ * vd_set_correspondences on level 0.  `out` (may be NULL) gets `levels` reports,
+ * coarsest first.  Synchronous; the _async form enqueues and returns,
+ * vd_hierarchy_get_reports waits.  An energy target set with vd_set_energy_target on a
+ * level's lattice gates that level's iterations. */
+vd_status vd_hierarchy_solve(vd_hierarchy *h, const vd_solve_params *params, vd_solve_report *out);
+vd_status vd_hierarchy_solve_async(vd_hierarchy *h, const vd_solve_params *params);
+vd_status vd_hierarchy_get_reports(vd_hierarchy *h, vd_solve_report *out);
+
+/* One-line description of the hierarchy's last error. */
+const char *vd_hierarchy_last_error(const vd_hierarchy *h);
 
 /* ---- Gauss-Newton early stop ----
  *

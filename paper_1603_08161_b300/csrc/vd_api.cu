@@ -82,11 +82,12 @@ struct vd_lattice {
     // host-side sizes of the current frame (for grid sizing)
     int n_active_h = 0, n_samples_h = 0, n_occ_h = 0;
     bool have_frame = false;
+    long frame_gen = 0;              // counts vd_set_frame / vd_set_correspondences calls
     // graph
     cudaGraphExec_t gexec = nullptr;
     vd_solve_params gparams{};
     Ctx gctx{};
-    int gkey_caps[5] = {0, 0, 0, 0, 0};
+    int gkey_caps[6] = {0, 0, 0, 0, 0, 0};
     long gen = 0, ggen = -1;         // buffer generation (pointers changed)
     int stall_extra = 0;             // vd_test_stall_barrier: arrivals awaited beyond the grid
     int launches_solve = 0, launches_frame = 0;
@@ -113,6 +114,10 @@ struct vd_lattice {
     bool gated = false;
     // learned warm start: features (6 nn), prediction (3 nn), backup of u and R (12 ld)
     float *warm = nullptr;
+    // cached B^T B of the dense samples (per occupied cell, 24 x 24), VD_APPLY_*
+    int apply_mode = VD_APPLY_MATRIX_FREE;
+    float *btb = nullptr;
+    int cap_occ = 0;
 };
 
 namespace {
@@ -265,6 +270,18 @@ vd_status ensure_scal(vd_lattice *L, int G, int K) {
 
 Scal *slot(vd_lattice *L, int g) { return (Scal *)(L->scal + L->scal_stride * (size_t)g); }
 
+// samples per occupied cell from which VD_APPLY_AUTO takes the cached blocks: a block
+// is 576 multiply-adds and 2,304 bytes per cell and iteration, the matrix-free apply of
+// one sample about 48 multiply-adds, 28 bytes and 8 corner gathers
+constexpr int kAutoSamplesPerCell = 32;
+
+bool use_cached(const vd_lattice *L) {
+    if (L->apply_mode == VD_APPLY_CACHED) return L->n_occ_h > 0;
+    if (L->apply_mode == VD_APPLY_AUTO)
+        return L->n_occ_h > 0 && (long)L->n_samples_h >= (long)kAutoSamplesPerCell * L->n_occ_h;
+    return false;
+}
+
 void refresh_ctx(vd_lattice *L) {
     Ctx &c = L->c;
     c.u = L->u;
@@ -300,6 +317,18 @@ void refresh_ctx(vd_lattice *L) {
     c.S = L->S;
     c.e_target = L->gated ? L->rep_dev + 15 : nullptr;
     c.cell_part = L->cell_part;
+    c.btb = (use_cached(L) && L->cap_occ >= L->n_occ_h) ? L->btb : nullptr;
+}
+
+// room for the cached blocks of the current frame's occupied cells (when they are used)
+vd_status ensure_btb(vd_lattice *L) {
+    if (L->apply_mode == VD_APPLY_MATRIX_FREE || L->n_occ_h <= L->cap_occ) return VD_OK;
+    dfree(L, L->btb);
+    L->cap_occ = 0;
+    const int cap = L->n_occ_h + L->n_occ_h / 4 + 64;
+    TRY(dalloc(L, &L->btb, (size_t)cap * kBtb));
+    L->cap_occ = cap;
+    return VD_OK;
 }
 
 void set_params_ctx(Ctx &c, const vd_solve_params *p) {
@@ -330,6 +359,8 @@ struct Grid {
     int node4;   // blocks over float4 groups of slots
     int samp, cells;
     int refine;  // blocks of the FP64 re-association (a grid-stride loop over the list)
+    int btb;     // blocks of the cached-B^T B apply (one warp per occupied cell)
+    int btb_build;  // blocks of its build (one warp per 64 samples)
     bool vec4;   // all-nodes lattice with nx % 4 == 0: float4 stencil
 };
 
@@ -343,6 +374,10 @@ Grid grids(vd_lattice *L) {
     // captured graph, stay the same for frames of similar size)
     g.cells = (int)std::min<long>(std::max<long>(round_pow2(std::max(L->n_samples_h, 1)) / 128, 1), (long)kSMs * 8);
     g.refine = std::min(g.samp, kSMs);
+    g.btb = (int)std::min<long>(std::max<long>((round_pow2(std::max(L->n_occ_h, 1)) + 7) / 8, 1), (long)kSMs * 8);
+    g.btb_build = (int)std::min<long>(
+        std::max<long>((round_pow2(std::max(L->n_samples_h, 1)) + 8 * kBtbChunk - 1) / (8 * kBtbChunk), 1),
+        (long)kSMs * 8);
     g.vec4 = L->all && (L->c.nx % 4 == 0);
     return g;
 }
@@ -396,7 +431,17 @@ template <bool kAll>
 void enqueue_apply(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K, int it) {
     if (gr.vec4) Lc.go(VD_KC_APPLY_STENCIL, k_apply_stencil<kAll, true>, gr.node4, kThreads, c, sc, K, it);
     else Lc.go(VD_KC_APPLY_STENCIL, k_apply_stencil<kAll, false>, gr.node, kThreads, c, sc, K, it);
-    Lc.go(VD_KC_APPLY_SAMPLES, k_cells<kOpApply, kAll>, gr.cells, kThreads, c, sc, K, it);
+    if (c.btb) Lc.go(VD_KC_APPLY_SAMPLES, k_cells_btb<kAll>, gr.btb, kThreads, c, sc, K, it);
+    else Lc.go(VD_KC_APPLY_SAMPLES, k_cells<kOpApply, kAll>, gr.cells, kThreads, c, sc, K, it);
+}
+
+// the cached blocks from this association's records (when the lattice uses them)
+template <bool kAll>
+void enqueue_btb(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int n_occ) {
+    if (!c.btb) return;
+    cudaMemsetAsync(c.btb, 0, sizeof(float) * kBtb * (size_t)std::max(n_occ, 1), Lc.st);
+    Lc.other();
+    Lc.go(VD_KC_RHS, k_btb_build<kAll>, gr.btb_build, kThreads, c, (const Scal *)sc);
 }
 
 // PCG position step: init, then K x (apply, x/r update, p update)
@@ -516,8 +561,9 @@ void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
         // the FP64 re-association runs in the first blocks of the right-hand side's node pass
         Lc.go(VD_KC_RHS, k_rhs_nodes_refine<kAll>, gr.refine + gr.node, kThreads, c, sc, gr.refine);
         Lc.go(VD_KC_RHS, k_cells<kOpRhs, kAll>, gr.cells, kThreads, c, sc, K, 0);
+        enqueue_btb<kAll>(Lc, c, sc, gr, L->n_occ_h);
     } else {
-        enqueue_rhs<kAll>(Lc, c, sc, gr, K);
+        enqueue_rhs<kAll>(Lc, c, sc, gr, K);  // the records, and so the cached blocks, are unchanged
     }
     int G = 0, chunk = 0;
     if (persistent_plan(L, &G, &chunk)) {
@@ -558,7 +604,8 @@ vd_status build_graph(vd_lattice *L, const vd_solve_params *P) {
     const Grid gr = grids(L);
     int pG = 0, pch = 0, pby = 0, pbz = 0;
     persistent_plan(L, &pG, &pch, &pby, &pbz);
-    const int caps[5] = {gr.node, gr.samp, gr.cells, L->S * 65536 + pch, pby * 65536 + pbz};
+    const int caps[6] = {gr.node, gr.samp, gr.cells, L->S * 65536 + pch, pby * 65536 + pbz,
+                         gr.btb * 65536 + (L->c.btb ? L->n_occ_h : 0)};
     const bool same = L->gexec && L->ggen == L->gen && !memcmp(&L->gparams, P, sizeof(*P)) &&
                       !memcmp(L->gkey_caps, caps, sizeof(caps)) && !memcmp(&L->gctx, &L->c, sizeof(Ctx));
     if (same) return VD_OK;
@@ -812,6 +859,7 @@ vd_status vd_set_correspondences(vd_lattice *L, const float *canon, const float 
         TRY(dalloc(L, &L->scell_s, (size_t)L->cap_S));
     }
     L->S = S;
+    L->frame_gen++;
     refresh_ctx(L);
     if (S > 0) {
         TRY(upload(L, L->sp_in, canon, sizeof(float) * 3 * S, mem));
@@ -847,6 +895,7 @@ vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const fl
     for (int a = 0; a < 9; a++) c.Rg[a] = pose ? pose[a] : ((a % 4 == 0) ? 1.f : 0.f);
     for (int a = 0; a < 3; a++) c.tg[a] = pose ? pose[9 + a] : 0.f;
     L->n_src = n_src;
+    L->frame_gen++;
     refresh_ctx(L);
     cudaStream_t st = L->stream;
     L->counting = 0;
@@ -874,6 +923,8 @@ vd_status vd_set_frame(vd_lattice *L, const float *depth, int W, int H, const fl
     L->have_frame = true;
     TRY(frame_active_set(L));
     TRY(sync_sizes(L));
+    TRY(ensure_btb(L));
+    refresh_ctx(L);
     const int nbc = grids(L).cells;
     k_cell_partition<<<(nbc + kThreads - 1) / kThreads, kThreads, 0, st>>>(L->occ_beg, L->counts + 1, nbc,
                                                                           L->cell_part);
@@ -1069,10 +1120,12 @@ vd_status vd_step_apply(vd_lattice *L, const vd_solve_params *P, const float *p,
     Launcher Lc{L, st};
     if (L->all) {
         k_gather_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(L->staging, c, c.p);
+        enqueue_btb<true>(Lc, c, sc, gr, L->n_occ_h);
         enqueue_apply<true>(Lc, c, sc, gr, 1, 0);
         k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.q, c, L->staging);
     } else {
         k_gather_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(L->staging, c, c.p);
+        enqueue_btb<false>(Lc, c, sc, gr, L->n_occ_h);
         enqueue_apply<false>(Lc, c, sc, gr, 1, 0);
         k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.q, c, L->staging);
     }
@@ -1100,21 +1153,25 @@ vd_status vd_step_pcg(vd_lattice *L, const vd_solve_params *P, float *delta, int
     if (persistent_plan(L, &pG, &pch)) {
         if (L->all) {
             enqueue_rhs<true>(Lc, c, sc, gr, K);
+            enqueue_btb<true>(Lc, c, sc, gr, L->n_occ_h);
             launch_persistent<true>(L, Lc, sc, K, tol2, apply, pG, pch);
             if (delta) k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         } else {
             enqueue_rhs<false>(Lc, c, sc, gr, K);
+            enqueue_btb<false>(Lc, c, sc, gr, L->n_occ_h);
             launch_persistent<false>(L, Lc, sc, K, tol2, apply, pG, pch);
             if (delta) k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         }
     } else if (L->all) {
         enqueue_rhs<true>(Lc, c, sc, gr, K);
+        enqueue_btb<true>(Lc, c, sc, gr, L->n_occ_h);
         enqueue_pcg<true>(Lc, c, sc, gr, K, tol2);
         Lc.other();
         if (delta) k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         if (apply) k_add_increment<true><<<gr.node, kThreads, 0, st>>>(c, sc);
     } else {
         enqueue_rhs<false>(Lc, c, sc, gr, K);
+        enqueue_btb<false>(Lc, c, sc, gr, L->n_occ_h);
         enqueue_pcg<false>(Lc, c, sc, gr, K, tol2);
         if (delta) k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         if (apply) k_add_increment<false><<<gr.node, kThreads, 0, st>>>(c, sc);
@@ -1171,6 +1228,56 @@ vd_status vd_step_energy(vd_lattice *L, const vd_solve_params *P, double out[4])
     return VD_OK;
 }
 
+vd_status vd_set_apply_mode(vd_lattice *L, int mode) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (mode != VD_APPLY_MATRIX_FREE && mode != VD_APPLY_CACHED && mode != VD_APPLY_AUTO)
+        return fail(L, VD_ERR_INVALID_ARG, "unknown apply mode %d", mode);
+    L->apply_mode = mode;
+    if (L->have_frame) TRY(ensure_btb(L));
+    refresh_ctx(L);
+    return VD_OK;
+}
+
+vd_status vd_get_apply_mode(const vd_lattice *L, int *mode, int *cached_now) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (mode) *mode = L->apply_mode;
+    if (cached_now) *cached_now = use_cached(L) ? 1 : 0;
+    return VD_OK;
+}
+
+vd_status vd_tune_apply(vd_lattice *L, const vd_solve_params *P, int *mode_out, float ms_out[2]) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    TRY(check_params(L, P));
+    if (!L->have_frame) return fail(L, VD_ERR_STATE, "vd_tune_apply before vd_set_frame");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float ms[2] = {0.f, 0.f};
+    const int modes[2] = {VD_APPLY_MATRIX_FREE, VD_APPLY_CACHED};
+    vd_status st = VD_OK;
+    for (int k = 0; k < 2 && st == VD_OK; k++) {
+        st = vd_set_apply_mode(L, modes[k]);
+        for (int rep = 0; rep < 3 && st == VD_OK; rep++) {  // the first replay warms up
+            if (rep == 1) cudaEventRecord(e0, L->stream);
+            st = vd_solve_async(L, P);
+        }
+        cudaEventRecord(e1, L->stream);
+        if (st == VD_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms[k], e0, e1);
+        ms[k] *= 0.5f;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != VD_OK) return st;
+    const int best = ms[1] < ms[0] ? VD_APPLY_CACHED : VD_APPLY_MATRIX_FREE;
+    TRY(vd_set_apply_mode(L, best));
+    if (mode_out) *mode_out = best;
+    if (ms_out) {
+        ms_out[0] = ms[0];
+        ms_out[1] = ms[1];
+    }
+    return VD_OK;
+}
+
 vd_status vd_profile_select(vd_lattice *L, int kc) {
     if (!L || kc < -1 || kc >= VD_KC_COUNT) return VD_ERR_INVALID_ARG;
     if (kc != L->prof_class) {
@@ -1198,7 +1305,7 @@ vd_status vd_launch_counts(vd_lattice *L, const vd_solve_params *P, int *per_sol
     const int assoc = P->fixed_association ? 1 : G;
     int pG = 0, pch = 0;
     const int per_gn = persistent_plan(L, &pG, &pch) ? 2 + 1 + 2 : 3 + 4 * K + 3;
-    const int n = assoc + G * per_gn + 1 + (P->init == VD_INIT_ZERO ? 1 : 0);
+    const int n = assoc * (use_cached(L) ? 2 : 1) + G * per_gn + 1 + (P->init == VD_INIT_ZERO ? 1 : 0);
     if (per_solve) *per_solve = n;
     if (per_frame) *per_frame = L->launches_frame;
     return VD_OK;
@@ -1708,6 +1815,191 @@ vd_status vd_get_warm_report(vd_lattice *L, vd_warm_report *out) {
     out->used_prediction = L->rep_host[13] != 0.0;
     out->status = VD_OK;
     return VD_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== hierarchy (Sec. 7.2)
+//
+// A hierarchy owns levels - 1 coarse lattices nested on a caller's lattice (level 0):
+// level l has (n_{l-1} // 2 + 1) nodes per axis at spacing 2^l h, the same origin, and
+// the same active-set mode, precision and stream.  Their frames are copied from level
+// 0's own device buffers whenever level 0 got a new frame or new pairs; their binning
+// keeps only the constraints whose cell exists on level 0 (the constraints of each
+// parent voxel gathered from its children, expressed trilinearly in the coarse nodes).
+// A solve enqueues, on level 0's stream: restriction of the state to every coarse level,
+// then from the coarsest up its captured flip-flop graph, the prolongation of its
+// increment to the next finer level and a rotation step there; then level 0's graph.
+
+struct vd_hierarchy {
+    std::vector<vd_lattice *> L;     // L[0] is the caller's; the others are owned
+    std::vector<float *> u_start;    // per coarse level, 3 planes of its ld
+    Scal *scal = nullptr;            // sums of the rotation steps after prolongation
+    long synced_gen = -1;
+    bool pending = false;
+    std::string err;
+};
+
+namespace {
+
+vd_status hfail(vd_hierarchy *H, vd_status s, const std::string &msg) {
+    H->err = msg;
+    return s;
+}
+
+// copy level 0's current frame and pairs into every coarse level
+vd_status hierarchy_sync(vd_hierarchy *H) {
+    vd_lattice *F = H->L[0];
+    if (H->synced_gen == F->frame_gen) return VD_OK;
+    const Ctx &c = F->c;
+    const float K[4] = {c.fx, c.fy, c.cx, c.cy};
+    float pose[12];
+    for (int a = 0; a < 9; a++) pose[a] = c.Rg[a];
+    for (int a = 0; a < 3; a++) pose[9 + a] = c.tg[a];
+    for (size_t l = 1; l < H->L.size(); l++) {
+        vd_lattice *Lc = H->L[l];
+        vd_status s = vd_set_correspondences(Lc, F->sp_in, F->sp_in + 3 * (size_t)F->S, F->S, VD_MEM_DEVICE);
+        if (s == VD_OK)
+            s = vd_set_frame(Lc, F->depth, F->W, F->H, K, pose, F->pts_in, F->nrm_in, F->n_src, VD_MEM_DEVICE);
+        if (s != VD_OK) return hfail(H, s, "level " + std::to_string(l) + ": " + Lc->err);
+    }
+    H->synced_gen = F->frame_gen;
+    return VD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vd_status vd_hierarchy_create(vd_lattice *fine, int levels, vd_hierarchy **out) {
+    if (!fine || !out || levels < 1 || levels > 8) return VD_ERR_INVALID_ARG;
+    *out = nullptr;
+    vd_hierarchy *H = new (std::nothrow) vd_hierarchy();
+    if (!H) return VD_ERR_OOM;
+    H->L.push_back(fine);
+    H->u_start.push_back(nullptr);
+    const Ctx &f = fine->c;
+    int dims[3] = {f.nx, f.ny, f.nz};
+    float h = f.h;
+    for (int l = 1; l < levels; l++) {
+        for (int a = 0; a < 3; a++) dims[a] = dims[a] / 2 + 1;
+        h *= 2.f;
+        vd_lattice_desc d{};
+        d.nx = dims[0];
+        d.ny = dims[1];
+        d.nz = dims[2];
+        d.origin[0] = f.ox;
+        d.origin[1] = f.oy;
+        d.origin[2] = f.oz;
+        d.spacing = h;
+        d.active_mode = fine->all ? VD_ACTIVE_ALL : VD_ACTIVE_SURFACE;
+        d.precision = fine->precision;
+        d.cuda_stream = fine->stream;
+        vd_lattice *Lc = nullptr;
+        vd_status s = vd_create_lattice(&d, &Lc);
+        if (s != VD_OK) {
+            vd_hierarchy_destroy(H);
+            return s;
+        }
+        Lc->apply_mode = VD_APPLY_AUTO;  // many samples per coarse cell: the cached blocks pay
+        Lc->c.dom_n[0] = f.nx;
+        Lc->c.dom_n[1] = f.ny;
+        Lc->c.dom_n[2] = f.nz;
+        Lc->c.dom_h = f.h;
+        H->L.push_back(Lc);
+        float *us = nullptr;
+        if (cudaMalloc(&us, sizeof(float) * 3 * (size_t)Lc->c.ld) != cudaSuccess) {
+            cudaGetLastError();
+            H->u_start.push_back(nullptr);
+            vd_hierarchy_destroy(H);
+            return VD_ERR_OOM;
+        }
+        H->u_start.push_back(us);
+    }
+    if (cudaMalloc(&H->scal, scal_bytes(1)) != cudaSuccess) {
+        cudaGetLastError();
+        H->scal = nullptr;
+        vd_hierarchy_destroy(H);
+        return VD_ERR_OOM;
+    }
+    *out = H;
+    return VD_OK;
+}
+
+vd_status vd_hierarchy_destroy(vd_hierarchy *H) {
+    if (!H) return VD_OK;
+    if (!H->L.empty() && H->L[0]->stream) cudaStreamSynchronize(H->L[0]->stream);
+    for (size_t l = 1; l < H->L.size(); l++) vd_destroy_lattice(H->L[l]);
+    for (float *p : H->u_start)
+        if (p) cudaFree(p);
+    if (H->scal) cudaFree(H->scal);
+    delete H;
+    return VD_OK;
+}
+
+vd_status vd_hierarchy_level(vd_hierarchy *H, int level, vd_lattice **out) {
+    if (!H || !out || level < 0 || level >= (int)H->L.size()) return VD_ERR_INVALID_ARG;
+    *out = H->L[level];
+    return VD_OK;
+}
+
+const char *vd_hierarchy_last_error(const vd_hierarchy *H) { return H ? H->err.c_str() : "null hierarchy"; }
+
+vd_status vd_hierarchy_solve_async(vd_hierarchy *H, const vd_solve_params *params) {
+    if (!H || !params) return VD_ERR_INVALID_ARG;
+    const int levels = (int)H->L.size();
+    vd_lattice *F = H->L[0];
+    for (int l = 0; l < levels; l++) {
+        vd_status s = check_params(F, &params[l]);
+        if (s != VD_OK) return hfail(H, s, "level schedule " + std::to_string(l) + ": " + F->err);
+    }
+    if (!F->have_frame) return hfail(H, VD_ERR_STATE, "the finest lattice has no frame");
+    vd_status s = hierarchy_sync(H);
+    if (s != VD_OK) return s;
+    cudaStream_t st = F->stream;
+    if (params[levels - 1].init == VD_INIT_ZERO)
+        k_reset_warp<<<blocks_for(F->c.nn), kThreads, 0, st>>>(F->u, F->R, F->c.nn, F->c.ld);
+    for (int l = 1; l < levels; l++) {
+        refresh_ctx(H->L[l]);
+        k_restrict_state<<<blocks_for(H->L[l]->c.nn), kThreads, 0, st>>>(H->L[l - 1]->c, H->L[l]->c, H->u_start[l]);
+    }
+    if (cudaGetLastError() != cudaSuccess) return hfail(H, VD_ERR_CUDA, "restriction launch failed");
+    for (int l = levels - 1; l >= 0; l--) {
+        vd_lattice *Ll = H->L[l];
+        vd_solve_params P = params[levels - 1 - l];
+        P.init = VD_INIT_PREV;
+        s = vd_solve_async(Ll, &P);
+        if (s != VD_OK) return hfail(H, s, "level " + std::to_string(l) + ": " + Ll->err);
+        if (l == 0) break;
+        vd_lattice *Lf = H->L[l - 1];
+        refresh_ctx(Lf);
+        k_prolongate<<<blocks_for(Lf->c.nn), kThreads, 0, st>>>(Ll->c, H->u_start[l], Lf->c);
+        cudaMemsetAsync(H->scal, 0, scal_bytes(1), st);
+        const Grid gr = grids(Lf);
+        if (Lf->all) k_fit_rotations<true, true><<<gr.node, kThreads, 0, st>>>(Lf->c, H->scal);
+        else k_fit_rotations<false, true><<<gr.node, kThreads, 0, st>>>(Lf->c, H->scal);
+        if (cudaGetLastError() != cudaSuccess) return hfail(H, VD_ERR_CUDA, "prolongation launch failed");
+    }
+    H->pending = true;
+    return VD_OK;
+}
+
+vd_status vd_hierarchy_get_reports(vd_hierarchy *H, vd_solve_report *out) {
+    if (!H) return VD_ERR_INVALID_ARG;
+    const int levels = (int)H->L.size();
+    vd_status worst = VD_OK;
+    for (int l = levels - 1; l >= 0; l--) {  // out[] coarsest first, like the schedule
+        vd_status s = vd_get_report(H->L[l], out ? out + (levels - 1 - l) : nullptr);
+        if (s != VD_OK && worst == VD_OK) worst = hfail(H, s, H->L[l]->err);
+    }
+    H->pending = false;
+    return worst;
+}
+
+vd_status vd_hierarchy_solve(vd_hierarchy *H, const vd_solve_params *params, vd_solve_report *out) {
+    vd_status s = vd_hierarchy_solve_async(H, params);
+    if (s != VD_OK) return s;
+    return vd_hierarchy_get_reports(H, out);
 }
 
 }  // extern "C"

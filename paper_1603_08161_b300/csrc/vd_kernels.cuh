@@ -61,6 +61,15 @@ struct Ctx {
     const int4 *cell_part;
     // samples whose FP32 association lies near a threshold, re-taken in FP64
     int *refine;
+    // coarse level of a hierarchy (Sec. 7.2): node counts and spacing of the finest
+    // lattice (same origin); a point belongs to this level only if its cell exists on
+    // the finest lattice.  dom_h = 0: no such restriction.
+    int dom_n[3];
+    float dom_h;
+    // cached B^T B of the dense samples (Sec. 7.1): per occupied cell a 24 x 24 block,
+    // row / column k * 3 + a (corner k, component a), built once per association;
+    // nullptr: the J^T J p of the samples is applied matrix-free
+    float *btb;
 };
 
 // Per-Gauss-Newton-iteration scalar block (FP64 sums and counters), zeroed at the
@@ -314,6 +323,13 @@ __global__ void k_point_cells(const float *__restrict__ pts, int n, Ctx c, int *
             f[a] = q - fl;
         }
         if (nrm && !(isfinite(nrm[3 * i]) && isfinite(nrm[3 * i + 1]) && isfinite(nrm[3 * i + 2]))) ok = false;
+        if (c.dom_h > 0.f) {  // gathered from the finest level: its cell must exist there
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const double fl = floor(__ddiv_rn(__dsub_rn((double)pts[3 * i + a], o[a]), (double)c.dom_h));
+                if (!(fl >= 0.0) || fl > (double)(c.dom_n[a] - 2)) ok = false;
+            }
+        }
         cell[i] = ok ? ci[0] + c.nx * (ci[1] + c.ny * ci[2]) : -1;
         frac[i] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.f);
     }
@@ -1065,6 +1081,129 @@ __device__ __forceinline__ void sparse_pairs(const Ctx &c, const VecView vec, fl
     }
 }
 
+// x += v for four consecutive floats (16-byte aligned) as one vector reduction in L2
+__device__ __forceinline__ void red_add_f4(float *x, float4 v) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(x), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+// ---- cached B^T B (Sec. 7.1: "pre-compute and cache B^T B before the PCG iteration
+// commences"), the dense samples' part of J^T J per occupied cell:
+//   B_cell[(k, a), (m, b)] = w_d sum_{samples j of the cell} alpha_k(j) g'_a(j) alpha_m(j) g'_b(j)
+// (v_j = alpha(j) (x) g'_j, a 24-vector; B_cell = w_d sum_j v_j v_j^T), stored as a full
+// row-major 24 x 24 block (576 floats).  The build is balanced by samples: each warp
+// takes 64 consecutive sorted samples, reads them 32 at a time (one coalesced load per
+// lane), broadcasts each sample's fractions and g' by shuffles, and lane l < 24 sums row
+// l of the partial block of every cell the 64 samples overlap (v_j[l] v_j[m] for every
+// m); each partial block is added to the (zeroed) block with vector reductions.
+constexpr int kBtb = 576;
+constexpr int kBtbChunk = 64;  // samples per warp of the build
+
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_btb_build(Ctx c, const Scal *sc) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->skip) return;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const int n_occ = *c.n_occ;
+    const int ns = n_occ > 0 ? c.occ_beg[n_occ] : 0;
+    const int k = lane / 3, a = lane - 3 * (lane / 3);
+    for (int j0 = warp * kBtbChunk; j0 < ns; j0 += nw * kBtbChunk) {
+        const int jend = min(j0 + kBtbChunk, ns);
+        int lo = 0, hi = n_occ;  // the cell holding sample j0: last cell starting at or before it
+        while (hi - lo > 1) {
+            const int m = (lo + hi) >> 1;
+            if (c.occ_beg[m] <= j0) lo = m;
+            else hi = m;
+        }
+        for (int ci = lo; ci < n_occ && c.occ_beg[ci] < jend; ci++) {
+            const int cb = max(c.occ_beg[ci], j0), ce = min(c.occ_beg[ci + 1], jend);
+            float acc[24];
+#pragma unroll
+            for (int m = 0; m < 24; m++) acc[m] = 0.f;
+            for (int jb = cb; jb < ce; jb += 32) {
+                float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f), g = f4;
+                if (jb + lane < ce) {
+                    f4 = c.frac[jb + lane];
+                    g = load_rec(c, jb + lane);
+                }
+                const int nj = min(32, ce - jb);
+#pragma unroll 2
+                for (int t = 0; t < nj; t++) {
+                    const float f[3] = {__shfl_sync(FULL, f4.x, t), __shfl_sync(FULL, f4.y, t),
+                                        __shfl_sync(FULL, f4.z, t)};
+                    const float gv[3] = {__shfl_sync(FULL, g.x, t), __shfl_sync(FULL, g.y, t), __shfl_sync(FULL, g.z, t)};
+                    const float vl = trilinear_weight(f, k) * (a == 0 ? gv[0] : (a == 1 ? gv[1] : gv[2]));
+#pragma unroll
+                    for (int kk = 0; kk < 8; kk++) {
+                        const float al = vl * trilinear_weight(f, kk);
+#pragma unroll
+                        for (int b = 0; b < 3; b++) acc[3 * kk + b] = fmaf(al, gv[b], acc[3 * kk + b]);
+                    }
+                }
+            }
+            if (lane < 24) {
+                float *row = c.btb + (size_t)ci * kBtb + lane * 24;
+#pragma unroll
+                for (int m4 = 0; m4 < 6; m4++)
+                    red_add_f4(row + 4 * m4, make_float4(c.w_d * acc[4 * m4], c.w_d * acc[4 * m4 + 1],
+                                                         c.w_d * acc[4 * m4 + 2], c.w_d * acc[4 * m4 + 3]));
+            }
+        }
+    }
+}
+
+// q += B_cell p_cell for occupied cell ci, one warp: lane l < 24 gathers p at corner l / 3,
+// component l % 3, forms row l of the product (p broadcast by shuffles) and adds it to
+// q there; part += p_cell . B_cell p_cell.  Every lane of the warp must call it.
+template <bool kAll, bool kFresh>
+__device__ __forceinline__ void btb_cell_apply(const Ctx &c, const VecView vec, int ci, float *dst, float &part) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < 24;
+    const int k = lane / 3, a = lane - 3 * (lane / 3);
+    int sl = 0;
+    float pl = 0.f;
+    if (act) {
+        sl = node_slot<kAll>(c, corner_node(c, c.occ_cell[ci], k));
+        pl = ldvv<kFresh>(vec, (size_t)a * c.ld + sl);
+    }
+    const float4 *B = reinterpret_cast<const float4 *>(c.btb + (size_t)ci * kBtb + (act ? lane : 0) * 24);
+    float q = 0.f;
+#pragma unroll
+    for (int m4 = 0; m4 < 6; m4++) {
+        const float4 b = act ? __ldg(B + m4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        q = fmaf(b.x, __shfl_sync(FULL, pl, 4 * m4), q);
+        q = fmaf(b.y, __shfl_sync(FULL, pl, 4 * m4 + 1), q);
+        q = fmaf(b.z, __shfl_sync(FULL, pl, 4 * m4 + 2), q);
+        q = fmaf(b.w, __shfl_sync(FULL, pl, 4 * m4 + 3), q);
+    }
+    if (act) {
+        part += pl * q;
+        if (q != 0.f) atomicAdd(&dst[(size_t)a * c.ld + sl], q);
+    }
+}
+
+// Streamed apply of the samples' part with the cached blocks (one warp per occupied
+// cell) plus the sparse pairs matrix-free, and the partial p.Ap.
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_cells_btb(Ctx c, Scal *sc, int K, int it) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->skip) return;
+    if (sc->stop || !(scal_rho(sc)[it] > 0.0)) return;
+    const VecView vec{c.p, nullptr, 0.f};
+    float part = 0.f;
+    double partd = 0.0;
+    const int n_occ = *c.n_occ;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int ci = warp; ci < n_occ; ci += nw) btb_cell_apply<kAll, false>(c, vec, ci, c.q, part);
+    sparse_pairs<kOpApply, kAll, false>(c, vec, c.q, nullptr, blockIdx.x + gridDim.x * threadIdx.x,
+                                        gridDim.x * blockDim.x, part, partd);
+    block_add_f64(part, scal_pq(sc, K) + it);
+}
+
 // Partition of the sorted samples among the nb blocks of the sample passes: block b
 // takes samples [b n / nb, (b + 1) n / nb) and the occupied cells that hold them.
 __global__ void k_cell_partition(const int *__restrict__ occ_beg, const int *__restrict__ n_occ_p, int nb,
@@ -1522,12 +1661,6 @@ __device__ __forceinline__ double block_total(float v, double *red) {
 
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
-// x += v for four consecutive floats (16-byte aligned) as one vector reduction in L2
-__device__ __forceinline__ void red_add_f4(float *x, float4 v) {
-    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(x), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w)
-                 : "memory");
-}
 
 template <bool kAll, bool kVec4>
 __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *sc, PcgAux ax, int K, double tol2,
@@ -1801,9 +1934,16 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             // ---- A: the samples' J^T J p into c.q (atomics), p formed from z and p_old
             const int lt = tid - kPcgStencil;
             const VecView pv{Zg, pold, beta};
-            if (s_ce > s_cb)
+            if (c.btb) {  // cached B^T B: an equal share of the occupied cells, a warp per cell
+                const int n_occ = *c.n_occ;
+                const int cb = (int)(((long long)n_occ * blockIdx.x) / G);
+                const int ce = (int)(((long long)n_occ * (blockIdx.x + 1)) / G);
+                for (int ci = cb + (lt >> 5); ci < ce; ci += kPcgSample >> 5)
+                    btb_cell_apply<kAll, true>(c, pv, ci, c.q, part);
+            } else if (s_ce > s_cb) {
                 cells_block<kOpApply, kAll, true>(c, pv, c.q, nullptr, s_cb, s_ce, tsm, part, lt, kPcgSample, 1, s_js,
                                                   s_je);
+            }
             double pd = 0.0;
             sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * lt, G * kPcgSample, part, pd);
         }
@@ -2221,6 +2361,69 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) 
     }
     block_add_f64(part, &sc->e_reg);
     block_add_int(degenerate, &sc->n_degenerate);
+}
+
+// ------------------------------------------------------------------ hierarchy (Sec. 7.2)
+
+// Start state of a coarse level c from the next finer level f: coarse node X takes u and
+// R of finer node 2X.  Along an axis where 2X is one past the finer lattice's last node
+// (n - 1 odd), u is extrapolated linearly from the last two finer nodes, 2 u(n-1) -
+// u(n-2) (per axis, so affine fields are reproduced), and R is the nearest finer node's.
+// u_start (3 planes of c.ld) keeps the start displacement for the prolongation.
+__global__ void k_restrict_state(Ctx f, Ctx c, float *__restrict__ u_start) {
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < c.nn; I += gridDim.x * blockDim.x) {
+        const int X = I % c.nx, t = I / c.nx, Y = t % c.ny, Z = t / c.ny;
+        const int xyz[3] = {X, Y, Z}, fd[3] = {f.nx, f.ny, f.nz};
+        int p0[3];
+        bool ext[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            ext[a] = 2 * xyz[a] >= fd[a];
+            p0[a] = ext[a] ? fd[a] - 1 : 2 * xyz[a];
+        }
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        for (int k = 0; k < 8; k++) {
+            const int kx = k & 1, ky = (k >> 1) & 1, kz = (k >> 2) & 1;
+            if ((kx && !ext[0]) || (ky && !ext[1]) || (kz && !ext[2])) continue;
+            const float w = (kx ? -1.f : (ext[0] ? 2.f : 1.f)) * (ky ? -1.f : (ext[1] ? 2.f : 1.f)) *
+                            (kz ? -1.f : (ext[2] ? 2.f : 1.f));
+            const int i = (p0[0] - kx) + f.nx * ((p0[1] - ky) + f.ny * (p0[2] - kz));
+            ax += w * f.u[i];
+            ay += w * f.u[f.ld + i];
+            az += w * f.u[2 * f.ld + i];
+        }
+        c.u[I] = u_start[I] = ax;
+        c.u[c.ld + I] = u_start[c.ld + I] = ay;
+        c.u[2 * c.ld + I] = u_start[2 * c.ld + I] = az;
+        const int i0 = p0[0] + f.nx * (p0[1] + f.ny * p0[2]);
+#pragma unroll
+        for (int e = 0; e < 9; e++) c.R[e * c.ld + I] = f.R[e * f.ld + i0];
+    }
+}
+
+// Jump start of the finer level f from the coarse solution: every finer node adds the
+// coarse displacement increment (u - u_start) interpolated trilinearly at its canonical
+// position, coarse coordinates (x/2, y/2, z/2) (weights 0, 1/2 or 1: exact in FP32).
+__global__ void k_prolongate(Ctx c, const float *__restrict__ u_start, Ctx f) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < f.nn; i += gridDim.x * blockDim.x) {
+        const int x = i % f.nx, t = i / f.nx, y = t % f.ny, z = t / f.ny;
+        const int X0 = min(x >> 1, c.nx - 2), Y0 = min(y >> 1, c.ny - 2), Z0 = min(z >> 1, c.nz - 2);
+        const float fr[3] = {0.5f * x - X0, 0.5f * y - Y0, 0.5f * z - Z0};
+        const int cell = X0 + c.nx * (Y0 + c.ny * Z0);
+        float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const float al = trilinear_weight(fr, k);
+            if (al == 0.f) continue;
+            const int nd = corner_node(c, cell, k);
+            ax += al * (c.u[nd] - u_start[nd]);
+            ay += al * (c.u[c.ld + nd] - u_start[c.ld + nd]);
+            az += al * (c.u[2 * c.ld + nd] - u_start[2 * c.ld + nd]);
+        }
+        f.u[i] += ax;
+        f.u[f.ld + i] += ay;
+        f.u[2 * f.ld + i] += az;
+    }
 }
 
 // ------------------------------------------------------------------ layout helpers

@@ -20,6 +20,7 @@ VD_ACTIVE_SURFACE, VD_ACTIVE_ALL = 0, 1
 VD_PREC_FP32, VD_PREC_MIXED = 0, 1
 VD_MEM_HOST, VD_MEM_DEVICE = 0, 1
 VD_INIT_PREV, VD_INIT_ZERO = 0, 1
+VD_APPLY_MATRIX_FREE, VD_APPLY_CACHED, VD_APPLY_AUTO = 0, 1, 2
 (VD_KC_ASSOCIATE, VD_KC_RHS, VD_KC_APPLY_STENCIL, VD_KC_APPLY_SAMPLES, VD_KC_UPDATE_X,
  VD_KC_UPDATE_P, VD_KC_ROTATION, VD_KC_ENERGY, VD_KC_PCG) = range(9)
 KERNEL_CLASSES = {"associate": 0, "rhs": 1, "apply_stencil": 2, "apply_samples": 3, "update_x": 4,
@@ -101,6 +102,16 @@ _SIGS = {
     "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
     "vd_batch_set_plan": [_P, _I, _I, ctypes.c_longlong],
     "vd_unet_get_tensor": [_P, _I, _P, ctypes.c_longlong, _PI],
+    "vd_set_apply_mode": [_P, _I],
+    "vd_get_apply_mode": [_P, _PI, _PI],
+    "vd_tune_apply": [_P, ctypes.POINTER(vd_solve_params), _PI, ctypes.POINTER(ctypes.c_float)],
+    "vd_hierarchy_create": [_P, _I, ctypes.POINTER(_P)],
+    "vd_hierarchy_destroy": [_P],
+    "vd_hierarchy_level": [_P, _I, ctypes.POINTER(_P)],
+    "vd_hierarchy_solve": [_P, _P, _P],
+    "vd_hierarchy_solve_async": [_P, _P],
+    "vd_hierarchy_get_reports": [_P, _P],
+    "vd_hierarchy_last_error": [_P],
     "vd_batch_create": [_P, _I, ctypes.POINTER(_P)],
     "vd_batch_destroy": [_P],
     "vd_batch_solve": [_P, ctypes.POINTER(vd_solve_params), _P],
@@ -132,7 +143,8 @@ VD_NOALLOC_MAX_NODES = 65536
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
-    _fn.restype = ctypes.c_char_p if _name in ("vd_last_error", "vd_batch_last_error") else ctypes.c_int
+    _fn.restype = (ctypes.c_char_p if _name in ("vd_last_error", "vd_batch_last_error", "vd_hierarchy_last_error")
+                   else ctypes.c_int)
     globals()[_name] = _fn
 
 
@@ -272,6 +284,20 @@ class Lattice:
         pu, _ = _ptr(uu)
         pr, _ = _ptr(RR)
         self._check(vd_set_warp(self.h, pu, pr, VD_MEM_DEVICE if dev else VD_MEM_HOST))
+
+    def set_apply_mode(self, mode):
+        self._check(vd_set_apply_mode(self.h, int(mode)))
+
+    def apply_mode(self):
+        m, now = ctypes.c_int(), ctypes.c_int()
+        self._check(vd_get_apply_mode(self.h, ctypes.byref(m), ctypes.byref(now)))
+        return m.value, bool(now.value)
+
+    def tune_apply(self, prm):
+        m = ctypes.c_int()
+        ms = (ctypes.c_float * 2)()
+        self._check(vd_tune_apply(self.h, ctypes.byref(prm), ctypes.byref(m), ms))
+        return m.value, (ms[0], ms[1])
 
     def test_stall_barrier(self, on):
         """Failure injection: make the position step's first grid-barrier wait run out."""
@@ -427,6 +453,82 @@ class Batch:
 
     def set_plan(self, streams, largest_first=True, run_ahead_nodes=(1 << 31) - 1):
         self._check(vd_batch_set_plan(self.h, int(streams), int(bool(largest_first)), int(run_ahead_nodes)))
+
+
+class _LevelView(Lattice):
+    """A level of a hierarchy: a lattice handle owned by the hierarchy (not destroyed here)."""
+
+    def __init__(self, handle, dims, fine):
+        self.h = handle
+        self.dims = tuple(dims)
+        self.nn = int(np.prod(self.dims))
+        self._fine = fine
+        self._keep = []
+
+    # the level's frame is level 0's (same samples, same depth map)
+    C = property(lambda self: self._fine.C)
+    W = property(lambda self: self._fine.W)
+    H = property(lambda self: self._fine.H)
+
+    def close(self):
+        self.h = None
+
+
+class Hierarchy:
+    """Coarse-to-fine solve (vd_hierarchy_*) on a Lattice (level 0)."""
+
+    def __init__(self, fine, levels):
+        self.fine = fine
+        h = _P()
+        st = vd_hierarchy_create(fine.h, int(levels), ctypes.byref(h))
+        if st != VD_OK:
+            raise VDError(st, "vd_hierarchy_create failed")
+        self.h = h
+        self.n_levels = int(levels)
+        self.levels = [fine]
+        dims = fine.dims
+        for l in range(1, levels):
+            dims = tuple(d // 2 + 1 for d in dims)
+            lh = _P()
+            vd_hierarchy_level(self.h, l, ctypes.byref(lh))
+            self.levels.append(_LevelView(lh, dims, fine))
+
+    def _check(self, st):
+        if st != VD_OK:
+            raise VDError(st, (vd_hierarchy_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            vd_hierarchy_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _params(self, schedule):
+        assert len(schedule) == self.n_levels
+        return (vd_solve_params * self.n_levels)(*schedule)
+
+    def solve(self, schedule):
+        """schedule: vd_solve_params per level, coarsest first; returns the reports."""
+        self._prm = self._params(schedule)
+        reps = (vd_solve_report * self.n_levels)()
+        st = vd_hierarchy_solve(self.h, self._prm, reps)
+        if st not in (VD_OK, VD_ERR_NUMERIC):
+            self._check(st)
+        return [r.as_dict() for r in reps]
+
+    def solve_async(self, schedule):
+        self._prm = self._params(schedule)
+        self._check(vd_hierarchy_solve_async(self.h, self._prm))
+
+    def reports(self):
+        reps = (vd_solve_report * self.n_levels)()
+        vd_hierarchy_get_reports(self.h, reps)
+        return [r.as_dict() for r in reps]
 
 
 class UNet:

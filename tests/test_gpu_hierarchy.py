@@ -1,0 +1,118 @@
+"""Coarse-to-fine solve (vd_hierarchy_*, Sec. 7.2) through the C ABI against the FP64
+oracle's hierarchy (oracle.Hierarchy) on the same seeded frames.
+
+Every level is compared: its association (target pixels, bit-exact), its warp after the
+whole solve (a coarse level keeps its own solution: within 1e-4 of its spacing) and its
+reported energy (1e-5 relative), the same tolerances as the single-level solves, in the
+fixed-association parity mode.  With re-association at every iteration the decisions
+are taken (in FP64 on both sides) on the FP32 and FP64 iterates, which differ by the
+FP32 rounding of the solve; a finer level starts from the prolongated coarse solution
+and so inherits the coarse level's rounding as well (a few 1e-7 m at 96^3), and the
+samples lying that close to a pixel boundary may go either way: there the count of
+differing target pixels per level is printed and bounded (1 in 1000 samples), and the
+energy must agree to 1e-3 (each flipped correspondence moves E by its own weighted
+residual; at 96^3 a few dozen of them move it by about 2e-4).  The frames carry samples beyond the finest lattice (inside
+the coarse ones), which the coarse levels must leave out as the finest does."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_08161_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1603_08161_b300 import vd as mod
+    return mod
+
+
+def _with_outside_samples(fr, k=40):
+    extra = fr.src_pts[:k].copy()
+    extra[:, 2] = fr.origin[2] + fr.spacing * (fr.dims[2] - 1) + 0.5 * fr.spacing  # past the last fine node
+    return dataclasses.replace(fr, src_pts=np.concatenate([fr.src_pts, extra]),
+                               src_nrm=np.concatenate([fr.src_nrm, fr.src_nrm[:k]]))
+
+
+def _compare(vd, fr, mode, levels, schedule, fixed):
+    om = oracle.ACTIVE_ALL if mode == "all" else oracle.ACTIVE_SURFACE
+    ref = oracle.Hierarchy(fr, levels, om)
+    res = ref.solve(schedule, fixed_association=fixed)
+    lat = vd.Lattice(fr.dims, fr.origin, fr.spacing, vd.VD_ACTIVE_ALL if mode == "all" else vd.VD_ACTIVE_SURFACE)
+    lat.set_frame_from(fr)
+    H = vd.Hierarchy(lat, levels)
+    prms = [vd.params(gn_iters=g, cg_iters=c, fixed_association=fixed, init=vd.VD_INIT_ZERO) for g, c in schedule]
+    reps = H.solve(prms)
+    out = []
+    for k in range(levels):                      # k-th entry: level levels - 1 - k
+        l = levels - 1 - k
+        g, o = H.levels[l], ref.levels[l]
+        h = float(np.float32(fr.spacing * 2 ** l))
+        pix, _, _ = g.association(prms[k])
+        pix0, _, _ = o.association()
+        u, _ = g.get_warp()
+        u0, _ = o.get_warp()
+        err = float(np.abs(u - u0).max())
+        e0 = res[k]["energy"][-1, 0]
+        rel = abs(reps[k]["e_total"] - e0) / e0
+        out.append((l, g.dims, int((pix != pix0).sum()), err / h, rel))
+        print(f"level {l} {g.dims}: {out[-1][2]} target pixels differ, |du|max {err / h:.2e} h, dE/E {rel:.2e}")
+        assert reps[k]["status"] == vd.VD_OK and reps[k]["gn_done"] == schedule[k][0]
+    for (l, _, nd, e, r), k in zip(out, range(levels)):
+        if fixed or nd == 0:
+            assert nd == 0, f"level {l}: {nd} target pixels differ"
+            assert e <= 1e-4, f"level {l}: |du|max = {e:.2e} h"
+            assert r <= 1e-5, f"level {l}: dE/E = {r:.2e}"
+            assert reps[k]["n_valid_corr"] == res[k]["n_valid"]
+        else:
+            assert nd <= max(2, fr.C // 1000), f"level {l}: {nd} target pixels differ"
+            assert r <= 1e-3, f"level {l}: dE/E = {r:.2e}"
+    return out
+
+
+@pytest.mark.parametrize("mode", ["all", "surface"])
+@pytest.mark.parametrize("fixed", [True, False])
+def test_hierarchy_matches_oracle_config1(vd, mode, fixed):
+    fr = _with_outside_samples(synth.config1())
+    rows = _compare(vd, fr, mode, 3, [(3, 10), (3, 10), (3, 10)], fixed)
+    for r in rows:
+        print(f"hierarchy {mode} fixed={fixed}: level {r[0]} {r[1]}: {r[2]} pixels differ, "
+              f"|du|max {r[3]:.2e} h, dE/E {r[4]:.2e}")
+
+
+def test_hierarchy_ragged_lattice(vd):
+    """Odd and even node counts per axis (13 x 11 x 9 -> 7 x 6 x 5), two levels."""
+    fr = synth.sphere_frame(W=53, H=37, f=50.0, n=(13, 11, 9), seed=3, n_sparse=7, name="ragged")
+    _compare(vd, fr, "all", 2, [(3, 10), (2, 10)], True)
+
+
+def test_hierarchy_single_level_is_the_plain_solve(vd):
+    fr = synth.config1()
+    lat = vd.Lattice(fr.dims, fr.origin, fr.spacing)
+    lat.set_frame_from(fr)
+    prm = vd.params(gn_iters=3, cg_iters=10, fixed_association=True, init=vd.VD_INIT_ZERO)
+    rep = vd.Hierarchy(lat, 1).solve([prm])[0]
+    u, _ = lat.get_warp()
+    plain = vd.Lattice(fr.dims, fr.origin, fr.spacing)
+    plain.set_frame_from(fr)
+    r0 = plain.solve(prm)
+    u0, _ = plain.get_warp()
+    # the same kernels on the same input (FP32 atomics may order sums differently)
+    assert np.abs(u - u0).max() <= 1e-5 * fr.spacing
+    assert abs(rep["e_total"] - r0["e_total"]) <= 1e-6 * r0["e_total"]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("fixed", [True, False])
+def test_hierarchy_matches_oracle_config2(vd, cfg2, fixed):
+    """96^3 -> 49^3 -> 25^3, 4 x 20 per level."""
+    rows = _compare(vd, cfg2, "all", 3, [(4, 20), (4, 20), (4, 20)], fixed)
+    for r in rows:
+        print(f"hierarchy config 2 fixed={fixed}: level {r[0]} {r[1]}: {r[2]} pixels differ, "
+              f"|du|max {r[3]:.2e} h, dE/E {r[4]:.2e}")
