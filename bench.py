@@ -247,6 +247,7 @@ def main():
     ap.add_argument("--learned-seqs", type=int, default=2,
                     help="test sequences (seeds 10001..) for the learned warm-start form (0: skip)")
     ap.add_argument("--learned-frames", type=int, default=9)
+    ap.add_argument("--hier-levels", type=int, default=3, help="deepest hierarchy tried (1: skip the variant)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -345,6 +346,86 @@ def main():
             variants[name] = {"value": world * 1000.0 / mv, "unit": "frames/s", "ms_per_step": mv,
                               "active_nodes": Lv.num_active(), "final_energy": rv["e_total"]}
             Lv.close()
+
+    # hierarchical coarse-to-fine form (Sec. 7.2) of the same frame: the coarse levels,
+    # then the 96^3 level until E <= E_plain (1 + 1e-5), E_plain the plain 10 x 20
+    # solve's final energy; a few schedules are timed once outside the timed region and
+    # the fastest one that reaches the tolerance is timed like the plain solve
+    if not args.no_variants and args.hier_levels > 1:
+        target = rep["e_total"] * (1.0 + 1e-5)
+        Lh = vd.Lattice(fr.dims, fr.origin, fr.spacing, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
+        Lh.set_energy_target(target)
+        cands = [(lv, g, c) for lv in range(2, args.hier_levels + 1) for g in (2, 3) for c in (20, 40)]
+        best = None
+        for lv, g, c in cands:
+            Hh = vd.Hierarchy(Lh, lv)
+            sched = [vd.params(gn_iters=g, cg_iters=c, fixed_association=False)] * (lv - 1) + \
+                    [vd.params(gn_iters=GN, cg_iters=CG, fixed_association=False, init=vd.VD_INIT_ZERO)]
+
+            def hstep(Hh=Hh, sched=sched):
+                Lh.set_correspondences(d_fh, d_ft)
+                Lh.set_frame(d_depth, fr.K, fr.pose, d_pts, d_nrm)
+                Hh.solve_async(sched)
+
+            class _HR:
+                def report(self, Hh=Hh):
+                    return Hh.reports()
+            for _ in range(2):
+                hstep()
+                reps_h = Hh.reports()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(3):
+                hstep()
+            ev1.record(stream)
+            reps_h = Hh.reports()
+            ms3 = ev0.elapsed_time(ev1) / 3
+            ok = reps_h[-1]["e_total"] <= target
+            if ok and (best is None or ms3 < best[0]):
+                if best is not None:
+                    best[1].close()
+                best = (ms3, Hh, hstep, _HR(), (lv, g, c))
+            else:
+                Hh.close()
+        if best is not None:
+            _, Hh, hstep, hrep, (lv, g, c) = best
+            msh, _ = timed_pass(hstep, hrep)
+            reps_h = Hh.reports()
+            mh = dist_max(statistics.mean(msh), world)
+            dims_l = [tuple(fr.dims)]
+            for _ in range(1, lv):
+                dims_l.append(tuple(d // 2 + 1 for d in dims_l[-1]))
+            variants["hierarchical"] = {
+                "value": world * 1000.0 / mh, "unit": "frames/s", "ms_per_step": mh,
+                "levels": [f"{d[0]}^3" for d in dims_l[::-1]],
+                "schedule": f"{g} GN x {c} PCG on each coarse level, then the 96^3 level until the tolerance",
+                "gn_fine": reps_h[-1]["gn_done"], "final_energy": reps_h[-1]["e_total"],
+                "energy_per_level": [r["e_total"] for r in reps_h],
+                "plain_same_tolerance": value, "speedup_vs_plain": value and (world * 1000.0 / mh) / value,
+                "tolerance": "E <= E_plain (1 + 1e-5), E_plain = the plain 10 x 20 solve's final energy",
+                "candidates": len(cands)}
+            Hh.close()
+        else:
+            variants["hierarchical"] = {"unavailable": "no candidate schedule reached the plain solve's energy"}
+        Lh.close()
+
+    # cached B^T B apply (Sec. 7.1) against the matrix-free one on the coarse levels of
+    # the hierarchy (the same frame on 25^3 and 49^3 lattices over the same cube) and on
+    # the 96^3 lattice: the solve time of each (10 x 20), as vd_tune_apply measures it
+    if not args.no_variants:
+        rows = {}
+        for n in (25, 49, 96):
+            dims_n, origin_n, h_n = synth.lattice_for(n)
+            Lb = vd.Lattice(dims_n, origin_n, h_n, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
+            Lb.set_correspondences(d_fh, d_ft)
+            Lb.set_frame(d_depth, fr.K, fr.pose, d_pts, d_nrm)
+            mode, (ms_mf, ms_c) = Lb.tune_apply(vd.params(gn_iters=GN, cg_iters=CG, fixed_association=False,
+                                                          init=vd.VD_INIT_ZERO))
+            rows[f"{n}^3"] = {"matrix_free_ms": ms_mf, "cached_ms": ms_c,
+                              "chosen": "cached" if mode == vd.VD_APPLY_CACHED else "matrix-free"}
+            Lb.close()
+        variants["cached_btb"] = {"unit": "ms per 10 x 20 solve", "per_lattice": rows,
+                                  "note": "same frame (36,266 samples) binned on each lattice"}
 
     # batched form (32 independent lattices of uneven size, 16^3..96^3, their own
     # 160x120..640x480 frames): one tuned graph launch per batch, against the same
