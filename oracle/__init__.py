@@ -13,6 +13,10 @@ Parity status of each part (what pins it is in tests/test_oracle_pins.py):
   * Jacobian .............................. pinned (central finite differences of E)
   * PCG position step ...................... pinned (dense Cholesky, closed forms)
   * rotation step .......................... pinned (brute-force search over SO(3))
+  * global pose by dense projective ICP (Sec. 6) pinned (gradient of the point-to-plane
+                                             energy by central differences; exact recovery of
+                                             a rigid motion of a three-plane corner; fixed
+                                             point at the true pose)
   * hierarchy (Sec. 7.2): restriction of the constraints, injection of the state and
     trilinear prolongation ................. pinned (affine fields reproduced exactly;
                                              data energies of a coarse-trilinear warp equal
@@ -87,6 +91,10 @@ def _load():
         "vdo_set_domain": (None, [P, i, i, i, ctypes.c_float]),
         "vdo_restrict_state": (None, [P, P]),
         "vdo_prolongate": (None, [P, D, P]),
+        "vdo_set_pose": (None, [P, D]),
+        "vdo_get_pose": (None, [P, D]),
+        "vdo_icp_system": (i, [P, D, D, D]),
+        "vdo_icp": (i, [P, i, D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -265,6 +273,29 @@ class Oracle:
 
     def fit_rotations(self):
         return _load().vdo_fit_rotations(self._c)
+
+    def set_pose(self, pose):
+        p = np.ascontiguousarray(pose, np.float64).reshape(12)
+        _load().vdo_set_pose(self._c, _ptr(p, ctypes.c_double))
+
+    def get_pose(self):
+        p = np.zeros(12)
+        _load().vdo_get_pose(self._c, _ptr(p, ctypes.c_double))
+        return p
+
+    def icp_system(self):
+        """(A 6x6, b 6, E, samples used) of the pose's normal equations at the current
+        pose and association (Sec. 6, dense projective ICP)."""
+        A, b, E = np.zeros(36), np.zeros(6), np.zeros(1)
+        n = _load().vdo_icp_system(self._c, _ptr(A, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                   _ptr(E, ctypes.c_double))
+        return A.reshape(6, 6), b, float(E[0]), n
+
+    def icp(self, iters):
+        """Dense projective ICP on the global pose; returns (steps, E before each)."""
+        e = np.zeros(max(iters, 1))
+        it = _load().vdo_icp(self._c, iters, _ptr(e, ctypes.c_double))
+        return it, e[:it]
 
     def solve(self, gn_iters, cg_iters, cg_tol=0.0, fixed_association=False, cholesky=False):
         e = np.zeros(gn_iters * 4)

@@ -1065,3 +1065,112 @@ void vdo_prolongate(const vdo_ctx *coarse, const double *u_start, vdo_ctx *fine)
     }
     fine->have_J = 0;
 }
+
+/* ------------------------------------------------------------------ global rigid pose (Sec. 6) */
+
+void vdo_set_pose(vdo_ctx *c, const double *pose)
+{
+    for (int a = 0; a < 9; a++) c->Rg[a] = pose[a];
+    for (int a = 0; a < 3; a++) c->tg[a] = pose[9 + a];
+    c->have_J = 0;
+}
+
+void vdo_get_pose(const vdo_ctx *c, double *pose)
+{
+    for (int a = 0; a < 9; a++) pose[a] = c->Rg[a];
+    for (int a = 0; a < 3; a++) pose[9 + a] = c->tg[a];
+}
+
+/* Normal equations of dense projective ICP for the global pose at the current pose and
+ * association: over the samples with w_c > 0, with q = sum_k alpha_k t_k (the lattice
+ * warp of the sample, before the pose), p = R_g q + t_g, residual r = n^a . (p - p^a)
+ * and its derivative J = ((R_g q) x n^a, n^a) for the pose perturbed as
+ * R_g <- exp([omega]x) R_g, t_g <- t_g + tau:
+ *   A = sum w_c J J^T (6 x 6, row-major), b = sum w_c J r, E = sum w_c r^2.
+ * Returns the number of samples used. */
+int vdo_icp_system(const vdo_ctx *c, double A[36], double b[6], double *E)
+{
+    int n = 0;
+    memset(A, 0, 36 * sizeof(double));
+    memset(b, 0, 6 * sizeof(double));
+    *E = 0.0;
+    int nd[8];
+    double al[8];
+    for (int s = 0; s < c->C; s++) {
+        if (!(c->wc[s] > 0)) continue;
+        double q[3] = {0, 0, 0}, tk[3], Rq[3];
+        corners(c, c->cell_c[s], c->frac_c + 3 * s, nd, al);
+        for (int k = 0; k < 8; k++) {
+            node_pos(c, nd[k], tk);
+            for (int a = 0; a < 3; a++) q[a] += al[k] * (tk[a] + c->u[3 * nd[k] + a]);
+        }
+        matvec3(c->Rg, q, Rq);
+        const double *pa = c->pa + 3 * s, *na = c->na + 3 * s;
+        double d[3] = {Rq[0] + c->tg[0] - pa[0], Rq[1] + c->tg[1] - pa[1], Rq[2] + c->tg[2] - pa[2]};
+        double r = dot3(na, d), J[6];
+        cross3(Rq, na, J);
+        for (int a = 0; a < 3; a++) J[3 + a] = na[a];
+        for (int i = 0; i < 6; i++) {
+            b[i] += c->wc[s] * J[i] * r;
+            for (int j = 0; j < 6; j++) A[6 * i + j] += c->wc[s] * J[i] * J[j];
+        }
+        *E += c->wc[s] * r * r;
+        n++;
+    }
+    return n;
+}
+
+/* Dense projective ICP (Sec. 6): `iters` Gauss-Newton steps on the pose, each after a
+ * projective association at the current pose (Sec. 5.1); the step solves A xi = -b by
+ * Cholesky and applies R_g <- exp([omega]x) R_g (Rodrigues), t_g <- t_g + tau.  Stops
+ * early when A is not positive definite.  Returns the steps taken; e_hist (iters
+ * entries, may be NULL) gets E before each step. */
+int vdo_icp(vdo_ctx *c, int iters, double *e_hist)
+{
+    int it = 0;
+    for (; it < iters; it++) {
+        vdo_associate(c);
+        double A[36], b[6], E;
+        vdo_icp_system(c, A, b, &E);
+        if (e_hist) e_hist[it] = E;
+        double L[36] = {0}, y[6], xi[6];
+        int bad = 0;
+        for (int j = 0; j < 6 && !bad; j++) {
+            double sj = A[6 * j + j];
+            for (int k = 0; k < j; k++) sj -= L[6 * j + k] * L[6 * j + k];
+            if (!(sj > 0)) { bad = 1; break; }
+            L[6 * j + j] = sqrt(sj);
+            for (int i = j + 1; i < 6; i++) {
+                double t = A[6 * i + j];
+                for (int k = 0; k < j; k++) t -= L[6 * i + k] * L[6 * j + k];
+                L[6 * i + j] = t / L[6 * j + j];
+            }
+        }
+        if (bad) break;
+        for (int i = 0; i < 6; i++) {               /* L y = -b */
+            double t = -b[i];
+            for (int k = 0; k < i; k++) t -= L[6 * i + k] * y[k];
+            y[i] = t / L[6 * i + i];
+        }
+        for (int i = 5; i >= 0; i--) {              /* L^T xi = y */
+            double t = y[i];
+            for (int k = i + 1; k < 6; k++) t -= L[6 * k + i] * xi[k];
+            xi[i] = t / L[6 * i + i];
+        }
+        double th = sqrt(dot3(xi, xi)), E3[9], Rn[9];
+        double K[9] = {0, -xi[2], xi[1], xi[2], 0, -xi[0], -xi[1], xi[0], 0};
+        double s1 = th > 0 ? sin(th) / th : 1.0, s2 = th > 0 ? (1.0 - cos(th)) / (th * th) : 0.5;
+        for (int r = 0; r < 3; r++)
+            for (int q = 0; q < 3; q++) {
+                double KK = K[3 * r] * K[q] + K[3 * r + 1] * K[3 + q] + K[3 * r + 2] * K[6 + q];
+                E3[3 * r + q] = (r == q ? 1.0 : 0.0) + s1 * K[3 * r + q] + s2 * KK;
+            }
+        for (int r = 0; r < 3; r++)
+            for (int q = 0; q < 3; q++)
+                Rn[3 * r + q] = E3[3 * r] * c->Rg[q] + E3[3 * r + 1] * c->Rg[3 + q] + E3[3 * r + 2] * c->Rg[6 + q];
+        memcpy(c->Rg, Rn, sizeof(Rn));
+        for (int a = 0; a < 3; a++) c->tg[a] += xi[3 + a];
+        c->have_J = 0;
+    }
+    return it;
+}

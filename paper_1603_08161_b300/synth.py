@@ -26,7 +26,7 @@ import math
 import numpy as np
 
 __all__ = ["Frame", "sphere_frame", "capsule_frame", "config1", "config2",
-           "batch_frames", "sequence_frames", "sequences", "lattice_for", "plane_frame"]
+           "batch_frames", "sequence_frames", "sequences", "lattice_for", "plane_frame", "corner_frame"]
 
 
 @dataclasses.dataclass
@@ -427,6 +427,66 @@ def plane_frame(W=32, H=24, f=30.0, n=8, depth=1.0, tilt_deg=0.0, shift=(0.0, 0.
                  src.astype(np.float32), np.tile(nrm, (src.shape[0], 1)).astype(np.float32),
                  np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
                  dims, origin, h, name)
+
+
+def corner_frame(W=64, H=48, f=60.0, n=16, rot=None, shift=(0.0, 0.0, 0.0), vertex=(0.02, -0.03, 0.7),
+                 step=2, margin=4, name="corner"):
+    """A cube corner pointing at the camera -- the three faces around the vertex, whose
+    outward normals each make the same angle (arccos 1/sqrt 3) with the view axis --
+    moved by the rigid motion (rot, shift): x -> rot x + shift.  Source = the unmoved
+    corner rendered by the same camera (every ``step``-th pixel), with the faces'
+    normals, kept only at pixels at least ``margin`` pixels from a face edge or the
+    silhouette (so that, for motions of a pixel or two, a sample's target pixel and its
+    central-difference neighbours lie on its own face).  Point-to-plane residuals then
+    vanish exactly at the true pose, and three independent planes fix all six pose
+    parameters."""
+    K = _intrinsics(W, H, f)
+    dirs = _rays(W, H, K)
+    Q = np.eye(3) if rot is None else np.asarray(rot, np.float64)
+    c = np.asarray(shift, np.float64)
+    # orthonormal outward normals with n_k . (0, 0, -1) = 1 / sqrt(3): the coordinate
+    # axes turned so that (1, 1, 1) / sqrt(3) points at the camera
+    a = np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0)
+    b = np.array([0.0, 0.0, -1.0])
+    v = np.cross(a, b)
+    Kx = np.array([[0, -v[2], v[1]], [v[2], 0, -v[0]], [-v[1], v[0], 0]])
+    Ralign = np.eye(3) + Kx + Kx @ Kx / (1.0 + a @ b)
+    nrm0 = (Ralign @ np.eye(3)).T                  # rows: the three outward normals
+    C0 = np.asarray(vertex, np.float64)
+
+    def render(Q, c):
+        n_k = nrm0 @ Q.T                           # moved planes n_k . x = n_k . (Q C0 + c)
+        d_k = n_k @ (Q @ C0 + c)
+        den = dirs @ n_k.T
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.where(den < 0, d_k[None, :] / den, -np.inf)
+        k = np.argmax(t, axis=1)                   # the ray enters the corner's solid last
+        tt = t[np.arange(len(k)), k]
+        p = tt[:, None] * dirs
+        inside = np.all(p @ n_k.T <= d_k[None, :] + 1e-12, axis=1)
+        ok = np.isfinite(tt) & (tt > 0) & inside
+        return np.where(ok, tt, 0.0), k, n_k, ok
+
+    t1, _, _, _ = render(Q, c)
+    dep = (t1 * dirs[:, 2]).reshape(H, W)
+    t0, k0, n0, ok0 = render(np.eye(3), np.zeros(3))
+    pts = t0[:, None] * dirs
+    face = np.where(ok0, k0, -1).reshape(H, W)
+    same = np.ones((H, W), bool)
+    for dy in range(-margin, margin + 1):
+        for dx in range(-margin, margin + 1):
+            sh = np.full((H, W), -2)
+            ys, xs = slice(max(dy, 0), H + min(dy, 0)), slice(max(dx, 0), W + min(dx, 0))
+            yd, xd = slice(max(-dy, 0), H + min(-dy, 0)), slice(max(-dx, 0), W + min(-dx, 0))
+            sh[yd, xd] = face[ys, xs]
+            same &= sh == face
+    sel = np.zeros(H * W, bool)
+    sel.reshape(H, W)[::step, ::step] = True
+    sel &= ok0 & same.ravel()
+    dims, origin, h = lattice_for(n)
+    return Frame(dep.astype(np.float32), K.astype(np.float32), _identity_pose(),
+                 pts[sel].astype(np.float32), n0[k0[sel]].astype(np.float32),
+                 np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), dims, origin, h, name)
 
 
 def config1(seed=0):

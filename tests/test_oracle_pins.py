@@ -753,3 +753,67 @@ def test_coarse_start_resolves_the_low_frequencies():
     H = oracle.Hierarchy(fr, 3)
     e3 = H.solve([(2, 10), (2, 10), (2, 10)])[-1]["energy"][-1, 0]
     assert e3 < 0.1 * e1
+
+
+# ---------------------------------------------------------------- global pose (Sec. 6)
+
+def _pose(Q, c):
+    return np.concatenate([np.asarray(Q, np.float64).ravel(), np.asarray(c, np.float64)])
+
+
+def test_icp_gradient_matches_finite_differences():
+    """b of the pose's normal equations is half the gradient of the point-to-plane energy
+    over the pose perturbation xi = (omega, tau) (R <- exp([omega]x) R, t <- t + tau),
+    checked by central differences with the association held fixed."""
+    rng = np.random.default_rng(21)
+    Q0 = _rand_rot(rng, 0.03)
+    fr = synth.corner_frame(rot=_rand_rot(rng, 0.05), shift=(0.01, -0.008, 0.012))
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    o.set_warp(rng.normal(0, 0.002, (o.nn, 3)))
+    P0 = _pose(Q0, rng.normal(0, 0.005, 3))
+    o.set_pose(P0)
+    o.associate()
+    A, b, E0, n = o.icp_system()
+    assert n > 50 and E0 > 0
+    eps = 1e-6
+    g = np.zeros(6)
+    for i in range(6):
+        xi = np.zeros(6)
+        for sgn in (1, -1):
+            xi[:] = 0
+            xi[i] = sgn * eps
+            w = xi[:3]
+            th = np.linalg.norm(w)
+            Kx = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+            Rw = np.eye(3) + (np.sin(th) / th if th else 1.0) * Kx + ((1 - np.cos(th)) / th ** 2 if th else 0.5) * Kx @ Kx
+            o.set_pose(_pose(Rw @ P0[:9].reshape(3, 3), P0[9:] + xi[3:]))
+            g[i] += sgn * o.icp_system()[2] / (2 * eps)
+    assert np.abs(g - 2 * b).max() <= 1e-6 * np.abs(2 * b).max()
+    assert np.allclose(A, A.T) and np.all(np.linalg.eigvalsh(A) > 0)
+
+
+def test_icp_recovers_a_rigid_motion():
+    """The observed corner is the canonical one moved by (Q, c): from the identity pose,
+    dense projective ICP converges to (Q, c), where every residual vanishes -- up to the
+    float32 rounding of the depth map and the samples (about 1e-8 here)."""
+    rng = np.random.default_rng(22)
+    Q = _rand_rot(rng, 0.012)
+    c = np.array([0.004, -0.003, 0.005])
+    fr = synth.corner_frame(rot=Q, shift=c)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    it, e = o.icp(8)
+    P = o.get_pose()
+    assert it == 8 and e[0] > 1e-3 and e[-1] < 1e-12
+    assert np.abs(P[:9].reshape(3, 3) - Q).max() < 1e-7
+    assert np.abs(P[9:] - c).max() < 1e-7
+
+
+def test_icp_keeps_the_true_pose():
+    """At the true pose the energy is zero (to the float32 rounding of the inputs) and
+    a step leaves the pose where it is."""
+    fr = synth.corner_frame()
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    it, e = o.icp(2)
+    P = o.get_pose()
+    assert e[0] < 1e-13
+    assert np.abs(P - _pose(np.eye(3), np.zeros(3))).max() < 1e-7
