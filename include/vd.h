@@ -175,6 +175,24 @@ vd_status vd_step_fit_rotations(vd_lattice *lat, int *n_degenerate);
  * association. */
 vd_status vd_step_energy(vd_lattice *lat, const vd_solve_params *params, double out[4]);
 
+/* ---- global rigid pose (Sec. 6: "dense projective ICP") ----
+ *
+ * Estimates the frame's global pose (R_g, t_g) with the lattice warp held fixed:
+ * `iters` Gauss-Newton steps of the point-to-plane energy of the dense samples,
+ *     sum_c w_c (n^a_c . (R_g q_c + t_g - p^a_c))^2,   q_c = p^_c + sum_k alpha_k u_k,
+ * each after a projective association at the current pose (Sec. 5.1: nearest pixel,
+ * Phi_d, Phi_n, Phi_v and w_c, with the thresholds of `params`), over the perturbation
+ * R_g <- exp([omega]x) R_g, t_g <- t_g + tau (6 x 6 normal equations, Cholesky in FP64,
+ * the pose kept in FP64 between steps).  Starts from the pose of the last vd_set_frame;
+ * the result becomes the frame's pose for the following solves and is written to
+ * pose_out (12 floats, row-major R_g then t_g, host; may be NULL).  steps (may be NULL)
+ * gets the steps taken: fewer than iters when the normal matrix stopped being positive
+ * definite (too few correspondences), the pose then being the last one reached.
+ * e_hist (host, iters doubles, may be NULL) gets the energy before each step.  Runs on
+ * the lattice's stream and waits for it.  iters in [0, 64]. */
+vd_status vd_estimate_pose(vd_lattice *lat, const vd_solve_params *params, int iters, float pose_out[12],
+                           int *steps, double *e_hist);
+
 /* ---- cached B^T B (Sec. 7.1) ----
  *
  * The paper precomputes and caches B^T B (the data constraints' part of the normal

@@ -114,6 +114,8 @@ struct vd_lattice {
     bool gated = false;
     // learned warm start: features (6 nn), prediction (3 nn), backup of u and R (12 ld)
     float *warm = nullptr;
+    // global pose estimation (dense projective ICP): device state, lazily allocated
+    IcpState *icp = nullptr;
     // cached B^T B of the dense samples (per occupied cell, 24 x 24), VD_APPLY_*
     int apply_mode = VD_APPLY_MATRIX_FREE;
     float *btb = nullptr;
@@ -1225,6 +1227,52 @@ vd_status vd_step_energy(vd_lattice *L, const vd_solve_params *P, double out[4])
     out[2] = h[1];
     out[3] = h[2];
     out[0] = (double)P->w_sparse * h[1] + (double)P->w_dense * h[0] + (double)P->w_reg * h[2];
+    return VD_OK;
+}
+
+vd_status vd_estimate_pose(vd_lattice *L, const vd_solve_params *P, int iters, float pose_out[12], int *steps,
+                           double *e_hist) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    TRY(check_params(L, P));
+    if (iters < 0 || iters > kIcpMaxSteps) return fail(L, VD_ERR_INVALID_ARG, "iters must be in [0, %d]", kIcpMaxSteps);
+    if (!L->have_frame) return fail(L, VD_ERR_STATE, "vd_estimate_pose before vd_set_frame");
+    if (!L->icp) {
+        void *q = nullptr;
+        if (cudaMalloc(&q, sizeof(IcpState)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(L, VD_ERR_OOM, "cudaMalloc of the pose state failed");
+        }
+        L->bufs.push_back({q, sizeof(IcpState)});
+        L->icp = (IcpState *)q;
+    }
+    set_params_ctx(L->c, P);
+    refresh_ctx(L);
+    IcpState h{};
+    for (int a = 0; a < 9; a++) h.pose[a] = L->c.Rg[a];
+    for (int a = 0; a < 3; a++) h.pose[9 + a] = L->c.tg[a];
+    cudaStream_t st = L->stream;
+    CK(cudaMemcpyAsync(L->icp, &h, sizeof(IcpState), cudaMemcpyHostToDevice, st));
+    const Grid gr = grids(L);
+    for (int it = 0; it < iters; it++) {
+        if (L->all) {
+            k_icp_assoc<true><<<gr.samp, kThreads, 0, st>>>(L->c, L->icp);
+            k_icp_refine<true><<<gr.refine, kThreads, 0, st>>>(L->c, L->icp);
+        } else {
+            k_icp_assoc<false><<<gr.samp, kThreads, 0, st>>>(L->c, L->icp);
+            k_icp_refine<false><<<gr.refine, kThreads, 0, st>>>(L->c, L->icp);
+        }
+        k_icp_step<<<1, 32, 0, st>>>(L->icp);
+    }
+    CKL();
+    CK(cudaMemcpyAsync(&h, L->icp, sizeof(IcpState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int a = 0; a < 9; a++) L->c.Rg[a] = (float)h.pose[a];
+    for (int a = 0; a < 3; a++) L->c.tg[a] = (float)h.pose[9 + a];
+    if (pose_out)
+        for (int a = 0; a < 12; a++) pose_out[a] = (float)h.pose[a];
+    if (steps) *steps = h.steps;
+    if (e_hist)
+        for (int k = 0; k < h.steps; k++) e_hist[k] = h.e_hist[k];
     return VD_OK;
 }
 

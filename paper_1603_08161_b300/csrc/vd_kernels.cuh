@@ -2426,6 +2426,216 @@ __global__ void k_prolongate(Ctx c, const float *__restrict__ u_start, Ctx f) {
     }
 }
 
+// ------------------------------------------------------------------ global rigid pose (Sec. 6)
+//
+// Dense projective ICP on the global pose (R_g, t_g) with the lattice warp fixed: each
+// step associates every sample projectively at the current pose (Sec. 5.1, the same
+// FP32 decisions re-taken in FP64 near a threshold as the solve's association), then
+// solves the 6 x 6 normal equations of sum_c w_c (n^a . (R_g q_c + t_g - p^a))^2, q_c =
+// p^_c + sum_k alpha_k u_k, over the perturbation R_g <- exp([omega]x) R_g, t_g <- t_g +
+// tau, whose Jacobian row is J = ((R_g q_c) x n^a, n^a).
+constexpr int kIcpMaxSteps = 64;
+
+struct IcpState {
+    double pose[12];                  // R_g (row-major), t_g in FP64 between steps
+    double sums[28];                  // upper triangle of A (21, row by row), b (6), E
+    double e_hist[kIcpMaxSteps];      // E before each step
+    int n_refine, steps, status;      // status 1: A not positive definite (pose kept)
+    int pad;
+};
+
+__device__ __forceinline__ Ctx with_pose(const Ctx &c, const IcpState *st) {
+    Ctx cl = c;
+#pragma unroll
+    for (int a = 0; a < 9; a++) cl.Rg[a] = (float)st->pose[a];
+#pragma unroll
+    for (int a = 0; a < 3; a++) cl.tg[a] = (float)st->pose[9 + a];
+    return cl;
+}
+
+// the 28 sums of sample i associated to pixel k with weight w (FP32 values)
+__device__ __forceinline__ void icp_terms(const Ctx &cl, int i, int k, float w, float acc[28]) {
+    const int cl_ = cl.cell[i];
+    float f[3];
+    sample_frac_f32(cl, i, f);
+    const float4 p4 = cl.sp[i];
+    V3<float> q{p4.x, p4.y, p4.z};
+#pragma unroll
+    for (int kk = 0; kk < 8; kk++) {
+        const int node = corner_node(cl, cl_, kk);
+        const float al = trilinear_weight(f, kk);
+        q.x += al * cl.u[node];
+        q.y += al * cl.u[cl.ld + node];
+        q.z += al * cl.u[2 * cl.ld + node];
+    }
+    const V3<float> Rq = rot<float>(cl.Rg, q);
+    const int px = k % cl.W, py = k / cl.W;
+    const float D = cl.depth[k];
+    const float4 m4 = load_nrm(cl, (size_t)k);
+    const V3<float> na{m4.x, m4.y, m4.z};
+    const V3<float> pa{D * ((px - cl.cx) / cl.fx), D * ((py - cl.cy) / cl.fy), D};
+    const V3<float> d{Rq.x + cl.tg[0] - pa.x, Rq.y + cl.tg[1] - pa.y, Rq.z + cl.tg[2] - pa.z};
+    const float r = dot(na, d);
+    const float J[6] = {Rq.y * na.z - Rq.z * na.y, Rq.z * na.x - Rq.x * na.z, Rq.x * na.y - Rq.y * na.x,
+                        na.x, na.y, na.z};
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < 6; a++)
+#pragma unroll
+        for (int b = a; b < 6; b++) acc[e++] += w * J[a] * J[b];
+#pragma unroll
+    for (int a = 0; a < 6; a++) acc[21 + a] += w * J[a] * r;
+    acc[27] += w * r * r;
+}
+
+// block sum of the 28 per-thread sums (FP32 within a warp, FP64 across warps), added to
+// st->sums by the block's first 28 threads
+__device__ __forceinline__ void icp_block_add(float acc[28], IcpState *st) {
+    __shared__ float wsum[32][28];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int e = 0; e < 28; e++) {
+        float v = acc[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        if (lane == 0) wsum[wid][e] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 28) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += (double)wsum[w][threadIdx.x];
+        if (t != 0.0) atomicAdd(&st->sums[threadIdx.x], t);
+    }
+}
+
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_icp_assoc(Ctx c, IcpState *st) {
+    if (st->status) return;
+    const Ctx cl = with_pose(c, st);
+    const int n = *c.n_samples;
+    float acc[28];
+#pragma unroll
+    for (int e = 0; e < 28; e++) acc[e] = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int pix;
+        float w;
+        float4 rec;
+        if (associate_sample_f32(cl, i, pix, w, rec)) {  // near a threshold: FP64 in k_icp_refine
+            c.refine[atomicAdd(&st->n_refine, 1)] = i;
+            continue;
+        }
+        if (w > 0.f) icp_terms(cl, i, pix, w, acc);
+    }
+    icp_block_add(acc, st);
+}
+
+// the listed samples associated again in FP64 (eight lanes per sample, as the solve's)
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads) k_icp_refine(Ctx c, IcpState *st) {
+    if (st->status) return;
+    const Ctx cl = with_pose(c, st);
+    const int n = st->n_refine;
+    const int k = threadIdx.x & 7;
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int wg = warp * gridDim.x + blockIdx.x;
+    const int per_round = 4 * nwarp * gridDim.x;
+    float acc[28];
+#pragma unroll
+    for (int e = 0; e < 28; e++) acc[e] = 0.f;
+    for (int g0 = 4 * wg; g0 < n; g0 += per_round) {
+        const int g = g0 + ((threadIdx.x & 31) >> 3);
+        V3<double> du{0.0, 0.0, 0.0}, dn{0.0, 0.0, 0.0};
+        int i = -1;
+        float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < n) {
+            i = c.refine[g];
+            const int cell = cl.cell[i];
+            const float4 n4 = cl.sn[i];
+            p4 = cl.sp[i];
+            double f[3];
+            sample_frac_f64(cl, cell, p4, f);
+            const int node = corner_node(cl, cell, k);
+            const double al = trilinear_weight(f, k);
+            du = {al * (double)cl.u[node], al * (double)cl.u[cl.ld + node], al * (double)cl.u[2 * cl.ld + node]};
+            float Rk[9];
+#pragma unroll
+            for (int e = 0; e < 9; e++) Rk[e] = cl.R[e * cl.ld + node];
+            const V3<double> rn = rot<double>(Rk, V3<double>{(double)n4.x, (double)n4.y, (double)n4.z});
+            dn = {al * rn.x, al * rn.y, al * rn.z};
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            du.x += __shfl_xor_sync(FULL, du.x, o);
+            du.y += __shfl_xor_sync(FULL, du.y, o);
+            du.z += __shfl_xor_sync(FULL, du.z, o);
+            dn.x += __shfl_xor_sync(FULL, dn.x, o);
+            dn.y += __shfl_xor_sync(FULL, dn.y, o);
+            dn.z += __shfl_xor_sync(FULL, dn.z, o);
+        }
+        if (k == 0 && g < n) {
+            int pix;
+            float w;
+            float4 rec;
+            associate_finish_f64(cl, p4, du, dn, pix, w, rec);
+            if (w > 0.f) icp_terms(cl, i, pix, w, acc);
+        }
+    }
+    icp_block_add(acc, st);
+}
+
+// one thread: A xi = -b by Cholesky (FP64), then R_g <- exp([omega]x) R_g (Rodrigues),
+// t_g <- t_g + tau; the sums are cleared for the next step
+__global__ void k_icp_step(IcpState *st) {
+    if (threadIdx.x != 0 || st->status) return;
+    double A[6][6], b[6], L[6][6] = {}, y[6], xi[6];
+    int e = 0;
+    for (int a = 0; a < 6; a++)
+        for (int c2 = a; c2 < 6; c2++) A[a][c2] = A[c2][a] = st->sums[e++];
+    for (int a = 0; a < 6; a++) b[a] = st->sums[21 + a];
+    if (st->steps < kIcpMaxSteps) st->e_hist[st->steps] = st->sums[27];
+    for (int k = 0; k < 28; k++) st->sums[k] = 0.0;
+    st->n_refine = 0;
+    for (int j = 0; j < 6; j++) {
+        double sj = A[j][j];
+        for (int k = 0; k < j; k++) sj -= L[j][k] * L[j][k];
+        if (!(sj > 0.0)) {
+            st->status = 1;
+            return;
+        }
+        L[j][j] = sqrt(sj);
+        for (int i = j + 1; i < 6; i++) {
+            double t = A[i][j];
+            for (int k = 0; k < j; k++) t -= L[i][k] * L[j][k];
+            L[i][j] = t / L[j][j];
+        }
+    }
+    for (int i = 0; i < 6; i++) {
+        double t = -b[i];
+        for (int k = 0; k < i; k++) t -= L[i][k] * y[k];
+        y[i] = t / L[i][i];
+    }
+    for (int i = 5; i >= 0; i--) {
+        double t = y[i];
+        for (int k = i + 1; k < 6; k++) t -= L[k][i] * xi[k];
+        xi[i] = t / L[i][i];
+    }
+    const double th = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+    const double K[9] = {0.0, -xi[2], xi[1], xi[2], 0.0, -xi[0], -xi[1], xi[0], 0.0};
+    const double s1 = th > 0.0 ? sin(th) / th : 1.0, s2 = th > 0.0 ? (1.0 - cos(th)) / (th * th) : 0.5;
+    double E3[9], Rn[9];
+    for (int r = 0; r < 3; r++)
+        for (int q = 0; q < 3; q++) {
+            const double KK = K[3 * r] * K[q] + K[3 * r + 1] * K[3 + q] + K[3 * r + 2] * K[6 + q];
+            E3[3 * r + q] = (r == q ? 1.0 : 0.0) + s1 * K[3 * r + q] + s2 * KK;
+        }
+    for (int r = 0; r < 3; r++)
+        for (int q = 0; q < 3; q++)
+            Rn[3 * r + q] = E3[3 * r] * st->pose[q] + E3[3 * r + 1] * st->pose[3 + q] + E3[3 * r + 2] * st->pose[6 + q];
+    for (int k = 0; k < 9; k++) st->pose[k] = Rn[k];
+    for (int a = 0; a < 3; a++) st->pose[9 + a] += xi[3 + a];
+    st->steps++;
+}
+
 // ------------------------------------------------------------------ layout helpers
 
 // AoS full-lattice (n x 3) -> slot SoA vector; entries outside M are dropped

@@ -102,6 +102,7 @@ _SIGS = {
     "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
     "vd_batch_set_plan": [_P, _I, _I, ctypes.c_longlong],
     "vd_unet_get_tensor": [_P, _I, _P, ctypes.c_longlong, _PI],
+    "vd_estimate_pose": [_P, ctypes.POINTER(vd_solve_params), _I, _P, _PI, _PD],
     "vd_set_apply_mode": [_P, _I],
     "vd_get_apply_mode": [_P, _PI, _PI],
     "vd_tune_apply": [_P, ctypes.POINTER(vd_solve_params), _PI, ctypes.POINTER(ctypes.c_float)],
@@ -284,6 +285,15 @@ class Lattice:
         pu, _ = _ptr(uu)
         pr, _ = _ptr(RR)
         self._check(vd_set_warp(self.h, pu, pr, VD_MEM_DEVICE if dev else VD_MEM_HOST))
+
+    def estimate_pose(self, prm, iters):
+        """Dense projective ICP on the global pose: (pose (12,), steps, E before each step)."""
+        pose = np.zeros(12, np.float32)
+        steps = ctypes.c_int()
+        e = np.zeros(max(iters, 1))
+        self._check(vd_estimate_pose(self.h, ctypes.byref(prm), int(iters), pose.ctypes.data, ctypes.byref(steps),
+                                     e.ctypes.data_as(_PD)))
+        return pose, steps.value, e[:steps.value]
 
     def set_apply_mode(self, mode):
         self._check(vd_set_apply_mode(self.h, int(mode)))
