@@ -17,6 +17,10 @@ Parity status of each part (what pins it is in tests/test_oracle_pins.py):
                                              energy by central differences; exact recovery of
                                              a rigid motion of a three-plane corner; fixed
                                              point at the true pose)
+  * marching cubes (Sec. 4) and rasterised samples (Sec. 5.1) pinned (watertight closed
+                                             surfaces, outward normals, plane fields exact,
+                                             sphere volume; pixel samples on their rays and
+                                             on the analytic surface)
   * hierarchy (Sec. 7.2): restriction of the constraints, injection of the state and
     trilinear prolongation ................. pinned (affine fields reproduced exactly;
                                              data energies of a coarse-trilinear warp equal
@@ -95,6 +99,9 @@ def _load():
         "vdo_get_pose": (None, [P, D]),
         "vdo_icp_system": (i, [P, D, D, D]),
         "vdo_icp": (i, [P, i, D]),
+        "vdo_mc_case": (i, [i, I]),
+        "vdo_marching_cubes": (ctypes.c_long, [F, i, i, i, D, d, d, D, D, ctypes.c_long]),
+        "vdo_render_samples": (ctypes.c_long, [P, D, D, ctypes.c_long, i, i, D, D, I, D, D, D, D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -306,6 +313,46 @@ class Oracle:
                               _ptr(st, ctypes.c_int))
         return {"gn_done": g, "energy": e.reshape(gn_iters, 4)[:g], "cg_done": cg[:g],
                 "n_valid": int(st[0]), "n_degenerate": int(st[1])}
+
+
+def mc_case(cs):
+    """Triangles (edge triples) of marching-cubes case cs (bit k: corner k inside)."""
+    e = np.zeros(36, np.int32)
+    n = _load().vdo_mc_case(int(cs), _ptr(e, ctypes.c_int))
+    return e[:3 * n].reshape(n, 3)
+
+
+def marching_cubes(grid, origin, spacing, iso=0.0):
+    """Triangles (n, 3, 3) and vertex normals (n, 3, 3) of the iso-surface of a grid
+    (sz, sy, sx) of float32 values at `origin`, `spacing` (Sec. 4)."""
+    g = np.ascontiguousarray(grid, np.float32)
+    sz, sy, sx = g.shape
+    o = np.ascontiguousarray(origin, np.float64)
+    lib = _load()
+    n = lib.vdo_marching_cubes(_ptr(g, ctypes.c_float), sx, sy, sz, _ptr(o, ctypes.c_double), float(spacing),
+                               float(iso), None, None, 0)
+    tri, nrm = np.zeros(9 * max(n, 1)), np.zeros(9 * max(n, 1))
+    lib.vdo_marching_cubes(_ptr(g, ctypes.c_float), sx, sy, sz, _ptr(o, ctypes.c_double), float(spacing),
+                           float(iso), _ptr(tri, ctypes.c_double), _ptr(nrm, ctypes.c_double), n)
+    return tri[:9 * n].reshape(n, 3, 3), nrm[:9 * n].reshape(n, 3, 3)
+
+
+def render_samples(ctx, tri, nrm, W, H, K, pose=None):
+    """Rasterise the mesh deformed by ctx's warp and `pose` (Sec. 5.1): per pixel the
+    winning triangle, depth, canonical point and normal, and the decision margin."""
+    tri = np.ascontiguousarray(tri, np.float64).reshape(-1, 9)
+    nrm = np.ascontiguousarray(nrm, np.float64).reshape(-1, 9)
+    Kd = np.ascontiguousarray(K, np.float64)
+    Pd = np.ascontiguousarray(np.eye(3).ravel().tolist() + [0, 0, 0] if pose is None else pose, np.float64)
+    win = np.zeros(W * H, np.int32)
+    dep, mar = np.zeros(W * H), np.zeros(W * H)
+    cp, cn = np.zeros(3 * W * H), np.zeros(3 * W * H)
+    cnt = _load().vdo_render_samples(ctx._c, _ptr(tri, ctypes.c_double), _ptr(nrm, ctypes.c_double), tri.shape[0],
+                                     W, H, _ptr(Kd, ctypes.c_double), _ptr(Pd, ctypes.c_double),
+                                     _ptr(win, ctypes.c_int), _ptr(dep, ctypes.c_double), _ptr(cp, ctypes.c_double),
+                                     _ptr(cn, ctypes.c_double), _ptr(mar, ctypes.c_double))
+    return {"count": int(cnt), "win": win.reshape(H, W), "depth": dep.reshape(H, W),
+            "point": cp.reshape(H, W, 3), "normal": cn.reshape(H, W, 3), "margin": mar.reshape(H, W)}
 
 
 def coarse_dims(dims):

@@ -1174,3 +1174,259 @@ int vdo_icp(vdo_ctx *c, int iters, double *e_hist)
     }
     return it;
 }
+
+/* ------------------------------------------------------------------ source samples (Sec. 4, 5.1) */
+
+/* Marching cubes case table, generated from the rule (the paper's Sec. 4 extracts the
+ * canonical isosurface by data-parallel marching cubes; no table is printed there):
+ *   corner k of a cell sits at (k & 1, (k >> 1) & 1, (k >> 2) & 1) and is inside when its
+ *   value is below the iso value; edge e joins corners (a, b), a < b:
+ *     x-edges 0..3 = (0,1) (2,3) (4,5) (6,7), y-edges 4..7 = (0,2) (1,3) (4,6) (5,7),
+ *     z-edges 8..11 = (0,4) (1,5) (2,6) (3,7);
+ *   on each face, walking its corners counter-clockwise as seen from outside the cell,
+ *   an edge crossed from outside to inside starts a segment that ends at the next
+ *   crossed edge of the walk (so diagonal inside corners of a face are separated, the
+ *   same way from both cells that share the face);
+ *   every crossed edge starts one segment and ends one, so the segments form loops; a
+ *   loop is started at its lowest edge, loops are taken in the order of their lowest
+ *   edge, and each is cut into the fan (v0, v_i, v_i+1).  The loops wind counter-
+ *   clockwise seen from outside the surface (the side above the iso value). */
+static int mc_tab[256][31];   /* [0] = triangles, then 3 edges per triangle */
+static int mc_ready = 0;
+
+static void mc_build(void)
+{
+    static const int E[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7},
+                                 {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+    int cyc[6][4];
+    for (int A = 0; A < 3; A++) {
+        int B = (A + 1) % 3, C = (A + 2) % 3;
+        for (int sgn = 0; sgn < 2; sgn++) {
+            int q[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};   /* (B, C) counter-clockwise about +A */
+            for (int i = 0; i < 4; i++) {
+                int j = sgn ? i : (4 - i) % 4;                  /* outward -A: walk backwards */
+                int k = (sgn << A) | (q[j][0] << B) | (q[j][1] << C);
+                cyc[2 * A + sgn][i] = k;
+            }
+        }
+    }
+    for (int cs = 0; cs < 256; cs++) {
+        int next[12];
+        for (int e = 0; e < 12; e++) next[e] = -1;
+        for (int f = 0; f < 6; f++) {
+            int ce[4], kind[4];          /* edge of each cycle step, +1 entry, -1 exit, 0 none */
+            for (int i = 0; i < 4; i++) {
+                int a = cyc[f][i], b = cyc[f][(i + 1) % 4];
+                int lo = a < b ? a : b, hi = a < b ? b : a;
+                for (int e = 0; e < 12; e++)
+                    if (E[e][0] == lo && E[e][1] == hi) ce[i] = e;
+                int ina = (cs >> a) & 1, inb = (cs >> b) & 1;
+                kind[i] = ina == inb ? 0 : (inb ? 1 : -1);
+            }
+            for (int i = 0; i < 4; i++) {
+                if (kind[i] != 1) continue;
+                for (int d = 1; d < 4; d++)
+                    if (kind[(i + d) % 4] != 0) { next[ce[i]] = ce[(i + d) % 4]; break; }
+            }
+        }
+        int used[12] = {0}, nt = 0;
+        for (int e0 = 0; e0 < 12; e0++) {
+            if (next[e0] < 0 || used[e0]) continue;
+            int loop[12], m = 0, e = e0;
+            do { loop[m++] = e; used[e] = 1; e = next[e]; } while (e != e0 && m < 12);
+            for (int i = 1; i + 1 < m; i++) {
+                mc_tab[cs][1 + 3 * nt] = loop[0];
+                mc_tab[cs][2 + 3 * nt] = loop[i];
+                mc_tab[cs][3 + 3 * nt] = loop[i + 1];
+                nt++;
+            }
+        }
+        mc_tab[cs][0] = nt;
+    }
+    mc_ready = 1;
+}
+
+int vdo_mc_case(int cs, int *edges)
+{
+    if (!mc_ready) mc_build();
+    for (int i = 0; i < 3 * mc_tab[cs][0]; i++) edges[i] = mc_tab[cs][1 + i];
+    return mc_tab[cs][0];
+}
+
+static double grid_at(const float *g, int sx, int sy, int x, int y, int z)
+{
+    return (double)g[(size_t)x + (size_t)sx * ((size_t)y + (size_t)sy * z)];
+}
+
+/* SDF gradient at grid point (x, y, z): central differences, one-sided at the border */
+static void grid_grad(const float *g, int sx, int sy, int sz, double hs, int x, int y, int z, double out[3])
+{
+    int n[3] = {sx, sy, sz}, p[3] = {x, y, z};
+    for (int a = 0; a < 3; a++) {
+        int lo[3] = {x, y, z}, hi[3] = {x, y, z};
+        lo[a] = p[a] > 0 ? p[a] - 1 : p[a];
+        hi[a] = p[a] + 1 < n[a] ? p[a] + 1 : p[a];
+        double d = grid_at(g, sx, sy, hi[0], hi[1], hi[2]) - grid_at(g, sx, sy, lo[0], lo[1], lo[2]);
+        out[a] = d / ((hi[a] - lo[a]) * hs);
+    }
+}
+
+/* Marching cubes over a (sx, sy, sz) grid of values g (x fastest) at origin o, spacing hs:
+ * the triangles in cell order (cell x fastest), in the table's order within a cell.  A
+ * vertex on edge (a, b) sits at p_a + t (p_b - p_a), t = (iso - g_a) / (g_b - g_a); its
+ * normal is the SDF gradient interpolated the same way, normalised.  Writes up to cap
+ * triangles (9 position and 9 normal doubles each; either may be NULL) and returns the
+ * number of triangles of the whole surface. */
+long vdo_marching_cubes(const float *g, int sx, int sy, int sz, const double o[3], double hs, double iso,
+                        double *tri, double *nrm, long cap)
+{
+    if (!mc_ready) mc_build();
+    static const int E[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7},
+                                 {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+    long n = 0;
+    for (int z = 0; z + 1 < sz; z++)
+        for (int y = 0; y + 1 < sy; y++)
+            for (int x = 0; x + 1 < sx; x++) {
+                double v[8];
+                int cs = 0;
+                for (int k = 0; k < 8; k++) {
+                    v[k] = grid_at(g, sx, sy, x + (k & 1), y + ((k >> 1) & 1), z + ((k >> 2) & 1));
+                    if (v[k] < iso) cs |= 1 << k;
+                }
+                for (int t = 0; t < mc_tab[cs][0]; t++, n++) {
+                    if (n >= cap) continue;
+                    for (int j = 0; j < 3; j++) {
+                        int e = mc_tab[cs][1 + 3 * t + j], a = E[e][0], b = E[e][1];
+                        double w = (iso - v[a]) / (v[b] - v[a]);
+                        int pa[3] = {x + (a & 1), y + ((a >> 1) & 1), z + ((a >> 2) & 1)};
+                        int pb[3] = {x + (b & 1), y + ((b >> 1) & 1), z + ((b >> 2) & 1)};
+                        double ga[3], gb[3], nn[3], L = 0;
+                        grid_grad(g, sx, sy, sz, hs, pa[0], pa[1], pa[2], ga);
+                        grid_grad(g, sx, sy, sz, hs, pb[0], pb[1], pb[2], gb);
+                        for (int c = 0; c < 3; c++) {
+                            double qa = o[c] + hs * pa[c], qb = o[c] + hs * pb[c];
+                            if (tri) tri[9 * n + 3 * j + c] = qa + w * (qb - qa);
+                            nn[c] = ga[c] + w * (gb[c] - ga[c]);
+                            L += nn[c] * nn[c];
+                        }
+                        L = sqrt(L);
+                        if (nrm)
+                            for (int c = 0; c < 3; c++) nrm[9 * n + 3 * j + c] = L > 0 ? nn[c] / L : 0.0;
+                    }
+                }
+            }
+    return n;
+}
+
+/* Rasterise the deformed mesh (Sec. 5.1: "rasterize the resulting mesh to obtain sample
+ * points S(p^_c)").  Each vertex p^ is deformed by the lattice warp and the pose,
+ * S(p^) = R_g (p^ + sum alpha_k u_k) + t_g (u = 0 outside the lattice), and projected,
+ * (f_x X / Z + c_x, f_y Y / Z + c_y), pixel centres at integer coordinates.  A pixel is
+ * covered by a triangle (all vertices with Z > 1e-3, non-zero screen area) when its
+ * centre has all three barycentric coordinates >= 0; among the covering triangles the
+ * one with the smallest depth Z = 1 / sum(lambda_i / Z_i) wins, ties to the lower
+ * triangle index.  Its sample is the perspective-correct interpolation of the canonical
+ * vertices, b_i = (lambda_i / Z_i) / sum_j (lambda_j / Z_j): p^ = sum b_i p^_i, n^ =
+ * normalise(sum b_i n^_i).  Writes per pixel (H x W): winning triangle (-1 if none),
+ * depth, canonical point and normal (any may be NULL), and the pixel's margin (the
+ * smallest screen distance, in pixels, from its centre to an edge of the winner, or
+ * to the depth of a runner-up scaled by f_x / Z: small values mark decisions that
+ * rounding may take either way).  Returns the number of covered pixels. */
+long vdo_render_samples(const vdo_ctx *c, const double *tri, const double *nrm, long ntri, int W, int H,
+                        const double K[4], const double pose[12], int *win, double *depth, double *cp,
+                        double *cn, double *margin)
+{
+    size_t np = (size_t)W * H;
+    int *best = (int *)xcalloc(np, sizeof(int));
+    double *bz = (double *)xcalloc(np, sizeof(double));
+    double *second = (double *)xcalloc(np, sizeof(double));
+    double *emin = (double *)xcalloc(np, sizeof(double));
+    double *bw = (double *)xcalloc(np * 3, sizeof(double));
+    for (size_t k = 0; k < np; k++) { best[k] = -1; bz[k] = 1e300; second[k] = 1e300; }
+    double *P = (double *)xcalloc((size_t)ntri * 9, sizeof(double));
+    for (long t = 0; t < ntri; t++)
+        for (int j = 0; j < 3; j++) {
+            const double *q = tri + 9 * t + 3 * j;
+            double f[3], acc[3] = {q[0], q[1], q[2]}, out[3];
+            int cell = locate(c, q, f);
+            if (cell >= 0) {
+                int nd[8];
+                double al[8];
+                corners(c, cell, f, nd, al);
+                for (int k = 0; k < 8; k++)
+                    for (int a = 0; a < 3; a++) acc[a] += al[k] * c->u[3 * nd[k] + a];
+            }
+            matvec3(pose, acc, out);
+            for (int a = 0; a < 3; a++) P[9 * t + 3 * j + a] = out[a] + pose[9 + a];
+        }
+    for (long t = 0; t < ntri; t++) {
+        double X[3], Y[3], Z[3];
+        int ok = 1;
+        for (int j = 0; j < 3; j++) {
+            Z[j] = P[9 * t + 3 * j + 2];
+            if (!(Z[j] > 1e-3)) ok = 0;
+            X[j] = K[0] * P[9 * t + 3 * j] / Z[j] + K[2];
+            Y[j] = K[1] * P[9 * t + 3 * j + 1] / Z[j] + K[3];
+        }
+        if (!ok) continue;
+        double area = (X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]);
+        if (area == 0.0) continue;
+        double xmin = fmin(X[0], fmin(X[1], X[2])), xmax = fmax(X[0], fmax(X[1], X[2]));
+        double ymin = fmin(Y[0], fmin(Y[1], Y[2])), ymax = fmax(Y[0], fmax(Y[1], Y[2]));
+        int u0 = (int)ceil(xmin), u1 = (int)floor(xmax), v0 = (int)ceil(ymin), v1 = (int)floor(ymax);
+        if (u0 < 0) u0 = 0;
+        if (v0 < 0) v0 = 0;
+        if (u1 > W - 1) u1 = W - 1;
+        if (v1 > H - 1) v1 = H - 1;
+        for (int v = v0; v <= v1; v++)
+            for (int u = u0; u <= u1; u++) {
+                double l[3], el[3];
+                for (int j = 0; j < 3; j++) {
+                    int a = (j + 1) % 3, b = (j + 2) % 3;
+                    double e = (X[b] - X[a]) * (v - Y[a]) - (Y[b] - Y[a]) * (u - X[a]);
+                    l[j] = e / area;
+                    double len = sqrt((X[b] - X[a]) * (X[b] - X[a]) + (Y[b] - Y[a]) * (Y[b] - Y[a]));
+                    el[j] = len > 0 ? fabs(e) / len : 0.0;
+                }
+                if (l[0] < 0 || l[1] < 0 || l[2] < 0) continue;
+                double s = l[0] / Z[0] + l[1] / Z[1] + l[2] / Z[2], zz = 1.0 / s;
+                size_t k = (size_t)v * W + u;
+                if (zz < bz[k] || (zz == bz[k] && t < best[k])) {
+                    second[k] = bz[k];
+                    bz[k] = zz;
+                    best[k] = (int)t;
+                    emin[k] = fmin(el[0], fmin(el[1], el[2]));
+                    for (int j = 0; j < 3; j++) bw[3 * k + j] = (l[j] / Z[j]) / s;
+                } else if (zz < second[k]) {
+                    second[k] = zz;
+                }
+            }
+    }
+    long cnt = 0;
+    for (size_t k = 0; k < np; k++) {
+        if (win) win[k] = best[k];
+        if (depth) depth[k] = best[k] >= 0 ? bz[k] : 0.0;
+        if (margin) margin[k] = best[k] >= 0 ? fmin(emin[k], second[k] < 1e299 ? (second[k] - bz[k]) * K[0] / bz[k] : 1e300) : 0.0;
+        if (best[k] < 0) {
+            if (cp) cp[3 * k] = cp[3 * k + 1] = cp[3 * k + 2] = 0.0;
+            if (cn) cn[3 * k] = cn[3 * k + 1] = cn[3 * k + 2] = 0.0;
+            continue;
+        }
+        cnt++;
+        long t = best[k];
+        double q[3] = {0, 0, 0}, m[3] = {0, 0, 0}, L = 0;
+        for (int j = 0; j < 3; j++)
+            for (int a = 0; a < 3; a++) {
+                q[a] += bw[3 * k + j] * tri[9 * t + 3 * j + a];
+                m[a] += bw[3 * k + j] * nrm[9 * t + 3 * j + a];
+            }
+        for (int a = 0; a < 3; a++) L += m[a] * m[a];
+        L = sqrt(L);
+        for (int a = 0; a < 3; a++) {
+            if (cp) cp[3 * k + a] = q[a];
+            if (cn) cn[3 * k + a] = L > 0 ? m[a] / L : 0.0;
+        }
+    }
+    free(best); free(bz); free(second); free(emin); free(bw); free(P);
+    return cnt;
+}

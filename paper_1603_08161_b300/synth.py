@@ -26,7 +26,7 @@ import math
 import numpy as np
 
 __all__ = ["Frame", "sphere_frame", "capsule_frame", "config1", "config2",
-           "batch_frames", "sequence_frames", "sequences", "lattice_for", "plane_frame", "corner_frame"]
+           "batch_frames", "sequence_frames", "sequences", "lattice_for", "plane_frame", "corner_frame", "sdf_grid"]
 
 
 @dataclasses.dataclass
@@ -487,6 +487,25 @@ def corner_frame(W=64, H=48, f=60.0, n=16, rot=None, shift=(0.0, 0.0, 0.0), vert
     return Frame(dep.astype(np.float32), K.astype(np.float32), _identity_pose(),
                  pts[sel].astype(np.float32), n0[k0[sel]].astype(np.float32),
                  np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), dims, origin, h, name)
+
+
+def sdf_grid(kind="sphere", n=64, seed=0, cube_min=(-0.5, -0.5, 0.5), cube_size=1.0, **kw):
+    """Signed distance of a canonical surface (negative inside) on an n^3 grid of nodes
+    over the 1 m cube, float32 array (z, y, x), with its origin and spacing: the input
+    of the marching cubes.  kind "sphere": radius kw.get("radius", 0.3) at (0, 0, 1);
+    "capsules": the unbent three-capsule surface of capsule_frame(seed)."""
+    hs = cube_size / (n - 1)
+    ax = np.asarray(cube_min, np.float64)[:, None] + hs * np.arange(n)[None, :]
+    z, y, x = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    pts = np.stack([x, y, z], -1).reshape(-1, 3)
+    if kind == "sphere":
+        d = np.linalg.norm(pts - np.array([0.0, 0.0, 1.0]), axis=1) - kw.get("radius", 0.3)
+    else:
+        rng = np.random.default_rng(seed)
+        radii = rng.uniform(0.05, 0.15, 3)
+        caps = _Capsules(radii, [0.0, 0.0], [np.array([0.0, 0.0, 1.0])] * 2)
+        d = caps.canon_sdf(pts)
+    return d.reshape(n, n, n).astype(np.float32), np.asarray(cube_min, np.float64), hs
 
 
 def config1(seed=0):

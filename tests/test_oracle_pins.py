@@ -817,3 +817,159 @@ def test_icp_keeps_the_true_pose():
     P = o.get_pose()
     assert e[0] < 1e-13
     assert np.abs(P - _pose(np.eye(3), np.zeros(3))).max() < 1e-7
+
+
+# ---------------------------------------------------------------- source samples (Sec. 4, 5.1)
+
+def _smooth_field(n=24, seed=0):
+    """A random smooth field whose zero set is closed and inside the grid."""
+    rng = np.random.default_rng(seed)
+    ax = np.linspace(-1, 1, n)
+    z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
+    f = x ** 2 + 1.3 * y ** 2 + 0.8 * z ** 2 - 0.45
+    for _ in range(4):
+        k = rng.normal(0, 3, 3)
+        f = f + 0.06 * np.sin(k[0] * x + k[1] * y + k[2] * z + rng.uniform(0, 6))
+    return f.astype(np.float32), np.array([-1.0, -1.0, -1.0]), 2.0 / (n - 1)
+
+
+def _edges_of(tri):
+    out = {}
+    for t in tri:
+        vs = [tuple(v) for v in t]
+        for a, b in ((0, 1), (1, 2), (2, 0)):
+            out.setdefault(frozenset((vs[a], vs[b])), []).append((vs[a], vs[b]))
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_marching_cubes_closed_oriented_surface(seed):
+    """A closed iso-surface inside the grid comes out watertight and consistently
+    oriented: every mesh edge belongs to exactly two triangles, which traverse it in
+    opposite directions (the face rule resolves a shared ambiguous face the same way in
+    both cells)."""
+    g, o, hs = _smooth_field(seed=seed)
+    tri, _ = oracle.marching_cubes(g, o, hs)
+    degenerate = np.linalg.norm(np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0]), axis=1) == 0
+    assert len(tri) > 500
+    for e, uses in _edges_of(tri[~degenerate] if degenerate.any() else tri).items():
+        if len(e) < 2:
+            continue
+        assert len(uses) == 2 and uses[0] == uses[1][::-1], uses
+
+
+def test_marching_cubes_sphere_volume_and_outward_normals():
+    """Sphere SDF: the mesh encloses 4/3 pi r^3 (divergence theorem, O(h^2) error),
+    every face normal (by vertex order) and every vertex normal points outward, and the
+    vertices lie on the sphere to O(h^2)."""
+    g, o, hs = synth.sdf_grid("sphere", n=64)
+    tri, nrm = oracle.marching_cubes(g, o, hs)
+    c = np.array([0.0, 0.0, 1.0])
+    vol = np.einsum("ij,ij->i", tri[:, 0] - c, np.cross(tri[:, 1] - c, tri[:, 2] - c)).sum() / 6.0
+    assert abs(vol - 4.0 / 3.0 * np.pi * 0.3 ** 3) < 0.01 * 4.0 / 3.0 * np.pi * 0.3 ** 3
+    fn = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    radial = tri.mean(1) - c
+    assert (np.einsum("ij,ij->i", fn, radial) > 0).all()
+    assert (np.einsum("ijk,ijk->ij", nrm, tri - c) > 0).all()
+    assert np.abs(np.linalg.norm(tri - c, axis=2) - 0.3).max() < 2 * hs ** 2 / 0.3
+
+
+def test_marching_cubes_linear_field_exact():
+    """A linear field's zero set is a plane: every vertex lies on it exactly (linear
+    interpolation along the edges is exact), every triangle is parallel to it, and its
+    normal is the field's gradient."""
+    n = 12
+    ax = np.linspace(0, 1, n)
+    z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
+    a = np.array([0.3, -0.5, 0.8])
+    g = (a[0] * x + a[1] * y + a[2] * z - 0.2).astype(np.float32)
+    tri, nrm = oracle.marching_cubes(g, [0, 0, 0], 1.0 / (n - 1))
+    assert len(tri) > 50
+    assert np.abs(tri @ a - 0.2).max() < 2e-7          # float32 field values
+    fn = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    big = np.linalg.norm(fn, axis=1) > 1e-12        # where the plane passes through a grid node,
+    fn = fn[big] / np.linalg.norm(fn[big], axis=1, keepdims=True)   # fans may hold empty triangles
+    assert big.sum() > 50
+    assert np.abs(fn - a / np.linalg.norm(a)).max() < 1e-5
+    assert np.abs(nrm - a / np.linalg.norm(a)).max() < 1e-5
+
+
+def test_marching_cubes_every_case_separates_corners():
+    """For every one of the 256 cases, a cell whose inside corners are at -1 and outside
+    ones at +1 gives triangles whose vertices are the midpoints of crossed edges only,
+    every crossed edge is used, and each triangle's normal points up the field (toward
+    the outside)."""
+    corners = np.array([[k & 1, (k >> 1) & 1, (k >> 2) & 1] for k in range(8)], np.float64)
+    for cs in range(1, 255):
+        ins = [(cs >> k) & 1 for k in range(8)]
+        g = np.array([[[-1.0 if ins[x + 2 * y + 4 * z] else 1.0 for x in range(2)] for y in range(2)]
+                      for z in range(2)], np.float32)
+        tri, _ = oracle.marching_cubes(g, [0, 0, 0], 1.0)
+        mids = {tuple((corners[a] + corners[b]) / 2) for a in range(8) for b in range(a + 1, 8)
+                if np.abs(corners[a] - corners[b]).sum() == 1 and ins[a] != ins[b]}
+        used = {tuple(v) for t in tri for v in t}
+        assert used == mids, cs
+        # the face normal points up the trilinear field's gradient at the centroid
+        vals = np.array([-1.0 if ins[k] else 1.0 for k in range(8)])
+        fn = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+        for t, n_ in zip(tri, fn):
+            x, y, z = t.mean(0)
+            wts = lambda k: ((x if k & 1 else 1 - x), (y if k & 2 else 1 - y), (z if k & 4 else 1 - z))
+            grad = np.zeros(3)
+            for k in range(8):
+                wx, wy, wz = wts(k)
+                sx, sy, sz = (1 if k & 1 else -1), (1 if k & 2 else -1), (1 if k & 4 else -1)
+                grad += vals[k] * np.array([sx * wy * wz, wx * sy * wz, wx * wy * sz])
+            assert n_ @ grad > 0, cs
+
+
+def test_raster_single_triangle_by_hand():
+    """One triangle facing the camera at depth 1: the covered pixels are exactly those
+    whose centres have non-negative barycentric coordinates, the depth is 1, and each
+    sample is the back-projected pixel centre (identity warp and pose)."""
+    fr = synth.plane_frame(W=40, H=30, f=30.0, n=4)
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    tri = np.array([[[-0.3, -0.2, 1.0], [0.35, -0.1, 1.0], [0.0, 0.33, 1.0]]])
+    nrm = np.tile([0.0, 0.0, -1.0], (1, 3, 1))
+    K = np.array([30.0, 30.0, 19.5, 14.5])
+    r = oracle.render_samples(o, tri, nrm, 40, 30, K)
+    X = 30.0 * tri[0, :, 0] + 19.5
+    Y = 30.0 * tri[0, :, 1] + 14.5
+    v, u = np.mgrid[0:30, 0:40]
+    area = (X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0])
+    lam = [((X[(j + 2) % 3] - X[(j + 1) % 3]) * (v - Y[(j + 1) % 3]) - (Y[(j + 2) % 3] - Y[(j + 1) % 3]) *
+            (u - X[(j + 1) % 3])) / area for j in range(3)]
+    inside = (lam[0] >= 0) & (lam[1] >= 0) & (lam[2] >= 0)
+    assert np.array_equal(r["win"] == 0, inside) and inside.sum() > 50
+    assert np.abs(r["depth"][inside] - 1.0).max() < 1e-12
+    ray = np.stack([(u - 19.5) / 30.0, (v - 14.5) / 30.0, np.ones_like(u, float)], -1)
+    assert np.abs(r["point"][inside] - ray[inside]).max() < 1e-12
+
+
+def test_raster_sphere_samples_on_rays_and_surface():
+    """The sphere mesh rendered with an identity warp: every sample lies on its pixel's
+    ray, on the sphere's front half to O(h^2), with an outward normal facing the camera;
+    the covered pixels are those of the sphere's projected disk (up to a pixel at its
+    rim).  With a translation warp u = d on every node, S(p^) = p^ + d is on the ray."""
+    g, og, hs = synth.sdf_grid("sphere", n=48)
+    tri, nrm = oracle.marching_cubes(g, og, hs)
+    fr = synth.config1()
+    o = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL)
+    K = fr.K.astype(np.float64)
+    r = oracle.render_samples(o, tri, nrm, fr.W, fr.H, K)
+    cov = r["win"] >= 0
+    v, u = np.mgrid[0:fr.H, 0:fr.W]
+    ray = np.stack([(u - K[2]) / K[0], (v - K[3]) / K[1], np.ones_like(u, float)], -1)
+    p = r["point"][cov]
+    assert np.abs(np.cross(p, ray[cov])).max() < 1e-12
+    c = np.array([0.0, 0.0, 1.0])
+    assert np.abs(np.linalg.norm(p - c, axis=1) - 0.3).max() < 2 * hs ** 2 / 0.3
+    assert (p[:, 2] < 1.0 + 1e-9).all() and (np.einsum("ij,ij->i", r["normal"][cov], ray[cov]) < 0).all()
+    rd = ray / np.linalg.norm(ray, axis=-1, keepdims=True)
+    miss = np.linalg.norm(np.cross(rd, c), axis=-1)          # ray's distance from the centre
+    assert cov[miss < 0.3 - 0.02].all() and not cov[miss > 0.3 + 0.02].any()
+    d = np.array([0.01, -0.02, 0.015])
+    o.set_warp(np.tile(d, (o.nn, 1)))
+    r2 = oracle.render_samples(o, tri, nrm, fr.W, fr.H, K)
+    cov2 = r2["win"] >= 0
+    assert np.abs(np.cross(r2["point"][cov2] + d, ray[cov2])).max() < 1e-12
