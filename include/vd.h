@@ -331,6 +331,65 @@ vd_status vd_fit_rotations_noalloc(int nx, int ny, int nz, float spacing, const 
                                    const float *rot_in, float *rot_out, double *e_reg,
                                    int *n_degenerate, void *cuda_stream);
 
+/* ---- source samples on the GPU (Sec. 4: marching cubes; Sec. 5.1: rasterisation) ----
+ *
+ * The paper extracts the canonical iso-surface with data-parallel marching cubes (one
+ * thread per cell, a prefix sum to compact the triangles) and rasterises the mesh,
+ * deformed by the current warp, to obtain the sample points S(p^_c).  A renderer holds
+ * one canonical mesh and a W x H z-buffer.
+ *
+ * Marching cubes: corner k of a cell is at (k & 1, (k >> 1) & 1, (k >> 2) & 1) and is
+ * inside when its value is below the iso value; the case table is generated from a face
+ * rule (walking each face counter-clockwise as seen from outside the cell, an edge
+ * crossed from outside to inside opens a segment that closes at the next crossed edge;
+ * the segments form loops, each cut into a fan from its lowest edge, edges numbered 4 A
+ * + b + 2 c for the edge along axis A whose lower corner has the other two coordinates
+ * (b, c)), which separates diagonal inside corners of a face the same way from both
+ * cells and gives watertight, consistently oriented surfaces (normals toward values
+ * above the iso value).  A vertex sits on its edge at t = (iso - g_a) / (g_b - g_a) from
+ * the lower corner; its normal is the grid's central-difference gradient interpolated
+ * the same way, normalised.  Triangles are ordered by cell (x fastest), then by the
+ * table.
+ *
+ * Rasterisation: each vertex p^ becomes S(p^) = R_g (p^ + sum alpha_k u_k) + t_g with
+ * the lattice's displacements (u = 0 outside the lattice, or everywhere when lat is
+ * NULL) and the given pose, and projects to (f_x X / Z + c_x, f_y Y / Z + c_y), pixel
+ * centres at integer coordinates.  A pixel centre with all three barycentric
+ * coordinates >= 0 is covered (triangles with a vertex at Z <= 1e-3 are skipped); the
+ * covering triangle of smallest depth 1 / sum(lambda_i / Z_i) wins, ties to the lower
+ * index.  Its sample is the perspective-correct interpolation of the canonical vertices
+ * and normals (normal renormalised). */
+typedef struct vd_renderer vd_renderer; /* opaque; owned by the library */
+
+/* A renderer for meshes of at most max_triangles triangles and W x H images. */
+vd_status vd_renderer_create(int max_triangles, int W, int H, vd_renderer **out);
+vd_status vd_renderer_destroy(vd_renderer *r);
+const char *vd_renderer_last_error(const vd_renderer *r);
+
+/* Marching cubes of the sx x sy x sz grid `sdf` (x fastest; `mem` says where it lives)
+ * at origin (host, 3 floats) and spacing into the renderer's canonical mesh.
+ * n_triangles (may be NULL) gets the surface's triangle count; VD_ERR_INVALID_ARG if it
+ * exceeds max_triangles (the mesh then holds the first max_triangles).  Synchronous. */
+vd_status vd_marching_cubes(vd_renderer *r, const float *sdf, int sx, int sy, int sz, const float origin[3],
+                            float spacing, float iso, int mem, int *n_triangles);
+
+/* The marching-cubes case table: the triangles of case cs (bit k set: corner k inside),
+ * as edge triples written to edges (up to 30 ints, may be NULL); returns the triangle
+ * count, or -1 for cs outside [0, 255].  Host only. */
+int vd_mc_case(int cs, int *edges);
+
+/* The canonical mesh: n_triangles x 9 vertex positions and normals (either may be NULL). */
+vd_status vd_get_mesh(vd_renderer *r, float *tri, float *nrm, int mem);
+
+/* Rasterise the mesh deformed by lat's warp (NULL: none) and `pose` (12 floats, host;
+ * NULL: identity) with intrinsics K (host), and write the samples of the covered pixels
+ * whose column and row are multiples of `stride`, in pixel order: canonical points and
+ * normals (cap x 3 floats each) and (pix, may be NULL) their pixel indices v W + u.
+ * count gets the number of such pixels (only the first cap are written).  Uses lat's
+ * stream when lat is given (after its pending work), else the renderer's.  Synchronous. */
+vd_status vd_render_samples(vd_renderer *r, const vd_lattice *lat, const float K[4], const float pose[12],
+                            int stride, float *pts, float *nrm, int *pix, int cap, int *count, int mem);
+
 /* ---- hierarchical coarse-to-fine solve (Sec. 7.2) ----
  *
  * A hierarchy nests levels - 1 coarse lattices on a lattice (level 0): level l has

@@ -16,6 +16,7 @@
 
 #include "vd.h"
 #include "vd_kernels.cuh"
+#include "vd_render.cuh"
 
 using namespace vd;
 
@@ -2048,6 +2049,212 @@ vd_status vd_hierarchy_solve(vd_hierarchy *H, const vd_solve_params *params, vd_
     vd_status s = vd_hierarchy_solve_async(H, params);
     if (s != VD_OK) return s;
     return vd_hierarchy_get_reports(H, out);
+}
+
+}  // extern "C"
+
+// ====================================================================== source samples (Sec. 4, 5.1)
+
+struct vd_renderer {
+    int max_tri = 0, W = 0, H = 0;
+    float *tri = nullptr, *nrm = nullptr, *posed = nullptr, *pose_dev = nullptr;
+    int *table = nullptr;
+    float *grid = nullptr;           // device copy of a host SDF grid
+    size_t cap_grid = 0;
+    int *cnt = nullptr, *off = nullptr, *sums = nullptr, *total = nullptr;
+    long cap_cells = 0;
+    unsigned long long *zbuf = nullptr;
+    int *flag = nullptr, *poff = nullptr;
+    float *stage = nullptr;          // W H x 7: points, normals, pixel index (host outputs)
+    int n_tri = 0;
+    cudaStream_t st = nullptr;
+    std::vector<void *> bufs;
+    std::string err;
+};
+
+namespace {
+
+template <typename T>
+bool ralloc(vd_renderer *R, T **p, size_t count) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    R->bufs.push_back(q);
+    *p = (T *)q;
+    return true;
+}
+
+void rfree(vd_renderer *R, void *p) {
+    if (!p) return;
+    for (size_t k = 0; k < R->bufs.size(); k++)
+        if (R->bufs[k] == p) {
+            cudaFree(p);
+            R->bufs.erase(R->bufs.begin() + k);
+            return;
+        }
+}
+
+vd_status rfail(vd_renderer *R, vd_status s, const char *msg) {
+    R->err = msg;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+vd_status vd_renderer_create(int max_triangles, int W, int H, vd_renderer **out) {
+    if (!out || max_triangles < 1 || W < 1 || H < 1 || (long)W * H > (long)kScanTile * kScanTile ||
+        (long)max_triangles * 9 > 0x7fffffffL)
+        return VD_ERR_INVALID_ARG;
+    *out = nullptr;
+    vd_renderer *R = new (std::nothrow) vd_renderer();
+    if (!R) return VD_ERR_OOM;
+    R->max_tri = max_triangles;
+    R->W = W;
+    R->H = H;
+    const size_t np = (size_t)W * H;
+    const bool ok = ralloc(R, &R->tri, 9 * (size_t)max_triangles) && ralloc(R, &R->nrm, 9 * (size_t)max_triangles) &&
+                    ralloc(R, &R->posed, 9 * (size_t)max_triangles) && ralloc(R, &R->pose_dev, 12) &&
+                    ralloc(R, &R->table, 256 * kMcRow) && ralloc(R, &R->sums, kScanTile) && ralloc(R, &R->total, 2) &&
+                    ralloc(R, &R->zbuf, np) && ralloc(R, &R->flag, np) && ralloc(R, &R->poff, np + 1) &&
+                    ralloc(R, &R->stage, 7 * np);
+    if (!ok || cudaStreamCreateWithFlags(&R->st, cudaStreamNonBlocking) != cudaSuccess) {
+        vd_renderer_destroy(R);
+        return VD_ERR_OOM;
+    }
+    const McTable T = mc_make_table();
+    if (cudaMemcpy(R->table, T.t, sizeof(T.t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        vd_renderer_destroy(R);
+        return VD_ERR_CUDA;
+    }
+    *out = R;
+    return VD_OK;
+}
+
+int vd_mc_case(int cs, int *edges) {
+    if (cs < 0 || cs > 255) return -1;
+    static const McTable T = mc_make_table();
+    const int n = T.t[cs][0];
+    if (edges)
+        for (int i = 0; i < 3 * n; i++) edges[i] = T.t[cs][1 + i];
+    return n;
+}
+
+vd_status vd_renderer_destroy(vd_renderer *R) {
+    if (!R) return VD_OK;
+    if (R->st) cudaStreamSynchronize(R->st);
+    for (void *p : R->bufs) cudaFree(p);
+    if (R->st) cudaStreamDestroy(R->st);
+    delete R;
+    return VD_OK;
+}
+
+const char *vd_renderer_last_error(const vd_renderer *R) { return R ? R->err.c_str() : "null renderer"; }
+
+vd_status vd_marching_cubes(vd_renderer *R, const float *sdf, int sx, int sy, int sz, const float origin[3],
+                            float spacing, float iso, int mem, int *n_triangles) {
+    if (!R) return VD_ERR_INVALID_ARG;
+    if (!sdf || !origin || sx < 2 || sy < 2 || sz < 2 || !(spacing > 0.f))
+        return rfail(R, VD_ERR_INVALID_ARG, "bad grid");
+    const long ncell = (long)(sx - 1) * (sy - 1) * (sz - 1);
+    if ((long)sx * sy * sz > (long)kScanTile * kScanTile) return rfail(R, VD_ERR_INVALID_ARG, "grid too large");
+    cudaStream_t st = R->st;
+    const float *g = sdf;
+    if (mem != VD_MEM_DEVICE) {
+        const size_t n = (size_t)sx * sy * sz;
+        if (n > R->cap_grid) {
+            rfree(R, R->grid);
+            R->grid = nullptr;
+            R->cap_grid = 0;
+            if (!ralloc(R, &R->grid, n)) return rfail(R, VD_ERR_OOM, "grid allocation failed");
+            R->cap_grid = n;
+        }
+        if (cudaMemcpyAsync(R->grid, sdf, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return rfail(R, VD_ERR_CUDA, "grid upload failed");
+        g = R->grid;
+    }
+    if (ncell > R->cap_cells) {
+        rfree(R, R->cnt);
+        rfree(R, R->off);
+        R->cnt = R->off = nullptr;
+        R->cap_cells = 0;
+        if (!ralloc(R, &R->cnt, (size_t)ncell) || !ralloc(R, &R->off, (size_t)ncell + 1))
+            return rfail(R, VD_ERR_OOM, "cell buffers");
+        R->cap_cells = ncell;
+    }
+    const Grid3 G{g, sx, sy, sz, origin[0], origin[1], origin[2], spacing, iso};
+    const int nb = blocks_for(ncell);
+    k_mc_count<<<nb, kThreads, 0, st>>>(G, R->table, R->cnt);
+    scan_launch(R->cnt, (int)ncell, R->off, R->total, R->sums, st);
+    k_mc_emit<<<nb, kThreads, 0, st>>>(G, R->table, R->off, R->max_tri, R->tri, R->nrm);
+    int total = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&total, R->total, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return rfail(R, VD_ERR_CUDA, "marching cubes launch failed");
+    if (n_triangles) *n_triangles = total;
+    R->n_tri = std::min(total, R->max_tri);
+    if (total > R->max_tri) return rfail(R, VD_ERR_INVALID_ARG, "more triangles than max_triangles");
+    return VD_OK;
+}
+
+vd_status vd_get_mesh(vd_renderer *R, float *tri, float *nrm, int mem) {
+    if (!R) return VD_ERR_INVALID_ARG;
+    const cudaMemcpyKind kind = mem == VD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t bytes = sizeof(float) * 9 * (size_t)R->n_tri;
+    if ((tri && cudaMemcpyAsync(tri, R->tri, bytes, kind, R->st) != cudaSuccess) ||
+        (nrm && cudaMemcpyAsync(nrm, R->nrm, bytes, kind, R->st) != cudaSuccess) ||
+        cudaStreamSynchronize(R->st) != cudaSuccess)
+        return rfail(R, VD_ERR_CUDA, "mesh download failed");
+    return VD_OK;
+}
+
+vd_status vd_render_samples(vd_renderer *R, const vd_lattice *lat, const float K[4], const float pose[12],
+                            int stride, float *pts, float *nrm, int *pix, int cap, int *count, int mem) {
+    if (!R) return VD_ERR_INVALID_ARG;
+    if (!K || stride < 1 || cap < 0 || (cap > 0 && (!pts || !nrm)) || !(K[0] > 0.f) || !(K[1] > 0.f))
+        return rfail(R, VD_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t st = lat ? lat->stream : R->st;
+    if (lat && cudaStreamSynchronize(R->st) != cudaSuccess) return rfail(R, VD_ERR_CUDA, "synchronize");
+    float ph[12];
+    for (int a = 0; a < 12; a++) ph[a] = pose ? pose[a] : ((a < 9 && a % 4 == 0) ? 1.f : 0.f);
+    if (cudaMemcpyAsync(R->pose_dev, ph, sizeof(ph), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return rfail(R, VD_ERR_CUDA, "pose upload failed");
+    Ctx c{};
+    if (lat) c = lat->c;
+    const int np = R->W * R->H;
+    const Cam cam{R->W, R->H, K[0], K[1], K[2], K[3]};
+    k_mesh_deform<<<blocks_for(3L * R->n_tri), kThreads, 0, st>>>(c, lat ? 1 : 0, R->tri, 3 * R->n_tri, R->pose_dev,
+                                                                   R->posed);
+    k_zbuf_clear<<<blocks_for(np), kThreads, 0, st>>>(R->zbuf, np);
+    k_raster<<<blocks_for(R->n_tri, 128), 128, 0, st>>>(R->posed, R->n_tri, cam, R->zbuf);
+    k_zbuf_flags<<<blocks_for(np), kThreads, 0, st>>>(R->zbuf, cam, stride, R->flag);
+    scan_launch(R->flag, np, R->poff, R->total + 1, R->sums, st);
+    const bool dev = mem == VD_MEM_DEVICE;
+    float *op = dev ? pts : R->stage, *on = dev ? nrm : R->stage + 3 * (size_t)np;
+    int *opix = dev ? pix : (pix ? reinterpret_cast<int *>(R->stage + 6 * (size_t)np) : nullptr);
+    const int wcap = dev ? cap : std::min(cap, np);
+    k_resolve<<<blocks_for(np), kThreads, 0, st>>>(R->zbuf, R->flag, R->poff, R->posed, R->tri, R->nrm, cam, wcap,
+                                                   op, on, opix);
+    int total = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&total, R->total + 1, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return rfail(R, VD_ERR_CUDA, "rasterisation launch failed");
+    if (count) *count = total;
+    if (!dev) {
+        const size_t n = (size_t)std::min(total, wcap);
+        if ((n && cudaMemcpy(pts, R->stage, 3 * n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) ||
+            (n && cudaMemcpy(nrm, R->stage + 3 * (size_t)np, 3 * n * sizeof(float), cudaMemcpyDeviceToHost) !=
+                      cudaSuccess) ||
+            (n && pix && cudaMemcpy(pix, R->stage + 6 * (size_t)np, n * sizeof(int), cudaMemcpyDeviceToHost) !=
+                             cudaSuccess))
+            return rfail(R, VD_ERR_CUDA, "sample download failed");
+    }
+    return VD_OK;
 }
 
 }  // extern "C"

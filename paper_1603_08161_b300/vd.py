@@ -103,6 +103,13 @@ _SIGS = {
     "vd_batch_set_plan": [_P, _I, _I, ctypes.c_longlong],
     "vd_unet_get_tensor": [_P, _I, _P, ctypes.c_longlong, _PI],
     "vd_estimate_pose": [_P, ctypes.POINTER(vd_solve_params), _I, _P, _PI, _PD],
+    "vd_mc_case": [_I, _PI],
+    "vd_renderer_create": [_I, _I, _I, ctypes.POINTER(_P)],
+    "vd_renderer_destroy": [_P],
+    "vd_renderer_last_error": [_P],
+    "vd_marching_cubes": [_P, _P, _I, _I, _I, _P, ctypes.c_float, ctypes.c_float, _I, _PI],
+    "vd_get_mesh": [_P, _P, _P, _I],
+    "vd_render_samples": [_P, _P, _P, _P, _I, _P, _P, _P, _I, _PI, _I],
     "vd_set_apply_mode": [_P, _I],
     "vd_get_apply_mode": [_P, _PI, _PI],
     "vd_tune_apply": [_P, ctypes.POINTER(vd_solve_params), _PI, ctypes.POINTER(ctypes.c_float)],
@@ -144,8 +151,8 @@ VD_NOALLOC_MAX_NODES = 65536
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
-    _fn.restype = (ctypes.c_char_p if _name in ("vd_last_error", "vd_batch_last_error", "vd_hierarchy_last_error")
-                   else ctypes.c_int)
+    _fn.restype = (ctypes.c_char_p if _name in ("vd_last_error", "vd_batch_last_error", "vd_hierarchy_last_error",
+                                                "vd_renderer_last_error") else ctypes.c_int)
     globals()[_name] = _fn
 
 
@@ -539,6 +546,68 @@ class Hierarchy:
         reps = (vd_solve_report * self.n_levels)()
         vd_hierarchy_get_reports(self.h, reps)
         return [r.as_dict() for r in reps]
+
+
+class Renderer:
+    """Canonical mesh by marching cubes and rasterised source samples (vd_renderer_*)."""
+
+    def __init__(self, max_triangles, W, H):
+        h = _P()
+        st = vd_renderer_create(int(max_triangles), int(W), int(H), ctypes.byref(h))
+        if st != VD_OK:
+            raise VDError(st, "vd_renderer_create failed")
+        self.h, self.W, self.H = h, int(W), int(H)
+        self.n_tri = 0
+
+    def _check(self, st):
+        if st != VD_OK:
+            raise VDError(st, (vd_renderer_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            vd_renderer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def marching_cubes(self, grid, origin, spacing, iso=0.0):
+        """grid: (sz, sy, sx) float32 numpy array or CUDA tensor; returns the triangle count."""
+        sz, sy, sx = grid.shape
+        pg, mem = _ptr(grid if not isinstance(grid, np.ndarray) else np.ascontiguousarray(grid, np.float32))
+        if isinstance(grid, np.ndarray):
+            self._g = np.ascontiguousarray(grid, np.float32)
+            pg = self._g.ctypes.data
+        o = np.ascontiguousarray(origin, np.float32)
+        n = ctypes.c_int()
+        self._check(vd_marching_cubes(self.h, pg, sx, sy, sz, o.ctypes.data, float(spacing), float(iso), mem,
+                                      ctypes.byref(n)))
+        self.n_tri = n.value
+        return n.value
+
+    def mesh(self):
+        t = np.zeros((self.n_tri, 3, 3), np.float32)
+        m = np.zeros((self.n_tri, 3, 3), np.float32)
+        self._check(vd_get_mesh(self.h, t.ctypes.data, m.ctypes.data, VD_MEM_HOST))
+        return t, m
+
+    def render(self, K, pose=None, lattice=None, stride=1, cap=None):
+        """(points (n, 3), normals (n, 3), pixel index (n,)) of the covered pixels, host."""
+        cap = self.W * self.H if cap is None else int(cap)
+        p = np.zeros((cap, 3), np.float32)
+        m = np.zeros((cap, 3), np.float32)
+        px = np.zeros(cap, np.int32)
+        kk = np.ascontiguousarray(K, np.float32)
+        pz = None if pose is None else np.ascontiguousarray(pose, np.float32)
+        n = ctypes.c_int()
+        self._check(vd_render_samples(self.h, None if lattice is None else lattice.h, kk.ctypes.data,
+                                      None if pz is None else pz.ctypes.data, int(stride), p.ctypes.data,
+                                      m.ctypes.data, px.ctypes.data, cap, ctypes.byref(n), VD_MEM_HOST))
+        k = min(n.value, cap)
+        return p[:k], m[:k], px[:k]
 
 
 class UNet:
