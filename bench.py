@@ -427,6 +427,51 @@ def main():
         variants["cached_btb"] = {"unit": "ms per 10 x 20 solve", "per_lattice": rows,
                                   "note": "same frame (36,266 samples) binned on each lattice"}
 
+    # source samples on the GPU (Sec. 4, 5.1): marching cubes of the canonical capsules'
+    # SDF on a 128^3 grid (once), then per frame the mesh rasterised at the lattice's warp
+    # (every 2nd pixel), vd_set_frame with those samples and the 10 x 20 solve
+    if not args.no_variants:
+        g, og, hs = synth.sdf_grid("capsules", n=128, seed=0)
+        Rr = vd.Renderer(4 << 20, fr.W, fr.H)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ntri = Rr.marching_cubes(g, og, hs)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_mc = ev0.elapsed_time(ev1)
+        cap = fr.W * fr.H
+        r_pts = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+        r_nrm = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+        Lr = vd.Lattice(fr.dims, fr.origin, fr.spacing, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
+        nsamp = [0]
+
+        def rstep():
+            n = Rr.render_into(r_pts, r_nrm, fr.K, fr.pose, Lr, stride=2)
+            nsamp[0] = n
+            Lr.set_correspondences(d_fh, d_ft)
+            Lr.set_frame(d_depth, fr.K, fr.pose, r_pts[:n], r_nrm[:n])
+            Lr.solve_async(prm)
+
+        for _ in range(args.warmup):
+            rstep()
+            Lr.report()
+        msr, _ = timed_pass(rstep, Lr)
+        rr = Lr.report()
+        # the rasterisation alone, at the final warp
+        ev0.record(stream)
+        for _ in range(10):
+            Rr.render_into(r_pts, r_nrm, fr.K, fr.pose, Lr, stride=2)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        mr = dist_max(statistics.mean(msr), world)
+        variants["source_samples"] = {
+            "value": world * 1000.0 / mr, "unit": "frames/s", "ms_per_step": mr,
+            "what": "per frame: rasterise the canonical mesh at the warp (every 2nd pixel), vd_set_frame, 10 x 20 solve",
+            "triangles": ntri, "marching_cubes_ms": ms_mc, "grid": "128^3 SDF of the canonical capsules",
+            "render_ms": ev0.elapsed_time(ev1) / 10, "samples": nsamp[0], "final_energy": rr["e_total"]}
+        Lr.close()
+        Rr.close()
+
     # batched form (32 independent lattices of uneven size, 16^3..96^3, their own
     # 160x120..640x480 frames): one tuned graph launch per batch, against the same
     # lattices solved one after another with vd_solve; frames are set before timing

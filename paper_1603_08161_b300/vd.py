@@ -594,6 +594,17 @@ class Renderer:
         self._check(vd_get_mesh(self.h, t.ctypes.data, m.ctypes.data, VD_MEM_HOST))
         return t, m
 
+    def render_into(self, pts, nrm, K, pose=None, lattice=None, stride=1):
+        """Samples into CUDA tensors pts, nrm (cap x 3 float32); returns the count."""
+        kk = np.ascontiguousarray(K, np.float32)
+        pz = None if pose is None else np.ascontiguousarray(pose, np.float32)
+        self._kp = (kk, pz)
+        n = ctypes.c_int()
+        self._check(vd_render_samples(self.h, None if lattice is None else lattice.h, kk.ctypes.data,
+                                      None if pz is None else pz.ctypes.data, int(stride), _ptr(pts)[0],
+                                      _ptr(nrm)[0], None, int(pts.shape[0]), ctypes.byref(n), VD_MEM_DEVICE))
+        return n.value
+
     def render(self, K, pose=None, lattice=None, stride=1, cap=None):
         """(points (n, 3), normals (n, 3), pixel index (n,)) of the covered pixels, host."""
         cap = self.W * self.H if cap is None else int(cap)

@@ -162,7 +162,9 @@ def test_bad_dims_rejected(env):
 #   * ReLU and rounding to BF16 (round to nearest even) are both non-decreasing, so a
 #     stored value computed from an FP32 sum within [y - e, y + e] of the exact y lies
 #     in [rne(relu(y - e)), rne(relu(y + e))];
-#   * a ReLU mask multiplies by exactly 0 or 1, taken from the stored activation.
+#   * a ReLU mask multiplies by exactly 0 or 1, taken from the stored activation;
+#   * the weights enter as BF16, the biases as the FP32 master values (added in the
+#     FP32 epilogue).
 # A wrong tap, a dropped edge voxel, a swapped operand or a missing skip path moves an
 # element by a whole term, far outside these intervals; the intervals are a few 1e-4
 # of sum|terms| wide (one BF16 step, 2^-8 relative, where rounding decides).
@@ -225,7 +227,8 @@ def test_every_kernel_element_by_element(env, dims):
     lam = 4.0
     net = vd.UNet(dims, seed=0)
     net.set_params(flat)
-    p = U.unpack(bf16(flat))
+    # the parameters as the kernels use them: BF16 weights, FP32 (master) biases
+    p = {name: (bf16(w), b) for name, (w, b) in U.unpack(flat.astype(np.float64)).items()}
     xin, tin = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     outf = torch.zeros((n, 3), device="cuda")
     net.forward(xin, outf)
