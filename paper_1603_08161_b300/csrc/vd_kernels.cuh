@@ -879,17 +879,18 @@ __device__ __forceinline__ void sub_sync(int bar_id, int nt) {
 
 template <int kOp, bool kAll, bool kFresh>
 __device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, float *dst, float *dst2, int cb, int ce,
-                                            float *tsm, float &part, int lt, int nt, int bar_id, int js = 0,
-                                            int je = 0x7fffffff) {
+                                            float *tsm, int tsm_cap, float &part, int lt, int nt, int bar_id,
+                                            int js = 0, int je = 0x7fffffff) {
     // the samples of cells [cb, ce), clipped to [js, je) (a cell may be shared with the
     // neighbouring range: each range adds its own samples' contributions)
     const int sb = max(c.occ_beg[cb], js), se = min(c.occ_beg[ce], je);
     const int items = kOp == kOpEnergy ? 1 : (ce - cb) * 8;
-    if (kOp != kOpEnergy && se - sb <= nt) {
-        // all the samples in one chunk: phase 1 once, then every round of (cell, corner)
-        // items reads the same factors
-        const int j = sb + lt;
-        if (j < se) {
+    if (kOp != kOpEnergy && se - sb <= tsm_cap) {
+        // all the samples' factors fit in shared memory (tsm_cap of them; a thread forms
+        // those of samples lt, lt + nt, ...): phase 1 once, then every round of (cell,
+        // corner) items reads the same factors
+        for (int j = sb + lt; j < se; j += nt) {
+            const int ls = j - sb;
             const int cl = c.cell[j];
             const float4 f4 = c.frac[j], g = load_rec(c, j);
             const float f[3] = {f4.x, f4.y, f4.z};
@@ -907,9 +908,9 @@ __device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, flo
             if (kOp == kOpApply) {
                 const float t = c.w_d * sv;
                 part += t * sv;
-                tsm[lt] = t;
+                tsm[ls] = t;
             } else {
-                tsm[lt] = -c.w_d * (sv + g.w);
+                tsm[ls] = -c.w_d * (sv + g.w);
             }
         }
         sub_sync(bar_id, nt);
@@ -1244,7 +1245,7 @@ __global__ void __launch_bounds__(kThreads) k_cells(Ctx c, Scal *sc, int K, int 
     // an equal share of the sorted samples per block (set up with the frame)
     const int4 cp = c.cell_part[blockIdx.x];
     if (cp.y > cp.x)
-        cells_block<kOp, kAll, false>(c, vec, dst, c.minv, cp.x, cp.y, tsm, part, threadIdx.x, blockDim.x, 0, cp.z,
+        cells_block<kOp, kAll, false>(c, vec, dst, c.minv, cp.x, cp.y, tsm, kThreads, part, threadIdx.x, blockDim.x, 0, cp.z,
                                       cp.w);
     // pairs spread one per block first: one SM issuing all their atomics would be the tail
     sparse_pairs<kOp, kAll, false>(c, vec, dst, c.minv, blockIdx.x + gridDim.x * threadIdx.x,
@@ -1548,6 +1549,7 @@ constexpr int kPcgThreads = 768;
 constexpr int kPcgMaxGroups = 2;  // float4 groups per thread: chunk <= 4 * 2 * 768
 constexpr int kPcgStencil = 512;                          // threads on the stencil in phase A
 constexpr int kPcgSample = kPcgThreads - kPcgStencil;      // threads on the samples in phase A
+constexpr int kPcgTsm = 1024;  // samples per CTA whose factors the single-pass sample phase keeps
 constexpr long long kBarrierCycles = 2000000000LL;
 
 struct PcgAux {
@@ -1683,7 +1685,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     // per own float4 group: 1 if a sample or a sparse pair touches one of its slots (its
     // J^T J p contributions arrive in c.q)
     __shared__ unsigned s_touch[kPcgMaxGroups * kPcgThreads / 32];
-    __shared__ float tsm[kPcgSample];
+    __shared__ float tsm[kPcgTsm];
     __shared__ float s_ab;
     float *sm = reinterpret_cast<float *>(sm4);
     const int chunk = ax.chunk;
@@ -1941,7 +1943,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                 for (int ci = cb + (lt >> 5); ci < ce; ci += kPcgSample >> 5)
                     btb_cell_apply<kAll, true>(c, pv, ci, c.q, part);
             } else if (s_ce > s_cb) {
-                cells_block<kOpApply, kAll, true>(c, pv, c.q, nullptr, s_cb, s_ce, tsm, part, lt, kPcgSample, 1, s_js,
+                cells_block<kOpApply, kAll, true>(c, pv, c.q, nullptr, s_cb, s_ce, tsm, kPcgTsm, part, lt, kPcgSample, 1, s_js,
                                                   s_je);
             }
             double pd = 0.0;
