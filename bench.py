@@ -480,11 +480,27 @@ def main():
         blats = []
         for bf in bframes:
             Lb = vd.Lattice(bf.dims, bf.origin, bf.spacing, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
+            Lb.set_apply_mode(vd.VD_APPLY_AUTO)     # cached B^T B where cells hold many samples
             Lb.set_frame_from(bf)
             blats.append(Lb)
         B = vd.Batch(blats)
         B.solve(prm)
+        # the persistent form (one cooperative launch per Gauss-Newton iteration for every
+        # lattice's position step), timed for the record before the tuner picks a plan
+        B.set_persistent(True, 512, 1, 4.0)
+        for _ in range(2):
+            B.solve(prm)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            B.solve_async(prm)
+            B.reports()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_persistent = e0.elapsed_time(e1) / 3
+        B.set_persistent(False)
         n_streams, _ = B.tune(prm)
+        plan = B.plan()
 
         def batch_step():
             B.solve_async(prm)
@@ -513,7 +529,8 @@ def main():
         variants["batched"] = {
             "value": world * len(blats) * 1000.0 / tb, "unit": "solves/s", "ms_per_batch": tb,
             "lattices": len(blats), "total_nodes": int(sum(int(np.prod(b.dims)) for b in bframes)),
-            "branches": n_streams, "launches_per_batch": B.launch_count(),
+            "branches": n_streams, "launches_per_batch": B.launch_count(), "tuned_plan": plan,
+            "persistent_form_ms": ms_persistent,
             "sequential_plain": {"value": world * len(blats) * 1000.0 / ts, "unit": "solves/s", "ms": ts},
             "speedup_vs_plain": ts / tb}
         B.close()

@@ -273,7 +273,9 @@ vd_status vd_batch_get_reports(vd_batch *batch, vd_solve_report *out);
  * of concurrent branches (1, 2, 4, ... up to the batch size) and branch order (largest
  * lattice first, or as given), then for the fastest of those each size threshold
  * (2^19, 2^17, 2^15, 2^13 active nodes) above which lattices run ahead with their
- * persistent position step; keep the fastest.  Runs the solve several times (the
+ * persistent position step, then the persistent form over every lattice
+ * (vd_batch_set_persistent) for 256 / 512 threads, 1 / 2 / 4 CTAs per SM, sample
+ * weights 1 / 4 and 8 / 16 branches; keep the fastest.  Runs the solve several times (the
  * lattices' warps change).  Reports the number of branches and the time per batched
  * solve (ms). */
 vd_status vd_batch_tune(vd_batch *batch, const vd_solve_params *params, int *streams, float *ms);
@@ -285,6 +287,22 @@ vd_status vd_batch_tune(vd_batch *batch, const vd_solve_params *params, int *str
  * lattice's size, e.g. 2^31 - 1, disables it; 0 makes every lattice run ahead).
  * VD_ERR_INVALID_ARG for NULL or out-of-range values. */
 vd_status vd_batch_set_plan(vd_batch *batch, int streams, int largest_first, long long run_ahead_nodes);
+
+/* Run the batch's position steps as one persistent cooperative kernel per Gauss-Newton
+ * iteration (on != 0): the CTAs, ctas_per_sm per SM, each of `threads` threads (256 or
+ * 512), are split among the lattices in proportion to (active nodes + sample_weight x
+ * samples), at least one each; each lattice's group runs its PCG (the recurrence of
+ * vd_solve, vectors in global memory) with its own barriers and reductions, and the
+ * other stages of the iteration run as per-lattice branches between these launches.
+ * on = 0 returns to the graph of per-lattice schedules.  VD_ERR_INVALID_ARG for other
+ * thread counts, ctas_per_sm outside [1, 8] or a negative weight; a setting the device
+ * cannot hold (the CTAs must all be resident) fails at the next solve. */
+vd_status vd_batch_set_persistent(vd_batch *batch, int on, int threads, int ctas_per_sm, float sample_weight);
+
+/* The batch's current plan (any pointer may be NULL): persistent form or not, its
+ * threads, CTAs per SM and sample weight, and the number of concurrent branches. */
+vd_status vd_batch_get_plan(const vd_batch *batch, int *persistent, int *threads, int *ctas_per_sm,
+                            float *sample_weight, int *streams);
 
 /* Kernel launches in one batched solve (after the first solve or tune). */
 vd_status vd_batch_launch_count(const vd_batch *batch, int *launches);

@@ -115,6 +115,8 @@ struct vd_lattice {
     bool gated = false;
     // learned warm start: features (6 nn), prediction (3 nn), backup of u and R (12 ld)
     float *warm = nullptr;
+    // persistent batched position step: published z and stencil q (6 ld), lazily allocated
+    float *batch_vecs = nullptr;
     // global pose estimation (dense projective ICP): device state, lazily allocated
     IcpState *icp = nullptr;
     // cached B^T B of the dense samples (per occupied cell, 24 x 24), VD_APPLY_*
@@ -553,8 +555,10 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     Lc.other();
 }
 
+// the stages of Gauss-Newton iteration g before its position step: association (unless
+// frozen), right-hand side and diagonal, the cached blocks
 template <bool kAll>
-void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
+void enqueue_gn_pre(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
     const Grid gr = grids(L);
     const Ctx c = L->c;
     Scal *sc = slot(L, g);
@@ -568,13 +572,15 @@ void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
     } else {
         enqueue_rhs<kAll>(Lc, c, sc, gr, K);  // the records, and so the cached blocks, are unchanged
     }
-    int G = 0, chunk = 0;
-    if (persistent_plan(L, &G, &chunk)) {
-        launch_persistent<kAll>(L, Lc, sc, K, P->cg_tol * P->cg_tol, 1, G, chunk);
-    } else {
-        enqueue_pcg<kAll>(Lc, c, sc, gr, K, P->cg_tol * P->cg_tol);
-        Lc.go(VD_KC_ROTATION, k_add_increment<kAll>, gr.node, kThreads, c, (const Scal *)sc);
-    }
+}
+
+// the stages after the position step: rotation fit, energies, the energy-target gate
+template <bool kAll>
+void enqueue_gn_post(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
+    const Grid gr = grids(L);
+    const Ctx c = L->c;
+    Scal *sc = slot(L, g);
+    const int K = P->cg_iters;
     Lc.go(VD_KC_ROTATION, k_fit_rotations<kAll, true>, gr.node, kThreads, c, sc);
     // the energies after the update (this iteration's correspondences): for the report
     // after the last iteration, and after every one when the energy target gates the next
@@ -582,19 +588,46 @@ void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
     if (c.e_target && g + 1 < P->gn_iters) Lc.go(-1, k_gn_gate, 1, 32, c, (const Scal *)sc, slot(L, g + 1));
 }
 
-void enqueue_solve(vd_lattice *L, const vd_solve_params *P, cudaStream_t st) {
-    Launcher Lc{L, st};
+template <bool kAll>
+void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
+    enqueue_gn_pre<kAll>(Lc, L, P, g);
+    const Grid gr = grids(L);
+    const Ctx c = L->c;
+    Scal *sc = slot(L, g);
+    const int K = P->cg_iters;
+    int G = 0, chunk = 0;
+    if (persistent_plan(L, &G, &chunk)) {
+        launch_persistent<kAll>(L, Lc, sc, K, P->cg_tol * P->cg_tol, 1, G, chunk);
+    } else {
+        enqueue_pcg<kAll>(Lc, c, sc, gr, K, P->cg_tol * P->cg_tol);
+        Lc.go(VD_KC_ROTATION, k_add_increment<kAll>, gr.node, kThreads, c, (const Scal *)sc);
+    }
+    enqueue_gn_post<kAll>(Lc, L, P, g);
+}
+
+// the start and the end of a solve: scalar blocks zeroed, the warp reset for VD_INIT_ZERO;
+// the report
+void enqueue_solve_begin(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, cudaStream_t st) {
     cudaMemsetAsync(L->scal, 0, L->scal_stride * (size_t)P->gn_iters, st);
     Lc.other();
     if (P->init == VD_INIT_ZERO)
         Lc.go(-1, k_reset_warp, blocks_for(L->c.nn), kThreads, L->u, L->R, L->c.nn, L->c.ld);
+}
+
+void enqueue_solve_end(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, cudaStream_t st) {
+    Lc.go(-1, k_finish_report, 1, 32, (Scal *)L->scal, L->scal_stride, P->gn_iters, L->c, L->rep_dev,
+          (const int *)(L->pcg_bar + 2));
+    cudaMemcpyAsync(L->rep_host, L->rep_dev, 11 * sizeof(double), cudaMemcpyDeviceToHost, st);
+}
+
+void enqueue_solve(vd_lattice *L, const vd_solve_params *P, cudaStream_t st) {
+    Launcher Lc{L, st};
+    enqueue_solve_begin(Lc, L, P, st);
     for (int g = 0; g < P->gn_iters; g++) {
         if (L->all) enqueue_gn<true>(Lc, L, P, g);
         else enqueue_gn<false>(Lc, L, P, g);
     }
-    Lc.go(-1, k_finish_report, 1, 32, (Scal *)L->scal, L->scal_stride, P->gn_iters, L->c, L->rep_dev,
-          (const int *)(L->pcg_bar + 2));
-    cudaMemcpyAsync(L->rep_host, L->rep_dev, 11 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    enqueue_solve_end(Lc, L, P, st);
 }
 
 // upper bound on the launches of one kernel class in a solve (sizes the event pool)
@@ -1388,6 +1421,18 @@ struct vd_batch {
     bool pending = false;
     int launches = 0;
     std::string err;
+    // persistent position step over every lattice (one cooperative launch per Gauss-Newton
+    // iteration): threads per CTA, CTAs per SM, weight of a sample against a node in the
+    // split of the CTAs among the lattices
+    bool persistent = false;
+    int pthreads = 512, pctas = 1;
+    float sample_weight = 2.f;
+    std::vector<void *> pbufs;       // items, barrier words, partial rows
+    PcgBatchItem *items = nullptr;
+    unsigned long long *words = nullptr;
+    double *part = nullptr;
+    size_t cap_items = 0, cap_words = 0, cap_part = 0;
+    std::vector<int> groups;         // CTAs per lattice of the last persistent build
 };
 
 namespace {
@@ -1406,6 +1451,10 @@ std::vector<char> batch_key(vd_batch *B, const vd_solve_params *P, int streams, 
     put(&streams, sizeof(streams));
     put(&largest, sizeof(largest));
     put(&coop_min, sizeof(coop_min));
+    put(&B->persistent, sizeof(B->persistent));
+    put(&B->pthreads, sizeof(B->pthreads));
+    put(&B->pctas, sizeof(B->pctas));
+    put(&B->sample_weight, sizeof(B->sample_weight));
     for (vd_lattice *L : B->L) {
         put(&L->gen, sizeof(L->gen));
         put(&L->c, sizeof(Ctx));
@@ -1425,9 +1474,19 @@ std::vector<int> batch_order(vd_batch *B, bool largest) {
     return o;
 }
 
+vd_status batch_build_persistent(vd_batch *B, const vd_solve_params *P, int streams, bool largest);
+
 vd_status batch_build(vd_batch *B, const vd_solve_params *P, int streams, bool largest, long coop_min) {
     std::vector<char> key = batch_key(B, P, streams, largest, coop_min);
     if (B->gexec && key == B->key) return VD_OK;
+    if (B->persistent) {
+        vd_status s = batch_build_persistent(B, P, streams, largest);
+        if (s == VD_OK) {
+            B->key = key;
+            B->gparams = *P;
+        }
+        return s;
+    }
     if (B->gexec) {
         cudaGraphExecDestroy(B->gexec);
         B->gexec = nullptr;
@@ -1497,6 +1556,227 @@ vd_status batch_build(vd_batch *B, const vd_solve_params *P, int streams, bool l
     return VD_OK;
 }
 
+template <typename T>
+vd_status bgrow(vd_batch *B, T **p, size_t *cap, size_t need) {
+    if (need <= *cap && *p) return VD_OK;
+    for (size_t k = 0; k < B->pbufs.size(); k++)
+        if (B->pbufs[k] == (void *)*p) {
+            cudaFree(*p);
+            B->pbufs.erase(B->pbufs.begin() + k);
+            break;
+        }
+    *p = nullptr;
+    *cap = 0;
+    void *q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(need, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(B, VD_ERR_OOM, "batch buffers");
+    }
+    B->pbufs.push_back(q);
+    *p = (T *)q;
+    *cap = need;
+    return VD_OK;
+}
+
+int batch_threads_ok(int t) { return t == 256 || t == 512; }
+
+int batch_occupancy(int threads) {
+    int occ = 0;
+    cudaError_t e = threads == 256
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_batch<256>, 256, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_batch<512>, 512, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return occ;
+}
+
+// One graph per batch: for every Gauss-Newton iteration, the lattices' stages before the
+// position step as branches on `streams` capture streams, then one cooperative launch of
+// k_pcg_batch for all position steps, then the stages after it as branches again.  The
+// CTAs (SMs x CTAs per SM) are split among the lattices in proportion to (active nodes +
+// sample_weight x samples), at least one each.
+vd_status batch_build_persistent(vd_batch *B, const vd_solve_params *P, int streams, bool largest) {
+    const int n = (int)B->L.size();
+    // a solve of the previous graph may still read the items and buffers rewritten below
+    if (cudaStreamSynchronize(B->L[0]->stream) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "synchronize");
+    const int K = P->cg_iters, GN = P->gn_iters;
+    const int occ = batch_occupancy(B->pthreads);
+    const int sms = B->L[0]->num_sms;
+    if (!B->L[0]->coop || occ < B->pctas || n > sms * B->pctas)
+        return bfail(B, VD_ERR_INVALID_ARG, "the persistent batch does not fit on the device with these settings");
+    const int T = sms * B->pctas;
+    while ((int)B->side.size() < streams) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "stream");
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "event");
+        B->side.push_back(st);
+        B->join.push_back(ev);
+    }
+    std::vector<double> w(n);
+    double W = 0.0;
+    for (int i = 0; i < n; i++) {
+        vd_lattice *L = B->L[i];
+        vd_status s = ensure_scal(L, GN, K);
+        if (s == VD_OK && !L->batch_vecs) s = dalloc(L, &L->batch_vecs, 6 * (size_t)L->c.ld);
+        if (s != VD_OK) return bfail(B, s, L->err.c_str());
+        set_params_ctx(L->c, P);
+        refresh_ctx(L);
+        const long N = active_nodes(L);
+        w[i] = (double)(4 * ((N + 3) / 4)) + (double)B->sample_weight * L->n_samples_h;
+        W += w[i];
+    }
+    // CTAs per lattice: at least one, the rest by the largest remainders; no more than
+    // 255 (the arrival count of a barrier word) or one per float4 group
+    std::vector<int> g(n, 1);
+    std::vector<std::pair<double, int>> rem;
+    int used = n;
+    for (int i = 0; i < n; i++) {
+        const double want = T * w[i] / std::max(W, 1.0);
+        const int extra = std::max(0, (int)want - 1);
+        g[i] += extra;
+        used += extra;
+        rem.push_back({want - (int)want, i});
+    }
+    std::sort(rem.begin(), rem.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first > b.first;
+    });
+    for (size_t k = 0; used < T && k < rem.size(); k++, used++) g[rem[k].second]++;
+    while (used > T) {  // forced minimums overshot: take CTAs back from the largest groups
+        int big = (int)(std::max_element(g.begin(), g.end()) - g.begin());
+        if (g[big] <= 1) break;
+        g[big]--;
+        used--;
+    }
+    long words_need = 0, part_need = 0;
+    std::vector<long> woff(n), poff(n);
+    std::vector<int> chunk(n), g0(n);
+    int start = 0;
+    for (int i = 0; i < n; i++) {
+        vd_lattice *L = B->L[i];
+        const long N = active_nodes(L), G4 = (N + 3) / 4;
+        g[i] = (int)std::max<long>(1, std::min<long>(std::min<long>(g[i], 255), G4));
+        chunk[i] = (int)(4 * ((G4 + g[i] - 1) / g[i]));
+        g0[i] = start;
+        start += g[i];
+        woff[i] = words_need;
+        words_need += 2 * K + 1;
+        poff[i] = part_need;
+        part_need += (long)(2 * K + 2) * g[i];
+    }
+    const int grid = start;
+    vd_status s = bgrow(B, &B->items, &B->cap_items, (size_t)GN * n);
+    if (s == VD_OK) s = bgrow(B, &B->words, &B->cap_words, (size_t)words_need);
+    if (s == VD_OK) s = bgrow(B, &B->part, &B->cap_part, (size_t)part_need);
+    if (s != VD_OK) return s;
+    std::vector<PcgBatchItem> items((size_t)GN * n);
+    for (int gi = 0; gi < GN; gi++)
+        for (int i = 0; i < n; i++) {
+            vd_lattice *L = B->L[i];
+            PcgBatchItem &it = items[(size_t)gi * n + i];
+            it.c = L->c;
+            it.sc = slot(L, gi);
+            it.part = B->part + poff[i];
+            it.words = B->words + woff[i];
+            it.z = L->batch_vecs;
+            it.qs = L->batch_vecs + 3 * (size_t)L->c.ld;
+            it.pbuf1 = L->vecs + 15 * (size_t)L->c.ld;
+            it.err = (int *)(L->pcg_bar + 2);
+            it.g0 = g0[i];
+            it.G = g[i];
+            it.chunk = chunk[i];
+            const unsigned long long two31 = 1ull << 31;
+            it.m_nx = (unsigned)((two31 + (unsigned long long)L->c.nx - 1) / (unsigned long long)L->c.nx);
+            it.m_ny = (unsigned)((two31 + (unsigned long long)L->c.ny - 1) / (unsigned long long)L->c.ny);
+        }
+    if (cudaMemcpy(B->items, items.data(), sizeof(PcgBatchItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(B, VD_ERR_CUDA, "item upload");
+    B->groups = g;
+    if (B->gexec) {
+        cudaGraphExecDestroy(B->gexec);
+        B->gexec = nullptr;
+    }
+    const std::vector<int> order = batch_order(B, largest);
+    if (cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bfail(B, VD_ERR_CUDA, "begin capture");
+    int launches = 0;
+    auto fork = [&]() {
+        cudaEventRecord(B->fork, B->cap);
+        for (int p = 0; p < streams; p++) cudaStreamWaitEvent(B->side[p], B->fork, 0);
+    };
+    auto joinall = [&]() {
+        for (int p = 0; p < streams; p++) {
+            cudaEventRecord(B->join[p], B->side[p]);
+            cudaStreamWaitEvent(B->cap, B->join[p], 0);
+        }
+    };
+    // the lattices' segments: before the first position step, and between position steps
+    auto segment = [&](int gi) {  // gi < 0: start + pre(0); else post(gi) + pre(gi + 1) or end
+        fork();
+        int k = 0;
+        for (int idx : order) {
+            vd_lattice *L = B->L[idx];
+            cudaStream_t st = B->side[k++ % streams];
+            const int saved = L->prof_class;
+            L->prof_class = -1;
+            L->counting = 0;
+            Launcher Lc{L, st};
+            if (gi < 0) {
+                enqueue_solve_begin(Lc, L, P, st);
+                cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), st);
+                Lc.other();
+            } else if (L->all) {
+                enqueue_gn_post<true>(Lc, L, P, gi);
+            } else {
+                enqueue_gn_post<false>(Lc, L, P, gi);
+            }
+            const int nxt = gi + 1;
+            if (nxt < GN) {
+                if (L->all) enqueue_gn_pre<true>(Lc, L, P, nxt);
+                else enqueue_gn_pre<false>(Lc, L, P, nxt);
+            } else {
+                enqueue_solve_end(Lc, L, P, st);
+            }
+            launches += L->counting;
+            L->prof_class = saved;
+        }
+        joinall();
+    };
+    segment(-1);
+    for (int gi = 0; gi < GN; gi++) {
+        cudaMemsetAsync(B->words, 0, sizeof(unsigned long long) * (size_t)words_need, B->cap);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(B->pthreads);
+        cfg.stream = B->cap;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const PcgBatchItem *its = B->items + (size_t)gi * n;
+        const double tol2 = P->cg_tol * P->cg_tol;
+        if (B->pthreads == 256) cudaLaunchKernelEx(&cfg, k_pcg_batch<256>, its, n, K, tol2, 1);
+        else cudaLaunchKernelEx(&cfg, k_pcg_batch<512>, its, n, K, tol2, 1);
+        launches++;
+        segment(gi);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&B->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(B, VD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    B->launches = launches;
+    return VD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1528,6 +1808,7 @@ vd_status vd_batch_destroy(vd_batch *B) {
     if (B->t0) cudaEventDestroy(B->t0);
     if (B->t1) cudaEventDestroy(B->t1);
     if (B->cap) cudaStreamDestroy(B->cap);
+    for (void *p : B->pbufs) cudaFree(p);
     delete B;
     return VD_OK;
 }
@@ -1620,6 +1901,46 @@ vd_status vd_batch_tune(vd_batch *B, const vd_solve_params *P, int *streams_out,
             best_c = cm;
         }
     }
+    // then the persistent position step over every lattice: threads per CTA, CTAs per SM,
+    // the sample weight of the CTA split, and the branches of the other stages
+    bool best_p = false;
+    int best_t = B->pthreads, best_k = B->pctas;
+    float best_w = B->sample_weight;
+    if (B->L[0]->coop) {
+        for (int th : {256, 512}) {
+            const int occ = batch_occupancy(th);
+            for (int k : {1, 2, 4}) {
+                if (k > occ || n > B->L[0]->num_sms * k) continue;
+                for (float sw : {1.f, 4.f})
+                    for (int st : {8, 16}) {
+                        if (st > n && st != 8) continue;
+                        B->persistent = true;
+                        B->pthreads = th;
+                        B->pctas = k;
+                        B->sample_weight = sw;
+                        float ms = 0.f;
+                        vd_status s = time_build(st, best_l, 0x7fffffffL, &ms);
+                        if (s != VD_OK) {
+                            B->err.clear();
+                            continue;
+                        }
+                        if (ms < best) {
+                            best = ms;
+                            best_p = true;
+                            best_t = th;
+                            best_k = k;
+                            best_w = sw;
+                            best_s = st;
+                            best_c = 0x7fffffffL;
+                        }
+                    }
+            }
+        }
+    }
+    B->persistent = best_p;
+    B->pthreads = best_t;
+    B->pctas = best_k;
+    B->sample_weight = best_w;
     B->streams = best_s;
     B->largest_first = best_l;
     B->coop_min = best_c;
@@ -1633,6 +1954,27 @@ vd_status vd_batch_set_plan(vd_batch *B, int streams, int largest_first, long lo
     B->streams = streams;
     B->largest_first = largest_first != 0;
     B->coop_min = run_ahead_nodes > 0x7fffffffLL ? 0x7fffffffL : (long)run_ahead_nodes;
+    return VD_OK;
+}
+
+vd_status vd_batch_set_persistent(vd_batch *B, int on, int threads, int ctas_per_sm, float sample_weight) {
+    if (!B || !batch_threads_ok(threads) || ctas_per_sm < 1 || ctas_per_sm > 8 || !(sample_weight >= 0.f))
+        return VD_ERR_INVALID_ARG;
+    B->persistent = on != 0;
+    B->pthreads = threads;
+    B->pctas = ctas_per_sm;
+    B->sample_weight = sample_weight;
+    return VD_OK;
+}
+
+vd_status vd_batch_get_plan(const vd_batch *B, int *persistent, int *threads, int *ctas_per_sm, float *sample_weight,
+                            int *streams) {
+    if (!B) return VD_ERR_INVALID_ARG;
+    if (persistent) *persistent = B->persistent ? 1 : 0;
+    if (threads) *threads = B->pthreads;
+    if (ctas_per_sm) *ctas_per_sm = B->pctas;
+    if (sample_weight) *sample_weight = B->sample_weight;
+    if (streams) *streams = B->streams > 0 ? B->streams : std::min<int>((int)B->L.size(), 8);
     return VD_OK;
 }
 

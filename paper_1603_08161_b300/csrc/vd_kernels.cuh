@@ -1574,9 +1574,10 @@ constexpr int kPcgMaxRows = 128;  // x-rows of one brick (bounds the plan's sear
 constexpr int kPcgMaxCtas = 255;  // the arrival count of a barrier word has 8 bits
 
 
-// Grid barrier that also reduces.  Each barrier of a launch has its own 64-bit word
-// (zeroed before the launch).  Thread 0 of each CTA writes the CTA's FP64 partial to
-// `row`, fences (publishing the CTA's writes) and adds to the word 1 (bits 0-7 count the
+// Grid barrier that also reduces, over the G CTAs that share `word` (a whole grid, or
+// one group of it: `bid` is the CTA's index in that group).  Each barrier of a launch
+// has its own 64-bit word (zeroed before the launch).  Thread 0 of each CTA writes the
+// CTA's FP64 partial to `row`, fences (publishing the CTA's writes) and adds to the word 1 (bits 0-7 count the
 // arrivals) plus, when a reference magnitude ref > 0 is given (the previous value of the
 // same sum: the same in every CTA), the partial in fixed point, round(part 2^(32 - e))
 // with ref = m 2^e, in bits 16-63 -- or 256 (bits 8-15) if it is not below 2^39.  Then it
@@ -1588,12 +1589,12 @@ constexpr int kPcgMaxCtas = 255;  // the arrival count of a barrier word has 8 b
 // otherwise every CTA sums `row` itself in CTA order.  Either way all CTAs get the same
 // `sum`.
 __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arrivals, double *row, unsigned long long *word,
-                                            double part, double ref, double &sum) {
+                                            double part, double ref, double &sum, unsigned bid) {
     __shared__ int s_ok, s_fast;
     __shared__ double s_sum;
     __syncthreads();
     if (threadIdx.x == 0) {
-        row[blockIdx.x] = part;
+        row[bid] = part;
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
         unsigned long long inc = 1;
         int e = 0;
@@ -1792,7 +1793,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     __syncthreads();
     double sum = 0.0;
     const unsigned arrivals = G + ax.extra;
-    bool ok = grid_reduce(ax.err, G, arrivals, ax.part, ax.words, block_total(part, red), 0.0, sum);
+    bool ok = grid_reduce(ax.err, G, arrivals, ax.part, ax.words, block_total(part, red), 0.0, sum, blockIdx.x);
     const double rho0 = ok ? sum : 0.0;
     double rho = rho0, pq_prev = 0.0;
     float beta = 0.f;
@@ -1950,7 +1951,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * lt, G * kPcgSample, part, pd);
         }
         ok = grid_reduce(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it, block_total(part, red),
-                         pq_prev, sum);
+                         pq_prev, sum, blockIdx.x);
         if (!ok) {
             stop = 1;
             break;
@@ -2008,7 +2009,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         }
         done = it + 1;
         ok = grid_reduce(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it, block_total(part, red), rho,
-                         sum);
+                         sum, blockIdx.x);
         if (!ok) {
             stop = 1;
             break;
@@ -2045,6 +2046,322 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         sc->cg_done = done;
         sc->stop = stop;
     }
+}
+
+// ------------------------------------------------------------------ batched position step (config 4)
+//
+// One cooperative launch runs the position step (Sec. 7.1) of every lattice of a batch.
+// The CTAs form one group per lattice (first CTA g0, G CTAs); each group runs the PCG
+// recurrence of k_pcg_persistent on its own lattice, with its own barrier words and FP64
+// partial rows, and never waits on another group.  The vectors stay in global memory (a
+// batch holds millions of nodes, more than the SMs' shared memory): each CTA owns a
+// contiguous range of the lattice's slots (a multiple of 4) and an equal share of its
+// sorted samples.  Per iteration:
+//   A: p = z + beta p_old for own slots (published), q_s = 2 w_r L p into qs (the
+//      neighbours' p formed from their published z and p_old, so no barrier is needed
+//      for p), the samples' and sparse pairs' J^T J p into the lattice's q by atomics,
+//      partial p.Ap -- group barrier + sum --
+//   B: x += alpha p, r -= alpha (q_s + q) (q cleared for the next iteration), z = Minv r
+//      (published), partial r.z -- group barrier + sum.
+struct PcgBatchItem {
+    Ctx c;                      // the lattice (slot-indexed vectors, samples, pairs)
+    Scal *sc;                   // this Gauss-Newton iteration's scalar block
+    double *part;               // (2K + 2) rows of G partials
+    unsigned long long *words;  // 2K + 1 barrier words, zeroed before the launch
+    float *z, *qs, *pbuf1;      // published z, stencil q, p of odd iterations (3 ld each)
+    int *err;                   // the lattice's error word (set when a barrier wait gives up)
+    int g0, G, chunk, pad;
+    // n / nx and n / ny as (2 n m) >> 32 with m = ceil(2^31 / d), exact for n d < 2^31
+    // (a slot over nx, then that quotient over ny)
+    unsigned m_nx, m_ny;
+};
+constexpr int kBatchTsm = 8192;  // samples per CTA whose factors the sample phase keeps
+
+template <bool kAll>
+__device__ __forceinline__ float batch_p(const PcgBatchItem &B, const float *pold, float beta, size_t i) {
+    return fmaf(beta, __ldcg(pold + i), __ldcg(B.z + i));
+}
+
+template <bool kAll>
+__device__ void pcg_batch_body(const PcgBatchItem &B, unsigned bid, int K, double tol2, int apply, double *red,
+                               float *tsm, int *s_rng, float *s_ab) {
+    const Ctx &c = B.c;
+    int *err = B.err;
+    Scal *sc = B.sc;
+    if (sc->skip) return;  // the same flag in every CTA of the group
+    const unsigned G = B.G;
+    const int N = active_count<kAll>(c);
+    const int N4 = 4 * groups4(N);
+    const int s_beg = (int)bid * B.chunk, s_end = min(s_beg + B.chunk, N4);
+    const int ng = s_end > s_beg ? (s_end - s_beg) >> 2 : 0;
+    const size_t ld = c.ld;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float w2 = 2.f * c.w_r;
+    const bool vec4 = kAll && (c.nx % 4 == 0);
+    if (tid == 0) {  // an equal share of the sorted samples and the occupied cells holding them
+        const int n_occ = *c.n_occ, ns = n_occ > 0 ? c.occ_beg[n_occ] : 0;
+        const int js = (int)(((long long)ns * bid) / G), je = (int)(((long long)ns * (bid + 1)) / G);
+        int lo = 0, hi = n_occ;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (c.occ_beg[m + 1] <= js) lo = m + 1;
+            else hi = m;
+        }
+        s_rng[0] = lo;
+        hi = n_occ;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (c.occ_beg[m] < je) lo = m + 1;
+            else hi = m;
+        }
+        s_rng[1] = je > js ? lo : s_rng[0];
+        s_rng[2] = js;
+        s_rng[3] = je;
+    }
+    // ---- init: Minv = 1/diag, z = Minv r, p_old = 0, x = 0, q = 0; rho0 = r.z
+    float part = 0.f;
+    for (int gl = tid; gl < ng; gl += nt) {
+        const int s = s_beg + 4 * gl;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const size_t o = a * ld + s;
+            const float4 dg = *reinterpret_cast<const float4 *>(c.minv + o);
+            const float4 rb = *reinterpret_cast<const float4 *>(c.r + o);
+            const float dv[4] = {dg.x, dg.y, dg.z, dg.w}, rv[4] = {rb.x, rb.y, rb.z, rb.w};
+            float mi[4], rr[4], z[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const bool in = s + e < N;
+                mi[e] = (in && dv[e] > 0.f) ? 1.0f / dv[e] : 0.f;
+                rr[e] = in ? rv[e] : 0.f;
+                z[e] = mi[e] * rr[e];
+                part += rr[e] * z[e];
+            }
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4 *>(c.minv + o) = make_float4(mi[0], mi[1], mi[2], mi[3]);
+            *reinterpret_cast<float4 *>(c.r + o) = make_float4(rr[0], rr[1], rr[2], rr[3]);
+            *reinterpret_cast<float4 *>(B.z + o) = make_float4(z[0], z[1], z[2], z[3]);
+            *reinterpret_cast<float4 *>(B.pbuf1 + o) = zero;
+            *reinterpret_cast<float4 *>(c.x + o) = zero;
+            *reinterpret_cast<float4 *>(c.q + o) = zero;
+        }
+    }
+    double sum = 0.0;
+    bool ok = grid_reduce(err, G, G, B.part, B.words, block_total(part, red), 0.0, sum, bid);
+    const double rho0 = ok ? sum : 0.0;
+    double rho = rho0, pq_prev = 0.0;
+    float beta = 0.f;
+    if (bid == 0 && tid == 0) scal_rho(sc)[0] = rho0;
+    int done = 0, stop = !ok;
+    const int cb = s_rng[0], ce = s_rng[1], js = s_rng[2], je = s_rng[3];
+    for (int it = 0; it < K && !stop; it++) {
+        if (!(rho > 0.0)) {
+            stop = 1;
+            break;
+        }
+        const float *__restrict__ pold = (it & 1) ? c.p : B.pbuf1;
+        float *__restrict__ pnew = (it & 1) ? B.pbuf1 : c.p;
+        part = 0.f;
+        // ---- A1 + A2: own p (published) and the stencil q_s = 2 w_r L p
+        for (int gl = tid; gl < ng; gl += nt) {
+            const int s0 = s_beg + 4 * gl;
+            if (vec4) {
+                const int x0 = s0 % c.nx, t = s0 / c.nx, y = t % c.ny, z = t / c.ny, pl = c.nx * c.ny;
+                const int offs[4] = {-c.nx, c.nx, -pl, pl};
+                const bool has[4] = {y > 0, y + 1 < c.ny, z > 0, z + 1 < c.nz};
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const size_t o = a * ld;
+                    const float4 zz = __ldcg(reinterpret_cast<const float4 *>(B.z + o + s0));
+                    const float4 oo = __ldcg(reinterpret_cast<const float4 *>(pold + o + s0));
+                    const float4 pc = make_float4(fmaf(beta, oo.x, zz.x), fmaf(beta, oo.y, zz.y), fmaf(beta, oo.z, zz.z),
+                                                  fmaf(beta, oo.w, zz.w));
+                    *reinterpret_cast<float4 *>(pnew + o + s0) = pc;
+                    const float left = x0 > 0 ? batch_p<kAll>(B, pold, beta, o + s0 - 1) : pc.x;
+                    const float right = x0 + 4 < c.nx ? batch_p<kAll>(B, pold, beta, o + s0 + 4) : pc.w;
+                    float4 d = make_float4((pc.x - left) + (pc.x - pc.y), (pc.y - pc.x) + (pc.y - pc.z),
+                                           (pc.z - pc.y) + (pc.z - pc.w), (pc.w - pc.z) + (pc.w - right));
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        if (!has[k]) continue;
+                        const float4 z4 = __ldcg(reinterpret_cast<const float4 *>(B.z + o + s0 + offs[k]));
+                        const float4 o4 = __ldcg(reinterpret_cast<const float4 *>(pold + o + s0 + offs[k]));
+                        d.x += pc.x - fmaf(beta, o4.x, z4.x);
+                        d.y += pc.y - fmaf(beta, o4.y, z4.y);
+                        d.z += pc.z - fmaf(beta, o4.z, z4.z);
+                        d.w += pc.w - fmaf(beta, o4.w, z4.w);
+                    }
+                    d = make_float4(w2 * d.x, w2 * d.y, w2 * d.z, w2 * d.w);
+                    *reinterpret_cast<float4 *>(B.qs + o + s0) = d;
+                    part += pc.x * d.x + pc.y * d.y + pc.z * d.z + pc.w * d.w;
+                }
+            } else {  // A1 only here: the stencil follows once every own p is published
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const size_t o = a * ld + s0;
+                    const float4 zz = __ldcg(reinterpret_cast<const float4 *>(B.z + o));
+                    const float4 oo = __ldcg(reinterpret_cast<const float4 *>(pold + o));
+                    *reinterpret_cast<float4 *>(pnew + o) = make_float4(fmaf(beta, oo.x, zz.x), fmaf(beta, oo.y, zz.y),
+                                                                        fmaf(beta, oo.z, zz.z), fmaf(beta, oo.w, zz.w));
+                }
+            }
+        }
+        if (!vec4) {
+            // A2 slot by slot (coalesced across the threads): a neighbour in this CTA's range
+            // reads the p just published (visible to the block after the barrier), another
+            // CTA's is formed from its z and p_old
+            __syncthreads();
+            for (int si = s_beg + tid; si < s_end; si += nt) {
+                float pi[3], q3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int a = 0; a < 3; a++) pi[a] = pnew[a * ld + si];
+                if (si < N) {
+                    int nb[6];
+                    if (kAll) {
+                        const int x = (int)(__umulhi(2u * (unsigned)si, B.m_nx));  // si / nx
+                        const int xr = si - x * c.nx;
+                        const int pl = c.nx * c.ny;
+                        const int zq = (int)(__umulhi(2u * (unsigned)x, B.m_ny));  // (si / nx) / ny
+                        const int yq = x - zq * c.ny;
+                        nb[0] = xr > 0 ? si - 1 : -1;
+                        nb[1] = xr + 1 < c.nx ? si + 1 : -1;
+                        nb[2] = yq > 0 ? si - c.nx : -1;
+                        nb[3] = yq + 1 < c.ny ? si + c.nx : -1;
+                        nb[4] = zq > 0 ? si - pl : -1;
+                        nb[5] = zq + 1 < c.nz ? si + pl : -1;
+                    } else {
+                        neighbours<kAll>(c, si, nb);
+                    }
+#pragma unroll
+                    for (int d = 0; d < 6; d++) {
+                        const int sj = nb[d];
+                        if (sj < 0) continue;
+                        const bool own = sj >= s_beg && sj < s_end;
+#pragma unroll
+                        for (int a = 0; a < 3; a++)
+                            q3[a] += pi[a] - (own ? pnew[a * ld + sj] : batch_p<kAll>(B, pold, beta, a * ld + sj));
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        q3[a] *= w2;
+                        part += pi[a] * q3[a];
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 3; a++) B.qs[a * ld + si] = q3[a];
+            }
+        }
+        // ---- A3: the samples' and sparse pairs' J^T J p (p formed from z and p_old): the
+        // cached blocks (an equal share of the occupied cells, a warp per cell) where the
+        // lattice has them, else the samples themselves
+        const VecView pv{B.z, pold, beta};
+        if (c.btb) {
+            const int n_occ = *c.n_occ;
+            const int cb2 = (int)(((long long)n_occ * bid) / G), ce2 = (int)(((long long)n_occ * (bid + 1)) / G);
+            for (int ci = cb2 + (tid >> 5); ci < ce2; ci += nt >> 5) btb_cell_apply<kAll, true>(c, pv, ci, c.q, part);
+        } else if (ce > cb) {
+            cells_block<kOpApply, kAll, true>(c, pv, c.q, nullptr, cb, ce, tsm, kBatchTsm, part, tid, nt, 0, js, je);
+        }
+        double pd = 0.0;
+        sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, bid + G * tid, G * nt, part, pd);
+        ok = grid_reduce(err, G, G, B.part + (size_t)(K + 1 + it) * G, B.words + 1 + 2 * it, block_total(part, red),
+                         pq_prev, sum, bid);
+        if (!ok) {
+            stop = 1;
+            break;
+        }
+        const double pq = sum;
+        pq_prev = pq;
+        if (!(pq > 0.0)) {
+            stop = 1;
+            break;
+        }
+        if (tid == 0) {
+            *s_ab = (float)(rho / pq);
+            if (bid == 0) scal_pq(sc, K)[it] = pq;
+        }
+        __syncthreads();
+        const float alpha = *s_ab;
+        // ---- B: x += alpha p, r -= alpha (q_s + q), q = 0, z = Minv r (published); r.z
+        part = 0.f;
+        for (int gl = tid; gl < ng; gl += nt) {
+            const int s = s_beg + 4 * gl;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const size_t o = a * ld + s;
+                const float4 pv4 = *reinterpret_cast<const float4 *>(pnew + o);
+                const float4 q1 = *reinterpret_cast<const float4 *>(B.qs + o);
+                const float4 q2 = __ldcg(reinterpret_cast<const float4 *>(c.q + o));
+                const float4 rv = *reinterpret_cast<const float4 *>(c.r + o);
+                const float4 mv = *reinterpret_cast<const float4 *>(c.minv + o);
+                const float4 xv = *reinterpret_cast<const float4 *>(c.x + o);
+                *reinterpret_cast<float4 *>(c.q + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 qv = f4add(q1, q2);
+                *reinterpret_cast<float4 *>(c.x + o) = make_float4(fmaf(alpha, pv4.x, xv.x), fmaf(alpha, pv4.y, xv.y),
+                                                                   fmaf(alpha, pv4.z, xv.z), fmaf(alpha, pv4.w, xv.w));
+                const float4 rn = make_float4(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y),
+                                              fmaf(-alpha, qv.z, rv.z), fmaf(-alpha, qv.w, rv.w));
+                const float4 zn = make_float4(mv.x * rn.x, mv.y * rn.y, mv.z * rn.z, mv.w * rn.w);
+                *reinterpret_cast<float4 *>(c.r + o) = rn;
+                *reinterpret_cast<float4 *>(B.z + o) = zn;
+                part += rn.x * zn.x + rn.y * zn.y + rn.z * zn.z + rn.w * zn.w;
+            }
+        }
+        done = it + 1;
+        ok = grid_reduce(err, G, G, B.part + (size_t)(it + 1) * G, B.words + 2 + 2 * it, block_total(part, red), rho, sum,
+                         bid);
+        if (!ok) {
+            stop = 1;
+            break;
+        }
+        const double rho1 = sum;
+        if (bid == 0 && tid == 0) scal_rho(sc)[it + 1] = rho1;
+        if (rho1 <= tol2 * rho0) {
+            stop = 1;
+            break;
+        }
+        if (tid == 0) *s_ab = (float)(rho1 / rho);
+        __syncthreads();
+        beta = *s_ab;
+        rho = rho1;
+    }
+    // ---- u += x when the step is applied
+    if (apply)
+        for (int gl = tid; gl < ng; gl += nt) {
+            const int s = s_beg + 4 * gl;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    if (s + e < N) c.u[a * ld + slot_node<kAll>(c, s + e)] += c.x[a * ld + s + e];
+        }
+    if (bid == 0 && tid == 0) {
+        sc->cg_done = done;
+        sc->stop = stop;
+    }
+}
+
+template <int kThreadsB>
+__global__ void __launch_bounds__(kThreadsB) k_pcg_batch(const PcgBatchItem *__restrict__ items, int n_items, int K,
+                                                          double tol2, int apply) {
+    __shared__ PcgBatchItem s_it;
+    __shared__ double red[32];
+    __shared__ float tsm[kBatchTsm];
+    __shared__ int s_rng[4];
+    __shared__ float s_ab;
+    if (threadIdx.x == 0) {  // the CTA's group: the last item whose first CTA is at or before this one
+        int lo = 0, hi = n_items;
+        while (hi - lo > 1) {
+            const int m = (lo + hi) >> 1;
+            if (items[m].g0 <= (int)blockIdx.x) lo = m;
+            else hi = m;
+        }
+        s_it = items[lo];
+    }
+    __syncthreads();
+    const unsigned bid = blockIdx.x - (unsigned)s_it.g0;
+    if (s_it.c.slot_of_node) pcg_batch_body<false>(s_it, bid, K, tol2, apply, red, tsm, s_rng, &s_ab);
+    else pcg_batch_body<true>(s_it, bid, K, tol2, apply, red, tsm, s_rng, &s_ab);
 }
 
 // ------------------------------------------------------------------ rotation step (Sec. 7.1)

@@ -101,6 +101,8 @@ _SIGS = {
     "vd_launch_counts": [_P, ctypes.POINTER(vd_solve_params), _PI, _PI],
     "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
     "vd_batch_set_plan": [_P, _I, _I, ctypes.c_longlong],
+    "vd_batch_set_persistent": [_P, _I, _I, _I, ctypes.c_float],
+    "vd_batch_get_plan": [_P, _PI, _PI, _PI, ctypes.POINTER(ctypes.c_float), _PI],
     "vd_unet_get_tensor": [_P, _I, _P, ctypes.c_longlong, _PI],
     "vd_estimate_pose": [_P, ctypes.POINTER(vd_solve_params), _I, _P, _PI, _PD],
     "vd_mc_case": [_I, _PI],
@@ -470,6 +472,18 @@ class Batch:
 
     def set_plan(self, streams, largest_first=True, run_ahead_nodes=(1 << 31) - 1):
         self._check(vd_batch_set_plan(self.h, int(streams), int(bool(largest_first)), int(run_ahead_nodes)))
+
+    def set_persistent(self, on=True, threads=512, ctas_per_sm=1, sample_weight=2.0):
+        self._check(vd_batch_set_persistent(self.h, int(bool(on)), int(threads), int(ctas_per_sm),
+                                            float(sample_weight)))
+
+    def plan(self):
+        p, t, k, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        w = ctypes.c_float()
+        self._check(vd_batch_get_plan(self.h, ctypes.byref(p), ctypes.byref(t), ctypes.byref(k), ctypes.byref(w),
+                                      ctypes.byref(st)))
+        return {"persistent": bool(p.value), "threads": t.value, "ctas_per_sm": k.value,
+                "sample_weight": w.value, "branches": st.value}
 
 
 class _LevelView(Lattice):

@@ -110,3 +110,54 @@ def test_batch_run_ahead_persistent_branch(vd):
         print(f"batch run-ahead {fr.dims}: |du|max = {err / fr.spacing:.2e} h, dE/E = {rel:.2e}")
         assert err <= 1e-4 * fr.spacing
         assert rel <= 1e-5
+
+
+@pytest.mark.parametrize("threads,ctas,weight", [(512, 1, 2.0), (256, 2, 1.0), (256, 1, 4.0)])
+def test_persistent_batch_matches_oracle(vd, threads, ctas, weight):
+    """The batch's position steps as one persistent cooperative kernel per Gauss-Newton
+    iteration (one CTA group per lattice, vectors in global memory), the other stages as
+    branches: every lattice matches the oracle and its own vd_solve."""
+    items = _frames()
+    prm = vd.params(gn_iters=4, cg_iters=10, fixed_association=True, init=vd.VD_INIT_ZERO)
+    lats = [_lattice(vd, m, fr) for m, fr in items]
+    batch = vd.Batch(lats)
+    batch.set_persistent(True, threads, ctas, weight)
+    reps = batch.solve(prm)
+    assert batch.plan()["persistent"]
+    with pytest.raises(vd.VDError):       # more resident CTAs than the device holds
+        other = vd.Batch(lats)
+        other.set_persistent(True, 512, 8, 1.0)
+        other.solve(prm)
+    for (mode, fr), lat, rep in zip(items, lats, reps):
+        assert rep["status"] == vd.VD_OK
+        u, _ = lat.get_warp()
+        ref = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL if mode == "all" else oracle.ACTIVE_SURFACE)
+        res = ref.solve(4, 10, fixed_association=True)
+        u0, _ = ref.get_warp()
+        assert np.abs(u - u0).max() <= 1e-4 * fr.spacing
+        assert abs(rep["e_total"] - res["energy"][-1, 0]) <= 1e-5 * res["energy"][-1, 0]
+        assert rep["cg_done"] == int(res["cg_done"][-1])
+    # a second solve replays the same graph
+    again = batch.solve(prm)
+    for a, b in zip(reps, again):
+        assert abs(a["e_total"] - b["e_total"]) <= 1e-6 * a["e_total"]
+
+
+def test_persistent_batch_free_association_and_tune(vd):
+    items = _frames()[:4]
+    prm = vd.params(gn_iters=3, cg_iters=8, init=vd.VD_INIT_ZERO)
+    lats = [_lattice(vd, m, fr) for m, fr in items]
+    batch = vd.Batch(lats)
+    batch.set_persistent(True, 512, 1, 2.0)
+    first = batch.solve(prm)
+    for (mode, fr), lat, rep in zip(items, lats, first):
+        ref = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL if mode == "all" else oracle.ACTIVE_SURFACE)
+        res = ref.solve(3, 8, fixed_association=False)
+        assert abs(rep["e_total"] - res["energy"][-1, 0]) <= 1e-5 * res["energy"][-1, 0]
+    streams, ms = batch.tune(prm)
+    plan = batch.plan()
+    print(f"tuned batch: {plan}, {ms:.3f} ms")
+    again = batch.solve(prm)
+    for a, b in zip(first, again):
+        assert a["n_valid_corr"] == b["n_valid_corr"]
+        assert abs(a["e_total"] - b["e_total"]) <= 1e-5 * a["e_total"]
