@@ -470,6 +470,19 @@ vd_status vd_set_energy_target(vd_lattice *lat, double e_target);
  * step (no cooperative launch) are unaffected.  Returns VD_ERR_INVALID_ARG for NULL. */
 vd_status vd_test_stall_barrier(vd_lattice *lat, int on);
 
+/* ---- check of the position step's grid reduction (tests; the paper has no counterpart) ----
+ *
+ * Runs `rounds` reductions of G per-CTA FP64 partials (parts: rounds x G, host) through
+ * the barrier reduction of the persistent position step, in a cooperative launch of G
+ * CTAs (G <= the SM count), round k using round k-1's sum as the scale of its
+ * fixed-point path (as the position step uses the previous p.Ap or r.z); out (host,
+ * 2 x rounds doubles) gets per round the barrier's sum and the FP64 sum of the partials
+ * in CTA order.  The barrier's sum agrees with the row sum to FP64 rounding when the
+ * round takes the row path (no positive previous sum, a partial too large, or a sum below
+ * 1/16 of the scale, as after a sharp drop), and to 3e-7 relative on the fixed-point path.  Allocates and frees its own
+ * device memory; VD_ERR_INVALID_ARG without cooperative launches or for bad sizes. */
+vd_status vd_test_grid_reduce(const double *parts, int G, int rounds, double *out);
+
 /* ---- learned warm start (the paper has no counterpart: Sec. 7.1 starts each frame from
  * the previous frame's warp) ----
  *

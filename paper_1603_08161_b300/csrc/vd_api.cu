@@ -460,9 +460,10 @@ void enqueue_pcg(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K, do
     }
 }
 
-// 9 floats per slot in shared memory (at most 225,792 bytes + 4 KB static), and at most
-// kPcgMaxGroups float4 groups per thread
-constexpr int kPcgMaxChunk = std::min(6272, 4 * kPcgMaxGroups * kPcgThreads);
+// 6 floats per slot in shared memory (p and z / q; r and x are in tensor memory), and
+// at most kPcgMaxGroups float4 groups per thread
+constexpr int kPcgMaxChunk = 4 * kPcgMaxGroups * kPcgThreads;
+constexpr int kPcgSmemPerSlot = 24;
 
 // Bricks of by x bz full x-rows for the persistent position step of an all-nodes
 // lattice (nx % 4 == 0): the fewest slots per CTA within the SM count, and among those
@@ -537,7 +538,7 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(kPcgThreads);
-    cfg.dynamicSmemBytes = (size_t)36 * chunk;
+    cfg.dynamicSmemBytes = (size_t)kPcgSmemPerSlot * chunk;
     cfg.stream = Lc.st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -828,7 +829,7 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
             L->coop = coop != 0;
             L->num_sms = sms;
         }
-        const int bytes = 36 * kPcgMaxChunk;
+        const int bytes = kPcgSmemPerSlot * kPcgMaxChunk;
         if (cudaFuncSetAttribute(k_pcg_persistent<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
             cudaFuncSetAttribute(k_pcg_persistent<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
             cudaFuncSetAttribute(k_pcg_persistent<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) {
@@ -2149,6 +2150,55 @@ vd_status vd_test_stall_barrier(vd_lattice *L, int on) {
     L->stall_extra = on ? 1 : 0;
     L->ggen = -1;  // the flag is a launch argument of the captured graph: re-capture
     return VD_OK;
+}
+
+vd_status vd_test_grid_reduce(const double *parts, int G, int rounds, double *out) {
+    if (!parts || !out || G < 1 || G > 148 || rounds < 1 || rounds > 4096) return VD_ERR_INVALID_ARG;
+    int dev = 0, coop = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) || !coop || G > sms) {
+        cudaGetLastError();
+        return VD_ERR_INVALID_ARG;
+    }
+    const size_t np = (size_t)rounds * G;
+    double *d_parts = nullptr, *d_rows = nullptr, *d_out = nullptr;
+    unsigned long long *d_words = nullptr;
+    int *d_err = nullptr;
+    vd_status st = VD_OK;
+    if (cudaMalloc(&d_parts, np * sizeof(double)) || cudaMalloc(&d_rows, np * sizeof(double)) ||
+        cudaMalloc(&d_out, 2 * (size_t)rounds * sizeof(double)) ||
+        cudaMalloc(&d_words, (size_t)rounds * sizeof(unsigned long long)) || cudaMalloc(&d_err, sizeof(int))) {
+        st = VD_ERR_OOM;
+    } else if (cudaMemcpy(d_parts, parts, np * sizeof(double), cudaMemcpyHostToDevice) ||
+               cudaMemset(d_words, 0, (size_t)rounds * sizeof(unsigned long long)) ||
+               cudaMemset(d_err, 0, sizeof(int)) || cudaMemset(d_out, 0, 2 * (size_t)rounds * sizeof(double))) {
+        st = VD_ERR_CUDA;
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(G);
+        cfg.blockDim = dim3(64);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int herr = 0;
+        if (cudaLaunchKernelEx(&cfg, k_test_grid_reduce, (const double *)d_parts, rounds, d_rows, d_words, d_err,
+                               d_out) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(out, d_out, 2 * (size_t)rounds * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = VD_ERR_CUDA;
+        else if (herr)
+            st = VD_ERR_TIMEOUT;
+    }
+    cudaGetLastError();
+    cudaFree(d_parts);
+    cudaFree(d_rows);
+    cudaFree(d_out);
+    cudaFree(d_words);
+    cudaFree(d_err);
+    return st;
 }
 
 vd_status vd_set_energy_target(vd_lattice *L, double e_target) {

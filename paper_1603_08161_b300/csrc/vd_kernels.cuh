@@ -1016,6 +1016,72 @@ __device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, flo
     }
 }
 
+// The samples' J^T J p (Eq. 2, kOpApply above) of the sorted samples [js, je), in
+// chunks of 32 consecutive samples per warp (lane l takes sample j0 + l): every lane
+// forms its sample's t = w_d g.(sum_k alpha_k p_k) and the 24 products alpha_k t g_a
+// (corner k, component a, at index 3 k + a); a segmented suffix sum over the lanes of
+// the same cell (the samples are sorted by cell, so a cell's lanes are contiguous)
+// leaves the sums of each cell's lanes in its first lane, which adds them to dst.
+// An equal number of samples per warp, whatever their spread over cells.
+// part += t (g.(sum alpha p)) per sample.
+template <bool kAll>
+__device__ __forceinline__ void samples_warp_apply(const Ctx &c, const VecView &vec, float *dst, int js, int je,
+                                                   float &part, int lt, int nt) {
+    const int lane = lt & 31;
+    for (int j0 = js + (lt & ~31); j0 < je; j0 += nt) {  // the same trip count in every lane of a warp
+        const int j = j0 + lane;
+        const bool has = j < je;
+        int cl = -1;
+        float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f), g = f4;
+        if (has) {
+            cl = c.cell[j];
+            f4 = c.frac[j];
+            g = load_rec(c, j);
+        }
+        const float f[3] = {f4.x, f4.y, f4.z};
+        float al[8], sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            al[k] = trilinear_weight(f, k);
+            if (has) {
+                const int vi = node_slot<kAll>(c, corner_node(c, cl, k));
+                sx += al[k] * ldvv<true>(vec, vi);
+                sy += al[k] * ldvv<true>(vec, c.ld + vi);
+                sz += al[k] * ldvv<true>(vec, 2 * (size_t)c.ld + vi);
+            }
+        }
+        const float sv = g.x * sx + g.y * sy + g.z * sz;
+        const float t = has ? c.w_d * sv : 0.f;
+        part += t * sv;
+        const float tg[3] = {t * g.x, t * g.y, t * g.z};
+        float v[24];
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) v[3 * k + a] = al[k] * tg[a];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int ko = __shfl_down_sync(FULL, cl, off);
+            const bool same = lane + off < 32 && ko == cl;
+#pragma unroll
+            for (int i = 0; i < 24; i++) {
+                const float o = __shfl_down_sync(FULL, v[i], off);
+                if (same) v[i] += o;
+            }
+        }
+        const int kp = __shfl_up_sync(FULL, cl, 1);
+        if (has && (lane == 0 || kp != cl)) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int sl = node_slot<kAll>(c, corner_node(c, cl, k));
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    if (v[3 * k + a] != 0.f) atomicAdd(&dst[(size_t)a * c.ld + sl], v[3 * k + a]);
+            }
+        }
+    }
+}
+
 // Sparse pairs (Eq. 3), one thread per pair; d = R_g (f^ + sum alpha u) + t_g - f in FP64.
 //   kOpRhs:    r_k -= w_s alpha_k R_g^T d,  diag_k += w_s alpha_k^2 |R_g col|^2
 //   kOpApply:  q_k += w_s alpha_k R_g^T R_g sum alpha p;  part += w_s |R_g sum alpha p|^2
@@ -1549,7 +1615,45 @@ constexpr int kPcgThreads = 768;
 constexpr int kPcgMaxGroups = 2;  // float4 groups per thread: chunk <= 4 * 2 * 768
 constexpr int kPcgStencil = 512;                          // threads on the stencil in phase A
 constexpr int kPcgSample = kPcgThreads - kPcgStencil;      // threads on the samples in phase A
-constexpr int kPcgTsm = 1024;  // samples per CTA whose factors the single-pass sample phase keeps
+constexpr int kPcgStencilGroups = kPcgMaxGroups * kPcgThreads / kPcgStencil;  // per stencil thread
+static_assert(kPcgStencilGroups * kPcgStencil == kPcgMaxGroups * kPcgThreads, "the stencil threads cover the chunk");
+// Tensor memory of the persistent position step: warp w reads and writes TMEM lanes
+// 32 (w % 4) .. + 31 (one lane per thread), columns 64 (w / 4) .. + 63: r of its
+// kPcgMaxGroups groups of phase B (12 columns each, component a at + 4 a), then, for a
+// stencil thread, x of its kPcgStencilGroups groups of A1
+constexpr int kPcgTmemCols = 512;
+constexpr int kPcgTmemX = 12 * kPcgMaxGroups;
+static_assert(64 * (kPcgThreads / 128) <= kPcgTmemCols && kPcgTmemX + 12 * kPcgStencilGroups <= 64, "TMEM slices");
+
+// 12 consecutive TMEM columns of this thread's lane to / from three float4 (tcgen05.ld
+// and its wait in one statement, so that no register is read before the data arrive;
+// warp-collective: every lane of the warp executes it)
+__device__ __forceinline__ void tmem_ld12(uint32_t ta, float4 (&v)[3]) {
+    uint32_t r[12];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%12];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%13];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
+        : "r"(ta), "r"(ta + 8)
+        : "memory");
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        v[a] = make_float4(__uint_as_float(r[4 * a]), __uint_as_float(r[4 * a + 1]), __uint_as_float(r[4 * a + 2]),
+                           __uint_as_float(r[4 * a + 3]));
+}
+__device__ __forceinline__ void tmem_st12(uint32_t ta, const float4 (&v)[3]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2,%3,%4,%5,%6,%7,%8,%9};\n"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%1], {%10,%11,%12,%13};\n" ::"r"(ta),
+        "r"(ta + 8), "r"(__float_as_uint(v[0].x)), "r"(__float_as_uint(v[0].y)), "r"(__float_as_uint(v[0].z)),
+        "r"(__float_as_uint(v[0].w)), "r"(__float_as_uint(v[1].x)), "r"(__float_as_uint(v[1].y)),
+        "r"(__float_as_uint(v[1].z)), "r"(__float_as_uint(v[1].w)), "r"(__float_as_uint(v[2].x)),
+        "r"(__float_as_uint(v[2].y)), "r"(__float_as_uint(v[2].z)), "r"(__float_as_uint(v[2].w))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 constexpr long long kBarrierCycles = 2000000000LL;
 
 struct PcgAux {
@@ -1577,8 +1681,9 @@ constexpr int kPcgMaxCtas = 255;  // the arrival count of a barrier word has 8 b
 // Grid barrier that also reduces, over the G CTAs that share `word` (a whole grid, or
 // one group of it: `bid` is the CTA's index in that group).  Each barrier of a launch
 // has its own 64-bit word (zeroed before the launch).  Thread 0 of each CTA writes the
-// CTA's FP64 partial to `row`, fences (publishing the CTA's writes) and adds to the word 1 (bits 0-7 count the
-// arrivals) plus, when a reference magnitude ref > 0 is given (the previous value of the
+// CTA's FP64 partial to `row` and, with a release atom (which publishes every write of
+// the CTA: the __syncthreads before it orders them before thread 0's), adds to the
+// word 1 (bits 0-7 count the arrivals) plus, when a reference magnitude ref > 0 is given (the previous value of the
 // same sum: the same in every CTA), the partial in fixed point, round(part 2^(32 - e))
 // with ref = m 2^e, in bits 16-63 -- or 256 (bits 8-15) if it is not below 2^39.  Then it
 // polls the word (acquire) until the count is G, for at most kBarrierCycles.  Integer
@@ -1586,16 +1691,15 @@ constexpr int kPcgMaxCtas = 255;  // the arrival count of a barrier word has 8 b
 // When no partial overflowed and the fixed-point sum is at least 2^28 (ref / 16; the
 // rounding of at most 160 partials, 80 units, is then below 3e-7 of it, the precision of
 // the FP32 partials themselves) that sum is the result, read with the barrier word;
-// otherwise every CTA sums `row` itself in CTA order.  Either way all CTAs get the same
-// `sum`.
+// otherwise every CTA sums `row` itself, in the same order in every CTA.  Either way all
+// CTAs get the same `sum`.
 __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arrivals, double *row, unsigned long long *word,
                                             double part, double ref, double &sum, unsigned bid) {
     __shared__ int s_ok, s_fast;
     __shared__ double s_sum;
     __syncthreads();
     if (threadIdx.x == 0) {
-        row[bid] = part;
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        row[bid] = part;  // ordered before the arrival by the release of the atom below
         unsigned long long inc = 1;
         int e = 0;
         const bool fixed = ref > 0.0 && isfinite(ref);
@@ -1650,6 +1754,28 @@ __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arriv
     return s_ok != 0;
 }
 
+// Test support: `rounds` reductions over the grid, round k summing the partials
+// parts[k * G + b] (one per CTA) with grid_reduce, the previous round's sum as the scale
+// of the fixed-point path (as the position step does); out[2 k] gets the barrier's
+// result, out[2 k + 1] the FP64 sum of the row in CTA order.  words: `rounds` zeroed
+// barrier words; rows: rounds x G doubles.
+__global__ void k_test_grid_reduce(const double *__restrict__ parts, int rounds, double *rows,
+                                   unsigned long long *words, int *err, double *out) {
+    const unsigned G = gridDim.x;
+    double ref = 0.0, sum = 0.0;
+    for (int k = 0; k < rounds; k++) {
+        const double mine = parts[(size_t)k * G + blockIdx.x];
+        if (!grid_reduce(err, G, G, rows + (size_t)k * G, words + k, mine, ref, sum, blockIdx.x)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double t = 0.0;
+            for (unsigned b = 0; b < G; b++) t += __ldcg(rows + (size_t)k * G + b);
+            out[2 * k] = sum;
+            out[2 * k + 1] = t;
+        }
+        ref = sum;
+    }
+}
+
 // FP64 block sum of one float per thread; valid in thread 0
 __device__ __forceinline__ double block_total(float v, double *red) {
     v = warp_sum(v);
@@ -1671,28 +1797,31 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     // Two grid barriers per iteration.  Phase A forms p = z + beta p_old itself (own
     // slots in shared memory; a remote neighbour's from its published z and p_old), so
     // no barrier is needed after the p update:
-    //   A: p update (own), q = 2 w_r L p (stencil warps) | samples' J^T J p (other warps)
+    //   A: x += alpha_old p_old and the p update (own), q = 2 w_r L p (stencil warps) |
+    //      samples' J^T J p (other warps)
     //   -- barrier + sum p.Ap --
-    //   B: x += alpha p, r -= alpha q, z = Minv r (published), r.z
+    //   B: r -= alpha q, z = Minv r (published), r.z
     //   -- barrier + sum r.z --
-    // Global buffers: c.minv (Minv), c.r (z, published; holds b on entry), ax.pbuf
-    // (p of even / odd iterations), c.q (the samples' contributions), c.x (result).
+    // p and z / q of own slots live in shared memory, r and x in tensor memory (each
+    // thread keeps the r of the groups it updates in phase B and the x of those it
+    // updates in A1).  Global buffers: c.minv (Minv), c.r (z, published; holds b on
+    // entry), ax.pbuf (p of even / odd iterations), c.q (the samples' contributions),
+    // c.x (result, written at the end).
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
-    __shared__ int s_cb, s_ce, s_js, s_je;
+    __shared__ int s_js, s_je;
     // per own float4 group: 1 if another CTA reads its p and z (a brick-face row, a slot
     // that a sample or a sparse pair touches, or any slot of a contiguous range)
     __shared__ unsigned s_pub[kPcgMaxGroups * kPcgThreads / 32];
     // per own float4 group: 1 if a sample or a sparse pair touches one of its slots (its
     // J^T J p contributions arrive in c.q)
     __shared__ unsigned s_touch[kPcgMaxGroups * kPcgThreads / 32];
-    __shared__ float tsm[kPcgTsm];
     __shared__ float s_ab;
+    __shared__ uint32_t s_tmem;
     float *sm = reinterpret_cast<float *>(sm4);
     const int chunk = ax.chunk;
     float *__restrict__ P = sm;               // p of own slots
-    float *__restrict__ Rr = sm + 3 * chunk;  // r of own slots
-    float *__restrict__ Q = sm + 6 * chunk;   // z between phases B and A, q within A..B
+    float *__restrict__ Q = sm + 3 * chunk;   // z between phases B and A, q within A..B
     float *__restrict__ Zg = c.r;
     if (sc->skip) return;  // the same flag for every CTA: none reaches a barrier
     const unsigned G = gridDim.x;
@@ -1715,26 +1844,21 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     const int tid = threadIdx.x;
     const float w2 = 2.f * c.w_r;
     const size_t ld = c.ld;
-    if (tid == 0) {
-        // an equal share of the sorted samples, and the occupied cells that hold them
+    if (tid < 32) {  // one SM per CTA: the columns are free
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tmem)),
+                     "r"(kPcgTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t t_r = s_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + 64u * (uint32_t)(tid >> 7);
+    const uint32_t t_x = t_r + kPcgTmemX;
+    if (tid == 0) {  // an equal share of the sorted samples
         const int n_occ = *c.n_occ, ns = n_occ > 0 ? c.occ_beg[n_occ] : 0;
-        const int js = (int)(((long long)ns * blockIdx.x) / G), je = (int)(((long long)ns * (blockIdx.x + 1)) / G);
-        int lo = 0, hi = n_occ;  // first cell whose end is past js
-        while (lo < hi) {
-            const int m = (lo + hi) >> 1;
-            if (c.occ_beg[m + 1] <= js) lo = m + 1;
-            else hi = m;
-        }
-        s_cb = lo;
-        hi = n_occ;  // first cell that starts at or after je
-        while (lo < hi) {
-            const int m = (lo + hi) >> 1;
-            if (c.occ_beg[m] < je) lo = m + 1;
-            else hi = m;
-        }
-        s_ce = je > js ? lo : s_cb;
-        s_js = js;
-        s_je = je;
+        s_js = (int)(((long long)ns * blockIdx.x) / G);
+        s_je = (int)(((long long)ns * (blockIdx.x + 1)) / G);
     }
     // ---- init: Minv = 1/diag, r = b, z = Minv r, p_old = 0, x = 0; rho0 = r.z
     float part = 0.f;
@@ -1743,43 +1867,55 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     for (int kk = 0; kk < kPcgMaxGroups; kk++) {
         const int gl = tid + kk * kPcgThreads;
         pub[kk] = touch[kk] = false;
-        if (gl >= ng) continue;
-        const int l = 4 * gl, s = gslot(l);
-        pub[kk] = true;
-        if (brick) {
-            const int r = fast_div(l, ax.m_nx), zl = fast_div(r, ax.m_by), yl = r - zl * ax.by;
-            pub[kk] = yl == 0 || yl == ax.by - 1 || zl == 0 || zl == ax.bz - 1;
-        }
+        float4 r3[3];
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            *reinterpret_cast<float4 *>(c.x + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 dg = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
-            const float4 rb = __ldcg(reinterpret_cast<const float4 *>(c.r + a * ld + s));
-            const float dv[4] = {dg.x, dg.y, dg.z, dg.w}, rv[4] = {rb.x, rb.y, rb.z, rb.w};
-            float mi[4], rr[4], z[4];
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const bool in = s + e < N;
-                mi[e] = (in && dv[e] > 0.f) ? 1.0f / dv[e] : 0.f;
-                rr[e] = in ? rv[e] : 0.f;
-                z[e] = mi[e] * rr[e];
-                part += rr[e] * z[e];
+        for (int a = 0; a < 3; a++) r3[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gl < ng) {
+            const int l = 4 * gl, s = gslot(l);
+            pub[kk] = true;
+            if (brick) {
+                const int r = fast_div(l, ax.m_nx), zl = fast_div(r, ax.m_by), yl = r - zl * ax.by;
+                pub[kk] = yl == 0 || yl == ax.by - 1 || zl == 0 || zl == ax.bz - 1;
             }
-            const float4 z4 = make_float4(z[0], z[1], z[2], z[3]), zero = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float4 *>(c.minv + a * ld + s) = make_float4(mi[0], mi[1], mi[2], mi[3]);
-            *reinterpret_cast<float4 *>(Rr + a * chunk + l) = make_float4(rr[0], rr[1], rr[2], rr[3]);
-            *reinterpret_cast<float4 *>(Q + a * chunk + l) = z4;
-            *reinterpret_cast<float4 *>(P + a * chunk + l) = zero;
-            *reinterpret_cast<float4 *>(Zg + a * ld + s) = z4;
-            *reinterpret_cast<float4 *>(ax.pbuf[1] + a * ld + s) = zero;
-        }
-        const int4 fl = __ldcg(reinterpret_cast<const int4 *>(ax.flag + s));
-        if (fl.x | fl.y | fl.z | fl.w) {  // the samples' contributions arrive here by atomics
 #pragma unroll
-            for (int a = 0; a < 3; a++) *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
-            pub[kk] = touch[kk] = true;
+            for (int a = 0; a < 3; a++) {
+                const float4 dg = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
+                const float4 rb = __ldcg(reinterpret_cast<const float4 *>(c.r + a * ld + s));
+                const float dv[4] = {dg.x, dg.y, dg.z, dg.w}, rv[4] = {rb.x, rb.y, rb.z, rb.w};
+                float mi[4], rr[4], z[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const bool in = s + e < N;
+                    mi[e] = (in && dv[e] > 0.f) ? 1.0f / dv[e] : 0.f;
+                    rr[e] = in ? rv[e] : 0.f;
+                    z[e] = mi[e] * rr[e];
+                    part += rr[e] * z[e];
+                }
+                const float4 z4 = make_float4(z[0], z[1], z[2], z[3]), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4 *>(c.minv + a * ld + s) = make_float4(mi[0], mi[1], mi[2], mi[3]);
+                r3[a] = make_float4(rr[0], rr[1], rr[2], rr[3]);
+                *reinterpret_cast<float4 *>(Q + a * chunk + l) = z4;
+                *reinterpret_cast<float4 *>(P + a * chunk + l) = zero;
+                *reinterpret_cast<float4 *>(Zg + a * ld + s) = z4;
+                *reinterpret_cast<float4 *>(ax.pbuf[1] + a * ld + s) = zero;
+            }
+            const int4 fl = __ldcg(reinterpret_cast<const int4 *>(ax.flag + s));
+            if (fl.x | fl.y | fl.z | fl.w) {  // the samples' contributions arrive here by atomics
+#pragma unroll
+                for (int a = 0; a < 3; a++) *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
+                pub[kk] = touch[kk] = true;
+            }
         }
+        tmem_st12(t_r + 12 * kk, r3);
     }
+    if (tid < kPcgStencil) {  // x = 0 (whole warps)
+        float4 z3[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) z3[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < kPcgStencilGroups; k++) tmem_st12(t_x + 12 * k, z3);
+    }
+    tmem_wait_st();
 #pragma unroll
     for (int kk = 0; kk < kPcgMaxGroups; kk++) {
         const unsigned m = __ballot_sync(FULL, pub[kk]), t = __ballot_sync(FULL, touch[kk]);
@@ -1800,6 +1936,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     if (blockIdx.x == 0 && tid == 0) scal_rho(sc)[0] = rho0;
     int done = 0;
     int stop = !ok;
+    // x += alpha p of an iteration is added by the next iteration's A1, which reads that
+    // p anyway; the last one after the loop
+    float alpha_pend = 0.f;
     for (int it = 0; it < K && !stop; it++) {
         if (!(rho > 0.0)) {
             stop = 1;
@@ -1807,23 +1946,36 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         }
         const float *__restrict__ pold = ax.pbuf[(it + 1) & 1];
         float *__restrict__ pnew = ax.pbuf[it & 1];
+        const float xa = alpha_pend;
+        alpha_pend = 0.f;
         part = 0.f;
         if (tid < kPcgStencil) {
-            // ---- A1: p = z + beta p_old for own slots
+            // ---- A1: x += alpha p_old (the previous step; x in tensor memory), p = z +
+            // beta p_old for own slots
 #pragma unroll 1
-            for (int gl = tid; gl < ng; gl += kPcgStencil) {
-                const int l = 4 * gl, s = gslot(l);
-                const bool pg = published(gl);
+            for (int k = 0; k < kPcgStencilGroups; k++) {  // whole warps (tensor memory)
+                const int gl = tid + k * kPcgStencil;
+                float4 x3[3];
+                if (xa != 0.f) tmem_ld12(t_x + 12 * k, x3);
+                if (gl < ng) {
+                    const int l = 4 * gl, s = gslot(l);
+                    const bool pg = published(gl);
 #pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
-                    const float4 zv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
-                    const float4 pn = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y),
-                                                  fmaf(beta, pv.z, zv.z), fmaf(beta, pv.w, zv.w));
-                    *reinterpret_cast<float4 *>(P + a * chunk + l) = pn;
-                    if (pg) *reinterpret_cast<float4 *>(pnew + a * ld + s) = pn;
+                    for (int a = 0; a < 3; a++) {
+                        const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
+                        const float4 zv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
+                        if (xa != 0.f)
+                            x3[a] = make_float4(fmaf(xa, pv.x, x3[a].x), fmaf(xa, pv.y, x3[a].y),
+                                                fmaf(xa, pv.z, x3[a].z), fmaf(xa, pv.w, x3[a].w));
+                        const float4 pn = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y),
+                                                      fmaf(beta, pv.z, zv.z), fmaf(beta, pv.w, zv.w));
+                        *reinterpret_cast<float4 *>(P + a * chunk + l) = pn;
+                        if (pg) *reinterpret_cast<float4 *>(pnew + a * ld + s) = pn;
+                    }
                 }
+                if (xa != 0.f) tmem_st12(t_x + 12 * k, x3);
             }
+            if (xa != 0.f) tmem_wait_st();
             sub_sync(2, kPcgStencil);
             // ---- A2: q = 2 w_r L p into Q
 #pragma unroll 1
@@ -1943,12 +2095,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                 const int ce = (int)(((long long)n_occ * (blockIdx.x + 1)) / G);
                 for (int ci = cb + (lt >> 5); ci < ce; ci += kPcgSample >> 5)
                     btb_cell_apply<kAll, true>(c, pv, ci, c.q, part);
-            } else if (s_ce > s_cb) {
-                cells_block<kOpApply, kAll, true>(c, pv, c.q, nullptr, s_cb, s_ce, tsm, kPcgTsm, part, lt, kPcgSample, 1, s_js,
-                                                  s_je);
+            } else {
+                samples_warp_apply<kAll>(c, pv, c.q, s_js, s_je, part, lt, kPcgSample);
             }
+            // the pairs go to the last warps, which hold the fewest cells
             double pd = 0.0;
-            sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * lt, G * kPcgSample, part, pd);
+            sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * (kPcgSample - 1 - lt), G * kPcgSample,
+                                               part, pd);
         }
         ok = grid_reduce(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it, block_total(part, red),
                          pq_prev, sum, blockIdx.x);
@@ -1968,45 +2121,47 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         }
         __syncthreads();
         const float alpha = s_ab;
-        // ---- B: x += alpha p; r -= alpha q; z = Minv r (Q and published); rho' = r.z
+        alpha_pend = alpha;
+        // ---- B: r -= alpha q; z = Minv r (Q and published); rho' = r.z
         part = 0.f;
 #pragma unroll
         for (int kk = 0; kk < kPcgMaxGroups; kk++) {
             const int gl = tid + kk * kPcgThreads;
-            if (gl >= ng) continue;
-            const int l = 4 * gl, s = gslot(l);
-            // every global load of the group first (one round trip): Minv, and the
-            // samples' contributions where they arrive
-            const bool touched = touched_group(gl), pg = published(gl);
-            float4 qg[3], mv[3];
+            float4 r3[3];
+            tmem_ld12(t_r + 12 * kk, r3);  // whole warps
+            if (gl < ng) {
+                const int l = 4 * gl, s = gslot(l);
+                // every global load of the group first (one round trip): Minv, and the
+                // samples' contributions where they arrive
+                const bool touched = touched_group(gl), pg = published(gl);
+                float4 qg[3], mv[3];
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                qg[a] = touched ? __ldcg(reinterpret_cast<const float4 *>(c.q + a * ld + s)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                mv[a] = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
-            }
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
-                float4 qv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
-                if (touched) {  // fold in (and clear) the samples' contributions
-                    qv = f4add(qv, qg[a]);
-                    *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int a = 0; a < 3; a++) {
+                    qg[a] = touched ? __ldcg(reinterpret_cast<const float4 *>(c.q + a * ld + s))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                    mv[a] = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
                 }
-                const float4 rv = *reinterpret_cast<const float4 *>(Rr + a * chunk + l);
-                // x lives in global memory (L2-resident; the 80 registers of a thread of a
-                // 768-thread CTA cannot hold it as well without spilling) and is updated
-                // by a reduction, which needs no load; this thread is its only writer
-                red_add_f4(c.x + a * ld + s, make_float4(alpha * pv.x, alpha * pv.y, alpha * pv.z, alpha * pv.w));
-                const float4 &mvv = mv[a];
-                const float4 rn = make_float4(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y),
-                                              fmaf(-alpha, qv.z, rv.z), fmaf(-alpha, qv.w, rv.w));
-                const float4 zn = make_float4(mvv.x * rn.x, mvv.y * rn.y, mvv.z * rn.z, mvv.w * rn.w);
-                *reinterpret_cast<float4 *>(Rr + a * chunk + l) = rn;
-                *reinterpret_cast<float4 *>(Q + a * chunk + l) = zn;
-                if (pg) *reinterpret_cast<float4 *>(Zg + a * ld + s) = zn;
-                part += rn.x * zn.x + rn.y * zn.y + rn.z * zn.z + rn.w * zn.w;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    float4 qv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
+                    if (touched) {  // fold in (and clear) the samples' contributions
+                        qv = f4add(qv, qg[a]);
+                        *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    const float4 rv = r3[a];
+                    const float4 &mvv = mv[a];
+                    const float4 rn = make_float4(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y),
+                                                  fmaf(-alpha, qv.z, rv.z), fmaf(-alpha, qv.w, rv.w));
+                    const float4 zn = make_float4(mvv.x * rn.x, mvv.y * rn.y, mvv.z * rn.z, mvv.w * rn.w);
+                    r3[a] = rn;
+                    *reinterpret_cast<float4 *>(Q + a * chunk + l) = zn;
+                    if (pg) *reinterpret_cast<float4 *>(Zg + a * ld + s) = zn;
+                    part += rn.x * zn.x + rn.y * zn.y + rn.z * zn.z + rn.w * zn.w;
+                }
             }
+            tmem_st12(t_r + 12 * kk, r3);
         }
+        tmem_wait_st();
         done = it + 1;
         ok = grid_reduce(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it, block_total(part, red), rho,
                          sum, blockIdx.x);
@@ -2025,20 +2180,28 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         beta = s_ab;
         rho = rho1;
     }
-    // ---- u += x when the step is applied
+    // ---- the last step's x += alpha p (every earlier one has passed A1), x to c.x; u += x
+    // when the step is applied
+    if (tid < kPcgStencil) {
+#pragma unroll 1
+        for (int k = 0; k < kPcgStencilGroups; k++) {
+            const int gl = tid + k * kPcgStencil;
+            float4 x3[3];
+            tmem_ld12(t_x + 12 * k, x3);  // whole warps
+            if (gl >= ng) continue;
+            const int l = 4 * gl, s = gslot(l);
 #pragma unroll
-    for (int kk = 0; kk < kPcgMaxGroups; kk++) {
-        const int gl = tid + kk * kPcgThreads;
-        if (gl >= ng) continue;
-        const int s = gslot(4 * gl);
+            for (int a = 0; a < 3; a++) {
+                const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
+                const float4 x4 = make_float4(fmaf(alpha_pend, pv.x, x3[a].x), fmaf(alpha_pend, pv.y, x3[a].y),
+                                              fmaf(alpha_pend, pv.z, x3[a].z), fmaf(alpha_pend, pv.w, x3[a].w));
+                *reinterpret_cast<float4 *>(c.x + a * ld + s) = x4;
+                if (apply) {
+                    const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const float4 x4 = __ldcg(reinterpret_cast<const float4 *>(c.x + a * ld + s));
-            if (apply) {
-                const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-                for (int e = 0; e < 4; e++)
-                    if (s + e < N) c.u[a * ld + slot_node<kAll>(c, s + e)] += xv[e];
+                    for (int e = 0; e < 4; e++)
+                        if (s + e < N) c.u[a * ld + slot_node<kAll>(c, s + e)] += xv[e];
+                }
             }
         }
     }
@@ -2046,6 +2209,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         sc->cg_done = done;
         sc->stop = stop;
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(kPcgTmemCols));
 }
 
 // ------------------------------------------------------------------ batched position step (config 4)

@@ -113,6 +113,7 @@ _SIGS = {
     "vd_get_mesh": [_P, _P, _P, _I],
     "vd_render_samples": [_P, _P, _P, _P, _I, _P, _P, _P, _I, _PI, _I],
     "vd_set_apply_mode": [_P, _I],
+    "vd_test_grid_reduce": [_P, _I, _I, _P],
     "vd_get_apply_mode": [_P, _PI, _PI],
     "vd_tune_apply": [_P, ctypes.POINTER(vd_solve_params), _PI, ctypes.POINTER(ctypes.c_float)],
     "vd_hierarchy_create": [_P, _I, ctypes.POINTER(_P)],
