@@ -1678,6 +1678,65 @@ constexpr int kPcgMaxRows = 128;  // x-rows of one brick (bounds the plan's sear
 constexpr int kPcgMaxCtas = 255;  // the arrival count of a barrier word has 8 bits
 
 
+// The scalar work around the grid barriers is done with integer operations on the bits
+// of the FP64 values (this GPU's FP64 pipe is narrow, and a chain of FP64 operations in
+// one thread sits on the critical path of every barrier).
+
+// round(|v| 2^k) with the sign of v (halves away from zero), for a finite v and
+// k <= 1012; false when it would reach 2^39 in magnitude (or v is not finite)
+__device__ __forceinline__ bool fixed_of(double v, int k, long long &out) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7ff);
+    if (E == 0x7ff) return false;
+    if (E == 0) {  // zero or subnormal: below 2^-1022 2^1012, rounds to 0
+        out = 0;
+        return true;
+    }
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);  // |v| = m 2^(E - 1075)
+    const int sh = E - 1075 + k;                                           // |v| 2^k = m 2^sh
+    if (sh >= -13) return false;                                           // m 2^sh >= 2^39
+    const unsigned long long a = sh < -63 ? 0ull : (m + (1ull << (-sh - 1))) >> (-sh);
+    if (a >= (1ull << 39)) return false;
+    out = (b >> 63) ? -(long long)a : (long long)a;
+    return true;
+}
+
+// fx 2^-k as an FP64 value (exact for |fx| < 2^53; the exponent must stay normal)
+__device__ __forceinline__ double double_of_fixed(long long fx, int k) {
+    if (fx == 0) return 0.0;
+    const unsigned long long sgn = fx < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long a = fx < 0 ? (unsigned long long)(-fx) : (unsigned long long)fx;
+    const int lz = __clzll((long long)a);
+    const unsigned long long m = lz >= 11 ? a << (lz - 11) : a >> (11 - lz);  // leading 1 at bit 52
+    const long long E = 1023 + (63 - lz) - k;
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | (m & 0xfffffffffffffull)));
+}
+
+// The FP32 quotient n / d of two FP64 values, from their signs, exponents and leading
+// 24 bits (rounded) and one FP32 division: within 3 2^-24 of the exact quotient,
+// relative (two roundings of the operands and one of the division).  Zero, subnormal or
+// non-finite operands, and quotients outside the normal FP32 range, take the FP64
+// division instead.
+__device__ __forceinline__ float f32_quot(double n, double d) {
+    const unsigned long long bn = (unsigned long long)__double_as_longlong(n),
+                             bd = (unsigned long long)__double_as_longlong(d);
+    const int en = (int)((bn >> 52) & 0x7ff), ed = (int)((bd >> 52) & 0x7ff);
+    if (en == 0 || ed == 0 || en == 0x7ff || ed == 0x7ff) return (float)(n / d);
+    // the leading bits as FP32 values in [1, 2] (a carry of the rounding gives 2)
+    auto lead = [](unsigned long long b) {
+        return __uint_as_float((unsigned)(0x3f800000u + (((b & 0xfffffffffffffull) + (1ull << 28)) >> 29)) |
+                               (unsigned)((b >> 63) << 31));
+    };
+    const float q = lead(bn) / lead(bd);  // |q| in [0.5, 2]
+    const int eq = (int)((__float_as_uint(q) >> 23) & 0xff) + (en - ed);
+    if (eq < 1 || eq > 254) return (float)(n / d);
+    return __uint_as_float((__float_as_uint(q) & 0x807fffffu) | ((unsigned)eq << 23));
+}
+
+struct NoPost {
+    __device__ void operator()(double) const {}
+};
+
 // Grid barrier that also reduces, over the G CTAs that share `word` (a whole grid, or
 // one group of it: `bid` is the CTA's index in that group).  Each barrier of a launch
 // has its own 64-bit word (zeroed before the launch).  Thread 0 of each CTA writes the
@@ -1692,21 +1751,26 @@ constexpr int kPcgMaxCtas = 255;  // the arrival count of a barrier word has 8 b
 // rounding of at most 160 partials, 80 units, is then below 3e-7 of it, the precision of
 // the FP32 partials themselves) that sum is the result, read with the barrier word;
 // otherwise every CTA sums `row` itself, in the same order in every CTA.  Either way all
-// CTAs get the same `sum`.
+// CTAs get the same `sum`.  kSynced: the caller has synchronised the CTA since its last
+// write that other CTAs read (block_sum does).  post(sum) runs in thread 0 before the
+// CTA's last __syncthreads here, so what it stores in shared memory is visible to every
+// thread on return.  The scale 2^e of ref is taken for 2^-960 <= ref < 2^961 (the
+// row path otherwise).
+template <bool kSynced = false, typename Post = NoPost>
 __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arrivals, double *row, unsigned long long *word,
-                                            double part, double ref, double &sum, unsigned bid) {
+                                            double part, double ref, double &sum, unsigned bid, Post post = Post()) {
     __shared__ int s_ok, s_fast;
     __shared__ double s_sum;
-    __syncthreads();
+    if (!kSynced) __syncthreads();
     if (threadIdx.x == 0) {
         row[bid] = part;  // ordered before the arrival by the release of the atom below
         unsigned long long inc = 1;
-        int e = 0;
-        const bool fixed = ref > 0.0 && isfinite(ref);
+        const long long rb = __double_as_longlong(ref);
+        const int e = (int)((rb >> 52) & 0x7ff) - 1023;  // ref = m 2^e, 1 <= m < 2
+        const bool fixed = rb > 0 && e >= -960 && e <= 960;  // positive, normal, finite
         if (fixed) {
-            e = ilogb(ref);
-            const double f = ldexp(part, 32 - e);
-            if (fabs(f) < 0x1p39) inc += (unsigned long long)llrint(f) << 16;
+            long long fxp;
+            if (fixed_of(part, 32 - e, fxp)) inc += (unsigned long long)fxp << 16;
             else inc += 256ull;
         }
         unsigned long long old;
@@ -1729,7 +1793,10 @@ __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arriv
         }
         const long long fx = (long long)w >> 16;
         const int fast = good && fixed && ((w >> 8) & 0xFFull) == 0 && (fx >= (1ll << 28) || fx <= -(1ll << 28));
-        if (fast) s_sum = ldexp((double)fx, e - 32);
+        if (fast) {
+            s_sum = double_of_fixed(fx, 32 - e);
+            post(s_sum);
+        }
         s_fast = fast;
         s_ok = good && !*(volatile int *)err;
     }
@@ -1746,7 +1813,10 @@ __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arriv
             for (unsigned b = threadIdx.x + 160u; b < G; b += 32) t += __ldcg(row + b);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-            if (threadIdx.x == 0) s_sum = t;
+            if (threadIdx.x == 0) {
+                s_sum = t;
+                post(t);
+            }
         }
         __syncthreads();
     }
@@ -1788,6 +1858,23 @@ __device__ __forceinline__ double block_total(float v, double *red) {
     return s;
 }
 
+// The same sum (FP32 warp sums, FP64 across the warps) for callers in which a
+// __syncthreads separates consecutive calls: no barrier before the warp sums are staged,
+// and one conversion to FP64 per warp sum in warp 0 only.  Valid in thread 0.
+__device__ __forceinline__ double block_sum(float v, float *redf) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) redf[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < (int)(blockDim.x >> 5) ? (double)redf[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    }
+    return s;
+}
+
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
 
@@ -1808,8 +1895,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     // entry), ax.pbuf (p of even / odd iterations), c.q (the samples' contributions),
     // c.x (result, written at the end).
     extern __shared__ float4 sm4[];
-    __shared__ double red[32];
-    __shared__ int s_js, s_je;
+    __shared__ float redf[32];
+    __shared__ int s_js, s_je, s_go;
     // per own float4 group: 1 if another CTA reads its p and z (a brick-face row, a slot
     // that a sample or a sparse pair touches, or any slot of a contiguous range)
     __shared__ unsigned s_pub[kPcgMaxGroups * kPcgThreads / 32];
@@ -1926,24 +2013,24 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     }
     auto published = [&](int gl) -> bool { return (s_pub[gl >> 5] >> (gl & 31)) & 1u; };
     auto touched_group = [&](int gl) -> bool { return (s_touch[gl >> 5] >> (gl & 31)) & 1u; };
-    __syncthreads();
-    double sum = 0.0;
+    // The FP64 scalars (rho0, rho, the previous p.Ap) live in thread 0, which takes every
+    // decision after a barrier and hands the others alpha or beta (s_ab) and whether to
+    // go on (s_go), through the barrier's last __syncthreads.
+    double sum = 0.0, rho0 = 0.0, rho = 0.0, pq_prev = 0.0;
     const unsigned arrivals = G + ax.extra;
-    bool ok = grid_reduce(ax.err, G, arrivals, ax.part, ax.words, block_total(part, red), 0.0, sum, blockIdx.x);
-    const double rho0 = ok ? sum : 0.0;
-    double rho = rho0, pq_prev = 0.0;
+    bool ok = grid_reduce<true>(ax.err, G, arrivals, ax.part, ax.words, block_sum(part, redf), 0.0, sum, blockIdx.x,
+                                [&](double r0) {
+                                    rho0 = rho = r0;
+                                    s_go = r0 > 0.0;
+                                    if (blockIdx.x == 0) scal_rho(sc)[0] = r0;
+                                });
     float beta = 0.f;
-    if (blockIdx.x == 0 && tid == 0) scal_rho(sc)[0] = rho0;
     int done = 0;
-    int stop = !ok;
+    int stop = !ok || !s_go;
     // x += alpha p of an iteration is added by the next iteration's A1, which reads that
     // p anyway; the last one after the loop
     float alpha_pend = 0.f;
     for (int it = 0; it < K && !stop; it++) {
-        if (!(rho > 0.0)) {
-            stop = 1;
-            break;
-        }
         const float *__restrict__ pold = ax.pbuf[(it + 1) & 1];
         float *__restrict__ pnew = ax.pbuf[it & 1];
         const float xa = alpha_pend;
@@ -2103,23 +2190,17 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * (kPcgSample - 1 - lt), G * kPcgSample,
                                                part, pd);
         }
-        ok = grid_reduce(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it, block_total(part, red),
-                         pq_prev, sum, blockIdx.x);
-        if (!ok) {
+        ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it,
+                               block_sum(part, redf), pq_prev, sum, blockIdx.x, [&](double pq) {
+                                   pq_prev = pq;
+                                   s_go = pq > 0.0;
+                                   if (s_go) s_ab = f32_quot(rho, pq);  // alpha
+                                   if (blockIdx.x == 0) scal_pq(sc, K)[it] = pq;
+                               });
+        if (!ok || !s_go) {
             stop = 1;
             break;
         }
-        const double pq = sum;
-        pq_prev = pq;
-        if (!(pq > 0.0)) {
-            stop = 1;
-            break;
-        }
-        if (tid == 0) {  // one FP64 division per CTA
-            s_ab = (float)(rho / pq);
-            if (blockIdx.x == 0) scal_pq(sc, K)[it] = pq;
-        }
-        __syncthreads();
         const float alpha = s_ab;
         alpha_pend = alpha;
         // ---- B: r -= alpha q; z = Minv r (Q and published); rho' = r.z
@@ -2163,22 +2244,19 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         }
         tmem_wait_st();
         done = it + 1;
-        ok = grid_reduce(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it, block_total(part, red), rho,
-                         sum, blockIdx.x);
-        if (!ok) {
+        ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it,
+                               block_sum(part, redf), rho, sum, blockIdx.x, [&](double rho1) {
+                                   if (blockIdx.x == 0) scal_rho(sc)[it + 1] = rho1;
+                                   // go on unless converged; a next step needs rho1 > 0
+                                   s_go = !(rho1 <= tol2 * rho0) && rho1 > 0.0;
+                                   if (s_go) s_ab = f32_quot(rho1, rho);  // beta
+                                   rho = rho1;
+                               });
+        if (!ok || !s_go) {
             stop = 1;
             break;
         }
-        const double rho1 = sum;
-        if (blockIdx.x == 0 && tid == 0) scal_rho(sc)[it + 1] = rho1;
-        if (rho1 <= tol2 * rho0) {
-            stop = 1;
-            break;
-        }
-        if (tid == 0) s_ab = (float)(rho1 / rho);
-        __syncthreads();
         beta = s_ab;
-        rho = rho1;
     }
     // ---- the last step's x += alpha p (every earlier one has passed A1), x to c.x; u += x
     // when the step is applied
