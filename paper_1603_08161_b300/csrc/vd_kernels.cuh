@@ -1737,6 +1737,15 @@ struct NoPost {
     __device__ void operator()(double) const {}
 };
 
+// v > 0 and finite, from its bits
+__device__ __forceinline__ bool pos_finite(double v) {
+    const long long b = __double_as_longlong(v);
+    return b > 0 && (b >> 52) < 0x7ff;
+}
+// a <= b for finite a, b >= 0, from their bits (the bit patterns of non-negative
+// doubles are ordered as the values)
+__device__ __forceinline__ bool le_nonneg(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+
 // Grid barrier that also reduces, over the G CTAs that share `word` (a whole grid, or
 // one group of it: `bid` is the CTA's index in that group).  Each barrier of a launch
 // has its own 64-bit word (zeroed before the launch).  Thread 0 of each CTA writes the
@@ -1798,7 +1807,9 @@ __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arriv
             post(s_sum);
         }
         s_fast = fast;
-        s_ok = good && !*(volatile int *)err;
+        // a complete count means that no CTA gave up on this barrier (one that gave up on
+        // an earlier one never arrives here): no second look at the error word
+        s_ok = good;
     }
     __syncthreads();
     if (!s_fast) {  // the same decision in every CTA
@@ -2013,15 +2024,16 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     }
     auto published = [&](int gl) -> bool { return (s_pub[gl >> 5] >> (gl & 31)) & 1u; };
     auto touched_group = [&](int gl) -> bool { return (s_touch[gl >> 5] >> (gl & 31)) & 1u; };
-    // The FP64 scalars (rho0, rho, the previous p.Ap) live in thread 0, which takes every
+    // The FP64 scalars (rho, the previous p.Ap, tol^2 rho0) live in thread 0, which takes every
     // decision after a barrier and hands the others alpha or beta (s_ab) and whether to
     // go on (s_go), through the barrier's last __syncthreads.
-    double sum = 0.0, rho0 = 0.0, rho = 0.0, pq_prev = 0.0;
+    double sum = 0.0, rho = 0.0, pq_prev = 0.0, thr = 0.0;
     const unsigned arrivals = G + ax.extra;
     bool ok = grid_reduce<true>(ax.err, G, arrivals, ax.part, ax.words, block_sum(part, redf), 0.0, sum, blockIdx.x,
                                 [&](double r0) {
-                                    rho0 = rho = r0;
-                                    s_go = r0 > 0.0;
+                                    rho = r0;
+                                    thr = tol2 * r0;  // the convergence threshold on rho
+                                    s_go = pos_finite(r0);
                                     if (blockIdx.x == 0) scal_rho(sc)[0] = r0;
                                 });
     float beta = 0.f;
@@ -2100,6 +2112,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                         }
                     }
                     const bool has[4] = {y > 0, y + 1 < c.ny, z > 0, z + 1 < c.nz};
+                    float4 q3[3];  // stored after the three are formed (no store between the loads)
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
                         const float *Pa = P + a * chunk;
@@ -2135,9 +2148,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                             d.w += pc.w - v.w;
                         }
                         d = make_float4(w2 * d.x, w2 * d.y, w2 * d.z, w2 * d.w);
-                        *reinterpret_cast<float4 *>(Q + a * chunk + l) = d;
+                        q3[a] = d;
                         part += pc.x * d.x + pc.y * d.y + pc.z * d.z + pc.w * d.w;
                     }
+#pragma unroll
+                    for (int a = 0; a < 3; a++) *reinterpret_cast<float4 *>(Q + a * chunk + l) = q3[a];
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
@@ -2193,7 +2208,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it,
                                block_sum(part, redf), pq_prev, sum, blockIdx.x, [&](double pq) {
                                    pq_prev = pq;
-                                   s_go = pq > 0.0;
+                                   s_go = pos_finite(pq);
                                    if (s_go) s_ab = f32_quot(rho, pq);  // alpha
                                    if (blockIdx.x == 0) scal_pq(sc, K)[it] = pq;
                                });
@@ -2247,8 +2262,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it,
                                block_sum(part, redf), rho, sum, blockIdx.x, [&](double rho1) {
                                    if (blockIdx.x == 0) scal_rho(sc)[it + 1] = rho1;
-                                   // go on unless converged; a next step needs rho1 > 0
-                                   s_go = !(rho1 <= tol2 * rho0) && rho1 > 0.0;
+                                   // go on unless converged (rho1 = r.Minv r >= 0); a next
+                                   // step needs rho1 > 0
+                                   s_go = pos_finite(rho1) && !le_nonneg(rho1, thr);
                                    if (s_go) s_ab = f32_quot(rho1, rho);  // beta
                                    rho = rho1;
                                });
