@@ -2799,6 +2799,18 @@ __device__ __forceinline__ bool sym4_top_rqi(const float N[4][4], float q[4], fl
     return true;
 }
 
+// The Jacobi fallback of the rotation step in FP32 (when the Rayleigh-quotient
+// iteration is not certified; rare), out of line so that its registers do not count
+// against the fast path's occupancy; returns lambda_1 - lambda_2.
+__device__ __noinline__ float horn_top_eigvec_f32(const float (&Nm)[4][4], float qv[4]) {
+    float a[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) a[r][k] = Nm[r][k];
+    return sym4_top_eigvec<float>(a, qv);
+}
+
 // The near-tie redo of the rotation step in FP64 (rare), kept out of line so that its
 // registers do not count against the FP32 path's occupancy.
 __device__ __noinline__ double horn_top_eigvec_f64(float Sxx, float Sxy, float Sxz, float Syx, float Syy, float Syz,
@@ -2884,7 +2896,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) 
             float qv[4] = {1.f, 0.f, 0.f, 0.f};
             bool unique = sym4_top_rqi(Nm, qv, 1e-4f * scale, scale);
             if (!unique) {
-                const float gap = sym4_top_eigvec<float>(Nm, qv);
+                const float gap = horn_top_eigvec_f32(Nm, qv);
                 unique = gap > 1e-5f * scale;
                 if (gap < 1e-4f * scale) {
                     // near-singular block (the rotation's sensitivity exceeds 1e4): polar
