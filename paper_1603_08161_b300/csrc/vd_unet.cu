@@ -301,6 +301,261 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
+// The same convolution as a persistent, pipelined kernel, for layers whose packed
+// weights (every input slice) fit in shared memory beside at least two slab buffers:
+// one CTA per SM walks the (plane, row pair) items in grid stride.  Warp 4 (one lane)
+// stages the weights once and then, slice after slice, the slab of the next (item, input
+// slice) by TMA into the next of `nstage` (2-4) buffers, as soon as the MMAs that read
+// it last are done; warp 5 (one lane) issues each slice's 27 x nblk MMAs into one of two
+// TMEM accumulators (one per item parity); warps 0-3 read the finished accumulator of an
+// item (tcgen05.ld, their 32 lanes each) for the epilogue while the next item's MMAs
+// run.  mbarriers: full[b] (slab b staged), empty[b] (the MMAs that read it are done),
+// tfull[a] (accumulator a complete), tempty[a] (its epilogue done: 128 arrivals), the
+// weights, and a drain for the error path.  Every wait is bounded; a wait that gives up
+// sets *err and its role stops, and the others then give up too.
+constexpr int kTcpMaxStages = 4;
+__host__ __device__ inline int tcp_smem_bytes(int W, int NF, int kchunks, int nstage) {
+    return nstage * 2 * tc_nvp(W) * 16 + kchunks * 27 * 16 * NF * 32;
+}
+constexpr int kTcpSmemMax = 225 * 1024;
+// the most slab buffers (2..4) that fit, 0 if two do not
+__host__ inline int tcp_stages(int W, int NF, int kchunks) {
+    for (int ns = kTcpMaxStages; ns >= 2; ns--)
+        if (tcp_smem_bytes(W, NF, kchunks, ns) <= kTcpSmemMax) return ns;
+    return 0;
+}
+// Partial accumulators per item: tap t goes to partial t % nacc and is issued by its own
+// lane (one MMA-issuing thread sustains only about one small MMA per 100 ns); the
+// epilogue adds the partials.  The most (<= 4) for which two items' accumulators fit the
+// 512 TMEM columns.
+constexpr int kTcpMaxAcc = 4;
+__host__ inline int tcp_nacc(int W, int NF) {
+    int n = kTcpMaxAcc;
+    while (n > 1 && 2 * n * tc_nblk(W) * 16 * NF > 512) n--;
+    return n;
+}
+__host__ inline int tcp_tmem_cols(int W, int NF) {
+    int c = 32;
+    while (c < 2 * tcp_nacc(W, NF) * tc_nblk(W) * 16 * NF) c <<= 1;
+    return c;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mb) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mb) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+}
+
+template <int NF>
+__global__ void __launch_bounds__(192, 1) k_conv3d_tcp(const __grid_constant__ CUtensorMap tmap, View in,
+                                                       const bf16 *__restrict__ Wtc, const float *__restrict__ bias,
+                                                       View out, int cout_real, int relu, float *__restrict__ outf,
+                                                       int tmem_cols, int nstage, int nacc, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar[14];
+    __shared__ uint32_t tmem_base;
+    constexpr int N = 16 * NF;
+    enum { FULL = 0, EMPTY = 4, TFULL = 8, TEMPTY = 10, WBAR = 12, DRAIN = 13 };
+    const int W = out.W, RW = tc_rw(W), nblk = tc_nblk(W), NVP = tc_nvp(W);
+    const int kchunks = in.nc / 16;
+    const int nyb = (out.H + kTcRows - 1) / kTcRows, n_items = out.D * nyb;
+    bf16 *slab = reinterpret_cast<bf16 *>(smraw);                                // [nstage][2 halves][NVP][8]
+    bf16 *wsl = reinterpret_cast<bf16 *>(smraw + 2 * (size_t)nstage * NVP * 16);  // [kchunks][27][N/8][2][8][8]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bar[0]);
+    auto ba = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    if (tid == 0) {
+        for (int i = 0; i < 14; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ba(i)),
+                         "r"((i == TEMPTY || i == TEMPTY + 1) ? 128 : (i >= EMPTY && i < TEMPTY) || i == DRAIN ? nblk * nacc : 1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&tmem_base)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    const int nz = 3 * (kTcRows + 2) * RW;  // staged voxels holding real rows
+    // the tails past the real rows are only ever read by dropped positions: zero them once
+    for (int i = tid; i < 2 * nstage * (NVP - nz); i += blockDim.x) {
+        const int hp = i / (NVP - nz), v = nz + i - hp * (NVP - nz);  // hp: buffer x half
+        *reinterpret_cast<uint4 *>(slab + ((size_t)hp * NVP + v) * 8) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tails, for the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    if (warp == 4) {
+        // ---- producer: the weights once, then the slabs
+        if (lane == 0) {
+            bool ok = true;
+            const uint32_t wbytes = (uint32_t)kchunks * 27u * N * 32u, sbytes = 2u * (uint32_t)nz * 16u;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ba(WBAR)), "r"(wbytes) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(wsl)),
+                         "l"(Wtc), "r"(wbytes), "r"(ba(WBAR))
+                         : "memory");
+            int b = 0, u = 0, lb = -1, lu = 0;  // buffer and its use count; the last stage issued
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                const int z = item / nyb, y0 = (item - z * nyb) * kTcRows;
+                for (int kc = 0; kc < kchunks; kc++) {
+                    if (u >= 1 && !mbar_wait(ba(EMPTY + b), (uint32_t)((u - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ba(FULL + b)), "r"(sbytes)
+                                 : "memory");
+#pragma unroll
+                    for (int h = 0; h < 2; h++)
+                        asm volatile(
+                            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+                            "{%2, %3, %4, %5}], [%6];" ::"r"(
+                                (uint32_t)__cvta_generic_to_shared(slab + ((size_t)(2 * b + h) * NVP) * 8)),
+                            "l"(&tmap), "r"(in.c0 + 16 * kc + 8 * h), "r"(0), "r"(y0), "r"(z), "r"(ba(FULL + b))
+                            : "memory");
+                    lb = b;
+                    lu = u;
+                    if (++b == nstage) {
+                        b = 0;
+                        u++;
+                    }
+                }
+            }
+            if (!ok) {
+                atomicExch(err, 1);
+                // the copies in flight land before the CTA leaves (bounded)
+                if (lb >= 0) mbar_wait(ba(FULL + lb), (uint32_t)(lu & 1));
+            }
+        }
+    } else if (warp == 5) {
+        // ---- MMA issue: every slice of an item into accumulator (item parity); lane
+        // pa nblk + blk issues the MMAs of block blk and of the taps of partial pa (one
+        // instruction issues the MMAs of all these lanes)
+        const int nis = nblk * nacc;
+        if (lane < nis) {
+            const int my_pa = lane / nblk, my_blk = lane - my_pa * nblk;
+            bool ok = mbar_wait(ba(WBAR), 0u);
+            const uint32_t a_base = (uint32_t)__cvta_generic_to_shared(slab), b0 = (uint32_t)__cvta_generic_to_shared(wsl);
+            // D F32, A and B BF16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+            int b = 0, u = 0, i = 0;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, i++) {
+                const int a = i & 1;
+                if (i >= 2 && !mbar_wait(ba(TEMPTY + a), (uint32_t)(((i >> 1) + 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int kc = 0; kc < kchunks; kc++) {
+                    if (!mbar_wait(ba(FULL + b), (uint32_t)(u & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    // descriptors of the slice's first tap; a shift of the start address by
+                    // 16 d bytes adds d to a descriptor (its start field holds address / 16,
+                    // and every shared address here stays below 2^18)
+                    const uint64_t da0 = tc_desc(a_base + (uint32_t)b * 2u * (uint32_t)NVP * 16u, (uint32_t)NVP * 16u, 128);
+                    const uint64_t db0 = tc_desc(b0 + (uint32_t)(kc * 27) * N * 32u, 128, 256);
+                    for (int j = 0; j * nacc < 27; j++) {
+                        const int tap = j * nacc + my_pa;
+                        if (tap < 27) {
+                            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                            const int off = ((dz + 1) * (kTcRows + 2) + 1 + dy) * RW + 1 + dx;
+                            const uint64_t db = db0 + (uint64_t)(tap * N * 2);
+                            const uint64_t da = da0 + (uint64_t)(my_blk * 128 + off);
+                            const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
+                            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                             tmem + (uint32_t)((((a * nacc + my_pa) * nblk) + my_blk) * N)),
+                                         "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                        }
+                    }
+                    mma_commit(ba(EMPTY + b));  // the slab is free once these MMAs are done
+                    if (++b == nstage) {
+                        b = 0;
+                        u++;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(ba(TFULL + a));  // the accumulator is complete
+            }
+            if (!ok) {
+                atomicExch(err, 1);
+                mma_commit(ba(DRAIN));  // every MMA issued is done before TMEM is released
+                mbar_wait(ba(DRAIN), 0u);
+            }
+        }
+    } else {
+        // ---- epilogue (warps 0-3: TMEM lanes 32 warp .. + 31)
+        int i = 0;
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x, i++) {
+            const int a = i & 1;
+            const bool got = __all_sync(0xffffffffu, mbar_wait(ba(TFULL + a), (uint32_t)((i >> 1) & 1)));
+            if (!got) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int z = item / nyb, y0 = (item - z * nyb) * kTcRows;
+            for (int blk = 0; blk < nblk; blk++) {
+                const int m = blk * 128 + warp * 32 + lane;
+                const int r = m / RW, j = m - r * RW, y = y0 + r;
+                const bool live = r < kTcRows && y < out.H && j < W;
+#pragma unroll
+                for (int h = 0; h < NF; h++) {
+                    float f[16];
+#pragma unroll
+                    for (int e = 0; e < 16; e++) f[e] = 0.f;
+                    for (int pa = 0; pa < nacc; pa++) {  // the sum of the partials
+                        uint32_t v[16];
+                        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) +
+                                            (uint32_t)((((a * nacc + pa) * nblk) + blk) * N + 16 * h);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                            "%15}, [%16];\n"
+                            "tcgen05.wait::ld.sync.aligned;\n"
+                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                              "=r"(v[14]), "=r"(v[15])
+                            : "r"(ta)
+                            : "memory");
+#pragma unroll
+                        for (int e = 0; e < 16; e++) f[e] += __uint_as_float(v[e]);
+                    }
+                    if (!live) continue;
+#pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        const int co = 16 * h + e;
+                        const float x = f[e] + ((bias && co < cout_real) ? bias[co] : 0.f);
+                        f[e] = relu ? fmaxf(x, 0.f) : x;
+                    }
+                    if (outf) {
+#pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (16 * h + e < cout_real)
+                                outf[((size_t)(z * out.H + y) * W + j) * cout_real + 16 * h + e] = f[e];
+                    } else if (16 * h + 16 <= cout_real) {
+                        bf16 *dst = out.p + vox(out, z, y, j) * out.C + 16 * h;
+                        st8(dst, f);
+                        st8(dst + 8, f + 8);
+                    } else {
+                        for (int e = 0; e < 16 && 16 * h + e < cout_real; e++)
+                            out.p[vox(out, z, y, j) * out.C + 16 * h + e] = __float2bfloat16_rn(f[e]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(ba(TEMPTY + a));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
 // dW[tap][ci][co] += sum_v X[v + off(tap)][ci] dY[v][co] over this block's voxel tiles;
 // block = (tap, 16-channel ci group, 16-channel co group, slice), 4 warps.
 __global__ void __launch_bounds__(128) k_wgrad(View X, View dY, float *__restrict__ dW, int CoutP, int slices) {
@@ -640,6 +895,27 @@ void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool
     const int creal = dgrad ? L.cinp : L.cout;
     const float *bias = dgrad ? nullptr : L.b;
     const int xt = (out.W + 15) / 16;
+    // The persistent, pipelined form for 48 or more output channels (the layers where it
+    // measured faster: the 16- and 32-channel layers run at the tensor core's rate for
+    // N = 16 or 32 MMAs in either form, and there the per-row-pair CTAs of k_conv3d_tc
+    // overlap better).
+    const int nstage = tcp_stages(out.W, nf, in.nc / 16);
+    if (out.W <= kTcMaxW && (nf == 3 || nf == 4 || nf == 6) && nstage >= 2) {
+        static int sms = 0;
+        if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 148;
+        const int items = out.D * ((out.H + kTcRows - 1) / kTcRows);
+        const int nb = std::min(items, sms);
+        const int sm = tcp_smem_bytes(out.W, nf, in.nc / 16, nstage), cols = tcp_tmem_cols(out.W, nf);
+        const int nacc = tcp_nacc(out.W, nf);
+        const bf16 *wtc = dgrad ? L.wtc : L.wfc;
+        const CUtensorMap &tm = U->tmaps.at(in.p - in.c0);
+        switch (nf) {
+            case 3: k_conv3d_tcp<3><<<nb, 192, sm, st>>>(tm, in, wtc, bias, out, creal, relu, outf, cols, nstage, nacc, err); break;
+            case 4: k_conv3d_tcp<4><<<nb, 192, sm, st>>>(tm, in, wtc, bias, out, creal, relu, outf, cols, nstage, nacc, err); break;
+            default: k_conv3d_tcp<6><<<nb, 192, sm, st>>>(tm, in, wtc, bias, out, creal, relu, outf, cols, nstage, nacc, err); break;
+        }
+        return;
+    }
     if (out.W <= kTcMaxW && (nf == 1 || nf == 2 || nf == 3 || nf == 4 || nf == 6)) {
         const int nb = out.D * ((out.H + kTcRows - 1) / kTcRows);
         const int sm = tc_smem_bytes(out.W, nf), cols = tc_tmem_cols(out.W, nf);
@@ -840,6 +1116,10 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
                                     tc_smem_bytes(kTcMaxW, N)) == cudaSuccess;
     VD_TC_SMEM(1) VD_TC_SMEM(2) VD_TC_SMEM(3) VD_TC_SMEM(4) VD_TC_SMEM(6)
 #undef VD_TC_SMEM
+#define VD_TCP_SMEM(N) \
+    ok = ok && cudaFuncSetAttribute(k_conv3d_tcp<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcpSmemMax) == cudaSuccess;
+    VD_TCP_SMEM(3) VD_TCP_SMEM(4) VD_TCP_SMEM(6)
+#undef VD_TCP_SMEM
     if (!ok || cudaStreamCreateWithFlags(&U->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         vd_unet_destroy(U);
