@@ -556,39 +556,79 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tcp(const __grid_constant__ C
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
-// dW[tap][ci][co] += sum_v X[v + off(tap)][ci] dY[v][co] over this block's voxel tiles;
-// block = (tap, 16-channel ci group, 16-channel co group, slice), 4 warps.
-__global__ void __launch_bounds__(128) k_wgrad(View X, View dY, float *__restrict__ dW, int CoutP, int slices) {
-    __shared__ __align__(32) float tile[4][16 * 16];
+// dW[tap][ci][co] += sum_v X[v + off(tap)][ci] dY[v][co].  A block (16-channel ci group,
+// 16-channel co group, slice) walks row bands (z, y, up to 128 voxels of x) in grid
+// stride; per band it stages, with 16-byte loads, the 9 rows (z + dz, y + dy) of X it
+// needs (x from one before the band to one past it, 16 ci) and the band of dY (16 co)
+// in shared memory, and forms every tap's 16 x 16 x 16 products from there: warp w
+// accumulates taps w, w + 8, w + 16, w + 24, each loaded operand serving up to 27 taps.
+// At the end the 27 accumulators go to dW by FP32 atomics.  (The tensor-core MMAs of
+// the convolutions do not fit here: with 16-96 channels a tap's GEMM is at most 96 wide,
+// and one operand descriptor cannot span several taps' different shifts.)
+constexpr int kWgTiles = 8;  // 16-voxel tiles per staged band
+__global__ void __launch_bounds__(256) k_wgrad(View X, View dY, float *__restrict__ dW, int CoutP, int slices) {
+    __shared__ __align__(32) bf16 xs[9][kWgTiles * 16 + 2][16];
+    __shared__ __align__(32) bf16 ys[kWgTiles * 16][16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nci = X.nc / 16, nco = dY.nc / 16;
+    const int nco = dY.nc / 16;
     int b = blockIdx.x;
     const int slice = b % slices;
     b /= slices;
-    const int cof = b % nco;
-    b /= nco;
-    const int cif = b % nci;
-    const int tap = b / nci;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int xt_n = (dY.W + 15) / 16;
-    const long ntiles = (long)dY.D * dY.H * xt_n;
-    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
-    wmma::fill_fragment(acc, 0.f);
-    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> a;
-    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> bm;
-    for (long t = (long)slice * 4 + warp; t < ntiles; t += (long)slices * 4) {
-        const int xt = (int)(t % xt_n), y = (int)((t / xt_n) % dY.H), z = (int)(t / ((long)xt_n * dY.H));
-        const int x0 = xt * 16;
-        wmma::load_matrix_sync(a, X.p + vox(X, z + dz, y + dy, x0 + dx) * X.C + 16 * cif, X.C);
-        wmma::load_matrix_sync(bm, dY.p + vox(dY, z, y, x0) * dY.C + 16 * cof, dY.C);
-        wmma::mma_sync(acc, a, bm, acc);
+    const int cof = b % nco, cif = b / nco;
+    const int xt_n = (dY.W + 15) / 16, nxc = (xt_n + kWgTiles - 1) / kWgTiles;
+    const long nbands = (long)dY.D * dY.H * nxc;
+    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) wmma::fill_fragment(acc[k], 0.f);
+    for (long band = slice; band < nbands; band += slices) {
+        const int xc = (int)(band % nxc);
+        const long zy = band / nxc;
+        const int y = (int)(zy % dY.H), z = (int)(zy / dY.H);
+        const int t0 = xc * kWgTiles, nt = min(kWgTiles, xt_n - t0), nv = 16 * nt, x0 = 16 * t0;
+        __syncthreads();  // the last band's operands are read
+        // X: row r = 3 (dz + 1) + dy + 1, voxel x0 - 1 + v (the zero halo and the row slack
+        // cover the ends), two 16-byte halves of the 16 ci
+        for (int i = threadIdx.x; i < 9 * (nv + 2) * 2; i += blockDim.x) {
+            const int h = i & 1, rv = i >> 1, r = rv / (nv + 2), v = rv - r * (nv + 2);
+            const int dz = r / 3 - 1, dy = r - 3 * (r / 3) - 1;
+            *reinterpret_cast<uint4 *>(&xs[r][v][8 * h]) =
+                *reinterpret_cast<const uint4 *>(X.p + vox(X, z + dz, y + dy, x0 - 1 + v) * X.C + 16 * cif + 8 * h);
+        }
+        for (int i = threadIdx.x; i < nv * 2; i += blockDim.x) {
+            const int h = i & 1, v = i >> 1;
+            *reinterpret_cast<uint4 *>(&ys[v][8 * h]) =
+                *reinterpret_cast<const uint4 *>(dY.p + vox(dY, z, y, x0 + v) * dY.C + 16 * cof + 8 * h);
+        }
+        __syncthreads();
+        for (int t = 0; t < nt; t++) {
+            wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> bm;
+            wmma::load_matrix_sync(bm, &ys[16 * t][0], 16);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int tap = warp + 8 * k;
+                if (tap < 27) {
+                    const int r = tap / 3, dx = tap % 3 - 1;  // r = 3 (dz + 1) + dy + 1
+                    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> a;
+                    wmma::load_matrix_sync(a, &xs[r][16 * t + 1 + dx][0], 16);
+                    wmma::mma_sync(acc[k], a, bm, acc[k]);
+                }
+            }
+        }
     }
-    wmma::store_matrix_sync(tile[warp], acc, 16, wmma::mem_row_major);
-    __syncwarp();
-    for (int e = lane; e < 256; e += 32) {
-        const int ci = 16 * cif + (e >> 4), co = 16 * cof + (e & 15);
-        const float v = tile[warp][e];
-        if (v != 0.f) atomicAdd(&dW[((size_t)tap * X.nc + ci) * CoutP + co], v);
+    __syncthreads();
+    float *tl = reinterpret_cast<float *>(&xs[0][0][0]) + 256 * warp;  // the staging area is free now
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int tap = warp + 8 * k;
+        if (tap >= 27) break;
+        wmma::store_matrix_sync(tl, acc[k], 16, wmma::mem_row_major);
+        __syncwarp();
+        for (int e = lane; e < 256; e += 32) {
+            const int ci = 16 * cif + (e >> 4), co = 16 * cof + (e & 15);
+            const float v = tl[e];
+            if (v != 0.f) atomicAdd(&dW[((size_t)tap * X.nc + ci) * CoutP + co], v);
+        }
+        __syncwarp();
     }
 }
 
@@ -944,9 +984,12 @@ void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool
 
 void wgrad(cudaStream_t st, View X, View dY, const LayerDev &L) {
     const int nci = X.nc / 16, nco = dY.nc / 16;
-    const long tiles = (long)dY.D * dY.H * ((dY.W + 15) / 16);
-    const int slices = (int)std::max<long>(1, std::min<long>(64, (tiles + 63) / 64));
-    k_wgrad<<<27 * nci * nco * slices, 128, 0, st>>>(X, dY, L.gw, L.coutp, slices);
+    const int xt_n = (dY.W + 15) / 16;
+    const long bands = (long)dY.D * dY.H * ((xt_n + kWgTiles - 1) / kWgTiles);
+    // about six blocks per SM in all (measured best among 2-16; each block ends with 27 x 256
+    // atomics)
+    const int slices = (int)std::max<long>(1, std::min<long>(bands, (6 * 148 + nci * nco - 1) / (nci * nco)));
+    k_wgrad<<<nci * nco * slices, 256, 0, st>>>(X, dY, L.gw, L.coutp, slices);
     k_bias_grad<<<(int)std::min<long>(2 * 148, (nvox(dY) * dY.nc / 8 + 255) / 256), 256, 0, st>>>(dY, L.cout, L.gb);
 }
 
