@@ -113,33 +113,54 @@ __global__ void __launch_bounds__(128) k_conv3d(View in, const bf16 *__restrict_
 // ------------------------------------------------------------------ tcgen05 convolution
 //
 // The convolution as an implicit GEMM on the 5th-generation tensor cores: a CTA of 4
-// warps owns kTcRows output rows (z, y0 ..), whole in x.  Output position m = r RW + j
+// warps owns R = tc_rows(W, H) output rows (z, y0 ..), whole in x.  Output position m = r RW + j
 // (row r, column j < RW = W + 2; columns j >= W are computed and dropped) needs, for tap
 // (dz, dy, dx), the staged input voxel m + off(tap), off = ((dz+1)(R+2) + 1 + dy) RW + 1 + dx,
 // so every tap's A operand (128 positions x 16 channels, K-major) is the staged slab
-// read from a shifted start address.  The slab holds the 3 x (kTcRows + 2) input rows
+// read from a shifted start address.  The slab holds the 3 x (R + 2) input rows
 // (x from -1 to W, zero outside the volume) of one 16-channel slice as two channel-half
 // planes of 16 B per voxel, staged by two TMA box loads: core matrices of 8 voxels x 8
 // channels are 128 contiguous bytes (SBO = 128, LBO = the plane stride).  B (N output
 // channels x 16 input channels of one tap, K-major) comes pre-packed in the same core
-// layout (one bulk copy).  One thread issues 27 taps x nblk MMAs (M = 128, N = 16 NF,
-// K = 16, BF16 in, FP32 accumulators in TMEM, nblk x N columns) per input slice and
-// commits them to an mbarrier; the warps then read their 32 TMEM lanes (tcgen05.ld) for
-// the epilogue.
-constexpr int kTcRows = 2;
+// layout (one bulk copy).  Lane blk of warp 0 issues the 27 taps' MMAs of block blk
+// (M = 128, N = 16 NF, K = 16, BF16 in, FP32 accumulators in TMEM, nblk x N columns) per
+// input slice and commits them to an mbarrier (a lane issues small MMAs at a limited
+// rate, so the blocks' lanes issue side by side); the warps then read their 32 TMEM
+// lanes (tcgen05.ld) for the epilogue.
 constexpr int kTcMaxW = 128;  // wider rows take the generic WMMA kernel
 __device__ __forceinline__ void st8(bf16 *p, const float f[8]);
 
 __host__ __device__ inline int tc_rw(int W) { return W + 2; }
-__host__ __device__ inline int tc_nblk(int W) { return (kTcRows * tc_rw(W) + 127) / 128; }
-// staged voxels per plane (the shifted A windows of the last block stay inside)
-__host__ __device__ inline int tc_nvp(int W) {
-    return (tc_nblk(W) * 128 + (2 * (kTcRows + 2) + 2) * tc_rw(W) + 2 + 7) / 8 * 8;
+// Output rows per CTA: the count (2..8, at most 4 blocks of 128 positions) that wastes
+// the fewest MMA positions on the dropped columns, the unused tail of the last block and
+// the rows past H of the last row group (at 96^3 five rows: 490 of 512 positions; two
+// rows used 196 of 256).
+__host__ __device__ inline int tc_rows(int W, int H) {
+    const int rw = tc_rw(W);
+    int best = 2;
+    long best_cost = -1;
+    for (int r = 2; r <= 8; r++) {
+        const int nblk = (r * rw + 127) / 128;
+        if (nblk > 4) break;
+        const long cost = (long)((H + r - 1) / r) * nblk;  // blocks per plane
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = r;
+        }
+    }
+    return best;
 }
-__host__ __device__ inline int tc_smem_bytes(int W, int NF) { return 2 * tc_nvp(W) * 16 + 27 * 16 * NF * 32 + 64; }
-__host__ inline int tc_tmem_cols(int W, int NF) {
+__host__ __device__ inline int tc_nblk(int W, int H) { return (tc_rows(W, H) * tc_rw(W) + 127) / 128; }
+// staged voxels per plane (the shifted A windows of the last block stay inside)
+__host__ __device__ inline int tc_nvp(int W, int H) {
+    return (tc_nblk(W, H) * 128 + (2 * (tc_rows(W, H) + 2) + 2) * tc_rw(W) + 2 + 7) / 8 * 8;
+}
+__host__ __device__ inline int tc_smem_bytes(int W, int H, int NF) {
+    return 2 * tc_nvp(W, H) * 16 + 27 * 16 * NF * 32 + 64;
+}
+__host__ inline int tc_tmem_cols(int W, int H, int NF) {
     int c = 32;
-    while (c < tc_nblk(W) * 16 * NF) c <<= 1;
+    while (c < tc_nblk(W, H) * 16 * NF) c <<= 1;
     return c;
 }
 
@@ -171,15 +192,15 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
     __shared__ __align__(8) uint64_t mbar, mbar_ld;
     __shared__ uint32_t tmem_base;
     constexpr int N = 16 * NF;
-    const int W = out.W, RW = tc_rw(W), nblk = tc_nblk(W), NVP = tc_nvp(W);
+    const int W = out.W, RW = tc_rw(W), R = tc_rows(W, out.H), nblk = tc_nblk(W, out.H), NVP = tc_nvp(W, out.H);
     bf16 *planes = reinterpret_cast<bf16 *>(smraw);                     // [2][NVP][8]
     bf16 *wsl = reinterpret_cast<bf16 *>(smraw + 2 * NVP * 16);         // [27][N/8][2][8][8]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nyb = (out.H + kTcRows - 1) / kTcRows;
-    const int z = blockIdx.x / nyb, y0 = (blockIdx.x - z * nyb) * kTcRows;
+    const int nyb = (out.H + R - 1) / R;
+    const int z = blockIdx.x / nyb, y0 = (blockIdx.x - z * nyb) * R;
     const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar), mbl = (uint32_t)__cvta_generic_to_shared(&mbar_ld);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(nblk));  // one commit per block's lane
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbl));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -193,7 +214,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const int nz = 3 * (kTcRows + 2) * RW;  // staged voxels holding real rows
+    const int nz = 3 * (R + 2) * RW;  // staged voxels holding real rows
     const int kchunks = in.nc / 16;
     // the tail past the real rows is only ever read by dropped positions: zero it once
     for (int i = tid; i < 2 * (NVP - nz); i += 128) {
@@ -205,7 +226,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
     for (int kc = 0; kc < kchunks && ok; kc++) {
         const int k0 = 16 * kc;
         // stage the slice with the tensor memory accelerator: per channel half one box of
-        // 8 channels x RW voxels x (kTcRows + 2) rows x 3 planes (buffer coordinates: x
+        // 8 channels x RW voxels x (R + 2) rows x 3 planes (buffer coordinates: x
         // from the halo column, rows from y0 - 1, planes from z - 1; rows and planes past
         // the buffer read as zero), plus the slice's weights by one bulk copy
         if (tid == 0) {
@@ -230,22 +251,23 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
             ok = false;
             break;
         }
-        if (tid == 0) {
+        if (tid < nblk) {  // lane blk: block blk's MMAs
+            const int blk = tid;
             const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(planes), b0 = (uint32_t)__cvta_generic_to_shared(wsl);
             // D F32, A and B BF16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+            // a shift of the start address by 16 d bytes adds d to a descriptor (its start
+            // field holds address / 16; shared addresses stay below 2^18)
+            const uint64_t da0 = tc_desc(a0 + (uint32_t)(blk * 128) * 16u, (uint32_t)NVP * 16u, 128);
+            const uint64_t db0 = tc_desc(b0, 128, 256);
             for (int tap = 0; tap < 27; tap++) {
                 const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                const int off = ((dz + 1) * (kTcRows + 2) + 1 + dy) * RW + 1 + dx;
-                const uint64_t db = tc_desc(b0 + (uint32_t)tap * N * 32u, 128, 256);
-                for (int blk = 0; blk < nblk; blk++) {
-                    const uint64_t da = tc_desc(a0 + (uint32_t)(blk * 128 + off) * 16u, (uint32_t)NVP * 16u, 128);
-                    const uint32_t acc = (kc > 0 || tap > 0) ? 1u : 0u;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                     tmem + (uint32_t)(blk * N)),
-                                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
-                }
+                const int off = ((dz + 1) * (R + 2) + 1 + dy) * RW + 1 + dx;
+                const uint32_t acc = (kc > 0 || tap > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                 tmem + (uint32_t)(blk * N)),
+                             "l"(da0 + (uint64_t)off), "l"(db0 + (uint64_t)(tap * N * 2)), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
                          : "memory");
@@ -260,7 +282,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
         for (int blk = 0; blk < nblk; blk++) {
             const int m = blk * 128 + warp * 32 + lane;
             const int r = m / RW, j = m - r * RW, y = y0 + r;
-            const bool live = r < kTcRows && y < out.H && j < W;
+            const bool live = r < R && y < out.H && j < W;
 #pragma unroll
             for (int h = 0; h < NF; h++) {
                 uint32_t v[16];
@@ -314,14 +336,14 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
 // weights, and a drain for the error path.  Every wait is bounded; a wait that gives up
 // sets *err and its role stops, and the others then give up too.
 constexpr int kTcpMaxStages = 4;
-__host__ __device__ inline int tcp_smem_bytes(int W, int NF, int kchunks, int nstage) {
-    return nstage * 2 * tc_nvp(W) * 16 + kchunks * 27 * 16 * NF * 32;
+__host__ __device__ inline int tcp_smem_bytes(int W, int H, int NF, int kchunks, int nstage) {
+    return nstage * 2 * tc_nvp(W, H) * 16 + kchunks * 27 * 16 * NF * 32;
 }
 constexpr int kTcpSmemMax = 225 * 1024;
 // the most slab buffers (2..4) that fit, 0 if two do not
-__host__ inline int tcp_stages(int W, int NF, int kchunks) {
+__host__ inline int tcp_stages(int W, int H, int NF, int kchunks) {
     for (int ns = kTcpMaxStages; ns >= 2; ns--)
-        if (tcp_smem_bytes(W, NF, kchunks, ns) <= kTcpSmemMax) return ns;
+        if (tcp_smem_bytes(W, H, NF, kchunks, ns) <= kTcpSmemMax) return ns;
     return 0;
 }
 // Partial accumulators per item: tap t goes to partial t % nacc and is issued by its own
@@ -329,14 +351,17 @@ __host__ inline int tcp_stages(int W, int NF, int kchunks) {
 // epilogue adds the partials.  The most (<= 4) for which two items' accumulators fit the
 // 512 TMEM columns.
 constexpr int kTcpMaxAcc = 4;
-__host__ inline int tcp_nacc(int W, int NF) {
+__host__ inline int tcp_nacc(int W, int H, int NF) {
     int n = kTcpMaxAcc;
-    while (n > 1 && 2 * n * tc_nblk(W) * 16 * NF > 512) n--;
+    while (n > 1 && 2 * n * tc_nblk(W, H) * 16 * NF > 512) n--;
     return n;
 }
-__host__ inline int tcp_tmem_cols(int W, int NF) {
+// 0 when even one partial per item does not fit (the per-row-group kernel then runs)
+__host__ inline int tcp_tmem_cols(int W, int H, int NF) {
+    const int need = 2 * tcp_nacc(W, H, NF) * tc_nblk(W, H) * 16 * NF;
+    if (need > 512) return 0;
     int c = 32;
-    while (c < 2 * tcp_nacc(W, NF) * tc_nblk(W) * 16 * NF) c <<= 1;
+    while (c < need) c <<= 1;
     return c;
 }
 
@@ -357,9 +382,9 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tcp(const __grid_constant__ C
     __shared__ uint32_t tmem_base;
     constexpr int N = 16 * NF;
     enum { FULL = 0, EMPTY = 4, TFULL = 8, TEMPTY = 10, WBAR = 12, DRAIN = 13 };
-    const int W = out.W, RW = tc_rw(W), nblk = tc_nblk(W), NVP = tc_nvp(W);
+    const int W = out.W, RW = tc_rw(W), R = tc_rows(W, out.H), nblk = tc_nblk(W, out.H), NVP = tc_nvp(W, out.H);
     const int kchunks = in.nc / 16;
-    const int nyb = (out.H + kTcRows - 1) / kTcRows, n_items = out.D * nyb;
+    const int nyb = (out.H + R - 1) / R, n_items = out.D * nyb;
     bf16 *slab = reinterpret_cast<bf16 *>(smraw);                                // [nstage][2 halves][NVP][8]
     bf16 *wsl = reinterpret_cast<bf16 *>(smraw + 2 * (size_t)nstage * NVP * 16);  // [kchunks][27][N/8][2][8][8]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -377,7 +402,7 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tcp(const __grid_constant__ C
                      "r"(tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    const int nz = 3 * (kTcRows + 2) * RW;  // staged voxels holding real rows
+    const int nz = 3 * (R + 2) * RW;  // staged voxels holding real rows
     // the tails past the real rows are only ever read by dropped positions: zero them once
     for (int i = tid; i < 2 * nstage * (NVP - nz); i += blockDim.x) {
         const int hp = i / (NVP - nz), v = nz + i - hp * (NVP - nz);  // hp: buffer x half
@@ -400,7 +425,7 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tcp(const __grid_constant__ C
                          : "memory");
             int b = 0, u = 0, lb = -1, lu = 0;  // buffer and its use count; the last stage issued
             for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-                const int z = item / nyb, y0 = (item - z * nyb) * kTcRows;
+                const int z = item / nyb, y0 = (item - z * nyb) * R;
                 for (int kc = 0; kc < kchunks; kc++) {
                     if (u >= 1 && !mbar_wait(ba(EMPTY + b), (uint32_t)((u - 1) & 1))) {
                         ok = false;
@@ -463,7 +488,7 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tcp(const __grid_constant__ C
                         const int tap = j * nacc + my_pa;
                         if (tap < 27) {
                             const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                            const int off = ((dz + 1) * (kTcRows + 2) + 1 + dy) * RW + 1 + dx;
+                            const int off = ((dz + 1) * (R + 2) + 1 + dy) * RW + 1 + dx;
                             const uint64_t db = db0 + (uint64_t)(tap * N * 2);
                             const uint64_t da = da0 + (uint64_t)(my_blk * 128 + off);
                             const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
@@ -499,11 +524,11 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tcp(const __grid_constant__ C
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int z = item / nyb, y0 = (item - z * nyb) * kTcRows;
+            const int z = item / nyb, y0 = (item - z * nyb) * R;
             for (int blk = 0; blk < nblk; blk++) {
                 const int m = blk * 128 + warp * 32 + lane;
                 const int r = m / RW, j = m - r * RW, y = y0 + r;
-                const bool live = r < kTcRows && y < out.H && j < W;
+                const bool live = r < R && y < out.H && j < W;
 #pragma unroll
                 for (int h = 0; h < NF; h++) {
                     float f[16];
@@ -939,14 +964,14 @@ void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool
     // measured faster: the 16- and 32-channel layers run at the tensor core's rate for
     // N = 16 or 32 MMAs in either form, and there the per-row-pair CTAs of k_conv3d_tc
     // overlap better).
-    const int nstage = tcp_stages(out.W, nf, in.nc / 16);
-    if (out.W <= kTcMaxW && (nf == 3 || nf == 4 || nf == 6) && nstage >= 2) {
+    const int nstage = tcp_stages(out.W, out.H, nf, in.nc / 16);
+    if (out.W <= kTcMaxW && (nf == 3 || nf == 4 || nf == 6) && nstage >= 2 && tcp_tmem_cols(out.W, out.H, nf) > 0) {
         static int sms = 0;
         if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 148;
-        const int items = out.D * ((out.H + kTcRows - 1) / kTcRows);
+        const int rows = tc_rows(out.W, out.H), items = out.D * ((out.H + rows - 1) / rows);
         const int nb = std::min(items, sms);
-        const int sm = tcp_smem_bytes(out.W, nf, in.nc / 16, nstage), cols = tcp_tmem_cols(out.W, nf);
-        const int nacc = tcp_nacc(out.W, nf);
+        const int sm = tcp_smem_bytes(out.W, out.H, nf, in.nc / 16, nstage), cols = tcp_tmem_cols(out.W, out.H, nf);
+        const int nacc = tcp_nacc(out.W, out.H, nf);
         const bf16 *wtc = dgrad ? L.wtc : L.wfc;
         const CUtensorMap &tm = U->tmaps.at(in.p - in.c0);
         switch (nf) {
@@ -956,9 +981,10 @@ void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool
         }
         return;
     }
-    if (out.W <= kTcMaxW && (nf == 1 || nf == 2 || nf == 3 || nf == 4 || nf == 6)) {
-        const int nb = out.D * ((out.H + kTcRows - 1) / kTcRows);
-        const int sm = tc_smem_bytes(out.W, nf), cols = tc_tmem_cols(out.W, nf);
+    if (out.W <= kTcMaxW && (nf == 1 || nf == 2 || nf == 3 || nf == 4 || nf == 6) &&
+        tc_smem_bytes(out.W, out.H, nf) <= kTcpSmemMax) {
+        const int rows = tc_rows(out.W, out.H), nb = out.D * ((out.H + rows - 1) / rows);
+        const int sm = tc_smem_bytes(out.W, out.H, nf), cols = tc_tmem_cols(out.W, out.H, nf);
         const bf16 *wtc = dgrad ? L.wtc : L.wfc;
         const CUtensorMap &tm = U->tmaps.at(in.p - in.c0);
         switch (nf) {
@@ -1100,7 +1126,7 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
         ok = ok && make_view(U, s.g, D / s.s, H / s.s, W / s.s, s.c);
     }
     // one TMA tensor map per buffer: dims (C, Wp, H + 2, D + 2), box (8 channels, W + 2
-    // voxels, kTcRows + 2 rows, 3 planes), zero fill past the buffer
+    // voxels, tc_rows + 2 rows, 3 planes), zero fill past the buffer
     if (ok) {
         static void *encode = nullptr;
         static std::once_flag once;
@@ -1122,7 +1148,7 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
                 const cuuint64_t dims[4] = {(cuuint64_t)v->C, (cuuint64_t)v->Wp, (cuuint64_t)v->H + 2, (cuuint64_t)v->D + 2};
                 const cuuint64_t strides[3] = {(cuuint64_t)v->C * 2, (cuuint64_t)v->C * 2 * v->Wp,
                                                (cuuint64_t)v->C * 2 * v->Wp * (v->H + 2)};
-                const cuuint32_t box[4] = {8, (cuuint32_t)tc_rw(v->W), kTcRows + 2, 3};
+                const cuuint32_t box[4] = {8, (cuuint32_t)tc_rw(v->W), (cuuint32_t)tc_rows(v->W, v->H) + 2, 3};
                 const cuuint32_t es[4] = {1, 1, 1, 1};
                 ok = v->W > kTcMaxW ||
                      ((EncodeFn)encode)(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, v->p, dims, strides, box, es,
@@ -1156,7 +1182,7 @@ vd_status vd_unet_create(int nx, int ny, int nz, unsigned long long seed, vd_une
     // the staged convolutions may take more than the default 48 KB of shared memory
 #define VD_TC_SMEM(N) \
     ok = ok && cudaFuncSetAttribute(k_conv3d_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    tc_smem_bytes(kTcMaxW, N)) == cudaSuccess;
+                                    kTcpSmemMax) == cudaSuccess;
     VD_TC_SMEM(1) VD_TC_SMEM(2) VD_TC_SMEM(3) VD_TC_SMEM(4) VD_TC_SMEM(6)
 #undef VD_TC_SMEM
 #define VD_TCP_SMEM(N) \
