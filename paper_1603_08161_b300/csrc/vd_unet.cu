@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
 
 // The same convolution as a persistent, pipelined kernel, for layers whose packed
 // weights (every input slice) fit in shared memory beside at least two slab buffers:
-// one CTA per SM walks the (plane, row pair) items in grid stride.  Warp 4 (one lane)
+// one CTA per SM walks the (plane, row group) items in grid stride.  Warp 4 (one lane)
 // stages the weights once and then, slice after slice, the slab of the next (item, input
 // slice) by TMA into the next of `nstage` (2-4) buffers, as soon as the MMAs that read
 // it last are done; warp 5 (one lane) issues each slice's 27 x nblk MMAs into one of two
@@ -962,7 +962,7 @@ void conv(cudaStream_t st, View in, const LayerDev &L, View out, bool relu, bool
     const int xt = (out.W + 15) / 16;
     // The persistent, pipelined form for 48 or more output channels (the layers where it
     // measured faster: the 16- and 32-channel layers run at the tensor core's rate for
-    // N = 16 or 32 MMAs in either form, and there the per-row-pair CTAs of k_conv3d_tc
+    // N = 16 or 32 MMAs in either form, and there the per-row-group CTAs of k_conv3d_tc
     // overlap better).
     const int nstage = tcp_stages(out.W, out.H, nf, in.nc / 16);
     if (out.W <= kTcMaxW && (nf == 3 || nf == 4 || nf == 6) && nstage >= 2 && tcp_tmem_cols(out.W, out.H, nf) > 0) {
