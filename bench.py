@@ -485,20 +485,27 @@ def main():
             blats.append(Lb)
         B = vd.Batch(blats)
         B.solve(prm)
-        # the persistent form (one cooperative launch per Gauss-Newton iteration for every
-        # lattice's position step), timed for the record before the tuner picks a plan
-        B.set_persistent(True, 512, 1, 4.0)
-        for _ in range(2):
-            B.solve(prm)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(3):
-            B.solve_async(prm)
-            B.reports()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_persistent = e0.elapsed_time(e1) / 3
-        B.set_persistent(False)
+        # the persistent forms (one cooperative launch per Gauss-Newton iteration for every
+        # lattice's position step: vectors in global memory, or waves of the shared-memory
+        # step), timed for the record before the tuner picks a plan
+
+        def form_ms():
+            for _ in range(2):
+                B.solve(prm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                B.solve_async(prm)
+                B.reports()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 3
+        B.set_persistent(vd.VD_BATCH_GLOBAL, 512, 1, 4.0)
+        ms_persistent = form_ms()
+        B.set_persistent(vd.VD_BATCH_WAVES)
+        ms_waves = form_ms()
+        waves_plan = {"ctas": int(sum(B.groups())), "waves": B.waves()}
+        B.set_persistent(vd.VD_BATCH_BRANCHES)
         n_streams, _ = B.tune(prm)
         plan = B.plan()
 
@@ -531,6 +538,7 @@ def main():
             "lattices": len(blats), "total_nodes": int(sum(int(np.prod(b.dims)) for b in bframes)),
             "branches": n_streams, "launches_per_batch": B.launch_count(), "tuned_plan": plan,
             "persistent_form_ms": ms_persistent,
+            "waves_form_ms": ms_waves, "waves_form": waves_plan,
             "sequential_plain": {"value": world * len(blats) * 1000.0 / ts, "unit": "solves/s", "ms": ts},
             "speedup_vs_plain": ts / tb}
         B.close()

@@ -245,6 +245,14 @@ vd_status vd_profile_read(vd_lattice *lat, double *total_ms, int *launches);
 vd_status vd_launch_counts(vd_lattice *lat, const vd_solve_params *params, int *per_solve,
                            int *per_frame);
 
+/* The partition of the persistent position step (Sec. 7.1) that vd_solve uses for this
+ * lattice (any pointer may be NULL): CTAs and slots per CTA (0, 0 when the position step
+ * is streamed instead), and for an all-nodes lattice the brick of by x bz x-rows that each
+ * CTA owns (0 x 0: contiguous slot ranges); padded = 1 when the bricks' rows are padded
+ * to a multiple of 4 slots or the far bricks are ragged (nx % 4 != 0, or ny, nz not
+ * multiples of by, bz). */
+vd_status vd_pcg_plan(vd_lattice *lat, int *ctas, int *chunk, int *by, int *bz, int *padded);
+
 /* ---- batched solve: many independent lattices in one graph launch ---- */
 
 typedef struct vd_batch vd_batch; /* opaque; references the lattices, owns no lattice data */
@@ -273,8 +281,9 @@ vd_status vd_batch_get_reports(vd_batch *batch, vd_solve_report *out);
  * of concurrent branches (1, 2, 4, ... up to the batch size) and branch order (largest
  * lattice first, or as given), then for the fastest of those each size threshold
  * (2^19, 2^17, 2^15, 2^13 active nodes) above which lattices run ahead with their
- * persistent position step, then the persistent form over every lattice
- * (vd_batch_set_persistent) for 256 / 512 threads, 1 / 2 / 4 CTAs per SM, sample
+ * persistent position step, then the waves of the shared-memory position step
+ * (VD_BATCH_WAVES) with 8 / 16 branches, then the persistent form with vectors in
+ * global memory (VD_BATCH_GLOBAL) for 256 / 512 threads, 1 / 2 / 4 CTAs per SM, sample
  * weights 1 / 4 and 8 / 16 branches; keep the fastest.  Runs the solve several times (the
  * lattices' warps change).  Reports the number of branches and the time per batched
  * solve (ms). */
@@ -288,24 +297,50 @@ vd_status vd_batch_tune(vd_batch *batch, const vd_solve_params *params, int *str
  * VD_ERR_INVALID_ARG for NULL or out-of-range values. */
 vd_status vd_batch_set_plan(vd_batch *batch, int streams, int largest_first, long long run_ahead_nodes);
 
-/* Run the batch's position steps as one persistent cooperative kernel per Gauss-Newton
- * iteration (on != 0): the CTAs, ctas_per_sm per SM, each of `threads` threads (256 or
- * 512), are split among the lattices in proportion to (active nodes + sample_weight x
- * samples), at least one each; each lattice's group runs its PCG (the recurrence of
- * vd_solve, vectors in global memory) with its own barriers and reductions, and the
- * other stages of the iteration run as per-lattice branches between these launches.
- * on = 0 returns to the graph of per-lattice schedules.  VD_ERR_INVALID_ARG for other
- * thread counts, ctas_per_sm outside [1, 8] or a negative weight; a setting the device
- * cannot hold (the CTAs must all be resident) fails at the next solve. */
-vd_status vd_batch_set_persistent(vd_batch *batch, int on, int threads, int ctas_per_sm, float sample_weight);
+/* Forms of a batch's position steps (the `form` of vd_batch_set_persistent). */
+#define VD_BATCH_BRANCHES 0 /* every lattice's schedule as a branch of the graph */
+#define VD_BATCH_GLOBAL 1   /* one cooperative kernel over all lattices, vectors in global memory */
+#define VD_BATCH_WAVES 2    /* one cooperative kernel, lattices in waves of the shared-memory step */
 
-/* The batch's current plan (any pointer may be NULL): persistent form or not, its
- * threads, CTAs per SM and sample weight, and the number of concurrent branches. */
+/* Run the batch's position steps as one persistent cooperative kernel per Gauss-Newton
+ * iteration, the other stages of the iteration as per-lattice branches between these
+ * launches.  form = VD_BATCH_GLOBAL: the CTAs, ctas_per_sm per SM, each of `threads`
+ * threads (256 or 512), are split among the lattices in proportion to (active nodes +
+ * sample_weight x samples), at least one each; each lattice's group runs its PCG (the
+ * recurrence of vd_solve, vectors in global memory) with its own barriers and
+ * reductions.  form = VD_BATCH_WAVES (threads, ctas_per_sm and sample_weight are then
+ * not used): one CTA per SM; each lattice takes the fewest CTAs whose slots fit in
+ * shared memory and runs the position step of vd_solve on them (vectors in shared and
+ * tensor memory, its own barriers); the lattices' CTA groups are packed into waves of
+ * at most one CTA per SM (largest first, first fit), and each CTA runs its groups wave
+ * after wave within the one launch.  Every lattice must fit on the SMs: at most
+ * SMs x 6,144 active nodes (909,312 on a 148-SM B300, e.g. a 96^3 lattice).  form =
+ * VD_BATCH_BRANCHES returns to the graph of per-lattice schedules.  VD_ERR_INVALID_ARG
+ * for another form, other thread counts, ctas_per_sm outside [1, 8] or a negative
+ * weight; a setting the device cannot hold (the CTAs must all be resident) fails at the
+ * next solve. */
+vd_status vd_batch_set_persistent(vd_batch *batch, int form, int threads, int ctas_per_sm, float sample_weight);
+
+/* VD_BATCH_WAVES: a lattice's CTA group holds at most `samples_per_cta` of its samples
+ * per CTA (beside the shared-memory bound on its nodes), up to one CTA per SM; a CTA's
+ * sample warps take their share of the samples' J^T J p while its stencil warps run.
+ * Default 1024; vd_batch_tune searches it.  VD_ERR_INVALID_ARG below 32. */
+vd_status vd_batch_set_wave_share(vd_batch *batch, int samples_per_cta);
+
+/* The batch's current plan (any pointer may be NULL): the form of its position steps
+ * (VD_BATCH_*), the threads, CTAs per SM and sample weight of VD_BATCH_GLOBAL, and the
+ * number of concurrent branches. */
 vd_status vd_batch_get_plan(const vd_batch *batch, int *persistent, int *threads, int *ctas_per_sm,
                             float *sample_weight, int *streams);
 
 /* Kernel launches in one batched solve (after the first solve or tune). */
 vd_status vd_batch_launch_count(const vd_batch *batch, int *launches);
+
+/* The CTA groups of the last persistent build (VD_BATCH_GLOBAL or VD_BATCH_WAVES):
+ * `ctas` (may be NULL; room for the batch's lattice count) receives each lattice's CTAs,
+ * `waves` (may be NULL) the number of waves over all launch sets (0 for
+ * VD_BATCH_GLOBAL).  Both are zero before the first such build. */
+vd_status vd_batch_get_groups(const vd_batch *batch, int *ctas, int *waves);
 
 /* One-line description of the batch's last error. */
 const char *vd_batch_last_error(const vd_batch *batch);

@@ -460,76 +460,104 @@ void enqueue_pcg(Launcher &Lc, const Ctx &c, Scal *sc, const Grid &gr, int K, do
     }
 }
 
-// 6 floats per slot in shared memory (p and z / q; r and x are in tensor memory), and
-// at most kPcgMaxGroups float4 groups per thread
+// 9 floats per slot in shared memory (p, z / q and Minv; r and x are in tensor memory),
+// and at most kPcgMaxGroups float4 groups per thread
 constexpr int kPcgMaxChunk = 4 * kPcgMaxGroups * kPcgThreads;
-constexpr int kPcgSmemPerSlot = 24;
+constexpr int kPcgSmemPerSlot = 36;
 
-// Bricks of by x bz full x-rows for the persistent position step of an all-nodes
-// lattice (nx % 4 == 0): the fewest slots per CTA within the SM count, and among those
-// the fewest x-rows with a neighbour in another CTA.  by = bz = 0 when none fits or
-// the bricks would hold more than 1.25x the slots of an even split.
-void brick_plan(const vd_lattice *L, int *by, int *bz) {
-    *by = *bz = 0;
+// A brick plan for the persistent position step of an all-nodes lattice: bricks of by x
+// bz x-rows, each row held as lx = nx rounded up to a multiple of 4 slots in shared
+// memory; G = ceil(ny / by) ceil(nz / bz) CTAs of chunk = by bz lx slots.  Exact (the
+// unpadded kernel form): nx % 4 == 0 and the bricks tile the lattice; otherwise a padded
+// brick (k_pcg_persistent<.., true>).
+struct BrickPlan {
+    int by = 0, bz = 0, lx = 0, G = 0, chunk = 0;
+    bool exact = false;
+};
+
+// The cost of a brick: its rows plus the neighbour rows it reads from other CTAs
+// (through L2), times lx; the padded form 10% dearer.  few == false: the cheapest brick
+// with G <= gmax; few == true: the least SM time (G x cost) with gmin <= G <= gmax.
+// by = 0 when none fits.
+BrickPlan brick_search(const vd_lattice *L, long gmin, long gmax, bool few) {
+    BrickPlan best;
     const Ctx &c = L->c;
-    if (!L->all || c.nx % 4 || !L->use_brick) return;
-    const long even = ((long)c.nn + L->num_sms - 1) / L->num_sms;
-    long best_chunk = 0, best_faces = 0;
-    for (int y = 1; y <= c.ny; y++) {
-        if (c.ny % y) continue;
-        for (int z = 1; z <= c.nz; z++) {
-            if (c.nz % z || y * z > kPcgMaxRows) continue;
-            const long G = (long)(c.ny / y) * (c.nz / z), chunk = (long)y * z * c.nx;
-            if (G > L->num_sms || chunk > kPcgMaxChunk || 4 * chunk > 5 * even) continue;
+    if (!L->all || !L->use_brick) return best;
+    const int lx = 4 * ((c.nx + 3) / 4);
+    gmax = std::min<long>(gmax, kPcgMaxCtas);
+    long best_key = -1;
+    for (int y = 1; y <= c.ny; y++)
+        for (int z = 1; z <= c.nz && (long)y * z <= kPcgMaxRows && (long)y * z * lx <= kPcgMaxChunk; z++) {
+            const long G = (long)((c.ny + y - 1) / y) * ((c.nz + z - 1) / z);
+            if (G > gmax || G < gmin) continue;
+            const bool exact = c.nx % 4 == 0 && c.ny % y == 0 && c.nz % z == 0;
+            const long rows = (long)y * z;
             const long faces = (y < c.ny ? 2L * z : 0) + (z < c.nz ? 2L * y : 0);
-            if (!best_chunk || chunk < best_chunk || (chunk == best_chunk && faces < best_faces)) {
-                best_chunk = chunk;
-                best_faces = faces;
-                *by = y;
-                *bz = z;
+            long cost = (rows + faces) * lx;
+            if (!exact) cost += cost / 10;
+            const long key = few ? G * cost : cost;
+            if (best_key < 0 || key < best_key) {
+                best_key = key;
+                best = BrickPlan{y, z, lx, (int)G, (int)(rows * lx), exact};
             }
         }
-    }
+    return best;
 }
 
+// The persistent position step's partition: bricks (b.by > 0), or contiguous slot ranges
+// of `chunk` slots (b.by == 0)
+struct PcgPlan {
+    int G = 0, chunk = 0;
+    BrickPlan b;
+};
+
 // Whether the position step runs as one persistent cooperative kernel, with how many
-// CTAs and how many slots per CTA (and the brick shape, 0 x 0 for a contiguous split).
-bool persistent_plan(vd_lattice *L, int *G, int *chunk, int *by = nullptr, int *bz = nullptr) {
-    if (by) *by = *bz = 0;
+// CTAs and how many slots per CTA: bricks where the cheapest one within the SM count holds
+// at most 1.25x the slots of an even split (2x for a padded brick), else contiguous
+// ranges over all SMs.
+bool persistent_plan(vd_lattice *L, int *G, int *chunk, PcgPlan *out = nullptr) {
     if (!L->use_persistent || !L->coop || L->in_batch) return false;
-    int y = 0, z = 0;
-    brick_plan(L, &y, &z);
-    if (y) {
-        *chunk = y * z * L->c.nx;
-        *G = (L->c.ny / y) * (L->c.nz / z);
-        if (*G > kPcgMaxCtas) return false;
-        if (by) {
-            *by = y;
-            *bz = z;
-        }
-        return true;
-    }
+    PcgPlan pl;
     const int N = L->all ? L->c.nn : L->n_active_h;
-    const int N4 = 4 * ((std::max(N, 1) + 3) / 4);
-    // all SMs take part even for a small active set: the samples' share of each
-    // iteration is spread over the CTAs, and a barrier costs the same for any count
-    int ch = (N4 + L->num_sms - 1) / L->num_sms;
-    ch = std::max(4 * ((ch + 3) / 4), 4);
-    if (ch > kPcgMaxChunk) return false;
-    *chunk = ch;
-    *G = (N4 + ch - 1) / ch;
-    return *G <= std::min(L->num_sms, kPcgMaxCtas);
+    const long even = ((long)std::max(N, 1) + L->num_sms - 1) / L->num_sms;
+    const BrickPlan b = brick_search(L, 1, L->num_sms, false);
+    if (b.by && (b.exact ? 4L * b.chunk <= 5 * even : (long)b.chunk <= 2 * even)) {
+        pl.G = b.G;
+        pl.chunk = b.chunk;
+        pl.b = b;
+    } else {
+        const int N4 = 4 * ((std::max(N, 1) + 3) / 4);
+        // all SMs take part even for a small active set: the samples' share of each
+        // iteration is spread over the CTAs, and a barrier costs the same for any count
+        int ch = (N4 + L->num_sms - 1) / L->num_sms;
+        ch = std::max(4 * ((ch + 3) / 4), 4);
+        if (ch > kPcgMaxChunk) return false;
+        pl.chunk = ch;
+        pl.G = (N4 + ch - 1) / ch;
+        if (pl.G > std::min(L->num_sms, kPcgMaxCtas)) return false;
+    }
+    *G = pl.G;
+    *chunk = pl.chunk;
+    if (out) *out = pl;
+    return true;
+}
+
+unsigned magic_of(int d) { return d > 0 ? (unsigned)(((1ull << 31) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u; }
+
+// the aux block of a persistent position step on plan pl
+PcgAux pcg_aux(const vd_lattice *L, double *part, unsigned long long *words, int extra, const PcgPlan &pl) {
+    const int lx = pl.b.by ? pl.b.lx : L->c.nx;
+    return PcgAux{part,       words, extra, (int *)(L->pcg_bar + 2), L->surf_flag, {L->c.p, L->vecs + 15 * (size_t)L->c.ld},
+                  pl.chunk,   pl.b.by, pl.b.bz, lx, magic_of(lx), magic_of(pl.b.by)};
 }
 
 template <bool kAll>
-void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2, int apply, int G, int chunk) {
-    int by = 0, bz = 0;
-    brick_plan(L, &by, &bz);
-    if (by && by * bz * L->c.nx != chunk) by = bz = 0;  // the plan the caller sized G for
-    auto magic = [](int d) { return d > 0 ? (unsigned)(((1ull << 31) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u; };
+void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2, int apply) {
+    int G = 0, chunk = 0;
+    PcgPlan pl;
+    if (!persistent_plan(L, &G, &chunk, &pl)) return;
     unsigned long long *words = reinterpret_cast<unsigned long long *>(L->pcg_part + (size_t)L->pcg_part_rows * L->num_sms);
-    PcgAux ax{L->pcg_part, words, L->stall_extra, (int *)(L->pcg_bar + 2), L->surf_flag,
-              {L->c.p, L->vecs + 15 * (size_t)L->c.ld}, chunk, by, bz, magic(L->c.nx), magic(by)};
+    const PcgAux ax = pcg_aux(L, L->pcg_part, words, L->stall_extra, pl);
     const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
     cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
     cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(2 * K + 1), Lc.st);
@@ -546,7 +574,8 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const Ctx c = L->c;
-    if (kAll && (c.nx % 4 == 0)) cudaLaunchKernelEx(&cfg, k_pcg_persistent<kAll, true>, c, sc, ax, K, tol2, apply);
+    if (kAll && pl.b.by && !pl.b.exact) cudaLaunchKernelEx(&cfg, k_pcg_persistent<true, true, true>, c, sc, ax, K, tol2, apply);
+    else if (kAll && (pl.b.by || c.nx % 4 == 0)) cudaLaunchKernelEx(&cfg, k_pcg_persistent<kAll, true>, c, sc, ax, K, tol2, apply);
     else cudaLaunchKernelEx(&cfg, k_pcg_persistent<kAll, false>, c, sc, ax, K, tol2, apply);
     L->counting++;
     if (prof) {
@@ -598,7 +627,7 @@ void enqueue_gn(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g) {
     const int K = P->cg_iters;
     int G = 0, chunk = 0;
     if (persistent_plan(L, &G, &chunk)) {
-        launch_persistent<kAll>(L, Lc, sc, K, P->cg_tol * P->cg_tol, 1, G, chunk);
+        launch_persistent<kAll>(L, Lc, sc, K, P->cg_tol * P->cg_tol, 1);
     } else {
         enqueue_pcg<kAll>(Lc, c, sc, gr, K, P->cg_tol * P->cg_tol);
         Lc.go(VD_KC_ROTATION, k_add_increment<kAll>, gr.node, kThreads, c, (const Scal *)sc);
@@ -639,8 +668,10 @@ int class_launches_per_solve(const vd_solve_params *P, int kc) {
 
 vd_status build_graph(vd_lattice *L, const vd_solve_params *P) {
     const Grid gr = grids(L);
-    int pG = 0, pch = 0, pby = 0, pbz = 0;
-    persistent_plan(L, &pG, &pch, &pby, &pbz);
+    int pG = 0, pch = 0;
+    PcgPlan pl;
+    persistent_plan(L, &pG, &pch, &pl);
+    const int pby = pl.b.by, pbz = pl.b.bz;
     const int caps[6] = {gr.node, gr.samp, gr.cells, L->S * 65536 + pch, pby * 65536 + pbz,
                          gr.btb * 65536 + (L->c.btb ? L->n_occ_h : 0)};
     const bool same = L->gexec && L->ggen == L->gen && !memcmp(&L->gparams, P, sizeof(*P)) &&
@@ -831,6 +862,7 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
         }
         const int bytes = kPcgSmemPerSlot * kPcgMaxChunk;
         if (cudaFuncSetAttribute(k_pcg_persistent<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
+            cudaFuncSetAttribute(k_pcg_persistent<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
             cudaFuncSetAttribute(k_pcg_persistent<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
             cudaFuncSetAttribute(k_pcg_persistent<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) {
             cudaGetLastError();
@@ -1191,12 +1223,12 @@ vd_status vd_step_pcg(vd_lattice *L, const vd_solve_params *P, float *delta, int
         if (L->all) {
             enqueue_rhs<true>(Lc, c, sc, gr, K);
             enqueue_btb<true>(Lc, c, sc, gr, L->n_occ_h);
-            launch_persistent<true>(L, Lc, sc, K, tol2, apply, pG, pch);
+            launch_persistent<true>(L, Lc, sc, K, tol2, apply);
             if (delta) k_scatter_slots<true><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         } else {
             enqueue_rhs<false>(Lc, c, sc, gr, K);
             enqueue_btb<false>(Lc, c, sc, gr, L->n_occ_h);
-            launch_persistent<false>(L, Lc, sc, K, tol2, apply, pG, pch);
+            launch_persistent<false>(L, Lc, sc, K, tol2, apply);
             if (delta) k_scatter_slots<false><<<blocks_for(c.nn), kThreads, 0, st>>>(c.x, c, L->staging);
         }
     } else if (L->all) {
@@ -1394,6 +1426,19 @@ vd_status vd_launch_counts(vd_lattice *L, const vd_solve_params *P, int *per_sol
     return VD_OK;
 }
 
+vd_status vd_pcg_plan(vd_lattice *L, int *ctas, int *chunk, int *by, int *bz, int *padded) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    int G = 0, ch = 0;
+    PcgPlan pl;
+    if (!persistent_plan(L, &G, &ch, &pl)) pl = PcgPlan{};
+    if (ctas) *ctas = pl.G;
+    if (chunk) *chunk = pl.chunk;
+    if (by) *by = pl.b.by;
+    if (bz) *bz = pl.b.bz;
+    if (padded) *padded = pl.b.by && !pl.b.exact ? 1 : 0;
+    return VD_OK;
+}
+
 }  // extern "C"
 
 // ====================================================================== batched solve
@@ -1426,6 +1471,10 @@ struct vd_batch {
     // iteration): threads per CTA, CTAs per SM, weight of a sample against a node in the
     // split of the CTAs among the lattices
     bool persistent = false;
+    // position steps in waves of the shared-memory persistent step (k_pcg_wave, one
+    // cooperative launch per Gauss-Newton iteration); overrides `persistent`
+    bool waves = false;
+    int wave_share = 1024;           // samples per CTA that size a lattice's group (at most)
     int pthreads = 512, pctas = 1;
     float sample_weight = 2.f;
     std::vector<void *> pbufs;       // items, barrier words, partial rows
@@ -1434,6 +1483,9 @@ struct vd_batch {
     double *part = nullptr;
     size_t cap_items = 0, cap_words = 0, cap_part = 0;
     std::vector<int> groups;         // CTAs per lattice of the last persistent build
+    int2 *wplan = nullptr;           // wave form: the CTAs' plan of every launch set
+    size_t cap_wplan = 0;
+    int n_waves = 0;
 };
 
 namespace {
@@ -1453,6 +1505,8 @@ std::vector<char> batch_key(vd_batch *B, const vd_solve_params *P, int streams, 
     put(&largest, sizeof(largest));
     put(&coop_min, sizeof(coop_min));
     put(&B->persistent, sizeof(B->persistent));
+    put(&B->waves, sizeof(B->waves));
+    put(&B->wave_share, sizeof(B->wave_share));
     put(&B->pthreads, sizeof(B->pthreads));
     put(&B->pctas, sizeof(B->pctas));
     put(&B->sample_weight, sizeof(B->sample_weight));
@@ -1476,12 +1530,13 @@ std::vector<int> batch_order(vd_batch *B, bool largest) {
 }
 
 vd_status batch_build_persistent(vd_batch *B, const vd_solve_params *P, int streams, bool largest);
+vd_status batch_build_waves(vd_batch *B, const vd_solve_params *P, int streams, bool largest);
 
 vd_status batch_build(vd_batch *B, const vd_solve_params *P, int streams, bool largest, long coop_min) {
     std::vector<char> key = batch_key(B, P, streams, largest, coop_min);
     if (B->gexec && key == B->key) return VD_OK;
-    if (B->persistent) {
-        vd_status s = batch_build_persistent(B, P, streams, largest);
+    if (B->waves || B->persistent) {
+        vd_status s = B->waves ? batch_build_waves(B, P, streams, largest) : batch_build_persistent(B, P, streams, largest);
         if (s == VD_OK) {
             B->key = key;
             B->gparams = *P;
@@ -1593,6 +1648,90 @@ int batch_occupancy(int threads) {
     return occ;
 }
 
+// Capture a batch graph whose position steps run as cooperative launches: the lattices'
+// stages before the first position step as branches on `streams` capture streams, then
+// per Gauss-Newton iteration gi the launches that steps(gi) enqueues on the capture stream
+// (it returns their count), then the stages after it as branches again.
+template <typename Steps>
+vd_status batch_capture(vd_batch *B, const vd_solve_params *P, int streams, bool largest, Steps steps) {
+    const int GN = P->gn_iters;
+    while ((int)B->side.size() < streams) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "stream");
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "event");
+        B->side.push_back(st);
+        B->join.push_back(ev);
+    }
+    if (B->gexec) {
+        cudaGraphExecDestroy(B->gexec);
+        B->gexec = nullptr;
+    }
+    const std::vector<int> order = batch_order(B, largest);
+    if (cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bfail(B, VD_ERR_CUDA, "begin capture");
+    int launches = 0;
+    auto fork = [&]() {
+        cudaEventRecord(B->fork, B->cap);
+        for (int p = 0; p < streams; p++) cudaStreamWaitEvent(B->side[p], B->fork, 0);
+    };
+    auto joinall = [&]() {
+        for (int p = 0; p < streams; p++) {
+            cudaEventRecord(B->join[p], B->side[p]);
+            cudaStreamWaitEvent(B->cap, B->join[p], 0);
+        }
+    };
+    // the lattices' segments: before the first position step, and between position steps
+    auto segment = [&](int gi) {  // gi < 0: start + pre(0); else post(gi) + pre(gi + 1) or end
+        fork();
+        int k = 0;
+        for (int idx : order) {
+            vd_lattice *L = B->L[idx];
+            cudaStream_t st = B->side[k++ % streams];
+            const int saved = L->prof_class;
+            L->prof_class = -1;
+            L->counting = 0;
+            Launcher Lc{L, st};
+            if (gi < 0) {
+                enqueue_solve_begin(Lc, L, P, st);
+                cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), st);
+                Lc.other();
+            } else if (L->all) {
+                enqueue_gn_post<true>(Lc, L, P, gi);
+            } else {
+                enqueue_gn_post<false>(Lc, L, P, gi);
+            }
+            const int nxt = gi + 1;
+            if (nxt < GN) {
+                if (L->all) enqueue_gn_pre<true>(Lc, L, P, nxt);
+                else enqueue_gn_pre<false>(Lc, L, P, nxt);
+            } else {
+                enqueue_solve_end(Lc, L, P, st);
+            }
+            launches += L->counting;
+            L->prof_class = saved;
+        }
+        joinall();
+    };
+    segment(-1);
+    for (int gi = 0; gi < GN; gi++) {
+        launches += steps(gi);
+        segment(gi);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&B->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(B, VD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    B->launches = launches;
+    return VD_OK;
+}
+
 // One graph per batch: for every Gauss-Newton iteration, the lattices' stages before the
 // position step as branches on `streams` capture streams, then one cooperative launch of
 // k_pcg_batch for all position steps, then the stages after it as branches again.  The
@@ -1608,14 +1747,6 @@ vd_status batch_build_persistent(vd_batch *B, const vd_solve_params *P, int stre
     if (!B->L[0]->coop || occ < B->pctas || n > sms * B->pctas)
         return bfail(B, VD_ERR_INVALID_ARG, "the persistent batch does not fit on the device with these settings");
     const int T = sms * B->pctas;
-    while ((int)B->side.size() < streams) {
-        cudaStream_t st;
-        cudaEvent_t ev;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "stream");
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "event");
-        B->side.push_back(st);
-        B->join.push_back(ev);
-    }
     std::vector<double> w(n);
     double W = 0.0;
     for (int i = 0; i < n; i++) {
@@ -1695,58 +1826,9 @@ vd_status batch_build_persistent(vd_batch *B, const vd_solve_params *P, int stre
     if (cudaMemcpy(B->items, items.data(), sizeof(PcgBatchItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(B, VD_ERR_CUDA, "item upload");
     B->groups = g;
-    if (B->gexec) {
-        cudaGraphExecDestroy(B->gexec);
-        B->gexec = nullptr;
-    }
-    const std::vector<int> order = batch_order(B, largest);
-    if (cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return bfail(B, VD_ERR_CUDA, "begin capture");
-    int launches = 0;
-    auto fork = [&]() {
-        cudaEventRecord(B->fork, B->cap);
-        for (int p = 0; p < streams; p++) cudaStreamWaitEvent(B->side[p], B->fork, 0);
-    };
-    auto joinall = [&]() {
-        for (int p = 0; p < streams; p++) {
-            cudaEventRecord(B->join[p], B->side[p]);
-            cudaStreamWaitEvent(B->cap, B->join[p], 0);
-        }
-    };
-    // the lattices' segments: before the first position step, and between position steps
-    auto segment = [&](int gi) {  // gi < 0: start + pre(0); else post(gi) + pre(gi + 1) or end
-        fork();
-        int k = 0;
-        for (int idx : order) {
-            vd_lattice *L = B->L[idx];
-            cudaStream_t st = B->side[k++ % streams];
-            const int saved = L->prof_class;
-            L->prof_class = -1;
-            L->counting = 0;
-            Launcher Lc{L, st};
-            if (gi < 0) {
-                enqueue_solve_begin(Lc, L, P, st);
-                cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), st);
-                Lc.other();
-            } else if (L->all) {
-                enqueue_gn_post<true>(Lc, L, P, gi);
-            } else {
-                enqueue_gn_post<false>(Lc, L, P, gi);
-            }
-            const int nxt = gi + 1;
-            if (nxt < GN) {
-                if (L->all) enqueue_gn_pre<true>(Lc, L, P, nxt);
-                else enqueue_gn_pre<false>(Lc, L, P, nxt);
-            } else {
-                enqueue_solve_end(Lc, L, P, st);
-            }
-            launches += L->counting;
-            L->prof_class = saved;
-        }
-        joinall();
-    };
-    segment(-1);
-    for (int gi = 0; gi < GN; gi++) {
+    B->n_waves = 0;
+    const double tol2 = P->cg_tol * P->cg_tol;
+    return batch_capture(B, P, streams, largest, [&](int gi) {
         cudaMemsetAsync(B->words, 0, sizeof(unsigned long long) * (size_t)words_need, B->cap);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
@@ -1758,24 +1840,165 @@ vd_status batch_build_persistent(vd_batch *B, const vd_solve_params *P, int stre
         cfg.attrs = at;
         cfg.numAttrs = 1;
         const PcgBatchItem *its = B->items + (size_t)gi * n;
-        const double tol2 = P->cg_tol * P->cg_tol;
         if (B->pthreads == 256) cudaLaunchKernelEx(&cfg, k_pcg_batch<256>, its, n, K, tol2, 1);
         else cudaLaunchKernelEx(&cfg, k_pcg_batch<512>, its, n, K, tol2, 1);
-        launches++;
-        segment(gi);
+        return 1;
+    });
+}
+
+// Position-step plan of one lattice inside a wave: the fewest CTAs that hold at most
+// `share` of the lattice's samples each (a CTA's sample warps take a share of them beside
+// its stencil; as far as the SMs allow) and whose slots fit in shared memory: bricks for
+// an all-nodes lattice, contiguous ranges for a surface set.  G = 0 when none fits.
+PcgPlan wave_plan(const vd_lattice *L, int cap, int share) {
+    PcgPlan w;
+    const long N = std::max(active_nodes(L), 1L), N4 = 4 * ((N + 3) / 4);
+    const long g_samples = ((long)L->n_samples_h + share - 1) / share;
+    if (L->all) {
+        BrickPlan b = brick_search(L, std::min<long>(g_samples, cap), cap, true);
+        if (!b.by) b = brick_search(L, 1, cap, true);
+        if (!b.by) return w;
+        w.G = b.G;
+        w.chunk = b.chunk;
+        w.b = b;
+        return w;
     }
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
-    if (e == cudaSuccess) {
-        e = cudaGraphInstantiate(&B->gexec, graph, 0);
-        cudaGraphDestroy(graph);
+    const long g_nodes = (N4 + kPcgMaxChunk - 1) / kPcgMaxChunk;
+    const long gmin = std::max(g_nodes, std::min(g_samples, std::min<long>(cap, N4 / 4)));
+    w.chunk = 4 * (int)(((N4 + gmin - 1) / gmin + 3) / 4);
+    w.G = (int)((N4 + w.chunk - 1) / w.chunk);
+    return w;
+}
+
+// One graph per batch whose position steps run in waves: per Gauss-Newton iteration one
+// cooperative launch of k_pcg_wave (one CTA per SM) per launch set, in which every
+// lattice's group runs the shared-memory persistent step of vd_solve.  A launch set holds
+// up to kWaveMaxItems lattices of one kernel form: the all-nodes lattices (bricks; the
+// padded form unless every one of them tiles exactly) and the surface-set lattices
+// (contiguous ranges); its groups
+// are packed into waves of at most one CTA per SM, largest first, each into the first
+// wave with room (first fit decreasing).  The other stages run as per-lattice branches
+// between these launches.
+vd_status batch_build_waves(vd_batch *B, const vd_solve_params *P, int streams, bool largest) {
+    const int n = (int)B->L.size();
+    if (cudaStreamSynchronize(B->L[0]->stream) != cudaSuccess) return bfail(B, VD_ERR_CUDA, "synchronize");
+    const int K = P->cg_iters, GN = P->gn_iters;
+    const int T = B->L[0]->num_sms;
+    if (!B->L[0]->coop) return bfail(B, VD_ERR_INVALID_ARG, "the wave form needs cooperative launches");
+    // the lattices' plans; launch sets by kernel form: 3 (all nodes, padded bricks, when
+    // any all-nodes lattice needs one), 2 (all nodes, exact bricks), 0 (surface sets)
+    std::vector<PcgPlan> wp(n);
+    bool exact = true;
+    for (int i = 0; i < n; i++) {
+        vd_lattice *L = B->L[i];
+        vd_status s = ensure_scal(L, GN, K);
+        if (s != VD_OK) return bfail(B, s, L->err.c_str());
+        set_params_ctx(L->c, P);
+        refresh_ctx(L);
+        wp[i] = wave_plan(L, T, B->wave_share);
+        if (!wp[i].G || wp[i].G > T || wp[i].G > kPcgMaxCtas)
+            return bfail(B, VD_ERR_INVALID_ARG, "a lattice of the batch is too large for the wave form");
+        if (L->all) exact = exact && wp[i].b.exact;
     }
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return bfail(B, VD_ERR_CUDA, cudaGetErrorString(e));
+    struct Set {
+        int form;
+        std::vector<int> lat;
+        int waves = 0, grid = 0, max_chunk = 4;
+        size_t plan_off = 0;
+    };
+    std::vector<Set> sets;
+    for (int form : {3, 2, 0})
+        for (int i = 0; i < n; i++) {
+            const int f = B->L[i]->all ? (exact ? 2 : 3) : 0;
+            if (f != form) continue;
+            if (sets.empty() || sets.back().form != form || (int)sets.back().lat.size() == kWaveMaxItems)
+                sets.push_back(Set{form, {}});
+            sets.back().lat.push_back(i);
+        }
+    // per set, first fit decreasing: the wave of each lattice's group and its first CTA
+    std::vector<int2> plan;
+    std::vector<int> place_wave(n), place_first(n), item_of(n);
+    for (Set &S : sets) {
+        std::vector<int> order = S.lat;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wp[a].G > wp[b].G; });
+        std::vector<int> fill;
+        for (int i : order) {
+            size_t w = 0;
+            while (w < fill.size() && fill[w] + wp[i].G > T) w++;
+            if (w == fill.size()) fill.push_back(0);
+            place_wave[i] = (int)w;
+            place_first[i] = fill[w];
+            fill[w] += wp[i].G;
+            S.grid = std::max(S.grid, fill[w]);
+            S.max_chunk = std::max(S.max_chunk, wp[i].chunk);
+        }
+        S.waves = (int)fill.size();
+        S.plan_off = plan.size();
+        plan.resize(plan.size() + (size_t)S.waves * S.grid, make_int2(-1, 0));
+        for (size_t k = 0; k < S.lat.size(); k++) {
+            const int i = S.lat[k];
+            item_of[i] = (int)k;
+            for (int b = 0; b < wp[i].G; b++)
+                plan[S.plan_off + (size_t)place_wave[i] * S.grid + place_first[i] + b] = make_int2((int)k, b);
+        }
     }
-    B->launches = launches;
-    return VD_OK;
+    const long words_need = (long)n * (2 * K + 1);
+    vd_status s = bgrow(B, &B->wplan, &B->cap_wplan, plan.size());
+    if (s == VD_OK) s = bgrow(B, &B->words, &B->cap_words, (size_t)words_need);
+    if (s != VD_OK) return s;
+    if (cudaMemcpy(B->wplan, plan.data(), sizeof(int2) * plan.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(B, VD_ERR_CUDA, "plan upload");
+    // the items of every (Gauss-Newton iteration, set): kernel parameters of its launch
+    std::vector<PcgWaveArgs> args((size_t)GN * sets.size());
+    for (int gi = 0; gi < GN; gi++)
+        for (size_t si = 0; si < sets.size(); si++) {
+            PcgWaveArgs &A = args[(size_t)gi * sets.size() + si];
+            memset(&A, 0, sizeof(A));
+            for (int i : sets[si].lat) {
+                vd_lattice *L = B->L[i];
+                PcgWaveItem &it = A.it[item_of[i]];
+                it.c = L->c;
+                it.ax = pcg_aux(L, L->pcg_part, B->words + (size_t)i * (2 * K + 1), 0, wp[i]);
+                it.sc = slot(L, gi);
+                it.G = wp[i].G;
+            }
+        }
+    const int bytes = kPcgSmemPerSlot * kPcgMaxChunk;
+    for (auto f : {k_pcg_wave<true, true, true>, k_pcg_wave<true, true, false>, k_pcg_wave<false, false, false>}) {
+        int occ = 0;
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kPcgThreads, bytes) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            return bfail(B, VD_ERR_INVALID_ARG, "the wave kernel does not fit on an SM");
+        }
+    }
+    B->groups.assign(n, 0);
+    B->n_waves = 0;
+    for (int i = 0; i < n; i++) B->groups[i] = wp[i].G;
+    for (const Set &S : sets) B->n_waves += S.waves;
+    const double tol2 = P->cg_tol * P->cg_tol;
+    return batch_capture(B, P, streams, largest, [&](int gi) {
+        cudaMemsetAsync(B->words, 0, sizeof(unsigned long long) * (size_t)words_need, B->cap);
+        for (size_t si = 0; si < sets.size(); si++) {
+            const Set &S = sets[si];
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(S.grid);
+            cfg.blockDim = dim3(kPcgThreads);
+            cfg.dynamicSmemBytes = (size_t)kPcgSmemPerSlot * S.max_chunk;
+            cfg.stream = B->cap;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeCooperative;
+            at[0].val.cooperative = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            const PcgWaveArgs &A = args[(size_t)gi * sets.size() + si];
+            const int2 *pl = B->wplan + S.plan_off;
+            if (S.form == 3) cudaLaunchKernelEx(&cfg, k_pcg_wave<true, true, true>, A, pl, S.waves, K, tol2, 1);
+            else if (S.form == 2) cudaLaunchKernelEx(&cfg, k_pcg_wave<true, true, false>, A, pl, S.waves, K, tol2, 1);
+            else cudaLaunchKernelEx(&cfg, k_pcg_wave<false, false, false>, A, pl, S.waves, K, tol2, 1);
+        }
+        return (int)sets.size();
+    });
 }
 
 }  // namespace
@@ -1902,11 +2125,34 @@ vd_status vd_batch_tune(vd_batch *B, const vd_solve_params *P, int *streams_out,
             best_c = cm;
         }
     }
-    // then the persistent position step over every lattice: threads per CTA, CTAs per SM,
-    // the sample weight of the CTA split, and the branches of the other stages
-    bool best_p = false;
+    // then the waves of the shared-memory position step, with the branches of the other
+    // stages
+    bool best_p = false, best_v = false;
     int best_t = B->pthreads, best_k = B->pctas;
     float best_w = B->sample_weight;
+    if (B->L[0]->coop) {
+        for (int st : {8, 16}) {
+            if (st > n && st != 8) continue;
+            B->waves = true;
+            B->persistent = false;
+            float ms = 0.f;
+            vd_status s = time_build(st, best_l, 0x7fffffffL, &ms);
+            B->waves = false;
+            if (s != VD_OK) {  // a lattice too large for the waves
+                B->err.clear();
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_v = true;
+                best_s = st;
+                best_c = 0x7fffffffL;
+            }
+        }
+    }
+    // then the persistent position step over every lattice with its vectors in global
+    // memory: threads per CTA, CTAs per SM, the sample weight of the CTA split, and the
+    // branches of the other stages
     if (B->L[0]->coop) {
         for (int th : {256, 512}) {
             const int occ = batch_occupancy(th);
@@ -1928,6 +2174,7 @@ vd_status vd_batch_tune(vd_batch *B, const vd_solve_params *P, int *streams_out,
                         if (ms < best) {
                             best = ms;
                             best_p = true;
+                            best_v = false;
                             best_t = th;
                             best_k = k;
                             best_w = sw;
@@ -1939,6 +2186,7 @@ vd_status vd_batch_tune(vd_batch *B, const vd_solve_params *P, int *streams_out,
         }
     }
     B->persistent = best_p;
+    B->waves = best_v;
     B->pthreads = best_t;
     B->pctas = best_k;
     B->sample_weight = best_w;
@@ -1961,17 +2209,25 @@ vd_status vd_batch_set_plan(vd_batch *B, int streams, int largest_first, long lo
 vd_status vd_batch_set_persistent(vd_batch *B, int on, int threads, int ctas_per_sm, float sample_weight) {
     if (!B || !batch_threads_ok(threads) || ctas_per_sm < 1 || ctas_per_sm > 8 || !(sample_weight >= 0.f))
         return VD_ERR_INVALID_ARG;
-    B->persistent = on != 0;
+    if (on < 0 || on > VD_BATCH_WAVES) return VD_ERR_INVALID_ARG;
+    B->persistent = on == VD_BATCH_GLOBAL;
+    B->waves = on == VD_BATCH_WAVES;
     B->pthreads = threads;
     B->pctas = ctas_per_sm;
     B->sample_weight = sample_weight;
     return VD_OK;
 }
 
+vd_status vd_batch_set_wave_share(vd_batch *B, int samples_per_cta) {
+    if (!B || samples_per_cta < 32) return VD_ERR_INVALID_ARG;
+    B->wave_share = samples_per_cta;
+    return VD_OK;
+}
+
 vd_status vd_batch_get_plan(const vd_batch *B, int *persistent, int *threads, int *ctas_per_sm, float *sample_weight,
                             int *streams) {
     if (!B) return VD_ERR_INVALID_ARG;
-    if (persistent) *persistent = B->persistent ? 1 : 0;
+    if (persistent) *persistent = B->waves ? VD_BATCH_WAVES : B->persistent ? VD_BATCH_GLOBAL : VD_BATCH_BRANCHES;
     if (threads) *threads = B->pthreads;
     if (ctas_per_sm) *ctas_per_sm = B->pctas;
     if (sample_weight) *sample_weight = B->sample_weight;
@@ -1982,6 +2238,14 @@ vd_status vd_batch_get_plan(const vd_batch *B, int *persistent, int *threads, in
 vd_status vd_batch_launch_count(const vd_batch *B, int *launches) {
     if (!B || !launches) return VD_ERR_INVALID_ARG;
     *launches = B->launches;
+    return VD_OK;
+}
+
+vd_status vd_batch_get_groups(const vd_batch *B, int *ctas, int *waves) {
+    if (!B) return VD_ERR_INVALID_ARG;
+    if (ctas)
+        for (size_t i = 0; i < B->L.size(); i++) ctas[i] = i < B->groups.size() ? B->groups[i] : 0;
+    if (waves) *waves = B->n_waves;
     return VD_OK;
 }
 

@@ -1666,8 +1666,11 @@ struct PcgAux {
     float *pbuf[2];    // p of even / odd iterations, published for the other CTAs
     int chunk;         // slots per CTA
     int by, bz;        // > 0: each CTA owns a brick of by x bz full x-rows (all-nodes
-                       // lattice, ny % by == nz % bz == 0); 0: a contiguous slot range
-    // n / nx and n / by as (2n m) >> 32 with m = ceil(2^31 / d), exact for n d < 2^31
+                       // lattice); 0: a contiguous slot range
+    int lx;            // a brick's local row length: nx, or nx rounded up to a multiple of
+                       // 4 for a padded brick (the bricks at the far y / z faces may then
+                       // also hold fewer rows than by x bz)
+    // n / lx and n / by as (2n m) >> 32 with m = ceil(2^31 / d), exact for n d < 2^31
     // (the local slot and row indices of a brick): no integer division in the loops
     unsigned m_nx, m_by;
 };
@@ -1889,9 +1892,36 @@ __device__ __forceinline__ double block_sum(float v, float *redf) {
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
 
-template <bool kAll, bool kVec4>
-__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *sc, PcgAux ax, int K, double tol2,
-                                                                   int apply) {
+// Tensor memory of a persistent position-step CTA: all kPcgTmemCols columns (one CTA per
+// SM), allocated by warp 0; returns the base address
+__device__ __forceinline__ uint32_t pcg_tmem_alloc(uint32_t *slot) {
+    if (threadIdx.x < 32) {  // one SM per CTA: the columns are free
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(slot)),
+                     "r"(kPcgTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return *slot;
+}
+__device__ __forceinline__ void pcg_tmem_free(uint32_t tmem) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kPcgTmemCols));
+}
+
+// One position step (Sec. 7.1) of one lattice by a group of G co-resident CTAs, this one
+// being number bid of the group; tmem: the CTA's tensor memory (kPcgTmemCols columns).
+// Returns with the CTA synchronised (its shared and tensor memory free for reuse).
+// kPad: a padded brick (rows of ax.lx slots in shared memory, nx of them real; ragged
+// bricks at the far faces): global vectors are then read and written element by element,
+// the padding elements stay zero and take no part in the stencil or the sums.
+template <bool kAll, bool kVec4, bool kPad = false>
+__device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, const PcgAux &ax, int K, double tol2,
+                                                    int apply, const unsigned bid, const unsigned G,
+                                                    const uint32_t tmem) {
     // Two grid barriers per iteration.  Phase A forms p = z + beta p_old itself (own
     // slots in shared memory; a remote neighbour's from its published z and p_old), so
     // no barrier is needed after the p update:
@@ -1900,11 +1930,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     //   -- barrier + sum p.Ap --
     //   B: r -= alpha q, z = Minv r (published), r.z
     //   -- barrier + sum r.z --
-    // p and z / q of own slots live in shared memory, r and x in tensor memory (each
-    // thread keeps the r of the groups it updates in phase B and the x of those it
-    // updates in A1).  Global buffers: c.minv (Minv), c.r (z, published; holds b on
-    // entry), ax.pbuf (p of even / odd iterations), c.q (the samples' contributions),
-    // c.x (result, written at the end).
+    // p, z / q and Minv of own slots live in shared memory, r and x in tensor memory
+    // (each thread keeps the r of the groups it updates in phase B and the x of those it
+    // updates in A1).  Global buffers: c.minv (the diagonal on entry, Minv on return),
+    // c.r (z, published; holds b on entry), ax.pbuf (p of even / odd iterations), c.q
+    // (the samples' contributions), c.x (result, written at the end).
     extern __shared__ float4 sm4[];
     __shared__ float redf[32];
     __shared__ int s_js, s_je, s_go;
@@ -1915,48 +1945,71 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     // J^T J p contributions arrive in c.q)
     __shared__ unsigned s_touch[kPcgMaxGroups * kPcgThreads / 32];
     __shared__ float s_ab;
-    __shared__ uint32_t s_tmem;
     float *sm = reinterpret_cast<float *>(sm4);
     const int chunk = ax.chunk;
     float *__restrict__ P = sm;               // p of own slots
     float *__restrict__ Q = sm + 3 * chunk;   // z between phases B and A, q within A..B
+    float *__restrict__ M = sm + 6 * chunk;   // Minv of own slots
     float *__restrict__ Zg = c.r;
     if (sc->skip) return;  // the same flag for every CTA: none reaches a barrier
-    const unsigned G = gridDim.x;
     const int N = active_count<kAll>(c);
     const int N4 = 4 * groups4(N);
-    // own slots: a brick of full x-rows (local index l = x + nx (row), row = yl + by zl)
+    // own slots: a brick of full x-rows (local index l = x + lx (row), row = yl + by zl)
     // or the contiguous range [s_beg, s_end) (local index l = slot - s_beg)
+    static_assert(!kPad || (kAll && kVec4), "padded bricks are all-nodes bricks");
     const bool brick = kVec4 && ax.by > 0;
     const int nx = c.nx, plane = c.nx * c.ny;
-    const int nby = brick ? c.ny / ax.by : 1;
-    const int y0 = brick ? (int)(blockIdx.x % nby) * ax.by : 0, z0 = brick ? (int)(blockIdx.x / nby) * ax.bz : 0;
-    const int s_beg = brick ? 0 : blockIdx.x * chunk;
+    const int lx = kPad ? ax.lx : nx;
+    const int nby = brick ? (c.ny + ax.by - 1) / ax.by : 1;
+    const int y0 = brick ? (int)(bid % nby) * ax.by : 0, z0 = brick ? (int)(bid / nby) * ax.bz : 0;
+    // rows of the brick that exist (fewer than by x bz in a ragged brick)
+    const int byA = kPad ? min(ax.by, c.ny - y0) : ax.by, bzA = kPad ? min(ax.bz, c.nz - z0) : ax.bz;
+    const int s_beg = brick ? 0 : bid * chunk;
     const int s_end = brick ? 0 : min(s_beg + chunk, N4);
     const int ng = brick ? chunk >> 2 : (s_end > s_beg ? (s_end - s_beg) >> 2 : 0);
     auto gslot = [&](int l) -> int {
         if (!brick) return s_beg + l;
         const int r = fast_div(l, ax.m_nx), rz = fast_div(r, ax.m_by);
-        return (l - r * nx) + nx * (y0 + (r - rz * ax.by)) + plane * (z0 + rz);
+        return (l - r * lx) + nx * (y0 + (r - rz * ax.by)) + plane * (z0 + rz);
+    };
+    // real elements of the group at local index l: 4, or (padded brick) 0 in a row past
+    // the lattice and min(4, nx - x) at the end of a row
+    auto gvalid = [&](int l) -> int {
+        if (!kPad) return 4;
+        const int r = fast_div(l, ax.m_nx), rz = fast_div(r, ax.m_by);
+        if (r - rz * ax.by >= byA || rz >= bzA) return 0;
+        return min(4, nx - (l - r * lx));
+    };
+    // a group of a global vector at slot s: one 16-byte access (nv is then 0 or 4), or
+    // element by element where the rows are not 16-byte aligned (nx % 4 != 0; elements
+    // past nv read as zero and are not written)
+    const bool rows16 = !kPad || (nx & 3) == 0;
+    auto gld = [&](const float *p, int nv) -> float4 {
+        if (rows16) return nv > 0 ? __ldcg(reinterpret_cast<const float4 *>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) v[e] = e < nv ? __ldcg(p + e) : 0.f;
+        return make_float4(v[0], v[1], v[2], v[3]);
+    };
+    auto gst = [&](float *p, int nv, float4 v) {
+        if (rows16) {
+            if (nv > 0) *reinterpret_cast<float4 *>(p) = v;
+            return;
+        }
+        const float a4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            if (e < nv) p[e] = a4[e];
     };
     const int tid = threadIdx.x;
     const float w2 = 2.f * c.w_r;
     const size_t ld = c.ld;
-    if (tid < 32) {  // one SM per CTA: the columns are free
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(&s_tmem)),
-                     "r"(kPcgTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t t_r = s_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + 64u * (uint32_t)(tid >> 7);
+    const uint32_t t_r = tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + 64u * (uint32_t)(tid >> 7);
     const uint32_t t_x = t_r + kPcgTmemX;
     if (tid == 0) {  // an equal share of the sorted samples
         const int n_occ = *c.n_occ, ns = n_occ > 0 ? c.occ_beg[n_occ] : 0;
-        s_js = (int)(((long long)ns * blockIdx.x) / G);
-        s_je = (int)(((long long)ns * (blockIdx.x + 1)) / G);
+        s_js = (int)(((long long)ns * bid) / G);
+        s_je = (int)(((long long)ns * (bid + 1)) / G);
     }
     // ---- init: Minv = 1/diag, r = b, z = Minv r, p_old = 0, x = 0; rho0 = r.z
     float part = 0.f;
@@ -1969,38 +2022,46 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
 #pragma unroll
         for (int a = 0; a < 3; a++) r3[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (gl < ng) {
-            const int l = 4 * gl, s = gslot(l);
+            const int l = 4 * gl, s = gslot(l), nv = gvalid(l);
             pub[kk] = true;
             if (brick) {
                 const int r = fast_div(l, ax.m_nx), zl = fast_div(r, ax.m_by), yl = r - zl * ax.by;
-                pub[kk] = yl == 0 || yl == ax.by - 1 || zl == 0 || zl == ax.bz - 1;
+                pub[kk] = nv > 0 && (yl == 0 || yl == byA - 1 || zl == 0 || zl == bzA - 1);
             }
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                const float4 dg = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
-                const float4 rb = __ldcg(reinterpret_cast<const float4 *>(c.r + a * ld + s));
+                const float4 dg = gld(c.minv + a * ld + s, nv);
+                const float4 rb = gld(c.r + a * ld + s, nv);
                 const float dv[4] = {dg.x, dg.y, dg.z, dg.w}, rv[4] = {rb.x, rb.y, rb.z, rb.w};
                 float mi[4], rr[4], z[4];
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    const bool in = s + e < N;
+                    const bool in = kPad ? e < nv : s + e < N;
                     mi[e] = (in && dv[e] > 0.f) ? 1.0f / dv[e] : 0.f;
                     rr[e] = in ? rv[e] : 0.f;
                     z[e] = mi[e] * rr[e];
                     part += rr[e] * z[e];
                 }
                 const float4 z4 = make_float4(z[0], z[1], z[2], z[3]), zero = make_float4(0.f, 0.f, 0.f, 0.f);
-                *reinterpret_cast<float4 *>(c.minv + a * ld + s) = make_float4(mi[0], mi[1], mi[2], mi[3]);
+                const float4 mi4 = make_float4(mi[0], mi[1], mi[2], mi[3]);
+                gst(c.minv + a * ld + s, nv, mi4);
+                *reinterpret_cast<float4 *>(M + a * chunk + l) = mi4;
                 r3[a] = make_float4(rr[0], rr[1], rr[2], rr[3]);
                 *reinterpret_cast<float4 *>(Q + a * chunk + l) = z4;
                 *reinterpret_cast<float4 *>(P + a * chunk + l) = zero;
-                *reinterpret_cast<float4 *>(Zg + a * ld + s) = z4;
-                *reinterpret_cast<float4 *>(ax.pbuf[1] + a * ld + s) = zero;
+                gst(Zg + a * ld + s, nv, z4);
+                gst(ax.pbuf[1] + a * ld + s, nv, zero);
             }
-            const int4 fl = __ldcg(reinterpret_cast<const int4 *>(ax.flag + s));
+            int4 fl;
+            if (kPad) {
+                fl = make_int4(nv > 0 ? __ldcg(ax.flag + s) : 0, nv > 1 ? __ldcg(ax.flag + s + 1) : 0,
+                               nv > 2 ? __ldcg(ax.flag + s + 2) : 0, nv > 3 ? __ldcg(ax.flag + s + 3) : 0);
+            } else {
+                fl = __ldcg(reinterpret_cast<const int4 *>(ax.flag + s));
+            }
             if (fl.x | fl.y | fl.z | fl.w) {  // the samples' contributions arrive here by atomics
 #pragma unroll
-                for (int a = 0; a < 3; a++) *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int a = 0; a < 3; a++) gst(c.q + a * ld + s, nv, make_float4(0.f, 0.f, 0.f, 0.f));
                 pub[kk] = touch[kk] = true;
             }
         }
@@ -2029,12 +2090,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
     // go on (s_go), through the barrier's last __syncthreads.
     double sum = 0.0, rho = 0.0, pq_prev = 0.0, thr = 0.0;
     const unsigned arrivals = G + ax.extra;
-    bool ok = grid_reduce<true>(ax.err, G, arrivals, ax.part, ax.words, block_sum(part, redf), 0.0, sum, blockIdx.x,
+    bool ok = grid_reduce<true>(ax.err, G, arrivals, ax.part, ax.words, block_sum(part, redf), 0.0, sum, bid,
                                 [&](double r0) {
                                     rho = r0;
                                     thr = tol2 * r0;  // the convergence threshold on rho
                                     s_go = pos_finite(r0);
-                                    if (blockIdx.x == 0) scal_rho(sc)[0] = r0;
+                                    if (bid == 0) scal_rho(sc)[0] = r0;
                                 });
     float beta = 0.f;
     int done = 0;
@@ -2059,6 +2120,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                 if (gl < ng) {
                     const int l = 4 * gl, s = gslot(l);
                     const bool pg = published(gl);
+                    const int nv = pg ? gvalid(l) : 0;
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
                         const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
@@ -2069,7 +2131,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                         const float4 pn = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y),
                                                       fmaf(beta, pv.z, zv.z), fmaf(beta, pv.w, zv.w));
                         *reinterpret_cast<float4 *>(P + a * chunk + l) = pn;
-                        if (pg) *reinterpret_cast<float4 *>(pnew + a * ld + s) = pn;
+                        if (pg) gst(pnew + a * ld + s, nv, pn);
                     }
                 }
                 if (xa != 0.f) tmem_st12(t_x + 12 * k, x3);
@@ -2085,20 +2147,30 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                     bool own[4];
                     int loff[4];
                     const int offs[4] = {-nx, nx, -plane, plane};
+                    int nv = 4;
                     if (brick) {
                         const int r = fast_div(l, ax.m_nx), zl = fast_div(r, ax.m_by), yl = r - zl * ax.by;
-                        x0 = l - r * nx;
+                        x0 = l - r * lx;
                         y = y0 + yl;
                         z = z0 + zl;
                         s0 = x0 + nx * y + plane * z;
                         own[0] = yl > 0;
-                        own[1] = yl + 1 < ax.by;
+                        own[1] = yl + 1 < byA;
                         own[2] = zl > 0;
-                        own[3] = zl + 1 < ax.bz;
-                        loff[0] = -nx;
-                        loff[1] = nx;
-                        loff[2] = -ax.by * nx;
-                        loff[3] = ax.by * nx;
+                        own[3] = zl + 1 < bzA;
+                        loff[0] = -lx;
+                        loff[1] = lx;
+                        loff[2] = -ax.by * lx;
+                        loff[3] = ax.by * lx;
+                        if (kPad) {
+                            nv = (yl < byA && zl < bzA) ? min(4, nx - x0) : 0;
+                            if (nv <= 0) {  // padding: q = 0
+#pragma unroll
+                                for (int a = 0; a < 3; a++)
+                                    *reinterpret_cast<float4 *>(Q + a * chunk + l) = make_float4(0.f, 0.f, 0.f, 0.f);
+                                continue;
+                            }
+                        }
                     } else {
                         s0 = s_beg + l;
                         x0 = s0 % nx;
@@ -2127,8 +2199,21 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                             right = (brick || s0 + 4 < s_end)
                                         ? Pa[l + 4]
                                         : fmaf(beta, __ldcg(Oa + s0 + 4), __ldcg(Za + s0 + 4));
-                        float4 d = make_float4((pc.x - left) + (pc.x - pc.y), (pc.y - pc.x) + (pc.y - pc.z),
-                                               (pc.z - pc.y) + (pc.z - pc.w), (pc.w - pc.z) + (pc.w - right));
+                        float4 d;
+                        if (kPad && nv < 4) {  // the end of a row: no edges to the padding
+                            const float pv[4] = {pc.x, pc.y, pc.z, pc.w};
+                            float dd[4];
+#pragma unroll
+                            for (int e = 0; e < 4; e++) {
+                                const float lf = e == 0 ? left : pv[e - 1];
+                                const float rt = (e < 3 && e + 1 < nv) ? pv[e + 1] : pv[e];
+                                dd[e] = e < nv ? (pv[e] - lf) + (pv[e] - rt) : 0.f;
+                            }
+                            d = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                        } else {
+                            d = make_float4((pc.x - left) + (pc.x - pc.y), (pc.y - pc.x) + (pc.y - pc.z),
+                                            (pc.z - pc.y) + (pc.z - pc.w), (pc.w - pc.z) + (pc.w - right));
+                        }
 #pragma unroll
                         for (int k = 0; k < 4; k++) {
                             if (!has[k]) continue;
@@ -2137,8 +2222,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                             if (own[k]) {
                                 v = *reinterpret_cast<const float4 *>(Pa + l + loff[k]);
                             } else {
-                                const float4 zz = __ldcg(reinterpret_cast<const float4 *>(Za + sj));
-                                const float4 oo = __ldcg(reinterpret_cast<const float4 *>(Oa + sj));
+                                const float4 zz = gld(Za + sj, nv);
+                                const float4 oo = gld(Oa + sj, nv);
                                 v = make_float4(fmaf(beta, oo.x, zz.x), fmaf(beta, oo.y, zz.y), fmaf(beta, oo.z, zz.z),
                                                 fmaf(beta, oo.w, zz.w));
                             }
@@ -2193,8 +2278,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             const VecView pv{Zg, pold, beta};
             if (c.btb) {  // cached B^T B: an equal share of the occupied cells, a warp per cell
                 const int n_occ = *c.n_occ;
-                const int cb = (int)(((long long)n_occ * blockIdx.x) / G);
-                const int ce = (int)(((long long)n_occ * (blockIdx.x + 1)) / G);
+                const int cb = (int)(((long long)n_occ * bid) / G);
+                const int ce = (int)(((long long)n_occ * (bid + 1)) / G);
                 for (int ci = cb + (lt >> 5); ci < ce; ci += kPcgSample >> 5)
                     btb_cell_apply<kAll, true>(c, pv, ci, c.q, part);
             } else {
@@ -2202,15 +2287,15 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             }
             // the pairs go to the last warps, which hold the fewest cells
             double pd = 0.0;
-            sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, blockIdx.x + G * (kPcgSample - 1 - lt), G * kPcgSample,
+            sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, bid + G * (kPcgSample - 1 - lt), G * kPcgSample,
                                                part, pd);
         }
         ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it,
-                               block_sum(part, redf), pq_prev, sum, blockIdx.x, [&](double pq) {
+                               block_sum(part, redf), pq_prev, sum, bid, [&](double pq) {
                                    pq_prev = pq;
                                    s_go = pos_finite(pq);
                                    if (s_go) s_ab = f32_quot(rho, pq);  // alpha
-                                   if (blockIdx.x == 0) scal_pq(sc, K)[it] = pq;
+                                   if (bid == 0) scal_pq(sc, K)[it] = pq;
                                });
         if (!ok || !s_go) {
             stop = 1;
@@ -2226,23 +2311,22 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             float4 r3[3];
             tmem_ld12(t_r + 12 * kk, r3);  // whole warps
             if (gl < ng) {
-                const int l = 4 * gl, s = gslot(l);
-                // every global load of the group first (one round trip): Minv, and the
-                // samples' contributions where they arrive
+                const int l = 4 * gl, s = gslot(l), nv = gvalid(l);
+                // the samples' contributions where they arrive (the group's one global
+                // round trip), Minv from shared memory
                 const bool touched = touched_group(gl), pg = published(gl);
                 float4 qg[3], mv[3];
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    qg[a] = touched ? __ldcg(reinterpret_cast<const float4 *>(c.q + a * ld + s))
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-                    mv[a] = __ldcg(reinterpret_cast<const float4 *>(c.minv + a * ld + s));
+                    qg[a] = touched ? gld(c.q + a * ld + s, nv) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    mv[a] = *reinterpret_cast<const float4 *>(M + a * chunk + l);
                 }
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
                     float4 qv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
                     if (touched) {  // fold in (and clear) the samples' contributions
                         qv = f4add(qv, qg[a]);
-                        *reinterpret_cast<float4 *>(c.q + a * ld + s) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        gst(c.q + a * ld + s, nv, make_float4(0.f, 0.f, 0.f, 0.f));
                     }
                     const float4 rv = r3[a];
                     const float4 &mvv = mv[a];
@@ -2251,7 +2335,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
                     const float4 zn = make_float4(mvv.x * rn.x, mvv.y * rn.y, mvv.z * rn.z, mvv.w * rn.w);
                     r3[a] = rn;
                     *reinterpret_cast<float4 *>(Q + a * chunk + l) = zn;
-                    if (pg) *reinterpret_cast<float4 *>(Zg + a * ld + s) = zn;
+                    if (pg) gst(Zg + a * ld + s, nv, zn);
                     part += rn.x * zn.x + rn.y * zn.y + rn.z * zn.z + rn.w * zn.w;
                 }
             }
@@ -2260,8 +2344,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
         tmem_wait_st();
         done = it + 1;
         ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it,
-                               block_sum(part, redf), rho, sum, blockIdx.x, [&](double rho1) {
-                                   if (blockIdx.x == 0) scal_rho(sc)[it + 1] = rho1;
+                               block_sum(part, redf), rho, sum, bid, [&](double rho1) {
+                                   if (bid == 0) scal_rho(sc)[it + 1] = rho1;
                                    // go on unless converged (rho1 = r.Minv r >= 0); a next
                                    // step needs rho1 > 0
                                    s_go = pos_finite(rho1) && !le_nonneg(rho1, thr);
@@ -2283,29 +2367,83 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *
             float4 x3[3];
             tmem_ld12(t_x + 12 * k, x3);  // whole warps
             if (gl >= ng) continue;
-            const int l = 4 * gl, s = gslot(l);
+            const int l = 4 * gl, s = gslot(l), nv = gvalid(l);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
                 const float4 x4 = make_float4(fmaf(alpha_pend, pv.x, x3[a].x), fmaf(alpha_pend, pv.y, x3[a].y),
                                               fmaf(alpha_pend, pv.z, x3[a].z), fmaf(alpha_pend, pv.w, x3[a].w));
-                *reinterpret_cast<float4 *>(c.x + a * ld + s) = x4;
+                gst(c.x + a * ld + s, nv, x4);
                 if (apply) {
                     const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
                     for (int e = 0; e < 4; e++)
-                        if (s + e < N) c.u[a * ld + slot_node<kAll>(c, s + e)] += xv[e];
+                        if (kPad ? e < nv : s + e < N) c.u[a * ld + slot_node<kAll>(c, s + e)] += xv[e];
                 }
             }
         }
     }
-    if (blockIdx.x == 0 && tid == 0) {
+    if (bid == 0 && tid == 0) {
         sc->cg_done = done;
         sc->stop = stop;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(kPcgTmemCols));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+template <bool kAll, bool kVec4, bool kPad = false>
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *sc, PcgAux ax, int K, double tol2,
+                                                                   int apply) {
+    __shared__ uint32_t s_tmem;
+    if (sc->skip) return;  // the same flag for every CTA: none reaches a barrier
+    const uint32_t tmem = pcg_tmem_alloc(&s_tmem);
+    pcg_persistent_body<kAll, kVec4, kPad>(c, sc, ax, K, tol2, apply, blockIdx.x, gridDim.x, tmem);
+    pcg_tmem_free(tmem);
+}
+
+// ------------------------------------------------------------------ position steps of a batch in waves
+//
+// The position steps (Sec. 7.1) of many lattices in one cooperative launch of one CTA per
+// SM, each lattice's vectors in shared and tensor memory exactly as in k_pcg_persistent.
+// A lattice takes a group of G CTAs (the fewest whose slots fit in shared memory); the
+// groups are packed into waves of at most gridDim.x CTAs.  CTA b runs, wave after wave,
+// the step of the group it belongs to in that wave (plan[w * gridDim.x + b] = {item,
+// index in the group}, item -1: none) and then moves on: a group waits only for its own
+// CTAs (its own barrier words and partial rows), never for a wave to end, and every CTA
+// of a later group is resident, so each group completes.  The items are a kernel
+// parameter (constant memory): the step reads its lattice's fields there as
+// k_pcg_persistent reads its own, without holding them in registers.
+struct PcgWaveItem {
+    Ctx c;
+    PcgAux ax;
+    Scal *sc;   // the lattice's scalar block of this Gauss-Newton iteration
+    int G;      // CTAs of the lattice's group
+    int pad;
+};
+constexpr int kWaveMaxItems = 56;  // lattices per launch (kernel parameters are limited to 32 KB)
+struct PcgWaveArgs {
+    PcgWaveItem it[kWaveMaxItems];
+};
+static_assert(sizeof(PcgWaveArgs) + 64 <= 32764, "the items fit in the kernel parameters");
+
+template <bool kAll, bool kVec4, bool kPad = false>
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_wave(const __grid_constant__ PcgWaveArgs args,
+                                                              const int2 *__restrict__ plan, int waves, int K,
+                                                              double tol2, int apply) {
+    __shared__ uint32_t s_tmem;
+    const uint32_t tmem = pcg_tmem_alloc(&s_tmem);
+    for (int w = 0; w < waves; w++) {
+        const int2 a = plan[(size_t)w * gridDim.x + blockIdx.x];
+        if (a.x < 0) continue;
+        const PcgWaveItem &it = args.it[a.x];
+        pcg_persistent_body<kAll, kVec4, kPad>(it.c, it.sc, it.ax, K, tol2, apply, (unsigned)a.y, (unsigned)it.G, tmem);
+        // every thread is done with this step's shared and tensor memory
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    pcg_tmem_free(tmem);
 }
 
 // ------------------------------------------------------------------ batched position step (config 4)

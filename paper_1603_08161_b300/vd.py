@@ -21,6 +21,8 @@ VD_PREC_FP32, VD_PREC_MIXED = 0, 1
 VD_MEM_HOST, VD_MEM_DEVICE = 0, 1
 VD_INIT_PREV, VD_INIT_ZERO = 0, 1
 VD_APPLY_MATRIX_FREE, VD_APPLY_CACHED, VD_APPLY_AUTO = 0, 1, 2
+VD_BATCH_BRANCHES, VD_BATCH_GLOBAL, VD_BATCH_WAVES = 0, 1, 2
+_BATCH_FORMS = {VD_BATCH_BRANCHES: "branches", VD_BATCH_GLOBAL: "global", VD_BATCH_WAVES: "waves"}
 (VD_KC_ASSOCIATE, VD_KC_RHS, VD_KC_APPLY_STENCIL, VD_KC_APPLY_SAMPLES, VD_KC_UPDATE_X,
  VD_KC_UPDATE_P, VD_KC_ROTATION, VD_KC_ENERGY, VD_KC_PCG) = range(9)
 KERNEL_CLASSES = {"associate": 0, "rhs": 1, "apply_stencil": 2, "apply_samples": 3, "update_x": 4,
@@ -99,6 +101,7 @@ _SIGS = {
     "vd_profile_select": [_P, _I],
     "vd_profile_read": [_P, _PD, _PI],
     "vd_launch_counts": [_P, ctypes.POINTER(vd_solve_params), _PI, _PI],
+    "vd_pcg_plan": [_P, _PI, _PI, _PI, _PI, _PI],
     "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
     "vd_batch_set_plan": [_P, _I, _I, ctypes.c_longlong],
     "vd_batch_set_persistent": [_P, _I, _I, _I, ctypes.c_float],
@@ -130,6 +133,8 @@ _SIGS = {
     "vd_batch_get_reports": [_P, _P],
     "vd_batch_tune": [_P, ctypes.POINTER(vd_solve_params), _PI, ctypes.POINTER(ctypes.c_float)],
     "vd_batch_launch_count": [_P, _PI],
+    "vd_batch_get_groups": [_P, _PI, _PI],
+    "vd_batch_set_wave_share": [_P, _I],
     "vd_batch_last_error": [_P],
     "vd_solve_batch": [_P, _I, ctypes.POINTER(vd_solve_params), _P],
     "vd_set_energy_target": [_P, ctypes.c_double],
@@ -417,6 +422,12 @@ class Lattice:
         self._check(vd_launch_counts(self.h, ctypes.byref(prm), ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
+    def pcg_plan(self):
+        """Partition of the persistent position step: CTAs, slots per CTA, brick rows."""
+        v = [ctypes.c_int() for _ in range(5)]
+        self._check(vd_pcg_plan(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("ctas", "chunk", "by", "bz", "padded"), [x.value for x in v]))
+
 
 class Batch:
     """Several lattices solved by one captured graph (vd_batch_*)."""
@@ -471,11 +482,27 @@ class Batch:
         self._check(vd_batch_launch_count(self.h, ctypes.byref(n)))
         return n.value
 
+    def set_wave_share(self, samples_per_cta):
+        self._check(vd_batch_set_wave_share(self.h, int(samples_per_cta)))
+
+    def groups(self):
+        """CTAs per lattice of the last persistent build."""
+        out = (ctypes.c_int * len(self.lattices))()
+        self._check(vd_batch_get_groups(self.h, out, None))
+        return list(out)
+
+    def waves(self):
+        w = ctypes.c_int()
+        self._check(vd_batch_get_groups(self.h, None, ctypes.byref(w)))
+        return w.value
+
     def set_plan(self, streams, largest_first=True, run_ahead_nodes=(1 << 31) - 1):
         self._check(vd_batch_set_plan(self.h, int(streams), int(bool(largest_first)), int(run_ahead_nodes)))
 
     def set_persistent(self, on=True, threads=512, ctas_per_sm=1, sample_weight=2.0):
-        self._check(vd_batch_set_persistent(self.h, int(bool(on)), int(threads), int(ctas_per_sm),
+        """on: a VD_BATCH_* form, or True / False for VD_BATCH_GLOBAL / VD_BATCH_BRANCHES."""
+        form = int(on) if not isinstance(on, bool) else (VD_BATCH_GLOBAL if on else VD_BATCH_BRANCHES)
+        self._check(vd_batch_set_persistent(self.h, form, int(threads), int(ctas_per_sm),
                                             float(sample_weight)))
 
     def plan(self):
@@ -483,8 +510,8 @@ class Batch:
         w = ctypes.c_float()
         self._check(vd_batch_get_plan(self.h, ctypes.byref(p), ctypes.byref(t), ctypes.byref(k), ctypes.byref(w),
                                       ctypes.byref(st)))
-        return {"persistent": bool(p.value), "threads": t.value, "ctas_per_sm": k.value,
-                "sample_weight": w.value, "branches": st.value}
+        return {"form": _BATCH_FORMS.get(p.value, p.value), "persistent": p.value != VD_BATCH_BRANCHES,
+                "threads": t.value, "ctas_per_sm": k.value, "sample_weight": w.value, "branches": st.value}
 
 
 class _LevelView(Lattice):

@@ -161,3 +161,63 @@ def test_persistent_batch_free_association_and_tune(vd):
     for a, b in zip(first, again):
         assert a["n_valid_corr"] == b["n_valid_corr"]
         assert abs(a["e_total"] - b["e_total"]) <= 1e-5 * a["e_total"]
+
+
+def _check_against_oracle(vd, items, lats, reps, gn, cg, single=True):
+    for (mode, fr), lat, rep in zip(items, lats, reps):
+        assert rep["status"] == vd.VD_OK
+        u, _ = lat.get_warp()
+        ref = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL if mode == "all" else oracle.ACTIVE_SURFACE)
+        res = ref.solve(gn, cg, fixed_association=True)
+        u0, _ = ref.get_warp()
+        err = float(np.abs(u - u0).max())
+        rel = abs(rep["e_total"] - res["energy"][-1, 0]) / res["energy"][-1, 0]
+        print(f"wave batch {fr.dims} ({mode}): |du|max = {err / fr.spacing:.2e} h, dE/E = {rel:.2e}")
+        assert err <= 1e-4 * fr.spacing
+        assert rel <= 1e-5
+        assert rep["cg_done"] == int(res["cg_done"][-1])
+        if single:
+            one = _lattice(vd, mode, fr)
+            one.solve(vd.params(gn_iters=gn, cg_iters=cg, fixed_association=True, init=vd.VD_INIT_ZERO))
+            u1, _ = one.get_warp()
+            assert np.abs(u - u1).max() <= 1e-5 * fr.spacing
+
+
+def test_wave_batch_mixed_forms_matches_oracle(vd):
+    """The position steps in waves of the shared-memory persistent step (VD_BATCH_WAVES):
+    all-nodes lattices of which one has nx % 4 != 0 (the scalar stencil for all of them)
+    and surface-set lattices (a launch of their own); every lattice matches the oracle,
+    its own vd_solve, and a replay of the same graph."""
+    items = _frames()
+    prm = vd.params(gn_iters=4, cg_iters=10, fixed_association=True, init=vd.VD_INIT_ZERO)
+    lats = [_lattice(vd, m, fr) for m, fr in items]
+    batch = vd.Batch(lats)
+    batch.set_persistent(vd.VD_BATCH_WAVES)
+    reps = batch.solve(prm)
+    assert batch.plan()["form"] == "waves"
+    _check_against_oracle(vd, items, lats, reps, 4, 10)
+    again = batch.solve(prm)
+    for a, b in zip(reps, again):
+        assert abs(a["e_total"] - b["e_total"]) <= 1e-6 * a["e_total"]
+
+
+def test_wave_batch_several_waves_matches_oracle(vd):
+    """All-nodes lattices with nx % 4 == 0 (float4 groups, bricks where one fits) whose
+    CTA groups need more than the SMs hold at once -- the 32^3 and 48^3 lattices see a
+    640x480 frame, so their groups are sized by their samples -- run in two or more waves
+    inside each launch; every lattice matches the oracle and its own vd_solve."""
+    import torch
+    items = [("all", synth.capsule_frame(W=320, H=240, f=262.5, n=64, seed=9, n_sparse=120)),
+             ("all", synth.capsule_frame(W=640, H=480, f=525.0, n=32, seed=7, n_sparse=60)),
+             ("all", synth.sphere_frame(W=640, H=480, f=525.0, n=48, seed=8, n_sparse=80)),
+             ("all", synth.config1())]
+    prm = vd.params(gn_iters=3, cg_iters=10, fixed_association=True, init=vd.VD_INIT_ZERO)
+    lats = [_lattice(vd, m, fr) for m, fr in items]
+    batch = vd.Batch(lats)
+    batch.set_persistent(vd.VD_BATCH_WAVES)
+    reps = batch.solve(prm)
+    need = sum(batch.groups())
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    print(f"wave batch groups {batch.groups()} ({need} CTAs, {sms} SMs), waves {batch.waves()}")
+    assert need > sms and batch.waves() >= 2
+    _check_against_oracle(vd, items, lats, reps, 3, 10)

@@ -237,6 +237,25 @@ def test_solve_parity_brick_partition(vd, n, bricks):
     assert abs(rep["e_total"] - e0[0]) / e0[0] <= 1e-5
 
 
+@pytest.mark.parametrize("n", [37, (45, 30, 27), 92, 93])
+def test_solve_parity_padded_bricks(vd, n):
+    """All-nodes lattices whose bricks are padded: nx % 4 != 0 (rows held as a multiple
+    of 4 slots in shared memory, the padding kept at zero) and / or ny, nz that the brick
+    does not divide (ragged bricks at the far faces), so the kernel reads and writes the
+    global vectors element by element; same tolerance as the other solves, and the plan
+    is the padded one."""
+    fr = synth.capsule_frame(W=320, H=240, f=262.5, n=n, seed=11, n_sparse=60, name=f"capsules{n}")
+    lat, ref, rep, res, u, u0, R, R0 = _solve_pair(vd, fr, "all", 3, 10)
+    plan = lat.pcg_plan()
+    print(f"{fr.dims}: plan {plan}, |du|max = {np.abs(u - u0).max() / fr.spacing:.2e} h")
+    assert plan["padded"] == 1 and plan["by"] > 0
+    assert rep["gn_done"] == 3 and rep["cg_done"] == int(res["cg_done"][-1])
+    assert np.abs(u - u0).max() <= 1e-4 * fr.spacing
+    assert np.abs(R - R0).max() <= 1e-4
+    e0 = res["energy"][-1]
+    assert abs(rep["e_total"] - e0[0]) / e0[0] <= 1e-5
+
+
 def test_solve_parity_config2_surface(vd, cfg2):
     lat, ref, rep, res, u, u0, R, R0 = _solve_pair(vd, cfg2, "surface", 10, 20)
     assert np.abs(u - u0).max() <= 1e-4 * cfg2.spacing
