@@ -282,7 +282,8 @@ vd_status vd_batch_get_reports(vd_batch *batch, vd_solve_report *out);
  * lattice first, or as given), then for the fastest of those each size threshold
  * (2^19, 2^17, 2^15, 2^13 active nodes) above which lattices run ahead with their
  * persistent position step, then the waves of the shared-memory position step
- * (VD_BATCH_WAVES) with 8 / 16 branches, then the persistent form with vectors in
+ * (VD_BATCH_WAVES) with 8 / 16 branches and 2^20 (no sample bound) / 4096 / 1024
+ * samples per CTA (vd_batch_set_wave_share), then the persistent form with vectors in
  * global memory (VD_BATCH_GLOBAL) for 256 / 512 threads, 1 / 2 / 4 CTAs per SM, sample
  * weights 1 / 4 and 8 / 16 branches; keep the fastest.  Runs the solve several times (the
  * lattices' warps change).  Reports the number of branches and the time per batched
@@ -324,7 +325,8 @@ vd_status vd_batch_set_persistent(vd_batch *batch, int form, int threads, int ct
 /* VD_BATCH_WAVES: a lattice's CTA group holds at most `samples_per_cta` of its samples
  * per CTA (beside the shared-memory bound on its nodes), up to one CTA per SM; a CTA's
  * sample warps take their share of the samples' J^T J p while its stencil warps run.
- * Default 1024; vd_batch_tune searches it.  VD_ERR_INVALID_ARG below 32. */
+ * Default 2^20 (in effect no sample bound); vd_batch_tune searches it.
+ * VD_ERR_INVALID_ARG below 32. */
 vd_status vd_batch_set_wave_share(vd_batch *batch, int samples_per_cta);
 
 /* The batch's current plan (any pointer may be NULL): the form of its position steps

@@ -513,15 +513,16 @@ struct PcgPlan {
 
 // Whether the position step runs as one persistent cooperative kernel, with how many
 // CTAs and how many slots per CTA: bricks where the cheapest one within the SM count holds
-// at most 1.25x the slots of an even split (2x for a padded brick), else contiguous
-// ranges over all SMs.
+// at most 1.25x the slots of an even split (a padded brick: at most 2x, and only where an
+// even split is 2,048 slots or more -- on smaller lattices the contiguous ranges measured
+// faster), else contiguous ranges over all SMs.
 bool persistent_plan(vd_lattice *L, int *G, int *chunk, PcgPlan *out = nullptr) {
     if (!L->use_persistent || !L->coop || L->in_batch) return false;
     PcgPlan pl;
     const int N = L->all ? L->c.nn : L->n_active_h;
     const long even = ((long)std::max(N, 1) + L->num_sms - 1) / L->num_sms;
     const BrickPlan b = brick_search(L, 1, L->num_sms, false);
-    if (b.by && (b.exact ? 4L * b.chunk <= 5 * even : (long)b.chunk <= 2 * even)) {
+    if (b.by && (b.exact ? 4L * b.chunk <= 5 * even : (long)b.chunk <= 2 * even && even >= 2048)) {
         pl.G = b.G;
         pl.chunk = b.chunk;
         pl.b = b;
@@ -1474,7 +1475,7 @@ struct vd_batch {
     // position steps in waves of the shared-memory persistent step (k_pcg_wave, one
     // cooperative launch per Gauss-Newton iteration); overrides `persistent`
     bool waves = false;
-    int wave_share = 1024;           // samples per CTA that size a lattice's group (at most)
+    int wave_share = 1 << 20;        // samples per CTA that size a lattice's group (at most)
     int pthreads = 512, pctas = 1;
     float sample_weight = 2.f;
     std::vector<void *> pbufs;       // items, barrier words, partial rows
@@ -2130,26 +2131,33 @@ vd_status vd_batch_tune(vd_batch *B, const vd_solve_params *P, int *streams_out,
     bool best_p = false, best_v = false;
     int best_t = B->pthreads, best_k = B->pctas;
     float best_w = B->sample_weight;
+    int best_share = B->wave_share;
     if (B->L[0]->coop) {
-        for (int st : {8, 16}) {
-            if (st > n && st != 8) continue;
-            B->waves = true;
-            B->persistent = false;
-            float ms = 0.f;
-            vd_status s = time_build(st, best_l, 0x7fffffffL, &ms);
-            B->waves = false;
-            if (s != VD_OK) {  // a lattice too large for the waves
-                B->err.clear();
-                break;
+        bool fits = true;
+        for (int share : {1 << 20, 4096, 1024})
+            for (int st : {8, 16}) {
+                if (!fits || (st > n && st != 8)) continue;
+                B->waves = true;
+                B->persistent = false;
+                B->wave_share = share;
+                float ms = 0.f;
+                vd_status s = time_build(st, best_l, 0x7fffffffL, &ms);
+                B->waves = false;
+                if (s != VD_OK) {  // a lattice too large for the waves
+                    B->err.clear();
+                    fits = false;
+                    continue;
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_v = true;
+                    best_s = st;
+                    best_share = share;
+                    best_c = 0x7fffffffL;
+                }
             }
-            if (ms < best) {
-                best = ms;
-                best_v = true;
-                best_s = st;
-                best_c = 0x7fffffffL;
-            }
-        }
     }
+    B->wave_share = best_share;
     // then the persistent position step over every lattice with its vectors in global
     // memory: threads per CTA, CTAs per SM, the sample weight of the CTA split, and the
     // branches of the other stages

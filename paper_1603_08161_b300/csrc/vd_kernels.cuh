@@ -1983,23 +1983,29 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
     // a group of a global vector at slot s: one 16-byte access (nv is then 0 or 4), or
     // element by element where the rows are not 16-byte aligned (nx % 4 != 0; elements
     // past nv read as zero and are not written)
-    const bool rows16 = !kPad || (nx & 3) == 0;
+    const bool rows16 = (nx & 3) == 0;
     auto gld = [&](const float *p, int nv) -> float4 {
-        if (rows16) return nv > 0 ? __ldcg(reinterpret_cast<const float4 *>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float v[4];
+        if constexpr (kPad) {
+            if (!rows16) {
+                float v[4];
 #pragma unroll
-        for (int e = 0; e < 4; e++) v[e] = e < nv ? __ldcg(p + e) : 0.f;
-        return make_float4(v[0], v[1], v[2], v[3]);
+                for (int e = 0; e < 4; e++) v[e] = e < nv ? __ldcg(p + e) : 0.f;
+                return make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+        return nv > 0 ? __ldcg(reinterpret_cast<const float4 *>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
     };
     auto gst = [&](float *p, int nv, float4 v) {
-        if (rows16) {
-            if (nv > 0) *reinterpret_cast<float4 *>(p) = v;
-            return;
-        }
-        const float a4[4] = {v.x, v.y, v.z, v.w};
+        if constexpr (kPad) {
+            if (!rows16) {
+                const float a4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int e = 0; e < 4; e++)
-            if (e < nv) p[e] = a4[e];
+                for (int e = 0; e < 4; e++)
+                    if (e < nv) p[e] = a4[e];
+                return;
+            }
+        }
+        if (nv > 0) *reinterpret_cast<float4 *>(p) = v;
     };
     const int tid = threadIdx.x;
     const float w2 = 2.f * c.w_r;

@@ -202,10 +202,10 @@ def test_wave_batch_mixed_forms_matches_oracle(vd):
 
 
 def test_wave_batch_several_waves_matches_oracle(vd):
-    """All-nodes lattices with nx % 4 == 0 (float4 groups, bricks where one fits) whose
-    CTA groups need more than the SMs hold at once -- the 32^3 and 48^3 lattices see a
-    640x480 frame, so their groups are sized by their samples -- run in two or more waves
-    inside each launch; every lattice matches the oracle and its own vd_solve."""
+    """All-nodes lattices with nx % 4 == 0 (float4 groups, bricks) whose CTA groups need
+    more than the SMs hold at once -- the 32^3 and 48^3 lattices see a 640x480 frame and
+    their groups are sized by their samples (at most 512 per CTA) -- run in two or more
+    waves inside each launch; every lattice matches the oracle and its own vd_solve."""
     import torch
     items = [("all", synth.capsule_frame(W=320, H=240, f=262.5, n=64, seed=9, n_sparse=120)),
              ("all", synth.capsule_frame(W=640, H=480, f=525.0, n=32, seed=7, n_sparse=60)),
@@ -215,6 +215,7 @@ def test_wave_batch_several_waves_matches_oracle(vd):
     lats = [_lattice(vd, m, fr) for m, fr in items]
     batch = vd.Batch(lats)
     batch.set_persistent(vd.VD_BATCH_WAVES)
+    batch.set_wave_share(512)
     reps = batch.solve(prm)
     need = sum(batch.groups())
     sms = torch.cuda.get_device_properties(0).multi_processor_count

@@ -237,13 +237,13 @@ def test_solve_parity_brick_partition(vd, n, bricks):
     assert abs(rep["e_total"] - e0[0]) / e0[0] <= 1e-5
 
 
-@pytest.mark.parametrize("n", [37, (45, 30, 27), 92, 93])
+@pytest.mark.parametrize("n", [69, (75, 62, 66), 92, 93])
 def test_solve_parity_padded_bricks(vd, n):
     """All-nodes lattices whose bricks are padded: nx % 4 != 0 (rows held as a multiple
-    of 4 slots in shared memory, the padding kept at zero) and / or ny, nz that the brick
-    does not divide (ragged bricks at the far faces), so the kernel reads and writes the
-    global vectors element by element; same tolerance as the other solves, and the plan
-    is the padded one."""
+    of 4 slots in shared memory, the padding kept at zero; the global vectors read and
+    written element by element) and / or ny, nz that the brick does not divide (ragged
+    bricks at the far faces); same tolerance as the other solves, and the plan is the
+    padded one (lattices of at least 2,048 slots per SM)."""
     fr = synth.capsule_frame(W=320, H=240, f=262.5, n=n, seed=11, n_sparse=60, name=f"capsules{n}")
     lat, ref, rep, res, u, u0, R, R0 = _solve_pair(vd, fr, "all", 3, 10)
     plan = lat.pcg_plan()
