@@ -117,6 +117,10 @@ struct vd_lattice {
     float *warm = nullptr;
     // persistent batched position step: published z and stencil q (6 ld), lazily allocated
     float *batch_vecs = nullptr;
+    // published vectors of a padded brick with unaligned rows (z, p even / odd, q; 3
+    // planes of pad_ldp floats each), allocated with such a plan
+    float *pad_vecs = nullptr;
+    size_t pad_ldp = 0;
     // global pose estimation (dense projective ICP): device state, lazily allocated
     IcpState *icp = nullptr;
     // cached B^T B of the dense samples (per occupied cell, 24 x 24), VD_APPLY_*
@@ -545,11 +549,45 @@ bool persistent_plan(vd_lattice *L, int *G, int *chunk, PcgPlan *out = nullptr) 
 
 unsigned magic_of(int d) { return d > 0 ? (unsigned)(((1ull << 31) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u; }
 
-// the aux block of a persistent position step on plan pl
-PcgAux pcg_aux(const vd_lattice *L, double *part, unsigned long long *words, int extra, const PcgPlan &pl) {
+// The kernel form of a plan (the kPad of k_pcg_persistent): 0 exact bricks or contiguous
+// ranges, 1 padded bricks with 16-byte-aligned rows (nx % 4 == 0), 2 padded bricks with
+// unaligned rows (their published vectors in the lattice's pad_vecs)
+int pcg_kpad(const vd_lattice *L, const PcgPlan &pl) {
+    if (!pl.b.by || pl.b.exact) return 0;
+    return L->c.nx % 4 ? 2 : 1;
+}
+
+// the published vectors of kernel form 2 (allocated, and zeroed once, outside any capture)
+vd_status ensure_pad(vd_lattice *L, const PcgPlan &pl, int kpad) {
+    if (kpad != 2) return VD_OK;
+    const size_t ldp = (((size_t)pl.b.lx * L->c.ny * L->c.nz) + 31) & ~(size_t)31;
+    if (L->pad_vecs && L->pad_ldp == ldp) return VD_OK;
+    dfree(L, L->pad_vecs);
+    L->pad_ldp = 0;
+    TRY(dalloc(L, &L->pad_vecs, 12 * ldp));
+    if (cudaMemsetAsync(L->pad_vecs, 0, sizeof(float) * 12 * ldp, L->stream) != cudaSuccess ||
+        cudaStreamSynchronize(L->stream) != cudaSuccess)
+        return fail(L, VD_ERR_CUDA, "zeroing the padded vectors");
+    L->pad_ldp = ldp;
+    return VD_OK;
+}
+
+// the aux block of a persistent position step on plan pl in kernel form kpad
+PcgAux pcg_aux(const vd_lattice *L, double *part, unsigned long long *words, int extra, const PcgPlan &pl, int kpad) {
     const int lx = pl.b.by ? pl.b.lx : L->c.nx;
-    return PcgAux{part,       words, extra, (int *)(L->pcg_bar + 2), L->surf_flag, {L->c.p, L->vecs + 15 * (size_t)L->c.ld},
-                  pl.chunk,   pl.b.by, pl.b.bz, lx, magic_of(lx), magic_of(pl.b.by)};
+    PcgAux ax{part,     words,   extra,   (int *)(L->pcg_bar + 2), L->surf_flag, {L->c.p, L->vecs + 15 * (size_t)L->c.ld},
+              pl.chunk, pl.b.by, pl.b.bz, lx,      magic_of(lx), magic_of(pl.b.by), nullptr, nullptr, 0,
+              magic_of(L->c.nx)};
+    if (kpad == 2) {
+        float *v = L->pad_vecs;
+        const size_t ldp = L->pad_ldp;
+        ax.zpad = v;
+        ax.pbuf[0] = v + 3 * ldp;
+        ax.pbuf[1] = v + 6 * ldp;
+        ax.qpad = v + 9 * ldp;
+        ax.ldp = (long long)ldp;
+    }
+    return ax;
 }
 
 template <bool kAll>
@@ -558,7 +596,9 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     PcgPlan pl;
     if (!persistent_plan(L, &G, &chunk, &pl)) return;
     unsigned long long *words = reinterpret_cast<unsigned long long *>(L->pcg_part + (size_t)L->pcg_part_rows * L->num_sms);
-    const PcgAux ax = pcg_aux(L, L->pcg_part, words, L->stall_extra, pl);
+    const int kpad = pcg_kpad(L, pl);
+    if (kpad == 2 && !L->pad_vecs) return;  // ensure_pad runs before the capture
+    const PcgAux ax = pcg_aux(L, L->pcg_part, words, L->stall_extra, pl, kpad);
     const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
     cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
     cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(2 * K + 1), Lc.st);
@@ -575,7 +615,10 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const Ctx c = L->c;
-    if (kAll && pl.b.by && !pl.b.exact) cudaLaunchKernelEx(&cfg, k_pcg_persistent<true, true, true>, c, sc, ax, K, tol2, apply);
+    if (kAll && kpad == 1)
+        cudaLaunchKernelEx(&cfg, k_pcg_persistent<true, true, 1>, c, sc, ax, K, tol2, apply);
+    else if (kAll && kpad == 2)
+        cudaLaunchKernelEx(&cfg, k_pcg_persistent<true, true, 2>, c, sc, ax, K, tol2, apply);
     else if (kAll && (pl.b.by || c.nx % 4 == 0)) cudaLaunchKernelEx(&cfg, k_pcg_persistent<kAll, true>, c, sc, ax, K, tol2, apply);
     else cudaLaunchKernelEx(&cfg, k_pcg_persistent<kAll, false>, c, sc, ax, K, tol2, apply);
     L->counting++;
@@ -671,7 +714,7 @@ vd_status build_graph(vd_lattice *L, const vd_solve_params *P) {
     const Grid gr = grids(L);
     int pG = 0, pch = 0;
     PcgPlan pl;
-    persistent_plan(L, &pG, &pch, &pl);
+    if (persistent_plan(L, &pG, &pch, &pl)) TRY(ensure_pad(L, pl, pcg_kpad(L, pl)));
     const int pby = pl.b.by, pbz = pl.b.bz;
     const int caps[6] = {gr.node, gr.samp, gr.cells, L->S * 65536 + pch, pby * 65536 + pbz,
                          gr.btb * 65536 + (L->c.btb ? L->n_occ_h : 0)};
@@ -863,7 +906,8 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
         }
         const int bytes = kPcgSmemPerSlot * kPcgMaxChunk;
         if (cudaFuncSetAttribute(k_pcg_persistent<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
-            cudaFuncSetAttribute(k_pcg_persistent<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
+            cudaFuncSetAttribute(k_pcg_persistent<true, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
+            cudaFuncSetAttribute(k_pcg_persistent<true, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
             cudaFuncSetAttribute(k_pcg_persistent<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
             cudaFuncSetAttribute(k_pcg_persistent<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) {
             cudaGetLastError();
@@ -1220,7 +1264,9 @@ vd_status vd_step_pcg(vd_lattice *L, const vd_solve_params *P, float *delta, int
     const double tol2 = P->cg_tol * P->cg_tol;
     Launcher Lc{L, st};
     int pG = 0, pch = 0;
-    if (persistent_plan(L, &pG, &pch)) {
+    PcgPlan ppl;
+    if (persistent_plan(L, &pG, &pch, &ppl)) {
+        TRY(ensure_pad(L, ppl, pcg_kpad(L, ppl)));
         if (L->all) {
             enqueue_rhs<true>(Lc, c, sc, gr, K);
             enqueue_btb<true>(Lc, c, sc, gr, L->n_occ_h);
@@ -1886,10 +1932,11 @@ vd_status batch_build_waves(vd_batch *B, const vd_solve_params *P, int streams, 
     const int K = P->cg_iters, GN = P->gn_iters;
     const int T = B->L[0]->num_sms;
     if (!B->L[0]->coop) return bfail(B, VD_ERR_INVALID_ARG, "the wave form needs cooperative launches");
-    // the lattices' plans; launch sets by kernel form: 3 (all nodes, padded bricks, when
-    // any all-nodes lattice needs one), 2 (all nodes, exact bricks), 0 (surface sets)
+    // the lattices' plans; launch sets by kernel form: all nodes in the most general brick
+    // form any of them needs -- 2 exact, 3 padded with 16-byte-aligned rows, 4 padded
+    // rows (nx % 4 != 0) -- and 0 for the surface sets
     std::vector<PcgPlan> wp(n);
-    bool exact = true;
+    int all_form = 2;
     for (int i = 0; i < n; i++) {
         vd_lattice *L = B->L[i];
         vd_status s = ensure_scal(L, GN, K);
@@ -1899,7 +1946,7 @@ vd_status batch_build_waves(vd_batch *B, const vd_solve_params *P, int streams, 
         wp[i] = wave_plan(L, T, B->wave_share);
         if (!wp[i].G || wp[i].G > T || wp[i].G > kPcgMaxCtas)
             return bfail(B, VD_ERR_INVALID_ARG, "a lattice of the batch is too large for the wave form");
-        if (L->all) exact = exact && wp[i].b.exact;
+        if (L->all && !wp[i].b.exact) all_form = std::max(all_form, L->c.nx % 4 ? 4 : 3);
     }
     struct Set {
         int form;
@@ -1908,13 +1955,20 @@ vd_status batch_build_waves(vd_batch *B, const vd_solve_params *P, int streams, 
         size_t plan_off = 0;
     };
     std::vector<Set> sets;
-    for (int form : {3, 2, 0})
+    for (int form : {4, 3, 2, 0})
         for (int i = 0; i < n; i++) {
-            const int f = B->L[i]->all ? (exact ? 2 : 3) : 0;
+            const int f = B->L[i]->all ? all_form : 0;
             if (f != form) continue;
             if (sets.empty() || sets.back().form != form || (int)sets.back().lat.size() == kWaveMaxItems)
                 sets.push_back(Set{form, {}});
             sets.back().lat.push_back(i);
+        }
+    // the kernel form of a set (kPad), and the padded vectors its lattices need
+    auto set_kpad = [](int form) { return form == 4 ? 2 : form == 3 ? 1 : 0; };
+    for (const Set &S : sets)
+        for (int i : S.lat) {
+            vd_status s = ensure_pad(B->L[i], wp[i], set_kpad(S.form));
+            if (s != VD_OK) return bfail(B, s, B->L[i]->err.c_str());
         }
     // per set, first fit decreasing: the wave of each lattice's group and its first CTA
     std::vector<int2> plan;
@@ -1959,13 +2013,14 @@ vd_status batch_build_waves(vd_batch *B, const vd_solve_params *P, int streams, 
                 vd_lattice *L = B->L[i];
                 PcgWaveItem &it = A.it[item_of[i]];
                 it.c = L->c;
-                it.ax = pcg_aux(L, L->pcg_part, B->words + (size_t)i * (2 * K + 1), 0, wp[i]);
+                it.ax = pcg_aux(L, L->pcg_part, B->words + (size_t)i * (2 * K + 1), 0, wp[i], set_kpad(sets[si].form));
                 it.sc = slot(L, gi);
                 it.G = wp[i].G;
             }
         }
     const int bytes = kPcgSmemPerSlot * kPcgMaxChunk;
-    for (auto f : {k_pcg_wave<true, true, true>, k_pcg_wave<true, true, false>, k_pcg_wave<false, false, false>}) {
+    for (auto f : {k_pcg_wave<true, true, 2>, k_pcg_wave<true, true, 1>, k_pcg_wave<true, true, 0>,
+                   k_pcg_wave<false, false, 0>}) {
         int occ = 0;
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kPcgThreads, bytes) != cudaSuccess || occ < 1) {
@@ -1994,9 +2049,10 @@ vd_status batch_build_waves(vd_batch *B, const vd_solve_params *P, int streams, 
             cfg.numAttrs = 1;
             const PcgWaveArgs &A = args[(size_t)gi * sets.size() + si];
             const int2 *pl = B->wplan + S.plan_off;
-            if (S.form == 3) cudaLaunchKernelEx(&cfg, k_pcg_wave<true, true, true>, A, pl, S.waves, K, tol2, 1);
-            else if (S.form == 2) cudaLaunchKernelEx(&cfg, k_pcg_wave<true, true, false>, A, pl, S.waves, K, tol2, 1);
-            else cudaLaunchKernelEx(&cfg, k_pcg_wave<false, false, false>, A, pl, S.waves, K, tol2, 1);
+            if (S.form == 4) cudaLaunchKernelEx(&cfg, k_pcg_wave<true, true, 2>, A, pl, S.waves, K, tol2, 1);
+            else if (S.form == 3) cudaLaunchKernelEx(&cfg, k_pcg_wave<true, true, 1>, A, pl, S.waves, K, tol2, 1);
+            else if (S.form == 2) cudaLaunchKernelEx(&cfg, k_pcg_wave<true, true, 0>, A, pl, S.waves, K, tol2, 1);
+            else cudaLaunchKernelEx(&cfg, k_pcg_wave<false, false, 0>, A, pl, S.waves, K, tol2, 1);
         }
         return (int)sets.size();
     });

@@ -870,6 +870,31 @@ __device__ __forceinline__ float ldvv(const VecView &v, size_t i) {
     return v.pold ? fmaf(v.beta, ldv<kFresh>(v.pold + i), a) : a;
 }
 
+// Where the sample passes of the persistent position step find a node's entries in the
+// vectors they read and add to (kMap): at x + lx (y + ny z), plane stride ld -- the layout
+// of the published vectors of a padded brick, whose rows of lx slots keep every float4
+// group aligned; otherwise (!kMap) at the node's slot with plane stride c.ld.
+struct SlotMap {
+    int lx;
+    unsigned m_nx;  // n / nx as (2n m_nx) >> 32, exact for n nx < 2^31
+    size_t ld;
+};
+
+template <bool kAll, bool kMap>
+__device__ __forceinline__ int map_corner(const Ctx &c, const SlotMap &m, int cell, int k) {
+    if constexpr (!kMap) {
+        return node_slot<kAll>(c, corner_node(c, cell, k));
+    } else {
+        const int pc = cell + (m.lx - c.nx) * (int)__umulhi(2u * (unsigned)cell, m.m_nx);
+        return pc + (k & 1) + m.lx * (((k >> 1) & 1) + c.ny * ((k >> 2) & 1));
+    }
+}
+
+template <bool kMap>
+__device__ __forceinline__ size_t map_ld(const Ctx &c, const SlotMap &m) {
+    return kMap ? m.ld : (size_t)c.ld;
+}
+
 // synchronise the threads running a cells_block: the whole block (bar_id 0) or the
 // nt threads of named barrier bar_id
 __device__ __forceinline__ void sub_sync(int bar_id, int nt) {
@@ -1024,9 +1049,10 @@ __device__ __forceinline__ void cells_block(const Ctx &c, const VecView vec, flo
 // leaves the sums of each cell's lanes in its first lane, which adds them to dst.
 // An equal number of samples per warp, whatever their spread over cells.
 // part += t (g.(sum alpha p)) per sample.
-template <bool kAll>
+template <bool kAll, bool kMap = false>
 __device__ __forceinline__ void samples_warp_apply(const Ctx &c, const VecView &vec, float *dst, int js, int je,
-                                                   float &part, int lt, int nt) {
+                                                   float &part, int lt, int nt, const SlotMap &m = SlotMap{}) {
+    const size_t ldm = map_ld<kMap>(c, m);
     const int lane = lt & 31;
     for (int j0 = js + (lt & ~31); j0 < je; j0 += nt) {  // the same trip count in every lane of a warp
         const int j = j0 + lane;
@@ -1044,10 +1070,10 @@ __device__ __forceinline__ void samples_warp_apply(const Ctx &c, const VecView &
         for (int k = 0; k < 8; k++) {
             al[k] = trilinear_weight(f, k);
             if (has) {
-                const int vi = node_slot<kAll>(c, corner_node(c, cl, k));
+                const int vi = map_corner<kAll, kMap>(c, m, cl, k);
                 sx += al[k] * ldvv<true>(vec, vi);
-                sy += al[k] * ldvv<true>(vec, c.ld + vi);
-                sz += al[k] * ldvv<true>(vec, 2 * (size_t)c.ld + vi);
+                sy += al[k] * ldvv<true>(vec, ldm + vi);
+                sz += al[k] * ldvv<true>(vec, 2 * ldm + vi);
             }
         }
         const float sv = g.x * sx + g.y * sy + g.z * sz;
@@ -1073,10 +1099,10 @@ __device__ __forceinline__ void samples_warp_apply(const Ctx &c, const VecView &
         if (has && (lane == 0 || kp != cl)) {
 #pragma unroll
             for (int k = 0; k < 8; k++) {
-                const int sl = node_slot<kAll>(c, corner_node(c, cl, k));
+                const int sl = map_corner<kAll, kMap>(c, m, cl, k);
 #pragma unroll
                 for (int a = 0; a < 3; a++)
-                    if (v[3 * k + a] != 0.f) atomicAdd(&dst[(size_t)a * c.ld + sl], v[3 * k + a]);
+                    if (v[3 * k + a] != 0.f) atomicAdd(&dst[(size_t)a * ldm + sl], v[3 * k + a]);
             }
         }
     }
@@ -1086,9 +1112,11 @@ __device__ __forceinline__ void samples_warp_apply(const Ctx &c, const VecView &
 //   kOpRhs:    r_k -= w_s alpha_k R_g^T d,  diag_k += w_s alpha_k^2 |R_g col|^2
 //   kOpApply:  q_k += w_s alpha_k R_g^T R_g sum alpha p;  part += w_s |R_g sum alpha p|^2
 //   kOpEnergy: partd += |d|^2
-template <int kOp, bool kAll, bool kFresh>
+template <int kOp, bool kAll, bool kFresh, bool kMap = false>
 __device__ __forceinline__ void sparse_pairs(const Ctx &c, const VecView vec, float *dst, float *dst2, int t0,
-                                             int nthreads, float &part, double &partd) {
+                                             int nthreads, float &part, double &partd, const SlotMap &m = SlotMap{}) {
+    static_assert(!kMap || kOp == kOpApply, "the slot map serves the position step only");
+    const size_t ldm = map_ld<kMap>(c, m);
     for (int sp = t0; sp < c.S; sp += nthreads) {
         const int cl = c.scell[sp];
         if (cl < 0) continue;
@@ -1101,11 +1129,11 @@ __device__ __forceinline__ void sparse_pairs(const Ctx &c, const VecView vec, fl
         for (int k = 0; k < 8; k++) {
             al[k] = trilinear_weight(f, k);
             const int nd = corner_node(c, cl, k);
-            sl[k] = node_slot<kAll>(c, nd);
+            sl[k] = map_corner<kAll, kMap>(c, m, cl, k);
             const int vi = (kOp == kOpApply) ? sl[k] : nd;
             sv.x += al[k] * ldvv<kFresh>(vec, vi);
-            sv.y += al[k] * ldvv<kFresh>(vec, c.ld + vi);
-            sv.z += al[k] * ldvv<kFresh>(vec, 2 * (size_t)c.ld + vi);
+            sv.y += al[k] * ldvv<kFresh>(vec, ldm + vi);
+            sv.z += al[k] * ldvv<kFresh>(vec, 2 * ldm + vi);
         }
         if (kOp == kOpApply) {
             const V3<float> t = rot<float>(c.Rg, sv);
@@ -1115,8 +1143,8 @@ __device__ __forceinline__ void sparse_pairs(const Ctx &c, const VecView vec, fl
             for (int k = 0; k < 8; k++) {
                 const float a = c.w_s * al[k];
                 atomicAdd(&dst[sl[k]], a * back.x);
-                atomicAdd(&dst[c.ld + sl[k]], a * back.y);
-                atomicAdd(&dst[2 * c.ld + sl[k]], a * back.z);
+                atomicAdd(&dst[ldm + sl[k]], a * back.y);
+                atomicAdd(&dst[2 * ldm + sl[k]], a * back.z);
             }
         } else {
             const float4 fh = c.fh[sp], ft = c.ft[sp];
@@ -1225,16 +1253,18 @@ __global__ void __launch_bounds__(kThreads) k_btb_build(Ctx c, const Scal *sc) {
 // q += B_cell p_cell for occupied cell ci, one warp: lane l < 24 gathers p at corner l / 3,
 // component l % 3, forms row l of the product (p broadcast by shuffles) and adds it to
 // q there; part += p_cell . B_cell p_cell.  Every lane of the warp must call it.
-template <bool kAll, bool kFresh>
-__device__ __forceinline__ void btb_cell_apply(const Ctx &c, const VecView vec, int ci, float *dst, float &part) {
+template <bool kAll, bool kFresh, bool kMap = false>
+__device__ __forceinline__ void btb_cell_apply(const Ctx &c, const VecView vec, int ci, float *dst, float &part,
+                                               const SlotMap &m = SlotMap{}) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < 24;
     const int k = lane / 3, a = lane - 3 * (lane / 3);
+    const size_t ldm = map_ld<kMap>(c, m);
     int sl = 0;
     float pl = 0.f;
     if (act) {
-        sl = node_slot<kAll>(c, corner_node(c, c.occ_cell[ci], k));
-        pl = ldvv<kFresh>(vec, (size_t)a * c.ld + sl);
+        sl = map_corner<kAll, kMap>(c, m, c.occ_cell[ci], k);
+        pl = ldvv<kFresh>(vec, (size_t)a * ldm + sl);
     }
     const float4 *B = reinterpret_cast<const float4 *>(c.btb + (size_t)ci * kBtb + (act ? lane : 0) * 24);
     float q = 0.f;
@@ -1248,7 +1278,7 @@ __device__ __forceinline__ void btb_cell_apply(const Ctx &c, const VecView vec, 
     }
     if (act) {
         part += pl * q;
-        if (q != 0.f) atomicAdd(&dst[(size_t)a * c.ld + sl], q);
+        if (q != 0.f) atomicAdd(&dst[(size_t)a * ldm + sl], q);
     }
 }
 
@@ -1673,6 +1703,11 @@ struct PcgAux {
     // n / lx and n / by as (2n m) >> 32 with m = ceil(2^31 / d), exact for n d < 2^31
     // (the local slot and row indices of a brick): no integer division in the loops
     unsigned m_nx, m_by;
+    // a padded brick with unaligned rows (nx % 4 != 0): z, q and (in pbuf) p published at
+    // x + lx (y + ny z), plane stride ldp; m_nx0: the multiply-high constant of nx
+    float *zpad, *qpad;
+    long long ldp;
+    unsigned m_nx0;
 };
 
 __device__ __forceinline__ int fast_div(int n, unsigned m) { return (int)__umulhi(2u * (unsigned)n, m); }
@@ -1915,10 +1950,12 @@ __device__ __forceinline__ void pcg_tmem_free(uint32_t tmem) {
 // One position step (Sec. 7.1) of one lattice by a group of G co-resident CTAs, this one
 // being number bid of the group; tmem: the CTA's tensor memory (kPcgTmemCols columns).
 // Returns with the CTA synchronised (its shared and tensor memory free for reuse).
-// kPad: a padded brick (rows of ax.lx slots in shared memory, nx of them real; ragged
-// bricks at the far faces): global vectors are then read and written element by element,
-// the padding elements stay zero and take no part in the stencil or the sums.
-template <bool kAll, bool kVec4, bool kPad = false>
+// kPad: 0, a brick that tiles the lattice with 16-byte-aligned rows; otherwise a padded
+// brick (rows of ax.lx slots in shared memory, nx of them real; ragged bricks at the far
+// faces; the padding elements stay zero and take no part in the stencil or the sums):
+// 1 where nx % 4 == 0 (global rows still 16-byte aligned), 2 where not (global vectors
+// then read and written element by element).
+template <bool kAll, bool kVec4, int kPad = 0>
 __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, const PcgAux &ax, int K, double tol2,
                                                     int apply, const unsigned bid, const unsigned G,
                                                     const uint32_t tmem) {
@@ -1950,7 +1987,11 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
     float *__restrict__ P = sm;               // p of own slots
     float *__restrict__ Q = sm + 3 * chunk;   // z between phases B and A, q within A..B
     float *__restrict__ M = sm + 6 * chunk;   // Minv of own slots
-    float *__restrict__ Zg = c.r;
+    // the published and accumulated vectors (z, p, the samples' q): at the node's slot, or
+    // for a padded brick with unaligned rows (kPad == 2) in ax.zpad, ax.pbuf and ax.qpad at
+    // x + lx (y + ny z) (plane stride ax.ldp), where every group is one aligned float4
+    float *__restrict__ Zg = kPad == 2 ? ax.zpad : c.r;
+    float *__restrict__ Qg = kPad == 2 ? ax.qpad : c.q;
     if (sc->skip) return;  // the same flag for every CTA: none reaches a barrier
     const int N = active_count<kAll>(c);
     const int N4 = 4 * groups4(N);
@@ -1981,35 +2022,53 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
         return min(4, nx - (l - r * lx));
     };
     // a group of a global vector at slot s: one 16-byte access (nv is then 0 or 4), or
-    // element by element where the rows are not 16-byte aligned (nx % 4 != 0; elements
-    // past nv read as zero and are not written)
-    const bool rows16 = (nx & 3) == 0;
+    // element by element where the rows are not 16-byte aligned (kPad == 2; elements past
+    // nv read as zero and are not written)
     auto gld = [&](const float *p, int nv) -> float4 {
-        if constexpr (kPad) {
-            if (!rows16) {
-                float v[4];
+        if constexpr (kPad == 2) {
+            float v[4];
 #pragma unroll
-                for (int e = 0; e < 4; e++) v[e] = e < nv ? __ldcg(p + e) : 0.f;
-                return make_float4(v[0], v[1], v[2], v[3]);
-            }
+            for (int e = 0; e < 4; e++) v[e] = e < nv ? __ldcg(p + e) : 0.f;
+            return make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            return nv > 0 ? __ldcg(reinterpret_cast<const float4 *>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        return nv > 0 ? __ldcg(reinterpret_cast<const float4 *>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
     };
     auto gst = [&](float *p, int nv, float4 v) {
-        if constexpr (kPad) {
-            if (!rows16) {
-                const float a4[4] = {v.x, v.y, v.z, v.w};
+        if constexpr (kPad == 2) {
+            const float a4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int e = 0; e < 4; e++)
-                    if (e < nv) p[e] = a4[e];
-                return;
-            }
+            for (int e = 0; e < 4; e++)
+                if (e < nv) p[e] = a4[e];
+        } else {
+            if (nv > 0) *reinterpret_cast<float4 *>(p) = v;
         }
-        if (nv > 0) *reinterpret_cast<float4 *>(p) = v;
     };
     const int tid = threadIdx.x;
     const float w2 = 2.f * c.w_r;
     const size_t ld = c.ld;
+    const size_t ldg = kPad == 2 ? (size_t)ax.ldp : ld;
+    const int pln = kPad == 2 ? lx * c.ny : plane;  // z stride of that layout
+    auto pslot = [&](int l) -> int {  // a group's slot in that layout
+        if constexpr (kPad != 2) {
+            return gslot(l);
+        } else {
+            const int r = fast_div(l, ax.m_nx), rz = fast_div(r, ax.m_by);
+            return (l - r * lx) + lx * (y0 + (r - rz * ax.by)) + pln * (z0 + rz);
+        }
+    };
+    auto pld = [&](const float *p, int nv) -> float4 {
+        if constexpr (kPad == 2) return nv > 0 ? __ldcg(reinterpret_cast<const float4 *>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        else return gld(p, nv);
+    };
+    auto pst = [&](float *p, int nv, float4 v) {
+        if constexpr (kPad == 2) {
+            if (nv > 0) *reinterpret_cast<float4 *>(p) = v;
+        } else {
+            gst(p, nv, v);
+        }
+    };
+
     const uint32_t t_r = tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + 64u * (uint32_t)(tid >> 7);
     const uint32_t t_x = t_r + kPcgTmemX;
     if (tid == 0) {  // an equal share of the sorted samples
@@ -2028,7 +2087,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
 #pragma unroll
         for (int a = 0; a < 3; a++) r3[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (gl < ng) {
-            const int l = 4 * gl, s = gslot(l), nv = gvalid(l);
+            const int l = 4 * gl, s = gslot(l), sp = pslot(l), nv = gvalid(l);
             pub[kk] = true;
             if (brick) {
                 const int r = fast_div(l, ax.m_nx), zl = fast_div(r, ax.m_by), yl = r - zl * ax.by;
@@ -2055,11 +2114,11 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                 r3[a] = make_float4(rr[0], rr[1], rr[2], rr[3]);
                 *reinterpret_cast<float4 *>(Q + a * chunk + l) = z4;
                 *reinterpret_cast<float4 *>(P + a * chunk + l) = zero;
-                gst(Zg + a * ld + s, nv, z4);
-                gst(ax.pbuf[1] + a * ld + s, nv, zero);
+                pst(Zg + a * ldg + sp, nv, z4);
+                pst(ax.pbuf[1] + a * ldg + sp, nv, zero);
             }
             int4 fl;
-            if (kPad) {
+            if (kPad == 2) {
                 fl = make_int4(nv > 0 ? __ldcg(ax.flag + s) : 0, nv > 1 ? __ldcg(ax.flag + s + 1) : 0,
                                nv > 2 ? __ldcg(ax.flag + s + 2) : 0, nv > 3 ? __ldcg(ax.flag + s + 3) : 0);
             } else {
@@ -2067,7 +2126,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
             }
             if (fl.x | fl.y | fl.z | fl.w) {  // the samples' contributions arrive here by atomics
 #pragma unroll
-                for (int a = 0; a < 3; a++) gst(c.q + a * ld + s, nv, make_float4(0.f, 0.f, 0.f, 0.f));
+                for (int a = 0; a < 3; a++) pst(Qg + a * ldg + sp, nv, make_float4(0.f, 0.f, 0.f, 0.f));
                 pub[kk] = touch[kk] = true;
             }
         }
@@ -2110,8 +2169,9 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
     // p anyway; the last one after the loop
     float alpha_pend = 0.f;
     for (int it = 0; it < K && !stop; it++) {
-        const float *__restrict__ pold = ax.pbuf[(it + 1) & 1];
-        float *__restrict__ pnew = ax.pbuf[it & 1];
+        // (a select, not an index into the parameter: no local copy of it)
+        const float *__restrict__ pold = (it & 1) ? ax.pbuf[0] : ax.pbuf[1];
+        float *__restrict__ pnew = (it & 1) ? ax.pbuf[1] : ax.pbuf[0];
         const float xa = alpha_pend;
         alpha_pend = 0.f;
         part = 0.f;
@@ -2124,7 +2184,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                 float4 x3[3];
                 if (xa != 0.f) tmem_ld12(t_x + 12 * k, x3);
                 if (gl < ng) {
-                    const int l = 4 * gl, s = gslot(l);
+                    const int l = 4 * gl, sp = pslot(l);
                     const bool pg = published(gl);
                     const int nv = pg ? gvalid(l) : 0;
 #pragma unroll
@@ -2137,7 +2197,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                         const float4 pn = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y),
                                                       fmaf(beta, pv.z, zv.z), fmaf(beta, pv.w, zv.w));
                         *reinterpret_cast<float4 *>(P + a * chunk + l) = pn;
-                        if (pg) gst(pnew + a * ld + s, nv, pn);
+                        if (pg) pst(pnew + a * ldg + sp, nv, pn);
                     }
                 }
                 if (xa != 0.f) tmem_st12(t_x + 12 * k, x3);
@@ -2152,14 +2212,15 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                     int x0, y, z, s0;
                     bool own[4];
                     int loff[4];
-                    const int offs[4] = {-nx, nx, -plane, plane};
+                    // s0, offs: the group and its neighbours' offsets in the published layout
+                    const int offs[4] = {-lx, lx, -pln, pln};
                     int nv = 4;
                     if (brick) {
                         const int r = fast_div(l, ax.m_nx), zl = fast_div(r, ax.m_by), yl = r - zl * ax.by;
                         x0 = l - r * lx;
                         y = y0 + yl;
                         z = z0 + zl;
-                        s0 = x0 + nx * y + plane * z;
+                        s0 = x0 + lx * y + pln * z;
                         own[0] = yl > 0;
                         own[1] = yl + 1 < byA;
                         own[2] = zl > 0;
@@ -2194,7 +2255,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
                         const float *Pa = P + a * chunk;
-                        const float *Za = Zg + a * ld, *Oa = pold + a * ld;
+                        const float *Za = Zg + a * ldg, *Oa = pold + a * ldg;
                         const float4 pc = *reinterpret_cast<const float4 *>(Pa + l);
                         float left = pc.x, right = pc.w;
                         if (x0 > 0)
@@ -2228,8 +2289,8 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                             if (own[k]) {
                                 v = *reinterpret_cast<const float4 *>(Pa + l + loff[k]);
                             } else {
-                                const float4 zz = gld(Za + sj, nv);
-                                const float4 oo = gld(Oa + sj, nv);
+                                const float4 zz = pld(Za + sj, nv);
+                                const float4 oo = pld(Oa + sj, nv);
                                 v = make_float4(fmaf(beta, oo.x, zz.x), fmaf(beta, oo.y, zz.y), fmaf(beta, oo.z, zz.z),
                                                 fmaf(beta, oo.w, zz.w));
                             }
@@ -2263,7 +2324,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
 #pragma unroll
                                 for (int a = 0; a < 3; a++) {
                                     const float pj = own ? P[a * chunk + (sj - s_beg)]
-                                                         : fmaf(beta, __ldcg(pold + a * ld + sj), __ldcg(Zg + a * ld + sj));
+                                                         : fmaf(beta, __ldcg(pold + a * ldg + sj), __ldcg(Zg + a * ldg + sj));
                                     q3[a] += pi[a] - pj;
                                 }
                             }
@@ -2279,7 +2340,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                 }
             }
         } else {
-            // ---- A: the samples' J^T J p into c.q (atomics), p formed from z and p_old
+            // ---- A: the samples' J^T J p into Qg (atomics), p formed from z and p_old
             const int lt = tid - kPcgStencil;
             const VecView pv{Zg, pold, beta};
             if (c.btb) {  // cached B^T B: an equal share of the occupied cells, a warp per cell
@@ -2287,14 +2348,22 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                 const int cb = (int)(((long long)n_occ * bid) / G);
                 const int ce = (int)(((long long)n_occ * (bid + 1)) / G);
                 for (int ci = cb + (lt >> 5); ci < ce; ci += kPcgSample >> 5)
-                    btb_cell_apply<kAll, true>(c, pv, ci, c.q, part);
+                    if constexpr (kPad == 2) btb_cell_apply<kAll, true, true>(c, pv, ci, Qg, part, SlotMap{lx, ax.m_nx0, ldg});
+                    else btb_cell_apply<kAll, true>(c, pv, ci, Qg, part);
             } else {
-                samples_warp_apply<kAll>(c, pv, c.q, s_js, s_je, part, lt, kPcgSample);
+                if constexpr (kPad == 2)
+                    samples_warp_apply<kAll, true>(c, pv, Qg, s_js, s_je, part, lt, kPcgSample, SlotMap{lx, ax.m_nx0, ldg});
+                else
+                    samples_warp_apply<kAll>(c, pv, Qg, s_js, s_je, part, lt, kPcgSample);
             }
             // the pairs go to the last warps, which hold the fewest cells
             double pd = 0.0;
-            sparse_pairs<kOpApply, kAll, true>(c, pv, c.q, nullptr, bid + G * (kPcgSample - 1 - lt), G * kPcgSample,
-                                               part, pd);
+            if constexpr (kPad == 2)
+                sparse_pairs<kOpApply, kAll, true, true>(c, pv, Qg, nullptr, bid + G * (kPcgSample - 1 - lt),
+                                                         G * kPcgSample, part, pd, SlotMap{lx, ax.m_nx0, ldg});
+            else
+                sparse_pairs<kOpApply, kAll, true>(c, pv, Qg, nullptr, bid + G * (kPcgSample - 1 - lt), G * kPcgSample,
+                                                   part, pd);
         }
         ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it,
                                block_sum(part, redf), pq_prev, sum, bid, [&](double pq) {
@@ -2317,14 +2386,14 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
             float4 r3[3];
             tmem_ld12(t_r + 12 * kk, r3);  // whole warps
             if (gl < ng) {
-                const int l = 4 * gl, s = gslot(l), nv = gvalid(l);
+                const int l = 4 * gl, sp = pslot(l), nv = gvalid(l);
                 // the samples' contributions where they arrive (the group's one global
                 // round trip), Minv from shared memory
                 const bool touched = touched_group(gl), pg = published(gl);
                 float4 qg[3], mv[3];
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    qg[a] = touched ? gld(c.q + a * ld + s, nv) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    qg[a] = touched ? pld(Qg + a * ldg + sp, nv) : make_float4(0.f, 0.f, 0.f, 0.f);
                     mv[a] = *reinterpret_cast<const float4 *>(M + a * chunk + l);
                 }
 #pragma unroll
@@ -2332,7 +2401,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                     float4 qv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
                     if (touched) {  // fold in (and clear) the samples' contributions
                         qv = f4add(qv, qg[a]);
-                        gst(c.q + a * ld + s, nv, make_float4(0.f, 0.f, 0.f, 0.f));
+                        pst(Qg + a * ldg + sp, nv, make_float4(0.f, 0.f, 0.f, 0.f));
                     }
                     const float4 rv = r3[a];
                     const float4 &mvv = mv[a];
@@ -2341,7 +2410,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                     const float4 zn = make_float4(mvv.x * rn.x, mvv.y * rn.y, mvv.z * rn.z, mvv.w * rn.w);
                     r3[a] = rn;
                     *reinterpret_cast<float4 *>(Q + a * chunk + l) = zn;
-                    if (pg) gst(Zg + a * ld + s, nv, zn);
+                    if (pg) pst(Zg + a * ldg + sp, nv, zn);
                     part += rn.x * zn.x + rn.y * zn.y + rn.z * zn.z + rn.w * zn.w;
                 }
             }
@@ -2398,7 +2467,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-template <bool kAll, bool kVec4, bool kPad = false>
+template <bool kAll, bool kVec4, int kPad = 0>
 __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(Ctx c, Scal *sc, PcgAux ax, int K, double tol2,
                                                                    int apply) {
     __shared__ uint32_t s_tmem;
@@ -2433,7 +2502,7 @@ struct PcgWaveArgs {
 };
 static_assert(sizeof(PcgWaveArgs) + 64 <= 32764, "the items fit in the kernel parameters");
 
-template <bool kAll, bool kVec4, bool kPad = false>
+template <bool kAll, bool kVec4, int kPad = 0>
 __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_wave(const __grid_constant__ PcgWaveArgs args,
                                                               const int2 *__restrict__ plan, int waves, int K,
                                                               double tol2, int apply) {
