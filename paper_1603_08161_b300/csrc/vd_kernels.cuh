@@ -3109,14 +3109,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) 
             float qv[4] = {1.f, 0.f, 0.f, 0.f};
             bool unique = sym4_top_rqi(Nm, qv, 1e-4f * scale, scale);
             if (!unique) {
-                const float gap = horn_top_eigvec_f32(Nm, qv);
+                // the out-of-line solvers get copies, so that the fast path's matrix and
+                // vector never have their address taken (they stay in registers)
+                float Nf[4][4], qf[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    qf[r] = qv[r];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) Nf[r][k] = Nm[r][k];
+                }
+                const float gap = horn_top_eigvec_f32(Nf, qf);
                 unique = gap > 1e-5f * scale;
                 if (gap < 1e-4f * scale) {
                     // near-singular block (the rotation's sensitivity exceeds 1e4): polar
                     // decomposition again in FP64
-                    const double gd = horn_top_eigvec_f64(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz, qv);
+                    const double gd = horn_top_eigvec_f64(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz, qf);
                     unique = gd > 1e-12 * (double)scale;
                 }
+#pragma unroll
+                for (int r = 0; r < 4; r++) qv[r] = qf[r];
             }
             if (!unique) {
                 keep = true;
