@@ -222,3 +222,42 @@ def test_wave_batch_several_waves_matches_oracle(vd):
     print(f"wave batch groups {batch.groups()} ({need} CTAs, {sms} SMs), waves {batch.waves()}")
     assert need > sms and batch.waves() >= 2
     _check_against_oracle(vd, items, lats, reps, 3, 10)
+
+
+def test_wave_batch_free_association_and_tune(vd):
+    """The wave form with re-association at every Gauss-Newton iteration (the bench's
+    mode): every lattice's final energy within 1e-5 of the oracle's free-association
+    solve; then the tuner (which times the wave form beside the others) and a replay."""
+    items = _frames()[:4]
+    prm = vd.params(gn_iters=3, cg_iters=8, init=vd.VD_INIT_ZERO)
+    lats = [_lattice(vd, m, fr) for m, fr in items]
+    batch = vd.Batch(lats)
+    batch.set_persistent(vd.VD_BATCH_WAVES)
+    first = batch.solve(prm)
+    for (mode, fr), lat, rep in zip(items, lats, first):
+        ref = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL if mode == "all" else oracle.ACTIVE_SURFACE)
+        res = ref.solve(3, 8, fixed_association=False)
+        assert abs(rep["e_total"] - res["energy"][-1, 0]) <= 1e-5 * res["energy"][-1, 0]
+    streams, ms = batch.tune(prm)
+    plan = batch.plan()
+    print(f"tuned batch: {plan}, {ms:.3f} ms")
+    assert plan["form"] in ("branches", "waves", "global")
+    again = batch.solve(prm)
+    for a, b in zip(first, again):
+        assert a["n_valid_corr"] == b["n_valid_corr"]
+        assert abs(a["e_total"] - b["e_total"]) <= 1e-5 * a["e_total"]
+
+
+def test_batch_plan_arguments(vd):
+    fr = synth.config1()
+    batch = vd.Batch([_lattice(vd, "all", fr)])
+    for bad in (lambda: batch.set_persistent(3), lambda: batch.set_persistent(-1),
+                lambda: batch.set_wave_share(16)):
+        with pytest.raises(vd.VDError) as e:
+            bad()
+        assert e.value.status == vd.VD_ERR_INVALID_ARG
+    batch.set_persistent(vd.VD_BATCH_WAVES)
+    assert batch.plan()["form"] == "waves"
+    assert batch.groups() == [0] and batch.waves() == 0      # before the first build
+    batch.solve(vd.params(gn_iters=1, cg_iters=4, fixed_association=True, init=vd.VD_INIT_ZERO))
+    assert batch.groups()[0] >= 1 and batch.waves() == 1
