@@ -867,6 +867,10 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
     c.nz = d->nz;
     c.nn = (int)nn;
     c.ld = (int)((nn + 31) / 32 * 32);
+    if (nn * d->nx < (1L << 31) && nn * d->ny < (1L << 31)) {
+        c.mdx = (unsigned)(((1ull << 31) + (unsigned long long)d->nx - 1) / (unsigned long long)d->nx);
+        c.mdy = (unsigned)(((1ull << 31) + (unsigned long long)d->ny - 1) / (unsigned long long)d->ny);
+    }
     c.ox = d->origin[0];
     c.oy = d->origin[1];
     c.oz = d->origin[2];

@@ -24,6 +24,9 @@ constexpr int kThreads = 256;
 struct Ctx {
     // lattice
     int nx, ny, nz, nn, ld;
+    // n / nx and n / ny as (2n m) >> 32 with m = ceil(2^31 / d), exact while n d < 2^31
+    // (set when nn nx and nn ny are below 2^31; 0: integer division)
+    unsigned mdx, mdy;
     float ox, oy, oz, h;
     // frame
     int W, H;
@@ -207,7 +210,15 @@ __device__ __forceinline__ int active_count(const Ctx &c) {
 template <bool kAll>
 __device__ __forceinline__ void neighbours(const Ctx &c, int s, int nb[6]) {
     if (kAll) {
-        const int x = s % c.nx, t = s / c.nx, y = t % c.ny, z = t / c.ny;
+        int t, z;
+        if (c.mdx) {  // multiply-high instead of two integer divisions
+            t = (int)__umulhi(2u * (unsigned)s, c.mdx);
+            z = (int)__umulhi(2u * (unsigned)t, c.mdy);
+        } else {
+            t = s / c.nx;
+            z = t / c.ny;
+        }
+        const int x = s - t * c.nx, y = t - z * c.ny;
         const int pl = c.nx * c.ny;
         nb[0] = x > 0 ? s - 1 : -1;
         nb[1] = x + 1 < c.nx ? s + 1 : -1;
