@@ -371,6 +371,7 @@ struct Grid {
     int btb;     // blocks of the cached-B^T B apply (one warp per occupied cell)
     int btb_build;  // blocks of its build (one warp per 64 samples)
     bool vec4;   // all-nodes lattice with nx % 4 == 0: float4 stencil
+    int assoc;   // blocks of the FP32 association (four lanes per sample)
 };
 
 Grid grids(vd_lattice *L) {
@@ -388,6 +389,7 @@ Grid grids(vd_lattice *L) {
         std::max<long>((round_pow2(std::max(L->n_samples_h, 1)) + 8 * kBtbChunk - 1) / (8 * kBtbChunk), 1),
         (long)kSMs * 8);
     g.vec4 = L->all && (L->c.nx % 4 == 0);
+    g.assoc = blocks_for(4L * round_pow2(std::max(L->n_samples_h, 1)));
     return g;
 }
 
@@ -638,7 +640,7 @@ void enqueue_gn_pre(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int g
     Scal *sc = slot(L, g);
     const int K = P->cg_iters;
     if (!(P->fixed_association && g > 0)) {
-        Lc.go(VD_KC_ASSOCIATE, k_associate<kAll>, gr.samp, kThreads, c, sc);
+        Lc.go(VD_KC_ASSOCIATE, k_associate<kAll>, gr.assoc, kThreads, c, sc);
         // the FP64 re-association runs in the first blocks of the right-hand side's node pass
         Lc.go(VD_KC_RHS, k_rhs_nodes_refine<kAll>, gr.refine + gr.node, kThreads, c, sc, gr.refine);
         Lc.go(VD_KC_RHS, k_cells<kOpRhs, kAll>, gr.cells, kThreads, c, sc, K, 0);
@@ -1175,10 +1177,10 @@ vd_status vd_step_associate(vd_lattice *L, const vd_solve_params *P) {
     const Grid gr = grids(L);
     CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, L->stream));
     if (L->all) {
-        k_associate<true><<<gr.samp, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+        k_associate<true><<<gr.assoc, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
         k_associate_refine<true><<<gr.refine, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
     } else {
-        k_associate<false><<<gr.samp, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
+        k_associate<false><<<gr.assoc, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
         k_associate_refine<false><<<gr.refine, kThreads, 0, L->stream>>>(L->c, slot(L, 0));
     }
     CKL();
@@ -2444,7 +2446,7 @@ void warm_features_enqueue(vd_lattice *L, float *in6) {
     const Ctx c = L->c;
     Scal *s0 = slot(L, 0);
     cudaMemsetAsync(L->scal, 0, 2 * L->scal_stride, st);
-    k_associate<kAll><<<gr.samp, kThreads, 0, st>>>(c, s0);
+    k_associate<kAll><<<gr.assoc, kThreads, 0, st>>>(c, s0);
     k_associate_refine<kAll><<<gr.refine, kThreads, 0, st>>>(c, s0);
     k_fit_rotations<kAll, false><<<gr.node, kThreads, 0, st>>>(c, s0);
     k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, s0, 1, 0);
@@ -2467,7 +2469,7 @@ void warm_select_enqueue(vd_lattice *L, const float *pred) {
     float *bak = L->warm + 9 * (size_t)c.nn;
     k_warm_apply<kAll><<<gr.node, kThreads, 0, st>>>(c, pred, bak);
     k_fit_rotations<kAll, true><<<gr.node, kThreads, 0, st>>>(c, s1);
-    k_associate<kAll><<<gr.samp, kThreads, 0, st>>>(c, s1);
+    k_associate<kAll><<<gr.assoc, kThreads, 0, st>>>(c, s1);
     k_associate_refine<kAll><<<gr.refine, kThreads, 0, st>>>(c, s1);
     k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, s1, 1, 0);
     k_warm_select<kAll><<<gr.node, kThreads, 0, st>>>(c, s0, s1, bak, L->rep_dev + 11);

@@ -754,6 +754,9 @@ __device__ bool associate_sample_f32(const Ctx &c, int i, int &pix, float &w_out
     return associate_finish_f32(c, p4, du, dn, pix, w_out, rec);
 }
 
+// Four lanes per sample: lane k of a quad gathers corners k and k + 4 (u and R), the quad
+// adds its corner sums by shuffles, and lane 0 finishes the association (a sample's
+// 96 gathered values spread over four threads: four times the loads in flight per SM).
 template <bool kAll>
 __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
     pdl_wait();
@@ -761,11 +764,53 @@ __global__ void __launch_bounds__(kThreads) k_associate(Ctx c, Scal *sc) {
     if (sc->skip) return;
     const int n = *c.n_samples;
     int valid = 0, refined = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int q = threadIdx.x & 3;
+    const int nq = (gridDim.x * blockDim.x) >> 2;
+    // the loop bound is the warp's first sample: uniform in the warp (shuffles)
+    const int first = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 2;
+    for (int i0 = first; i0 < n; i0 += nq) {
+        const int i = i0 + ((threadIdx.x & 31) >> 2);
+        const bool has = i < n;
+        V3<float> du{0.f, 0.f, 0.f}, dn{0.f, 0.f, 0.f};
+        float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (has) {
+            const int cl = c.cell[i];
+            const float4 n4 = c.sn[i];
+            p4 = c.sp[i];
+            float f[3];
+            sample_frac_f32(c, i, f);
+            const V3<float> nh{n4.x, n4.y, n4.z};
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int k = q + 4 * h;
+                const int node = corner_node(c, cl, k);
+                const float al = trilinear_weight(f, k);
+                du.x += al * c.u[node];
+                du.y += al * c.u[c.ld + node];
+                du.z += al * c.u[2 * c.ld + node];
+                float Rk[9];
+#pragma unroll
+                for (int e = 0; e < 9; e++) Rk[e] = c.R[e * c.ld + node];
+                const V3<float> rn = rot<float>(Rk, nh);
+                dn.x += al * rn.x;
+                dn.y += al * rn.y;
+                dn.z += al * rn.z;
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            du.x += __shfl_xor_sync(FULL, du.x, o);
+            du.y += __shfl_xor_sync(FULL, du.y, o);
+            du.z += __shfl_xor_sync(FULL, du.z, o);
+            dn.x += __shfl_xor_sync(FULL, dn.x, o);
+            dn.y += __shfl_xor_sync(FULL, dn.y, o);
+            dn.z += __shfl_xor_sync(FULL, dn.z, o);
+        }
+        if (!has || q != 0) continue;
         int pix;
         float w;
         float4 rec;
-        const bool near = associate_sample_f32(c, i, pix, w, rec);
+        const bool near = associate_finish_f32(c, p4, du, dn, pix, w, rec);
         if (near) {  // re-taken in FP64 by k_associate_refine (and counted there)
             c.refine[atomicAdd(&sc->n_refine, 1)] = i;
             refined++;
