@@ -62,6 +62,19 @@ NCU_TRAFFIC = {
 }
 
 
+def batch_roofline(frames, ms_batch):
+    """Algorithmic bytes of every lattice's position steps in one batched solve (GN
+    launches of CG iterations, per iteration 108 B per node and 28 B per sample and pair)
+    over the whole batch's time: a lower bound on the position steps' own rate (the
+    per-lattice stages between them are in the denominator too)."""
+    b = sum(GN * algorithmic_bytes("pcg", int(np.prod(f.dims)), f.C, f.S) for f in frames)
+    gbs = b / (ms_batch * 1e-3) / 1e9
+    peak, kind = peaks()
+    return {"algorithmic_bytes_per_batch": int(b), "achieved_GBps_whole_batch": gbs,
+            "frac_whole_batch": gbs / peak, "peak_GBps": peak, "peak_kind": kind,
+            "note": "denominator: the whole batch (stages included); per wave launch see profiles/k_pcg_wave_batch32.md"}
+
+
 def kernel_source_hash():
     """sha256 prefix of csrc/vd_kernels.cuh with its // comments and the whitespace
     runs removed: the code the counters were taken on, not its commentary."""
@@ -539,6 +552,7 @@ def main():
             "branches": n_streams, "launches_per_batch": B.launch_count(), "tuned_plan": plan,
             "persistent_form_ms": ms_persistent,
             "waves_form_ms": ms_waves, "waves_form": waves_plan,
+            "position_steps_roofline": batch_roofline(bframes, tb),
             "sequential_plain": {"value": world * len(blats) * 1000.0 / ts, "unit": "solves/s", "ms": ts},
             "speedup_vs_plain": ts / tb}
         B.close()

@@ -517,12 +517,27 @@ struct PcgPlan {
     BrickPlan b;
 };
 
+// The kernel form of a plan (the kPad of k_pcg_persistent): 0 exact bricks or contiguous
+// ranges, 1 padded bricks with 16-byte-aligned rows (nx % 4 == 0), 2 padded bricks with
+// unaligned rows (their published vectors in the lattice's pad_vecs)
+int pcg_kpad(const vd_lattice *L, const PcgPlan &pl) {
+    if (!pl.b.by || pl.b.exact) return 0;
+    return L->c.nx % 4 ? 2 : 1;
+}
+
+// plane stride of the padded published vectors of plan pl
+size_t pad_ld(const vd_lattice *L, const PcgPlan &pl) {
+    return (((size_t)pl.b.lx * L->c.ny * L->c.nz) + 31) & ~(size_t)31;
+}
+
 // Whether the position step runs as one persistent cooperative kernel, with how many
 // CTAs and how many slots per CTA: bricks where the cheapest one within the SM count holds
 // at most 1.25x the slots of an even split (a padded brick: at most 2x, and only where an
 // even split is 2,048 slots or more -- on smaller lattices the contiguous ranges measured
-// faster), else contiguous ranges over all SMs.
-bool persistent_plan(vd_lattice *L, int *G, int *chunk, PcgPlan *out = nullptr) {
+// faster), else contiguous ranges over all SMs.  A padded plan with unaligned rows needs
+// the lattice's padded vectors, which ensure_pad allocates outside any capture: until
+// then (want == false) the step is streamed instead.
+bool persistent_plan(vd_lattice *L, int *G, int *chunk, PcgPlan *out = nullptr, bool want = false) {
     if (!L->use_persistent || !L->coop || L->in_batch) return false;
     PcgPlan pl;
     const int N = L->all ? L->c.nn : L->n_active_h;
@@ -543,6 +558,7 @@ bool persistent_plan(vd_lattice *L, int *G, int *chunk, PcgPlan *out = nullptr) 
         pl.G = (N4 + ch - 1) / ch;
         if (pl.G > std::min(L->num_sms, kPcgMaxCtas)) return false;
     }
+    if (!want && pcg_kpad(L, pl) == 2 && !(L->pad_vecs && L->pad_ldp == pad_ld(L, pl))) return false;
     *G = pl.G;
     *chunk = pl.chunk;
     if (out) *out = pl;
@@ -551,18 +567,11 @@ bool persistent_plan(vd_lattice *L, int *G, int *chunk, PcgPlan *out = nullptr) 
 
 unsigned magic_of(int d) { return d > 0 ? (unsigned)(((1ull << 31) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u; }
 
-// The kernel form of a plan (the kPad of k_pcg_persistent): 0 exact bricks or contiguous
-// ranges, 1 padded bricks with 16-byte-aligned rows (nx % 4 == 0), 2 padded bricks with
-// unaligned rows (their published vectors in the lattice's pad_vecs)
-int pcg_kpad(const vd_lattice *L, const PcgPlan &pl) {
-    if (!pl.b.by || pl.b.exact) return 0;
-    return L->c.nx % 4 ? 2 : 1;
-}
 
 // the published vectors of kernel form 2 (allocated, and zeroed once, outside any capture)
 vd_status ensure_pad(vd_lattice *L, const PcgPlan &pl, int kpad) {
     if (kpad != 2) return VD_OK;
-    const size_t ldp = (((size_t)pl.b.lx * L->c.ny * L->c.nz) + 31) & ~(size_t)31;
+    const size_t ldp = pad_ld(L, pl);
     if (L->pad_vecs && L->pad_ldp == ldp) return VD_OK;
     dfree(L, L->pad_vecs);
     L->pad_ldp = 0;
@@ -599,7 +608,6 @@ void launch_persistent(vd_lattice *L, Launcher &Lc, Scal *sc, int K, double tol2
     if (!persistent_plan(L, &G, &chunk, &pl)) return;
     unsigned long long *words = reinterpret_cast<unsigned long long *>(L->pcg_part + (size_t)L->pcg_part_rows * L->num_sms);
     const int kpad = pcg_kpad(L, pl);
-    if (kpad == 2 && !L->pad_vecs) return;  // ensure_pad runs before the capture
     const PcgAux ax = pcg_aux(L, L->pcg_part, words, L->stall_extra, pl, kpad);
     const bool prof = L->prof_class == VD_KC_PCG && L->ev_used + 2 <= (int)L->ev.size();
     cudaMemsetAsync(L->pcg_bar, 0, 4 * sizeof(unsigned), Lc.st);
@@ -716,7 +724,8 @@ vd_status build_graph(vd_lattice *L, const vd_solve_params *P) {
     const Grid gr = grids(L);
     int pG = 0, pch = 0;
     PcgPlan pl;
-    if (persistent_plan(L, &pG, &pch, &pl)) TRY(ensure_pad(L, pl, pcg_kpad(L, pl)));
+    if (persistent_plan(L, &pG, &pch, &pl, true)) TRY(ensure_pad(L, pl, pcg_kpad(L, pl)));
+    persistent_plan(L, &pG, &pch, &pl);
     const int pby = pl.b.by, pbz = pl.b.bz;
     const int caps[6] = {gr.node, gr.samp, gr.cells, L->S * 65536 + pch, pby * 65536 + pbz,
                          gr.btb * 65536 + (L->c.btb ? L->n_occ_h : 0)};
@@ -1271,8 +1280,8 @@ vd_status vd_step_pcg(vd_lattice *L, const vd_solve_params *P, float *delta, int
     Launcher Lc{L, st};
     int pG = 0, pch = 0;
     PcgPlan ppl;
+    if (persistent_plan(L, &pG, &pch, &ppl, true)) TRY(ensure_pad(L, ppl, pcg_kpad(L, ppl)));
     if (persistent_plan(L, &pG, &pch, &ppl)) {
-        TRY(ensure_pad(L, ppl, pcg_kpad(L, ppl)));
         if (L->all) {
             enqueue_rhs<true>(Lc, c, sc, gr, K);
             enqueue_btb<true>(Lc, c, sc, gr, L->n_occ_h);
@@ -1613,6 +1622,12 @@ vd_status batch_build(vd_batch *B, const vd_solve_params *P, int streams, bool l
         if (s != VD_OK) return bfail(B, s, L->err.c_str());
         set_params_ctx(L->c, P);
         refresh_ctx(L);
+        int pG = 0, pch = 0;
+        PcgPlan pl;
+        if (active_nodes(L) >= coop_min && persistent_plan(L, &pG, &pch, &pl, true)) {
+            s = ensure_pad(L, pl, pcg_kpad(L, pl));  // a run-ahead lattice's padded vectors
+            if (s != VD_OK) return bfail(B, s, L->err.c_str());
+        }
     }
     const std::vector<int> order = batch_order(B, largest);
     if (cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
