@@ -86,12 +86,15 @@ def test_batch_needs_frames(vd):
 
 
 @pytest.mark.slow
-def test_batch_run_ahead_persistent_branch(vd):
-    """A 64^3 all-nodes lattice in a batch with small ones, under a plan that makes
-    lattices of at least 2^17 active nodes run ahead with their persistent (cooperative)
-    position step while the others' streamed schedules follow as branches; every lattice
-    of the batch matches the oracle within the parity tolerances."""
-    items = [("all", synth.capsule_frame(W=320, H=240, f=262.5, n=64, seed=9, n_sparse=120)),
+@pytest.mark.parametrize("n", [64, 69])
+def test_batch_run_ahead_persistent_branch(vd, n):
+    """A 64^3 (exact bricks) or 69^3 (padded bricks with unaligned rows, whose padded
+    vectors the batch allocates before its capture) all-nodes lattice in a batch with
+    small ones, under a plan that makes lattices of at least 2^17 active nodes run ahead
+    with their persistent (cooperative) position step while the others' streamed
+    schedules follow as branches; every lattice of the batch matches the oracle within the
+    parity tolerances."""
+    items = [("all", synth.capsule_frame(W=320, H=240, f=262.5, n=n, seed=9, n_sparse=120)),
              ("all", synth.capsule_frame(W=160, H=120, f=131.25, n=24, seed=5, n_sparse=40)),
              ("surface", synth.config1())]
     prm = vd.params(gn_iters=3, cg_iters=10, fixed_association=True, init=vd.VD_INIT_ZERO)
@@ -99,7 +102,8 @@ def test_batch_run_ahead_persistent_branch(vd):
     batch = vd.Batch(lats)
     batch.set_plan(2, True, 1 << 17)
     reps = batch.solve(prm)
-    assert 64 ** 3 >= (1 << 17) > 24 ** 3
+    assert n ** 3 >= (1 << 17) > 24 ** 3
+    assert lats[0].pcg_plan()["padded"] == (1 if n % 4 else 0)
     for (mode, fr), lat, rep in zip(items, lats, reps):
         u, _ = lat.get_warp()
         ref = oracle.Oracle.from_frame(fr, oracle.ACTIVE_ALL if mode == "all" else oracle.ACTIVE_SURFACE)
