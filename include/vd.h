@@ -124,6 +124,21 @@ vd_status vd_get_report(vd_lattice *lat, vd_solve_report *out);
 /* Copy the warp out: disp = u (nx*ny*nz x 3), rot = R (nx*ny*nz x 9, may be NULL). */
 vd_status vd_get_warp(const vd_lattice *lat, float *disp, float *rot, int mem);
 
+/* The same read without waiting for it: on the lattice's stream the warp (after the work
+ * enqueued before, e.g. vd_solve_async) is converted into a readback buffer of the
+ * lattice's own (allocated on the first call), and a second stream of the lattice copies
+ * it to disp / rot (either may be NULL), so that the copy overlaps what the caller
+ * enqueues next (the next frame's vd_set_frame and vd_solve_async, which no longer wait
+ * for it).  mem: VD_MEM_HOST (page-locked buffers, for the copy to run asynchronously)
+ * or VD_MEM_DEVICE.  The buffers hold the warp once vd_get_warp_wait returns; a later
+ * vd_get_warp_async waits on the GPU for the previous copy to finish before it reuses the
+ * readback buffer.  VD_ERR_INVALID_ARG for another mem; VD_ERR_CUDA if a copy cannot be
+ * enqueued. */
+vd_status vd_get_warp_async(vd_lattice *lat, float *disp, float *rot, int mem);
+
+/* Wait until the copies of the last vd_get_warp_async have landed. */
+vd_status vd_get_warp_wait(vd_lattice *lat);
+
 /* Replace the warp (warm start, or resume a sequence): disp may be NULL (u = 0),
  * rot may be NULL (R = I). */
 vd_status vd_set_warp(vd_lattice *lat, const float *disp, const float *rot, int mem);

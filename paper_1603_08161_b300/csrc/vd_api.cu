@@ -49,6 +49,11 @@ struct vd_lattice {
     int precision = VD_PREC_FP32;
     cudaStream_t stream = nullptr;   // caller's (or own) stream: where work is ordered
     cudaStream_t cap = nullptr;      // private stream used for graph capture
+    // asynchronous read of the warp (vd_get_warp_async): a readback buffer (12 x nn
+    // floats), the stream that copies it out, and its events (ready to copy, copied)
+    float *rb = nullptr;
+    cudaStream_t rb_st = nullptr;
+    cudaEvent_t rb_ready = nullptr, rb_done = nullptr;
     bool own_stream = false;
     std::string err;
 
@@ -959,11 +964,18 @@ vd_status vd_create_lattice(const vd_lattice_desc *d, vd_lattice **out) {
 vd_status vd_destroy_lattice(vd_lattice *L) {
     if (!L) return VD_OK;
     if (L->stream) cudaStreamSynchronize(L->stream);
+    if (L->rb_st) cudaStreamSynchronize(L->rb_st);
     if (L->gexec) cudaGraphExecDestroy(L->gexec);
     for (auto &b : L->bufs) cudaFree(b.ptr);
     for (auto e : L->ev) cudaEventDestroy(e);
     if (L->rep_host) cudaFreeHost(L->rep_host);
     if (L->cap) cudaStreamDestroy(L->cap);
+    if (L->rb_st) {
+        cudaStreamSynchronize(L->rb_st);
+        cudaStreamDestroy(L->rb_st);
+    }
+    if (L->rb_ready) cudaEventDestroy(L->rb_ready);
+    if (L->rb_done) cudaEventDestroy(L->rb_done);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     delete L;
     return VD_OK;
@@ -1105,6 +1117,40 @@ vd_status vd_get_warp(const vd_lattice *Lc, float *disp, float *rot, int mem) {
         TRY(download(L, rot, L->staging, sizeof(float) * 9 * (size_t)c.nn, mem));
         CK(cudaStreamSynchronize(st));
     }
+    return VD_OK;
+}
+
+vd_status vd_get_warp_async(vd_lattice *L, float *disp, float *rot, int mem) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (mem != VD_MEM_HOST && mem != VD_MEM_DEVICE) return fail(L, VD_ERR_INVALID_ARG, "bad memory kind");
+    const Ctx &c = L->c;
+    if (!L->rb) {
+        TRY(dalloc(L, &L->rb, 12 * (size_t)c.nn));
+        if (cudaStreamCreateWithFlags(&L->rb_st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L->rb_ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L->rb_done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(L, VD_ERR_CUDA, "readback stream");
+        }
+    }
+    cudaStream_t st = L->stream;
+    // the previous copy is done with the readback buffer before it is written again
+    CK(cudaStreamWaitEvent(st, L->rb_done, 0));
+    if (disp) k_soa_to_aos<<<blocks_for(c.nn), kThreads, 0, st>>>(L->u, 3, c.nn, c.ld, L->rb);
+    if (rot) k_soa_to_aos<<<blocks_for(c.nn), kThreads, 0, st>>>(L->R, 9, c.nn, c.ld, L->rb + 3 * (size_t)c.nn);
+    CKL();
+    CK(cudaEventRecord(L->rb_ready, st));
+    CK(cudaStreamWaitEvent(L->rb_st, L->rb_ready, 0));
+    const cudaMemcpyKind kind = mem == VD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (disp) CK(cudaMemcpyAsync(disp, L->rb, sizeof(float) * 3 * (size_t)c.nn, kind, L->rb_st));
+    if (rot) CK(cudaMemcpyAsync(rot, L->rb + 3 * (size_t)c.nn, sizeof(float) * 9 * (size_t)c.nn, kind, L->rb_st));
+    CK(cudaEventRecord(L->rb_done, L->rb_st));
+    return VD_OK;
+}
+
+vd_status vd_get_warp_wait(vd_lattice *L) {
+    if (!L) return VD_ERR_INVALID_ARG;
+    if (L->rb_done) CK(cudaEventSynchronize(L->rb_done));
     return VD_OK;
 }
 

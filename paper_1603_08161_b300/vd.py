@@ -102,6 +102,8 @@ _SIGS = {
     "vd_profile_read": [_P, _PD, _PI],
     "vd_launch_counts": [_P, ctypes.POINTER(vd_solve_params), _PI, _PI],
     "vd_pcg_plan": [_P, _PI, _PI, _PI, _PI, _PI],
+    "vd_get_warp_async": [_P, _P, _P, _I],
+    "vd_get_warp_wait": [_P],
     "vd_fit_rotations_noalloc": [_I, _I, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P],
     "vd_batch_set_plan": [_P, _I, _I, ctypes.c_longlong],
     "vd_batch_set_persistent": [_P, _I, _I, _I, ctypes.c_float],
@@ -288,6 +290,21 @@ class Lattice:
         if isinstance(R, np.ndarray):
             R = R.reshape(self.nn, 3, 3)
         return u, R
+
+    def get_warp_async(self, out_u, out_R=None):
+        """Enqueue the read of u (and R) into the given arrays without waiting (see
+        vd_get_warp_async): page-locked host tensors or CUDA tensors, kept alive here until
+        get_warp_wait."""
+        pu, mem = _ptr(out_u)
+        pr, mr = _ptr(out_R)
+        if out_R is not None and mr != mem:
+            raise ValueError("u and R must both be host arrays or both CUDA tensors")
+        self._rb_keep = [out_u, out_R]
+        self._check(vd_get_warp_async(self.h, pu, pr, mem))
+
+    def get_warp_wait(self):
+        self._check(vd_get_warp_wait(self.h))
+        self._rb_keep = []
 
     def set_warp(self, u=None, R=None):
         """u (nn, 3) and R (nn, 9) or None: numpy (host) or CUDA tensors (device)."""

@@ -543,3 +543,39 @@ def test_device_pointers_and_async(vd):
     # persistent position step: assoc once + 3 x (rhs 2, pcg 1, rotation 1, energy 1) + report
     # + reset; streamed position step: 4 launches per PCG iteration instead of the 1
     assert per_solve in (1 + 3 * 5 + 1 + 1, 1 + 3 * (3 + 4 * 8 + 3) + 1 + 1) and per_frame > 0
+
+
+def test_get_warp_async_matches_get_warp(vd):
+    """vd_get_warp_async (readback overlapped with the next frame's work) delivers the
+    same warp as vd_get_warp: into page-locked host buffers and device buffers, u alone
+    and u with R, over consecutive frames (the readback buffer reused while the next
+    solve runs)."""
+    import torch
+    fr = FRAMES["ragged"]
+    prm = vd.params(gn_iters=2, cg_iters=6, fixed_association=True)
+    lat = vd.Lattice(fr.dims, fr.origin, fr.spacing)
+    lat.set_frame_from(fr)
+    host = [torch.empty((lat.nn, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    hostR = torch.empty((lat.nn, 9), dtype=torch.float32).pin_memory()
+    dev = torch.empty((lat.nn, 3), dtype=torch.float32, device="cuda:0")
+    got = []
+    for k in range(3):
+        lat.solve_async(prm)
+        lat.report()
+        if k < 2:
+            lat.get_warp_async(host[k])
+        else:
+            lat.get_warp_async(dev, None)
+        u_ref, R_ref = lat.get_warp()          # the warp of this frame, read synchronously
+        got.append(u_ref)
+        lat.get_warp_wait()
+        out = (host[k] if k < 2 else dev).cpu().numpy()
+        assert np.array_equal(out, u_ref)
+    assert not np.array_equal(got[0], got[2])  # the warp moved between the frames
+    lat.get_warp_async(host[0], hostR)
+    lat.get_warp_wait()
+    u_ref, R_ref = lat.get_warp()
+    assert np.array_equal(host[0].numpy(), u_ref)
+    assert np.array_equal(hostR.numpy().reshape(-1, 3, 3), R_ref)
+    with pytest.raises(ValueError):
+        lat.get_warp_async(host[0], dev)      # host and device outputs mixed
