@@ -265,3 +265,26 @@ def test_batch_plan_arguments(vd):
     assert batch.groups() == [0] and batch.waves() == 0      # before the first build
     batch.solve(vd.params(gn_iters=1, cg_iters=4, fixed_association=True, init=vd.VD_INIT_ZERO))
     assert batch.groups()[0] >= 1 and batch.waves() == 1
+
+
+def test_wave_batch_refuses_a_lattice_too_large(vd):
+    """A lattice whose slots do not fit in the SMs' shared memory at one CTA per SM
+    (100^3 all nodes: more than 148 x 6,144 slots) cannot take the wave form: the solve
+    reports VD_ERR_INVALID_ARG and the batch still solves in the branch form."""
+    import torch
+    n = 100
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert n ** 3 > sms * 6144
+    fr = synth.config1()
+    small = _lattice(vd, "all", fr)
+    big = vd.Lattice((n, n, n), fr.origin, 1.0 / n)
+    big.set_frame_from(fr)
+    batch = vd.Batch([small, big])
+    batch.set_persistent(vd.VD_BATCH_WAVES)
+    prm = vd.params(gn_iters=1, cg_iters=2, fixed_association=True, init=vd.VD_INIT_ZERO)
+    with pytest.raises(vd.VDError) as e:
+        batch.solve(prm)
+    assert e.value.status == vd.VD_ERR_INVALID_ARG
+    batch.set_persistent(vd.VD_BATCH_BRANCHES)
+    reps = batch.solve(prm)
+    assert all(r["status"] == vd.VD_OK for r in reps)
