@@ -1830,6 +1830,9 @@ __device__ __forceinline__ float f32_quot(double n, double d) {
 struct NoPost {
     __device__ void operator()(double) const {}
 };
+struct NoWork {
+    __device__ void operator()() const {}
+};
 
 // v > 0 and finite, from its bits
 __device__ __forceinline__ bool pos_finite(double v) {
@@ -1855,17 +1858,23 @@ __device__ __forceinline__ bool le_nonneg(double a, double b) { return __double_
 // the FP32 partials themselves) that sum is the result, read with the barrier word;
 // otherwise every CTA sums `row` itself, in the same order in every CTA.  Either way all
 // CTAs get the same `sum`.  kSynced: the caller has synchronised the CTA since its last
-// write that other CTAs read (block_sum does).  post(sum) runs in thread 0 before the
-// CTA's last __syncthreads here, so what it stores in shared memory is visible to every
-// thread on return.  The scale 2^e of ref is taken for 2^-960 <= ref < 2^961 (the
-// row path otherwise).
-template <bool kSynced = false, typename Post = NoPost>
+// write that other CTAs read (block_sum does).  The thread kLead (lane 0 of its warp; it
+// holds `part` and `ref`) arrives and waits; post(sum) runs in it before the CTA's last
+// __syncthreads here, so what it stores in shared memory is visible to every thread on
+// return.  The other threads run during() while it waits (work that needs neither the
+// sum nor other CTAs' data).  The scale 2^e of ref is taken for 2^-960 <= ref < 2^961
+// (the row path otherwise).
+template <bool kSynced = false, unsigned kLead = 0, typename Post = NoPost, typename During = NoWork>
 __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arrivals, double *row, unsigned long long *word,
-                                            double part, double ref, double &sum, unsigned bid, Post post = Post()) {
+                                            double part, double ref, double &sum, unsigned bid, Post post = Post(),
+                                            During during = During()) {
+    static_assert(kLead % 32 == 0, "the lead thread is lane 0 of its warp");
     __shared__ int s_ok, s_fast;
     __shared__ double s_sum;
     if (!kSynced) __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x != kLead) {
+        during();
+    } else {
         row[bid] = part;  // ordered before the arrival by the release of the atom below
         unsigned long long inc = 1;
         const long long rb = __double_as_longlong(ref);
@@ -1907,18 +1916,19 @@ __device__ __forceinline__ bool grid_reduce(int *err, unsigned G, unsigned arriv
     }
     __syncthreads();
     if (!s_fast) {  // the same decision in every CTA
-        if (threadIdx.x < 32) {
+        if ((threadIdx.x >> 5) == (kLead >> 5)) {
+            const unsigned lane = threadIdx.x & 31u;
             double v[5];
 #pragma unroll
             for (int k = 0; k < 5; k++) {  // all loads in flight before the first add
-                const unsigned b = threadIdx.x + 32u * k;
+                const unsigned b = lane + 32u * k;
                 v[k] = b < G ? __ldcg(row + b) : 0.0;
             }
             double t = (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
-            for (unsigned b = threadIdx.x + 160u; b < G; b += 32) t += __ldcg(row + b);
+            for (unsigned b = lane + 160u; b < G; b += 32) t += __ldcg(row + b);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == kLead) {
                 s_sum = t;
                 post(t);
             }
@@ -1965,14 +1975,15 @@ __device__ __forceinline__ double block_total(float v, double *red) {
 
 // The same sum (FP32 warp sums, FP64 across the warps) for callers in which a
 // __syncthreads separates consecutive calls: no barrier before the warp sums are staged,
-// and one conversion to FP64 per warp sum in warp 0 only.  Valid in thread 0.
+// and one conversion to FP64 per warp sum in warp kWarp only.  Valid in its lane 0.
+template <int kWarp = 0>
 __device__ __forceinline__ double block_sum(float v, float *redf) {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) redf[wid] = v;
     __syncthreads();
     double s = 0.0;
-    if (wid == 0) {
+    if (wid == kWarp) {
         s = lane < (int)(blockDim.x >> 5) ? (double)redf[lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
@@ -2018,11 +2029,13 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
     // Two grid barriers per iteration.  Phase A forms p = z + beta p_old itself (own
     // slots in shared memory; a remote neighbour's from its published z and p_old), so
     // no barrier is needed after the p update:
-    //   A: x += alpha_old p_old and the p update (own), q = 2 w_r L p (stencil warps) |
-    //      samples' J^T J p (other warps)
+    //   A: the p update (own), q = 2 w_r L p (stencil warps) | samples' J^T J p (other
+    //      warps)
     //   -- barrier + sum p.Ap --
     //   B: r -= alpha q, z = Minv r (published), r.z
-    //   -- barrier + sum r.z --
+    //   -- barrier + sum r.z; meanwhile x += alpha p (stencil warps) --
+    // The first thread of the sample warps (kLead) arrives at the barriers and waits, so
+    // that the stencil warps are free to update x during the second wait.
     // p, z / q and Minv of own slots live in shared memory, r and x in tensor memory
     // (each thread keeps the r of the groups it updates in phase B and the x of those it
     // updates in A1).  Global buffers: c.minv (the diagonal on entry, Minv on return),
@@ -2125,6 +2138,8 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
         }
     };
 
+    constexpr unsigned kLead = kPcgStencil;
+    constexpr int kLeadWarp = kPcgStencil / 32;
     const uint32_t t_r = tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + 64u * (uint32_t)(tid >> 7);
     const uint32_t t_x = t_r + kPcgTmemX;
     if (tid == 0) {  // an equal share of the sorted samples
@@ -2206,12 +2221,13 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
     }
     auto published = [&](int gl) -> bool { return (s_pub[gl >> 5] >> (gl & 31)) & 1u; };
     auto touched_group = [&](int gl) -> bool { return (s_touch[gl >> 5] >> (gl & 31)) & 1u; };
-    // The FP64 scalars (rho, the previous p.Ap, tol^2 rho0) live in thread 0, which takes every
-    // decision after a barrier and hands the others alpha or beta (s_ab) and whether to
-    // go on (s_go), through the barrier's last __syncthreads.
+    // The FP64 scalars (rho, the previous p.Ap, tol^2 rho0) live in thread kLead, which takes
+    // every decision after a barrier and hands the others alpha or beta (s_ab) and whether
+    // to go on (s_go), through the barrier's last __syncthreads.
     double sum = 0.0, rho = 0.0, pq_prev = 0.0, thr = 0.0;
     const unsigned arrivals = G + ax.extra;
-    bool ok = grid_reduce<true>(ax.err, G, arrivals, ax.part, ax.words, block_sum(part, redf), 0.0, sum, bid,
+    bool ok = grid_reduce<true, kLead>(ax.err, G, arrivals, ax.part, ax.words, block_sum<kLeadWarp>(part, redf), 0.0,
+                                       sum, bid,
                                 [&](double r0) {
                                     rho = r0;
                                     thr = tol2 * r0;  // the convergence threshold on rho
@@ -2221,44 +2237,28 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
     float beta = 0.f;
     int done = 0;
     int stop = !ok || !s_go;
-    // x += alpha p of an iteration is added by the next iteration's A1, which reads that
-    // p anyway; the last one after the loop
-    float alpha_pend = 0.f;
     for (int it = 0; it < K && !stop; it++) {
         // (a select, not an index into the parameter: no local copy of it)
         const float *__restrict__ pold = (it & 1) ? ax.pbuf[0] : ax.pbuf[1];
         float *__restrict__ pnew = (it & 1) ? ax.pbuf[1] : ax.pbuf[0];
-        const float xa = alpha_pend;
-        alpha_pend = 0.f;
         part = 0.f;
         if (tid < kPcgStencil) {
-            // ---- A1: x += alpha p_old (the previous step; x in tensor memory), p = z +
-            // beta p_old for own slots
+            // ---- A1: p = z + beta p_old for own slots
 #pragma unroll 1
-            for (int k = 0; k < kPcgStencilGroups; k++) {  // whole warps (tensor memory)
-                const int gl = tid + k * kPcgStencil;
-                float4 x3[3];
-                if (xa != 0.f) tmem_ld12(t_x + 12 * k, x3);
-                if (gl < ng) {
-                    const int l = 4 * gl, sp = pslot(l);
-                    const bool pg = published(gl);
-                    const int nv = pg ? gvalid(l) : 0;
+            for (int gl = tid; gl < ng; gl += kPcgStencil) {
+                const int l = 4 * gl, sp = pslot(l);
+                const bool pg = published(gl);
+                const int nv = pg ? gvalid(l) : 0;
 #pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
-                        const float4 zv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
-                        if (xa != 0.f)
-                            x3[a] = make_float4(fmaf(xa, pv.x, x3[a].x), fmaf(xa, pv.y, x3[a].y),
-                                                fmaf(xa, pv.z, x3[a].z), fmaf(xa, pv.w, x3[a].w));
-                        const float4 pn = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y),
-                                                      fmaf(beta, pv.z, zv.z), fmaf(beta, pv.w, zv.w));
-                        *reinterpret_cast<float4 *>(P + a * chunk + l) = pn;
-                        if (pg) pst(pnew + a * ldg + sp, nv, pn);
-                    }
+                for (int a = 0; a < 3; a++) {
+                    const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
+                    const float4 zv = *reinterpret_cast<const float4 *>(Q + a * chunk + l);
+                    const float4 pn = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y),
+                                                  fmaf(beta, pv.z, zv.z), fmaf(beta, pv.w, zv.w));
+                    *reinterpret_cast<float4 *>(P + a * chunk + l) = pn;
+                    if (pg) pst(pnew + a * ldg + sp, nv, pn);
                 }
-                if (xa != 0.f) tmem_st12(t_x + 12 * k, x3);
             }
-            if (xa != 0.f) tmem_wait_st();
             sub_sync(2, kPcgStencil);
             // ---- A2: q = 2 w_r L p into Q
 #pragma unroll 1
@@ -2421,8 +2421,8 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
                 sparse_pairs<kOpApply, kAll, true>(c, pv, Qg, nullptr, bid + G * (kPcgSample - 1 - lt), G * kPcgSample,
                                                    part, pd);
         }
-        ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it,
-                               block_sum(part, redf), pq_prev, sum, bid, [&](double pq) {
+        ok = grid_reduce<true, kLead>(ax.err, G, arrivals, ax.part + (size_t)(K + 1 + it) * G, ax.words + 1 + 2 * it,
+                                      block_sum<kLeadWarp>(part, redf), pq_prev, sum, bid, [&](double pq) {
                                    pq_prev = pq;
                                    s_go = pos_finite(pq);
                                    if (s_go) s_ab = f32_quot(rho, pq);  // alpha
@@ -2433,7 +2433,6 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
             break;
         }
         const float alpha = s_ab;
-        alpha_pend = alpha;
         // ---- B: r -= alpha q; z = Minv r (Q and published); rho' = r.z
         part = 0.f;
 #pragma unroll
@@ -2474,23 +2473,47 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
         }
         tmem_wait_st();
         done = it + 1;
-        ok = grid_reduce<true>(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it,
-                               block_sum(part, redf), rho, sum, bid, [&](double rho1) {
-                                   if (bid == 0) scal_rho(sc)[it + 1] = rho1;
-                                   // go on unless converged (rho1 = r.Minv r >= 0); a next
-                                   // step needs rho1 > 0
-                                   s_go = pos_finite(rho1) && !le_nonneg(rho1, thr);
-                                   if (s_go) s_ab = f32_quot(rho1, rho);  // beta
-                                   rho = rho1;
-                               });
+        // x += alpha p (x in tensor memory; p is this iteration's until the next A1), by
+        // the stencil warps while kLead waits
+        auto x_step = [&]() {
+            if (tid >= kPcgStencil || alpha == 0.f) return;
+#pragma unroll 1
+            for (int k = 0; k < kPcgStencilGroups; k++) {  // whole warps (tensor memory)
+                const int gl = tid + k * kPcgStencil;
+                float4 x3[3];
+                tmem_ld12(t_x + 12 * k, x3);
+                if (gl < ng) {
+                    const int l = 4 * gl;
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
+                        x3[a] = make_float4(fmaf(alpha, pv.x, x3[a].x), fmaf(alpha, pv.y, x3[a].y),
+                                            fmaf(alpha, pv.z, x3[a].z), fmaf(alpha, pv.w, x3[a].w));
+                    }
+                }
+                tmem_st12(t_x + 12 * k, x3);
+            }
+            tmem_wait_st();
+        };
+        ok = grid_reduce<true, kLead>(ax.err, G, arrivals, ax.part + (size_t)(it + 1) * G, ax.words + 2 + 2 * it,
+                                      block_sum<kLeadWarp>(part, redf), rho, sum, bid,
+                                      [&](double rho1) {
+                                          if (bid == 0) scal_rho(sc)[it + 1] = rho1;
+                                          // go on unless converged (rho1 = r.Minv r >= 0);
+                                          // a next step needs rho1 > 0
+                                          s_go = pos_finite(rho1) && !le_nonneg(rho1, thr);
+                                          if (s_go) s_ab = f32_quot(rho1, rho);  // beta
+                                          rho = rho1;
+                                      },
+                                      x_step);
         if (!ok || !s_go) {
             stop = 1;
             break;
         }
         beta = s_ab;
     }
-    // ---- the last step's x += alpha p (every earlier one has passed A1), x to c.x; u += x
-    // when the step is applied
+    // ---- x (every step added during its second barrier) to c.x; u += x when the step is
+    // applied
     if (tid < kPcgStencil) {
 #pragma unroll 1
         for (int k = 0; k < kPcgStencilGroups; k++) {
@@ -2501,9 +2524,7 @@ __device__ __forceinline__ void pcg_persistent_body(const Ctx &c, Scal *sc, cons
             const int l = 4 * gl, s = gslot(l), nv = gvalid(l);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                const float4 pv = *reinterpret_cast<const float4 *>(P + a * chunk + l);
-                const float4 x4 = make_float4(fmaf(alpha_pend, pv.x, x3[a].x), fmaf(alpha_pend, pv.y, x3[a].y),
-                                              fmaf(alpha_pend, pv.z, x3[a].z), fmaf(alpha_pend, pv.w, x3[a].w));
+                const float4 x4 = x3[a];
                 gst(c.x + a * ld + s, nv, x4);
                 if (apply) {
                     const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
