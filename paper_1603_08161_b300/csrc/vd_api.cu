@@ -377,6 +377,7 @@ struct Grid {
     int btb_build;  // blocks of its build (one warp per 64 samples)
     bool vec4;   // all-nodes lattice with nx % 4 == 0: float4 stencil
     int assoc;   // blocks of the FP32 association (four lanes per sample)
+    int fit;     // blocks of the staged rotation step (all-nodes lattices; kFitTile threads)
 };
 
 Grid grids(vd_lattice *L) {
@@ -395,7 +396,16 @@ Grid grids(vd_lattice *L) {
         (long)kSMs * 8);
     g.vec4 = L->all && (L->c.nx % 4 == 0);
     g.assoc = blocks_for(4L * round_pow2(std::max(L->n_samples_h, 1)));
+    g.fit = blocks_for(L->c.nn, kFitTile, 4);
     return g;
+}
+
+// the rotation step (Sec. 7.1) and E_reg on stream st: node data staged in shared memory
+// on an all-nodes lattice
+template <bool kAll, bool kFit>
+void launch_fit_rotations(const Ctx &c, Scal *sc, const Grid &gr, cudaStream_t st) {
+    if (kAll) k_fit_rotations_staged<kFit><<<gr.fit, kFitTile, 0, st>>>(c, sc);
+    else k_fit_rotations<kAll, kFit><<<gr.node, kThreads, 0, st>>>(c, sc);
 }
 
 // Launches the kernels of a schedule on one stream.  Consecutive kernels are chained
@@ -670,7 +680,8 @@ void enqueue_gn_post(Launcher &Lc, vd_lattice *L, const vd_solve_params *P, int 
     const Ctx c = L->c;
     Scal *sc = slot(L, g);
     const int K = P->cg_iters;
-    Lc.go(VD_KC_ROTATION, k_fit_rotations<kAll, true>, gr.node, kThreads, c, sc);
+    if (kAll) Lc.go(VD_KC_ROTATION, k_fit_rotations_staged<true>, gr.fit, kFitTile, c, sc);
+    else Lc.go(VD_KC_ROTATION, k_fit_rotations<kAll, true>, gr.node, kThreads, c, sc);
     // the energies after the update (this iteration's correspondences): for the report
     // after the last iteration, and after every one when the energy target gates the next
     if (c.e_target || g + 1 == P->gn_iters) Lc.go(VD_KC_ENERGY, k_cells<kOpEnergy, kAll>, gr.cells, kThreads, c, sc, K, 0);
@@ -1370,8 +1381,8 @@ vd_status vd_step_fit_rotations(vd_lattice *L, int *n_degenerate) {
     cudaStream_t st = L->stream;
     const Grid gr = grids(L);
     CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, st));
-    if (L->all) k_fit_rotations<true, true><<<gr.node, kThreads, 0, st>>>(L->c, slot(L, 0));
-    else k_fit_rotations<false, true><<<gr.node, kThreads, 0, st>>>(L->c, slot(L, 0));
+    if (L->all) launch_fit_rotations<true, true>(L->c, slot(L, 0), gr, st);
+    else launch_fit_rotations<false, true>(L->c, slot(L, 0), gr, st);
     CKL();
     int d = 0;
     CK(cudaMemcpyAsync(&d, (char *)slot(L, 0) + offsetof(Scal, n_degenerate), sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1388,7 +1399,7 @@ vd_status vd_step_energy(vd_lattice *L, const vd_solve_params *P, double out[4])
     Scal *sc = slot(L, 0);
     CK(cudaMemsetAsync(L->scal, 0, L->scal_stride, st));
     if (L->all) {
-        k_fit_rotations<true, false><<<gr.node, kThreads, 0, st>>>(L->c, sc);
+        launch_fit_rotations<true, false>(L->c, sc, gr, st);
         k_cells<kOpEnergy, true><<<gr.cells, kThreads, 0, st>>>(L->c, sc, 1, 0);
     } else {
         k_fit_rotations<false, false><<<gr.node, kThreads, 0, st>>>(L->c, sc);
@@ -2509,7 +2520,7 @@ void warm_features_enqueue(vd_lattice *L, float *in6) {
     cudaMemsetAsync(L->scal, 0, 2 * L->scal_stride, st);
     k_associate<kAll><<<gr.assoc, kThreads, 0, st>>>(c, s0);
     k_associate_refine<kAll><<<gr.refine, kThreads, 0, st>>>(c, s0);
-    k_fit_rotations<kAll, false><<<gr.node, kThreads, 0, st>>>(c, s0);
+    launch_fit_rotations<kAll, false>(c, s0, gr, st);
     k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, s0, 1, 0);
     Ctx cd = c;
     cd.w_r = 0.f;
@@ -2529,7 +2540,7 @@ void warm_select_enqueue(vd_lattice *L, const float *pred) {
     Scal *s0 = slot(L, 0), *s1 = slot(L, 1);
     float *bak = L->warm + 9 * (size_t)c.nn;
     k_warm_apply<kAll><<<gr.node, kThreads, 0, st>>>(c, pred, bak);
-    k_fit_rotations<kAll, true><<<gr.node, kThreads, 0, st>>>(c, s1);
+    launch_fit_rotations<kAll, true>(c, s1, gr, st);
     k_associate<kAll><<<gr.assoc, kThreads, 0, st>>>(c, s1);
     k_associate_refine<kAll><<<gr.refine, kThreads, 0, st>>>(c, s1);
     k_cells<kOpEnergy, kAll><<<gr.cells, kThreads, 0, st>>>(c, s1, 1, 0);
@@ -2812,8 +2823,8 @@ vd_status vd_hierarchy_solve_async(vd_hierarchy *H, const vd_solve_params *param
         k_prolongate<<<blocks_for(Lf->c.nn), kThreads, 0, st>>>(Ll->c, H->u_start[l], Lf->c);
         cudaMemsetAsync(H->scal, 0, scal_bytes(1), st);
         const Grid gr = grids(Lf);
-        if (Lf->all) k_fit_rotations<true, true><<<gr.node, kThreads, 0, st>>>(Lf->c, H->scal);
-        else k_fit_rotations<false, true><<<gr.node, kThreads, 0, st>>>(Lf->c, H->scal);
+        if (Lf->all) launch_fit_rotations<true, true>(Lf->c, H->scal, gr, st);
+        else launch_fit_rotations<false, true>(Lf->c, H->scal, gr, st);
         if (cudaGetLastError() != cudaSuccess) return hfail(H, VD_ERR_CUDA, "prolongation launch failed");
     }
     H->pending = true;

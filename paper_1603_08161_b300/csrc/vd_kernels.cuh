@@ -3116,6 +3116,93 @@ __device__ __noinline__ double horn_top_eigvec_f64(float Sxx, float Sxy, float S
     return gd;
 }
 
+// The rotation step of one node from A = sum_j (t_i - t_j)(t^_i - t^_j)^T / h^2 (three
+// columns, one per axis; at least two axes present): Horn's quaternion warm-started at
+// the previous rotation Ri, as described above.  Returns true where the node keeps Ri (no
+// certified unique fit); Ri holds the new rotation otherwise.
+__device__ __forceinline__ bool fit_node_rotation(const float (&A)[3][3], float (&Ri)[9]) {
+    // previous rotation usable as a warm start if orthonormal
+    float orth = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float d = Ri[r] * Ri[k] + Ri[3 + r] * Ri[3 + k] + Ri[6 + r] * Ri[6 + k] - (r == k ? 1.f : 0.f);
+            orth = fmaxf(orth, fabsf(d));
+        }
+    const bool warm = orth < 1e-3f;
+    float B[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            B[r][k] = warm ? Ri[r] * A[0][k] + Ri[3 + r] * A[1][k] + Ri[6 + r] * A[2][k] : A[r][k];
+    // Horn's matrix from S = B^T (S_ab = sum_j e_a d_b)
+    const float Sxx = B[0][0], Sxy = B[1][0], Sxz = B[2][0];
+    const float Syx = B[0][1], Syy = B[1][1], Syz = B[2][1];
+    const float Szx = B[0][2], Szy = B[1][2], Szz = B[2][2];
+    float Nm[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
+                      {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
+                      {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
+                      {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
+    float scale = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) scale = fmaxf(scale, fabsf(Nm[r][k]));
+    // fast path: Rayleigh-quotient iteration from the identity (the previous
+    // rotation when warm), certified unique with a gap above 1e-4 of the scale;
+    // otherwise cyclic Jacobi, and FP64 for a near-singular block
+    float qv[4] = {1.f, 0.f, 0.f, 0.f};
+    bool unique = sym4_top_rqi(Nm, qv, 1e-4f * scale, scale);
+    if (!unique) {
+        // the out-of-line solvers get copies, so that the fast path's matrix and
+        // vector never have their address taken (they stay in registers)
+        float Nf[4][4], qf[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            qf[r] = qv[r];
+#pragma unroll
+            for (int k = 0; k < 4; k++) Nf[r][k] = Nm[r][k];
+        }
+        const float gap = horn_top_eigvec_f32(Nf, qf);
+        unique = gap > 1e-5f * scale;
+        if (gap < 1e-4f * scale) {
+            // near-singular block (the rotation's sensitivity exceeds 1e4): polar
+            // decomposition again in FP64
+            const double gd = horn_top_eigvec_f64(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz, qf);
+            unique = gd > 1e-12 * (double)scale;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) qv[r] = qf[r];
+    }
+    if (!unique) return true;
+    float w = qv[0], x = qv[1], y = qv[2], z = qv[3];
+    if (warm) {  // q = q(R0) * q(D)
+        float q0[4];
+        mat_to_quat(Ri, q0);
+        const float w2 = q0[0] * w - q0[1] * x - q0[2] * y - q0[3] * z;
+        const float x2 = q0[0] * x + q0[1] * w + q0[2] * z - q0[3] * y;
+        const float y2 = q0[0] * y - q0[1] * z + q0[2] * w + q0[3] * x;
+        const float z2 = q0[0] * z + q0[1] * y - q0[2] * x + q0[3] * w;
+        w = w2;
+        x = x2;
+        y = y2;
+        z = z2;
+    }
+    const float inv = 1.f / (w * w + x * x + y * y + z * z);
+    Ri[0] = (w * w + x * x - y * y - z * z) * inv;
+    Ri[1] = 2.f * (x * y - w * z) * inv;
+    Ri[2] = 2.f * (x * z + w * y) * inv;
+    Ri[3] = 2.f * (x * y + w * z) * inv;
+    Ri[4] = (w * w - x * x + y * y - z * z) * inv;
+    Ri[5] = 2.f * (y * z - w * x) * inv;
+    Ri[6] = 2.f * (x * z - w * y) * inv;
+    Ri[7] = 2.f * (y * z + w * x) * inv;
+    Ri[8] = (w * w - x * x - y * y + z * z) * inv;
+    return false;
+}
+
 template <bool kAll, bool kFit>
 __global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) {
     pdl_wait();
@@ -3151,87 +3238,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) 
         const bool two_axes = __popc(axes) >= 2;
         bool keep = !two_axes;
         if (kFit && two_axes) {
-            // previous rotation usable as a warm start if orthonormal
-            float orth = 0.f;
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float d = Ri[r] * Ri[k] + Ri[3 + r] * Ri[3 + k] + Ri[6 + r] * Ri[6 + k] - (r == k ? 1.f : 0.f);
-                    orth = fmaxf(orth, fabsf(d));
-                }
-            const bool warm = orth < 1e-3f;
-            float B[3][3];
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int k = 0; k < 3; k++)
-                    B[r][k] = warm ? Ri[r] * A[0][k] + Ri[3 + r] * A[1][k] + Ri[6 + r] * A[2][k] : A[r][k];
-            // Horn's matrix from S = B^T (S_ab = sum_j e_a d_b)
-            const float Sxx = B[0][0], Sxy = B[1][0], Sxz = B[2][0];
-            const float Syx = B[0][1], Syy = B[1][1], Syz = B[2][1];
-            const float Szx = B[0][2], Szy = B[1][2], Szz = B[2][2];
-            float Nm[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
-                              {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
-                              {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
-                              {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
-            float scale = 0.f;
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int k = 0; k < 4; k++) scale = fmaxf(scale, fabsf(Nm[r][k]));
-            // fast path: Rayleigh-quotient iteration from the identity (the previous
-            // rotation when warm), certified unique with a gap above 1e-4 of the scale;
-            // otherwise cyclic Jacobi, and FP64 for a near-singular block
-            float qv[4] = {1.f, 0.f, 0.f, 0.f};
-            bool unique = sym4_top_rqi(Nm, qv, 1e-4f * scale, scale);
-            if (!unique) {
-                // the out-of-line solvers get copies, so that the fast path's matrix and
-                // vector never have their address taken (they stay in registers)
-                float Nf[4][4], qf[4];
-#pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    qf[r] = qv[r];
-#pragma unroll
-                    for (int k = 0; k < 4; k++) Nf[r][k] = Nm[r][k];
-                }
-                const float gap = horn_top_eigvec_f32(Nf, qf);
-                unique = gap > 1e-5f * scale;
-                if (gap < 1e-4f * scale) {
-                    // near-singular block (the rotation's sensitivity exceeds 1e4): polar
-                    // decomposition again in FP64
-                    const double gd = horn_top_eigvec_f64(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz, qf);
-                    unique = gd > 1e-12 * (double)scale;
-                }
-#pragma unroll
-                for (int r = 0; r < 4; r++) qv[r] = qf[r];
-            }
-            if (!unique) {
-                keep = true;
-            } else {
-                float w = qv[0], x = qv[1], y = qv[2], z = qv[3];
-                if (warm) {  // q = q(R0) * q(D)
-                    float q0[4];
-                    mat_to_quat(Ri, q0);
-                    const float w2 = q0[0] * w - q0[1] * x - q0[2] * y - q0[3] * z;
-                    const float x2 = q0[0] * x + q0[1] * w + q0[2] * z - q0[3] * y;
-                    const float y2 = q0[0] * y - q0[1] * z + q0[2] * w + q0[3] * x;
-                    const float z2 = q0[0] * z + q0[1] * y - q0[2] * x + q0[3] * w;
-                    w = w2;
-                    x = x2;
-                    y = y2;
-                    z = z2;
-                }
-                const float inv = 1.f / (w * w + x * x + y * y + z * z);
-                Ri[0] = (w * w + x * x - y * y - z * z) * inv;
-                Ri[1] = 2.f * (x * y - w * z) * inv;
-                Ri[2] = 2.f * (x * z + w * y) * inv;
-                Ri[3] = 2.f * (x * y + w * z) * inv;
-                Ri[4] = (w * w - x * x + y * y - z * z) * inv;
-                Ri[5] = 2.f * (y * z - w * x) * inv;
-                Ri[6] = 2.f * (x * z - w * y) * inv;
-                Ri[7] = 2.f * (y * z + w * x) * inv;
-                Ri[8] = (w * w - x * x - y * y + z * z) * inv;
+            keep = fit_node_rotation(A, Ri);
+            if (!keep) {
 #pragma unroll
                 for (int e = 0; e < 9; e++) c.R[e * c.ld + i] = Ri[e];
             }
@@ -3250,6 +3258,125 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit_rotations(Ctx c, Scal *sc) 
             const float rx = (ui.x - uj.x) + ex, ry = (ui.y - uj.y) + ey, rz = (ui.z - uj.z) + ez;
             part += rx * rx + ry * ry + rz * rz;
         }
+    }
+    block_add_f64(part, &sc->e_reg);
+    block_add_int(degenerate, &sc->n_degenerate);
+}
+
+// The rotation step and E_reg of an all-nodes lattice, node data staged in shared
+// memory.  Each CTA takes batches of kFitTile consecutive nodes (one per thread); for the
+// batch it copies, by cp.async (no registers held while the copies fly), u of the batch's
+// own row segment with one node on either side and of the four segments kFitTile long at
+// -nx, +nx, -nx ny and +nx ny, and R of the batch's nodes, the next batch's copies in
+// flight while the current one is fitted (two stages).  The per-node arithmetic is that
+// of k_fit_rotations, so the rotations are the same to the bit; only the order in which
+// the E_reg terms are summed differs.
+constexpr int kFitTile = 128;                    // nodes per batch (threads per CTA)
+constexpr int kFitSeg = kFitTile + 2;            // the batch's own row segment, one node each side
+constexpr int kFitU = kFitSeg + 4 * kFitTile;    // staged u values per component
+struct FitStage {
+    float u[3][kFitU];   // [0, kFitSeg): nodes s0 - 1 ..; then the -nx, +nx, -plane, +plane segments
+    float R[9][kFitTile];
+};
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// the copies of the batch starting at node s0 (only nodes inside [0, N) are copied)
+__device__ __forceinline__ void fit_stage_issue(const Ctx &c, FitStage &S, int s0, int N) {
+    const int t = threadIdx.x, pl = c.nx * c.ny;
+    const int offs[4] = {-c.nx, c.nx, -pl, pl};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float *ua = c.u + (size_t)a * c.ld;
+        for (int e = t; e < kFitSeg; e += kFitTile) {
+            const int j = s0 - 1 + e;
+            if (j >= 0 && j < N) cp_async4(&S.u[a][e], ua + j);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int j = s0 + offs[k] + t;
+            if (j >= 0 && j < N) cp_async4(&S.u[a][kFitSeg + k * kFitTile + t], ua + j);
+        }
+    }
+    if (s0 + t < N) {
+#pragma unroll
+        for (int e = 0; e < 9; e++) cp_async4(&S.R[e][t], c.R + (size_t)e * c.ld + s0 + t);
+    }
+}
+
+template <bool kFit>
+__global__ void __launch_bounds__(kFitTile, 4) k_fit_rotations_staged(Ctx c, Scal *sc) {
+    __shared__ FitStage S[2];
+    pdl_wait();
+    pdl_trigger();
+    if (sc->skip) return;
+    const int N = c.nn, nbatch = (N + kFitTile - 1) / kFitTile;
+    const int t = threadIdx.x;
+    float part = 0.f;
+    int degenerate = 0;
+    const float ih = 1.f / c.h;
+    int b = blockIdx.x;
+    if (b < nbatch) fit_stage_issue(c, S[0], b * kFitTile, N);
+    cp_async_commit();
+    for (int k = 0; b < nbatch; k++, b += gridDim.x) {
+        if (b + (int)gridDim.x < nbatch) fit_stage_issue(c, S[(k + 1) & 1], (b + gridDim.x) * kFitTile, N);
+        cp_async_commit();
+        cp_async_wait_prev();  // this thread's copies of batch b have landed
+        __syncthreads();       // and every thread's
+        const FitStage &B = S[k & 1];
+        const int i = b * kFitTile + t;
+        if (i < N) {
+            int nb[6];
+            neighbours<true>(c, i, nb);
+            // the stage positions of the node and of its neighbours -x, +x, -y, +y, -z, +z
+            auto at = [&](int d) -> int { return d < 2 ? t + 2 * d : kFitSeg + (d - 2) * kFitTile + t; };
+            const float3 ui = make_float3(B.u[0][t + 1], B.u[1][t + 1], B.u[2][t + 1]);
+            float A[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            int axes = 0;
+#pragma unroll
+            for (int d = 0; d < 6; d++) {
+                if (nb[d] < 0) continue;
+                const int a = d >> 1, q = at(d);
+                axes |= 1 << a;
+                const float3 uj = make_float3(B.u[0][q], B.u[1][q], B.u[2][q]);
+                // column a of A/h^2: e_a + (u_j - u_i)/h for +a, e_a + (u_i - u_j)/h for -a
+                const float sg = (d & 1) ? ih : -ih;
+                A[0][a] += (a == 0 ? 1.f : 0.f) + sg * (uj.x - ui.x);
+                A[1][a] += (a == 1 ? 1.f : 0.f) + sg * (uj.y - ui.y);
+                A[2][a] += (a == 2 ? 1.f : 0.f) + sg * (uj.z - ui.z);
+            }
+            float Ri[9];
+#pragma unroll
+            for (int e = 0; e < 9; e++) Ri[e] = B.R[e][t];
+            const bool two_axes = __popc(axes) >= 2;
+            bool keep = !two_axes;
+            if (kFit && two_axes) {
+                keep = fit_node_rotation(A, Ri);
+                if (!keep) {
+#pragma unroll
+                    for (int e = 0; e < 9; e++) c.R[(size_t)e * c.ld + i] = Ri[e];
+                }
+            }
+            degenerate += kFit && keep;
+            // E_reg terms of the directed edges i -> j: (u_i - u_j) - (R_i - I)(t^_i - t^_j)
+#pragma unroll
+            for (int d = 0; d < 6; d++) {
+                if (nb[d] < 0) continue;
+                const int a = d >> 1, q = at(d);
+                const float sg = (d & 1) ? c.h : -c.h;  // t^_i - t^_j = -sg e_a
+                const float ex = sg * (Ri[a] - (a == 0 ? 1.f : 0.f));
+                const float ey = sg * (Ri[3 + a] - (a == 1 ? 1.f : 0.f));
+                const float ez = sg * (Ri[6 + a] - (a == 2 ? 1.f : 0.f));
+                const float rx = (ui.x - B.u[0][q]) + ex, ry = (ui.y - B.u[1][q]) + ey, rz = (ui.z - B.u[2][q]) + ez;
+                part += rx * rx + ry * ry + rz * rz;
+            }
+        }
+        __syncthreads();  // the stage is refilled by the next batch but one
     }
     block_add_f64(part, &sc->e_reg);
     block_add_int(degenerate, &sc->n_degenerate);
