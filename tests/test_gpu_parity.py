@@ -143,8 +143,9 @@ def test_apply_JtJ(vd, mode, name):
 
 
 @pytest.mark.parametrize("mode", ["all", "surface"])
-def test_fit_rotations_and_energy(vd, mode):
-    fr = FRAMES["cfg1"]
+@pytest.mark.parametrize("name", ["cfg1", "ragged"])
+def test_fit_rotations_and_energy(vd, mode, name):
+    fr = FRAMES[name]
     lat, ref = _pair(vd, fr, mode)
     prm = vd.params()
     u, R = _rand_warp(np.random.default_rng(4), lat.nn, su=0.01)
@@ -164,6 +165,45 @@ def test_fit_rotations_and_energy(vd, mode):
     assert np.abs(Rg[m] - R0[m]).max() < 1e-5
     assert np.abs(np.einsum("nij,nkj->nik", Rg[m], Rg[m]) - np.eye(3)).max() < 1e-5
     np.testing.assert_allclose(lat.energy(prm), ref.energy(), rtol=1e-5)
+
+
+def _rand_warp_fast(rng, nn, su, sr):
+    """_rand_warp without the per-node loop (Rodrigues' formula on all nodes at once)."""
+    u = rng.normal(0, su, (nn, 3)).astype(np.float32)
+    w = rng.normal(0, sr, (nn, 3))
+    th = np.linalg.norm(w, axis=1)
+    k = w / th[:, None]
+    K = np.zeros((nn, 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -k[:, 2], k[:, 1], -k[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = k[:, 2], -k[:, 1], k[:, 0]
+    R = np.eye(3) + np.sin(th)[:, None, None] * K + (1 - np.cos(th))[:, None, None] * (K @ K)
+    return u, R.astype(np.float32)
+
+
+def test_rotation_step_many_batches_per_cta(vd):
+    """The rotation step of an all-nodes lattice stages 128 nodes per batch; at 47 x 45 x
+    43 = 90,945 nodes the 592 CTAs take 711 batches, the last one 65 nodes long, so CTAs
+    run the two-stage copy pipeline over more than one batch and the ragged end.
+    Rotations (Sec. 7.1), the count of nodes that keep theirs, and E_reg (Eq. 4) against
+    the oracle's rotation step on the same warp."""
+    fr = synth.sphere_frame(W=64, H=48, f=60.0, n=(47, 45, 43), seed=11, n_sparse=5, name="many-batches")
+    lat, ref = _pair(vd, fr, "all")
+    prm = vd.params()
+    assert lat.nn == 90945 and lat.nn % 128 == 65
+    h = fr.spacing
+    for call, (su, sr) in enumerate([(0.1 * h, 0.1), (0.05 * h, 0.4)]):
+        u, R = _rand_warp_fast(np.random.default_rng(500 + call), lat.nn, su, sr)
+        lat.set_warp(u, R)
+        ref.set_warp(u.astype(np.float64), R.astype(np.float64))
+        lat.associate(prm)
+        ref.associate()
+        assert lat.fit_rotations() == ref.fit_rotations()
+        _, Rg = lat.get_warp()
+        _, R0 = ref.get_warp()
+        err = np.abs(Rg - R0).max()
+        assert err < 1e-5, f"call {call}: rotation error {err:.3e}"
+        e, e0 = lat.energy(prm), ref.energy()
+        assert abs(e[3] - e0[3]) <= 1e-5 * e0[3], f"call {call}: E_reg {e[3]} vs {e0[3]}"
 
 
 @pytest.mark.parametrize("mode", ["all", "surface"])
