@@ -246,6 +246,29 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_batch(args, vd, synth, stream):
+    """The workload of the batched form's profile: the bench's batch (all nodes, cached
+    B^T B where the tuner of each lattice takes it) in the waves form, two 10 x 20 solves
+    and nothing else, so that a capture of one position-step launch has few launches
+    before it."""
+    import torch
+    prm = vd.params(gn_iters=GN, cg_iters=CG, fixed_association=False, init=vd.VD_INIT_ZERO)
+    lats = []
+    for bf in synth.batch_frames(args.batch, workers=8):
+        Lb = vd.Lattice(bf.dims, bf.origin, bf.spacing, vd.VD_ACTIVE_ALL, stream=stream.cuda_stream)
+        Lb.set_apply_mode(vd.VD_APPLY_AUTO)
+        Lb.set_frame_from(bf)
+        lats.append(Lb)
+    B = vd.Batch(lats)
+    B.set_persistent(vd.VD_BATCH_WAVES)
+    for _ in range(2):
+        B.solve(prm)
+    torch.cuda.synchronize()
+    B.close()
+    for Lb in lats:
+        Lb.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -261,6 +284,9 @@ def main():
                     help="test sequences (seeds 10001..) for the learned warm-start form (0: skip)")
     ap.add_argument("--learned-frames", type=int, default=9)
     ap.add_argument("--hier-levels", type=int, default=3, help="deepest hierarchy tried (1: skip the variant)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="profiling workload only: the batch of --batch lattices in the waves form, solved "
+                         "twice (10 x 20); prints nothing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -275,6 +301,9 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)          # a real stream: the library orders its work on it
     torch.cuda.set_stream(stream)
+    if args.profile_batch:
+        profile_batch(args, vd, synth, stream)
+        return
     fr = synth.config2(seed=rank)
     nn = int(np.prod(fr.dims))
     prm = vd.params(gn_iters=GN, cg_iters=CG, fixed_association=False, init=vd.VD_INIT_ZERO)
