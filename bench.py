@@ -53,6 +53,26 @@ def algorithmic_bytes(kernel, nn, C, S):
     return BYTES_PER_NODE[kernel] * nn
 
 
+def frame_algorithmic_bytes(nn, C, S, W, H, gn=GN, cg=CG):
+    """Algorithmic bytes of one whole frame, each pass counted once (FP32): per CG
+    iteration N*108 + C*28 + S*28 (as the position step); per Gauss-Newton iteration the
+    association C*(24 source sample + 16 lookup + 28 record), the right-hand side N*(12 u
+    + 36 R + 24 b and diagonal) and the rotation step N*(12 u + 36 R); once per frame the
+    energy C*28 + N*48 and the target maps H*W*(4 depth + 24 vertex and normal)."""
+    per_cg = 108 * nn + 28 * C + 28 * S
+    per_gn = cg * per_cg + 68 * C + 72 * nn + 48 * nn
+    return gn * per_gn + 28 * C + 48 * nn + 28 * W * H
+
+
+def frame_roofline(frames_per_s, nn, C, S, W, H, peak_gbs):
+    """The whole frame against the HBM roofline: the frames/s that the measured bandwidth
+    bounds it to (all its algorithmic bytes moved at the peak) and the fraction reached."""
+    b = frame_algorithmic_bytes(nn, C, S, W, H)
+    bound = peak_gbs * 1e9 / b
+    return {"algorithmic_bytes_per_frame": int(b), "bound_frames_per_s": bound,
+            "achieved_GBps": frames_per_s * b / 1e9, "frac": frames_per_s / bound}
+
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture of the kernel, valid only while the kernel source is the one that was captured
 # (kernel_source_hash of csrc/vd_kernels.cuh); see profiles/.
@@ -676,6 +696,7 @@ def main():
                      "traffic": ncu_traffic(rk),
                      "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": avg_s * 1e6,
                      "launches_timed": k_n},
+        "frame_roofline": frame_roofline(value / world, nn, fr.C, fr.S, fr.W, fr.H, peak),
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
